@@ -1,0 +1,233 @@
+"""FP64 CPU oracle of the sparse narrow-band level-set grid (test infrastructure).
+
+Only the tests, the smoke check and the benchmark's CPU baseline use this
+package.  It wraps ``sg_oracle.c`` (plain loops in double precision, see the
+header of that file for the passages each routine follows) through ctypes and
+shares no code with the CUDA library.  Arrays are numpy, package-major with
+64 values per package (in-package index d = i + 4j + 16k).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import types
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sg_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+SPHERE, PLANE, TORUS, PRISM, ROUNDED_BOX = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile sg_oracle.c into liboracle.so next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+                               "-std=c11", "-D_DEFAULT_SOURCE", "-shared", "-fPIC",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Shape(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("centre", C.c_double * 3),
+                ("rot", C.c_double * 9), ("p", C.c_double * 8)]
+
+
+class _Grid(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("dims", C.c_int32 * 3), ("pad", C.c_int32),
+                ("h", C.c_double), ("far_value", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _lib.or_tag.restype = C.c_int64
+        _lib.or_sdf.restype = C.c_double
+        _lib.or_sdf.argtypes = [C.POINTER(_Shape), C.c_double, C.c_double, C.c_double]
+        _lib.or_get_threads.restype = C.c_int
+        for f in ("or_wendland", "or_wendland_dq"):
+            getattr(_lib, f).restype = C.c_double
+            getattr(_lib, f).argtypes = [C.c_double]
+        _lib.or_heaviside.restype = C.c_double
+        _lib.or_heaviside.argtypes = [C.c_double, C.c_double]
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().or_get_threads())
+
+
+def _shape(s) -> _Shape:
+    out = _Shape()
+    out.kind = int(s.kind)
+    out.centre[:] = list(s.centre)
+    out.rot[:] = list(s.rot)
+    out.p[:] = list(s.p)
+    return out
+
+
+def far_value(spec) -> float:
+    """F = 4 lc = 16 h: larger than any active |phi| of the +-2 cell band."""
+    return 16.0 * float(spec.h)
+
+
+def _grid(spec, far=None) -> _Grid:
+    g = _Grid()
+    g.lo[:] = [float(v) for v in spec.lo]
+    g.dims[:] = [int(v) for v in spec.dims]
+    g.h = float(spec.h)
+    g.far_value = far_value(spec) if far is None else float(far)
+    return g
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def sdf(shape, x, y, z):
+    x, y, z = _f64(x), _f64(y), _f64(z)
+    out = np.empty_like(x)
+    lib().or_sdf_many(C.byref(_shape(shape)), C.c_int64(x.size), _p(x), _p(y), _p(z), _p(out))
+    return out
+
+
+def wendland(q):
+    return lib().or_wendland(float(q))
+
+
+def wendland_dq(q):
+    return lib().or_wendland_dq(float(q))
+
+
+def heaviside(z, eps):
+    return lib().or_heaviside(float(z), float(eps))
+
+
+def tag(spec, shape):
+    """Returns (cell_pkg int32[nc], cell_type uint8[nc], P, near_ties)."""
+    nc = spec.n_cells
+    cell_pkg = np.empty(nc, np.int32)
+    cell_type = np.empty(nc, np.uint8)
+    ties = C.c_int64(0)
+    P = lib().or_tag(C.byref(_grid(spec)), C.byref(_shape(shape)), _p(cell_pkg), _p(cell_type), C.byref(ties))
+    return cell_pkg, cell_type, int(P), int(ties.value)
+
+
+def tables(spec, cell_pkg, cell_type, P):
+    """Returns (pkg_cell int32[P], pkg_type uint8[P], nbr int32[P,27])."""
+    pkg_cell = np.empty(P, np.int32)
+    pkg_type = np.empty(P, np.uint8)
+    nbr = np.empty((P, 27), np.int32)
+    lib().or_tables(C.byref(_grid(spec)), _p(np.ascontiguousarray(cell_pkg, np.int32)),
+                    _p(np.ascontiguousarray(cell_type, np.uint8)), C.c_int64(P), _p(pkg_cell), _p(pkg_type),
+                    _p(nbr))
+    return pkg_cell, pkg_type, nbr
+
+
+def init_sdf(spec, shape, P, pkg_cell, far=None):
+    phi = np.empty((P, 64), np.float64)
+    lib().or_init_sdf(C.byref(_grid(spec, far)), C.byref(_shape(shape)), C.c_int64(P),
+                      _p(np.ascontiguousarray(pkg_cell, np.int32)), _p(phi))
+    return phi
+
+
+def gradient(spec, nbr, phi):
+    phi = _f64(phi)
+    P = phi.shape[0]
+    out = [np.empty((P, 64), np.float64) for _ in range(3)]
+    lib().or_gradient(C.byref(_grid(spec)), C.c_int64(P), _p(np.ascontiguousarray(nbr, np.int32)), _p(phi),
+                      *[_p(o) for o in out])
+    return tuple(out)
+
+
+def laplacian(spec, nbr, phi):
+    phi = _f64(phi)
+    P = phi.shape[0]
+    out = np.empty((P, 64), np.float64)
+    lib().or_laplacian(C.byref(_grid(spec)), C.c_int64(P), _p(np.ascontiguousarray(nbr, np.int32)), _p(phi),
+                       _p(out))
+    return out
+
+
+def reinit_s0(spec, phi0):
+    phi0 = _f64(phi0)
+    out = np.empty_like(phi0)
+    lib().or_reinit_s0(C.byref(_grid(spec)), C.c_int64(phi0.shape[0]), _p(phi0), _p(out))
+    return out
+
+
+def reinit_step(spec, nbr, phi0, s0, phi_in, dt):
+    phi0, s0, phi_in = _f64(phi0), _f64(s0), _f64(phi_in)
+    out = np.empty_like(phi_in)
+    lib().or_reinit_step(C.byref(_grid(spec)), C.c_int64(phi_in.shape[0]), _p(np.ascontiguousarray(nbr, np.int32)),
+                         _p(phi0), _p(s0), _p(phi_in), _p(out), C.c_double(dt))
+    return out
+
+
+def reinit(spec, nbr, phi, iterations, cfl):
+    phi = np.array(phi, dtype=np.float64, copy=True, order="C")
+    lib().or_reinit(C.byref(_grid(spec)), C.c_int64(phi.shape[0]), _p(np.ascontiguousarray(nbr, np.int32)),
+                    _p(phi), C.c_int32(iterations), C.c_double(cfl))
+    return phi
+
+
+def kernel_integrals(spec, nbr, phi):
+    phi = _f64(phi)
+    P = phi.shape[0]
+    out = [np.empty((P, 64), np.float64) for _ in range(4)]
+    lib().or_kernel_integrals(C.byref(_grid(spec)), C.c_int64(P), _p(np.ascontiguousarray(nbr, np.int32)),
+                              _p(phi), *[_p(o) for o in out])
+    return tuple(out)
+
+
+def probe(spec, cell_pkg, nbr, fields, x, y, z):
+    """fields: (phi, gx, gy, gz, W, Gx, Gy, Gz); returns (phi, nx, ny, nz, W, Gx, Gy, Gz)."""
+    fs = [_f64(f) for f in fields]
+    x, y, z = (np.ascontiguousarray(v, np.float32) for v in (x, y, z))
+    n = x.size
+    outs = [np.empty(n, np.float64) for _ in range(8)]
+    farr = (C.c_void_p * 8)(*[f.ctypes.data for f in fs])
+    oarr = (C.c_void_p * 8)(*[o.ctypes.data for o in outs])
+    lib().or_probe(C.byref(_grid(spec)), _p(np.ascontiguousarray(cell_pkg, np.int32)),
+                   _p(np.ascontiguousarray(nbr, np.int32)), farr, C.c_int64(n), _p(x), _p(y), _p(z), oarr)
+    return tuple(outs)
+
+
+def morton_keys(spec, x, y, z):
+    x, y, z = (np.ascontiguousarray(v, np.float32) for v in (x, y, z))
+    keys = np.empty(x.size, np.uint64)
+    lib().or_morton_keys(C.byref(_grid(spec)), C.c_int64(x.size), _p(x), _p(y), _p(z), _p(keys))
+    return keys
+
+
+def morton_order(keys):
+    keys = np.ascontiguousarray(keys, np.uint64)
+    order = np.empty(keys.size, np.int64)
+    lib().or_morton_order(C.c_int64(keys.size), _p(keys), _p(order))
+    return order
+
+
+def build_grid(spec, shape, far=None):
+    """Tag, allocate, build tables and initialise phi.  Returns a namespace."""
+    cell_pkg, cell_type, P, ties = tag(spec, shape)
+    pkg_cell, pkg_type, nbr = tables(spec, cell_pkg, cell_type, P)
+    phi = init_sdf(spec, shape, P, pkg_cell, far)
+    return types.SimpleNamespace(spec=spec, shape=shape, P=P, near_ties=ties, cell_pkg=cell_pkg,
+                                 cell_type=cell_type, pkg_cell=pkg_cell, pkg_type=pkg_type, nbr=nbr, phi=phi)

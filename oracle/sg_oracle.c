@@ -1,0 +1,577 @@
+/*
+ * sg_oracle.c -- plain FP64 CPU oracle of the sparse narrow-band level-set grid.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls this code;
+ * it is loaded by the tests, by the smoke check and by the benchmark's CPU
+ * baseline.  It shares no source with the CUDA library.
+ *
+ * Every routine is a literal loop over cells, packages or data points in
+ * double precision, following the paper ("Contiguous Storage of Grid Data for
+ * Heterogeneous Computing", Gu & Hu) where it defines the step, and the
+ * readings listed in the design notes where it is silent:
+ *
+ *   storage, far packages 0/1 ............ "Array Storage and Access"
+ *   package / cell / data index .......... "Indexing"
+ *   27-entry neighbourhood, index shift .. "Neighbourhood", Listing 2
+ *   core / inner tagging, sorting ........ "Initialization Process", steps 1-3
+ *   level-set values, neighbourhood ...... "Initialization Process", steps 4-5
+ *   regularised central difference ....... "Small Feature Cleaning", Listing 5
+ *   kernel integral, trilinear probe ..... "Integral with SPH Smoothing Kernel
+ *                                           and Grid-Particle Coupling"
+ *   Godunov reinitialisation ............. not in the paper; Sussman, Smereka &
+ *                                           Osher (1994) with the Godunov
+ *                                           Hamiltonian of Rouy & Tourin (1992)
+ *   Wendland C2 kernel ................... Wendland (1995)
+ *   Morton order ......................... bit interleave of fine indices
+ *
+ * Package size is 4 per axis; the in-package data index is d = i + 4j + 16k.
+ * Background cell index is c = I + nx (J + ny K).  Package ids 0 and 1 are the
+ * far-field inside (negative) and outside (positive) packages; active packages
+ * follow from id 2 in increasing cell index.
+ *
+ * Compile with -O2 -fopenmp -ffp-contract=off (no fused multiply-add, no
+ * fast-math) so that every float and double operation is a single IEEE op.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define PKG 4
+#define PKG3 64
+
+typedef struct {
+    int32_t kind; /* 0 sphere, 1 plane, 2 torus, 3 prism, 4 rounded box */
+    int32_t pad;
+    double centre[3];
+    double rot[9]; /* row-major, local -> world */
+    double p[8];
+} or_shape;
+
+typedef struct {
+    double lo[3];
+    int32_t dims[3];
+    int32_t pad;
+    double h;         /* fine spacing; coarse cell lc = 4h */
+    double far_value; /* F: far packages hold -F (inside) and +F (outside) */
+} or_grid;
+
+/* ------------------------------------------------------------------------- */
+/* threads                                                                    */
+/* ------------------------------------------------------------------------- */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int or_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------- */
+/* Signed distance functions (negative inside), exact for each primitive.     */
+/* ------------------------------------------------------------------------- */
+static void to_local(const or_shape *s, double x, double y, double z, double q[3]) {
+    double d0 = x - s->centre[0], d1 = y - s->centre[1], d2 = z - s->centre[2];
+    for (int i = 0; i < 3; ++i) q[i] = s->rot[0 * 3 + i] * d0 + s->rot[1 * 3 + i] * d1 + s->rot[2 * 3 + i] * d2;
+}
+
+static double clamp01(double t) { return t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t); }
+
+/* squared distance from (px,py) to the segment a-b */
+static double seg_dist2(double px, double py, double ax, double ay, double bx, double by) {
+    double ex = bx - ax, ey = by - ay, wx = px - ax, wy = py - ay;
+    double t = clamp01((wx * ex + wy * ey) / (ex * ex + ey * ey));
+    double dx = wx - t * ex, dy = wy - t * ey;
+    return dx * dx + dy * dy;
+}
+
+/* exact signed distance to a filled triangle in the plane */
+static double triangle_sdf(double px, double py, const double *t) {
+    double d2 = seg_dist2(px, py, t[0], t[1], t[2], t[3]);
+    double e2 = seg_dist2(px, py, t[2], t[3], t[4], t[5]);
+    double f2 = seg_dist2(px, py, t[4], t[5], t[0], t[1]);
+    if (e2 < d2) d2 = e2;
+    if (f2 < d2) d2 = f2;
+    double orient = (t[2] - t[0]) * (t[5] - t[1]) - (t[3] - t[1]) * (t[4] - t[0]);
+    double c0 = (t[2] - t[0]) * (py - t[1]) - (t[3] - t[1]) * (px - t[0]);
+    double c1 = (t[4] - t[2]) * (py - t[3]) - (t[5] - t[3]) * (px - t[2]);
+    double c2 = (t[0] - t[4]) * (py - t[5]) - (t[1] - t[5]) * (px - t[4]);
+    int inside = (orient > 0.0) ? (c0 > 0.0 && c1 > 0.0 && c2 > 0.0) : (c0 < 0.0 && c1 < 0.0 && c2 < 0.0);
+    return inside ? -sqrt(d2) : sqrt(d2);
+}
+
+double or_sdf(const or_shape *s, double x, double y, double z) {
+    double q[3];
+    to_local(s, x, y, z, q);
+    switch (s->kind) {
+    case 0: /* sphere */
+        return sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) - s->p[0];
+    case 1: /* plane q_z = 0 */
+        return q[2];
+    case 2: { /* torus about local z */
+        double a = sqrt(q[0] * q[0] + q[1] * q[1]) - s->p[0];
+        return sqrt(a * a + q[2] * q[2]) - s->p[1];
+    }
+    case 3: { /* triangle extruded over [p6, p7] */
+        double w0 = triangle_sdf(q[0], q[1], s->p);
+        double zc = 0.5 * (s->p[6] + s->p[7]), hz = 0.5 * (s->p[7] - s->p[6]);
+        double w1 = fabs(q[2] - zc) - hz;
+        double in = w0 > w1 ? w0 : w1;
+        if (in > 0.0) in = 0.0;
+        double a = w0 > 0.0 ? w0 : 0.0, b = w1 > 0.0 ? w1 : 0.0;
+        return in + sqrt(a * a + b * b);
+    }
+    case 4: { /* box with half extents p0..p2 rounded by p3 */
+        double r = s->p[3], o = 0.0, m = -INFINITY;
+        for (int i = 0; i < 3; ++i) {
+            double d = fabs(q[i]) - (s->p[i] - r);
+            if (d > 0.0) o += d * d;
+            if (d > m) m = d;
+        }
+        return sqrt(o) + (m < 0.0 ? m : 0.0) - r;
+    }
+    default:
+        return NAN;
+    }
+}
+
+void or_sdf_many(const or_shape *s, int64_t n, const double *x, const double *y, const double *z, double *out) {
+    for (int64_t i = 0; i < n; ++i) out[i] = or_sdf(s, x[i], y[i], z[i]);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Tagging and package allocation ("Initialization Process", steps 1-3, 5)    */
+/* ------------------------------------------------------------------------- */
+/*
+ * cell_type[c]: 0 far inside, 1 far outside, 2 core, 3 inner.
+ * Core: |d(cell centre)| < lc (1 - 2^-10), the strict "distance less than the
+ *       cell size" test with the threshold moved off exact lattice ties.
+ * Inner: not core and one of the 26 neighbouring cells is core.
+ * Package ids: 2 + number of active cells with a smaller cell index, which is
+ *       the "sorted by spatial location" order with cells in linear order.
+ * Far cells map to package 0 when d < 0 and to package 1 otherwise.
+ * Returns P, the package count including the two far packages.
+ * near_ties receives the number of cells with ||d| - T| < 1e-9 lc, where
+ * float-float evaluation might decide differently.
+ */
+int64_t or_tag(const or_grid *g, const or_shape *s, int32_t *cell_pkg, uint8_t *cell_type, int64_t *near_ties) {
+    const int64_t nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
+    const int64_t nc = nx * ny * nz;
+    const double lc = 4.0 * g->h;
+    const double T = lc * (1.0 - ldexp(1.0, -10));
+    double *d = (double *)malloc(sizeof(double) * (size_t)(nc > 0 ? nc : 1));
+    int64_t ties = 0;
+#pragma omp parallel for schedule(static) reduction(+ : ties)
+    for (int64_t c = 0; c < nc; ++c) {
+        int64_t I = c % nx, J = (c / nx) % ny, K = c / (nx * ny);
+        double x = g->lo[0] + (4.0 * (double)I + 2.0) * g->h;
+        double y = g->lo[1] + (4.0 * (double)J + 2.0) * g->h;
+        double z = g->lo[2] + (4.0 * (double)K + 2.0) * g->h;
+        d[c] = or_sdf(s, x, y, z);
+        cell_type[c] = fabs(d[c]) < T ? 2 : (d[c] < 0.0 ? 0 : 1);
+        if (fabs(fabs(d[c]) - T) < 1e-9 * lc) ties++;
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < nc; ++c) {
+        if (cell_type[c] == 2) continue;
+        int64_t I = c % nx, J = (c / nx) % ny, K = c / (nx * ny);
+        int found = 0;
+        for (int dk = -1; dk <= 1 && !found; ++dk)
+            for (int dj = -1; dj <= 1 && !found; ++dj)
+                for (int di = -1; di <= 1 && !found; ++di) {
+                    int64_t a = I + di, b = J + dj, e = K + dk;
+                    if (a < 0 || b < 0 || e < 0 || a >= nx || b >= ny || e >= nz) continue;
+                    if (cell_type[a + nx * (b + ny * e)] == 2) found = 1;
+                }
+        if (found) cell_type[c] = 3;
+    }
+    int64_t next = 2;
+    for (int64_t c = 0; c < nc; ++c) {
+        if (cell_type[c] >= 2)
+            cell_pkg[c] = (int32_t)next++;
+        else
+            cell_pkg[c] = cell_type[c]; /* 0 inside, 1 outside */
+    }
+    free(d);
+    if (near_ties) *near_ties = ties;
+    return next;
+}
+
+/*
+ * Per-package meta data and neighbourhood ("Initialization Process", step 5;
+ * "Neighbourhood"): nbr[p][n] with n = (di+1) + 3(dj+1) + 9(dk+1) is the
+ * package of cell (I+di, J+dj, K+dk); cells outside the domain map to the
+ * outside far package 1.  The far packages are their own neighbours.
+ * pkg_cell of the far packages is -1.
+ */
+void or_tables(const or_grid *g, const int32_t *cell_pkg, const uint8_t *cell_type, int64_t P, int32_t *pkg_cell,
+               uint8_t *pkg_type, int32_t *nbr) {
+    const int64_t nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
+    const int64_t nc = nx * ny * nz;
+    for (int f = 0; f < 2; ++f) {
+        pkg_cell[f] = -1;
+        pkg_type[f] = (uint8_t)f;
+        for (int n = 0; n < 27; ++n) nbr[f * 27 + n] = f;
+    }
+    for (int64_t c = 0; c < nc; ++c) {
+        int32_t p = cell_pkg[c];
+        if (p < 2) continue;
+        pkg_cell[p] = (int32_t)c;
+        pkg_type[p] = cell_type[c];
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 2; p < P; ++p) {
+        int64_t c = pkg_cell[p];
+        int64_t I = c % nx, J = (c / nx) % ny, K = c / (nx * ny);
+        for (int dk = -1; dk <= 1; ++dk)
+            for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                    int64_t a = I + di, b = J + dj, e = K + dk;
+                    int n = (di + 1) + 3 * (dj + 1) + 9 * (dk + 1);
+                    if (a < 0 || b < 0 || e < 0 || a >= nx || b >= ny || e >= nz)
+                        nbr[p * 27 + n] = 1;
+                    else
+                        nbr[p * 27 + n] = cell_pkg[a + nx * (b + ny * e)];
+                }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Index shift (Listing 2): a shift s per axis in [-4, 7] relative to the     */
+/* package origin selects neighbour n = (s + 4) / 4 and data s + 4 - 4n.      */
+/* Returns the flat index package * 64 + data index.                          */
+/* ------------------------------------------------------------------------- */
+static inline int64_t shift_index(const int32_t *nb, int sx, int sy, int sz) {
+    int nx = (sx + PKG) / PKG, ny = (sy + PKG) / PKG, nz = (sz + PKG) / PKG;
+    int64_t pkg = nb[nx + 3 * ny + 9 * nz];
+    int dx = sx + PKG - nx * PKG, dy = sy + PKG - ny * PKG, dz = sz + PKG - nz * PKG;
+    return pkg * PKG3 + dx + PKG * dy + PKG * PKG * dz;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Level-set values ("Initialization Process", step 4), cell-centred data:   */
+/* x = lo + (4 I + i + 0.5) h.  Far packages hold -F and +F.                  */
+/* ------------------------------------------------------------------------- */
+void or_init_sdf(const or_grid *g, const or_shape *s, int64_t P, const int32_t *pkg_cell, double *phi) {
+    const int64_t nx = g->dims[0], ny = g->dims[1];
+    for (int d = 0; d < PKG3; ++d) {
+        phi[d] = -g->far_value;
+        phi[PKG3 + d] = g->far_value;
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 2; p < P; ++p) {
+        int64_t c = pkg_cell[p];
+        int64_t I = c % nx, J = (c / nx) % ny, K = c / (nx * ny);
+        for (int k = 0; k < PKG; ++k)
+            for (int j = 0; j < PKG; ++j)
+                for (int i = 0; i < PKG; ++i) {
+                    double x = g->lo[0] + ((double)(4 * I + i) + 0.5) * g->h;
+                    double y = g->lo[1] + ((double)(4 * J + j) + 0.5) * g->h;
+                    double z = g->lo[2] + ((double)(4 * K + k) + 0.5) * g->h;
+                    phi[p * PKG3 + i + PKG * j + PKG * PKG * k] = or_sdf(s, x, y, z);
+                }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Regularised central difference (Listing 5), three axes, divided by h:      */
+/* p = phi(+e) - phi(0), m = phi(0) - phi(-e), grad = (p + m) / (2h).         */
+/* Far packages keep a zero gradient.                                         */
+/* ------------------------------------------------------------------------- */
+void or_gradient(const or_grid *g, int64_t P, const int32_t *nbr, const double *phi, double *gx, double *gy,
+                 double *gz) {
+    double *out[3] = {gx, gy, gz};
+    for (int a = 0; a < 3; ++a)
+        for (int d = 0; d < 2 * PKG3; ++d) out[a][d] = 0.0;
+    const double inv2h = 1.0 / (2.0 * g->h);
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 2; p < P; ++p) {
+        const int32_t *nb = nbr + p * 27;
+        for (int k = 0; k < PKG; ++k)
+            for (int j = 0; j < PKG; ++j)
+                for (int i = 0; i < PKG; ++i) {
+                    double c = phi[shift_index(nb, i, j, k)];
+                    for (int a = 0; a < 3; ++a) {
+                        int ex = a == 0, ey = a == 1, ez = a == 2;
+                        double pl = phi[shift_index(nb, i + ex, j + ey, k + ez)] - c;
+                        double mi = c - phi[shift_index(nb, i - ex, j - ey, k - ez)];
+                        out[a][p * PKG3 + i + PKG * j + PKG * PKG * k] = (pl + mi) * inv2h;
+                    }
+                }
+    }
+}
+
+/* 7-point Laplacian: sum over axes of (phi(+e) - 2 phi(0) + phi(-e)) / h^2.  */
+void or_laplacian(const or_grid *g, int64_t P, const int32_t *nbr, const double *phi, double *lap) {
+    for (int d = 0; d < 2 * PKG3; ++d) lap[d] = 0.0;
+    const double inv_h2 = 1.0 / (g->h * g->h);
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 2; p < P; ++p) {
+        const int32_t *nb = nbr + p * 27;
+        for (int k = 0; k < PKG; ++k)
+            for (int j = 0; j < PKG; ++j)
+                for (int i = 0; i < PKG; ++i) {
+                    double c = phi[shift_index(nb, i, j, k)];
+                    double s = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        int ex = a == 0, ey = a == 1, ez = a == 2;
+                        s += phi[shift_index(nb, i + ex, j + ey, k + ez)] - 2.0 * c +
+                             phi[shift_index(nb, i - ex, j - ey, k - ez)];
+                    }
+                    lap[p * PKG3 + i + PKG * j + PKG * PKG * k] = s * inv_h2;
+                }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Reinitialisation (Sussman, Smereka & Osher 1994; Godunov Hamiltonian).     */
+/*   S0 = phi0 / sqrt(phi0^2 + h^2) from phi0 = phi at entry,                 */
+/*   a = D^- phi, b = D^+ phi per axis,                                       */
+/*   phi0 > 0: G = sum max(max(a,0)^2, min(b,0)^2)                            */
+/*   phi0 < 0: G = sum max(min(a,0)^2, max(b,0)^2)                            */
+/*   phi_new = phi - dt S0 (sqrt(G) - 1), dt = cfl h; phi0 = 0: unchanged.    */
+/* Jacobi sweeps; far packages are never changed.                             */
+/* ------------------------------------------------------------------------- */
+void or_reinit_s0(const or_grid *g, int64_t P, const double *phi0, double *s0) {
+    const double h2 = g->h * g->h;
+    for (int64_t i = 0; i < P * PKG3; ++i) s0[i] = phi0[i] / sqrt(phi0[i] * phi0[i] + h2);
+}
+
+void or_reinit_step(const or_grid *g, int64_t P, const int32_t *nbr, const double *phi0, const double *s0,
+                    const double *phi_in, double *phi_out, double dt) {
+    const double inv_h = 1.0 / g->h;
+    for (int d = 0; d < 2 * PKG3; ++d) phi_out[d] = phi_in[d];
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 2; p < P; ++p) {
+        const int32_t *nb = nbr + p * 27;
+        for (int k = 0; k < PKG; ++k)
+            for (int j = 0; j < PKG; ++j)
+                for (int i = 0; i < PKG; ++i) {
+                    int64_t at = p * PKG3 + i + PKG * j + PKG * PKG * k;
+                    double c = phi_in[at];
+                    double G = 0.0;
+                    for (int ax = 0; ax < 3; ++ax) {
+                        int ex = ax == 0, ey = ax == 1, ez = ax == 2;
+                        double a = (c - phi_in[shift_index(nb, i - ex, j - ey, k - ez)]) * inv_h;
+                        double b = (phi_in[shift_index(nb, i + ex, j + ey, k + ez)] - c) * inv_h;
+                        double u, v;
+                        if (phi0[at] > 0.0) {
+                            u = a > 0.0 ? a : 0.0;
+                            v = b < 0.0 ? b : 0.0;
+                        } else {
+                            u = a < 0.0 ? a : 0.0;
+                            v = b > 0.0 ? b : 0.0;
+                        }
+                        G += (u * u > v * v) ? u * u : v * v;
+                    }
+                    if (phi0[at] == 0.0)
+                        phi_out[at] = c;
+                    else
+                        phi_out[at] = c - dt * s0[at] * (sqrt(G) - 1.0);
+                }
+    }
+}
+
+void or_reinit(const or_grid *g, int64_t P, const int32_t *nbr, double *phi, int32_t iterations, double cfl) {
+    size_t n = (size_t)(P * PKG3);
+    double *phi0 = (double *)malloc(n * sizeof(double));
+    double *s0 = (double *)malloc(n * sizeof(double));
+    double *tmp = (double *)malloc(n * sizeof(double));
+    memcpy(phi0, phi, n * sizeof(double));
+    or_reinit_s0(g, P, phi0, s0);
+    double *a = phi, *b = tmp;
+    for (int32_t it = 0; it < iterations; ++it) {
+        or_reinit_step(g, P, nbr, phi0, s0, a, b, cfl * g->h);
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    if (a != phi) memcpy(phi, a, n * sizeof(double));
+    free(phi0);
+    free(s0);
+    free(tmp);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Kernel integrals ("Integral with SPH Smoothing Kernel"):                   */
+/*   Wendland C2, support 2h:  w(q) = (1 - q/2)^4 (1 + 2q) for q < 2, else 0  */
+/*                             w'(q) = -5 q (1 - q/2)^3                       */
+/*   smoothed Heaviside, eps = h: H(z) = 0 (z < -eps), 1 (z > eps),           */
+/*                             1/2 (1 + z/eps + sin(pi z / eps) / pi) between */
+/*   W  = sum_s w(|s|) H(-phi(x + s h)) / sum_s w(|s|)                        */
+/*   G^ = h grad W = sum_s w'(|s|) (-s/|s|) H(-phi(x + s h)) / sum_s w(|s|)   */
+/* summed over all 125 offsets s in {-2..2}^3 (taps at |s| >= 2 weigh 0).     */
+/* Far packages: W = 1 inside, 0 outside; G^ = 0.                             */
+/* ------------------------------------------------------------------------- */
+double or_wendland(double q) {
+    if (q >= 2.0) return 0.0;
+    double t = 1.0 - 0.5 * q;
+    return t * t * t * t * (1.0 + 2.0 * q);
+}
+
+double or_wendland_dq(double q) {
+    if (q >= 2.0) return 0.0;
+    double t = 1.0 - 0.5 * q;
+    return -5.0 * q * t * t * t;
+}
+
+double or_heaviside(double z, double eps) {
+    if (z < -eps) return 0.0;
+    if (z > eps) return 1.0;
+    return 0.5 * (1.0 + z / eps + sin(M_PI * z / eps) / M_PI);
+}
+
+void or_kernel_integrals(const or_grid *g, int64_t P, const int32_t *nbr, const double *phi, double *W, double *Gx,
+                         double *Gy, double *Gz) {
+    const double eps = g->h;
+    for (int d = 0; d < PKG3; ++d) {
+        W[d] = 1.0;
+        W[PKG3 + d] = 0.0;
+        Gx[d] = Gy[d] = Gz[d] = 0.0;
+        Gx[PKG3 + d] = Gy[PKG3 + d] = Gz[PKG3 + d] = 0.0;
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 2; p < P; ++p) {
+        const int32_t *nb = nbr + p * 27;
+        for (int k = 0; k < PKG; ++k)
+            for (int j = 0; j < PKG; ++j)
+                for (int i = 0; i < PKG; ++i) {
+                    double num = 0.0, den = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+                    for (int sz = -2; sz <= 2; ++sz)
+                        for (int sy = -2; sy <= 2; ++sy)
+                            for (int sx = -2; sx <= 2; ++sx) {
+                                double q = sqrt((double)(sx * sx + sy * sy + sz * sz));
+                                double w = or_wendland(q);
+                                double H = or_heaviside(-phi[shift_index(nb, i + sx, j + sy, k + sz)], eps);
+                                num += w * H;
+                                den += w;
+                                if (q > 0.0) {
+                                    double dw = or_wendland_dq(q) * H / q;
+                                    gx += dw * (double)(-sx);
+                                    gy += dw * (double)(-sy);
+                                    gz += dw * (double)(-sz);
+                                }
+                            }
+                    int64_t at = p * PKG3 + i + PKG * j + PKG * PKG * k;
+                    W[at] = num / den;
+                    Gx[at] = gx / den;
+                    Gy[at] = gy / den;
+                    Gz[at] = gz / den;
+                }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Particle probe ("Grid-Particle Coupling"): trilinear interpolation.        */
+/* The fine lattice coordinate is decided in float32 exactly as the device    */
+/* does it:  u = (x - (float)lo) / (float)h - 0.5f, clamped to +-2^24,        */
+/* i0 = floor(u).  Home cell I = floor(i0 / 4), local l0 = i0 - 4I.  Corners  */
+/* l0 + {0,1} are reached from the home package by the index shift; a home    */
+/* cell outside the domain is the outside far package.  Weights t = u - i0.   */
+/* Outputs (in input order): phi, normal n = g/|g| (0 when |g| = 0), W, G^.   */
+/* ------------------------------------------------------------------------- */
+static void lattice(const or_grid *g, int a, float x, int64_t *i0, double *t) {
+    float lo = (float)g->lo[a], h = (float)g->h;
+    float u = (x - lo) / h - 0.5f;
+    const float lim = 16777216.0f;
+    if (u < -lim) u = -lim;
+    if (u > lim) u = lim;
+    float f = floorf(u);
+    *i0 = (int64_t)f;
+    *t = (double)u - (double)f;
+}
+
+void or_probe(const or_grid *g, const int32_t *cell_pkg, const int32_t *nbr, const double *const fields[8], int64_t n,
+              const float *x, const float *y, const float *z, double *const out[8]) {
+    /* fields: phi, gx, gy, gz, W, Gx, Gy, Gz (package-major, 64 per package)
+       out:    phi, nx, ny, nz, W, Gx, Gy, Gz */
+    const int64_t nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t i0[3];
+        double t[3];
+        lattice(g, 0, x[q], &i0[0], &t[0]);
+        lattice(g, 1, y[q], &i0[1], &t[1]);
+        lattice(g, 2, z[q], &i0[2], &t[2]);
+        int64_t I[3];
+        int l0[3];
+        for (int a = 0; a < 3; ++a) {
+            I[a] = i0[a] >= 0 ? i0[a] / 4 : -((-i0[a] + 3) / 4);
+            l0[a] = (int)(i0[a] - 4 * I[a]);
+        }
+        int64_t home = 1;
+        if (I[0] >= 0 && I[1] >= 0 && I[2] >= 0 && I[0] < nx && I[1] < ny && I[2] < nz)
+            home = cell_pkg[I[0] + nx * (I[1] + ny * I[2])];
+        const int32_t *nb = nbr + home * 27;
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int c = 0; c < 8; ++c) {
+            int a0 = c & 1, a1 = (c >> 1) & 1, a2 = (c >> 2) & 1;
+            double w = (a0 ? t[0] : 1.0 - t[0]) * (a1 ? t[1] : 1.0 - t[1]) * (a2 ? t[2] : 1.0 - t[2]);
+            int64_t at = shift_index(nb, l0[0] + a0, l0[1] + a1, l0[2] + a2);
+            for (int f = 0; f < 8; ++f) acc[f] += w * fields[f][at];
+        }
+        double gn = sqrt(acc[1] * acc[1] + acc[2] * acc[2] + acc[3] * acc[3]);
+        out[0][q] = acc[0];
+        for (int a = 0; a < 3; ++a) out[1 + a][q] = gn > 0.0 ? acc[1 + a] / gn : 0.0;
+        for (int f = 4; f < 8; ++f) out[f][q] = acc[f];
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Morton order of particles: key = interleave of k_a = clamp(i0_a + 1, 0,    */
+/* 2^21 - 1), 21 bits per axis, x in the lowest bit; order = stable sort by   */
+/* (key, input index).                                                        */
+/* ------------------------------------------------------------------------- */
+void or_morton_keys(const or_grid *g, int64_t n, const float *x, const float *y, const float *z, uint64_t *keys) {
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < n; ++q) {
+        const float *src[3] = {x, y, z};
+        uint64_t k[3];
+        for (int a = 0; a < 3; ++a) {
+            int64_t i0;
+            double t;
+            lattice(g, a, src[a][q], &i0, &t);
+            int64_t v = i0 + 1;
+            if (v < 0) v = 0;
+            if (v > (1 << 21) - 1) v = (1 << 21) - 1;
+            k[a] = (uint64_t)v;
+        }
+        uint64_t key = 0;
+        for (int b = 0; b < 21; ++b)
+            for (int a = 0; a < 3; ++a) key |= ((k[a] >> b) & 1ull) << (3 * b + a);
+        keys[q] = key;
+    }
+}
+
+typedef struct {
+    uint64_t key;
+    int64_t idx;
+} or_kv;
+
+static int kv_cmp(const void *pa, const void *pb) {
+    const or_kv *a = (const or_kv *)pa, *b = (const or_kv *)pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return a->idx < b->idx ? -1 : (a->idx > b->idx ? 1 : 0);
+}
+
+void or_morton_order(int64_t n, const uint64_t *keys, int64_t *order) {
+    or_kv *kv = (or_kv *)malloc(sizeof(or_kv) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        kv[i].key = keys[i];
+        kv[i].idx = i;
+    }
+    qsort(kv, (size_t)n, sizeof(or_kv), kv_cmp);
+    for (int64_t i = 0; i < n; ++i) order[i] = kv[i].idx;
+    free(kv);
+}

@@ -1,0 +1,341 @@
+"""Seeded synthetic inputs shared by the CPU oracle and the CUDA library.
+
+This module holds no arithmetic of the sparse-grid method itself: no signed
+distance evaluation, tagging, stencil or interpolation.  It only produces
+*inputs*: shape descriptors, grid descriptors, random bodies and particle
+positions, all drawn from one counter-based generator (SplitMix64, Steele,
+Lea & Flood 2014) so that both sides see bit-identical data.
+
+Shapes are described in a local frame: a world point x maps to the local
+point q = R^T (x - centre), where ``rot`` is R stored row-major (local to
+world).  Kinds and their parameter vector ``p``:
+
+* SPHERE       p[0] = radius
+* PLANE        the plane q_z = 0 (normal = third column of R); no parameters
+* TORUS        p[0] = major radius (about the local z axis), p[1] = minor radius
+* PRISM        p[0:6] = triangle (ax, ay, bx, by, cx, cy) in the local xy
+               plane, extruded over q_z in [p[6], p[7]]
+* ROUNDED_BOX  p[0:3] = half extents, p[3] = rounding radius
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SPHERE, PLANE, TORUS, PRISM, ROUNDED_BOX = 0, 1, 2, 3, 4
+KIND_NAMES = {SPHERE: "sphere", PLANE: "plane", TORUS: "torus", PRISM: "prism",
+              ROUNDED_BOX: "rounded_box"}
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+# ----------------------------------------------------------------------------
+# Generator
+# ----------------------------------------------------------------------------
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """n outputs of SplitMix64 started at state ``seed``, skipping ``offset``.
+
+    Counter form of the published generator: output k is mix(seed + (k+1)*gamma)
+    with the two xor-shift-multiply rounds of Steele, Lea & Flood (2014).
+    """
+    with np.errstate(over="ignore"):
+        k = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + k * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+class Stream:
+    """Sequential view over one SplitMix64 sequence."""
+
+    def __init__(self, seed: int):
+        self.seed = int(seed)
+        self.pos = 0
+
+    def u64(self, n: int) -> np.ndarray:
+        out = splitmix64(self.seed, n, self.pos)
+        self.pos += n
+        return out
+
+    def uniform(self, n: int) -> np.ndarray:
+        """Floats in [0, 1) from the top 24 bits (exact in float32)."""
+        return (self.u64(n) >> np.uint64(40)).astype(np.float64) * (1.0 / (1 << 24))
+
+    def uniform53(self, n: int) -> np.ndarray:
+        """Doubles in [0, 1) from the top 53 bits."""
+        return (self.u64(n) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
+# ----------------------------------------------------------------------------
+# Descriptors
+# ----------------------------------------------------------------------------
+@dataclasses.dataclass
+class Shape:
+    kind: int
+    centre: tuple = (0.0, 0.0, 0.0)
+    rot: tuple = (1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0)
+    p: tuple = (0.0,) * 8
+
+    def __post_init__(self):
+        self.centre = tuple(float(v) for v in self.centre)
+        self.rot = tuple(float(v) for v in self.rot)
+        p = [float(v) for v in self.p] + [0.0] * 8
+        self.p = tuple(p[:8])
+
+
+@dataclasses.dataclass
+class GridSpec:
+    """Background mesh: dims coarse cells of size lc = 4h starting at lo."""
+    lo: tuple
+    dims: tuple
+    h: float
+
+    @property
+    def lc(self) -> float:
+        return 4.0 * self.h
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.dims[0]) * int(self.dims[1]) * int(self.dims[2])
+
+    def hi(self):
+        return tuple(self.lo[a] + self.dims[a] * self.lc for a in range(3))
+
+
+def sphere(radius, centre=(0.0, 0.0, 0.0), rot=None) -> Shape:
+    return Shape(SPHERE, centre, rot or Shape(SPHERE).rot, (radius,))
+
+
+def plane(normal, point=(0.0, 0.0, 0.0)) -> Shape:
+    """Plane through ``point`` whose local z axis is the unit ``normal``."""
+    n = np.asarray(normal, dtype=np.float64)
+    n = n / np.linalg.norm(n)
+    a = np.array([1.0, 0.0, 0.0]) if abs(n[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    e1 = a - n * np.dot(a, n)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(n, e1)
+    R = np.stack([e1, e2, n], axis=1)  # columns: local axes in world frame
+    return Shape(PLANE, point, tuple(R.reshape(-1)), ())
+
+
+def torus(major, minor, centre=(0.0, 0.0, 0.0), rot=None) -> Shape:
+    return Shape(TORUS, centre, rot or Shape(TORUS).rot, (major, minor))
+
+
+def prism(tri, z0, z1, centre=(0.0, 0.0, 0.0), rot=None) -> Shape:
+    (ax, ay), (bx, by), (cx, cy) = tri
+    return Shape(PRISM, centre, rot or Shape(PRISM).rot, (ax, ay, bx, by, cx, cy, z0, z1))
+
+
+def rounded_box(half, rounding, centre=(0.0, 0.0, 0.0), rot=None) -> Shape:
+    return Shape(ROUNDED_BOX, centre, rot or Shape(ROUNDED_BOX).rot,
+                 (half[0], half[1], half[2], rounding))
+
+
+def quat_to_rot(q) -> tuple:
+    """Row-major rotation matrix of the unit quaternion (w, x, y, z)."""
+    w, x, y, z = q
+    return (1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+            2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+            2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y))
+
+
+def random_rotation(stream: Stream) -> tuple:
+    """Uniform random rotation (Shoemake 1992, 'Uniform random rotations')."""
+    u1, u2, u3 = stream.uniform53(3)
+    a, b = math.sqrt(1.0 - u1), math.sqrt(u1)
+    t2, t3 = 2.0 * math.pi * u2, 2.0 * math.pi * u3
+    q = (b * math.cos(t3), a * math.sin(t2), a * math.cos(t2), b * math.sin(t3))
+    return quat_to_rot(q)
+
+
+# ----------------------------------------------------------------------------
+# Named workloads
+# ----------------------------------------------------------------------------
+def _box_grid(lo, hi, h) -> GridSpec:
+    lc = 4.0 * h
+    dims = tuple(int(round((hi[a] - lo[a]) / lc)) for a in range(3))
+    return GridSpec(tuple(float(v) for v in lo), dims, float(h))
+
+
+def sphere_small():
+    """Unit sphere at the origin in [-1.5, 1.5]^3 with h = 0.05 (15^3 cells)."""
+    return sphere(1.0), _box_grid((-1.5,) * 3, (1.5,) * 3, 0.05)
+
+
+def torus_large(h=0.002):
+    """Torus R = 0.6, r = 0.2 about z in [-1,1]^2 x [-0.4,0.4]."""
+    return torus(0.6, 0.2), _box_grid((-1.0, -1.0, -0.4), (1.0, 1.0, 0.4), h)
+
+
+PRISM_TRIANGLE = ((0.0, 0.0), (1.0, 0.0), (0.3, 0.8))
+
+
+def prism_large(h=0.002):
+    """Triangle (0,0),(1,0),(0.3,0.8) extruded over z in [0,1]."""
+    return (prism(PRISM_TRIANGLE, 0.0, 1.0),
+            _box_grid((-0.2, -0.2, -0.2), (1.2, 1.0, 1.2), h))
+
+
+# ----------------------------------------------------------------------------
+# Particle samplers (geometric sampling from shape parameters only)
+# ----------------------------------------------------------------------------
+def _unit_dirs(stream: Stream, n: int) -> np.ndarray:
+    """Uniform directions: z uniform in [-1,1], azimuth uniform (Archimedes)."""
+    z = 2.0 * stream.uniform53(n) - 1.0
+    t = 2.0 * math.pi * stream.uniform53(n)
+    s = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return np.stack([s * np.cos(t), s * np.sin(t), z], axis=1)
+
+
+def sphere_shell_particles(n, radius, half_width, centre=(0.0, 0.0, 0.0), seed=0):
+    """n points uniform in the shell radius-half_width < |x-c| < radius+half_width.
+
+    For a sphere this shell is exactly the set |phi| < half_width.
+    Returns float32 arrays x, y, z.
+    """
+    st = Stream(seed)
+    d = _unit_dirs(st, n)
+    r0, r1 = radius - half_width, radius + half_width
+    r = np.cbrt(r0 ** 3 + st.uniform53(n) * (r1 ** 3 - r0 ** 3))
+    pts = d * r[:, None] + np.asarray(centre)[None, :]
+    return tuple(np.ascontiguousarray(pts[:, a], dtype=np.float32) for a in range(3))
+
+
+def torus_band_particles(n, major, minor, half_width, seed=0, jitter=0.0):
+    """n points uniform in the tube minor-w < dist(x, core circle) < minor+w.
+
+    The volume element rho (major + rho cos v) drho dv du of the tube is sampled
+    exactly: rho with density ~ rho, then acceptance (major + rho cos v)/(major + rho_max).
+    Optional uniform jitter in [-jitter, jitter)^3 is added afterwards.
+    """
+    st = Stream(seed)
+    out = []
+    got = 0
+    r0, r1 = minor - half_width, minor + half_width
+    while got < n:
+        m = int((n - got) * 1.4) + 1024
+        rho = np.sqrt(r0 * r0 + st.uniform53(m) * (r1 * r1 - r0 * r0))
+        v = 2.0 * math.pi * st.uniform53(m)
+        u = 2.0 * math.pi * st.uniform53(m)
+        acc = st.uniform53(m) * (major + r1) < (major + rho * np.cos(v))
+        rho, v, u = rho[acc], v[acc], u[acc]
+        s = major + rho * np.cos(v)
+        pts = np.stack([s * np.cos(u), s * np.sin(u), rho * np.sin(v)], axis=1)
+        out.append(pts)
+        got += len(pts)
+    pts = np.concatenate(out)[:n]
+    if jitter > 0:
+        pts = pts + (2.0 * st.uniform53(3 * n).reshape(n, 3) - 1.0) * jitter
+    return tuple(np.ascontiguousarray(pts[:, a], dtype=np.float32) for a in range(3))
+
+
+def prism_band_particles(n, tri, z0, z1, half_width, seed=0, jitter=0.0):
+    """n points near the surface of an extruded triangle.
+
+    A face is picked with probability proportional to its area (three side
+    rectangles, two caps), a point uniform on that face, then an offset along
+    the face normal uniform in [-half_width, half_width), then optional jitter.
+    """
+    st = Stream(seed)
+    P = np.asarray(tri, dtype=np.float64)
+    L = z1 - z0
+    # orientation of the triangle (sign of twice its area)
+    area2 = (P[1, 0] - P[0, 0]) * (P[2, 1] - P[0, 1]) - (P[1, 1] - P[0, 1]) * (P[2, 0] - P[0, 0])
+    orient = 1.0 if area2 > 0 else -1.0
+    edges = [(P[i], P[(i + 1) % 3]) for i in range(3)]
+    areas = [np.linalg.norm(b - a) * L for a, b in edges] + [abs(area2) / 2] * 2
+    cum = np.cumsum(areas) / np.sum(areas)
+    f = np.searchsorted(cum, st.uniform53(n), side="right")
+    a_, b_ = st.uniform53(n), st.uniform53(n)
+    t = (2.0 * st.uniform53(n) - 1.0) * half_width
+    pts = np.zeros((n, 3))
+    for k, (a, b) in enumerate(edges):
+        m = f == k
+        e = b - a
+        nrm = np.array([e[1], -e[0]]) * orient / np.linalg.norm(e)  # outward
+        xy = a[None, :] + a_[m, None] * e[None, :] + t[m, None] * nrm[None, :]
+        pts[m, 0:2] = xy
+        pts[m, 2] = z0 + b_[m] * L
+    for k, (zc, sgn) in ((3, (z0, -1.0)), (4, (z1, 1.0))):
+        m = f == k
+        s, r = a_[m], b_[m]
+        flip = s + r > 1.0
+        s = np.where(flip, 1.0 - s, s)
+        r = np.where(flip, 1.0 - r, r)
+        xy = P[0][None, :] + s[:, None] * (P[1] - P[0])[None, :] + r[:, None] * (P[2] - P[0])[None, :]
+        pts[m, 0:2] = xy
+        pts[m, 2] = zc + sgn * t[m]
+    if jitter > 0:
+        pts = pts + (2.0 * st.uniform53(3 * n).reshape(n, 3) - 1.0) * jitter
+    return tuple(np.ascontiguousarray(pts[:, a], dtype=np.float32) for a in range(3))
+
+
+def box_particles(n, lo, hi, seed=0):
+    """n points uniform in the axis-aligned box [lo, hi)."""
+    st = Stream(seed)
+    u = st.uniform53(3 * n).reshape(3, n)
+    return tuple(np.ascontiguousarray(lo[a] + u[a] * (hi[a] - lo[a]), dtype=np.float32)
+                 for a in range(3))
+
+
+# ----------------------------------------------------------------------------
+# Random bodies (batched workloads)
+# ----------------------------------------------------------------------------
+def shape_area(s: Shape) -> float:
+    """Closed-form surface area of a shape (used only to pick a spacing)."""
+    if s.kind == SPHERE:
+        return 4.0 * math.pi * s.p[0] ** 2
+    if s.kind == TORUS:
+        return 4.0 * math.pi ** 2 * s.p[0] * s.p[1]
+    if s.kind == ROUNDED_BOX:
+        a, b, c, r = (s.p[0] - s.p[3], s.p[1] - s.p[3], s.p[2] - s.p[3], s.p[3])
+        return 8 * (a * b + b * c + a * c) + 4 * math.pi * r * (a + b + c) + 4 * math.pi * r * r
+    raise ValueError("area not defined for kind %d" % s.kind)
+
+
+def bounding_radius(s: Shape) -> float:
+    if s.kind == SPHERE:
+        return s.p[0]
+    if s.kind == TORUS:
+        return s.p[0] + s.p[1]
+    if s.kind == ROUNDED_BOX:
+        return math.sqrt(s.p[0] ** 2 + s.p[1] ** 2 + s.p[2] ** 2)
+    raise ValueError("bounding radius not defined for kind %d" % s.kind)
+
+
+def random_bodies(n, seed=1, p_lo=1e2, p_hi=1e5, kinds=(SPHERE, TORUS, ROUNDED_BOX),
+                  pkg_per_area=4.6, margin_cells=4):
+    """n random bodies, each with its own grid.
+
+    Body k: kind uniform over ``kinds``; size r ~ U[0.1, 1]; uniform random
+    rotation; a target package count log-uniform in [p_lo, p_hi] fixes the
+    coarse cell lc = sqrt(pkg_per_area * area / target) and h = lc / 4.  The
+    domain is a cube around the body with ``margin_cells`` coarse cells beyond
+    its bounding sphere.  Returns a list of (Shape, GridSpec, target).
+    """
+    st = Stream(seed)
+    out = []
+    for _ in range(n):
+        kind = kinds[int(st.uniform53(1)[0] * len(kinds)) % len(kinds)]
+        r = 0.1 + 0.9 * st.uniform53(1)[0]
+        rot = random_rotation(st)
+        target = math.exp(math.log(p_lo) + st.uniform53(1)[0] * (math.log(p_hi) - math.log(p_lo)))
+        if kind == SPHERE:
+            s = sphere(r, rot=rot)
+        elif kind == TORUS:
+            s = torus(r, r / 3.0, rot=rot)
+        else:
+            s = rounded_box((r, 0.75 * r, 0.5 * r), 0.1 * r, rot=rot)
+        lc = math.sqrt(pkg_per_area * shape_area(s) / target)
+        h = lc / 4.0
+        half = bounding_radius(s) + margin_cells * lc
+        m = int(math.ceil(2.0 * half / lc))
+        lo = tuple(-0.5 * m * lc for _ in range(3))
+        out.append((s, GridSpec(lo, (m, m, m), h), target))
+    return out
