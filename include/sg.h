@@ -1,0 +1,221 @@
+/*
+ * sg.h -- C ABI of libsg, a CUDA (sm_103a) implementation of the contiguous
+ * sparse-grid storage of "Contiguous Storage of Grid Data for Heterogeneous
+ * Computing" (Gu & Hu) and of the level-set sweeps run over it.
+ *
+ * Storage ("MeshWithGridDataPackages", Listing 1; "Array Storage and Access"):
+ *   - a background mesh of dims[0] x dims[1] x dims[2] coarse cells of size
+ *     lc = 4h starting at lo; cell index c = I + nx (J + ny K);
+ *   - cells cut by the band own a 4x4x4 data package; package ids 0 and 1 are
+ *     the far-field inside (value -F) and outside (+F) packages, active
+ *     packages follow from id 2 in increasing cell index ("Indexing");
+ *   - every field is one contiguous float array [P][64], data index
+ *     d = i + 4j + 16k inside a package (structure of arrays);
+ *   - cell_pkg[nc] (int32) maps a cell to its package; pkg_cell[P] (int32,
+ *     -1 for the far packages) and pkg_type[P] (uint8: 0 far inside,
+ *     1 far outside, 2 core, 3 inner) are the per-package meta data;
+ *   - nbr[P][27] (int32) holds the packages of the 3x3x3 cell neighbourhood,
+ *     entry (di+1) + 3(dj+1) + 9(dk+1) ("Neighbourhood"); cells outside the
+ *     domain are the outside far package; far packages are their own
+ *     neighbours ("Initialization Process", step 5).
+ *
+ * Conventions for every call:
+ *   - all work is queued on the grid's CUDA stream and the call returns a
+ *     launch-time status; only sg_tag_allocate and sg_status_sync block;
+ *   - device-side problems set a sticky error word, reported by
+ *     sg_status_sync;
+ *   - no C++ exception crosses this interface;
+ *   - state order: sg_create -> sg_tag_allocate -> sg_init_sdf -> the sweeps
+ *     and the probe; a call out of order returns SG_ERR_STATE;
+ *   - the grid owns every array it allocates; particle arrays belong to the
+ *     caller;
+ *   - a failed call leaves the grid in its previous state and records a
+ *     message for sg_last_error.
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SG_API __attribute__((visibility("default")))
+#else
+#define SG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sg_grid sg_grid;
+typedef int32_t sg_status;
+
+enum {
+    SG_OK = 0,
+    SG_ERR_INVALID = 1,  /* bad argument (null pointer, size, kind, mode) */
+    SG_ERR_OOM = 2,      /* the allocator returned NULL */
+    SG_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+    SG_ERR_STATE = 4,    /* call out of order (e.g. a sweep before init) */
+    SG_ERR_CAPACITY = 5, /* sizes beyond the supported range */
+    SG_ERR_TIMEOUT = 6,  /* a bounded device wait gave up */
+    SG_ERR_DEVICE = 7    /* a kernel reported an inconsistency */
+};
+
+enum { SG_SHAPE_SPHERE = 0, SG_SHAPE_PLANE = 1, SG_SHAPE_TORUS = 2, SG_SHAPE_PRISM = 3, SG_SHAPE_ROUNDED_BOX = 4 };
+
+/* Analytic body, in a local frame: a world point x maps to q = R^T (x - centre)
+ * with R = rot (row-major, local to world).  Parameters p per kind:
+ *   sphere: p0 radius; plane: q_z = 0; torus: p0 major (about local z), p1
+ *   minor; prism: triangle (p0,p1),(p2,p3),(p4,p5) extruded over q_z in
+ *   [p6, p7]; rounded box: half extents p0..p2, rounding p3.
+ * Host struct, copied by value. */
+typedef struct {
+    int32_t kind;
+    int32_t pad;
+    double centre[3];
+    double rot[9];
+    double p[8];
+} sg_shape;
+
+/* Grid description (host struct, copied).  far_value <= 0 selects F = 16h. */
+typedef struct {
+    double lo[3];
+    int32_t dims[3];
+    int32_t reserved;
+    double h;         /* fine spacing; the coarse cell is 4h */
+    double far_value; /* F */
+} sg_grid_desc;
+
+/* Optional device-memory hook.  alloc returns device memory of at least
+ * `bytes` usable on `stream` (NULL on failure); free releases it.  With a
+ * NULL allocator the library uses cudaMallocAsync / cudaFreeAsync. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
+    void *ctx;
+} sg_allocator;
+
+enum {
+    SG_FIELD_PHI = 0,  /* level set phi */
+    SG_FIELD_GX = 1,   /* gradient of phi */
+    SG_FIELD_GY = 2,
+    SG_FIELD_GZ = 3,
+    SG_FIELD_W = 4,    /* kernel weight integral */
+    SG_FIELD_GWX = 5,  /* h * gradient of W */
+    SG_FIELD_GWY = 6,
+    SG_FIELD_GWZ = 7,
+    SG_FIELD_LAP = 8,  /* 7-point Laplacian of phi */
+    SG_FIELD_S0 = 9,   /* smoothed sign of the last sg_reinit call */
+    SG_N_FLOAT_FIELDS = 10,
+    SG_FIELD_CELL_PKG = 100, /* int32 [nx*ny*nz] */
+    SG_FIELD_PKG_CELL = 101, /* int32 [P] */
+    SG_FIELD_PKG_TYPE = 102, /* uint8 [P] */
+    SG_FIELD_NBR = 103       /* int32 [P*27] */
+};
+
+/* Morton-order the particles inside sg_probe (see sg_probe). */
+#define SG_PROBE_MORTON 1
+
+/* Create an empty grid on `stream` (a cudaStream_t; NULL = legacy default).
+ * Errors: SG_ERR_INVALID (null pointers, h <= 0, a dimension < 1),
+ * SG_ERR_CAPACITY (more than 2^31 - 1 cells or 4*dims >= 2^21). */
+SG_API sg_status sg_create(const sg_grid_desc *desc, const sg_allocator *alloc, void *stream, sg_grid **out);
+
+/* Release every array the grid owns (stream-ordered), then the handle. */
+SG_API sg_status sg_destroy(sg_grid *g);
+
+/* Band tagging and package allocation ("Initialization Process", steps 1-3
+ * and 5; "Indexing"; "Neighbourhood").  A cell is core when the distance
+ * from its centre lo + (4I + 2)h to the surface is below lc (1 - 2^-10)
+ * (float-float evaluation), inner when it is not core and one of its 26
+ * neighbours is core; ids follow the cell index.  Fills cell_pkg, pkg_cell,
+ * pkg_type and nbr and writes P (including the 2 far packages) to
+ * *n_packages.  Synchronises the stream (P sizes the package arrays).
+ * May be called again to re-tag; previous field contents are discarded. */
+SG_API sg_status sg_tag_allocate(sg_grid *g, const sg_shape *shape, int64_t *n_packages);
+
+/* Level-set values ("Initialization Process", step 4): phi at the
+ * cell-centred data points lo + (4I + i + 0.5) h, evaluated in float-float
+ * and rounded once; far packages hold -F and +F.  Requires a tagged grid. */
+SG_API sg_status sg_init_sdf(sg_grid *g, const sg_shape *shape);
+
+/* Regularised central difference (Listing 5) on every active package:
+ * g_a = ((phi(+e_a) - phi(0)) + (phi(0) - phi(-e_a))) / (2h); neighbours
+ * through the index shift of Listing 2.  Far packages keep g = 0.
+ * Writes SG_FIELD_GX/GY/GZ.  Requires phi. */
+SG_API sg_status sg_gradient(sg_grid *g);
+
+/* 7-point Laplacian sum_a (phi(+e_a) - 2 phi + phi(-e_a)) / h^2 on every
+ * active package (the stencil benchmark of "Performance Evaluation").
+ * Writes SG_FIELD_LAP.  Requires phi. */
+SG_API sg_status sg_laplacian(sg_grid *g);
+
+/* Reinitialisation: `iterations` Jacobi sweeps of
+ * phi <- phi - dt S0 (sqrt(G) - 1), dt = cfl h, S0 = phi0 / sqrt(phi0^2 + h^2)
+ * with phi0 = phi at entry, and the Godunov sum G over the axes of
+ * max(max(D-,0)^2, min(D+,0)^2) where phi0 > 0 and
+ * max(min(D-,0)^2, max(D+,0)^2) where phi0 < 0 (no change where phi0 = 0).
+ * Far packages are fixed.  Not in the paper (Sussman, Smereka & Osher 1994;
+ * Rouy & Tourin 1992).  Errors: SG_ERR_INVALID for iterations < 0 or
+ * cfl <= 0.  Requires phi. */
+SG_API sg_status sg_reinit(sg_grid *g, int32_t iterations, float cfl);
+
+/* Kernel integrals ("Integral with SPH Smoothing Kernel and Grid-Particle
+ * Coupling"), mode 0 (exact): with the Wendland C2 kernel w(q) of support
+ * 2h and the smoothed Heaviside H of half width h, over the offsets s of
+ * the 5^3 stencil (taps with |s| >= 2 weigh zero):
+ *   W  = sum_s w(|s|) H(-phi(x+sh)) / sum_s w(|s|)
+ *   G^ = h grad W = sum_s w'(|s|) (-s/|s|) H(-phi(x+sh)) / sum_s w(|s|).
+ * Far packages: W = 1 inside, 0 outside, G^ = 0.  Writes SG_FIELD_W and
+ * SG_FIELD_GWX/GWY/GWZ.  `mlp` must be NULL for mode 0.
+ * Errors: SG_ERR_INVALID for an unknown mode.  Requires phi. */
+SG_API sg_status sg_kernel_integrals(sg_grid *g, int32_t mode, const void *mlp);
+
+/* Particle probe ("Grid-Particle Coupling"): trilinear interpolation of phi,
+ * grad phi, W and G^ at n particles.  x, y, z are device arrays of n floats;
+ * the eight outputs are device arrays of n floats in input order (any may
+ * be NULL to skip it).  The lattice coordinate is taken in float32:
+ * u = (x - lo)/h - 0.5 clamped to +-2^24, i0 = floor(u), t = u - i0, home
+ * cell floor(i0/4) (the outside far package when outside the domain),
+ * corners reached through the home package's neighbourhood.  The normal is
+ * grad/|grad| (0 where |grad| = 0).  Fields not yet computed read as 0.
+ * With SG_PROBE_MORTON the particles are walked in Morton order (stable
+ * sort by the bit interleave of k_a = clamp(i0_a + 1, 0, 4 dims_a + 1), x in
+ * the lowest bit) and results are written back in input order.
+ * Errors: SG_ERR_INVALID (n < 0, null positions), SG_ERR_CAPACITY
+ * (n >= 2^31).  Requires phi. */
+SG_API sg_status sg_probe(sg_grid *g, int64_t n, const float *x, const float *y, const float *z, float *phi, float *nx,
+                   float *ny, float *nz, float *W, float *Gx, float *Gy, float *Gz, int32_t flags);
+
+/* Morton keys (as in sg_probe) and the stable sorted order of n particles:
+ * keys[n] (uint64) and order[n] (int32, order[r] = input index of rank r),
+ * device arrays owned by the caller.  Requires a tagged grid. */
+SG_API sg_status sg_morton_order(sg_grid *g, int64_t n, const float *x, const float *y, const float *z, uint64_t *keys,
+                          int32_t *order);
+
+/* Borrow the device pointer and element count of a field; valid until the
+ * grid is destroyed or re-tagged.  A float field that was never written is
+ * allocated and zeroed on first request. */
+SG_API sg_status sg_get_field(sg_grid *g, int32_t field, void **dev_ptr, int64_t *n_elems);
+
+/* Number of packages P (including the far packages); 0 before tagging. */
+SG_API int64_t sg_n_packages(const sg_grid *g);
+
+/* Change the stream used by later calls. */
+SG_API sg_status sg_set_stream(sg_grid *g, void *stream);
+
+/* Synchronise the grid's stream and return the sticky device error status
+ * (SG_OK, SG_ERR_DEVICE or SG_ERR_TIMEOUT) or SG_ERR_CUDA. */
+SG_API sg_status sg_status_sync(sg_grid *g);
+
+/* Message of the last failed call on this grid ("" if none). */
+SG_API const char *sg_last_error(const sg_grid *g);
+
+/* Library version string. */
+SG_API const char *sg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SG_H */

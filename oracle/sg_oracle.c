@@ -530,8 +530,8 @@ void or_probe(const or_grid *g, const int32_t *cell_pkg, const int32_t *nbr, con
 
 /* ------------------------------------------------------------------------- */
 /* Morton order of particles: key = interleave of k_a = clamp(i0_a + 1, 0,    */
-/* 2^21 - 1), 21 bits per axis, x in the lowest bit; order = stable sort by   */
-/* (key, input index).                                                        */
+/* 4 dims_a + 1) (at most 21 bits per axis), x in the lowest bit; order =     */
+/* stable sort by (key, input index).                                         */
 /* ------------------------------------------------------------------------- */
 void or_morton_keys(const or_grid *g, int64_t n, const float *x, const float *y, const float *z, uint64_t *keys) {
 #pragma omp parallel for schedule(static)
@@ -542,9 +542,9 @@ void or_morton_keys(const or_grid *g, int64_t n, const float *x, const float *y,
             int64_t i0;
             double t;
             lattice(g, a, src[a][q], &i0, &t);
-            int64_t v = i0 + 1;
+            int64_t v = i0 + 1, vmax = 4 * (int64_t)g->dims[a] + 1;
             if (v < 0) v = 0;
-            if (v > (1 << 21) - 1) v = (1 << 21) - 1;
+            if (v > vmax) v = vmax;
             k[a] = (uint64_t)v;
         }
         uint64_t key = 0;

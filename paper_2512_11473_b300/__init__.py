@@ -1,0 +1,279 @@
+"""Python binding of libsg, the sm_103a CUDA library for contiguous sparse-grid
+level sets (Gu & Hu, "Contiguous Storage of Grid Data for Heterogeneous
+Computing").
+
+Argument marshalling only: every step runs in the library's kernels.  PyTorch
+supplies device memory (the caching allocator, through the library's
+allocator hook), the current CUDA stream, and tensor views of the library's
+device arrays.  There is no CPU fallback: without ``libsg.so`` or a CUDA
+device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsg.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "sg.h")
+
+SG_OK, SG_ERR_INVALID, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_STATE, SG_ERR_CAPACITY, SG_ERR_TIMEOUT, SG_ERR_DEVICE = range(8)
+STATUS_NAMES = ["SG_OK", "SG_ERR_INVALID", "SG_ERR_OOM", "SG_ERR_CUDA", "SG_ERR_STATE", "SG_ERR_CAPACITY",
+                "SG_ERR_TIMEOUT", "SG_ERR_DEVICE"]
+
+FIELDS = {"phi": 0, "gx": 1, "gy": 2, "gz": 3, "W": 4, "Gx": 5, "Gy": 6, "Gz": 7, "lap": 8, "S0": 9}
+INT_FIELDS = {"cell_pkg": (100, "<i4"), "pkg_cell": (101, "<i4"), "pkg_type": (102, "|u1"), "nbr": (103, "<i4")}
+PROBE_MORTON = 1
+PROBE_OUTPUTS = ("phi", "nx", "ny", "nz", "W", "Gx", "Gy", "Gz")
+
+
+class SgError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__("%s: %s" % (name, msg))
+
+
+class sg_shape(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("centre", C.c_double * 3), ("rot", C.c_double * 9),
+                ("p", C.c_double * 8)]
+
+
+class sg_grid_desc(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("dims", C.c_int32 * 3), ("reserved", C.c_int32), ("h", C.c_double),
+                ("far_value", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class sg_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+def declared_symbols(header=HEADER):
+    """Names of the functions the public header declares."""
+    text = open(header).read()
+    return re.findall(r"^SG_API\s+[\w\s\*]+?\b(sg_\w+)\s*\(", text, flags=re.M)
+
+
+_lib = None
+
+
+def lib():
+    """Load libsg.so (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libsg.so not built: run `python -m paper_2512_11473_b300.build` "
+                              "(or __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.sg_create.argtypes = [C.POINTER(sg_grid_desc), C.POINTER(sg_allocator), vp, C.POINTER(vp)]
+        L.sg_destroy.argtypes = [vp]
+        L.sg_tag_allocate.argtypes = [vp, C.POINTER(sg_shape), C.POINTER(i64)]
+        L.sg_init_sdf.argtypes = [vp, C.POINTER(sg_shape)]
+        L.sg_gradient.argtypes = [vp]
+        L.sg_laplacian.argtypes = [vp]
+        L.sg_reinit.argtypes = [vp, i32, C.c_float]
+        L.sg_kernel_integrals.argtypes = [vp, i32, vp]
+        L.sg_probe.argtypes = [vp, i64, vp, vp, vp] + [vp] * 8 + [i32]
+        L.sg_morton_order.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.sg_get_field.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(i64)]
+        L.sg_n_packages.argtypes = [vp]
+        L.sg_n_packages.restype = i64
+        L.sg_set_stream.argtypes = [vp, vp]
+        L.sg_status_sync.argtypes = [vp]
+        L.sg_last_error.argtypes = [vp]
+        L.sg_last_error.restype = C.c_char_p
+        L.sg_version.restype = C.c_char_p
+        for name in declared_symbols():
+            f = getattr(L, name)
+            if f.restype is C.c_int:  # default: sg_status
+                f.restype = i32
+        _lib = L
+    return _lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class _CudaArray:
+    """Minimal __cuda_array_interface__ holder for zero-copy tensor views."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def _as_shape(s) -> sg_shape:
+    out = sg_shape()
+    out.kind = int(s.kind)
+    out.centre[:] = [float(v) for v in s.centre]
+    out.rot[:] = [float(v) for v in s.rot]
+    out.p[:] = [float(v) for v in s.p]
+    return out
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+class _TorchAllocator:
+    """Routes the library's allocations through torch's caching allocator."""
+
+    def __init__(self, device):
+        torch = _torch()
+        self.device = device
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), device=self.device, stream=stream or 0)
+            except Exception:  # out of memory: the library reports SG_ERR_OOM
+                return None
+
+        def _free(ptr, nbytes, stream, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc_fn = ALLOC_FN(_alloc)
+        self.free_fn = FREE_FN(_free)
+        self.struct = sg_allocator(self.alloc_fn, self.free_fn, None)
+
+
+class Grid:
+    """A sparse narrow-band grid on one CUDA device.
+
+    ``spec`` needs ``lo`` (3 floats), ``dims`` (3 ints) and ``h``.  Calls are
+    queued on ``stream`` (default: torch's current stream at construction).
+    """
+
+    def __init__(self, spec, far_value=0.0, stream=None, torch_allocator=True):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2512_11473_b300 needs a CUDA device")
+        self._lib = lib()
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.spec = spec
+        d = sg_grid_desc()
+        d.lo[:] = [float(v) for v in spec.lo]
+        d.dims[:] = [int(v) for v in spec.dims]
+        d.h = float(spec.h)
+        d.far_value = float(far_value)
+        self._alloc = _TorchAllocator(self.device) if torch_allocator else None
+        h = C.c_void_p()
+        st = self._lib.sg_create(C.byref(d), C.byref(self._alloc.struct) if self._alloc else None,
+                                 C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != SG_OK:
+            raise SgError(st, "sg_create failed")
+        self._h = h
+        self.P = 0
+
+    # -- plumbing ------------------------------------------------------------
+    def _check(self, st):
+        if st != SG_OK:
+            raise SgError(st, self._lib.sg_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self._check(self._lib.sg_set_stream(self._h, C.c_void_p(stream.cuda_stream)))
+
+    def sync(self):
+        """Synchronise the stream; raise on a sticky device error."""
+        self._check(self._lib.sg_status_sync(self._h))
+
+    # -- the hot path --------------------------------------------------------
+    def tag_allocate(self, shape) -> int:
+        n = C.c_int64(0)
+        self._check(self._lib.sg_tag_allocate(self._h, C.byref(_as_shape(shape)), C.byref(n)))
+        self.P = int(n.value)
+        return self.P
+
+    def init_sdf(self, shape):
+        self._check(self._lib.sg_init_sdf(self._h, C.byref(_as_shape(shape))))
+
+    def gradient(self):
+        self._check(self._lib.sg_gradient(self._h))
+
+    def laplacian(self):
+        self._check(self._lib.sg_laplacian(self._h))
+
+    def reinit(self, iterations, cfl=0.5):
+        self._check(self._lib.sg_reinit(self._h, int(iterations), float(cfl)))
+
+    def kernel_integrals(self, mode=0, mlp=None):
+        self._check(self._lib.sg_kernel_integrals(self._h, int(mode), mlp))
+
+    def probe(self, x, y, z, morton=True, out=None, outputs=PROBE_OUTPUTS):
+        """Probe at device float32 tensors x, y, z; returns a dict of outputs.
+
+        ``out`` may supply preallocated device tensors (dict by name)."""
+        torch = _torch()
+        n = x.numel()
+        res = {}
+        for name in PROBE_OUTPUTS:
+            if name in outputs:
+                res[name] = out[name] if out is not None else torch.empty(n, dtype=torch.float32, device=x.device)
+        ptrs = [_ptr(res.get(name)) for name in PROBE_OUTPUTS]
+        self._check(self._lib.sg_probe(self._h, n, _ptr(x), _ptr(y), _ptr(z), *ptrs,
+                                       PROBE_MORTON if morton else 0))
+        return res
+
+    def morton_order(self, x, y, z):
+        torch = _torch()
+        n = x.numel()
+        keys = torch.empty(n, dtype=torch.int64, device=x.device)
+        order = torch.empty(n, dtype=torch.int32, device=x.device)
+        self._check(self._lib.sg_morton_order(self._h, n, _ptr(x), _ptr(y), _ptr(z), _ptr(keys), _ptr(order)))
+        return keys, order
+
+    # -- views ---------------------------------------------------------------
+    def field(self, name):
+        """Borrowed zero-copy tensor view of a device array of the grid."""
+        torch = _torch()
+        p = C.c_void_p()
+        n = C.c_int64()
+        if name in FIELDS:
+            self._check(self._lib.sg_get_field(self._h, FIELDS[name], C.byref(p), C.byref(n)))
+            t = torch.as_tensor(_CudaArray(p.value, (n.value,), "<f4"), device="cuda")
+            return t.view(-1, 64)
+        fid, typestr = INT_FIELDS[name]
+        self._check(self._lib.sg_get_field(self._h, fid, C.byref(p), C.byref(n)))
+        t = torch.as_tensor(_CudaArray(p.value, (n.value,), typestr), device="cuda")
+        return t.view(-1, 27) if name == "nbr" else t
+
+    def n_packages(self) -> int:
+        return int(self._lib.sg_n_packages(self._h))
+
+
+def version() -> str:
+    return lib().sg_version().decode()

@@ -1,0 +1,425 @@
+// sg_api.cu -- the extern "C" entry points of libsg (declared in sg.h):
+// argument checks, state order, ownership of the device arrays and launch of
+// the kernels in sg_tag.cu, sg_sweep.cu and sg_probe.cu on the grid's stream.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "sg_internal.cuh"
+
+namespace sg {
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+ff split(double v) {
+    float hi = (float)v;
+    float lo = (float)(v - (double)hi);
+    return ff{hi, lo};
+}
+
+}  // namespace
+
+void* grid_alloc(sg_grid* g, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (g->user_alloc) {
+        p = g->alloc.alloc(bytes, (void*)g->stream, g->alloc.ctx);
+    } else if (cudaMallocAsync(&p, bytes, g->stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void grid_free(sg_grid* g, Buf& b) {
+    if (b.p) {
+        if (g->user_alloc)
+            g->alloc.free(b.p, b.bytes, (void*)g->stream, g->alloc.ctx);
+        else
+            cudaFreeAsync(b.p, g->stream);
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+bool ensure(sg_grid* g, Buf& b, size_t bytes) {
+    if (b.p && b.bytes >= bytes) return true;
+    grid_free(g, b);
+    b.p = grid_alloc(g, bytes);
+    if (!b.p) return false;
+    b.bytes = bytes;
+    return true;
+}
+
+sg_status fail(sg_grid* g, sg_status st, const std::string& msg) {
+    if (g) g->last_error = msg;
+    return st;
+}
+
+sg_status cuda_fail(sg_grid* g, cudaError_t e, const char* where) {
+    return fail(g, SG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+GridF grid_f(const sg_grid* g) {
+    GridF G;
+    for (int a = 0; a < 3; ++a) {
+        G.lo[a] = (float)g->desc.lo[a];
+        G.dims[a] = g->desc.dims[a];
+    }
+    G.h = (float)g->desc.h;
+    G.h_d = g->desc.h;
+    G.F = (float)g->F;
+    return G;
+}
+
+GridFF grid_ff(const sg_grid* g) {
+    GridFF G;
+    for (int a = 0; a < 3; ++a) {
+        G.lo[a] = split(g->desc.lo[a]);
+        G.dims[a] = g->desc.dims[a];
+    }
+    G.h = split(g->desc.h);
+    G.T = split(4.0 * g->desc.h * (1.0 - std::ldexp(1.0, -10)));
+    return G;
+}
+
+ShapeFF shape_ff(const sg_shape* s) {
+    ShapeFF S;
+    S.kind = s->kind;
+    for (int i = 0; i < 3; ++i) S.centre[i] = split(s->centre[i]);
+    for (int i = 0; i < 9; ++i) S.rot[i] = split(s->rot[i]);
+    for (int i = 0; i < 8; ++i) S.p[i] = split(s->p[i]);
+    return S;
+}
+
+float* field_ptr(sg_grid* g, int f, bool zero_new) {
+    const size_t bytes = (size_t)g->P * PKG3 * sizeof(float);
+    Buf& b = g->field[f];
+    if (b.p && b.bytes >= bytes) return (float*)b.p;
+    if (!ensure(g, b, bytes)) return nullptr;
+    if (zero_new && cudaMemsetAsync(b.p, 0, bytes, g->stream) != cudaSuccess) return nullptr;
+    return (float*)b.p;
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+#define SG_CHECK_GRID(g)                                                  \
+    do {                                                                  \
+        if (!(g)) return SG_ERR_INVALID;                                  \
+    } while (0)
+#define SG_CUDA(g, call, where)                                           \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return cuda_fail((g), e_, (where));        \
+    } while (0)
+
+static bool valid_shape(const sg_shape* s) {
+    return s && s->kind >= SG_SHAPE_SPHERE && s->kind <= SG_SHAPE_ROUNDED_BOX;
+}
+
+extern "C" {
+
+const char* sg_version(void) { return "libsg 0.1 (sm_103a)"; }
+
+sg_status sg_create(const sg_grid_desc* desc, const sg_allocator* alloc, void* stream, sg_grid** out) {
+    if (!desc || !out) return SG_ERR_INVALID;
+    *out = nullptr;
+    if (!(desc->h > 0.0) || !std::isfinite(desc->h)) return SG_ERR_INVALID;
+    int64_t nc = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (desc->dims[a] < 1) return SG_ERR_INVALID;
+        if (4LL * desc->dims[a] + 1 >= (1LL << 21)) return SG_ERR_CAPACITY;
+        nc *= desc->dims[a];
+    }
+    if (nc >= (1LL << 31)) return SG_ERR_CAPACITY;
+    if (alloc && (!alloc->alloc || !alloc->free)) return SG_ERR_INVALID;
+    sg_grid* g = new (std::nothrow) sg_grid();
+    if (!g) return SG_ERR_OOM;
+    g->desc = *desc;
+    g->F = desc->far_value > 0.0 ? desc->far_value : 16.0 * desc->h;
+    g->nc = nc;
+    g->stream = (cudaStream_t)stream;
+    if (alloc) {
+        g->alloc = *alloc;
+        g->user_alloc = true;
+    }
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        return SG_ERR_CUDA;
+    }
+    if (!ensure(g, g->err, 256)) {
+        delete g;
+        return SG_ERR_OOM;
+    }
+    if (cudaMemsetAsync(g->err.p, 0, 256, g->stream) != cudaSuccess ||
+        cudaMallocHost(&g->host_pin.p, 256) != cudaSuccess) {
+        cudaGetLastError();
+        grid_free(g, g->err);
+        delete g;
+        return SG_ERR_CUDA;
+    }
+    g->host_pin.bytes = 256;
+    *out = g;
+    return SG_OK;
+}
+
+sg_status sg_destroy(sg_grid* g) {
+    SG_CHECK_GRID(g);
+    DeviceGuard dg(g->device);
+    Buf* bufs[] = {&g->cell_pkg, &g->cell_type, &g->pkg_cell, &g->pkg_type, &g->nbr,
+                   &g->phi_tmp,  &g->err,       &g->scratch};
+    for (Buf* b : bufs) grid_free(g, *b);
+    for (int f = 0; f < SG_N_FLOAT_FIELDS; ++f) grid_free(g, g->field[f]);
+    if (g->host_pin.p) cudaFreeHost(g->host_pin.p);
+    delete g;
+    return SG_OK;
+}
+
+sg_status sg_set_stream(sg_grid* g, void* stream) {
+    SG_CHECK_GRID(g);
+    g->stream = (cudaStream_t)stream;
+    return SG_OK;
+}
+
+int64_t sg_n_packages(const sg_grid* g) { return g ? g->P : 0; }
+
+const char* sg_last_error(const sg_grid* g) { return g ? g->last_error.c_str() : "null grid"; }
+
+sg_status sg_tag_allocate(sg_grid* g, const sg_shape* shape, int64_t* n_packages) {
+    SG_CHECK_GRID(g);
+    if (!valid_shape(shape)) return fail(g, SG_ERR_INVALID, "sg_tag_allocate: bad shape");
+    DeviceGuard dg(g->device);
+    const int64_t nc = g->nc;
+    const GridFF G = grid_ff(g);
+    const ShapeFF S = shape_ff(shape);
+    const size_t act_bytes = ((size_t)nc * 4 + 255) & ~(size_t)255;
+    if (!ensure(g, g->cell_type, (size_t)nc) || !ensure(g, g->cell_pkg, (size_t)nc * 4) ||
+        !ensure(g, g->scratch, act_bytes + scan_scratch_bytes(nc) + 256))
+        return fail(g, SG_ERR_OOM, "sg_tag_allocate: out of device memory");
+    uint32_t* active = (uint32_t*)g->scratch.p;
+    uint32_t* total = (uint32_t*)((char*)g->scratch.p + act_bytes);
+    void* scan_scratch = (char*)g->scratch.p + act_bytes + 256;
+    uint8_t* ct = (uint8_t*)g->cell_type.p;
+    SG_CUDA(g, launch_tag_flags(G, S, ct, active, nc, g->stream), "tag flags");
+    SG_CUDA(g, launch_tag_inner(G, ct, active, nc, g->stream), "tag inner");
+    SG_CUDA(g, exclusive_scan_u32(active, active, nc, total, scan_scratch, g->stream), "tag scan");
+    SG_CUDA(g, cudaMemcpyAsync(g->host_pin.p, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream), "tag count");
+    SG_CUDA(g, cudaStreamSynchronize(g->stream), "tag sync");
+    const int64_t P = 2 + (int64_t)*(uint32_t*)g->host_pin.p;
+    if (P >= (1LL << 31) / NB) return fail(g, SG_ERR_CAPACITY, "sg_tag_allocate: too many packages");
+    // the package arrays and every field are sized by P: start afresh
+    for (int f = 0; f < SG_N_FLOAT_FIELDS; ++f) grid_free(g, g->field[f]);
+    grid_free(g, g->phi_tmp);
+    if (!ensure(g, g->pkg_cell, (size_t)P * 4) || !ensure(g, g->pkg_type, (size_t)P) ||
+        !ensure(g, g->nbr, (size_t)P * NB * 4)) {
+        g->state = 0;
+        return fail(g, SG_ERR_OOM, "sg_tag_allocate: out of device memory");
+    }
+    g->P = P;
+    SG_CUDA(g, launch_tag_scatter(ct, active, (int32_t*)g->cell_pkg.p, (int32_t*)g->pkg_cell.p,
+                                  (uint8_t*)g->pkg_type.p, nc, g->stream),
+            "tag scatter");
+    SG_CUDA(g, launch_fill_nbr(G, (const int32_t*)g->cell_pkg.p, (const int32_t*)g->pkg_cell.p, (int32_t*)g->nbr.p, P,
+                               g->stream),
+            "fill nbr");
+    g->state = 1;
+    if (n_packages) *n_packages = P;
+    return SG_OK;
+}
+
+sg_status sg_init_sdf(sg_grid* g, const sg_shape* shape) {
+    SG_CHECK_GRID(g);
+    if (!valid_shape(shape)) return fail(g, SG_ERR_INVALID, "sg_init_sdf: bad shape");
+    if (g->state < 1) return fail(g, SG_ERR_STATE, "sg_init_sdf: grid not tagged");
+    DeviceGuard dg(g->device);
+    float* phi = field_ptr(g, SG_FIELD_PHI, false);
+    if (!phi) return fail(g, SG_ERR_OOM, "sg_init_sdf: out of device memory");
+    SG_CUDA(g, launch_init_sdf(grid_ff(g), shape_ff(shape), (const int32_t*)g->pkg_cell.p, phi, (float)g->F, g->P,
+                               g->stream),
+            "init sdf");
+    g->state = 2;
+    return SG_OK;
+}
+
+sg_status sg_gradient(sg_grid* g) {
+    SG_CHECK_GRID(g);
+    if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_gradient: phi not initialised");
+    DeviceGuard dg(g->device);
+    float* o[3];
+    for (int a = 0; a < 3; ++a)
+        if (!(o[a] = field_ptr(g, SG_FIELD_GX + a, false))) return fail(g, SG_ERR_OOM, "sg_gradient: out of memory");
+    for (int a = 0; a < 3; ++a) SG_CUDA(g, launch_set_far(o[a], 0.0f, 0.0f, g->stream), "gradient far");
+    SG_CUDA(g, launch_gradient(grid_f(g), (const int32_t*)g->nbr.p, (const float*)g->field[SG_FIELD_PHI].p, o[0], o[1],
+                               o[2], g->P, g->stream),
+            "gradient");
+    return SG_OK;
+}
+
+sg_status sg_laplacian(sg_grid* g) {
+    SG_CHECK_GRID(g);
+    if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_laplacian: phi not initialised");
+    DeviceGuard dg(g->device);
+    float* lap = field_ptr(g, SG_FIELD_LAP, false);
+    if (!lap) return fail(g, SG_ERR_OOM, "sg_laplacian: out of memory");
+    SG_CUDA(g, launch_set_far(lap, 0.0f, 0.0f, g->stream), "laplacian far");
+    SG_CUDA(g, launch_laplacian(grid_f(g), (const int32_t*)g->nbr.p, (const float*)g->field[SG_FIELD_PHI].p, lap, g->P,
+                                g->stream),
+            "laplacian");
+    return SG_OK;
+}
+
+sg_status sg_reinit(sg_grid* g, int32_t iterations, float cfl) {
+    SG_CHECK_GRID(g);
+    if (iterations < 0 || !(cfl > 0.0f) || !std::isfinite(cfl)) return fail(g, SG_ERR_INVALID, "sg_reinit: bad args");
+    if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_reinit: phi not initialised");
+    DeviceGuard dg(g->device);
+    float* phi = (float*)g->field[SG_FIELD_PHI].p;
+    float* s0 = field_ptr(g, SG_FIELD_S0, false);
+    if (!s0 || !ensure(g, g->phi_tmp, (size_t)g->P * PKG3 * 4)) return fail(g, SG_ERR_OOM, "sg_reinit: out of memory");
+    float* tmp = (float*)g->phi_tmp.p;
+    const GridF G = grid_f(g);
+    const float dt = (float)((double)cfl * g->desc.h);
+    const int32_t* nbr = (const int32_t*)g->nbr.p;
+    SG_CUDA(g, launch_set_far(s0, -1.0f, 1.0f, g->stream), "reinit far");
+    SG_CUDA(g, launch_set_far(tmp, -(float)g->F, (float)g->F, g->stream), "reinit far");
+    SG_CUDA(g, launch_reinit_s0(G, phi, s0, g->P, g->stream), "reinit s0");
+    float* a = phi;
+    float* b = tmp;
+    for (int32_t it = 0; it < iterations; ++it) {
+        SG_CUDA(g, launch_reinit_step(G, nbr, s0, a, b, dt, g->P, g->stream), "reinit step");
+        float* t = a;
+        a = b;
+        b = t;
+    }
+    if (a != phi) SG_CUDA(g, launch_copy_active(a, phi, g->P, g->stream), "reinit copy");
+    return SG_OK;
+}
+
+sg_status sg_kernel_integrals(sg_grid* g, int32_t mode, const void* mlp) {
+    SG_CHECK_GRID(g);
+    if (mode != 0 || mlp != nullptr) return fail(g, SG_ERR_INVALID, "sg_kernel_integrals: unsupported mode");
+    if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_kernel_integrals: phi not initialised");
+    DeviceGuard dg(g->device);
+    float* o[4];
+    for (int a = 0; a < 4; ++a)
+        if (!(o[a] = field_ptr(g, SG_FIELD_W + a, false)))
+            return fail(g, SG_ERR_OOM, "sg_kernel_integrals: out of memory");
+    SG_CUDA(g, launch_kernel_integrals(grid_f(g), (const int32_t*)g->nbr.p, (const float*)g->field[SG_FIELD_PHI].p, o[0],
+                                       o[1], o[2], o[3], g->P, g->stream),
+            "kernel integrals");
+    return SG_OK;
+}
+
+sg_status sg_morton_order(sg_grid* g, int64_t n, const float* x, const float* y, const float* z, uint64_t* keys,
+                          int32_t* order) {
+    SG_CHECK_GRID(g);
+    if (n < 0 || (n > 0 && (!x || !y || !z || !order))) return fail(g, SG_ERR_INVALID, "sg_morton_order: bad args");
+    if (n >= (1LL << 31)) return fail(g, SG_ERR_CAPACITY, "sg_morton_order: too many particles");
+    if (g->state < 1) return fail(g, SG_ERR_STATE, "sg_morton_order: grid not tagged");
+    if (n == 0) return SG_OK;
+    DeviceGuard dg(g->device);
+    const GridF G = grid_f(g);
+    if (!ensure(g, g->scratch, sort_scratch_bytes(n, morton_bits(G))))
+        return fail(g, SG_ERR_OOM, "sg_morton_order: out of memory");
+    SG_CUDA(g, morton_sort(G, n, x, y, z, keys, order, g->scratch.p, g->stream), "morton sort");
+    return SG_OK;
+}
+
+sg_status sg_probe(sg_grid* g, int64_t n, const float* x, const float* y, const float* z, float* phi, float* nx,
+                   float* ny, float* nz, float* W, float* Gx, float* Gy, float* Gz, int32_t flags) {
+    SG_CHECK_GRID(g);
+    if (n < 0 || (n > 0 && (!x || !y || !z))) return fail(g, SG_ERR_INVALID, "sg_probe: bad args");
+    if (n >= (1LL << 31)) return fail(g, SG_ERR_CAPACITY, "sg_probe: too many particles");
+    if (flags & ~SG_PROBE_MORTON) return fail(g, SG_ERR_INVALID, "sg_probe: unknown flags");
+    if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_probe: phi not initialised");
+    if (n == 0) return SG_OK;
+    DeviceGuard dg(g->device);
+    ProbeFields F;
+    const int src[8] = {SG_FIELD_PHI, SG_FIELD_GX, SG_FIELD_GY, SG_FIELD_GZ,
+                        SG_FIELD_W,   SG_FIELD_GWX, SG_FIELD_GWY, SG_FIELD_GWZ};
+    for (int f = 0; f < 8; ++f) {
+        bool fresh = !g->field[src[f]].p;
+        F.f[f] = field_ptr(g, src[f], true);
+        if (!F.f[f]) return fail(g, SG_ERR_OOM, "sg_probe: out of memory");
+        if (fresh && src[f] == SG_FIELD_W) SG_CUDA(g, launch_set_far((float*)F.f[f], 1.0f, 0.0f, g->stream), "probe W far");
+    }
+    ProbeOut O{{phi, nx, ny, nz, W, Gx, Gy, Gz}};
+    const GridF G = grid_f(g);
+    const int32_t* order = nullptr;
+    if (flags & SG_PROBE_MORTON) {
+        size_t sb = sort_scratch_bytes(n, morton_bits(G));
+        size_t ob = ((size_t)n * 4 + 255) & ~(size_t)255;
+        if (!ensure(g, g->scratch, sb + ob)) return fail(g, SG_ERR_OOM, "sg_probe: out of memory");
+        int32_t* ord = (int32_t*)((char*)g->scratch.p + sb);
+        SG_CUDA(g, morton_sort(G, n, x, y, z, nullptr, ord, g->scratch.p, g->stream), "probe sort");
+        order = ord;
+    }
+    SG_CUDA(g, launch_probe(G, (const int32_t*)g->cell_pkg.p, (const int32_t*)g->nbr.p, F, n, x, y, z, order, O,
+                            g->stream),
+            "probe");
+    return SG_OK;
+}
+
+sg_status sg_get_field(sg_grid* g, int32_t field, void** dev_ptr, int64_t* n_elems) {
+    SG_CHECK_GRID(g);
+    if (!dev_ptr || !n_elems) return fail(g, SG_ERR_INVALID, "sg_get_field: null output");
+    DeviceGuard dg(g->device);
+    if (field >= 0 && field < SG_N_FLOAT_FIELDS) {
+        if (g->state < 1) return fail(g, SG_ERR_STATE, "sg_get_field: grid not tagged");
+        bool fresh = !g->field[field].p;
+        float* p = field_ptr(g, field, true);
+        if (!p) return fail(g, SG_ERR_OOM, "sg_get_field: out of memory");
+        if (fresh && field == SG_FIELD_W) SG_CUDA(g, launch_set_far(p, 1.0f, 0.0f, g->stream), "field W far");
+        *dev_ptr = p;
+        *n_elems = g->P * PKG3;
+        return SG_OK;
+    }
+    if (g->state < 1) return fail(g, SG_ERR_STATE, "sg_get_field: grid not tagged");
+    switch (field) {
+    case SG_FIELD_CELL_PKG:
+        *dev_ptr = g->cell_pkg.p;
+        *n_elems = g->nc;
+        return SG_OK;
+    case SG_FIELD_PKG_CELL:
+        *dev_ptr = g->pkg_cell.p;
+        *n_elems = g->P;
+        return SG_OK;
+    case SG_FIELD_PKG_TYPE:
+        *dev_ptr = g->pkg_type.p;
+        *n_elems = g->P;
+        return SG_OK;
+    case SG_FIELD_NBR:
+        *dev_ptr = g->nbr.p;
+        *n_elems = g->P * NB;
+        return SG_OK;
+    default:
+        return fail(g, SG_ERR_INVALID, "sg_get_field: unknown field");
+    }
+}
+
+sg_status sg_status_sync(sg_grid* g) {
+    SG_CHECK_GRID(g);
+    DeviceGuard dg(g->device);
+    SG_CUDA(g, cudaStreamSynchronize(g->stream), "sync");
+    SG_CUDA(g, cudaMemcpy(g->host_pin.p, g->err.p, sizeof(int32_t), cudaMemcpyDeviceToHost), "error word");
+    int32_t w = *(int32_t*)g->host_pin.p;
+    if (w & ERR_TIMEOUT) return fail(g, SG_ERR_TIMEOUT, "device wait timed out");
+    if (w) return fail(g, SG_ERR_DEVICE, "device reported an inconsistency");
+    return SG_OK;
+}
+
+}  // extern "C"

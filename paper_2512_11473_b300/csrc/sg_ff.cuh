@@ -1,0 +1,188 @@
+// sg_ff.cuh -- float-float ("double-float") arithmetic and analytic signed
+// distance functions evaluated in it.
+//
+// A value is an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2,
+// about 48 significant bits.  The error-free transforms are Knuth's TwoSum,
+// Dekker's Fast2Sum and the FMA-based TwoProduct; division and square root
+// take one Newton correction on a float estimate (Dekker 1971; Karp &
+// Markstein 1997).  All primitive operations use the round-to-nearest
+// intrinsics so that no compiler contraction can break an error-free step.
+//
+// The band predicate |d(cell centre)| < T decides which packages exist, so it
+// must agree with an exact evaluation; float-float keeps the error near
+// 1e-14 relative, far below the margin between any cell and the threshold.
+// The initial level set is evaluated the same way and rounded to float once.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace sg {
+
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_make(float a) { return ff{a, 0.0f}; }
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return ff{s, e};
+}
+
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return ff{s, e};
+}
+
+__device__ __forceinline__ ff two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return ff{p, e};
+}
+
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    ff s = two_sum(x.hi, y.hi);
+    ff t = two_sum(x.lo, y.lo);
+    float e = __fadd_rn(s.lo, t.hi);
+    ff u = fast_two_sum(s.hi, e);
+    float e2 = __fadd_rn(u.lo, t.lo);
+    return fast_two_sum(u.hi, e2);
+}
+
+__device__ __forceinline__ ff ff_neg(ff x) { return ff{-x.hi, -x.lo}; }
+__device__ __forceinline__ ff ff_sub(ff x, ff y) { return ff_add(x, ff_neg(y)); }
+
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+    ff p = two_prod(x.hi, y.hi);
+    float c = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.hi));
+    return fast_two_sum(p.hi, __fadd_rn(p.lo, c));
+}
+
+__device__ __forceinline__ ff ff_mul_f(ff x, float b) {
+    ff p = two_prod(x.hi, b);
+    return fast_two_sum(p.hi, __fmaf_rn(x.lo, b, p.lo));
+}
+
+__device__ __forceinline__ ff ff_sqr(ff x) { return ff_mul(x, x); }
+
+__device__ __forceinline__ ff ff_div(ff x, ff y) {
+    float q1 = __fdiv_rn(x.hi, y.hi);
+    ff r = ff_sub(x, ff_mul_f(y, q1));
+    float q2 = __fdiv_rn(r.hi, y.hi);
+    r = ff_sub(r, ff_mul_f(y, q2));
+    float q3 = __fdiv_rn(r.hi, y.hi);
+    ff q = fast_two_sum(q1, q2);
+    return ff_add(q, ff_make(q3));
+}
+
+// sqrt(x) for x >= 0: s = sqrtf(hi), then s + (x - s^2) / (2 s).
+__device__ __forceinline__ ff ff_sqrt(ff x) {
+    if (!(x.hi > 0.0f)) return ff{0.0f, 0.0f};
+    float s = __fsqrt_rn(x.hi);
+    ff r = ff_sub(x, two_prod(s, s));
+    float c = __fdiv_rn(r.hi, __fmul_rn(2.0f, s));
+    return fast_two_sum(s, c);
+}
+
+__device__ __forceinline__ bool ff_lt(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool ff_gt(ff a, ff b) { return ff_lt(b, a); }
+__device__ __forceinline__ bool ff_neg_p(ff a) { return a.hi < 0.0f || (a.hi == 0.0f && a.lo < 0.0f); }
+__device__ __forceinline__ ff ff_abs(ff a) { return ff_neg_p(a) ? ff_neg(a) : a; }
+__device__ __forceinline__ ff ff_max(ff a, ff b) { return ff_lt(a, b) ? b : a; }
+__device__ __forceinline__ ff ff_min(ff a, ff b) { return ff_lt(a, b) ? a : b; }
+__device__ __forceinline__ ff ff_clamp01(ff t) {
+    if (ff_neg_p(t)) return ff{0.0f, 0.0f};
+    if (ff_gt(t, ff{1.0f, 0.0f})) return ff{1.0f, 0.0f};
+    return t;
+}
+__device__ __forceinline__ float ff_to_float(ff a) { return __fadd_rn(a.hi, a.lo); }
+
+// ---------------------------------------------------------------------------
+// Shapes, pre-split on the host into float-float constants.
+// ---------------------------------------------------------------------------
+enum { SHAPE_SPHERE = 0, SHAPE_PLANE = 1, SHAPE_TORUS = 2, SHAPE_PRISM = 3, SHAPE_ROUNDED_BOX = 4 };
+
+struct ShapeFF {
+    int kind;
+    ff centre[3];
+    ff rot[9];  // row-major, local -> world
+    ff p[8];
+};
+
+// local coordinates q = R^T (x - centre)
+__device__ __forceinline__ void ff_to_local(const ShapeFF& s, const ff x[3], ff q[3]) {
+    ff d[3] = {ff_sub(x[0], s.centre[0]), ff_sub(x[1], s.centre[1]), ff_sub(x[2], s.centre[2])};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        q[i] = ff_add(ff_add(ff_mul(s.rot[i], d[0]), ff_mul(s.rot[3 + i], d[1])), ff_mul(s.rot[6 + i], d[2]));
+}
+
+// squared distance from p to the segment a-b, all in the plane
+__device__ __forceinline__ ff ff_seg_dist2(ff px, ff py, ff ax, ff ay, ff bx, ff by) {
+    ff ex = ff_sub(bx, ax), ey = ff_sub(by, ay);
+    ff wx = ff_sub(px, ax), wy = ff_sub(py, ay);
+    ff t = ff_clamp01(ff_div(ff_add(ff_mul(wx, ex), ff_mul(wy, ey)), ff_add(ff_sqr(ex), ff_sqr(ey))));
+    ff dx = ff_sub(wx, ff_mul(t, ex)), dy = ff_sub(wy, ff_mul(t, ey));
+    return ff_add(ff_sqr(dx), ff_sqr(dy));
+}
+
+__device__ __forceinline__ ff ff_cross(ff ax, ff ay, ff bx, ff by) { return ff_sub(ff_mul(ax, by), ff_mul(ay, bx)); }
+
+__device__ inline ff ff_triangle_sdf(ff px, ff py, const ff* t) {
+    ff d2 = ff_seg_dist2(px, py, t[0], t[1], t[2], t[3]);
+    d2 = ff_min(d2, ff_seg_dist2(px, py, t[2], t[3], t[4], t[5]));
+    d2 = ff_min(d2, ff_seg_dist2(px, py, t[4], t[5], t[0], t[1]));
+    ff orient = ff_cross(ff_sub(t[2], t[0]), ff_sub(t[3], t[1]), ff_sub(t[4], t[0]), ff_sub(t[5], t[1]));
+    ff c0 = ff_cross(ff_sub(t[2], t[0]), ff_sub(t[3], t[1]), ff_sub(px, t[0]), ff_sub(py, t[1]));
+    ff c1 = ff_cross(ff_sub(t[4], t[2]), ff_sub(t[5], t[3]), ff_sub(px, t[2]), ff_sub(py, t[3]));
+    ff c2 = ff_cross(ff_sub(t[0], t[4]), ff_sub(t[1], t[5]), ff_sub(px, t[4]), ff_sub(py, t[5]));
+    const ff zero{0.0f, 0.0f};
+    bool inside = ff_gt(orient, zero) ? (ff_gt(c0, zero) && ff_gt(c1, zero) && ff_gt(c2, zero))
+                                      : (ff_lt(c0, zero) && ff_lt(c1, zero) && ff_lt(c2, zero));
+    ff d = ff_sqrt(d2);
+    return inside ? ff_neg(d) : d;
+}
+
+// Exact signed distance (negative inside) of each primitive, in float-float.
+__device__ inline ff ff_sdf(const ShapeFF& s, const ff x[3]) {
+    ff q[3];
+    ff_to_local(s, x, q);
+    const ff zero{0.0f, 0.0f};
+    switch (s.kind) {
+    case SHAPE_SPHERE:
+        return ff_sub(ff_sqrt(ff_add(ff_add(ff_sqr(q[0]), ff_sqr(q[1])), ff_sqr(q[2]))), s.p[0]);
+    case SHAPE_PLANE:
+        return q[2];
+    case SHAPE_TORUS: {
+        ff a = ff_sub(ff_sqrt(ff_add(ff_sqr(q[0]), ff_sqr(q[1]))), s.p[0]);
+        return ff_sub(ff_sqrt(ff_add(ff_sqr(a), ff_sqr(q[2]))), s.p[1]);
+    }
+    case SHAPE_PRISM: {
+        ff w0 = ff_triangle_sdf(q[0], q[1], s.p);
+        ff zc = ff_mul_f(ff_add(s.p[6], s.p[7]), 0.5f);
+        ff hz = ff_mul_f(ff_sub(s.p[7], s.p[6]), 0.5f);
+        ff w1 = ff_sub(ff_abs(ff_sub(q[2], zc)), hz);
+        ff in = ff_min(ff_max(w0, w1), zero);
+        ff a = ff_max(w0, zero), b = ff_max(w1, zero);
+        return ff_add(in, ff_sqrt(ff_add(ff_sqr(a), ff_sqr(b))));
+    }
+    case SHAPE_ROUNDED_BOX: {
+        ff r = s.p[3];
+        ff o = zero, m = ff{-INFINITY, 0.0f};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            ff d = ff_sub(ff_abs(q[i]), ff_sub(s.p[i], r));
+            if (ff_gt(d, zero)) o = ff_add(o, ff_sqr(d));
+            if (ff_gt(d, m)) m = d;
+        }
+        return ff_sub(ff_add(ff_sqrt(o), ff_min(m, zero)), r);
+    }
+    default:
+        return ff{NAN, 0.0f};
+    }
+}
+
+}  // namespace sg

@@ -1,0 +1,124 @@
+// sg_internal.cuh -- grid object and launcher declarations shared by the
+// translation units of libsg.  Not part of the public interface.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sg.h"
+#include "sg_ff.cuh"
+
+namespace sg {
+
+constexpr int PKG = 4;    // data per axis in a package
+constexpr int PKG3 = 64;  // data per package
+constexpr int NB = 27;    // entries of the neighbourhood table
+
+// device error word bits
+constexpr int ERR_BAD_INDEX = 1;
+constexpr int ERR_TIMEOUT = 2;
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// Scalars every stencil kernel needs, in float.
+struct GridF {
+    float lo[3];
+    float h;
+    int dims[3];
+    float F;
+    double h_d;  // h in double, for host-side constants
+};
+
+// Scalars of the tagging/init kernels, in float-float.
+struct GridFF {
+    ff lo[3];
+    ff h;
+    ff T;  // core threshold lc (1 - 2^-10)
+    int dims[3];
+};
+
+}  // namespace sg
+
+struct sg_grid {
+    sg_grid_desc desc;
+    double F = 0;
+    int64_t nc = 0;   // background cells
+    int64_t P = 0;    // packages incl. the 2 far packages
+    int state = 0;    // 0 created, 1 tagged, 2 phi valid
+    sg_allocator alloc{};
+    bool user_alloc = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+
+    sg::Buf cell_pkg, cell_type, pkg_cell, pkg_type, nbr;
+    sg::Buf field[SG_N_FLOAT_FIELDS];
+    sg::Buf phi_tmp;
+    sg::Buf err;       // int32 sticky device error word
+    sg::Buf scratch;   // reusable temporary space (scans, sort)
+    sg::Buf host_pin;  // pinned host word for read-backs
+    std::string last_error;
+};
+
+namespace sg {
+
+// memory (sg_api.cu)
+void* grid_alloc(sg_grid* g, size_t bytes);
+void grid_free(sg_grid* g, Buf& b);
+bool ensure(sg_grid* g, Buf& b, size_t bytes);  // (re)allocates when too small
+sg_status fail(sg_grid* g, sg_status st, const std::string& msg);
+sg_status cuda_fail(sg_grid* g, cudaError_t e, const char* where);
+float* field_ptr(sg_grid* g, int f, bool zero_new);
+GridF grid_f(const sg_grid* g);
+GridFF grid_ff(const sg_grid* g);
+ShapeFF shape_ff(const sg_shape* s);
+
+// scans (sg_scan.cu): exclusive prefix sum of n uint32 values into out
+// (may alias in), total into *total (device).  Scratch: scan_scratch_bytes(n).
+size_t scan_scratch_bytes(int64_t n);
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, void* scratch,
+                               cudaStream_t s);
+
+// tagging / init (sg_tag.cu)
+cudaError_t launch_tag_flags(const GridFF& G, const ShapeFF& S, uint8_t* cell_type, uint32_t* active, int64_t nc,
+                             cudaStream_t s);
+cudaError_t launch_tag_inner(const GridFF& G, uint8_t* cell_type, uint32_t* active, int64_t nc, cudaStream_t s);
+cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* prefix, int32_t* cell_pkg,
+                               int32_t* pkg_cell, uint8_t* pkg_type, int64_t nc, cudaStream_t s);
+cudaError_t launch_fill_nbr(const GridFF& G, const int32_t* cell_pkg, const int32_t* pkg_cell, int32_t* nbr,
+                            int64_t P, cudaStream_t s);
+cudaError_t launch_init_sdf(const GridFF& G, const ShapeFF& S, const int32_t* pkg_cell, float* phi, float F,
+                            int64_t P, cudaStream_t s);
+
+// sweeps (sg_sweep.cu)
+cudaError_t launch_set_far(float* f, float v_in, float v_out, cudaStream_t s);
+cudaError_t launch_gradient(const GridF& G, const int32_t* nbr, const float* phi, float* gx, float* gy, float* gz,
+                            int64_t P, cudaStream_t s);
+cudaError_t launch_laplacian(const GridF& G, const int32_t* nbr, const float* phi, float* lap, int64_t P,
+                             cudaStream_t s);
+cudaError_t launch_reinit_s0(const GridF& G, const float* phi, float* s0, int64_t P, cudaStream_t s);
+cudaError_t launch_reinit_step(const GridF& G, const int32_t* nbr, const float* s0, const float* phi_in,
+                               float* phi_out, float dt, int64_t P, cudaStream_t s);
+cudaError_t launch_copy_active(const float* src, float* dst, int64_t P, cudaStream_t s);
+cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const float* phi, float* W, float* gx,
+                                    float* gy, float* gz, int64_t P, cudaStream_t s);
+
+// probe (sg_probe.cu)
+struct ProbeFields {
+    const float* f[8];  // phi, gx, gy, gz, W, Gx, Gy, Gz
+};
+struct ProbeOut {
+    float* o[8];  // phi, nx, ny, nz, W, Gx, Gy, Gz (entries may be null)
+};
+int morton_bits(const GridF& G);  // significant key bits
+size_t sort_scratch_bytes(int64_t n, int key_bits);
+cudaError_t morton_sort(const GridF& G, int64_t n, const float* x, const float* y, const float* z, uint64_t* keys_out,
+                        int32_t* order_out, void* scratch, cudaStream_t s);
+cudaError_t launch_probe(const GridF& G, const int32_t* cell_pkg, const int32_t* nbr, const ProbeFields& F,
+                         int64_t n, const float* x, const float* y, const float* z, const int32_t* order,
+                         const ProbeOut& out, cudaStream_t s);
+
+}  // namespace sg

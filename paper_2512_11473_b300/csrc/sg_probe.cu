@@ -1,0 +1,307 @@
+// sg_probe.cu -- particle probe ("Grid-Particle Coupling"): trilinear
+// interpolation of the package fields at particle positions, with particles
+// optionally walked in Morton order, and the Morton sort itself (an LSD radix
+// sort written for this library: per-tile digit histograms, an exclusive scan
+// of the digit-major histogram table, and a stable scatter staged through
+// shared memory so that global writes of one digit run are contiguous).
+#include "sg_internal.cuh"
+
+namespace sg {
+namespace {
+
+constexpr int PR_THREADS = 256;
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096 keys per tile
+constexpr int RS_WARPS = RS_THREADS / 32;
+
+// Fine lattice coordinate in float32: u = (x - lo)/h - 1/2 clamped to
+// +-2^24, i0 = floor(u), t = u - i0 (exact).
+__device__ __forceinline__ void lattice(float x, float lo, float h, int& i0, float& t) {
+    float u = __fsub_rn(__fdiv_rn(__fsub_rn(x, lo), h), 0.5f);
+    u = fminf(fmaxf(u, -16777216.0f), 16777216.0f);
+    float f = floorf(u);
+    i0 = (int)f;
+    t = __fsub_rn(u, f);
+}
+
+__device__ __forceinline__ uint64_t spread3(uint64_t v) {  // bit b -> bit 3b (21 bits)
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__device__ __forceinline__ uint64_t morton_key(const GridF& G, float x, float y, float z) {
+    const float pos[3] = {x, y, z};
+    uint64_t key = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int i0;
+        float t;
+        lattice(pos[a], G.lo[a], G.h, i0, t);
+        int k = i0 + 1;
+        k = k < 0 ? 0 : (k > 4 * G.dims[a] + 1 ? 4 * G.dims[a] + 1 : k);
+        key |= spread3((uint64_t)k) << a;
+    }
+    return key;
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(RS_THREADS) k_morton_keys(GridF G, int64_t n, const float* __restrict__ x,
+                                                            const float* __restrict__ y, const float* __restrict__ z,
+                                                            KeyT* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                            uint64_t* __restrict__ keys_out) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = morton_key(G, x[q], y[q], z[q]);
+        keys[q] = (KeyT)k;
+        vals[q] = (uint32_t)q;
+        if (keys_out) keys_out[q] = k;
+    }
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const KeyT* __restrict__ keys, int64_t n, int shift,
+                                                        uint32_t* __restrict__ hist, int64_t nb) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll 4
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        int64_t i = base + r * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                           KeyT* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                           int64_t n, int shift, const uint32_t* __restrict__ offs,
+                                                           int64_t nb) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    KeyT* s_k = (KeyT*)smem;
+    uint32_t* s_v = (uint32_t*)(smem + RS_TILE * sizeof(KeyT));
+    __shared__ uint32_t s_start[256], s_run[256], s_goff[256];
+    __shared__ uint32_t s_wc[RS_WARPS][256];
+    __shared__ uint32_t s_scan[RS_WARPS + 1];
+
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    const int tile_n = (int)min((int64_t)RS_TILE, n - base);
+
+    s_start[t] = 0;
+    s_run[t] = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) s_wc[w][t] = 0xffffffffu;
+    __syncthreads();
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        int i = r * RS_THREADS + t;
+        if (i < tile_n) atomicAdd(&s_start[(uint32_t)(kin[base + i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    {  // exclusive scan of the 256 tile counts
+        uint32_t v = s_start[t];
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) s_scan[warp] = incl;
+        __syncthreads();
+        if (t == 0) {
+            uint32_t acc = 0;
+            for (int w = 0; w < RS_WARPS; ++w) {
+                uint32_t c = s_scan[w];
+                s_scan[w] = acc;
+                acc += c;
+            }
+        }
+        __syncthreads();
+        uint32_t ex = s_scan[warp] + incl - v;
+        __syncthreads();
+        s_start[t] = ex;
+        s_goff[t] = offs[(int64_t)t * nb + blockIdx.x] - ex;
+    }
+    __syncthreads();
+
+    // stable ranking, 256 items per round in input order
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int i = r * RS_THREADS + t;
+        const bool valid = i < tile_n;
+        KeyT key = valid ? kin[base + i] : (KeyT)0;
+        uint32_t val = valid ? vin[base + i] : 0u;
+        const uint32_t dg = valid ? ((uint32_t)(key >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t lower = peers & ((1u << lane) - 1u);
+        const uint32_t rank = __popc(lower);
+        const bool leader = lower == 0;
+        if (valid && leader) s_wc[warp][dg] = ((uint32_t)r << 16) | (uint32_t)__popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t pre = 0;
+            for (int w = 0; w < warp; ++w) {
+                uint32_t e = s_wc[w][dg];
+                if ((e >> 16) == (uint32_t)r) pre += e & 0xffffu;
+            }
+            uint32_t pos = s_start[dg] + s_run[dg] + pre + rank;
+            s_k[pos] = key;
+            s_v[pos] = val;
+        }
+        __syncthreads();
+        if (valid && leader) atomicAdd(&s_run[dg], (uint32_t)__popc(peers));
+        __syncthreads();
+    }
+    // write runs of equal digits to contiguous global ranges
+    for (int j = t; j < tile_n; j += RS_THREADS) {
+        KeyT key = s_k[j];
+        uint32_t dg = (uint32_t)(key >> shift) & 255u;
+        uint32_t g = s_goff[dg] + (uint32_t)j;
+        kout[g] = key;
+        vout[g] = s_v[j];
+    }
+}
+
+__device__ __forceinline__ int64_t corner_index(const int32_t* __restrict__ nb, int sx, int sy, int sz) {
+    // index shift (Listing 2) for shifts in [0, 4] from the home package
+    int nx = (sx + PKG) >> 2, ny = (sy + PKG) >> 2, nz = (sz + PKG) >> 2;
+    int pkg = __ldg(nb + nx + 3 * ny + 9 * nz);
+    return (int64_t)pkg * PKG3 + (sx + PKG - nx * PKG) + PKG * (sy + PKG - ny * PKG) + PKG * PKG * (sz + PKG - nz * PKG);
+}
+
+__global__ void __launch_bounds__(PR_THREADS) k_probe(GridF G, const int32_t* __restrict__ cell_pkg,
+                                                       const int32_t* __restrict__ nbr, ProbeFields F, int64_t n,
+                                                       const float* __restrict__ x, const float* __restrict__ y,
+                                                       const float* __restrict__ z, const int32_t* __restrict__ order,
+                                                       ProbeOut out) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = order ? (int64_t)__ldg(order + r) : r;
+        const float pos[3] = {__ldg(x + q), __ldg(y + q), __ldg(z + q)};
+        int i0[3], l[3];
+        float t[3];
+        bool inside = true;
+        int64_t c = 0, stride = 1;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lattice(pos[a], G.lo[a], G.h, i0[a], t[a]);
+            int I = i0[a] >> 2;  // floor division by 4
+            l[a] = i0[a] & 3;
+            inside &= I >= 0 && I < G.dims[a];
+            c += (int64_t)I * stride;
+            stride *= G.dims[a];
+        }
+        const int64_t home = inside ? (int64_t)__ldg(cell_pkg + c) : 1;
+        const int32_t* nb = nbr + home * NB;
+        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int cr = 0; cr < 8; ++cr) {
+            const int a0 = cr & 1, a1 = (cr >> 1) & 1, a2 = (cr >> 2) & 1;
+            const float w = (a0 ? t[0] : 1.0f - t[0]) * (a1 ? t[1] : 1.0f - t[1]) * (a2 ? t[2] : 1.0f - t[2]);
+            const int64_t at = corner_index(nb, l[0] + a0, l[1] + a1, l[2] + a2);
+#pragma unroll
+            for (int f = 0; f < 8; ++f) acc[f] = fmaf(w, __ldg(F.f[f] + at), acc[f]);
+        }
+        const float gn = sqrtf(acc[1] * acc[1] + acc[2] * acc[2] + acc[3] * acc[3]);
+        const float inv = gn > 0.0f ? 1.0f / gn : 0.0f;
+        if (out.o[0]) out.o[0][q] = acc[0];
+        if (out.o[1]) out.o[1][q] = acc[1] * inv;
+        if (out.o[2]) out.o[2][q] = acc[2] * inv;
+        if (out.o[3]) out.o[3][q] = acc[3] * inv;
+#pragma unroll
+        for (int f = 4; f < 8; ++f)
+            if (out.o[f]) out.o[f][q] = acc[f];
+    }
+}
+
+unsigned blocks_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 148 * 64) b = 148 * 64;
+    return (unsigned)b;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <typename KeyT>
+cudaError_t sort_impl(const GridF& G, int64_t n, int key_bits, const float* x, const float* y, const float* z,
+                      uint64_t* keys_out, int32_t* order_out, void* scratch, cudaStream_t s) {
+    const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
+    char* sp = (char*)scratch;
+    KeyT* k0 = (KeyT*)sp;
+    sp += align256(n * sizeof(KeyT));
+    KeyT* k1 = (KeyT*)sp;
+    sp += align256(n * sizeof(KeyT));
+    uint32_t* v0 = (uint32_t*)sp;
+    sp += align256(n * sizeof(uint32_t));
+    uint32_t* v1 = (uint32_t*)sp;
+    sp += align256(n * sizeof(uint32_t));
+    uint32_t* hist = (uint32_t*)sp;
+    sp += align256(256 * nb * sizeof(uint32_t));
+    void* scan_scratch = sp;
+
+    k_morton_keys<KeyT><<<blocks_for(n, RS_THREADS), RS_THREADS, 0, s>>>(G, n, x, y, z, k0, v0, keys_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int passes = (key_bits + 7) / 8;
+    const size_t smem = RS_TILE * (sizeof(KeyT) + sizeof(uint32_t));
+    e = cudaFuncSetAttribute(k_rs_scatter<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    KeyT* K[2] = {k0, k1};
+    uint32_t* V[2] = {v0, v1};
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        uint32_t* vout = (p == passes - 1) ? (uint32_t*)order_out : V[1 - cur];
+        k_rs_hist<KeyT><<<(unsigned)nb, RS_THREADS, 0, s>>>(K[cur], n, shift, hist, nb);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = exclusive_scan_u32(hist, hist, 256 * nb, nullptr, scan_scratch, s)) != cudaSuccess) return e;
+        k_rs_scatter<KeyT><<<(unsigned)nb, RS_THREADS, smem, s>>>(K[cur], V[cur], K[1 - cur], vout, n, shift, hist, nb);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        cur = 1 - cur;
+    }
+    if (passes == 0)
+        return cudaMemcpyAsync(order_out, V[0], n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+int morton_bits(const GridF& G) {
+    int m = 0;
+    for (int a = 0; a < 3; ++a) {
+        int v = 4 * G.dims[a] + 1, b = 0;
+        while ((1 << b) <= v) ++b;
+        if (b > m) m = b;
+    }
+    return 3 * m;
+}
+
+size_t sort_scratch_bytes(int64_t n, int key_bits) {
+    const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
+    size_t ks = key_bits <= 32 ? 4 : 8;
+    return 2 * align256(n * ks) + 2 * align256(n * 4) + align256(256 * nb * 4) + scan_scratch_bytes(256 * nb) + 256;
+}
+
+cudaError_t morton_sort(const GridF& G, int64_t n, const float* x, const float* y, const float* z, uint64_t* keys_out,
+                        int32_t* order_out, void* scratch, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int bits = morton_bits(G);
+    if (bits <= 32) return sort_impl<uint32_t>(G, n, bits, x, y, z, keys_out, order_out, scratch, s);
+    return sort_impl<uint64_t>(G, n, bits, x, y, z, keys_out, order_out, scratch, s);
+}
+
+cudaError_t launch_probe(const GridF& G, const int32_t* cell_pkg, const int32_t* nbr, const ProbeFields& F,
+                         int64_t n, const float* x, const float* y, const float* z, const int32_t* order,
+                         const ProbeOut& out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_probe<<<blocks_for(n, PR_THREADS), PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sg

@@ -1,0 +1,164 @@
+// sg_tag.cu -- band tagging, package numbering, neighbourhood table and
+// initial level-set values ("Initialization Process", steps 1-5).
+//
+// One thread per background cell for the flags, one per (package, entry)
+// for the table, one per data point for the level set.  All integer
+// results are exact; the only floating-point decision (core or not) is
+// taken on a float-float distance.
+#include "sg_internal.cuh"
+
+namespace sg {
+namespace {
+
+constexpr int TAG_THREADS = 256;
+
+__device__ __forceinline__ void cell_coords(int64_t c, const int* dims, int64_t& I, int64_t& J, int64_t& K) {
+    I = c % dims[0];
+    J = (c / dims[0]) % dims[1];
+    K = c / ((int64_t)dims[0] * dims[1]);
+}
+
+// Step 1: core cells, |d(centre)| < T; far cells keep the sign of d.
+__global__ void __launch_bounds__(TAG_THREADS) k_tag_flags(GridFF G, ShapeFF S, uint8_t* __restrict__ cell_type,
+                                                            uint32_t* __restrict__ active, int64_t nc) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t I[3];
+        cell_coords(c, G.dims, I[0], I[1], I[2]);
+        ff x[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) x[a] = ff_add(G.lo[a], ff_mul_f(G.h, (float)(4 * I[a] + 2)));
+        ff d = ff_sdf(S, x);
+        uint8_t t = ff_lt(ff_abs(d), G.T) ? 2 : (ff_neg_p(d) ? 0 : 1);
+        cell_type[c] = t;
+        active[c] = t == 2;
+    }
+}
+
+// Step 2: inner cells, not core and one of the 26 neighbours is core.
+__global__ void __launch_bounds__(TAG_THREADS) k_tag_inner(GridFF G, uint8_t* cell_type,
+                                                            uint32_t* __restrict__ active, int64_t nc) {
+    const int nx = G.dims[0], ny = G.dims[1], nz = G.dims[2];
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        if (cell_type[c] == 2) continue;
+        int64_t I, J, K;
+        cell_coords(c, G.dims, I, J, K);
+        bool found = false;
+        for (int dk = -1; dk <= 1; ++dk)
+            for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                    int64_t a = I + di, b = J + dj, e = K + dk;
+                    if (a < 0 || b < 0 || e < 0 || a >= nx || b >= ny || e >= nz) continue;
+                    found |= cell_type[a + nx * (b + (int64_t)ny * e)] == 2;
+                }
+        if (found) {
+            cell_type[c] = 3;  // other threads only test for == 2, unaffected
+            active[c] = 1;
+        }
+    }
+}
+
+// Step 3: ids in increasing cell index = 2 + exclusive prefix of active.
+__global__ void __launch_bounds__(TAG_THREADS) k_tag_scatter(const uint8_t* __restrict__ cell_type,
+                                                              const uint32_t* __restrict__ prefix,
+                                                              int32_t* __restrict__ cell_pkg,
+                                                              int32_t* __restrict__ pkg_cell,
+                                                              uint8_t* __restrict__ pkg_type, int64_t nc) {
+    if (blockIdx.x == 0 && threadIdx.x < 2) {
+        pkg_cell[threadIdx.x] = -1;
+        pkg_type[threadIdx.x] = (uint8_t)threadIdx.x;
+    }
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        uint8_t t = cell_type[c];
+        if (t >= 2) {
+            int32_t id = 2 + (int32_t)prefix[c];
+            cell_pkg[c] = id;
+            pkg_cell[id] = (int32_t)c;
+            pkg_type[id] = t;
+        } else {
+            cell_pkg[c] = t;
+        }
+    }
+}
+
+// Step 5: neighbourhood; outside the domain -> package 1; far packages self.
+__global__ void __launch_bounds__(TAG_THREADS) k_fill_nbr(GridFF G, const int32_t* __restrict__ cell_pkg,
+                                                           const int32_t* __restrict__ pkg_cell,
+                                                           int32_t* __restrict__ nbr, int64_t P) {
+    const int nx = G.dims[0], ny = G.dims[1], nz = G.dims[2];
+    const int64_t total = P * NB;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = e / NB;
+        int n = (int)(e - p * NB);
+        if (p < 2) {
+            nbr[e] = (int32_t)p;
+            continue;
+        }
+        int64_t I, J, K;
+        cell_coords(pkg_cell[p], G.dims, I, J, K);
+        int64_t a = I + (n % 3) - 1, b = J + (n / 3) % 3 - 1, c = K + n / 9 - 1;
+        bool in = a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz;
+        nbr[e] = in ? cell_pkg[a + nx * (b + (int64_t)ny * c)] : 1;
+    }
+}
+
+// Step 4: phi at cell-centred data points, float-float, rounded once.
+__global__ void __launch_bounds__(TAG_THREADS) k_init_sdf(GridFF G, ShapeFF S, const int32_t* __restrict__ pkg_cell,
+                                                           float* __restrict__ phi, int64_t P) {
+    const int64_t total = (P - 2) * PKG3;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = 2 + e / PKG3;
+        int d = (int)(e & (PKG3 - 1));
+        int64_t I[3];
+        cell_coords(pkg_cell[p], G.dims, I[0], I[1], I[2]);
+        int l[3] = {d & 3, (d >> 2) & 3, d >> 4};
+        ff x[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) x[a] = ff_add(G.lo[a], ff_mul_f(G.h, (float)(4 * I[a] + l[a]) + 0.5f));
+        phi[p * PKG3 + d] = ff_to_float(ff_sdf(S, x));
+    }
+}
+
+unsigned grid_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > (1 << 20)) b = 1 << 20;  // grid-stride beyond
+    return (unsigned)b;
+}
+
+}  // namespace
+
+cudaError_t launch_tag_flags(const GridFF& G, const ShapeFF& S, uint8_t* cell_type, uint32_t* active, int64_t nc,
+                             cudaStream_t s) {
+    k_tag_flags<<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, cell_type, active, nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tag_inner(const GridFF& G, uint8_t* cell_type, uint32_t* active, int64_t nc, cudaStream_t s) {
+    k_tag_inner<<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_type, active, nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* prefix, int32_t* cell_pkg,
+                               int32_t* pkg_cell, uint8_t* pkg_type, int64_t nc, cudaStream_t s) {
+    k_tag_scatter<<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(cell_type, prefix, cell_pkg, pkg_cell, pkg_type,
+                                                                     nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_nbr(const GridFF& G, const int32_t* cell_pkg, const int32_t* pkg_cell, int32_t* nbr,
+                            int64_t P, cudaStream_t s) {
+    k_fill_nbr<<<grid_for(P * NB, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_pkg, pkg_cell, nbr, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_sdf(const GridFF& G, const ShapeFF& S, const int32_t* pkg_cell, float* phi, float F,
+                            int64_t P, cudaStream_t s) {
+    cudaError_t e = launch_set_far(phi, -F, F, s);
+    if (e != cudaSuccess) return e;
+    if (P > 2) k_init_sdf<<<grid_for((P - 2) * PKG3, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, pkg_cell, phi, P);
+    return cudaGetLastError();
+}
+
+}  // namespace sg

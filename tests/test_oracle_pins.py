@@ -672,7 +672,7 @@ def test_morton_keys_bit_loop():
         for a, v in enumerate((x[q], y[q], z[q])):
             u = (np.float32(v) - np.float32(spec.lo[a])) / np.float32(spec.h) - np.float32(0.5)
             i0 = int(np.floor(np.float32(u)))
-            k.append(min(max(i0 + 1, 0), 2 ** 21 - 1))
+            k.append(min(max(i0 + 1, 0), 4 * spec.dims[a] + 1))
         ref = 0
         for b in range(21):
             for a in range(3):
