@@ -1,0 +1,480 @@
+#!/usr/bin/env python
+"""Benchmark of the sparse-grid level-set hot path on one or more B300s.
+
+Workload (per GPU): the torus (R = 0.6, r = 0.2) and the extruded triangular
+prism, each on its own sparse grid at h = 0.002.  One step runs, for each
+body: band tagging and package allocation, float-float level-set init,
+gradient, 50 Godunov reinitialisation sweeps (CFL 0.5), exact kernel
+integrals, and a Morton-ordered probe of 50M particles in the band.
+
+Prints one JSON line.  ``value`` is cell-updates/s over the whole step (init,
+gradient, each reinit sweep and the integrals each update every active data
+point once; probe time counts in the denominator, probes are reported
+separately).  ``--impl reference`` times the FP64 CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import sg_inputs as si  # noqa: E402
+
+CFL = 0.5
+BAND_HALF_WIDTH_CELLS = 2  # particles within +-2 coarse cells of the surface
+HBM_FALLBACK_GBS = 6400.0
+
+
+# ----------------------------------------------------------------------------
+# host-side helpers (also exercised by the CPU multi-process tests)
+# ----------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def combine_over_ranks(seconds: float, units: float, backend_device=None):
+    """(max seconds over ranks, sum of units over ranks); identity at world 1."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return seconds, units
+    dev = backend_device or "cpu"
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def source_digest(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profile_traffic(kernel_file, summary):
+    """DRAM traffic per launch from a committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(p):
+        return None
+    fields = {}
+    for line in open(p):
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha256_16",
+                                                    "units_per_launch")):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("kernel_source_sha256_16") != source_digest(kernel_file):
+        return None
+    try:
+        return float(fields["traffic_bytes_per_launch"]), float(fields.get("units_per_launch", "nan"))
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if r[5 + k].strip().lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+def bodies_for(names, h):
+    out = []
+    for name in names:
+        if name == "torus":
+            shape, spec = si.torus_large(h)
+        elif name == "prism":
+            shape, spec = si.prism_large(h)
+        elif name == "sphere_small":
+            shape, spec = si.sphere_small()
+        else:
+            raise ValueError(name)
+        out.append((name, shape, spec))
+    return out
+
+
+def particles_for(name, shape, spec, n, seed):
+    w = BAND_HALF_WIDTH_CELLS * spec.lc
+    jit = 0.5 * spec.h
+    if name == "torus":
+        return si.torus_band_particles(n, shape.p[0], shape.p[1], w, seed=seed, jitter=jit)
+    if name == "prism":
+        tri = ((shape.p[0], shape.p[1]), (shape.p[2], shape.p[3]), (shape.p[4], shape.p[5]))
+        return si.prism_band_particles(n, tri, shape.p[6], shape.p[7], w, seed=seed, jitter=jit)
+    return si.sphere_shell_particles(n, shape.p[0], 3 * spec.h, seed=seed)
+
+
+class Body:
+    def __init__(self, sg, torch, name, shape, spec, n_particles, seed, iters):
+        self.name, self.shape, self.spec, self.iters = name, shape, spec, iters
+        self.g = sg.Grid(spec)
+        self.P = self.g.tag_allocate(shape)
+        self.n_pt = 64 * (self.P - 2)
+        x, y, z = particles_for(name, shape, spec, n_particles, seed)
+        dev = [torch.from_numpy(v).cuda() for v in (x, y, z)]
+        # the workload's particles are stored in Morton order (input preparation)
+        _, order = self.g.morton_order(*dev)
+        order = order.long()
+        self.X = [v[order].contiguous() for v in dev]
+        self.n = n_particles
+        self.out = {k: torch.empty(n_particles, dtype=torch.float32, device="cuda") for k in sg.PROBE_OUTPUTS}
+        self.host_x = None
+        self.host_out = None
+
+    def pin_host(self, torch):
+        self.host_x = [v.cpu().pin_memory() for v in self.X]
+        self.host_out = {k: torch.empty(self.n, dtype=torch.float32).pin_memory() for k in self.out}
+
+    def run(self, ev=None, phases=None):
+        g = self.g
+
+        def mark(name):
+            if ev is not None:
+                e = ev()
+                e.record()
+                phases.append((self.name + ":" + name, e))
+
+        mark("start")
+        g.tag_allocate(self.shape)
+        mark("tag")
+        g.init_sdf(self.shape)
+        mark("init")
+        g.gradient()
+        mark("gradient")
+        g.reinit(self.iters, CFL)
+        mark("reinit")
+        g.kernel_integrals()
+        mark("integrals")
+        g.probe(*self.X, morton=True, out=self.out)
+        mark("probe")
+
+    def run_e2e(self):
+        for d, h in zip(self.X, self.host_x):
+            d.copy_(h, non_blocking=True)
+        self.run()
+        for k, v in self.out.items():
+            self.host_out[k].copy_(v, non_blocking=True)
+
+
+def phase_totals(phases):
+    """Sum the durations between consecutive markers per phase name (ms)."""
+    tot = {}
+    for (n0, e0), (n1, e1) in zip(phases[:-1], phases[1:]):
+        if n1.endswith(":start"):
+            continue
+        key = n1
+        tot[key] = tot.get(key, 0.0) + e0.elapsed_time(e1)
+    return tot
+
+
+# ----------------------------------------------------------------------------
+# oracle (CPU) samples
+# ----------------------------------------------------------------------------
+_PARTICLE_CACHE = {}
+
+
+def oracle_sample(frac, iters, n_particles_full, seed=2):
+    """Oracle pass over a spatial sample of the torus workload: the sub-domain
+    x in [-1, -1 + 2 frac] of the h = 0.002 torus grid, the same per-point
+    steps (tag/init, gradient, iters reinit sweeps, integrals), and a Morton
+    sort plus probe of frac * n_particles_full band particles.
+    Returns (cell_updates, probes, seconds, description)."""
+    import oracle
+    shape, spec = si.torus_large()
+    nx = max(1, int(round(spec.dims[0] * frac)))
+    sub = si.GridSpec(spec.lo, (nx, spec.dims[1], spec.dims[2]), spec.h)
+    m = max(1000, int(n_particles_full * nx / spec.dims[0]))
+    key = (m, seed)
+    if key not in _PARTICLE_CACHE:
+        _PARTICLE_CACHE.clear()
+        _PARTICLE_CACHE[key] = particles_for("torus", shape, spec, m, seed)
+    x, y, z = _PARTICLE_CACHE[key]
+    t0 = time.perf_counter()
+    G = oracle.build_grid(sub, shape)
+    gx, gy, gz = oracle.gradient(sub, G.nbr, G.phi)
+    phi = oracle.reinit(sub, G.nbr, G.phi, iters, CFL)
+    W, Gx, Gy, Gz = oracle.kernel_integrals(sub, G.nbr, phi)
+    keys = oracle.morton_keys(sub, x, y, z)
+    order = oracle.morton_order(keys)
+    oracle.probe(sub, G.cell_pkg, G.nbr, [phi, gx, gy, gz, W, Gx, Gy, Gz], x[order], y[order], z[order])
+    secs = time.perf_counter() - t0
+    n_pt = 64 * (G.P - 2)
+    desc = ("torus h=0.002 sub-domain x in [-1, %.3f] (%d of %d cell columns, %d packages), %d reinit sweeps, "
+            "%d probes" % (sub.lo[0] + nx * sub.lc, nx, spec.dims[0], G.P, iters, m))
+    return n_pt * (iters + 3), m, secs, desc
+
+
+def oracle_calibrate(iters, n_particles_full, frac=0.04):
+    """Seconds the full oracle pass would take, extrapolated linearly from a
+    small spatial sample."""
+    _, _, secs, _ = oracle_sample(frac, iters, n_particles_full)
+    return secs / frac
+
+
+def cpu_threads():
+    import oracle
+    return oracle.get_threads()
+
+
+# ----------------------------------------------------------------------------
+# arms
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    est = oracle_calibrate(args.iters, args.particles)
+    budget = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    frac = min(1.0, max(0.02, budget / est))
+    for _ in range(args.warmup):
+        oracle_sample(frac, args.iters, args.particles)
+    total_u, total_s, desc = 0.0, 0.0, ""
+    for _ in range(args.steps):
+        u, _, s, desc = oracle_sample(frac, args.iters, args.particles)
+        total_u += u
+        total_s += s
+    value = total_u / total_s
+    line = {"impl": "reference", "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "torus+prism h=0.002, 50 reinit sweeps, exact integrals, 50M Morton probes "
+                                   "per body (oracle: bounded spatial sample per step)", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_sg(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2512_11473_b300 import build as sg_build
+    sg_build.build()  # no-op unless a source is newer than libsg.so
+    import paper_2512_11473_b300 as sg
+
+    names = args.bodies.split(",")
+    bodies = [Body(sg, torch, n, s, sp, args.particles, 2 + k, args.iters)
+              for k, (n, s, sp) in enumerate(bodies_for(names, args.h))]
+    torch.cuda.synchronize()
+    cell_updates = sum(b.n_pt * (args.iters + 3) for b in bodies)
+    probes = sum(b.n for b in bodies)
+
+    for _ in range(args.warmup):
+        for b in bodies:
+            b.run()
+    torch.cuda.synchronize()
+    barrier()
+
+    Ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = sg.kernel_launch_count()
+    phases = []
+    torch.cuda.synchronize()
+    barrier()
+    t_start = Ev()
+    t_start.record()
+    for _ in range(args.steps):
+        for b in bodies:
+            b.run(Ev, phases)
+    t_end = Ev()
+    t_end.record()
+    torch.cuda.synchronize()
+    barrier()
+    launches = sg.kernel_launch_count() - launches0
+    clk = clocks.stop()
+    secs = t_start.elapsed_time(t_end) / 1e3
+    tmax, units = combine_over_ranks(secs, cell_updates * args.steps, "cuda")
+    value = units / tmax
+
+    # per-phase breakdown (device events on the launching stream)
+    tot = phase_totals(phases)
+    breakdown = {k: v / args.steps for k, v in sorted(tot.items())}
+    probe_ms = sum(v for k, v in breakdown.items() if k.endswith(":probe"))
+
+    # dominant kernel: one reinit sweep; subtract the per-call set-up
+    # (smoothed sign + far fill) measured separately, divide by the sweeps
+    setup_ms = {}
+    for b in bodies:
+        e0, e1 = Ev(), Ev()
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            b.g.reinit(0, CFL)
+        e1.record()
+        torch.cuda.synchronize()
+        setup_ms[b.name] = e0.elapsed_time(e1) / reps
+    sweep_ms = {b.name: (breakdown[b.name + ":reinit"] - setup_ms[b.name]) / args.iters for b in bodies}
+    big = max(bodies, key=lambda b: b.P)
+    alg_bytes = 12.0 * big.n_pt + 108.0 * (big.P - 2)
+    hbm, peak_kind = measured_peaks()
+    achieved = alg_bytes / (sweep_ms[big.name] * 1e-3) / 1e9
+    prof = profile_traffic(os.path.join(ROOT, "paper_2512_11473_b300", "csrc", "sg_sweep.cu"),
+                           "reinit_step_torus_h0.002.md")
+    traffic = None
+    if prof is not None:
+        tb, units_prof = prof
+        traffic = tb * (big.n_pt / units_prof) if units_prof == units_prof and units_prof > 0 else tb
+
+    line = {
+        "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": "torus (R 0.6, r 0.2) + prism ((0,0),(1,0),(0.3,0.8) x [0,1]) at h=%g: tag/allocate, "
+                        "init, gradient, %d reinit sweeps (CFL 0.5), exact kernel integrals, Morton probe of "
+                        "%d particles per body" % (args.h, args.iters, args.particles),
+            "bodies": {b.name: {"packages": b.P, "points": b.n_pt, "cells": b.spec.n_cells} for b in bodies},
+            "cell_updates_per_step": cell_updates, "probes_per_step": probes,
+            "l2": "inputs larger than L2: every reinit sweep streams >= 196 MB and a step touches several GB",
+            "parallelism": "replicas (independent bodies per GPU, no collective)",
+        },
+        "probes_per_s": probes / (probe_ms * 1e-3) if probe_ms > 0 else None,
+        "breakdown_ms_per_step": breakdown,
+        "roofline": {"bound": "hbm", "kernel": "k_reinit_step (%s)" % big.name, "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
+                     "launch_ms": sweep_ms[big.name]},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        for b in bodies:
+            b.pin_host(torch)
+        for _ in range(max(1, min(args.warmup, 2))):
+            for b in bodies:
+                b.run_e2e()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = Ev(), Ev()
+        e0.record()
+        for _ in range(args.steps):
+            for b in bodies:
+                b.run_e2e()
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        esecs, eunits = combine_over_ranks(e0.elapsed_time(e1) / 1e3, cell_updates * args.steps, "cuda")
+        line["e2e"] = {"value": eunits / esecs, "unit": "cell-updates/s",
+                       "h2d_bytes_per_step": sum(12 * b.n for b in bodies),
+                       "d2h_bytes_per_step": sum(4 * len(b.out) * b.n for b in bodies)}
+    if not args.no_cpu_baseline and rank == 0 and ws == 1:
+        est = oracle_calibrate(args.iters, args.particles)
+        frac = min(1.0, max(0.02, 15.0 / est))
+        u, m, s, desc = oracle_sample(frac, args.iters, args.particles)
+        line["cpu_baseline"] = {"value": u / s, "unit": "cell-updates/s", "cores": cpu_threads(), "kind": "oracle",
+                                "sample": desc, "seconds": s}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["sg", "reference"], default="sg")
+    ap.add_argument("--bodies", default="torus,prism")
+    ap.add_argument("--h", type=float, default=0.002)
+    ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--particles", type=int, default=50_000_000, help="probe particles per body")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_sg(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

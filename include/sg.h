@@ -215,6 +215,10 @@ SG_API const char *sg_last_error(const sg_grid *g);
 /* Library version string. */
 SG_API const char *sg_version(void);
 
+/* Number of CUDA kernels this process has launched through the library so
+ * far (all grids, all devices); for accounting launches in a timed region. */
+SG_API int64_t sg_kernel_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

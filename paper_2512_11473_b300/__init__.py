@@ -91,6 +91,7 @@ def lib():
         L.sg_last_error.argtypes = [vp]
         L.sg_last_error.restype = C.c_char_p
         L.sg_version.restype = C.c_char_p
+        L.sg_kernel_launch_count.restype = i64
         for name in declared_symbols():
             f = getattr(L, name)
             if f.restype is C.c_int:  # default: sg_status
@@ -277,3 +278,8 @@ class Grid:
 
 def version() -> str:
     return lib().sg_version().decode()
+
+
+def kernel_launch_count() -> int:
+    """Kernels launched by libsg in this process so far."""
+    return int(lib().sg_kernel_launch_count())

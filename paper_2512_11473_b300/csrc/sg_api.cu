@@ -1,6 +1,7 @@
 // sg_api.cu -- the extern "C" entry points of libsg (declared in sg.h):
 // argument checks, state order, ownership of the device arrays and launch of
 // the kernels in sg_tag.cu, sg_sweep.cu and sg_probe.cu on the grid's stream.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -10,6 +11,8 @@
 namespace sg {
 
 namespace {
+
+std::atomic<int64_t> g_launches{0};
 
 struct DeviceGuard {
     int prev = -1;
@@ -29,6 +32,8 @@ ff split(double v) {
 }
 
 }  // namespace
+
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void* grid_alloc(sg_grid* g, size_t bytes) {
     if (bytes == 0) bytes = 256;
@@ -133,6 +138,8 @@ static bool valid_shape(const sg_shape* s) {
 extern "C" {
 
 const char* sg_version(void) { return "libsg 0.1 (sm_103a)"; }
+
+int64_t sg_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 sg_status sg_create(const sg_grid_desc* desc, const sg_allocator* alloc, void* stream, sg_grid** out) {
     if (!desc || !out) return SG_ERR_INVALID;

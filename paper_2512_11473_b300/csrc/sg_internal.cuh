@@ -65,6 +65,9 @@ struct sg_grid {
 
 namespace sg {
 
+// process-wide count of kernels launched by the library (sg_api.cu)
+void note_launch(int n = 1);
+
 // memory (sg_api.cu)
 void* grid_alloc(sg_grid* g, size_t bytes);
 void grid_free(sg_grid* g, Buf& b);

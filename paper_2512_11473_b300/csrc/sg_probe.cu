@@ -246,6 +246,7 @@ cudaError_t sort_impl(const GridF& G, int64_t n, int key_bits, const float* x, c
     void* scan_scratch = sp;
 
     k_morton_keys<KeyT><<<blocks_for(n, RS_THREADS), RS_THREADS, 0, s>>>(G, n, x, y, z, k0, v0, keys_out);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int passes = (key_bits + 7) / 8;
@@ -259,9 +260,11 @@ cudaError_t sort_impl(const GridF& G, int64_t n, int key_bits, const float* x, c
         const int shift = 8 * p;
         uint32_t* vout = (p == passes - 1) ? (uint32_t*)order_out : V[1 - cur];
         k_rs_hist<KeyT><<<(unsigned)nb, RS_THREADS, 0, s>>>(K[cur], n, shift, hist, nb);
+        note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = exclusive_scan_u32(hist, hist, 256 * nb, nullptr, scan_scratch, s)) != cudaSuccess) return e;
         k_rs_scatter<KeyT><<<(unsigned)nb, RS_THREADS, smem, s>>>(K[cur], V[cur], K[1 - cur], vout, n, shift, hist, nb);
+        note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         cur = 1 - cur;
     }
@@ -301,6 +304,7 @@ cudaError_t launch_probe(const GridF& G, const int32_t* cell_pkg, const int32_t*
                          const ProbeOut& out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_probe<<<blocks_for(n, PR_THREADS), PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, out);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -116,8 +116,11 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uin
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     uint32_t* partial = (uint32_t*)scratch;
     k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, partial);
+    note_launch();
     k_scan_spine<<<1, SPINE_THREADS, 0, s>>>(partial, nb, total);
+    note_launch();
     k_scan_down<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, partial);
+    note_launch();
     return cudaGetLastError();
 }
 

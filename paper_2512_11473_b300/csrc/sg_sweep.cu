@@ -227,6 +227,7 @@ double wendland_dq(double q) {
 
 cudaError_t launch_set_far(float* f, float v_in, float v_out, cudaStream_t s) {
     k_set_far<<<1, 2 * PKG3, 0, s>>>(f, v_in, v_out);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -234,6 +235,7 @@ cudaError_t launch_gradient(const GridF& G, const int32_t* nbr, const float* phi
                             int64_t P, cudaStream_t s) {
     if (P <= 2) return cudaSuccess;
     k_gradient<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, phi, gx, gy, gz, P, (float)(1.0 / (2.0 * G.h_d)));
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -241,6 +243,7 @@ cudaError_t launch_laplacian(const GridF& G, const int32_t* nbr, const float* ph
                              cudaStream_t s) {
     if (P <= 2) return cudaSuccess;
     k_laplacian<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, phi, lap, P, (float)(1.0 / (G.h_d * G.h_d)));
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -248,6 +251,7 @@ cudaError_t launch_reinit_s0(const GridF& G, const float* phi, float* s0, int64_
     if (P <= 2) return cudaSuccess;
     int64_t n = (P - 2) * PKG3;
     k_reinit_s0<<<flat_blocks(n), SW_THREADS, 0, s>>>(phi, s0, n, (float)(G.h_d * G.h_d));
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -255,6 +259,7 @@ cudaError_t launch_reinit_step(const GridF& G, const int32_t* nbr, const float* 
                                float* phi_out, float dt, int64_t P, cudaStream_t s) {
     if (P <= 2) return cudaSuccess;
     k_reinit_step<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, s0, phi_in, phi_out, P, (float)(1.0 / G.h_d), dt);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -262,6 +267,7 @@ cudaError_t launch_copy_active(const float* src, float* dst, int64_t P, cudaStre
     if (P <= 2) return cudaSuccess;
     int64_t n = (P - 2) * PKG3;
     k_copy<<<flat_blocks(n), SW_THREADS, 0, s>>>(src + 2 * PKG3, dst + 2 * PKG3, n);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -282,6 +288,7 @@ cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const fl
     }
     K.inv_eps = (float)(1.0 / G.h_d);
     k_kernel_integrals<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, K);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -132,11 +132,13 @@ unsigned grid_for(int64_t n, int threads) {
 cudaError_t launch_tag_flags(const GridFF& G, const ShapeFF& S, uint8_t* cell_type, uint32_t* active, int64_t nc,
                              cudaStream_t s) {
     k_tag_flags<<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, cell_type, active, nc);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_tag_inner(const GridFF& G, uint8_t* cell_type, uint32_t* active, int64_t nc, cudaStream_t s) {
     k_tag_inner<<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_type, active, nc);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -144,12 +146,14 @@ cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* prefix,
                                int32_t* pkg_cell, uint8_t* pkg_type, int64_t nc, cudaStream_t s) {
     k_tag_scatter<<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(cell_type, prefix, cell_pkg, pkg_cell, pkg_type,
                                                                      nc);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_fill_nbr(const GridFF& G, const int32_t* cell_pkg, const int32_t* pkg_cell, int32_t* nbr,
                             int64_t P, cudaStream_t s) {
     k_fill_nbr<<<grid_for(P * NB, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_pkg, pkg_cell, nbr, P);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -157,7 +161,10 @@ cudaError_t launch_init_sdf(const GridFF& G, const ShapeFF& S, const int32_t* pk
                             int64_t P, cudaStream_t s) {
     cudaError_t e = launch_set_far(phi, -F, F, s);
     if (e != cudaSuccess) return e;
-    if (P > 2) k_init_sdf<<<grid_for((P - 2) * PKG3, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, pkg_cell, phi, P);
+    if (P > 2) {
+        k_init_sdf<<<grid_for((P - 2) * PKG3, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, pkg_cell, phi, P);
+        note_launch();
+    }
     return cudaGetLastError();
 }
 
