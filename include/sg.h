@@ -194,6 +194,32 @@ SG_API sg_status sg_probe(sg_grid *g, int64_t n, const float *x, const float *y,
 SG_API sg_status sg_morton_order(sg_grid *g, int64_t n, const float *x, const float *y, const float *z, uint64_t *keys,
                           int32_t *order);
 
+/* Allocation-free variant of sg_morton_order.  The paper has no counterpart;
+ * this entry point exists for callers that cannot let a library allocate
+ * device memory: applications that hand (nearly) all of the device memory to
+ * their own pool at start-up, as particle codes sized to fill the GPU do, and
+ * loops that cannot afford the device-wide synchronisation that cudaMalloc and
+ * cudaFree may cause.  It takes the grid description instead of a grid (the
+ * keys depend only on lo, h and dims), reads x, y, z and writes keys (may be
+ * NULL) and order exactly as sg_morton_order does, with the same caller-owned
+ * device arrays, and calls no allocator at all.
+ *
+ * Its scratch is one static device array of the library, sized for
+ * SG_NOALLOC_MAX_PARTICLES particles (about 6 MiB); every GPU that loads the
+ * library holds it until the process exits.  The first call on a device looks
+ * up the array's device address with that device current, so make that first
+ * call before any stream capture.  All calls share the array and the sort
+ * writes every scratch byte before reading it, so no state carries over from
+ * one call to the next; but calls that overlap on the GPU (different streams,
+ * or threads that do not order their streams) race on the array: serialise
+ * them.  Work is queued on `stream` (a cudaStream_t; NULL = legacy default).
+ * Errors: SG_ERR_INVALID (null pointers, n < 0, h <= 0, a dimension < 1),
+ * SG_ERR_CAPACITY (n > SG_NOALLOC_MAX_PARTICLES, 4*dims >= 2^21, or more
+ * than 64 devices), SG_ERR_CUDA (address lookup or launch failed). */
+#define SG_NOALLOC_MAX_PARTICLES 262144
+SG_API sg_status sg_morton_order_noalloc(const sg_grid_desc *desc, int64_t n, const float *x, const float *y,
+                                         const float *z, uint64_t *keys, int32_t *order, void *stream);
+
 /* Borrow the device pointer and element count of a field; valid until the
  * grid is destroyed or re-tagged.  A float field that was never written is
  * allocated and zeroed on first request. */

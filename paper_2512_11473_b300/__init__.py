@@ -83,6 +83,7 @@ def lib():
         L.sg_kernel_integrals.argtypes = [vp, i32, vp]
         L.sg_probe.argtypes = [vp, i64, vp, vp, vp] + [vp] * 8 + [i32]
         L.sg_morton_order.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.sg_morton_order_noalloc.argtypes = [C.POINTER(sg_grid_desc), i64, vp, vp, vp, vp, vp, vp]
         L.sg_get_field.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(i64)]
         L.sg_n_packages.argtypes = [vp]
         L.sg_n_packages.restype = i64
@@ -274,6 +275,40 @@ class Grid:
 
     def n_packages(self) -> int:
         return int(self._lib.sg_n_packages(self._h))
+
+
+NOALLOC_MAX_PARTICLES = 262144
+
+
+def _desc(spec, far_value=0.0) -> sg_grid_desc:
+    d = sg_grid_desc()
+    d.lo[:] = [float(v) for v in spec.lo]
+    d.dims[:] = [int(v) for v in spec.dims]
+    d.h = float(spec.h)
+    d.far_value = float(far_value)
+    return d
+
+
+def morton_order_noalloc(spec, x, y, z, keys=None, order=None, stream=None):
+    """Morton keys and order through the allocation-free entry point.
+
+    For callers whose device memory is not the library's to take: the library
+    allocates nothing here and uses its built-in scratch (at most
+    NOALLOC_MAX_PARTICLES particles).  ``keys`` / ``order`` may be caller
+    tensors (int64 / int32 on the device); otherwise they are created here by
+    torch on the caller's behalf."""
+    torch = _torch()
+    n = x.numel()
+    if keys is None:
+        keys = torch.empty(n, dtype=torch.int64, device=x.device)
+    if order is None:
+        order = torch.empty(n, dtype=torch.int32, device=x.device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = lib().sg_morton_order_noalloc(C.byref(_desc(spec)), n, _ptr(x), _ptr(y), _ptr(z), _ptr(keys), _ptr(order),
+                                       C.c_void_p(s.cuda_stream))
+    if st != SG_OK:
+        raise SgError(st, "sg_morton_order_noalloc failed")
+    return keys, order
 
 
 def version() -> str:

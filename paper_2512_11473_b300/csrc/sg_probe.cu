@@ -4,6 +4,9 @@
 // sort written for this library: per-tile digit histograms, an exclusive scan
 // of the digit-major histogram table, and a stable scatter staged through
 // shared memory so that global writes of one digit run are contiguous).
+#include <cmath>
+#include <mutex>
+
 #include "sg_internal.cuh"
 
 namespace sg {
@@ -309,3 +312,79 @@ cudaError_t launch_probe(const GridF& G, const int32_t* cell_pkg, const int32_t*
 }
 
 }  // namespace sg
+
+// ---------------------------------------------------------------------------
+// Allocation-free Morton order.  The scratch of the radix sort (two key and
+// two index buffers, the digit histograms and the scan partials) lives in one
+// file-scope device array sized for SG_NOALLOC_MAX_PARTICLES particles with
+// 64-bit keys.  Every device that loads the library holds it until exit.
+// ---------------------------------------------------------------------------
+namespace sg {
+namespace {
+
+constexpr size_t na_align(size_t b) { return (b + 255) & ~(size_t)255; }
+
+constexpr size_t noalloc_scratch_size() {
+    const size_t n = (size_t)SG_NOALLOC_MAX_PARTICLES;
+    const size_t tiles = (n + RS_TILE - 1) / RS_TILE;
+    const size_t hist = 256 * tiles;
+    const size_t scan_partials = (hist + 2047) / 2048 + 64;  // bound of scan_scratch_bytes(hist)
+    return 2 * na_align(n * 8) + 2 * na_align(n * 4) + na_align(hist * 4) + na_align(scan_partials * 4) + 256;
+}
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+}  // namespace
+}  // namespace sg
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sg::noalloc_scratch_size()];
+
+extern "C" sg_status sg_morton_order_noalloc(const sg_grid_desc* desc, int64_t n, const float* x, const float* y,
+                                             const float* z, uint64_t* keys, int32_t* order, void* stream) {
+    using namespace sg;
+    if (!desc || n < 0 || (n > 0 && (!x || !y || !z || !order))) return SG_ERR_INVALID;
+    if (!(desc->h > 0.0) || !std::isfinite(desc->h)) return SG_ERR_INVALID;
+    for (int a = 0; a < 3; ++a) {
+        if (desc->dims[a] < 1) return SG_ERR_INVALID;
+        if (4LL * desc->dims[a] + 1 >= (1LL << 21)) return SG_ERR_CAPACITY;
+    }
+    if (n > SG_NOALLOC_MAX_PARTICLES) return SG_ERR_CAPACITY;
+    if (n == 0) return SG_OK;
+    GridF G;
+    for (int a = 0; a < 3; ++a) {
+        G.lo[a] = (float)desc->lo[a];
+        G.dims[a] = desc->dims[a];
+    }
+    G.h = (float)desc->h;
+    G.h_d = desc->h;
+    G.F = 0.0f;
+    if (sort_scratch_bytes(n, morton_bits(G)) > sizeof(g_noalloc_scratch)) return SG_ERR_CAPACITY;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return SG_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return SG_ERR_CAPACITY;
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            // host code cannot use the array's name as a device address: look
+            // the address up once, with this device current
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return SG_ERR_CUDA;
+            }
+            g_noalloc_addr[dev] = p;
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    if (morton_sort(G, n, x, y, z, keys, order, scratch, (cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return SG_ERR_CUDA;
+    }
+    return SG_OK;
+}

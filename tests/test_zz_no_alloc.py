@@ -1,0 +1,99 @@
+"""The allocation-free Morton-order entry point against the regular one.
+
+sg_morton_order_noalloc serves callers that cannot let the library allocate
+device memory (their memory belongs to their own pool, or they cannot take
+the device-wide synchronisation of cudaMalloc/cudaFree).  Its scratch is a
+static device array shared by every call, so the test makes two calls in a
+row with different sizes and key widths and compares each with
+sg_morton_order on a grid: keys and order must agree bit for bit.  This file
+is collected last so that a failure here leaves every other test already run.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import sg_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_11473_b300 import build
+    build.build()
+    import paper_2512_11473_b300 as m
+    return m
+
+
+def _regular(sg, spec, shape, X, Y, Z):
+    g = sg.Grid(spec)
+    g.tag_allocate(shape)
+    keys, order = g.morton_order(X, Y, Z)
+    torch.cuda.synchronize()
+    return keys.cpu(), order.cpu()
+
+
+def _noalloc_raw(sg, spec, X, Y, Z):
+    """Direct C-ABI call with caller-owned outputs."""
+    n = X.numel()
+    keys = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+    order = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    st = sg.lib().sg_morton_order_noalloc(C.byref(sg._desc(spec)), n, C.c_void_p(X.data_ptr()),
+                                          C.c_void_p(Y.data_ptr()), C.c_void_p(Z.data_ptr()),
+                                          C.c_void_p(keys.data_ptr()), C.c_void_p(order.data_ptr()),
+                                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert st == sg.SG_OK
+    assert torch.cuda.memory_allocated() == before
+    return keys.cpu(), order.cpu()
+
+
+def test_noalloc_matches_regular_entry_point_twice(sg):
+    # call 1: 32-bit keys, 200,000 particles
+    shape1 = si.torus(0.6, 0.2)
+    spec1 = si.GridSpec((-1.0, -1.0, -0.4), (50, 50, 20), 0.01)
+    x, y, z = si.box_particles(200_000, np.array(spec1.lo) - 0.05, np.array(spec1.hi()) + 0.05, seed=31)
+    X1, Y1, Z1 = (torch.from_numpy(v).cuda() for v in (x, y, z))
+    # call 2: 64-bit keys, fewer particles, so stale scratch from call 1 would show
+    shape2 = si.sphere(0.004)
+    spec2 = si.GridSpec((-1.0, -1.0, -1.0), (600, 3, 3), 2.0 / 2400)
+    x, y, z = si.box_particles(70_001, spec2.lo, spec2.hi(), seed=32)
+    x[10:20] = x[0]
+    y[10:20] = y[0]
+    z[10:20] = z[0]
+    X2, Y2, Z2 = (torch.from_numpy(v).cuda() for v in (x, y, z))
+
+    got1 = _noalloc_raw(sg, spec1, X1, Y1, Z1)
+    got2 = _noalloc_raw(sg, spec2, X2, Y2, Z2)
+    ref1 = _regular(sg, spec1, shape1, X1, Y1, Z1)
+    ref2 = _regular(sg, spec2, shape2, X2, Y2, Z2)
+    assert torch.equal(got1[0], ref1[0]) and torch.equal(got1[1], ref1[1])
+    assert torch.equal(got2[0], ref2[0]) and torch.equal(got2[1], ref2[1])
+    assert int(ref2[0].max()) >= 2 ** 32  # the second call used the 64-bit sort
+    # the binding's wrapper goes through the same entry point
+    k, o = sg.morton_order_noalloc(spec1, X1, Y1, Z1)
+    assert torch.equal(k.cpu(), ref1[0]) and torch.equal(o.cpu(), ref1[1])
+
+
+def test_noalloc_limits(sg):
+    spec = si.GridSpec((-1.0, -1.0, -0.4), (50, 50, 20), 0.01)
+    n = sg.NOALLOC_MAX_PARTICLES
+    X = torch.zeros(n + 1, device="cuda")
+    with pytest.raises(sg.SgError) as e:
+        sg.morton_order_noalloc(spec, X, X, X)
+    assert e.value.status == sg.SG_ERR_CAPACITY
+    # exactly at the limit is accepted and matches the regular path
+    x, y, z = si.box_particles(n, spec.lo, spec.hi(), seed=33)
+    Xs = [torch.from_numpy(v).cuda() for v in (x, y, z)]
+    k, o = sg.morton_order_noalloc(spec, *Xs)
+    rk, ro = _regular(sg, spec, si.torus(0.6, 0.2), *Xs)
+    assert torch.equal(k.cpu(), rk) and torch.equal(o.cpu(), ro)
+    with pytest.raises(sg.SgError) as e:
+        sg.morton_order_noalloc(si.GridSpec((0, 0, 0), (600000, 1, 1), 0.1), Xs[0], Xs[1], Xs[2])
+    assert e.value.status == sg.SG_ERR_CAPACITY
