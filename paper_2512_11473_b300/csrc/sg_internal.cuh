@@ -6,7 +6,7 @@
 
 #include <string>
 
-#include "../../include/sg.h"
+#include "sg.h"
 #include "sg_ff.cuh"
 
 namespace sg {

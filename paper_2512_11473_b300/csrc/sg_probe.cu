@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_morton_keys(GridF G, int64_t n, 
     }
 }
 
+// Per-tile digit histogram, written digit-major: hist[d * nb + tile].
 template <typename KeyT>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const KeyT* __restrict__ keys, int64_t n, int shift,
                                                         uint32_t* __restrict__ hist, int64_t nb) {
@@ -82,6 +83,12 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const KeyT* __restrict__
     hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
+// Stable scatter of one 8-bit digit.  Warp w ranks its own contiguous 512
+// keys of the tile in 16 rounds of 32 (match_any groups equal digits; a
+// warp-private counter per digit gives the rank), so the rank order is the
+// input order.  A block pass turns the per-warp counts into tile offsets, the
+// keys are staged in shared memory in digit order and written out so that
+// each digit's run is one contiguous global range.
 template <typename KeyT>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            KeyT* __restrict__ kout, uint32_t* __restrict__ vout,
@@ -90,83 +97,78 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const KeyT* __restric
     extern __shared__ __align__(16) unsigned char smem[];
     KeyT* s_k = (KeyT*)smem;
     uint32_t* s_v = (uint32_t*)(smem + RS_TILE * sizeof(KeyT));
-    __shared__ uint32_t s_start[256], s_run[256], s_goff[256];
-    __shared__ uint32_t s_wc[RS_WARPS][256];
-    __shared__ uint32_t s_scan[RS_WARPS + 1];
+    __shared__ uint32_t s_cnt[RS_WARPS][256];
+    __shared__ uint32_t s_start[256], s_goff[256];
+    __shared__ uint32_t s_wsum[RS_WARPS];
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    const int tile_n = (int)min((int64_t)RS_TILE, n - base);
+    const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+    const int tile_n = (int)min((int64_t)RS_TILE, n - tile0);
+    const int wbase = warp * (RS_TILE / RS_WARPS);
 
-    s_start[t] = 0;
-    s_run[t] = 0;
 #pragma unroll
-    for (int w = 0; w < RS_WARPS; ++w) s_wc[w][t] = 0xffffffffu;
-    __syncthreads();
+    for (int w = 0; w < RS_WARPS; ++w) s_cnt[w][t] = 0;
+    KeyT key[RS_ITEMS];
+    uint32_t val[RS_ITEMS], rank[RS_ITEMS];
+#pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
-        int i = r * RS_THREADS + t;
-        if (i < tile_n) atomicAdd(&s_start[(uint32_t)(kin[base + i] >> shift) & 255u], 1u);
+        const int i = wbase + 32 * r + lane;
+        key[r] = i < tile_n ? kin[tile0 + i] : (KeyT)0;
+        val[r] = i < tile_n ? vin[tile0 + i] : 0u;
     }
     __syncthreads();
-    {  // exclusive scan of the 256 tile counts
-        uint32_t v = s_start[t];
-        uint32_t incl = v;
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const bool valid = wbase + 32 * r + lane < tile_n;
+        const uint32_t dg = valid ? ((uint32_t)(key[r] >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t below = __popc(peers & lt);
+        const uint32_t before = valid ? s_cnt[warp][dg] : 0u;
+        __syncwarp();
+        if (valid && below == 0) s_cnt[warp][dg] = before + __popc(peers);
+        __syncwarp();
+        rank[r] = before + below;
+    }
+    __syncthreads();
+    {  // per digit t: exclusive prefix over warps, then over digits
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            const uint32_t c = s_cnt[w][t];
+            s_cnt[w][t] = run;
+            run += c;
+        }
+        uint32_t incl = run;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += u;
         }
-        if (lane == 31) s_scan[warp] = incl;
+        if (lane == 31) s_wsum[warp] = incl;
         __syncthreads();
-        if (t == 0) {
-            uint32_t acc = 0;
-            for (int w = 0; w < RS_WARPS; ++w) {
-                uint32_t c = s_scan[w];
-                s_scan[w] = acc;
-                acc += c;
-            }
-        }
-        __syncthreads();
-        uint32_t ex = s_scan[warp] + incl - v;
-        __syncthreads();
-        s_start[t] = ex;
-        s_goff[t] = offs[(int64_t)t * nb + blockIdx.x] - ex;
+        uint32_t wpre = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) wpre += w < warp ? s_wsum[w] : 0u;
+        const uint32_t start = wpre + incl - run;
+        s_start[t] = start;
+        s_goff[t] = offs[(int64_t)t * nb + blockIdx.x] - start;
     }
     __syncthreads();
-
-    // stable ranking, 256 items per round in input order
+#pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
-        const int i = r * RS_THREADS + t;
-        const bool valid = i < tile_n;
-        KeyT key = valid ? kin[base + i] : (KeyT)0;
-        uint32_t val = valid ? vin[base + i] : 0u;
-        const uint32_t dg = valid ? ((uint32_t)(key >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-        const uint32_t lower = peers & ((1u << lane) - 1u);
-        const uint32_t rank = __popc(lower);
-        const bool leader = lower == 0;
-        if (valid && leader) s_wc[warp][dg] = ((uint32_t)r << 16) | (uint32_t)__popc(peers);
-        __syncthreads();
-        if (valid) {
-            uint32_t pre = 0;
-            for (int w = 0; w < warp; ++w) {
-                uint32_t e = s_wc[w][dg];
-                if ((e >> 16) == (uint32_t)r) pre += e & 0xffffu;
-            }
-            uint32_t pos = s_start[dg] + s_run[dg] + pre + rank;
-            s_k[pos] = key;
-            s_v[pos] = val;
+        if (wbase + 32 * r + lane < tile_n) {
+            const uint32_t dg = (uint32_t)(key[r] >> shift) & 255u;
+            const uint32_t pos = s_start[dg] + s_cnt[warp][dg] + rank[r];
+            s_k[pos] = key[r];
+            s_v[pos] = val[r];
         }
-        __syncthreads();
-        if (valid && leader) atomicAdd(&s_run[dg], (uint32_t)__popc(peers));
-        __syncthreads();
     }
-    // write runs of equal digits to contiguous global ranges
+    __syncthreads();
     for (int j = t; j < tile_n; j += RS_THREADS) {
-        KeyT key = s_k[j];
-        uint32_t dg = (uint32_t)(key >> shift) & 255u;
-        uint32_t g = s_goff[dg] + (uint32_t)j;
-        kout[g] = key;
+        const KeyT k = s_k[j];
+        const uint32_t g = s_goff[(uint32_t)(k >> shift) & 255u] + (uint32_t)j;
+        kout[g] = k;
         vout[g] = s_v[j];
     }
 }
