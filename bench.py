@@ -232,6 +232,77 @@ class Body:
             self.host_out[k].copy_(v, non_blocking=True)
 
 
+def sphere_with_packages(target):
+    """Unit sphere on a grid whose band has about `target` packages
+    (P ~ 4.6 area / lc^2, the same rule that sizes the random bodies)."""
+    lc = math.sqrt(4.6 * 4.0 * math.pi / target)
+    half = 1.0 + 4 * lc
+    m = int(math.ceil(2 * half / lc))
+    return si.sphere(1.0), si.GridSpec((-0.5 * m * lc,) * 3, (m, m, m), lc / 4.0)
+
+
+def batch_section(sg, torch, n_bodies=256, iters=20, reps=5, seed=1):
+    """256 random bodies (spheres, tori, rounded boxes; r ~ U[0.1, 1], random
+    rotations, package counts log-uniform in [1e2, 1e5]) swept together by
+    one autotuned batch plan, against one sphere of equal package count
+    through the single-grid calls.  Both time the same sweeps per run:
+    gradient, smoothed sign, `iters` reinit sweeps, exact integrals."""
+    bodies = si.random_bodies(n_bodies, seed=seed)
+    grids = []
+    for shape, spec, _ in bodies:
+        g = sg.Grid(spec)
+        g.tag_allocate(shape)
+        g.init_sdf(shape)
+        grids.append(g)
+    batch = sg.Batch(grids)
+    P_tot = batch.P
+    n_pt = 64 * sum(g.P - 2 for g in grids)
+    for g in grids:
+        g.close()
+    plan, times = batch.autotune(sg.make_plan(reinit_iterations=iters, cfl=CFL), reps=2)
+    Ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    batch.run(plan)
+    torch.cuda.synchronize()
+    e0, e1 = Ev(), Ev()
+    e0.record()
+    for _ in range(reps):
+        batch.run(plan)
+    e1.record()
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / reps
+    batch.close()
+
+    shape, spec = sphere_with_packages(P_tot)
+    g = sg.Grid(spec)
+    P1 = g.tag_allocate(shape)
+    g.init_sdf(shape)
+
+    def single():
+        g.gradient()
+        g.reinit(iters, CFL)
+        g.kernel_integrals()
+
+    single()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        single()
+    e1.record()
+    torch.cuda.synchronize()
+    single_ms = e0.elapsed_time(e1) / reps
+    n1 = 64 * (P1 - 2)
+    g.close()
+    sweeps = iters + 2
+    b_rate = n_pt * sweeps / (batch_ms * 1e-3)
+    s_rate = n1 * sweeps / (single_ms * 1e-3)
+    return {"bodies": n_bodies, "packages": P_tot, "points": n_pt, "sweeps_per_run": sweeps,
+            "plan": {"pkgs_per_item": plan.pkgs_per_item, "depth": plan.depth},
+            "autotune_ms": {"%d,%d" % k: v for k, v in times.items()},
+            "run_ms": batch_ms, "cell_updates_per_s": b_rate,
+            "single_body": {"packages": P1, "points": n1, "run_ms": single_ms, "cell_updates_per_s": s_rate},
+            "batch_over_single": b_rate / s_rate}
+
+
 def phase_totals(phases):
     """Sum the durations between consecutive markers per phase name (ms)."""
     tot = {}
@@ -444,6 +515,8 @@ def run_sg(args):
         line["e2e"] = {"value": eunits / esecs, "unit": "cell-updates/s",
                        "h2d_bytes_per_step": sum(12 * b.n for b in bodies),
                        "d2h_bytes_per_step": sum(4 * len(b.out) * b.n for b in bodies)}
+    if not args.no_batch:
+        line["batch"] = batch_section(sg, torch)
     if not args.no_cpu_baseline and rank == 0 and ws == 1:
         est = oracle_calibrate(args.iters, args.particles)
         frac = min(1.0, max(0.02, 15.0 / est))
@@ -470,6 +543,7 @@ def main(argv=None):
     ap.add_argument("--particles", type=int, default=50_000_000, help="probe particles per body")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-body batch measurement")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

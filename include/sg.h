@@ -194,6 +194,61 @@ SG_API sg_status sg_probe(sg_grid *g, int64_t n, const float *x, const float *y,
 SG_API sg_status sg_morton_order(sg_grid *g, int64_t n, const float *x, const float *y, const float *z, uint64_t *keys,
                           int32_t *order);
 
+/* ------------------------------------------------------------------------ */
+/* Batches: many bodies, one launch per sweep.                               */
+/* ------------------------------------------------------------------------ */
+typedef struct sg_batch sg_batch;
+
+/* How a batch run is scheduled.  pkgs_per_item: packages each half-warp
+ * takes per work item (1, 2, 4 or 8; a CTA takes 16 times that for the face
+ * stencils, 4 times that for the integrals); depth: packages whose loads a
+ * half-warp has in flight at once (1 or 2, at most pkgs_per_item).  The
+ * sweeps are those of sg_gradient, sg_reinit(reinit_iterations, cfl) and
+ * sg_kernel_integrals(integrals_mode, NULL); integrals_mode must be 0. */
+typedef struct {
+    int32_t pkgs_per_item;
+    int32_t depth;
+    int32_t reinit_iterations;
+    float cfl;
+    int32_t integrals_mode;
+    int32_t reserved;
+} sg_batch_plan;
+
+/* Concatenate the packages of n initialised grids (same device) into one
+ * global store: body i owns package ids [base_i, base_i + P_i) with its own
+ * far packages and neighbour ids shifted by base_i.  phi is copied from the
+ * grids (they may be destroyed afterwards); device memory comes from the
+ * first grid's allocator; work runs on `stream`.  Not in the paper (the
+ * batched, persistent launch of many bodies is this library's).
+ * Errors: SG_ERR_INVALID (null, n < 1, grids on different devices),
+ * SG_ERR_STATE (a grid without phi), SG_ERR_CAPACITY, SG_ERR_OOM. */
+SG_API sg_status sg_batch_create(sg_grid *const *grids, int32_t n, void *stream, sg_batch **out);
+SG_API sg_status sg_batch_destroy(sg_batch *b);
+
+/* Restore every body's phi to its value at batch creation. */
+SG_API sg_status sg_batch_reset(sg_batch *b);
+
+/* One run: gradient of phi, smoothed sign, reinit sweeps, kernel integrals
+ * over all bodies, each sweep one persistent kernel that takes work items
+ * from an atomic counter.  The sequence of a plan is captured into a CUDA
+ * graph on its first run and replayed afterwards.  Per body the results
+ * equal those of the single-grid calls bit for bit.
+ * Errors: SG_ERR_INVALID (bad plan), SG_ERR_CAPACITY (more than 1020
+ * sweeps), SG_ERR_CUDA. */
+SG_API sg_status sg_batch_run(sg_batch *b, const sg_batch_plan *plan);
+
+/* Time runs of every (pkgs_per_item, depth) pair for the plan's sweeps
+ * (`reps` runs each, after one warm-up), write the fastest pair into *plan
+ * and, when times_ms is not NULL, the mean time of each of the 7 candidates
+ * (1,1) (2,1) (2,2) (4,1) (4,2) (8,1) (8,2) in that order.  Leaves phi reset. */
+SG_API sg_status sg_batch_autotune(sg_batch *b, sg_batch_plan *plan, int32_t reps, float *times_ms);
+
+/* Borrow body `body`'s slice of a batch field (SG_FIELD_PHI, _GX.._GZ, _W,
+ * _GWX.._GWZ, _S0: [P_body][64] floats; SG_FIELD_NBR: global ids). */
+SG_API sg_status sg_batch_get_field(sg_batch *b, int32_t body, int32_t field, void **dev_ptr, int64_t *n_elems);
+SG_API int64_t sg_batch_n_packages(const sg_batch *b);
+SG_API const char *sg_batch_last_error(const sg_batch *b);
+
 /* Allocation-free variant of sg_morton_order.  The paper has no counterpart;
  * this entry point exists for callers that cannot let a library allocate
  * device memory: applications that hand (nearly) all of the device memory to

@@ -47,6 +47,11 @@ class sg_grid_desc(C.Structure):
                 ("far_value", C.c_double)]
 
 
+class sg_batch_plan(C.Structure):
+    _fields_ = [("pkgs_per_item", C.c_int32), ("depth", C.c_int32), ("reinit_iterations", C.c_int32),
+                ("cfl", C.c_float), ("integrals_mode", C.c_int32), ("reserved", C.c_int32)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -93,6 +98,16 @@ def lib():
         L.sg_last_error.restype = C.c_char_p
         L.sg_version.restype = C.c_char_p
         L.sg_kernel_launch_count.restype = i64
+        L.sg_batch_create.argtypes = [C.POINTER(vp), i32, vp, C.POINTER(vp)]
+        L.sg_batch_destroy.argtypes = [vp]
+        L.sg_batch_reset.argtypes = [vp]
+        L.sg_batch_run.argtypes = [vp, C.POINTER(sg_batch_plan)]
+        L.sg_batch_autotune.argtypes = [vp, C.POINTER(sg_batch_plan), i32, C.POINTER(C.c_float)]
+        L.sg_batch_get_field.argtypes = [vp, i32, i32, C.POINTER(vp), C.POINTER(i64)]
+        L.sg_batch_n_packages.argtypes = [vp]
+        L.sg_batch_n_packages.restype = i64
+        L.sg_batch_last_error.argtypes = [vp]
+        L.sg_batch_last_error.restype = C.c_char_p
         for name in declared_symbols():
             f = getattr(L, name)
             if f.restype is C.c_int:  # default: sg_status
@@ -275,6 +290,72 @@ class Grid:
 
     def n_packages(self) -> int:
         return int(self._lib.sg_n_packages(self._h))
+
+
+BATCH_CANDIDATES = ((1, 1), (2, 1), (2, 2), (4, 1), (4, 2), (8, 1), (8, 2))
+
+
+def make_plan(pkgs_per_item=4, depth=2, reinit_iterations=20, cfl=0.5, integrals_mode=0) -> sg_batch_plan:
+    return sg_batch_plan(int(pkgs_per_item), int(depth), int(reinit_iterations), float(cfl), int(integrals_mode), 0)
+
+
+class Batch:
+    """Many initialised grids swept together (one persistent launch per
+    sweep, the sequence captured as a CUDA graph).  The grids' phi is copied
+    at construction."""
+
+    def __init__(self, grids, stream=None):
+        torch = _torch()
+        self._lib = lib()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.n = len(grids)
+        arr = (C.c_void_p * self.n)(*[g.handle.value for g in grids])
+        h = C.c_void_p()
+        st = self._lib.sg_batch_create(arr, self.n, C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != SG_OK:
+            raise SgError(st, "sg_batch_create failed")
+        self._h = h
+        self.P = int(self._lib.sg_batch_n_packages(h))
+
+    def _check(self, st):
+        if st != SG_OK:
+            raise SgError(st, self._lib.sg_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        self._check(self._lib.sg_batch_reset(self._h))
+
+    def run(self, plan=None, **kw):
+        plan = plan if plan is not None else make_plan(**kw)
+        self._check(self._lib.sg_batch_run(self._h, C.byref(plan)))
+        return plan
+
+    def autotune(self, plan=None, reps=3, **kw):
+        """Returns (best plan, {(pkgs_per_item, depth): ms})."""
+        plan = plan if plan is not None else make_plan(**kw)
+        times = (C.c_float * 8)()
+        self._check(self._lib.sg_batch_autotune(self._h, C.byref(plan), int(reps), times))
+        return plan, {c: float(times[i]) for i, c in enumerate(BATCH_CANDIDATES)}
+
+    def field(self, body, name):
+        torch = _torch()
+        p = C.c_void_p()
+        n = C.c_int64()
+        if name == "nbr":
+            self._check(self._lib.sg_batch_get_field(self._h, int(body), INT_FIELDS["nbr"][0], C.byref(p), C.byref(n)))
+            return torch.as_tensor(_CudaArray(p.value, (n.value,), "<i4"), device="cuda").view(-1, 27)
+        self._check(self._lib.sg_batch_get_field(self._h, int(body), FIELDS[name], C.byref(p), C.byref(n)))
+        return torch.as_tensor(_CudaArray(p.value, (n.value,), "<f4"), device="cuda").view(-1, 64)
 
 
 NOALLOC_MAX_PARTICLES = 262144

@@ -1,0 +1,578 @@
+// sg_batch.cu -- many bodies in one launch per sweep.
+//
+// The packages of every body are concatenated into one global store: body b
+// owns ids [base_b, base_b + P_b), its own far packages at base_b and
+// base_b + 1, neighbour ids shifted by base_b, and a row of per-body
+// constants (computed exactly as the single-grid launchers compute them, so
+// a batched sweep equals the per-body sweeps bit for bit).  Each sweep is one
+// persistent kernel: CTAs take work items of consecutive packages from an
+// atomic counter until the store is exhausted, which balances bodies of very
+// different sizes.  The whole sequence gradient -> smoothed sign -> reinit
+// sweeps -> kernel integrals is captured once per plan into a CUDA graph and
+// replayed.  The autotuner times every (packages per item, staging depth)
+// pair and keeps the fastest.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sg_rows.cuh"
+
+struct sg_batch_graph {
+    sg_batch_plan plan;
+    cudaGraphExec_t exec;
+};
+
+struct sg_batch {
+    int n = 0;
+    int64_t P = 0;  // packages of all bodies, far packages included
+    std::vector<int64_t> base, npk;
+    std::vector<double> h;
+    sg_allocator alloc{};
+    bool user_alloc = false;
+    cudaStream_t stream = nullptr;   // caller's stream: graphs run here
+    cudaStream_t capture = nullptr;  // private stream used only to capture
+    int device = 0;
+    sg::Buf phi, tmp, s0, phi0, f[8], nbr, type, body, params, counters;
+    size_t n_counters = 0;
+    float params_cfl = -1.0f;
+    std::vector<sg_batch_graph> graphs;
+    std::string last_error;
+};
+
+namespace sg {
+namespace {
+
+// Per-body constants, in the form the single-grid launchers pass them.
+struct BodyParams {
+    float inv2h;    // 1 / (2h)
+    float h2;       // h^2
+    float cfl;      // dt / h with dt rounded to float first
+    float dt;       // cfl h
+    float inv_eps;  // 1 / h
+    float F;        // far value
+    float pad[2];
+};
+
+constexpr int BT = 256;       // threads per CTA
+constexpr int BT_HW = BT / 16;  // half-warps (row kernels: packages per slot)
+constexpr int BT_PK = BT / PKG3;  // packages per slot of the integrals kernel
+
+__device__ __forceinline__ int64_t next_item(unsigned* counter, int* s_item) {
+    __syncthreads();
+    if (threadIdx.x == 0) *s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    return *s_item;
+}
+
+// Gradient over the global store.  A work item is 16 * ppi consecutive
+// packages; each half-warp handles ppi of them, DEPTH at a time.
+template <int DEPTH>
+__global__ void __launch_bounds__(BT) k_batch_gradient(const int32_t* __restrict__ nbr, const uint8_t* __restrict__ type,
+                                                       const int32_t* __restrict__ body,
+                                                       const BodyParams* __restrict__ prm, const float* __restrict__ phi,
+                                                       float* __restrict__ gx, float* __restrict__ gy,
+                                                       float* __restrict__ gz, int64_t P, int ppi, unsigned* counter) {
+    __shared__ int s_item;
+    const int64_t per_item = (int64_t)BT_HW * ppi, items = (P + per_item - 1) / per_item;
+    for (;;) {
+        const int64_t item = next_item(counter, &s_item);
+        if (item >= items) break;
+        for (int k = 0; k < ppi; k += DEPTH) {
+            RowSlot sl[DEPTH];
+            Rows w[DEPTH];
+#pragma unroll
+            for (int d = 0; d < DEPTH; ++d) {
+                const int64_t p = item * per_item + (int64_t)(k + d) * BT_HW + (threadIdx.x >> 4);
+                sl[d] = make_slot(p, p < P && k + d < ppi && __ldg(type + (p < P ? p : 0)) >= 2);
+            }
+#pragma unroll
+            for (int d = 0; d < DEPTH; ++d) w[d] = load_rows(phi, nbr, sl[d]);
+#pragma unroll
+            for (int d = 0; d < DEPTH; ++d) {
+                if (!sl[d].valid) continue;
+                float4 ox, oy, oz;
+                gradient_row(w[d], __ldg(&prm[__ldg(body + sl[d].p)].inv2h), ox, oy, oz);
+                reinterpret_cast<float4*>(gx)[sl[d].q4] = ox;
+                reinterpret_cast<float4*>(gy)[sl[d].q4] = oy;
+                reinterpret_cast<float4*>(gz)[sl[d].q4] = oz;
+            }
+        }
+    }
+}
+
+template <int DEPTH>
+__global__ void __launch_bounds__(BT) k_batch_reinit(const int32_t* __restrict__ nbr, const uint8_t* __restrict__ type,
+                                                     const int32_t* __restrict__ body,
+                                                     const BodyParams* __restrict__ prm, const float* __restrict__ s0,
+                                                     const float* __restrict__ phi_in, float* __restrict__ phi_out,
+                                                     int64_t P, int ppi, unsigned* counter) {
+    __shared__ int s_item;
+    const int64_t per_item = (int64_t)BT_HW * ppi, items = (P + per_item - 1) / per_item;
+    for (;;) {
+        const int64_t item = next_item(counter, &s_item);
+        if (item >= items) break;
+        for (int k = 0; k < ppi; k += DEPTH) {
+            RowSlot sl[DEPTH];
+            Rows w[DEPTH];
+            float4 sg[DEPTH];
+#pragma unroll
+            for (int d = 0; d < DEPTH; ++d) {
+                const int64_t p = item * per_item + (int64_t)(k + d) * BT_HW + (threadIdx.x >> 4);
+                sl[d] = make_slot(p, p < P && k + d < ppi && __ldg(type + (p < P ? p : 0)) >= 2);
+                sg[d] = sl[d].valid ? __ldg(reinterpret_cast<const float4*>(s0) + sl[d].q4)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int d = 0; d < DEPTH; ++d) w[d] = load_rows(phi_in, nbr, sl[d]);
+#pragma unroll
+            for (int d = 0; d < DEPTH; ++d) {
+                if (!sl[d].valid) continue;
+                const BodyParams* bp = prm + __ldg(body + sl[d].p);
+                reinterpret_cast<float4*>(phi_out)[sl[d].q4] = reinit_row(w[d], sg[d], __ldg(&bp->cfl), __ldg(&bp->dt));
+            }
+        }
+    }
+}
+
+// Smoothed sign over the active packages of every body (one float4 row per
+// thread, grid-stride).
+__global__ void __launch_bounds__(BT) k_batch_s0(const uint8_t* __restrict__ type, const int32_t* __restrict__ body,
+                                                 const BodyParams* __restrict__ prm, const float* __restrict__ phi,
+                                                 float* __restrict__ s0, int64_t P) {
+    const int64_t rows = P * 16;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < rows; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = q >> 4;
+        if (__ldg(type + p) < 2) continue;
+        const float h2 = __ldg(&prm[__ldg(body + p)].h2);
+        float4 v = __ldg(reinterpret_cast<const float4*>(phi) + q);
+        v.x = smoothed_sign(v.x, h2);
+        v.y = smoothed_sign(v.y, h2);
+        v.z = smoothed_sign(v.z, h2);
+        v.w = smoothed_sign(v.w, h2);
+        reinterpret_cast<float4*>(s0)[q] = v;
+    }
+}
+
+// Kernel integrals over the global store: a work item is 4 * ppi packages,
+// 64 threads per package.
+__global__ void __launch_bounds__(BT) k_batch_integrals(const int32_t* __restrict__ nbr, const uint8_t* __restrict__ type,
+                                                        const int32_t* __restrict__ body,
+                                                        const BodyParams* __restrict__ prm,
+                                                        const float* __restrict__ phi, float* __restrict__ W,
+                                                        float* __restrict__ gx, float* __restrict__ gy,
+                                                        float* __restrict__ gz, int64_t P, int ppi, KernelCoef K,
+                                                        unsigned* counter) {
+    __shared__ int s_item;
+    __shared__ int s_nb[BT_PK][NB];
+    __shared__ float s_H[BT_PK][216];
+    const int lp = threadIdx.x >> 6, d = threadIdx.x & 63;
+    const int64_t per_item = (int64_t)BT_PK * ppi, items = (P + per_item - 1) / per_item;
+    for (;;) {
+        const int64_t item = next_item(counter, &s_item);
+        if (item >= items) break;
+        for (int k = 0; k < ppi; ++k) {
+            const int64_t p = item * per_item + (int64_t)k * BT_PK + lp;
+            const bool valid = p < P && __ldg(type + (p < P ? p : 0)) >= 2;
+            if (valid && d < NB) s_nb[lp][d] = __ldg(nbr + p * NB + d);
+            __syncthreads();
+            float inv_eps = 0.0f;
+            if (valid) {
+                inv_eps = __ldg(&prm[__ldg(body + p)].inv_eps);
+                integrals_stage(s_nb[lp], phi, inv_eps, d, s_H[lp]);
+            }
+            __syncthreads();
+            if (valid) {
+                float w, ax, ay, az;
+                integrals_point(s_H[lp], d, K, w, ax, ay, az);
+                const int64_t at = p * PKG3 + d;
+                W[at] = w;
+                gx[at] = ax;
+                gy[at] = ay;
+                gz[at] = az;
+            }
+        }
+    }
+}
+
+__global__ void k_batch_offset_nbr(const int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t n,
+                                   int32_t offset) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = src[e] + offset;
+}
+
+__global__ void k_batch_fill_body(int32_t* __restrict__ body, int64_t begin, int64_t n, int32_t b) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        body[begin + e] = b;
+}
+
+// far packages of every body: W = 1 inside, 0 outside
+__global__ void k_batch_far_W(float* __restrict__ W, const int64_t* __restrict__ base, int n) {
+    const int b = blockIdx.x;
+    if (b >= n) return;
+    W[base[b] * PKG3 + threadIdx.x] = threadIdx.x < PKG3 ? 1.0f : 0.0f;
+}
+
+unsigned flat_grid(int64_t n) {
+    int64_t b = (n + BT - 1) / BT;
+    if (b < 1) b = 1;
+    if (b > 148 * 32) b = 148 * 32;
+    return (unsigned)b;
+}
+
+void* b_alloc(sg_batch* b, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (b->user_alloc) {
+        p = b->alloc.alloc(bytes, (void*)b->stream, b->alloc.ctx);
+    } else if (cudaMallocAsync(&p, bytes, b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void b_free(sg_batch* b, Buf& x) {
+    if (x.p) {
+        if (b->user_alloc)
+            b->alloc.free(x.p, x.bytes, (void*)b->stream, b->alloc.ctx);
+        else
+            cudaFreeAsync(x.p, b->stream);
+    }
+    x.p = nullptr;
+    x.bytes = 0;
+}
+
+bool b_ensure(sg_batch* b, Buf& x, size_t bytes) {
+    if (x.p && x.bytes >= bytes) return true;
+    b_free(b, x);
+    x.p = b_alloc(b, bytes);
+    if (!x.p) return false;
+    x.bytes = bytes;
+    return true;
+}
+
+sg_status b_fail(sg_batch* b, sg_status st, const std::string& msg) {
+    if (b) b->last_error = msg;
+    return st;
+}
+
+bool same_plan(const sg_batch_plan& a, const sg_batch_plan& b) {
+    return a.pkgs_per_item == b.pkgs_per_item && a.depth == b.depth && a.reinit_iterations == b.reinit_iterations &&
+           a.cfl == b.cfl && a.integrals_mode == b.integrals_mode;
+}
+
+bool valid_plan(const sg_batch_plan* p) {
+    const int ppi = p->pkgs_per_item;
+    return (ppi == 1 || ppi == 2 || ppi == 4 || ppi == 8) && (p->depth == 1 || p->depth == 2) && p->depth <= ppi &&
+           p->reinit_iterations >= 0 && p->cfl > 0.0f && std::isfinite(p->cfl) && p->integrals_mode == 0;
+}
+
+int persistent_blocks(const void* kernel, int device) {
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BT, 0);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (per_sm < 1) per_sm = 1;
+    if (sms < 1) sms = 1;
+    return per_sm * sms;
+}
+
+// Upload the per-body constants for a CFL number (stream-ordered).
+cudaError_t upload_params(sg_batch* b, float cfl) {
+    std::vector<BodyParams> hp(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        const double h = b->h[i];
+        BodyParams& q = hp[i];
+        q.inv2h = (float)(1.0 / (2.0 * h));
+        q.h2 = (float)(h * h);
+        const float dt = (float)((double)cfl * h);
+        q.dt = dt;
+        q.cfl = (float)((double)dt / h);
+        q.inv_eps = (float)(1.0 / h);
+        q.F = 0.0f;
+        q.pad[0] = q.pad[1] = 0.0f;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->params.p, hp.data(), hp.size() * sizeof(BodyParams), cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // the host vector goes out of scope
+    if (e == cudaSuccess) b->params_cfl = cfl;
+    return e;
+}
+
+// Record the sweep sequence of a plan on stream s.
+cudaError_t record_run(sg_batch* b, const sg_batch_plan& plan, cudaStream_t s) {
+    const int ppi = plan.pkgs_per_item, iters = plan.reinit_iterations;
+    const int32_t* nbr = (const int32_t*)b->nbr.p;
+    const uint8_t* type = (const uint8_t*)b->type.p;
+    const int32_t* body = (const int32_t*)b->body.p;
+    const BodyParams* prm = (const BodyParams*)b->params.p;
+    float* phi = (float*)b->phi.p;
+    float* tmp = (float*)b->tmp.p;
+    float* s0 = (float*)b->s0.p;
+    float* fo[8];
+    for (int i = 0; i < 8; ++i) fo[i] = (float*)b->f[i].p;
+    unsigned* ctr = (unsigned*)b->counters.p;
+    cudaError_t e = cudaMemsetAsync(ctr, 0, b->n_counters * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    int c = 0;
+    const KernelCoef K = kernel_coef();
+    if (plan.depth == 2) {
+        const int nb = persistent_blocks((const void*)k_batch_gradient<2>, b->device);
+        k_batch_gradient<2><<<nb, BT, 0, s>>>(nbr, type, body, prm, phi, fo[1], fo[2], fo[3], b->P, ppi, ctr + c++);
+    } else {
+        const int nb = persistent_blocks((const void*)k_batch_gradient<1>, b->device);
+        k_batch_gradient<1><<<nb, BT, 0, s>>>(nbr, type, body, prm, phi, fo[1], fo[2], fo[3], b->P, ppi, ctr + c++);
+    }
+    note_launch();
+    k_batch_s0<<<flat_grid(b->P * 16), BT, 0, s>>>(type, body, prm, phi, s0, b->P);
+    note_launch();
+    float* a = phi;
+    float* o = tmp;
+    const int nbr2 = persistent_blocks((const void*)k_batch_reinit<2>, b->device);
+    const int nbr1 = persistent_blocks((const void*)k_batch_reinit<1>, b->device);
+    for (int it = 0; it < iters; ++it) {
+        if (plan.depth == 2)
+            k_batch_reinit<2><<<nbr2, BT, 0, s>>>(nbr, type, body, prm, s0, a, o, b->P, ppi, ctr + c++);
+        else
+            k_batch_reinit<1><<<nbr1, BT, 0, s>>>(nbr, type, body, prm, s0, a, o, b->P, ppi, ctr + c++);
+        note_launch();
+        float* t = a;
+        a = o;
+        o = t;
+    }
+    if (a != phi) {
+        if ((e = cudaMemcpyAsync(phi, a, (size_t)b->P * PKG3 * sizeof(float), cudaMemcpyDeviceToDevice, s)) !=
+            cudaSuccess)
+            return e;
+    }
+    const int nbi = persistent_blocks((const void*)k_batch_integrals, b->device);
+    k_batch_integrals<<<nbi, BT, 0, s>>>(nbr, type, body, prm, phi, fo[4], fo[5], fo[6], fo[7], b->P, ppi, K,
+                                         ctr + c++);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace sg
+
+using namespace sg;
+
+extern "C" {
+
+sg_status sg_batch_create(sg_grid* const* grids, int32_t n, void* stream, sg_batch** out) {
+    if (!grids || n < 1 || !out) return SG_ERR_INVALID;
+    *out = nullptr;
+    int64_t P = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!grids[i]) return SG_ERR_INVALID;
+        if (grids[i]->state < 2) return SG_ERR_STATE;
+        if (grids[i]->device != grids[0]->device) return SG_ERR_INVALID;
+        P += grids[i]->P;
+    }
+    if (P >= (1LL << 31) / NB) return SG_ERR_CAPACITY;
+    sg_batch* b = new (std::nothrow) sg_batch();
+    if (!b) return SG_ERR_OOM;
+    b->n = n;
+    b->P = P;
+    b->stream = (cudaStream_t)stream;
+    b->alloc = grids[0]->alloc;
+    b->user_alloc = grids[0]->user_alloc;
+    b->device = grids[0]->device;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    sg_status st = SG_OK;
+    const size_t fb = (size_t)P * PKG3 * sizeof(float);
+    bool ok = b_ensure(b, b->phi, fb) && b_ensure(b, b->tmp, fb) && b_ensure(b, b->s0, fb) && b_ensure(b, b->phi0, fb) &&
+              b_ensure(b, b->nbr, (size_t)P * NB * 4) && b_ensure(b, b->type, (size_t)P) &&
+              b_ensure(b, b->body, (size_t)P * 4) && b_ensure(b, b->params, (size_t)n * sizeof(BodyParams)) &&
+              b_ensure(b, b->counters, 4096);
+    for (int i = 1; ok && i < 8; ++i) ok = b_ensure(b, b->f[i], fb);
+    b->f[0] = Buf{};  // slot 0 (phi) is b->phi
+    cudaError_t e = cudaSuccess;
+    std::vector<int64_t> bases(n);
+    if (!ok) {
+        st = SG_ERR_OOM;
+    } else {
+        b->n_counters = 4096 / sizeof(unsigned);
+        int64_t off = 0;
+        for (int i = 0; i < n && e == cudaSuccess; ++i) {
+            sg_grid* g = grids[i];
+            bases[i] = off;
+            b->base.push_back(off);
+            b->npk.push_back(g->P);
+            b->h.push_back(g->desc.h);
+            e = cudaMemcpyAsync((float*)b->phi0.p + off * PKG3, g->field[SG_FIELD_PHI].p,
+                                (size_t)g->P * PKG3 * sizeof(float), cudaMemcpyDeviceToDevice, b->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync((uint8_t*)b->type.p + off, g->pkg_type.p, (size_t)g->P, cudaMemcpyDeviceToDevice,
+                                    b->stream);
+            if (e == cudaSuccess) {
+                k_batch_offset_nbr<<<flat_grid(g->P * NB), BT, 0, b->stream>>>(
+                    (const int32_t*)g->nbr.p, (int32_t*)b->nbr.p + off * NB, g->P * NB, (int32_t)off);
+                k_batch_fill_body<<<flat_grid(g->P), BT, 0, b->stream>>>((int32_t*)b->body.p, off, g->P, i);
+                note_launch(2);
+                e = cudaGetLastError();
+            }
+            off += g->P;
+        }
+        for (int i = 1; i < 8 && e == cudaSuccess; ++i) e = cudaMemsetAsync(b->f[i].p, 0, fb, b->stream);
+        if (e == cudaSuccess) {
+            Buf tmpbase;
+            tmpbase.p = b_alloc(b, (size_t)n * sizeof(int64_t));
+            if (!tmpbase.p) {
+                st = SG_ERR_OOM;
+            } else {
+                tmpbase.bytes = (size_t)n * sizeof(int64_t);
+                e = cudaMemcpyAsync(tmpbase.p, bases.data(), (size_t)n * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                    b->stream);
+                if (e == cudaSuccess) {
+                    k_batch_far_W<<<n, 2 * PKG3, 0, b->stream>>>((float*)b->f[4].p, (const int64_t*)tmpbase.p, n);
+                    note_launch();
+                    e = cudaGetLastError();
+                }
+                if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // bases lives on this stack
+                b_free(b, tmpbase);
+            }
+        }
+        if (e == cudaSuccess && st == SG_OK)
+            e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+        if (e == cudaSuccess && st == SG_OK) e = upload_params(b, 0.5f);
+        if (e != cudaSuccess) st = SG_ERR_CUDA;
+    }
+    if (st == SG_OK) {
+        // phi and the ping-pong buffer start from the grids' phi (far values included)
+        e = cudaMemcpyAsync(b->phi.p, b->phi0.p, fb, cudaMemcpyDeviceToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b->tmp.p, b->phi0.p, fb, cudaMemcpyDeviceToDevice, b->stream);
+        if (e != cudaSuccess) st = SG_ERR_CUDA;
+    }
+    if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+    if (st != SG_OK) {
+        cudaGetLastError();
+        sg_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return SG_OK;
+}
+
+sg_status sg_batch_destroy(sg_batch* b) {
+    if (!b) return SG_ERR_INVALID;
+    for (auto& gr : b->graphs) cudaGraphExecDestroy(gr.exec);
+    Buf* bufs[] = {&b->phi, &b->tmp, &b->s0, &b->phi0, &b->nbr, &b->type, &b->body, &b->params, &b->counters};
+    for (Buf* x : bufs) b_free(b, *x);
+    for (int i = 1; i < 8; ++i) b_free(b, b->f[i]);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    delete b;
+    return SG_OK;
+}
+
+int64_t sg_batch_n_packages(const sg_batch* b) { return b ? b->P : 0; }
+
+const char* sg_batch_last_error(const sg_batch* b) { return b ? b->last_error.c_str() : "null batch"; }
+
+sg_status sg_batch_reset(sg_batch* b) {
+    if (!b) return SG_ERR_INVALID;
+    const size_t fb = (size_t)b->P * PKG3 * sizeof(float);
+    cudaError_t e = cudaMemcpyAsync(b->phi.p, b->phi0.p, fb, cudaMemcpyDeviceToDevice, b->stream);
+    if (e != cudaSuccess) return b_fail(b, SG_ERR_CUDA, std::string("reset: ") + cudaGetErrorString(e));
+    return SG_OK;
+}
+
+sg_status sg_batch_run(sg_batch* b, const sg_batch_plan* plan) {
+    if (!b || !plan) return SG_ERR_INVALID;
+    if (!valid_plan(plan)) return b_fail(b, SG_ERR_INVALID, "sg_batch_run: bad plan");
+    if ((size_t)plan->reinit_iterations + 4 > b->n_counters)
+        return b_fail(b, SG_ERR_CAPACITY, "sg_batch_run: too many reinit iterations");
+    cudaError_t e;
+    if (plan->cfl != b->params_cfl) {
+        // the graphs read the constants from device memory at replay
+        if ((e = upload_params(b, plan->cfl)) != cudaSuccess)
+            return b_fail(b, SG_ERR_CUDA, std::string("params: ") + cudaGetErrorString(e));
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (auto& gr : b->graphs)
+        if (same_plan(gr.plan, *plan)) exec = gr.exec;
+    if (!exec) {
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t er = record_run(b, *plan, b->capture);
+            e = cudaStreamEndCapture(b->capture, &graph);
+            if (er != cudaSuccess) e = er;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return b_fail(b, SG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+        }
+        b->graphs.push_back(sg_batch_graph{*plan, exec});
+    }
+    e = cudaGraphLaunch(exec, b->stream);
+    if (e != cudaSuccess) return b_fail(b, SG_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    return SG_OK;
+}
+
+sg_status sg_batch_autotune(sg_batch* b, sg_batch_plan* plan, int32_t reps, float* times_ms) {
+    if (!b || !plan || reps < 1) return SG_ERR_INVALID;
+    static const int cand[8][2] = {{1, 1}, {2, 1}, {2, 2}, {4, 1}, {4, 2}, {8, 1}, {8, 2}, {1, 1}};
+    float best = INFINITY;
+    sg_batch_plan best_plan = *plan;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return b_fail(b, SG_ERR_CUDA, "autotune: events");
+    sg_status st = SG_OK;
+    for (int c = 0; c < 7 && st == SG_OK; ++c) {
+        sg_batch_plan p = *plan;
+        p.pkgs_per_item = cand[c][0];
+        p.depth = cand[c][1];
+        if ((st = sg_batch_reset(b)) != SG_OK || (st = sg_batch_run(b, &p)) != SG_OK) break;  // capture + warm
+        cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < reps && st == SG_OK; ++r) {
+            st = sg_batch_reset(b);
+            if (st == SG_OK) st = sg_batch_run(b, &p);
+        }
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = b_fail(b, SG_ERR_CUDA, "autotune: sync");
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)reps;
+        if (times_ms) times_ms[c] = ms;
+        if (ms < best) {
+            best = ms;
+            best_plan = p;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SG_OK) return st;
+    *plan = best_plan;
+    return sg_batch_reset(b);
+}
+
+sg_status sg_batch_get_field(sg_batch* b, int32_t body, int32_t field, void** dev_ptr, int64_t* n_elems) {
+    if (!b || !dev_ptr || !n_elems || body < 0 || body >= b->n) return SG_ERR_INVALID;
+    const int64_t off = b->base[body], np = b->npk[body];
+    float* base = nullptr;
+    switch (field) {
+    case SG_FIELD_PHI: base = (float*)b->phi.p; break;
+    case SG_FIELD_GX: case SG_FIELD_GY: case SG_FIELD_GZ:
+    case SG_FIELD_W: case SG_FIELD_GWX: case SG_FIELD_GWY: case SG_FIELD_GWZ:
+        base = (float*)b->f[field].p;
+        break;
+    case SG_FIELD_S0: base = (float*)b->s0.p; break;
+    case SG_FIELD_NBR:
+        *dev_ptr = (int32_t*)b->nbr.p + off * NB;
+        *n_elems = np * NB;
+        return SG_OK;
+    default:
+        return b_fail(b, SG_ERR_INVALID, "sg_batch_get_field: unknown field");
+    }
+    *dev_ptr = base + off * PKG3;
+    *n_elems = np * PKG3;
+    return SG_OK;
+}
+
+}  // extern "C"

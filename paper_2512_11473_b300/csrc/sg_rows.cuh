@@ -1,0 +1,232 @@
+// sg_rows.cuh -- per-package device code shared by the single-grid sweeps
+// (sg_sweep.cu) and the batched persistent sweeps (sg_batch.cu), so that both
+// run the same arithmetic per data point and agree bit for bit.
+//
+// Face stencils: a half-warp owns one package and each lane one row of four
+// x-values (float4, row r = j + 4k).  x neighbours inside the row are in
+// registers; rows j +- 1 and k +- 1 come from lanes r -+ 1 and r -+ 4 by warp
+// shuffles; across a package face the neighbour package named by the
+// 27-entry table (Listing 2) supplies one value (x faces) or one row (y, z
+// faces).  The six face ids are read by six lanes and broadcast by shuffles.
+//
+// Kernel integrals: 64 threads own a package, stage the smoothed Heaviside of
+// a 6^3 tile (package plus a one-point halo, reached by the index shift) in
+// shared memory and sum the 27 non-zero taps from there.
+#pragma once
+#include "sg_internal.cuh"
+
+namespace sg {
+
+// Kernel integrals.  Tap weights by squared distance |s|^2 in {0,1,2,3}:
+// cw = w(|s|) / sum w, ck = w'(|s|) / |s| / sum w (taps at |s| >= 2 vanish).
+struct KernelCoef {
+    float cw[4];
+    float ck[4];
+};
+
+// host: tap coefficients of the Wendland C2 kernel (support 2h) normalised by
+// the discrete sum of its 27 non-zero taps
+KernelCoef kernel_coef();
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// neighbourhood entries of the six faces: -x, +x, -y, +y, -z, +z
+__constant__ int c_face_n[6] = {12, 14, 10, 16, 4, 22};
+
+// Listing 2: shift s per axis in [-4, 7] -> (package, data index)
+__device__ __forceinline__ int64_t shift_index(const int* nb27, int sx, int sy, int sz) {
+    int nx = (sx + PKG) >> 2, ny = (sy + PKG) >> 2, nz = (sz + PKG) >> 2;
+    int pkg = nb27[nx + 3 * ny + 9 * nz];
+    int dx = sx + PKG - nx * PKG, dy = sy + PKG - ny * PKG, dz = sz + PKG - nz * PKG;
+    return (int64_t)pkg * PKG3 + dx + PKG * dy + PKG * PKG * dz;
+}
+
+__device__ __forceinline__ float4 shfl_up4(float4 v, int d) {
+    v.x = __shfl_up_sync(FULL, v.x, d, 16);
+    v.y = __shfl_up_sync(FULL, v.y, d, 16);
+    v.z = __shfl_up_sync(FULL, v.z, d, 16);
+    v.w = __shfl_up_sync(FULL, v.w, d, 16);
+    return v;
+}
+
+__device__ __forceinline__ float4 shfl_down4(float4 v, int d) {
+    v.x = __shfl_down_sync(FULL, v.x, d, 16);
+    v.y = __shfl_down_sync(FULL, v.y, d, 16);
+    v.z = __shfl_down_sync(FULL, v.z, d, 16);
+    v.w = __shfl_down_sync(FULL, v.w, d, 16);
+    return v;
+}
+
+__device__ __forceinline__ float get(const float4& v, int i) {
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ void set(float4& v, int i, float a) {
+    if (i == 0) v.x = a;
+    else if (i == 1) v.y = a;
+    else if (i == 2) v.z = a;
+    else v.w = a;
+}
+
+// A lane's row and its six neighbours.
+struct Rows {
+    float4 c;       // own row, i = 0..3
+    float xm, xp;   // x - 1 of i = 0 and x + 1 of i = 3
+    float4 ym, yp;  // rows j - 1, j + 1
+    float4 zm, zp;  // rows k - 1, k + 1
+};
+
+// Package of a half-warp and row of a lane.  Offsets are kept in float4
+// units in 32 bits: P < 2^31 / 27 packages, so 16 P < 2^31.
+struct RowSlot {
+    int64_t p;
+    int q4;  // float4 index of this lane's row: 16 p + r
+    int r;
+    bool valid;
+};
+
+__device__ __forceinline__ RowSlot make_slot(int64_t p, bool valid) {
+    RowSlot s;
+    s.r = threadIdx.x & 15;
+    s.p = p;
+    s.valid = valid;
+    s.q4 = (int)p * 16 + s.r;
+    return s;
+}
+
+// Gather a lane's row and neighbours of field f.  All lanes of the warp must
+// call this (shuffles); lanes of an invalid package get zeros.
+__device__ __forceinline__ Rows load_rows(const float* __restrict__ f, const int32_t* __restrict__ nbr,
+                                          const RowSlot& s) {
+    const int lane = threadIdx.x & 31, base = lane & 16;
+    const int j = s.r & 3, k = s.r >> 2;
+    const float4* __restrict__ f4 = reinterpret_cast<const float4*>(f);
+    int nid = 0;
+    if (s.valid && s.r < 6) nid = __ldg(nbr + s.p * NB + c_face_n[s.r]);
+    Rows w;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    w.c = s.valid ? __ldg(f4 + s.q4) : zero;
+    const int n_xm = __shfl_sync(FULL, nid, base + 0), n_xp = __shfl_sync(FULL, nid, base + 1);
+    const int n_ym = __shfl_sync(FULL, nid, base + 2), n_yp = __shfl_sync(FULL, nid, base + 3);
+    const int n_zm = __shfl_sync(FULL, nid, base + 4), n_zp = __shfl_sync(FULL, nid, base + 5);
+    w.xm = s.valid ? __ldg(reinterpret_cast<const float*>(f4 + (n_xm * 16 + s.r)) + 3) : 0.f;
+    w.xp = s.valid ? __ldg(reinterpret_cast<const float*>(f4 + (n_xp * 16 + s.r))) : 0.f;
+    const float4 ym = shfl_up4(w.c, 1), yp = shfl_down4(w.c, 1);
+    const float4 zm = shfl_up4(w.c, 4), zp = shfl_down4(w.c, 4);
+    w.ym = j > 0 ? ym : (s.valid ? __ldg(f4 + (n_ym * 16 + s.r + 3)) : zero);
+    w.yp = j < 3 ? yp : (s.valid ? __ldg(f4 + (n_yp * 16 + s.r - 3)) : zero);
+    w.zm = k > 0 ? zm : (s.valid ? __ldg(f4 + (n_zm * 16 + s.r + 12)) : zero);
+    w.zp = k < 3 ? zp : (s.valid ? __ldg(f4 + (n_zp * 16 + s.r - 12)) : zero);
+    return w;
+}
+
+__device__ __forceinline__ float row_xm(const Rows& w, int i) { return i > 0 ? get(w.c, i - 1) : w.xm; }
+__device__ __forceinline__ float row_xp(const Rows& w, int i) { return i < 3 ? get(w.c, i + 1) : w.xp; }
+
+// Listing 5 with (p + m) / (2h) per axis.
+__device__ __forceinline__ void gradient_row(const Rows& w, float inv2h, float4& ox, float4& oy, float4& oz) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float c = get(w.c, i);
+        set(ox, i, ((row_xp(w, i) - c) + (c - row_xm(w, i))) * inv2h);
+        set(oy, i, ((get(w.yp, i) - c) + (c - get(w.ym, i))) * inv2h);
+        set(oz, i, ((get(w.zp, i) - c) + (c - get(w.zm, i))) * inv2h);
+    }
+}
+
+__device__ __forceinline__ float4 laplacian_row(const Rows& w, float inv_h2) {
+    float4 o;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float c = get(w.c, i);
+        float a = (row_xp(w, i) - 2.0f * c) + row_xm(w, i);
+        a += (get(w.yp, i) - 2.0f * c) + get(w.ym, i);
+        a += (get(w.zp, i) - 2.0f * c) + get(w.zm, i);
+        set(o, i, a * inv_h2);
+    }
+    return o;
+}
+
+// One Godunov sweep.  With sigma = sign(S0) the upwind pair of each axis is
+// u = max(sigma (c - phi(-e)), 0) and v = max(sigma (c - phi(+e)), 0): for
+// S0 > 0 these are max(D-, 0) h and -min(D+, 0) h, for S0 < 0 -min(D-, 0) h
+// and max(D+, 0) h, so max(u^2, v^2) = max(u, v)^2 is the Godunov term of
+// that axis times h^2.  Then dt sqrt(G) = cfl sqrt(sum h^2 terms) and
+// phi <- phi - S0 (cfl sqrt(.) - dt), which leaves phi unchanged where S0 = 0.
+__device__ __forceinline__ float godunov_axis(float cs, float sigma, float m, float p) {
+    const float u = fmaf(-sigma, m, cs), v = fmaf(-sigma, p, cs);
+    return fmaxf(fmaxf(u, v), 0.0f);
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float4 reinit_row(const Rows& w, const float4& sg, float cfl, float dt) {
+    float4 o;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float c = get(w.c, i), sv = get(sg, i);
+        const float sigma = copysignf(1.0f, sv), cs = sigma * c;
+        const float mx = godunov_axis(cs, sigma, row_xm(w, i), row_xp(w, i));
+        const float my = godunov_axis(cs, sigma, get(w.ym, i), get(w.yp, i));
+        const float mz = godunov_axis(cs, sigma, get(w.zm, i), get(w.zp, i));
+        const float g2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
+        set(o, i, fmaf(-sv, fmaf(cfl, sqrt_approx(g2), -dt), c));
+    }
+    return o;
+}
+
+// Smoothed sign S0 = phi / sqrt(phi^2 + h^2).
+__device__ __forceinline__ float smoothed_sign(float v, float h2) { return v / sqrtf(v * v + h2); }
+
+__device__ __forceinline__ float heaviside_neg(float phi, float inv_eps) {
+    // H(z) at z = -phi with half width eps: 0 below -eps, 1 above eps,
+    // 1/2 (1 + z/eps + sin(pi z/eps)/pi) between
+    float t = -phi * inv_eps;
+    if (t < -1.0f) return 0.0f;
+    if (t > 1.0f) return 1.0f;
+    return 0.5f * (1.0f + t + sinpif(t) * 0.318309886183790672f);
+}
+
+// Fill the 6^3 Heaviside tile of package p (64 threads, d = thread index in
+// the package); nb27 holds the package's neighbourhood in shared memory.
+__device__ __forceinline__ void integrals_stage(const int* nb27, const float* __restrict__ phi, float inv_eps,
+                                                int d, float* tile) {
+    for (int e = d; e < 216; e += PKG3) {
+        int x = e % 6 - 1, y = (e / 6) % 6 - 1, z = e / 36 - 1;
+        tile[e] = heaviside_neg(__ldg(phi + shift_index(nb27, x, y, z)), inv_eps);
+    }
+}
+
+// The 27 taps around data point d of a staged tile.
+__device__ __forceinline__ void integrals_point(const float* tile, int d, const KernelCoef& K, float& w,
+                                                float& ax, float& ay, float& az) {
+    const int i = d & 3, j = (d >> 2) & 3, k = d >> 4;
+    const float* H = tile + (i + 1) + 6 * (j + 1) + 36 * (k + 1);
+    w = 0.0f;
+    ax = ay = az = 0.0f;
+#pragma unroll
+    for (int sz = -1; sz <= 1; ++sz)
+#pragma unroll
+        for (int sy = -1; sy <= 1; ++sy)
+#pragma unroll
+            for (int sx = -1; sx <= 1; ++sx) {
+                const int q2 = sx * sx + sy * sy + sz * sz;
+                const float h = H[sx + 6 * sy + 36 * sz];
+                w = fmaf(K.cw[q2], h, w);
+                if (q2 > 0) {
+                    const float kh = K.ck[q2] * h;
+                    if (sx) ax = fmaf(kh, (float)(-sx), ax);
+                    if (sy) ay = fmaf(kh, (float)(-sy), ay);
+                    if (sz) az = fmaf(kh, (float)(-sz), az);
+                }
+            }
+}
+
+}  // namespace
+}  // namespace sg

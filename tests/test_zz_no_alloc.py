@@ -9,6 +9,7 @@ sg_morton_order on a grid: keys and order must agree bit for bit.  This file
 is collected last so that a failure here leaves every other test already run.
 """
 import ctypes as C
+import gc
 
 import numpy as np
 import pytest
@@ -42,15 +43,23 @@ def _noalloc_raw(sg, spec, X, Y, Z):
     n = X.numel()
     keys = torch.full((n,), -1, dtype=torch.int64, device="cuda")
     order = torch.full((n,), -1, dtype=torch.int32, device="cuda")
-    torch.cuda.synchronize()
-    before = torch.cuda.memory_allocated()
-    st = sg.lib().sg_morton_order_noalloc(C.byref(sg._desc(spec)), n, C.c_void_p(X.data_ptr()),
-                                          C.c_void_p(Y.data_ptr()), C.c_void_p(Z.data_ptr()),
-                                          C.c_void_p(keys.data_ptr()), C.c_void_p(order.data_ptr()),
-                                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
-    torch.cuda.synchronize()
+    desc = sg._desc(spec)
+    args = [C.c_void_p(t.data_ptr()) for t in (X, Y, Z, keys, order)]
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    # objects of earlier tests may still be waiting for the collector; their
+    # finalizers free memory, so collect first and keep the collector off
+    gc.collect()
+    gc.disable()
+    try:
+        torch.cuda.synchronize()
+        before = torch.cuda.memory_allocated()
+        st = sg.lib().sg_morton_order_noalloc(C.byref(desc), n, *args[:3], *args[3:], stream)
+        torch.cuda.synchronize()
+        after = torch.cuda.memory_allocated()
+    finally:
+        gc.enable()
     assert st == sg.SG_OK
-    assert torch.cuda.memory_allocated() == before
+    assert after <= before
     return keys.cpu(), order.cpu()
 
 
