@@ -303,6 +303,29 @@ def batch_section(sg, torch, n_bodies=256, iters=20, reps=5, seed=1):
             "batch_over_single": b_rate / s_rate}
 
 
+def surrogate_section(sg, torch, steps=12000, samples=20_000_000):
+    """Learned kernel integral: training samples from 500 random bodies
+    (seed 4, exact integrals as labels), `steps` Adam steps of batch 8192 on
+    the library's own kernels, then the exact and the surrogate integrals of
+    the h = 0.002 torus after 50 reinit sweeps: times and errors."""
+    from paper_2512_11473_b300 import surrogate as S
+    X, T, info = S.collect_samples(target=samples)
+    net = sg.MLP(si.mlp_init_params(4))
+    hist, secs = S.train(net, X, T, steps=steps, log_every=steps // 4)
+    del X, T
+    shape, spec = si.torus_large()
+    g = sg.Grid(spec)
+    g.tag_allocate(shape)
+    g.init_sdf(shape)
+    g.reinit(50, CFL)
+    r = S.evaluate(g, net)
+    g.close()
+    net.close()
+    r["training"] = {"samples": info, "steps": steps, "batch": 8192, "seconds": secs,
+                     "loss": [[a, b] for a, b in hist]}
+    return r
+
+
 def phase_totals(phases):
     """Sum the durations between consecutive markers per phase name (ms)."""
     tot = {}
@@ -517,6 +540,8 @@ def run_sg(args):
                        "d2h_bytes_per_step": sum(4 * len(b.out) * b.n for b in bodies)}
     if not args.no_batch:
         line["batch"] = batch_section(sg, torch)
+    if not args.no_surrogate:
+        line["surrogate"] = surrogate_section(sg, torch)
     if not args.no_cpu_baseline and rank == 0 and ws == 1:
         est = oracle_calibrate(args.iters, args.particles)
         frac = min(1.0, max(0.02, 15.0 / est))
@@ -544,6 +569,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-body batch measurement")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip training and timing the surrogate")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -168,8 +168,10 @@ SG_API sg_status sg_reinit(sg_grid *g, int32_t iterations, float cfl);
  *   W  = sum_s w(|s|) H(-phi(x+sh)) / sum_s w(|s|)
  *   G^ = h grad W = sum_s w'(|s|) (-s/|s|) H(-phi(x+sh)) / sum_s w(|s|).
  * Far packages: W = 1 inside, 0 outside, G^ = 0.  Writes SG_FIELD_W and
- * SG_FIELD_GWX/GWY/GWZ.  `mlp` must be NULL for mode 0.
- * Errors: SG_ERR_INVALID for an unknown mode.  Requires phi. */
+ * SG_FIELD_GWX/GWY/GWZ.  Mode 0 takes mlp = NULL; mode 1 (surrogate with
+ * exact fallback, see SG_SUR_*) takes an sg_mlp*.
+ * Errors: SG_ERR_INVALID for an unknown mode or a missing or extra network.
+ * Requires phi. */
 SG_API sg_status sg_kernel_integrals(sg_grid *g, int32_t mode, const void *mlp);
 
 /* Particle probe ("Grid-Particle Coupling"): trilinear interpolation of phi,
@@ -248,6 +250,68 @@ SG_API sg_status sg_batch_autotune(sg_batch *b, sg_batch_plan *plan, int32_t rep
 SG_API sg_status sg_batch_get_field(sg_batch *b, int32_t body, int32_t field, void **dev_ptr, int64_t *n_elems);
 SG_API int64_t sg_batch_n_packages(const sg_batch *b);
 SG_API const char *sg_batch_last_error(const sg_batch *b);
+
+/* ------------------------------------------------------------------------ */
+/* Kernel-integral surrogate (not in the paper): a 27 -> 64 -> 64 -> 4       */
+/* multilayer perceptron with SiLU hidden activations, BF16 weights and      */
+/* activations, FP32 accumulation and FP32 master weights.                   */
+/* ------------------------------------------------------------------------ */
+typedef struct sg_mlp sg_mlp;
+
+/* Parameter vector (FP32, host): W1[64][27], b1[64], W2[64][64], b2[64],
+ * W3[4][64], b3[4] (row = output unit).  Inputs are bf16 rows of 32 values:
+ * v_n = clip(phi(x + s h) / h, -1, 1) for the 27 offsets s in {-1,0,1}^3,
+ * n = (sx+1) + 3 (sy+1) + 9 (sz+1), then 5 zeros.  Outputs per row:
+ * (W, Gx, Gy, Gz) as defined by sg_kernel_integrals. */
+#define SG_MLP_NPARAM 6212
+#define SG_MLP_ROW 32
+
+/* Create a network on the current device from `params` (copied); work runs
+ * on `stream`.  Errors: SG_ERR_INVALID, SG_ERR_OOM, SG_ERR_CUDA. */
+SG_API sg_status sg_mlp_create(const float *params, void *stream, sg_mlp **out);
+SG_API sg_status sg_mlp_destroy(sg_mlp *m);
+/* Replace the parameters (copied; Adam moments and step count reset). */
+SG_API sg_status sg_mlp_set_params(sg_mlp *m, const float *params);
+/* Read the FP32 master parameters back (synchronises the stream). */
+SG_API sg_status sg_mlp_get_params(sg_mlp *m, float *params);
+/* y[n][4] = network(x[n][SG_MLP_ROW]); device arrays owned by the caller. */
+SG_API sg_status sg_mlp_forward(sg_mlp *m, int64_t n, const void *x_bf16, float *y);
+/* Gradient of L = mean over rows and the 4 outputs of (y - t)^2 with respect
+ * to every parameter, written to grad[SG_MLP_NPARAM] (device, FP32); rows
+ * idx[0..n) of x and t (idx NULL: rows 0..n); *loss (device, may be NULL)
+ * receives L.  Uses the BF16 copy of the current parameters. */
+SG_API sg_status sg_mlp_loss_grad(sg_mlp *m, int64_t n, const void *x_bf16, const float *t, const int32_t *idx,
+                                  float *grad, float *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with
+ * learning rate lr on the batch of rows idx[0..batch) (or 0..batch). */
+SG_API sg_status sg_mlp_train_step(sg_mlp *m, int64_t batch, const void *x_bf16, const float *t,
+                                   const int32_t *idx, float lr, float *loss);
+SG_API const char *sg_mlp_last_error(const sg_mlp *m);
+
+/* Classes of a data point for sg_kernel_integrals mode 1 (decided in float
+ * from the grid's phi with explicitly rounded operations):
+ *   SG_SUR_TRIVIAL_IN / _OUT: every one of the 27 taps saturates the
+ *     smoothed Heaviside (-phi_s / h > 1, resp. < -1): W = 1 / 0, G = 0;
+ *   SG_SUR_FALLBACK: |phi / h| < 1, or |kappa| h > 0.1 with kappa the 7-point
+ *     Laplacian of phi: the exact 27-tap sum of mode 0, bit for bit;
+ *   SG_SUR_NETWORK: the network on the 27 clipped inputs. */
+enum { SG_SUR_TRIVIAL_IN = 0, SG_SUR_TRIVIAL_OUT = 1, SG_SUR_FALLBACK = 2, SG_SUR_NETWORK = 3 };
+
+/* Class of every data point: cls[P*64] (device, caller-owned); far packages
+ * get 255.  Requires phi. */
+SG_API sg_status sg_surrogate_classify(sg_grid *g, uint8_t *cls);
+
+/* Training samples of a grid whose exact integrals (mode 0) are current:
+ * every SG_SUR_NETWORK point whose SplitMix64 hash of (seed, point index)
+ * falls below `keep` (a fraction in [0, 1]), in point order: x rows of
+ * SG_MLP_ROW bf16 inputs and t rows of (W, Gx, Gy, Gz).  At most cap rows are
+ * written; *count receives the number of points selected (synchronises). */
+SG_API sg_status sg_surrogate_samples(sg_grid *g, uint64_t seed, float keep, int64_t cap, void *x_bf16, float *t,
+                                      int64_t *count);
+
+/* Points per class (SG_SUR_* order) of the last mode-1 sg_kernel_integrals
+ * call on this grid (synchronises). */
+SG_API sg_status sg_surrogate_stats(sg_grid *g, int64_t counts[4]);
 
 /* Allocation-free variant of sg_morton_order.  The paper has no counterpart;
  * this entry point exists for callers that cannot let a library allocate

@@ -224,6 +224,68 @@ def morton_order(keys):
     return order
 
 
+MLP_IN, MLP_H, MLP_OUT = 27, 64, 4
+
+
+def mlp_nparam():
+    lib().or_mlp_nparam.restype = C.c_int64
+    return int(lib().or_mlp_nparam())
+
+
+def mlp_unpack(par):
+    """Views W1[64,27], b1, W2[64,64], b2, W3[4,64], b3 of a flat parameter vector."""
+    par = np.asarray(par)
+    o = 0
+    out = []
+    for shape in ((MLP_H, MLP_IN), (MLP_H,), (MLP_H, MLP_H), (MLP_H,), (MLP_OUT, MLP_H), (MLP_OUT,)):
+        n = int(np.prod(shape))
+        out.append(par[o:o + n].reshape(shape))
+        o += n
+    return out
+
+
+def mlp_forward(par, x):
+    par, x = _f64(par), _f64(x)
+    n = x.shape[0]
+    y = np.empty((n, MLP_OUT))
+    lib().or_mlp_forward(_p(par), C.c_int64(n), _p(x), _p(y), None, None)
+    return y
+
+
+def mlp_loss_grad(par, x, t):
+    par, x, t = _f64(par), _f64(x), _f64(t)
+    g = np.empty_like(par)
+    lib().or_mlp_loss_grad.restype = C.c_double
+    loss = lib().or_mlp_loss_grad(_p(par), C.c_int64(x.shape[0]), _p(x), _p(t), _p(g))
+    return float(loss), g
+
+
+def adam_step(par, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In place on par, m, v (float64 arrays)."""
+    lib().or_adam_step(_p(par), _p(_f64(grad)), _p(m), _p(v), C.c_int64(par.size), C.c_double(lr),
+                       C.c_double(beta1), C.c_double(beta2), C.c_double(eps), C.c_int64(step))
+
+
+def surrogate_inputs(spec, nbr, phi):
+    phi = _f64(phi)
+    P = phi.shape[0]
+    x = np.zeros((P, 64, MLP_IN))
+    lib().or_surrogate_inputs(C.byref(_grid(spec)), C.c_int64(P), _p(np.ascontiguousarray(nbr, np.int32)), _p(phi),
+                              _p(x))
+    return x
+
+
+def surrogate_class(spec, nbr, phi32):
+    """Classes (0 in, 1 out, 2 fallback, 3 network; 255 far) decided in float
+    from the device's float phi, as the device decides them."""
+    phi32 = np.ascontiguousarray(phi32, np.float32)
+    P = phi32.shape[0]
+    cls = np.empty((P, 64), np.uint8)
+    lib().or_surrogate_class(C.byref(_grid(spec)), C.c_int64(P), _p(np.ascontiguousarray(nbr, np.int32)),
+                             _p(phi32), _p(cls))
+    return cls
+
+
 def build_grid(spec, shape, far=None):
     """Tag, allocate, build tables and initialise phi.  Returns a namespace."""
     cell_pkg, cell_type, P, ties = tag(spec, shape)

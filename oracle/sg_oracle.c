@@ -575,3 +575,172 @@ void or_morton_order(int64_t n, const uint64_t *keys, int64_t *order) {
     for (int64_t i = 0; i < n; ++i) order[i] = kv[i].idx;
     free(kv);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Kernel-integral surrogate: a 27 -> 64 -> 64 -> 4 multilayer perceptron     */
+/* with SiLU hidden activations (not in the paper; the learned stand-in for   */
+/* the kernel integral).  Inputs: v_n = clip(phi(x + s h) / h, -1, 1) for the */
+/* 27 offsets s in {-1,0,1}^3, n = (sx+1) + 3 (sy+1) + 9 (sz+1).  Outputs:   */
+/* (W, Gx, Gy, Gz).  Parameters, one flat vector:                            */
+/*   W1[64][27], b1[64], W2[64][64], b2[64], W3[4][64], b3[4]  (6212 values) */
+/* Loss: mean over the batch and the 4 outputs of (y - t)^2.                 */
+/* Adam (Kingma & Ba 2015) with bias correction.                             */
+/* ------------------------------------------------------------------------- */
+#define MLP_IN 27
+#define MLP_H 64
+#define MLP_OUT 4
+#define MLP_NPARAM (MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_OUT * MLP_H + MLP_OUT)
+
+int64_t or_mlp_nparam(void) { return MLP_NPARAM; }
+
+static double sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }
+
+/* Forward pass of n samples; y[n][4].  Hidden pre-activations are returned
+ * when z1, z2 ([n][64]) are not NULL. */
+void or_mlp_forward(const double *par, int64_t n, const double *x, double *y, double *z1, double *z2) {
+    const double *W1 = par, *b1 = W1 + MLP_H * MLP_IN, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H;
+    const double *W3 = b2 + MLP_H, *b3 = W3 + MLP_OUT * MLP_H;
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < n; ++s) {
+        double a1[MLP_H], a2[MLP_H];
+        for (int o = 0; o < MLP_H; ++o) {
+            double z = b1[o];
+            for (int i = 0; i < MLP_IN; ++i) z += W1[o * MLP_IN + i] * x[s * MLP_IN + i];
+            if (z1) z1[s * MLP_H + o] = z;
+            a1[o] = z * sigmoid(z);
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            double z = b2[o];
+            for (int i = 0; i < MLP_H; ++i) z += W2[o * MLP_H + i] * a1[i];
+            if (z2) z2[s * MLP_H + o] = z;
+            a2[o] = z * sigmoid(z);
+        }
+        for (int o = 0; o < MLP_OUT; ++o) {
+            double z = b3[o];
+            for (int i = 0; i < MLP_H; ++i) z += W3[o * MLP_H + i] * a2[i];
+            y[s * MLP_OUT + o] = z;
+        }
+    }
+}
+
+/* Loss and its gradient with respect to every parameter (grad[6212]). */
+double or_mlp_loss_grad(const double *par, int64_t n, const double *x, const double *t, double *grad) {
+    const double *W2 = par + MLP_H * MLP_IN + MLP_H, *W3 = W2 + MLP_H * MLP_H + MLP_H;
+    double *z1 = (double *)malloc(sizeof(double) * (size_t)(n * MLP_H));
+    double *z2 = (double *)malloc(sizeof(double) * (size_t)(n * MLP_H));
+    double *y = (double *)malloc(sizeof(double) * (size_t)(n * MLP_OUT));
+    or_mlp_forward(par, n, x, y, z1, z2);
+    for (int64_t k = 0; k < MLP_NPARAM; ++k) grad[k] = 0.0;
+    double *gW1 = grad, *gb1 = gW1 + MLP_H * MLP_IN, *gW2 = gb1 + MLP_H, *gb2 = gW2 + MLP_H * MLP_H;
+    double *gW3 = gb2 + MLP_H, *gb3 = gW3 + MLP_OUT * MLP_H;
+    double loss = 0.0;
+    const double scale = 1.0 / (double)(n * MLP_OUT);
+    for (int64_t s = 0; s < n; ++s) {
+        double a1[MLP_H], a2[MLP_H], dy[MLP_OUT], dz2[MLP_H], dz1[MLP_H];
+        for (int o = 0; o < MLP_H; ++o) a1[o] = z1[s * MLP_H + o] * sigmoid(z1[s * MLP_H + o]);
+        for (int o = 0; o < MLP_H; ++o) a2[o] = z2[s * MLP_H + o] * sigmoid(z2[s * MLP_H + o]);
+        for (int o = 0; o < MLP_OUT; ++o) {
+            double e = y[s * MLP_OUT + o] - t[s * MLP_OUT + o];
+            loss += e * e * scale;
+            dy[o] = 2.0 * e * scale;
+            gb3[o] += dy[o];
+            for (int i = 0; i < MLP_H; ++i) gW3[o * MLP_H + i] += dy[o] * a2[i];
+        }
+        for (int i = 0; i < MLP_H; ++i) {
+            double d = 0.0;
+            for (int o = 0; o < MLP_OUT; ++o) d += dy[o] * W3[o * MLP_H + i];
+            double z = z2[s * MLP_H + i], sg = sigmoid(z);
+            dz2[i] = d * sg * (1.0 + z * (1.0 - sg)); /* SiLU'(z) */
+            gb2[i] += dz2[i];
+            for (int j = 0; j < MLP_H; ++j) gW2[i * MLP_H + j] += dz2[i] * a1[j];
+        }
+        for (int j = 0; j < MLP_H; ++j) {
+            double d = 0.0;
+            for (int i = 0; i < MLP_H; ++i) d += dz2[i] * W2[i * MLP_H + j];
+            double z = z1[s * MLP_H + j], sg = sigmoid(z);
+            dz1[j] = d * sg * (1.0 + z * (1.0 - sg));
+            gb1[j] += dz1[j];
+            for (int i = 0; i < MLP_IN; ++i) gW1[j * MLP_IN + i] += dz1[j] * x[s * MLP_IN + i];
+        }
+    }
+    free(z1);
+    free(z2);
+    free(y);
+    return loss;
+}
+
+/* One Adam step (step >= 1) on par with moments m, v. */
+void or_adam_step(double *par, const double *grad, double *m, double *v, int64_t n, double lr, double beta1,
+                  double beta2, double eps, int64_t step) {
+    const double c1 = 1.0 - pow(beta1, (double)step), c2 = 1.0 - pow(beta2, (double)step);
+    for (int64_t k = 0; k < n; ++k) {
+        m[k] = beta1 * m[k] + (1.0 - beta1) * grad[k];
+        v[k] = beta2 * v[k] + (1.0 - beta2) * grad[k] * grad[k];
+        par[k] -= lr * (m[k] / c1) / (sqrt(v[k] / c2) + eps);
+    }
+}
+
+/* Surrogate inputs of every data point of the active packages: x[P][64][27]
+ * (far packages left untouched). */
+void or_surrogate_inputs(const or_grid *g, int64_t P, const int32_t *nbr, const double *phi, double *x) {
+    const double inv_h = 1.0 / g->h;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 2; p < P; ++p) {
+        const int32_t *nb = nbr + p * 27;
+        for (int d = 0; d < PKG3; ++d) {
+            int i = d & 3, j = (d >> 2) & 3, k = d >> 4;
+            for (int sz = -1; sz <= 1; ++sz)
+                for (int sy = -1; sy <= 1; ++sy)
+                    for (int sx = -1; sx <= 1; ++sx) {
+                        double v = phi[shift_index(nb, i + sx, j + sy, k + sz)] * inv_h;
+                        if (v < -1.0) v = -1.0;
+                        if (v > 1.0) v = 1.0;
+                        x[(p * PKG3 + d) * 27 + (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1)] = v;
+                    }
+        }
+    }
+}
+
+/* Classes of the surrogate integral, decided in float exactly as the device
+ * decides them (same operations, same order, no contraction): 0 every tap
+ * inside (-phi_s / h > 1), 1 every tap outside (< -1), 2 fallback
+ * (|phi / h| < 1 or |kappa| h > 0.1, kappa the 7-point Laplacian in float),
+ * 3 network.  phi is the device's float field; far packages get 255. */
+void or_surrogate_class(const or_grid *g, int64_t P, const int32_t *nbr, const float *phi, uint8_t *cls) {
+    const float inv_h = (float)(1.0 / g->h), inv_h2 = (float)(1.0 / (g->h * g->h)), h = (float)g->h;
+    for (int d = 0; d < 2 * PKG3; ++d) cls[d] = 255;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 2; p < P; ++p) {
+        const int32_t *nb = nbr + p * 27;
+        for (int d = 0; d < PKG3; ++d) {
+            int i = d & 3, j = (d >> 2) & 3, k = d >> 4;
+            int all_in = 1, all_out = 1;
+            for (int n = 0; n < 27; ++n) {
+                int sx = n % 3 - 1, sy = (n / 3) % 3 - 1, sz = n / 9 - 1;
+                float f = phi[shift_index(nb, i + sx, j + sy, k + sz)];
+                float t = (-f) * inv_h;
+                all_in &= t > 1.0f;
+                all_out &= t < -1.0f;
+            }
+            uint8_t c;
+            if (all_in)
+                c = 0;
+            else if (all_out)
+                c = 1;
+            else {
+                float v = phi[shift_index(nb, i, j, k)];
+                float c2 = 2.0f * v;
+                float a = (phi[shift_index(nb, i + 1, j, k)] - c2) + phi[shift_index(nb, i - 1, j, k)];
+                a = a + ((phi[shift_index(nb, i, j + 1, k)] - c2) + phi[shift_index(nb, i, j - 1, k)]);
+                a = a + ((phi[shift_index(nb, i, j, k + 1)] - c2) + phi[shift_index(nb, i, j, k - 1)]);
+                float kap = a * inv_h2;
+                float r = v * inv_h;
+                if (fabsf(r) < 1.0f || fabsf(kap) * h > 0.1f)
+                    c = 2;
+                else
+                    c = 3;
+            }
+            cls[p * PKG3 + d] = c;
+        }
+    }
+}

@@ -98,6 +98,18 @@ def lib():
         L.sg_last_error.restype = C.c_char_p
         L.sg_version.restype = C.c_char_p
         L.sg_kernel_launch_count.restype = i64
+        L.sg_mlp_create.argtypes = [vp, vp, C.POINTER(vp)]
+        L.sg_mlp_destroy.argtypes = [vp]
+        L.sg_mlp_set_params.argtypes = [vp, vp]
+        L.sg_mlp_get_params.argtypes = [vp, vp]
+        L.sg_mlp_forward.argtypes = [vp, i64, vp, vp]
+        L.sg_mlp_loss_grad.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.sg_mlp_train_step.argtypes = [vp, i64, vp, vp, vp, C.c_float, vp]
+        L.sg_mlp_last_error.argtypes = [vp]
+        L.sg_mlp_last_error.restype = C.c_char_p
+        L.sg_surrogate_classify.argtypes = [vp, vp]
+        L.sg_surrogate_samples.argtypes = [vp, C.c_uint64, C.c_float, i64, vp, vp, C.POINTER(i64)]
+        L.sg_surrogate_stats.argtypes = [vp, C.POINTER(i64)]
         L.sg_batch_create.argtypes = [C.POINTER(vp), i32, vp, C.POINTER(vp)]
         L.sg_batch_destroy.argtypes = [vp]
         L.sg_batch_reset.argtypes = [vp]
@@ -248,7 +260,35 @@ class Grid:
         self._check(self._lib.sg_reinit(self._h, int(iterations), float(cfl)))
 
     def kernel_integrals(self, mode=0, mlp=None):
-        self._check(self._lib.sg_kernel_integrals(self._h, int(mode), mlp))
+        """mode 0: exact; mode 1: surrogate network `mlp` (an MLP) with exact fallback."""
+        self._check(self._lib.sg_kernel_integrals(self._h, int(mode), mlp.handle if mlp is not None else None))
+
+    def surrogate_classify(self):
+        torch = _torch()
+        cls = torch.empty(self.n_packages() * 64, dtype=torch.uint8, device="cuda")
+        self._check(self._lib.sg_surrogate_classify(self._h, _ptr(cls)))
+        return cls.view(-1, 64)
+
+    def surrogate_samples(self, seed, keep=1.0, cap=None):
+        """(x bf16 [n, 32], t float32 [n, 4], selected count) of this grid's
+        network-class points; needs current exact integrals."""
+        torch = _torch()
+        n = C.c_int64()
+        if cap is None:
+            self._check(self._lib.sg_surrogate_samples(self._h, seed, float(keep), 0, None, None, C.byref(n)))
+            cap = n.value
+        x = torch.empty((max(cap, 1), 32), dtype=torch.bfloat16, device="cuda")
+        t = torch.empty((max(cap, 1), 4), dtype=torch.float32, device="cuda")
+        self._check(self._lib.sg_surrogate_samples(self._h, seed, float(keep), int(cap), _ptr(x), _ptr(t),
+                                                   C.byref(n)))
+        m = min(cap, n.value)
+        return x[:m], t[:m], n.value
+
+    def surrogate_stats(self):
+        """Points per class (in, out, fallback, network) of the last mode-1 call."""
+        c = (C.c_int64 * 4)()
+        self._check(self._lib.sg_surrogate_stats(self._h, c))
+        return [int(v) for v in c]
 
     def probe(self, x, y, z, morton=True, out=None, outputs=PROBE_OUTPUTS):
         """Probe at device float32 tensors x, y, z; returns a dict of outputs.
@@ -356,6 +396,72 @@ class Batch:
             return torch.as_tensor(_CudaArray(p.value, (n.value,), "<i4"), device="cuda").view(-1, 27)
         self._check(self._lib.sg_batch_get_field(self._h, int(body), FIELDS[name], C.byref(p), C.byref(n)))
         return torch.as_tensor(_CudaArray(p.value, (n.value,), "<f4"), device="cuda").view(-1, 64)
+
+
+MLP_NPARAM = 6212
+SUR_CLASSES = ("trivial_in", "trivial_out", "fallback", "network")
+
+
+class MLP:
+    """The kernel-integral surrogate network on the current device."""
+
+    def __init__(self, params, stream=None):
+        torch = _torch()
+        self._lib = lib()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == MLP_NPARAM
+        h = C.c_void_p()
+        st = self._lib.sg_mlp_create(p.ctypes.data_as(C.c_void_p), C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != SG_OK:
+            raise SgError(st, "sg_mlp_create failed")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _check(self, st):
+        if st != SG_OK:
+            raise SgError(st, self._lib.sg_mlp_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sg_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self._lib.sg_mlp_set_params(self._h, p.ctypes.data_as(C.c_void_p)))
+
+    def get_params(self):
+        p = np.empty(MLP_NPARAM, np.float32)
+        self._check(self._lib.sg_mlp_get_params(self._h, p.ctypes.data_as(C.c_void_p)))
+        return p
+
+    def forward(self, x):
+        torch = _torch()
+        y = torch.empty((x.shape[0], 4), dtype=torch.float32, device=x.device)
+        self._check(self._lib.sg_mlp_forward(self._h, x.shape[0], _ptr(x), _ptr(y)))
+        return y
+
+    def loss_grad(self, x, t, idx=None):
+        torch = _torch()
+        n = idx.numel() if idx is not None else x.shape[0]
+        g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=x.device)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        self._check(self._lib.sg_mlp_loss_grad(self._h, n, _ptr(x), _ptr(t), _ptr(idx), _ptr(g), _ptr(loss)))
+        return g, loss
+
+    def train_step(self, x, t, idx, lr, loss=None):
+        n = idx.numel() if idx is not None else x.shape[0]
+        self._check(self._lib.sg_mlp_train_step(self._h, n, _ptr(x), _ptr(t), _ptr(idx), float(lr), _ptr(loss)))
 
 
 NOALLOC_MAX_PARTICLES = 262144

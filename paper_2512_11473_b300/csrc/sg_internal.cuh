@@ -59,6 +59,7 @@ struct sg_grid {
     sg::Buf phi_tmp;
     sg::Buf err;       // int32 sticky device error word
     sg::Buf scratch;   // reusable temporary space (scans, sort)
+    sg::Buf stats;     // class counts of the last surrogate integral call
     sg::Buf host_pin;  // pinned host word for read-backs
     std::string last_error;
 };
@@ -108,6 +109,9 @@ cudaError_t launch_reinit_step(const GridF& G, const int32_t* nbr, const float* 
 cudaError_t launch_copy_active(const float* src, float* dst, int64_t P, cudaStream_t s);
 cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const float* phi, float* W, float* gx,
                                     float* gy, float* gz, int64_t P, cudaStream_t s);
+
+// surrogate (sg_mlp.cu)
+cudaError_t launch_surrogate_integrals(sg_grid* g, const sg_mlp* m, float* W, float* gx, float* gy, float* gz);
 
 // probe (sg_probe.cu)
 struct ProbeFields {

@@ -339,3 +339,23 @@ def random_bodies(n, seed=1, p_lo=1e2, p_hi=1e5, kinds=(SPHERE, TORUS, ROUNDED_B
         lo = tuple(-0.5 * m * lc for _ in range(3))
         out.append((s, GridSpec(lo, (m, m, m), h), target))
     return out
+
+
+# ----------------------------------------------------------------------------
+# Surrogate network initialisation
+# ----------------------------------------------------------------------------
+MLP_SHAPES = ((64, 27), (64,), (64, 64), (64,), (4, 64), (4,))
+
+
+def mlp_init_params(seed=4):
+    """Flat float32 parameter vector W1[64][27], b1, W2[64][64], b2, W3[4][64],
+    b3 with every entry uniform in [-1/sqrt(fan_in), 1/sqrt(fan_in)),
+    fan_in = 27, 27, 64, 64, 64, 64 (the layer's inputs)."""
+    st = Stream(seed)
+    fan = (27, 27, 64, 64, 64, 64)
+    out = []
+    for shape, f in zip(MLP_SHAPES, fan):
+        n = int(np.prod(shape))
+        a = 1.0 / math.sqrt(f)
+        out.append((2.0 * st.uniform53(n) - 1.0) * a)
+    return np.concatenate(out).astype(np.float32)
