@@ -494,6 +494,25 @@ def run_sg(args):
         tb, units_prof = prof
         traffic = tb * (big.n_pt / units_prof) if units_prof == units_prof and units_prof > 0 else tb
 
+    # the step's particles are stored in Morton order, so the probe's sort
+    # check finds them sorted and skips the radix passes; the full sort of
+    # the same particles in a shuffled order is timed here for reference
+    big_b = max(bodies, key=lambda b: b.P)
+    perm = torch.randperm(big_b.n, device="cuda")
+    shuffled = [v[perm].contiguous() for v in big_b.X]
+    del perm
+    sort_ms = {}
+    for label, pts in (("morton_ordered_input", big_b.X), ("shuffled_input", shuffled)):
+        big_b.g.morton_order(*pts)
+        e0, e1 = Ev(), Ev()
+        e0.record()
+        for _ in range(3):
+            big_b.g.morton_order(*pts)
+        e1.record()
+        torch.cuda.synchronize()
+        sort_ms[label] = e0.elapsed_time(e1) / 3
+    del shuffled
+
     line = {
         "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
@@ -508,6 +527,7 @@ def run_sg(args):
             "parallelism": "replicas (independent bodies per GPU, no collective)",
         },
         "probes_per_s": probes / (probe_ms * 1e-3) if probe_ms > 0 else None,
+        "morton_sort_ms_%s_%dM" % (big.name, big.n // 1_000_000): sort_ms,
         "breakdown_ms_per_step": breakdown,
         "roofline": {"bound": "hbm", "kernel": "k_reinit_step (%s)" % big.name, "achieved": achieved,
                      "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,

@@ -102,9 +102,22 @@ GridFF grid_ff(const sg_grid* g) {
 ShapeFF shape_ff(const sg_shape* s) {
     ShapeFF S;
     S.kind = s->kind;
-    for (int i = 0; i < 3; ++i) S.centre[i] = split(s->centre[i]);
-    for (int i = 0; i < 9; ++i) S.rot[i] = split(s->rot[i]);
-    for (int i = 0; i < 8; ++i) S.p[i] = split(s->p[i]);
+    bool plain = true;
+    for (int i = 0; i < 3; ++i) {
+        S.centre[i] = split(s->centre[i]);
+        S.cf[i] = (float)s->centre[i];
+        plain &= s->centre[i] == 0.0;
+    }
+    for (int i = 0; i < 9; ++i) {
+        S.rot[i] = split(s->rot[i]);
+        S.rf[i] = (float)s->rot[i];
+        plain &= s->rot[i] == ((i % 4 == 0) ? 1.0 : 0.0);
+    }
+    for (int i = 0; i < 8; ++i) {
+        S.p[i] = split(s->p[i]);
+        S.pf[i] = (float)s->p[i];
+    }
+    S.plain = plain ? 1 : 0;
     return S;
 }
 
@@ -373,16 +386,17 @@ sg_status sg_probe(sg_grid* g, int64_t n, const float* x, const float* y, const 
     ProbeOut O{{phi, nx, ny, nz, W, Gx, Gy, Gz}};
     const GridF G = grid_f(g);
     const int32_t* order = nullptr;
+    const int* unsorted = nullptr;
     if (flags & SG_PROBE_MORTON) {
         size_t sb = sort_scratch_bytes(n, morton_bits(G));
         size_t ob = ((size_t)n * 4 + 255) & ~(size_t)255;
         if (!ensure(g, g->scratch, sb + ob)) return fail(g, SG_ERR_OOM, "sg_probe: out of memory");
         int32_t* ord = (int32_t*)((char*)g->scratch.p + sb);
-        SG_CUDA(g, morton_sort(G, n, x, y, z, nullptr, ord, g->scratch.p, g->stream), "probe sort");
+        SG_CUDA(g, morton_sort(G, n, x, y, z, nullptr, ord, g->scratch.p, g->stream, false, &unsorted), "probe sort");
         order = ord;
     }
-    SG_CUDA(g, launch_probe(G, (const int32_t*)g->cell_pkg.p, (const int32_t*)g->nbr.p, F, n, x, y, z, order, O,
-                            g->stream),
+    SG_CUDA(g, launch_probe(G, (const int32_t*)g->cell_pkg.p, (const int32_t*)g->nbr.p, F, n, x, y, z, order, unsorted,
+                            O, g->stream),
             "probe");
     return SG_OK;
 }

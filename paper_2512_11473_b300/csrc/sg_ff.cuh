@@ -107,9 +107,11 @@ enum { SHAPE_SPHERE = 0, SHAPE_PLANE = 1, SHAPE_TORUS = 2, SHAPE_PRISM = 3, SHAP
 
 struct ShapeFF {
     int kind;
+    int plain;  // rotation is the identity and the centre the origin: q = x
     ff centre[3];
     ff rot[9];  // row-major, local -> world
     ff p[8];
+    float cf[3], rf[9], pf[8];  // the same in float, for the float pre-filter
 };
 
 // local coordinates q = R^T (x - centre)
@@ -149,7 +151,11 @@ __device__ inline ff ff_triangle_sdf(ff px, ff py, const ff* t) {
 // Exact signed distance (negative inside) of each primitive, in float-float.
 __device__ inline ff ff_sdf(const ShapeFF& s, const ff x[3]) {
     ff q[3];
-    ff_to_local(s, x, q);
+    if (s.plain) {
+        q[0] = x[0], q[1] = x[1], q[2] = x[2];
+    } else {
+        ff_to_local(s, x, q);
+    }
     const ff zero{0.0f, 0.0f};
     switch (s.kind) {
     case SHAPE_SPHERE:
@@ -182,6 +188,66 @@ __device__ inline ff ff_sdf(const ShapeFF& s, const ff x[3]) {
     }
     default:
         return ff{NAN, 0.0f};
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The same distances in plain float, for the pre-filter of the band
+// predicate: decisions far from the thresholds are taken here, the rest in
+// float-float.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float f_seg_dist2(float px, float py, float ax, float ay, float bx, float by) {
+    const float ex = bx - ax, ey = by - ay, wx = px - ax, wy = py - ay;
+    const float t = fminf(fmaxf((wx * ex + wy * ey) / (ex * ex + ey * ey), 0.0f), 1.0f);
+    const float dx = wx - t * ex, dy = wy - t * ey;
+    return dx * dx + dy * dy;
+}
+
+__device__ inline float f_sdf(const ShapeFF& s, const float x[3]) {
+    float q[3];
+    if (s.plain) {
+        q[0] = x[0], q[1] = x[1], q[2] = x[2];
+    } else {
+        const float d0 = x[0] - s.cf[0], d1 = x[1] - s.cf[1], d2 = x[2] - s.cf[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) q[i] = s.rf[i] * d0 + s.rf[3 + i] * d1 + s.rf[6 + i] * d2;
+    }
+    const float* p = s.pf;
+    switch (s.kind) {
+    case SHAPE_SPHERE:
+        return sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) - p[0];
+    case SHAPE_PLANE:
+        return q[2];
+    case SHAPE_TORUS: {
+        const float a = sqrtf(q[0] * q[0] + q[1] * q[1]) - p[0];
+        return sqrtf(a * a + q[2] * q[2]) - p[1];
+    }
+    case SHAPE_PRISM: {
+        float d2 = f_seg_dist2(q[0], q[1], p[0], p[1], p[2], p[3]);
+        d2 = fminf(d2, f_seg_dist2(q[0], q[1], p[2], p[3], p[4], p[5]));
+        d2 = fminf(d2, f_seg_dist2(q[0], q[1], p[4], p[5], p[0], p[1]));
+        const float orient = (p[2] - p[0]) * (p[5] - p[1]) - (p[3] - p[1]) * (p[4] - p[0]);
+        const float c0 = (p[2] - p[0]) * (q[1] - p[1]) - (p[3] - p[1]) * (q[0] - p[0]);
+        const float c1 = (p[4] - p[2]) * (q[1] - p[3]) - (p[5] - p[3]) * (q[0] - p[2]);
+        const float c2 = (p[0] - p[4]) * (q[1] - p[5]) - (p[1] - p[5]) * (q[0] - p[4]);
+        const bool inside = orient > 0.0f ? (c0 > 0.0f && c1 > 0.0f && c2 > 0.0f) : (c0 < 0.0f && c1 < 0.0f && c2 < 0.0f);
+        const float w0 = inside ? -sqrtf(d2) : sqrtf(d2);
+        const float w1 = fabsf(q[2] - 0.5f * (p[6] + p[7])) - 0.5f * (p[7] - p[6]);
+        const float a = fmaxf(w0, 0.0f), b = fmaxf(w1, 0.0f);
+        return fminf(fmaxf(w0, w1), 0.0f) + sqrtf(a * a + b * b);
+    }
+    case SHAPE_ROUNDED_BOX: {
+        float o = 0.0f, m = -INFINITY;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float d = fabsf(q[i]) - (p[i] - p[3]);
+            if (d > 0.0f) o += d * d;
+            m = fmaxf(m, d);
+        }
+        return sqrtf(o) + fminf(m, 0.0f) - p[3];
+    }
+    default:
+        return NAN;
     }
 }
 

@@ -82,9 +82,10 @@ ShapeFF shape_ff(const sg_shape* s);
 
 // scans (sg_scan.cu): exclusive prefix sum of n uint32 values into out
 // (may alias in), total into *total (device).  Scratch: scan_scratch_bytes(n).
+// With run != nullptr the kernels do nothing when *run == 0 (device flag).
 size_t scan_scratch_bytes(int64_t n);
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, void* scratch,
-                               cudaStream_t s);
+                               cudaStream_t s, const int* run = nullptr);
 
 // tagging / init (sg_tag.cu)
 cudaError_t launch_tag_flags(const GridFF& G, const ShapeFF& S, uint8_t* cell_type, uint32_t* active, int64_t nc,
@@ -122,10 +123,15 @@ struct ProbeOut {
 };
 int morton_bits(const GridF& G);  // significant key bits
 size_t sort_scratch_bytes(int64_t n, int key_bits);
+// Stable Morton sort.  The key pass also checks whether the keys are already
+// non-decreasing; if so the radix passes return at once and order_out is
+// the identity (written only when identity_out, else left to the caller,
+// who reads the device flag *unsorted_out: 0 = input already in order).
 cudaError_t morton_sort(const GridF& G, int64_t n, const float* x, const float* y, const float* z, uint64_t* keys_out,
-                        int32_t* order_out, void* scratch, cudaStream_t s);
+                        int32_t* order_out, void* scratch, cudaStream_t s, bool identity_out = true,
+                        const int** unsorted_out = nullptr);
 cudaError_t launch_probe(const GridF& G, const int32_t* cell_pkg, const int32_t* nbr, const ProbeFields& F,
                          int64_t n, const float* x, const float* y, const float* z, const int32_t* order,
-                         const ProbeOut& out, cudaStream_t s);
+                         const int* unsorted, const ProbeOut& out, cudaStream_t s);
 
 }  // namespace sg

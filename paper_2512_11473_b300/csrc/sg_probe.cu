@@ -53,23 +53,42 @@ __device__ __forceinline__ uint64_t morton_key(const GridF& G, float x, float y,
     return key;
 }
 
+// Keys, identity indices, and the sortedness check: *unsorted is set when
+// some key exceeds its successor's (one atomic per warp that finds one, and
+// none once the flag is seen set).
 template <typename KeyT>
 __global__ void __launch_bounds__(RS_THREADS) k_morton_keys(GridF G, int64_t n, const float* __restrict__ x,
                                                             const float* __restrict__ y, const float* __restrict__ z,
                                                             KeyT* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                            uint64_t* __restrict__ keys_out) {
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t k = morton_key(G, x[q], y[q], z[q]);
-        keys[q] = (KeyT)k;
-        vals[q] = (uint32_t)q;
-        if (keys_out) keys_out[q] = k;
+                                                            uint64_t* __restrict__ keys_out, int* unsorted) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t iters = (n + stride - 1) / stride;
+    for (int64_t it = 0; it < iters; ++it) {  // uniform trip count: every lane takes part in the vote
+        const int64_t q = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        bool bad = false;
+        if (q < n) {
+            const uint64_t k = morton_key(G, x[q], y[q], z[q]);
+            keys[q] = (KeyT)k;
+            vals[q] = (uint32_t)q;
+            if (keys_out) keys_out[q] = k;
+            if (q + 1 < n) bad = k > morton_key(G, x[q + 1], y[q + 1], z[q + 1]);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, bad);
+        if (m && (threadIdx.x & 31) == __ffs(m) - 1 && *(volatile int*)unsorted == 0) atomicOr(unsorted, 1);
     }
+}
+
+__global__ void k_identity_if_sorted(const int* __restrict__ unsorted, int32_t* __restrict__ order, int64_t n) {
+    if (*unsorted) return;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        order[q] = (int32_t)q;
 }
 
 // Per-tile digit histogram, written digit-major: hist[d * nb + tile].
 template <typename KeyT>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const KeyT* __restrict__ keys, int64_t n, int shift,
-                                                        uint32_t* __restrict__ hist, int64_t nb) {
+                                                        uint32_t* __restrict__ hist, int64_t nb, const int* run) {
+    if (*run == 0) return;  // keys already in order
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -93,7 +112,8 @@ template <typename KeyT>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            KeyT* __restrict__ kout, uint32_t* __restrict__ vout,
                                                            int64_t n, int shift, const uint32_t* __restrict__ offs,
-                                                           int64_t nb) {
+                                                           int64_t nb, const int* run) {
+    if (*run == 0) return;  // keys already in order
     extern __shared__ __align__(16) unsigned char smem[];
     KeyT* s_k = (KeyT*)smem;
     uint32_t* s_v = (uint32_t*)(smem + RS_TILE * sizeof(KeyT));
@@ -184,9 +204,11 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe(GridF G, const int32_t* __
                                                        const int32_t* __restrict__ nbr, ProbeFields F, int64_t n,
                                                        const float* __restrict__ x, const float* __restrict__ y,
                                                        const float* __restrict__ z, const int32_t* __restrict__ order,
-                                                       ProbeOut out) {
+                                                       const int* __restrict__ unsorted, ProbeOut out) {
+    // with the input already in Morton order the walk is the input order
+    const bool use_order = order && (!unsorted || *unsorted != 0);
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = order ? (int64_t)__ldg(order + r) : r;
+        const int64_t q = use_order ? (int64_t)__ldg(order + r) : r;
         const float pos[3] = {__ldg(x + q), __ldg(y + q), __ldg(z + q)};
         int i0[3], l[3];
         float t[3];
@@ -235,9 +257,12 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 template <typename KeyT>
 cudaError_t sort_impl(const GridF& G, int64_t n, int key_bits, const float* x, const float* y, const float* z,
-                      uint64_t* keys_out, int32_t* order_out, void* scratch, cudaStream_t s) {
+                      uint64_t* keys_out, int32_t* order_out, void* scratch, cudaStream_t s, bool identity_out,
+                      const int** unsorted_out) {
     const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
     char* sp = (char*)scratch;
+    int* unsorted = (int*)sp;
+    sp += 256;
     KeyT* k0 = (KeyT*)sp;
     sp += align256(n * sizeof(KeyT));
     KeyT* k1 = (KeyT*)sp;
@@ -250,10 +275,11 @@ cudaError_t sort_impl(const GridF& G, int64_t n, int key_bits, const float* x, c
     sp += align256(256 * nb * sizeof(uint32_t));
     void* scan_scratch = sp;
 
-    k_morton_keys<KeyT><<<blocks_for(n, RS_THREADS), RS_THREADS, 0, s>>>(G, n, x, y, z, k0, v0, keys_out);
-    note_launch();
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaMemsetAsync(unsorted, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
+    k_morton_keys<KeyT><<<blocks_for(n, RS_THREADS), RS_THREADS, 0, s>>>(G, n, x, y, z, k0, v0, keys_out, unsorted);
+    note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int passes = (key_bits + 7) / 8;
     const size_t smem = RS_TILE * (sizeof(KeyT) + sizeof(uint32_t));
     e = cudaFuncSetAttribute(k_rs_scatter<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -264,17 +290,26 @@ cudaError_t sort_impl(const GridF& G, int64_t n, int key_bits, const float* x, c
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         uint32_t* vout = (p == passes - 1) ? (uint32_t*)order_out : V[1 - cur];
-        k_rs_hist<KeyT><<<(unsigned)nb, RS_THREADS, 0, s>>>(K[cur], n, shift, hist, nb);
+        k_rs_hist<KeyT><<<(unsigned)nb, RS_THREADS, 0, s>>>(K[cur], n, shift, hist, nb, unsorted);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = exclusive_scan_u32(hist, hist, 256 * nb, nullptr, scan_scratch, s)) != cudaSuccess) return e;
-        k_rs_scatter<KeyT><<<(unsigned)nb, RS_THREADS, smem, s>>>(K[cur], V[cur], K[1 - cur], vout, n, shift, hist, nb);
+        if ((e = exclusive_scan_u32(hist, hist, 256 * nb, nullptr, scan_scratch, s, unsorted)) != cudaSuccess)
+            return e;
+        k_rs_scatter<KeyT><<<(unsigned)nb, RS_THREADS, smem, s>>>(K[cur], V[cur], K[1 - cur], vout, n, shift, hist,
+                                                                  nb, unsorted);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         cur = 1 - cur;
     }
-    if (passes == 0)
-        return cudaMemcpyAsync(order_out, V[0], n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    if (passes == 0) {
+        if ((e = cudaMemcpyAsync(order_out, V[0], n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return e;
+    } else if (identity_out) {
+        k_identity_if_sorted<<<blocks_for(n, RS_THREADS), RS_THREADS, 0, s>>>(unsorted, order_out, n);
+        note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (unsorted_out) *unsorted_out = unsorted;
     return cudaSuccess;
 }
 
@@ -297,18 +332,20 @@ size_t sort_scratch_bytes(int64_t n, int key_bits) {
 }
 
 cudaError_t morton_sort(const GridF& G, int64_t n, const float* x, const float* y, const float* z, uint64_t* keys_out,
-                        int32_t* order_out, void* scratch, cudaStream_t s) {
+                        int32_t* order_out, void* scratch, cudaStream_t s, bool identity_out,
+                        const int** unsorted_out) {
     if (n <= 0) return cudaSuccess;
     const int bits = morton_bits(G);
-    if (bits <= 32) return sort_impl<uint32_t>(G, n, bits, x, y, z, keys_out, order_out, scratch, s);
-    return sort_impl<uint64_t>(G, n, bits, x, y, z, keys_out, order_out, scratch, s);
+    if (bits <= 32)
+        return sort_impl<uint32_t>(G, n, bits, x, y, z, keys_out, order_out, scratch, s, identity_out, unsorted_out);
+    return sort_impl<uint64_t>(G, n, bits, x, y, z, keys_out, order_out, scratch, s, identity_out, unsorted_out);
 }
 
 cudaError_t launch_probe(const GridF& G, const int32_t* cell_pkg, const int32_t* nbr, const ProbeFields& F,
                          int64_t n, const float* x, const float* y, const float* z, const int32_t* order,
-                         const ProbeOut& out, cudaStream_t s) {
+                         const int* unsorted, const ProbeOut& out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_probe<<<blocks_for(n, PR_THREADS), PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, out);
+    k_probe<<<blocks_for(n, PR_THREADS), PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, unsorted, out);
     note_launch();
     return cudaGetLastError();
 }

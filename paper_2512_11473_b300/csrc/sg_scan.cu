@@ -45,7 +45,8 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n,
-                                                               uint32_t* __restrict__ partial) {
+                                                               uint32_t* __restrict__ partial, const int* go) {
+    if (go && *go == 0) return;
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     uint32_t s = 0;
 #pragma unroll
@@ -63,7 +64,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __
 }
 
 __global__ void __launch_bounds__(SPINE_THREADS) k_scan_spine(uint32_t* __restrict__ partial, int64_t nb,
-                                                               uint32_t* __restrict__ total) {
+                                                               uint32_t* __restrict__ total, const int* go) {
+    if (go && *go == 0) return;
     __shared__ uint32_t carry_s;
     if (threadIdx.x == 0) carry_s = 0;
     __syncthreads();
@@ -82,7 +84,8 @@ __global__ void __launch_bounds__(SPINE_THREADS) k_scan_spine(uint32_t* __restri
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* in, uint32_t* out, int64_t n,
-                                                             const uint32_t* __restrict__ partial) {
+                                                             const uint32_t* __restrict__ partial, const int* go) {
+    if (go && *go == 0) return;
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     uint32_t v[SCAN_ITEMS];
     uint32_t s = 0;
@@ -108,18 +111,18 @@ size_t scan_scratch_bytes(int64_t n) {
 }
 
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, void* scratch,
-                               cudaStream_t s) {
+                               cudaStream_t s, const int* go) {
     if (n <= 0) {
         if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
         return cudaSuccess;
     }
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     uint32_t* partial = (uint32_t*)scratch;
-    k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, partial);
+    k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, partial, go);
     note_launch();
-    k_scan_spine<<<1, SPINE_THREADS, 0, s>>>(partial, nb, total);
+    k_scan_spine<<<1, SPINE_THREADS, 0, s>>>(partial, nb, total, go);
     note_launch();
-    k_scan_down<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, partial);
+    k_scan_down<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, partial, go);
     note_launch();
     return cudaGetLastError();
 }

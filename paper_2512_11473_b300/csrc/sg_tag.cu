@@ -18,17 +18,36 @@ __device__ __forceinline__ void cell_coords(int64_t c, const int* dims, int64_t&
     K = c / ((int64_t)dims[0] * dims[1]);
 }
 
-// Step 1: core cells, |d(centre)| < T; far cells keep the sign of d.
+// Step 1: core cells, |d(centre)| < T; far cells keep the sign of d.  The
+// distance is first evaluated in float; when it is farther than `margin`
+// from both T and 0 in magnitude, the float decision stands (the float error
+// of these formulas is below 1e-6 (1 + |x|), the margin is 1.5e-4 (1 + |x|)),
+// otherwise it is decided on the float-float distance.
 __global__ void __launch_bounds__(TAG_THREADS) k_tag_flags(GridFF G, ShapeFF S, uint8_t* __restrict__ cell_type,
                                                             uint32_t* __restrict__ active, int64_t nc) {
+    const float Tf = G.T.hi;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         int64_t I[3];
         cell_coords(c, G.dims, I[0], I[1], I[2]);
-        ff x[3];
+        float xf[3];
+        float xmax = 0.0f;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) x[a] = ff_add(G.lo[a], ff_mul_f(G.h, (float)(4 * I[a] + 2)));
-        ff d = ff_sdf(S, x);
-        uint8_t t = ff_lt(ff_abs(d), G.T) ? 2 : (ff_neg_p(d) ? 0 : 1);
+        for (int a = 0; a < 3; ++a) {
+            xf[a] = G.lo[a].hi + G.h.hi * (float)(4 * I[a] + 2);
+            xmax = fmaxf(xmax, fabsf(xf[a]));
+        }
+        const float df = f_sdf(S, xf);
+        const float margin = 1.5e-4f * (1.0f + xmax);
+        uint8_t t;
+        if (fabsf(fabsf(df) - Tf) > margin && fabsf(df) > margin) {
+            t = fabsf(df) < Tf ? 2 : (df < 0.0f ? 0 : 1);
+        } else {
+            ff x[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) x[a] = ff_add(G.lo[a], ff_mul_f(G.h, (float)(4 * I[a] + 2)));
+            const ff d = ff_sdf(S, x);
+            t = ff_lt(ff_abs(d), G.T) ? 2 : (ff_neg_p(d) ? 0 : 1);
+        }
         cell_type[c] = t;
         active[c] = t == 2;
     }

@@ -409,3 +409,40 @@ def test_allocator_hook_and_default_pool(sg):
     assert torch.equal(a.field("gx"), b.field("gx"))
     a.close()
     b.close()
+
+
+def test_morton_sorted_input_fast_path(sg):
+    """Keys already in order: identity order, same keys; one swapped pair
+    forces the full sort; probe results do not depend on the path."""
+    shape, spec = CASES["torus_anisotropic"]
+    g = sg.Grid(spec)
+    g.tag_allocate(shape)
+    g.init_sdf(shape)
+    g.gradient()
+    g.kernel_integrals()
+    x, y, z = si.box_particles(100_000, spec.lo, spec.hi(), seed=77)
+    rk = oracle.morton_keys(spec, x, y, z)
+    ro = oracle.morton_order(rk)
+    xs, ys, zs = x[ro], y[ro], z[ro]
+    D = [torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (xs, ys, zs)]
+    keys, order = g.morton_order(*D)
+    assert np.array_equal(H(order), np.arange(len(xs)))
+    assert np.array_equal(H(keys).view(np.uint64), rk[ro])
+    a = g.probe(*D, morton=True)
+    b = g.probe(*D, morton=False)
+    for k in a:
+        assert torch.equal(a[k], b[k])
+    # swap two particles with different keys: no longer sorted
+    i, j = 10, 50_000
+    assert rk[ro[i]] != rk[ro[j]]
+    xs2, ys2, zs2 = xs.copy(), ys.copy(), zs.copy()
+    for v in (xs2, ys2, zs2):
+        v[i], v[j] = v[j], v[i]
+    D2 = [torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (xs2, ys2, zs2)]
+    keys2, order2 = g.morton_order(*D2)
+    rk2 = oracle.morton_keys(spec, xs2, ys2, zs2)
+    assert np.array_equal(H(order2).astype(np.int64), oracle.morton_order(rk2))
+    c = g.probe(*D2, morton=True)
+    d = g.probe(*D2, morton=False)
+    for k in c:
+        assert torch.equal(c[k], d[k])
