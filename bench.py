@@ -78,14 +78,19 @@ def measured_peaks():
     return HBM_FALLBACK_GBS, "fallback"
 
 
-def source_digest(path):
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def source_digest(*paths):
+    h = hashlib.sha256()
+    for path in paths:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
-def profile_traffic(kernel_file, summary):
+def profile_traffic(kernel_files, summary):
     """DRAM traffic per launch from a committed ncu summary, or None when the
     kernel source changed since the counters were taken."""
+    if isinstance(kernel_files, str):
+        kernel_files = [kernel_files]
     p = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(p):
         return None
@@ -95,7 +100,7 @@ def profile_traffic(kernel_file, summary):
                                                     "units_per_launch")):
             k, v = line.split(":", 1)
             fields[k.strip()] = v.strip().strip("`")
-    if fields.get("kernel_source_sha256_16") != source_digest(kernel_file):
+    if fields.get("kernel_source_sha256_16") != source_digest(*kernel_files):
         return None
     try:
         return float(fields["traffic_bytes_per_launch"]), float(fields.get("units_per_launch", "nan"))
@@ -484,10 +489,13 @@ def run_sg(args):
         setup_ms[b.name] = e0.elapsed_time(e1) / reps
     sweep_ms = {b.name: (breakdown[b.name + ":reinit"] - setup_ms[b.name]) / args.iters for b in bodies}
     big = max(bodies, key=lambda b: b.P)
-    alg_bytes = 12.0 * big.n_pt + 108.0 * (big.P - 2)
+    # read phi and S0, write phi (12 B per point) and the 32-byte face row
+    # of every package
+    alg_bytes = 12.0 * big.n_pt + 32.0 * (big.P - 2)
     hbm, peak_kind = measured_peaks()
     achieved = alg_bytes / (sweep_ms[big.name] * 1e-3) / 1e9
-    prof = profile_traffic(os.path.join(ROOT, "paper_2512_11473_b300", "csrc", "sg_sweep.cu"),
+    csrc = os.path.join(ROOT, "paper_2512_11473_b300", "csrc")
+    prof = profile_traffic([os.path.join(csrc, "sg_sweep.cu"), os.path.join(csrc, "sg_rows.cuh")],
                            "reinit_step_torus_h0.002.md")
     traffic = None
     if prof is not None:

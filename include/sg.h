@@ -178,7 +178,7 @@ SG_API sg_status sg_kernel_integrals(sg_grid *g, int32_t mode, const void *mlp);
  * grad phi, W and G^ at n particles.  x, y, z are device arrays of n floats;
  * the eight outputs are device arrays of n floats in input order (any may
  * be NULL to skip it).  The lattice coordinate is taken in float32:
- * u = (x - lo)/h - 0.5 clamped to +-2^24, i0 = floor(u), t = u - i0, home
+ * u = (x - lo) * (1/h) - 0.5 with 1/h rounded to float once, clamped to +-2^24, i0 = floor(u), t = u - i0, home
  * cell floor(i0/4) (the outside far package when outside the domain),
  * corners reached through the home package's neighbourhood.  The normal is
  * grad/|grad| (0 where |grad| = 0).  Fields not yet computed read as 0.

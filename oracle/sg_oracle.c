@@ -475,15 +475,15 @@ void or_kernel_integrals(const or_grid *g, int64_t P, const int32_t *nbr, const 
 /* ------------------------------------------------------------------------- */
 /* Particle probe ("Grid-Particle Coupling"): trilinear interpolation.        */
 /* The fine lattice coordinate is decided in float32 exactly as the device    */
-/* does it:  u = (x - (float)lo) / (float)h - 0.5f, clamped to +-2^24,        */
+/* does it:  u = (x - (float)lo) * (float)(1/h) - 0.5f, clamped to +-2^24,    */
 /* i0 = floor(u).  Home cell I = floor(i0 / 4), local l0 = i0 - 4I.  Corners  */
 /* l0 + {0,1} are reached from the home package by the index shift; a home    */
 /* cell outside the domain is the outside far package.  Weights t = u - i0.   */
 /* Outputs (in input order): phi, normal n = g/|g| (0 when |g| = 0), W, G^.   */
 /* ------------------------------------------------------------------------- */
 static void lattice(const or_grid *g, int a, float x, int64_t *i0, double *t) {
-    float lo = (float)g->lo[a], h = (float)g->h;
-    float u = (x - lo) / h - 0.5f;
+    float lo = (float)g->lo[a], inv_h = (float)(1.0 / g->h);
+    float u = (x - lo) * inv_h - 0.5f;
     const float lim = 16777216.0f;
     if (u < -lim) u = -lim;
     if (u > lim) u = lim;

@@ -85,6 +85,7 @@ GridF grid_f(const sg_grid* g) {
     G.h = (float)g->desc.h;
     G.h_d = g->desc.h;
     G.F = (float)g->F;
+    G.inv_h = (float)(1.0 / g->desc.h);
     return G;
 }
 
@@ -200,7 +201,7 @@ sg_status sg_create(const sg_grid_desc* desc, const sg_allocator* alloc, void* s
 sg_status sg_destroy(sg_grid* g) {
     SG_CHECK_GRID(g);
     DeviceGuard dg(g->device);
-    Buf* bufs[] = {&g->cell_pkg, &g->cell_type, &g->pkg_cell, &g->pkg_type, &g->nbr,
+    Buf* bufs[] = {&g->cell_pkg, &g->cell_type, &g->pkg_cell, &g->pkg_type, &g->nbr, &g->faces,
                    &g->phi_tmp,  &g->err,       &g->scratch,  &g->stats};
     for (Buf* b : bufs) grid_free(g, *b);
     for (int f = 0; f < SG_N_FLOAT_FIELDS; ++f) grid_free(g, g->field[f]);
@@ -245,7 +246,7 @@ sg_status sg_tag_allocate(sg_grid* g, const sg_shape* shape, int64_t* n_packages
     for (int f = 0; f < SG_N_FLOAT_FIELDS; ++f) grid_free(g, g->field[f]);
     grid_free(g, g->phi_tmp);
     if (!ensure(g, g->pkg_cell, (size_t)P * 4) || !ensure(g, g->pkg_type, (size_t)P) ||
-        !ensure(g, g->nbr, (size_t)P * NB * 4)) {
+        !ensure(g, g->nbr, (size_t)P * NB * 4) || !ensure(g, g->faces, (size_t)P * 8 * 4)) {
         g->state = 0;
         return fail(g, SG_ERR_OOM, "sg_tag_allocate: out of device memory");
     }
@@ -256,6 +257,7 @@ sg_status sg_tag_allocate(sg_grid* g, const sg_shape* shape, int64_t* n_packages
     SG_CUDA(g, launch_fill_nbr(G, (const int32_t*)g->cell_pkg.p, (const int32_t*)g->pkg_cell.p, (int32_t*)g->nbr.p, P,
                                g->stream),
             "fill nbr");
+    SG_CUDA(g, launch_fill_faces((const int32_t*)g->nbr.p, (int32_t*)g->faces.p, P, g->stream), "fill faces");
     g->state = 1;
     if (n_packages) *n_packages = P;
     return SG_OK;
@@ -283,7 +285,7 @@ sg_status sg_gradient(sg_grid* g) {
     for (int a = 0; a < 3; ++a)
         if (!(o[a] = field_ptr(g, SG_FIELD_GX + a, false))) return fail(g, SG_ERR_OOM, "sg_gradient: out of memory");
     for (int a = 0; a < 3; ++a) SG_CUDA(g, launch_set_far(o[a], 0.0f, 0.0f, g->stream), "gradient far");
-    SG_CUDA(g, launch_gradient(grid_f(g), (const int32_t*)g->nbr.p, (const float*)g->field[SG_FIELD_PHI].p, o[0], o[1],
+    SG_CUDA(g, launch_gradient(grid_f(g), (const int32_t*)g->faces.p, (const float*)g->field[SG_FIELD_PHI].p, o[0], o[1],
                                o[2], g->P, g->stream),
             "gradient");
     return SG_OK;
@@ -296,7 +298,7 @@ sg_status sg_laplacian(sg_grid* g) {
     float* lap = field_ptr(g, SG_FIELD_LAP, false);
     if (!lap) return fail(g, SG_ERR_OOM, "sg_laplacian: out of memory");
     SG_CUDA(g, launch_set_far(lap, 0.0f, 0.0f, g->stream), "laplacian far");
-    SG_CUDA(g, launch_laplacian(grid_f(g), (const int32_t*)g->nbr.p, (const float*)g->field[SG_FIELD_PHI].p, lap, g->P,
+    SG_CUDA(g, launch_laplacian(grid_f(g), (const int32_t*)g->faces.p, (const float*)g->field[SG_FIELD_PHI].p, lap, g->P,
                                 g->stream),
             "laplacian");
     return SG_OK;
@@ -313,14 +315,14 @@ sg_status sg_reinit(sg_grid* g, int32_t iterations, float cfl) {
     float* tmp = (float*)g->phi_tmp.p;
     const GridF G = grid_f(g);
     const float dt = (float)((double)cfl * g->desc.h);
-    const int32_t* nbr = (const int32_t*)g->nbr.p;
+    const int32_t* faces = (const int32_t*)g->faces.p;
     SG_CUDA(g, launch_set_far(s0, -1.0f, 1.0f, g->stream), "reinit far");
     SG_CUDA(g, launch_set_far(tmp, -(float)g->F, (float)g->F, g->stream), "reinit far");
     SG_CUDA(g, launch_reinit_s0(G, phi, s0, g->P, g->stream), "reinit s0");
     float* a = phi;
     float* b = tmp;
     for (int32_t it = 0; it < iterations; ++it) {
-        SG_CUDA(g, launch_reinit_step(G, nbr, s0, a, b, dt, g->P, g->stream), "reinit step");
+        SG_CUDA(g, launch_reinit_step(G, faces, s0, a, b, dt, g->P, g->stream), "reinit step");
         float* t = a;
         a = b;
         b = t;

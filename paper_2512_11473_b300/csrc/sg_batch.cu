@@ -34,7 +34,7 @@ struct sg_batch {
     cudaStream_t stream = nullptr;   // caller's stream: graphs run here
     cudaStream_t capture = nullptr;  // private stream used only to capture
     int device = 0;
-    sg::Buf phi, tmp, s0, phi0, f[8], nbr, type, body, params, counters;
+    sg::Buf phi, tmp, s0, phi0, f[8], nbr, faces, type, body, params, counters;
     size_t n_counters = 0;
     float params_cfl = -1.0f;
     std::vector<sg_batch_graph> graphs;
@@ -69,7 +69,7 @@ __device__ __forceinline__ int64_t next_item(unsigned* counter, int* s_item) {
 // Gradient over the global store.  A work item is 16 * ppi consecutive
 // packages; each half-warp handles ppi of them, DEPTH at a time.
 template <int DEPTH>
-__global__ void __launch_bounds__(BT) k_batch_gradient(const int32_t* __restrict__ nbr, const uint8_t* __restrict__ type,
+__global__ void __launch_bounds__(BT) k_batch_gradient(const int32_t* __restrict__ faces, const uint8_t* __restrict__ type,
                                                        const int32_t* __restrict__ body,
                                                        const BodyParams* __restrict__ prm, const float* __restrict__ phi,
                                                        float* __restrict__ gx, float* __restrict__ gy,
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(BT) k_batch_gradient(const int32_t* __restrict
                 sl[d] = make_slot(p, p < P && k + d < ppi && __ldg(type + (p < P ? p : 0)) >= 2);
             }
 #pragma unroll
-            for (int d = 0; d < DEPTH; ++d) w[d] = load_rows(phi, nbr, sl[d]);
+            for (int d = 0; d < DEPTH; ++d) w[d] = load_rows(phi, faces, sl[d]);
 #pragma unroll
             for (int d = 0; d < DEPTH; ++d) {
                 if (!sl[d].valid) continue;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(BT) k_batch_gradient(const int32_t* __restrict
 }
 
 template <int DEPTH>
-__global__ void __launch_bounds__(BT) k_batch_reinit(const int32_t* __restrict__ nbr, const uint8_t* __restrict__ type,
+__global__ void __launch_bounds__(BT) k_batch_reinit(const int32_t* __restrict__ faces, const uint8_t* __restrict__ type,
                                                      const int32_t* __restrict__ body,
                                                      const BodyParams* __restrict__ prm, const float* __restrict__ s0,
                                                      const float* __restrict__ phi_in, float* __restrict__ phi_out,
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(BT) k_batch_reinit(const int32_t* __restrict__
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
-            for (int d = 0; d < DEPTH; ++d) w[d] = load_rows(phi_in, nbr, sl[d]);
+            for (int d = 0; d < DEPTH; ++d) w[d] = load_rows(phi_in, faces, sl[d]);
 #pragma unroll
             for (int d = 0; d < DEPTH; ++d) {
                 if (!sl[d].valid) continue;
@@ -304,6 +304,7 @@ cudaError_t upload_params(sg_batch* b, float cfl) {
 cudaError_t record_run(sg_batch* b, const sg_batch_plan& plan, cudaStream_t s) {
     const int ppi = plan.pkgs_per_item, iters = plan.reinit_iterations;
     const int32_t* nbr = (const int32_t*)b->nbr.p;
+    const int32_t* faces = (const int32_t*)b->faces.p;
     const uint8_t* type = (const uint8_t*)b->type.p;
     const int32_t* body = (const int32_t*)b->body.p;
     const BodyParams* prm = (const BodyParams*)b->params.p;
@@ -319,10 +320,10 @@ cudaError_t record_run(sg_batch* b, const sg_batch_plan& plan, cudaStream_t s) {
     const KernelCoef K = kernel_coef();
     if (plan.depth == 2) {
         const int nb = persistent_blocks((const void*)k_batch_gradient<2>, b->device);
-        k_batch_gradient<2><<<nb, BT, 0, s>>>(nbr, type, body, prm, phi, fo[1], fo[2], fo[3], b->P, ppi, ctr + c++);
+        k_batch_gradient<2><<<nb, BT, 0, s>>>(faces, type, body, prm, phi, fo[1], fo[2], fo[3], b->P, ppi, ctr + c++);
     } else {
         const int nb = persistent_blocks((const void*)k_batch_gradient<1>, b->device);
-        k_batch_gradient<1><<<nb, BT, 0, s>>>(nbr, type, body, prm, phi, fo[1], fo[2], fo[3], b->P, ppi, ctr + c++);
+        k_batch_gradient<1><<<nb, BT, 0, s>>>(faces, type, body, prm, phi, fo[1], fo[2], fo[3], b->P, ppi, ctr + c++);
     }
     note_launch();
     k_batch_s0<<<flat_grid(b->P * 16), BT, 0, s>>>(type, body, prm, phi, s0, b->P);
@@ -333,9 +334,9 @@ cudaError_t record_run(sg_batch* b, const sg_batch_plan& plan, cudaStream_t s) {
     const int nbr1 = persistent_blocks((const void*)k_batch_reinit<1>, b->device);
     for (int it = 0; it < iters; ++it) {
         if (plan.depth == 2)
-            k_batch_reinit<2><<<nbr2, BT, 0, s>>>(nbr, type, body, prm, s0, a, o, b->P, ppi, ctr + c++);
+            k_batch_reinit<2><<<nbr2, BT, 0, s>>>(faces, type, body, prm, s0, a, o, b->P, ppi, ctr + c++);
         else
-            k_batch_reinit<1><<<nbr1, BT, 0, s>>>(nbr, type, body, prm, s0, a, o, b->P, ppi, ctr + c++);
+            k_batch_reinit<1><<<nbr1, BT, 0, s>>>(faces, type, body, prm, s0, a, o, b->P, ppi, ctr + c++);
         note_launch();
         float* t = a;
         a = o;
@@ -385,7 +386,8 @@ sg_status sg_batch_create(sg_grid* const* grids, int32_t n, void* stream, sg_bat
     sg_status st = SG_OK;
     const size_t fb = (size_t)P * PKG3 * sizeof(float);
     bool ok = b_ensure(b, b->phi, fb) && b_ensure(b, b->tmp, fb) && b_ensure(b, b->s0, fb) && b_ensure(b, b->phi0, fb) &&
-              b_ensure(b, b->nbr, (size_t)P * NB * 4) && b_ensure(b, b->type, (size_t)P) &&
+              b_ensure(b, b->nbr, (size_t)P * NB * 4) && b_ensure(b, b->faces, (size_t)P * 8 * 4) &&
+              b_ensure(b, b->type, (size_t)P) &&
               b_ensure(b, b->body, (size_t)P * 4) && b_ensure(b, b->params, (size_t)n * sizeof(BodyParams)) &&
               b_ensure(b, b->counters, 4096);
     for (int i = 1; ok && i < 8; ++i) ok = b_ensure(b, b->f[i], fb);
@@ -417,6 +419,7 @@ sg_status sg_batch_create(sg_grid* const* grids, int32_t n, void* stream, sg_bat
             }
             off += g->P;
         }
+        if (e == cudaSuccess) e = launch_fill_faces((const int32_t*)b->nbr.p, (int32_t*)b->faces.p, P, b->stream);
         for (int i = 1; i < 8 && e == cudaSuccess; ++i) e = cudaMemsetAsync(b->f[i].p, 0, fb, b->stream);
         if (e == cudaSuccess) {
             Buf tmpbase;
@@ -460,7 +463,7 @@ sg_status sg_batch_create(sg_grid* const* grids, int32_t n, void* stream, sg_bat
 sg_status sg_batch_destroy(sg_batch* b) {
     if (!b) return SG_ERR_INVALID;
     for (auto& gr : b->graphs) cudaGraphExecDestroy(gr.exec);
-    Buf* bufs[] = {&b->phi, &b->tmp, &b->s0, &b->phi0, &b->nbr, &b->type, &b->body, &b->params, &b->counters};
+    Buf* bufs[] = {&b->phi, &b->tmp, &b->s0, &b->phi0, &b->nbr, &b->faces, &b->type, &b->body, &b->params, &b->counters};
     for (Buf* x : bufs) b_free(b, *x);
     for (int i = 1; i < 8; ++i) b_free(b, b->f[i]);
     if (b->capture) cudaStreamDestroy(b->capture);

@@ -30,7 +30,8 @@ struct GridF {
     float h;
     int dims[3];
     float F;
-    double h_d;  // h in double, for host-side constants
+    double h_d;   // h in double, for host-side constants
+    float inv_h;  // 1/h rounded to float once (the probe's lattice coordinate)
 };
 
 // Scalars of the tagging/init kernels, in float-float.
@@ -55,6 +56,7 @@ struct sg_grid {
     int device = 0;
 
     sg::Buf cell_pkg, cell_type, pkg_cell, pkg_type, nbr;
+    sg::Buf faces;  // int32 [P][8]: the six face neighbours (-x,+x,-y,+y,-z,+z), then 2 zeros
     sg::Buf field[SG_N_FLOAT_FIELDS];
     sg::Buf phi_tmp;
     sg::Buf err;       // int32 sticky device error word
@@ -95,17 +97,19 @@ cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* prefix,
                                int32_t* pkg_cell, uint8_t* pkg_type, int64_t nc, cudaStream_t s);
 cudaError_t launch_fill_nbr(const GridFF& G, const int32_t* cell_pkg, const int32_t* pkg_cell, int32_t* nbr,
                             int64_t P, cudaStream_t s);
+// faces[p][8] = the six face entries of nbr[p][27] (one 32-byte row per package)
+cudaError_t launch_fill_faces(const int32_t* nbr, int32_t* faces, int64_t P, cudaStream_t s);
 cudaError_t launch_init_sdf(const GridFF& G, const ShapeFF& S, const int32_t* pkg_cell, float* phi, float F,
                             int64_t P, cudaStream_t s);
 
 // sweeps (sg_sweep.cu)
 cudaError_t launch_set_far(float* f, float v_in, float v_out, cudaStream_t s);
-cudaError_t launch_gradient(const GridF& G, const int32_t* nbr, const float* phi, float* gx, float* gy, float* gz,
+cudaError_t launch_gradient(const GridF& G, const int32_t* faces, const float* phi, float* gx, float* gy, float* gz,
                             int64_t P, cudaStream_t s);
-cudaError_t launch_laplacian(const GridF& G, const int32_t* nbr, const float* phi, float* lap, int64_t P,
+cudaError_t launch_laplacian(const GridF& G, const int32_t* faces, const float* phi, float* lap, int64_t P,
                              cudaStream_t s);
 cudaError_t launch_reinit_s0(const GridF& G, const float* phi, float* s0, int64_t P, cudaStream_t s);
-cudaError_t launch_reinit_step(const GridF& G, const int32_t* nbr, const float* s0, const float* phi_in,
+cudaError_t launch_reinit_step(const GridF& G, const int32_t* faces, const float* s0, const float* phi_in,
                                float* phi_out, float dt, int64_t P, cudaStream_t s);
 cudaError_t launch_copy_active(const float* src, float* dst, int64_t P, cudaStream_t s);
 cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const float* phi, float* W, float* gx,

@@ -18,10 +18,11 @@ constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096 keys per tile
 constexpr int RS_WARPS = RS_THREADS / 32;
 
-// Fine lattice coordinate in float32: u = (x - lo)/h - 1/2 clamped to
-// +-2^24, i0 = floor(u), t = u - i0 (exact).
-__device__ __forceinline__ void lattice(float x, float lo, float h, int& i0, float& t) {
-    float u = __fsub_rn(__fdiv_rn(__fsub_rn(x, lo), h), 0.5f);
+// Fine lattice coordinate in float32: u = (x - lo) * inv_h - 1/2 with
+// inv_h = 1/h rounded to float once, clamped to +-2^24, i0 = floor(u),
+// t = u - i0 (exact).
+__device__ __forceinline__ void lattice(float x, float lo, float inv_h, int& i0, float& t) {
+    float u = __fsub_rn(__fmul_rn(__fsub_rn(x, lo), inv_h), 0.5f);
     u = fminf(fmaxf(u, -16777216.0f), 16777216.0f);
     float f = floorf(u);
     i0 = (int)f;
@@ -45,7 +46,7 @@ __device__ __forceinline__ uint64_t morton_key(const GridF& G, float x, float y,
     for (int a = 0; a < 3; ++a) {
         int i0;
         float t;
-        lattice(pos[a], G.lo[a], G.h, i0, t);
+        lattice(pos[a], G.lo[a], G.inv_h, i0, t);
         int k = i0 + 1;
         k = k < 0 ? 0 : (k > 4 * G.dims[a] + 1 ? 4 * G.dims[a] + 1 : k);
         key |= spread3((uint64_t)k) << a;
@@ -63,18 +64,22 @@ __global__ void __launch_bounds__(RS_THREADS) k_morton_keys(GridF G, int64_t n, 
                                                             uint64_t* __restrict__ keys_out, int* unsorted) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t iters = (n + stride - 1) / stride;
+    const int lane = threadIdx.x & 31;
     for (int64_t it = 0; it < iters; ++it) {  // uniform trip count: every lane takes part in the vote
         const int64_t q = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-        bool bad = false;
+        uint64_t k = 0;
         if (q < n) {
-            const uint64_t k = morton_key(G, x[q], y[q], z[q]);
+            k = morton_key(G, x[q], y[q], z[q]);
             keys[q] = (KeyT)k;
             vals[q] = (uint32_t)q;
             if (keys_out) keys_out[q] = k;
-            if (q + 1 < n) bad = k > morton_key(G, x[q + 1], y[q + 1], z[q + 1]);
         }
+        // the successor's key: from the next lane, or computed by the last lane
+        uint64_t next = __shfl_down_sync(0xffffffffu, k, 1);
+        if (lane == 31 && q + 1 < n) next = morton_key(G, x[q + 1], y[q + 1], z[q + 1]);
+        const bool bad = q + 1 < n && k > next;
         const unsigned m = __ballot_sync(0xffffffffu, bad);
-        if (m && (threadIdx.x & 31) == __ffs(m) - 1 && *(volatile int*)unsorted == 0) atomicOr(unsorted, 1);
+        if (m && lane == __ffs(m) - 1 && *(volatile int*)unsorted == 0) atomicOr(unsorted, 1);
     }
 }
 
@@ -216,7 +221,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe(GridF G, const int32_t* __
         int64_t c = 0, stride = 1;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            lattice(pos[a], G.lo[a], G.h, i0[a], t[a]);
+            lattice(pos[a], G.lo[a], G.inv_h, i0[a], t[a]);
             int I = i0[a] >> 2;  // floor division by 4
             l[a] = i0[a] & 3;
             inside &= I >= 0 && I < G.dims[a];
@@ -399,6 +404,7 @@ extern "C" sg_status sg_morton_order_noalloc(const sg_grid_desc* desc, int64_t n
     G.h = (float)desc->h;
     G.h_d = desc->h;
     G.F = 0.0f;
+    G.inv_h = (float)(1.0 / desc->h);
     if (sort_scratch_bytes(n, morton_bits(G)) > sizeof(g_noalloc_scratch)) return SG_ERR_CAPACITY;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {

@@ -32,9 +32,6 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// neighbourhood entries of the six faces: -x, +x, -y, +y, -z, +z
-__constant__ int c_face_n[6] = {12, 14, 10, 16, 4, 22};
-
 // Listing 2: shift s per axis in [-4, 7] -> (package, data index)
 __device__ __forceinline__ int64_t shift_index(const int* nb27, int sx, int sy, int sz) {
     int nx = (sx + PKG) >> 2, ny = (sy + PKG) >> 2, nz = (sz + PKG) >> 2;
@@ -96,15 +93,17 @@ __device__ __forceinline__ RowSlot make_slot(int64_t p, bool valid) {
     return s;
 }
 
-// Gather a lane's row and neighbours of field f.  All lanes of the warp must
-// call this (shuffles); lanes of an invalid package get zeros.
-__device__ __forceinline__ Rows load_rows(const float* __restrict__ f, const int32_t* __restrict__ nbr,
+// Gather a lane's row and neighbours of field f.  faces[p][8] holds the six
+// face neighbours of package p (-x, +x, -y, +y, -z, +z), one 32-byte row.
+// All lanes of the warp must call this (shuffles); lanes of an invalid
+// package get zeros.
+__device__ __forceinline__ Rows load_rows(const float* __restrict__ f, const int32_t* __restrict__ faces,
                                           const RowSlot& s) {
     const int lane = threadIdx.x & 31, base = lane & 16;
     const int j = s.r & 3, k = s.r >> 2;
     const float4* __restrict__ f4 = reinterpret_cast<const float4*>(f);
     int nid = 0;
-    if (s.valid && s.r < 6) nid = __ldg(nbr + s.p * NB + c_face_n[s.r]);
+    if (s.valid && s.r < 6) nid = __ldg(faces + s.p * 8 + s.r);
     Rows w;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     w.c = s.valid ? __ldg(f4 + s.q4) : zero;

@@ -21,11 +21,11 @@ __global__ void __launch_bounds__(SW_THREADS) k_set_far(float* f, float v_in, fl
     f[threadIdx.x] = threadIdx.x < PKG3 ? v_in : v_out;
 }
 
-__global__ void __launch_bounds__(ROW_THREADS) k_gradient(const int32_t* __restrict__ nbr, const float* __restrict__ phi,
+__global__ void __launch_bounds__(ROW_THREADS) k_gradient(const int32_t* __restrict__ faces, const float* __restrict__ phi,
                                                            float* __restrict__ gx, float* __restrict__ gy,
                                                            float* __restrict__ gz, int64_t P, float inv2h) {
     const RowSlot s = row_slot(P);
-    const Rows w = load_rows(phi, nbr, s);
+    const Rows w = load_rows(phi, faces, s);
     if (!s.valid) return;
     float4 ox, oy, oz;
     gradient_row(w, inv2h, ox, oy, oz);
@@ -34,11 +34,11 @@ __global__ void __launch_bounds__(ROW_THREADS) k_gradient(const int32_t* __restr
     reinterpret_cast<float4*>(gz)[s.q4] = oz;
 }
 
-__global__ void __launch_bounds__(ROW_THREADS) k_laplacian(const int32_t* __restrict__ nbr,
+__global__ void __launch_bounds__(ROW_THREADS) k_laplacian(const int32_t* __restrict__ faces,
                                                             const float* __restrict__ phi, float* __restrict__ lap,
                                                             int64_t P, float inv_h2) {
     const RowSlot s = row_slot(P);
-    const Rows w = load_rows(phi, nbr, s);
+    const Rows w = load_rows(phi, faces, s);
     if (!s.valid) return;
     reinterpret_cast<float4*>(lap)[s.q4] = laplacian_row(w, inv_h2);
 }
@@ -49,14 +49,14 @@ __global__ void __launch_bounds__(SW_THREADS) k_reinit_s0(const float* __restric
         s0[2 * PKG3 + e] = smoothed_sign(phi[2 * PKG3 + e], h2);
 }
 
-__global__ void __launch_bounds__(ROW_THREADS) k_reinit_step(const int32_t* __restrict__ nbr,
+__global__ void __launch_bounds__(ROW_THREADS) k_reinit_step(const int32_t* __restrict__ faces,
                                                               const float* __restrict__ s0,
                                                               const float* __restrict__ phi_in,
                                                               float* __restrict__ phi_out, int64_t P, float cfl,
                                                               float dt) {
     const RowSlot s = row_slot(P);
     const float4 sg = s.valid ? __ldg(reinterpret_cast<const float4*>(s0) + s.q4) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const Rows w = load_rows(phi_in, nbr, s);
+    const Rows w = load_rows(phi_in, faces, s);
     if (!s.valid) return;
     reinterpret_cast<float4*>(phi_out)[s.q4] = reinit_row(w, sg, cfl, dt);
 }
@@ -139,18 +139,18 @@ cudaError_t launch_set_far(float* f, float v_in, float v_out, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_gradient(const GridF& G, const int32_t* nbr, const float* phi, float* gx, float* gy, float* gz,
+cudaError_t launch_gradient(const GridF& G, const int32_t* faces, const float* phi, float* gx, float* gy, float* gz,
                             int64_t P, cudaStream_t s) {
     if (P <= 2) return cudaSuccess;
-    k_gradient<<<row_blocks(P), ROW_THREADS, 0, s>>>(nbr, phi, gx, gy, gz, P, (float)(1.0 / (2.0 * G.h_d)));
+    k_gradient<<<row_blocks(P), ROW_THREADS, 0, s>>>(faces, phi, gx, gy, gz, P, (float)(1.0 / (2.0 * G.h_d)));
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_laplacian(const GridF& G, const int32_t* nbr, const float* phi, float* lap, int64_t P,
+cudaError_t launch_laplacian(const GridF& G, const int32_t* faces, const float* phi, float* lap, int64_t P,
                              cudaStream_t s) {
     if (P <= 2) return cudaSuccess;
-    k_laplacian<<<row_blocks(P), ROW_THREADS, 0, s>>>(nbr, phi, lap, P, (float)(1.0 / (G.h_d * G.h_d)));
+    k_laplacian<<<row_blocks(P), ROW_THREADS, 0, s>>>(faces, phi, lap, P, (float)(1.0 / (G.h_d * G.h_d)));
     note_launch();
     return cudaGetLastError();
 }
@@ -163,11 +163,11 @@ cudaError_t launch_reinit_s0(const GridF& G, const float* phi, float* s0, int64_
     return cudaGetLastError();
 }
 
-cudaError_t launch_reinit_step(const GridF& G, const int32_t* nbr, const float* s0, const float* phi_in,
+cudaError_t launch_reinit_step(const GridF& G, const int32_t* faces, const float* s0, const float* phi_in,
                                float* phi_out, float dt, int64_t P, cudaStream_t s) {
     if (P <= 2) return cudaSuccess;
     // dt sqrt(G) = (dt / h) sqrt(h^2 G) and dt / h is the CFL number
-    k_reinit_step<<<row_blocks(P), ROW_THREADS, 0, s>>>(nbr, s0, phi_in, phi_out, P, (float)(dt / G.h_d), dt);
+    k_reinit_step<<<row_blocks(P), ROW_THREADS, 0, s>>>(faces, s0, phi_in, phi_out, P, (float)(dt / G.h_d), dt);
     note_launch();
     return cudaGetLastError();
 }

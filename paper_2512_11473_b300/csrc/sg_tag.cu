@@ -121,6 +121,17 @@ __global__ void __launch_bounds__(TAG_THREADS) k_fill_nbr(GridFF G, const int32_
     }
 }
 
+// Compact face table: entries 12, 14, 10, 16, 4, 22 of each neighbourhood.
+__global__ void __launch_bounds__(TAG_THREADS) k_fill_faces(const int32_t* __restrict__ nbr,
+                                                             int32_t* __restrict__ faces, int64_t P) {
+    const int face_n[8] = {12, 14, 10, 16, 4, 22, -1, -1};
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P * 8;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int f = (int)(e & 7);
+        faces[e] = face_n[f] < 0 ? 0 : nbr[(e >> 3) * NB + face_n[f]];
+    }
+}
+
 // Step 4: phi at cell-centred data points, float-float, rounded once.
 __global__ void __launch_bounds__(TAG_THREADS) k_init_sdf(GridFF G, ShapeFF S, const int32_t* __restrict__ pkg_cell,
                                                            float* __restrict__ phi, int64_t P) {
@@ -172,6 +183,12 @@ cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* prefix,
 cudaError_t launch_fill_nbr(const GridFF& G, const int32_t* cell_pkg, const int32_t* pkg_cell, int32_t* nbr,
                             int64_t P, cudaStream_t s) {
     k_fill_nbr<<<grid_for(P * NB, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_pkg, pkg_cell, nbr, P);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_faces(const int32_t* nbr, int32_t* faces, int64_t P, cudaStream_t s) {
+    k_fill_faces<<<grid_for(P * 8, TAG_THREADS), TAG_THREADS, 0, s>>>(nbr, faces, P);
     note_launch();
     return cudaGetLastError();
 }

@@ -286,7 +286,7 @@ def test_dense_twin_probe(tiny):
     nx, ny, nz = spec.dims
     i0, t = [], []
     for a, v in enumerate((x, y, z)):
-        u = (v - np.float32(spec.lo[a])) / np.float32(h) - np.float32(0.5)
+        u = (v - np.float32(spec.lo[a])) * np.float32(1.0 / h) - np.float32(0.5)
         f = np.floor(u.astype(np.float32))
         i0.append(f.astype(np.int64))
         t.append(u.astype(np.float64) - f.astype(np.float64))
@@ -619,7 +619,7 @@ def test_probe_reproduces_linear_field():
     out = oracle.probe(spec, G.cell_pkg, G.nbr, fields, x, y, z)
     # the lattice coordinate u is decided in float32; the probe interpolates at
     # the point lo + (u + 0.5) h that u represents exactly
-    pts = np.stack([(np.asarray(v, np.float32) - np.float32(spec.lo[a])) / np.float32(spec.h) - np.float32(0.5)
+    pts = np.stack([(np.asarray(v, np.float32) - np.float32(spec.lo[a])) * np.float32(1.0 / spec.h) - np.float32(0.5)
                     for a, v in enumerate((x, y, z))], 1).astype(np.float64)
     pts = np.asarray(spec.lo)[None, :] + (pts + 0.5) * spec.h
     exact = (pts - p0) @ n
@@ -670,7 +670,7 @@ def test_morton_keys_bit_loop():
     for q in range(0, 300, 7):
         k = []
         for a, v in enumerate((x[q], y[q], z[q])):
-            u = (np.float32(v) - np.float32(spec.lo[a])) / np.float32(spec.h) - np.float32(0.5)
+            u = (np.float32(v) - np.float32(spec.lo[a])) * np.float32(1.0 / spec.h) - np.float32(0.5)
             i0 = int(np.floor(np.float32(u)))
             k.append(min(max(i0 + 1, 0), 4 * spec.dims[a] + 1))
         ref = 0
