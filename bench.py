@@ -331,6 +331,45 @@ def surrogate_section(sg, torch, steps=12000, samples=20_000_000):
     return r
 
 
+PAPER_TABLE1_MS = {  # "Performance Evaluation", Table 1 (units unstated; CPU unnamed)
+    "sequential_1_thread": 22.948, "sequential_4_threads": 7.429,
+    "stencil_1_thread": 59.972, "stencil_4_threads": 21.378,
+}
+
+
+def table1_section(sg, torch, reps=20):
+    """The paper's Table 1 workload on the GPU: the shelled sphere at 1/1024,
+    a sequential update of every active value (read + write 4 B per point)
+    and the 7-point Laplacian (read 4 B, write 4 B per point, one face row
+    per package)."""
+    shape, spec = si.shelled_sphere()
+    g = sg.Grid(spec)
+    P = g.tag_allocate(shape)
+    g.init_sdf(shape)
+    n_pt = 64 * (P - 2)
+    Ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    out = {}
+    for name, fn, nbytes in (("sequential", lambda: g.sequential_update(1e-7), 8.0 * n_pt),
+                             ("laplacian", g.laplacian, 8.0 * n_pt + 32.0 * (P - 2))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = Ev(), Ev()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": ms, "cell_updates_per_s": n_pt / (ms * 1e-3),
+                     "achieved_GBs": nbytes / (ms * 1e-3) / 1e9}
+    g.close()
+    hbm, kind = measured_peaks()
+    for v in out.values():
+        v["hbm_frac_of_%s" % kind] = v["achieved_GBs"] / hbm
+    return {"workload": "shelled sphere, centre (0.5, 0.5, 0.5), radii 0.3 / 0.31, h = 1/1024",
+            "packages": P, "points": n_pt, "gpu": out, "paper_cpu_ms_context": PAPER_TABLE1_MS}
+
+
 def phase_totals(phases):
     """Sum the durations between consecutive markers per phase name (ms)."""
     tot = {}
@@ -566,6 +605,7 @@ def run_sg(args):
         line["e2e"] = {"value": eunits / esecs, "unit": "cell-updates/s",
                        "h2d_bytes_per_step": sum(12 * b.n for b in bodies),
                        "d2h_bytes_per_step": sum(4 * len(b.out) * b.n for b in bodies)}
+    line["table1"] = table1_section(sg, torch)
     if not args.no_batch:
         line["batch"] = batch_section(sg, torch)
     if not args.no_surrogate:

@@ -62,13 +62,22 @@ enum {
     SG_ERR_DEVICE = 7    /* a kernel reported an inconsistency */
 };
 
-enum { SG_SHAPE_SPHERE = 0, SG_SHAPE_PLANE = 1, SG_SHAPE_TORUS = 2, SG_SHAPE_PRISM = 3, SG_SHAPE_ROUNDED_BOX = 4 };
+enum {
+    SG_SHAPE_SPHERE = 0,
+    SG_SHAPE_PLANE = 1,
+    SG_SHAPE_TORUS = 2,
+    SG_SHAPE_PRISM = 3,
+    SG_SHAPE_ROUNDED_BOX = 4,
+    SG_SHAPE_SHELL = 5
+};
 
 /* Analytic body, in a local frame: a world point x maps to q = R^T (x - centre)
  * with R = rot (row-major, local to world).  Parameters p per kind:
  *   sphere: p0 radius; plane: q_z = 0; torus: p0 major (about local z), p1
  *   minor; prism: triangle (p0,p1),(p2,p3),(p4,p5) extruded over q_z in
- *   [p6, p7]; rounded box: half extents p0..p2, rounding p3.
+ *   [p6, p7]; rounded box: half extents p0..p2, rounding p3; shell: the
+ *   solid between the spheres of radii p0 < p1 (the shelled sphere of the
+ *   paper's "Performance Evaluation").
  * Host struct, copied by value. */
 typedef struct {
     int32_t kind;
@@ -145,6 +154,11 @@ SG_API sg_status sg_init_sdf(sg_grid *g, const sg_shape *shape);
  * through the index shift of Listing 2.  Far packages keep g = 0.
  * Writes SG_FIELD_GX/GY/GZ.  Requires phi. */
 SG_API sg_status sg_gradient(sg_grid *g);
+
+/* The "sequential" benchmark of "Performance Evaluation": a small change to
+ * every active value, phi <- phi + delta on every active package (far
+ * packages untouched).  Requires phi. */
+SG_API sg_status sg_sequential_update(sg_grid *g, float delta);
 
 /* 7-point Laplacian sum_a (phi(+e_a) - 2 phi + phi(-e_a)) / h^2 on every
  * active package (the stencil benchmark of "Performance Evaluation").

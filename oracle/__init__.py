@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sg_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-SPHERE, PLANE, TORUS, PRISM, ROUNDED_BOX = 0, 1, 2, 3, 4
+SPHERE, PLANE, TORUS, PRISM, ROUNDED_BOX, SHELL = 0, 1, 2, 3, 4, 5
 
 
 def build(force: bool = False) -> str:
@@ -155,6 +155,13 @@ def gradient(spec, nbr, phi):
     lib().or_gradient(C.byref(_grid(spec)), C.c_int64(P), _p(np.ascontiguousarray(nbr, np.int32)), _p(phi),
                       *[_p(o) for o in out])
     return tuple(out)
+
+
+def sequential(phi32, delta):
+    """phi + delta on the active packages, in float32."""
+    phi = np.array(phi32, dtype=np.float32, copy=True, order="C")
+    lib().or_sequential(C.c_int64(phi.shape[0]), _p(phi), C.c_float(delta))
+    return phi
 
 
 def laplacian(spec, nbr, phi):

@@ -44,7 +44,7 @@
 #define PKG3 64
 
 typedef struct {
-    int32_t kind; /* 0 sphere, 1 plane, 2 torus, 3 prism, 4 rounded box */
+    int32_t kind; /* 0 sphere, 1 plane, 2 torus, 3 prism, 4 rounded box, 5 shell */
     int32_t pad;
     double centre[3];
     double rot[9]; /* row-major, local -> world */
@@ -140,6 +140,10 @@ double or_sdf(const or_shape *s, double x, double y, double z) {
             if (d > m) m = d;
         }
         return sqrt(o) + (m < 0.0 ? m : 0.0) - r;
+    }
+    case 5: { /* shell between the spheres of radii p0 < p1 */
+        double r = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+        return fabs(r - 0.5 * (s->p[0] + s->p[1])) - 0.5 * (s->p[1] - s->p[0]);
     }
     default:
         return NAN;
@@ -310,6 +314,12 @@ void or_gradient(const or_grid *g, int64_t P, const int32_t *nbr, const double *
                     }
                 }
     }
+}
+
+/* "Sequential" access of the paper's benchmark: phi <- phi + delta on every  */
+/* active value, in float as the device stores it.                            */
+void or_sequential(int64_t P, float *phi, float delta) {
+    for (int64_t i = 2 * PKG3; i < P * PKG3; ++i) phi[i] = phi[i] + delta;
 }
 
 /* 7-point Laplacian: sum over axes of (phi(+e) - 2 phi(0) + phi(-e)) / h^2.  */

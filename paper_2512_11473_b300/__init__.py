@@ -84,6 +84,7 @@ def lib():
         L.sg_init_sdf.argtypes = [vp, C.POINTER(sg_shape)]
         L.sg_gradient.argtypes = [vp]
         L.sg_laplacian.argtypes = [vp]
+        L.sg_sequential_update.argtypes = [vp, C.c_float]
         L.sg_reinit.argtypes = [vp, i32, C.c_float]
         L.sg_kernel_integrals.argtypes = [vp, i32, vp]
         L.sg_probe.argtypes = [vp, i64, vp, vp, vp] + [vp] * 8 + [i32]
@@ -255,6 +256,10 @@ class Grid:
 
     def laplacian(self):
         self._check(self._lib.sg_laplacian(self._h))
+
+    def sequential_update(self, delta):
+        """phi <- phi + delta on every active value (the paper's sequential benchmark)."""
+        self._check(self._lib.sg_sequential_update(self._h, float(delta)))
 
     def reinit(self, iterations, cfl=0.5):
         self._check(self._lib.sg_reinit(self._h, int(iterations), float(cfl)))

@@ -146,7 +146,7 @@ using namespace sg;
     } while (0)
 
 static bool valid_shape(const sg_shape* s) {
-    return s && s->kind >= SG_SHAPE_SPHERE && s->kind <= SG_SHAPE_ROUNDED_BOX;
+    return s && s->kind >= SG_SHAPE_SPHERE && s->kind <= SG_SHAPE_SHELL;
 }
 
 extern "C" {
@@ -288,6 +288,17 @@ sg_status sg_gradient(sg_grid* g) {
     SG_CUDA(g, launch_gradient(grid_f(g), (const int32_t*)g->faces.p, (const float*)g->field[SG_FIELD_PHI].p, o[0], o[1],
                                o[2], g->P, g->stream),
             "gradient");
+    return SG_OK;
+}
+
+sg_status sg_sequential_update(sg_grid* g, float delta) {
+    SG_CHECK_GRID(g);
+    if (!std::isfinite(delta)) return fail(g, SG_ERR_INVALID, "sg_sequential_update: delta not finite");
+    if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_sequential_update: phi not initialised");
+    DeviceGuard dg(g->device);
+    SG_CUDA(g, launch_sequential(g->field[SG_FIELD_PHI].p ? (float*)g->field[SG_FIELD_PHI].p : nullptr, delta, g->P,
+                                 g->stream),
+            "sequential update");
     return SG_OK;
 }
 

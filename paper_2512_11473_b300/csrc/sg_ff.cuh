@@ -103,7 +103,7 @@ __device__ __forceinline__ float ff_to_float(ff a) { return __fadd_rn(a.hi, a.lo
 // ---------------------------------------------------------------------------
 // Shapes, pre-split on the host into float-float constants.
 // ---------------------------------------------------------------------------
-enum { SHAPE_SPHERE = 0, SHAPE_PLANE = 1, SHAPE_TORUS = 2, SHAPE_PRISM = 3, SHAPE_ROUNDED_BOX = 4 };
+enum { SHAPE_SPHERE = 0, SHAPE_PLANE = 1, SHAPE_TORUS = 2, SHAPE_PRISM = 3, SHAPE_ROUNDED_BOX = 4, SHAPE_SHELL = 5 };
 
 struct ShapeFF {
     int kind;
@@ -162,6 +162,11 @@ __device__ inline ff ff_sdf(const ShapeFF& s, const ff x[3]) {
         return ff_sub(ff_sqrt(ff_add(ff_add(ff_sqr(q[0]), ff_sqr(q[1])), ff_sqr(q[2]))), s.p[0]);
     case SHAPE_PLANE:
         return q[2];
+    case SHAPE_SHELL: {  // | |q| - (r0 + r1)/2 | - (r1 - r0)/2
+        ff r = ff_sqrt(ff_add(ff_add(ff_sqr(q[0]), ff_sqr(q[1])), ff_sqr(q[2])));
+        ff mid = ff_mul_f(ff_add(s.p[0], s.p[1]), 0.5f), half = ff_mul_f(ff_sub(s.p[1], s.p[0]), 0.5f);
+        return ff_sub(ff_abs(ff_sub(r, mid)), half);
+    }
     case SHAPE_TORUS: {
         ff a = ff_sub(ff_sqrt(ff_add(ff_sqr(q[0]), ff_sqr(q[1]))), s.p[0]);
         return ff_sub(ff_sqrt(ff_add(ff_sqr(a), ff_sqr(q[2]))), s.p[1]);
@@ -218,6 +223,8 @@ __device__ inline float f_sdf(const ShapeFF& s, const float x[3]) {
         return sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) - p[0];
     case SHAPE_PLANE:
         return q[2];
+    case SHAPE_SHELL:
+        return fabsf(sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) - 0.5f * (p[0] + p[1])) - 0.5f * (p[1] - p[0]);
     case SHAPE_TORUS: {
         const float a = sqrtf(q[0] * q[0] + q[1] * q[1]) - p[0];
         return sqrtf(a * a + q[2] * q[2]) - p[1];

@@ -112,6 +112,8 @@ cudaError_t launch_reinit_s0(const GridF& G, const float* phi, float* s0, int64_
 cudaError_t launch_reinit_step(const GridF& G, const int32_t* faces, const float* s0, const float* phi_in,
                                float* phi_out, float dt, int64_t P, cudaStream_t s);
 cudaError_t launch_copy_active(const float* src, float* dst, int64_t P, cudaStream_t s);
+// phi <- phi + delta on the active packages
+cudaError_t launch_sequential(float* phi, float delta, int64_t P, cudaStream_t s);
 cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const float* phi, float* W, float* gx,
                                     float* gy, float* gz, int64_t P, cudaStream_t s);
 

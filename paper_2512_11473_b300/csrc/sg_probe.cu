@@ -54,32 +54,42 @@ __device__ __forceinline__ uint64_t morton_key(const GridF& G, float x, float y,
     return key;
 }
 
-// Keys, identity indices, and the sortedness check: *unsorted is set when
-// some key exceeds its successor's (one atomic per warp that finds one, and
-// none once the flag is seen set).
-template <typename KeyT>
-__global__ void __launch_bounds__(RS_THREADS) k_morton_keys(GridF G, int64_t n, const float* __restrict__ x,
-                                                            const float* __restrict__ y, const float* __restrict__ z,
-                                                            KeyT* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                            uint64_t* __restrict__ keys_out, int* unsorted) {
+// Sortedness check, reading the positions only: *unsorted is set when some
+// key exceeds its successor's (one atomic per warp that finds one, and none
+// once the flag is seen set).  The successor's key comes from the next lane.
+__global__ void __launch_bounds__(RS_THREADS) k_morton_check(GridF G, int64_t n, const float* __restrict__ x,
+                                                             const float* __restrict__ y, const float* __restrict__ z,
+                                                             int* unsorted) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t iters = (n + stride - 1) / stride;
     const int lane = threadIdx.x & 31;
     for (int64_t it = 0; it < iters; ++it) {  // uniform trip count: every lane takes part in the vote
         const int64_t q = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-        uint64_t k = 0;
-        if (q < n) {
-            k = morton_key(G, x[q], y[q], z[q]);
-            keys[q] = (KeyT)k;
-            vals[q] = (uint32_t)q;
-            if (keys_out) keys_out[q] = k;
-        }
-        // the successor's key: from the next lane, or computed by the last lane
+        const uint64_t k = q < n ? morton_key(G, x[q], y[q], z[q]) : 0;
         uint64_t next = __shfl_down_sync(0xffffffffu, k, 1);
         if (lane == 31 && q + 1 < n) next = morton_key(G, x[q + 1], y[q + 1], z[q + 1]);
         const bool bad = q + 1 < n && k > next;
         const unsigned m = __ballot_sync(0xffffffffu, bad);
         if (m && lane == __ffs(m) - 1 && *(volatile int*)unsorted == 0) atomicOr(unsorted, 1);
+    }
+}
+
+// Keys and identity indices for the radix passes (skipped when the input is
+// already in order), and the caller's copy of the keys when asked for.
+template <typename KeyT>
+__global__ void __launch_bounds__(RS_THREADS) k_morton_keys(GridF G, int64_t n, const float* __restrict__ x,
+                                                            const float* __restrict__ y, const float* __restrict__ z,
+                                                            KeyT* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                            uint64_t* __restrict__ keys_out, const int* unsorted) {
+    const bool sort = *unsorted != 0;
+    if (!sort && !keys_out) return;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = morton_key(G, x[q], y[q], z[q]);
+        if (sort) {
+            keys[q] = (KeyT)k;
+            vals[q] = (uint32_t)q;
+        }
+        if (keys_out) keys_out[q] = k;
     }
 }
 
@@ -282,8 +292,9 @@ cudaError_t sort_impl(const GridF& G, int64_t n, int key_bits, const float* x, c
 
     cudaError_t e = cudaMemsetAsync(unsorted, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
+    k_morton_check<<<blocks_for(n, RS_THREADS), RS_THREADS, 0, s>>>(G, n, x, y, z, unsorted);
     k_morton_keys<KeyT><<<blocks_for(n, RS_THREADS), RS_THREADS, 0, s>>>(G, n, x, y, z, k0, v0, keys_out, unsorted);
-    note_launch();
+    note_launch(2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int passes = (key_bits + 7) / 8;
     const size_t smem = RS_TILE * (sizeof(KeyT) + sizeof(uint32_t));

@@ -61,6 +61,18 @@ __global__ void __launch_bounds__(ROW_THREADS) k_reinit_step(const int32_t* __re
     reinterpret_cast<float4*>(phi_out)[s.q4] = reinit_row(w, sg, cfl, dt);
 }
 
+// One float4 row per thread, grid-stride over the active packages.
+__global__ void __launch_bounds__(SW_THREADS) k_sequential(float4* __restrict__ phi, float delta, int64_t rows) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < rows; q += (int64_t)gridDim.x * blockDim.x) {
+        float4 v = phi[32 + q];  // skip the two far packages (32 rows)
+        v.x += delta;
+        v.y += delta;
+        v.z += delta;
+        v.w += delta;
+        phi[32 + q] = v;
+    }
+}
+
 __global__ void __launch_bounds__(SW_THREADS) k_copy(const float* __restrict__ src, float* __restrict__ dst,
                                                       int64_t n) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
@@ -168,6 +180,16 @@ cudaError_t launch_reinit_step(const GridF& G, const int32_t* faces, const float
     if (P <= 2) return cudaSuccess;
     // dt sqrt(G) = (dt / h) sqrt(h^2 G) and dt / h is the CFL number
     k_reinit_step<<<row_blocks(P), ROW_THREADS, 0, s>>>(faces, s0, phi_in, phi_out, P, (float)(dt / G.h_d), dt);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sequential(float* phi, float delta, int64_t P, cudaStream_t s) {
+    if (P <= 2) return cudaSuccess;
+    const int64_t rows = (P - 2) * 16;
+    int64_t b = (rows + SW_THREADS - 1) / SW_THREADS;
+    if (b > 148 * 16) b = 148 * 16;
+    k_sequential<<<(unsigned)b, SW_THREADS, 0, s>>>(reinterpret_cast<float4*>(phi), delta, rows);
     note_launch();
     return cudaGetLastError();
 }

@@ -16,6 +16,7 @@ world).  Kinds and their parameter vector ``p``:
 * PRISM        p[0:6] = triangle (ax, ay, bx, by, cx, cy) in the local xy
                plane, extruded over q_z in [p[6], p[7]]
 * ROUNDED_BOX  p[0:3] = half extents, p[3] = rounding radius
+* SHELL        p[0] < p[1]: the solid between two concentric spheres
 """
 from __future__ import annotations
 
@@ -24,9 +25,9 @@ import math
 
 import numpy as np
 
-SPHERE, PLANE, TORUS, PRISM, ROUNDED_BOX = 0, 1, 2, 3, 4
+SPHERE, PLANE, TORUS, PRISM, ROUNDED_BOX, SHELL = 0, 1, 2, 3, 4, 5
 KIND_NAMES = {SPHERE: "sphere", PLANE: "plane", TORUS: "torus", PRISM: "prism",
-              ROUNDED_BOX: "rounded_box"}
+              ROUNDED_BOX: "rounded_box", SHELL: "shell"}
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -137,6 +138,10 @@ def rounded_box(half, rounding, centre=(0.0, 0.0, 0.0), rot=None) -> Shape:
                  (half[0], half[1], half[2], rounding))
 
 
+def shell(r_in, r_out, centre=(0.0, 0.0, 0.0)) -> Shape:
+    return Shape(SHELL, centre, Shape(SHELL).rot, (r_in, r_out))
+
+
 def quat_to_rot(q) -> tuple:
     """Row-major rotation matrix of the unit quaternion (w, x, y, z)."""
     w, x, y, z = q
@@ -171,6 +176,12 @@ def sphere_small():
 def torus_large(h=0.002):
     """Torus R = 0.6, r = 0.2 about z in [-1,1]^2 x [-0.4,0.4]."""
     return torus(0.6, 0.2), _box_grid((-1.0, -1.0, -0.4), (1.0, 1.0, 0.4), h)
+
+
+def shelled_sphere(h=1.0 / 1024):
+    """The benchmark body of the paper's Table 1: a shell centred at
+    (0.5, 0.5, 0.5) with radii 0.3 and 0.31, at resolution h in [0, 1]^3."""
+    return shell(0.3, 0.31, (0.5, 0.5, 0.5)), _box_grid((0.0,) * 3, (1.0,) * 3, h)
 
 
 PRISM_TRIANGLE = ((0.0, 0.0), (1.0, 0.0), (0.3, 0.8))

@@ -686,3 +686,25 @@ def test_morton_order_stable():
     keys = rng.integers(0, 50, 5000).astype(np.uint64)  # many ties
     order = oracle.morton_order(keys)
     assert np.array_equal(order, np.argsort(keys, kind="stable"))
+
+
+def test_sdf_shell_closed_form():
+    """Shell between radii 0.3 and 0.31 about (0.5, 0.5, 0.5): distance to the
+    nearer of the two spheres, negative between them."""
+    s = si.shell(0.3, 0.31, (0.5, 0.5, 0.5))
+    d = np.array([0.6, -1.0, 0.25])
+    d /= np.linalg.norm(d)
+    r = np.array([0.0, 0.1, 0.3, 0.302, 0.305, 0.309, 0.31, 0.5])
+    pts = 0.5 + r[:, None] * d[None, :]
+    got = oracle.sdf(s, pts[:, 0], pts[:, 1], pts[:, 2])
+    expect = np.where(r < 0.305, 0.3 - r, r - 0.31)
+    assert np.allclose(got, expect, atol=1e-15)
+    # the thickest inside point is the mid radius, at minus half the thickness
+    assert abs(got[4] + 0.005) < 1e-15
+
+
+def test_sequential_update_is_plain_addition():
+    phi = np.arange(5 * 64, dtype=np.float32).reshape(5, 64) * np.float32(0.001)
+    out = oracle.sequential(phi, 1e-3)
+    assert np.array_equal(out[:2], phi[:2])
+    assert np.array_equal(out[2:], phi[2:] + np.float32(1e-3))
