@@ -217,6 +217,23 @@ def probe(spec, cell_pkg, nbr, fields, x, y, z):
     return tuple(outs)
 
 
+def relax(spec, cell_pkg, nbr, fields, x, y, z, steps, step=0.1):
+    """Particle relaxation: `steps` times probe, then move by
+    -step h clip(phi/h, -1, 1) n with float32 positions.  Returns the final
+    (x, y, z) (float32) and the last step's probe (phi, nx, ny, nz, W, Gx, Gy,
+    Gz)."""
+    fs = [_f64(f) for f in fields]
+    x, y, z = (np.array(v, np.float32, copy=True) for v in (x, y, z))
+    n = x.size
+    outs = [np.zeros(n, np.float64) for _ in range(8)]
+    farr = (C.c_void_p * 8)(*[f.ctypes.data for f in fs])
+    oarr = (C.c_void_p * 8)(*[o.ctypes.data for o in outs])
+    lib().or_relax(C.byref(_grid(spec)), _p(np.ascontiguousarray(cell_pkg, np.int32)),
+                   _p(np.ascontiguousarray(nbr, np.int32)), farr, C.c_int64(n), _p(x), _p(y), _p(z),
+                   C.c_int32(int(steps)), C.c_double(float(step)), oarr)
+    return (x, y, z), tuple(outs)
+
+
 def morton_keys(spec, x, y, z):
     x, y, z = (np.ascontiguousarray(v, np.float32) for v in (x, y, z))
     keys = np.empty(x.size, np.uint64)

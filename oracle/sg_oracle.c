@@ -539,6 +539,30 @@ void or_probe(const or_grid *g, const int32_t *cell_pkg, const int32_t *nbr, con
 }
 
 /* ------------------------------------------------------------------------- */
+/* Particle relaxation: the coupling of Sec. "Grid-Particle Coupling" used as */
+/* a surface force.  Each step probes every particle (or_probe above) and     */
+/* then moves it by -step h clip(phi/h, -1, 1) n, the position being stored   */
+/* in float32 after each step.  out holds the probe of the last step.         */
+/* ------------------------------------------------------------------------- */
+void or_relax(const or_grid *g, const int32_t *cell_pkg, const int32_t *nbr, const double *const fields[8], int64_t n,
+              float *x, float *y, float *z, int32_t steps, double step, double *const out[8]) {
+    const double h = g->h;
+    for (int32_t k = 0; k < steps; ++k) {
+        or_probe(g, cell_pkg, nbr, fields, n, x, y, z, out);
+#pragma omp parallel for schedule(static)
+        for (int64_t q = 0; q < n; ++q) {
+            double s = out[0][q] / h;
+            if (s < -1.0) s = -1.0;
+            if (s > 1.0) s = 1.0;
+            const double m = step * h * s;
+            x[q] = (float)((double)x[q] - m * out[1][q]);
+            y[q] = (float)((double)y[q] - m * out[2][q]);
+            z[q] = (float)((double)z[q] - m * out[3][q]);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Morton order of particles: key = interleave of k_a = clamp(i0_a + 1, 0,    */
 /* 4 dims_a + 1) (at most 21 bits per axis), x in the lowest bit; order =     */
 /* stable sort by (key, input index).                                         */

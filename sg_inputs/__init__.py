@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
 
 import numpy as np
 
@@ -285,6 +286,128 @@ def prism_band_particles(n, tri, z0, z1, half_width, seed=0, jitter=0.0):
     if jitter > 0:
         pts = pts + (2.0 * st.uniform53(3 * n).reshape(n, 3) - 1.0) * jitter
     return tuple(np.ascontiguousarray(pts[:, a], dtype=np.float32) for a in range(3))
+
+
+def rounded_box_band_particles(n, half, rounding, half_width, seed=0, jitter=0.0):
+    """n points near the surface of a rounded box (local frame, float64).
+
+    The surface is split into its 6 flat faces, 12 quarter-cylinder edges and
+    8 sphere-octant corners of the core box with half extents half - rounding;
+    a piece is picked with probability proportional to its area, a point
+    uniform on it, then an offset along its outward normal uniform in
+    [-half_width, half_width), then optional jitter in [-jitter, jitter)^3.
+    Returns an (n, 3) array.
+    """
+    st = Stream(seed)
+    rho = float(rounding)
+    a = np.asarray(half, dtype=np.float64) - rho
+    pieces = []  # (kind, axis, signs)
+    areas = []
+    for i in range(3):
+        j, k = (i + 1) % 3, (i + 2) % 3
+        for s in (-1.0, 1.0):
+            pieces.append(("face", i, (s,)))
+            areas.append(4.0 * a[j] * a[k])
+    for i in range(3):
+        for sj in (-1.0, 1.0):
+            for sk in (-1.0, 1.0):
+                pieces.append(("edge", i, (sj, sk)))
+                areas.append(math.pi * rho * a[i])
+    for s0 in (-1.0, 1.0):
+        for s1 in (-1.0, 1.0):
+            for s2 in (-1.0, 1.0):
+                pieces.append(("corner", 0, (s0, s1, s2)))
+                areas.append(0.5 * math.pi * rho * rho)
+    cum = np.cumsum(areas) / np.sum(areas)
+    f = np.minimum(np.searchsorted(cum, st.uniform53(n), side="right"), len(pieces) - 1)
+    u1, u2 = st.uniform53(n), st.uniform53(n)
+    dirs = np.abs(_unit_dirs(st, n))
+    t = (2.0 * st.uniform53(n) - 1.0) * half_width
+    # per-piece tables: kind (0 face, 1 edge, 2 corner), axis, signs
+    kind = np.array([("face", "edge", "corner").index(pc[0]) for pc in pieces])
+    axis = np.array([pc[1] for pc in pieces])
+    sgn = np.array([tuple(pc[2]) + (1.0,) * (3 - len(pc[2])) for pc in pieces])
+    q = np.zeros((n, 3))
+    nrm = np.zeros((n, 3))
+    kf = kind[f]
+    r = np.nonzero(kf == 0)[0]  # faces
+    if r.size:
+        i = axis[f[r]]
+        j, k = (i + 1) % 3, (i + 2) % 3
+        sv = sgn[f[r], 0]
+        q[r, i] = sv * (a[i] + rho)
+        q[r, j] = (2.0 * u1[r] - 1.0) * a[j]
+        q[r, k] = (2.0 * u2[r] - 1.0) * a[k]
+        nrm[r, i] = sv
+    r = np.nonzero(kf == 1)[0]  # edges
+    if r.size:
+        i = axis[f[r]]
+        j, k = (i + 1) % 3, (i + 2) % 3
+        sj, sk = sgn[f[r], 0], sgn[f[r], 1]
+        th = 0.5 * math.pi * u2[r]
+        nrm[r, j] = sj * np.cos(th)
+        nrm[r, k] = sk * np.sin(th)
+        q[r, i] = (2.0 * u1[r] - 1.0) * a[i]
+        q[r, j] = sj * a[j] + rho * nrm[r, j]
+        q[r, k] = sk * a[k] + rho * nrm[r, k]
+    r = np.nonzero(kf == 2)[0]  # corners
+    if r.size:
+        sv = sgn[f[r]]
+        nrm[r] = sv * dirs[r]
+        q[r] = sv * a[None, :] + rho * nrm[r]
+    pts = q + t[:, None] * nrm
+    if jitter > 0:
+        pts = pts + (2.0 * st.uniform53(3 * n).reshape(n, 3) - 1.0) * jitter
+    return pts
+
+
+def body_band_particles(shape: Shape, n, half_width, seed=0, jitter=0.0):
+    """n points near the surface of a sphere, torus or rounded box, sampled in
+    the body's own frame (sphere: uniform in the shell |phi| < half_width;
+    torus: uniform in the tube band; rounded box: surface point plus normal
+    offset) and carried to the world frame x = centre + R q.  Returns float32
+    arrays x, y, z."""
+    if shape.kind == SPHERE:
+        loc = np.stack(sphere_shell_particles(n, shape.p[0], half_width, seed=seed), axis=1).astype(np.float64)
+        if jitter > 0:
+            loc = loc + (2.0 * Stream(seed + 0x9E37).uniform53(3 * n).reshape(n, 3) - 1.0) * jitter
+    elif shape.kind == TORUS:
+        loc = np.stack(torus_band_particles(n, shape.p[0], shape.p[1], half_width, seed=seed, jitter=jitter),
+                       axis=1).astype(np.float64)
+    elif shape.kind == ROUNDED_BOX:
+        loc = rounded_box_band_particles(n, shape.p[0:3], shape.p[3], half_width, seed=seed, jitter=jitter)
+    else:
+        raise ValueError("no band sampler for kind %d" % shape.kind)
+    R = np.asarray(shape.rot, dtype=np.float64).reshape(3, 3)
+    w = loc @ R.T + np.asarray(shape.centre)[None, :]
+    return tuple(np.ascontiguousarray(w[:, a], dtype=np.float32) for a in range(3))
+
+
+def relax_particles(bodies, n_total, seed=5, band_cells=2.0, jitter_h=0.5):
+    """Particles of a batch relaxation: n_total points over the bodies of
+    ``random_bodies``, body b getting a share proportional to its target
+    package count (so particles per package are about equal), sampled by
+    ``body_band_particles`` with half-width band_cells coarse cells, jitter
+    jitter_h fine cells and seed seed + b, stored body after body.
+    Returns (x, y, z, offsets) with offsets[b] the first particle of body b."""
+    tgt = np.array([t for _, _, t in bodies], dtype=np.float64)
+    share = np.floor(n_total * tgt / tgt.sum()).astype(np.int64)
+    rest = int(n_total - share.sum())
+    share[:rest] += 1
+    offsets = np.zeros(len(bodies) + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(share)
+    out = [np.empty(int(n_total), dtype=np.float32) for _ in range(3)]
+
+    def one(b):  # bodies draw from their own streams: any schedule gives the same arrays
+        shape, spec, _ = bodies[b]
+        v = body_band_particles(shape, int(share[b]), band_cells * spec.lc, seed=seed + b, jitter=jitter_h * spec.h)
+        for a in range(3):
+            out[a][offsets[b]:offsets[b + 1]] = v[a]
+
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(one, range(len(bodies))))
+    return out[0], out[1], out[2], offsets
 
 
 def box_particles(n, lo, hi, seed=0):
