@@ -308,6 +308,92 @@ def batch_section(sg, torch, n_bodies=256, iters=20, reps=5, seed=1):
             "batch_over_single": b_rate / s_rate}
 
 
+def sort_segments(grids, X, offsets):
+    """Input preparation: each body's segment of the device particles X put in
+    its Morton order (the walk order of the relaxation)."""
+    for b, g in enumerate(grids):
+        s, e = int(offsets[b]), int(offsets[b + 1])
+        if e > s:
+            seg = [v[s:e] for v in X]
+            _, order = g.morton_order(*seg)
+            o = order.long()
+            for v, sv in zip(X, seg):
+                v[s:e] = sv[o]
+            del o, order, seg
+
+
+def relax_section(sg, torch, net, trained, n_particles=100_000_000, steps=50, n_bodies=64, reps=3, seed=1):
+    """Grid-particle coupling at scale: the first 64 bodies of the 256-body
+    batch (spheres, tori, rounded boxes), 10^8 particles near their surfaces
+    (shares proportional to package counts, Morton order per body), one graph
+    of [gradient, 20 reinit sweeps, surrogate integrals with fallback] + 50
+    relaxation steps, each a probe of phi, n, W, G and a move by
+    -0.1 h clip(phi/h, -1, 1) n.  Positions are restored between timed
+    replays (outside the timed region)."""
+    t0 = time.perf_counter()
+    bodies = si.random_bodies(n_bodies, seed=seed)
+    grids = []
+    for shape, spec, _ in bodies:
+        g = sg.Grid(spec)
+        g.tag_allocate(shape)
+        g.init_sdf(shape)
+        grids.append(g)
+    x, y, z, off = si.relax_particles(bodies, n_particles, seed=5)
+    gen_s = time.perf_counter() - t0
+    X0 = [torch.from_numpy(v).cuda() for v in (x, y, z)]
+    del x, y, z
+    sort_segments(grids, X0, off)
+    batch = sg.Batch(grids)
+    P_tot = batch.P
+    P_act = sum(g.P - 2 for g in grids)
+    for g in grids:
+        g.close()
+    batch.set_surrogate(net)
+    plan, _ = batch.autotune(sg.make_plan(reinit_iterations=20, cfl=CFL, integrals_mode=1), reps=1)
+    X = [v.clone() for v in X0]
+    out = {k: torch.empty_like(X[0]) for k in ("W", "Gx", "Gy", "Gz")}
+    Ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(sweeps):
+        ms = []
+        for r in range(reps + 1):  # the first call captures the graph and warms up
+            batch.reset()
+            for v, v0 in zip(X, X0):
+                v.copy_(v0)
+            e0, e1 = Ev(), Ev()
+            e0.record()
+            batch.relax(*X, off, steps, 0.1, plan=plan, sweeps=sweeps, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            if r:
+                ms.append(e0.elapsed_time(e1))
+        return sum(ms) / len(ms)
+
+    full_ms = timed(True)
+    relax_ms = timed(False)
+    # moved distance after the 50 steps, a check that the run relaxed something
+    moved = float(torch.sqrt(sum((a - b) ** 2 for a, b in zip(X, X0))).max())
+    batch.close()
+    step_ms = relax_ms / steps
+    n_out = len(out)
+    alg_bytes = n_particles * (24 + 4 * n_out) + 32 * 64 * P_act
+    hbm, kind = measured_peaks()
+    achieved = alg_bytes / (step_ms * 1e-3) / 1e9
+    return {"workload": "%d mixed bodies (first %d of the 256-body batch, seed %d), %d particles near their surfaces, "
+                        "20 reinit sweeps + surrogate integrals with fallback, %d relaxation steps of 0.1 h, one graph"
+                        % (n_bodies, n_bodies, seed, n_particles, steps),
+            "packages": P_tot, "particles": n_particles, "steps": steps,
+            "plan": {"pkgs_per_item": plan.pkgs_per_item, "depth": plan.depth},
+            "surrogate_weights": "trained (surrogate section)" if trained else "random-init (surrogate not trained)",
+            "graph_ms": full_ms, "relax_only_ms": relax_ms, "sweeps_ms": full_ms - relax_ms, "step_ms": step_ms,
+            "particle_steps_per_s": n_particles * steps / (relax_ms * 1e-3),
+            "pipeline_particle_steps_per_s": n_particles * steps / (full_ms * 1e-3),
+            "roofline": {"kernel": "k_batch_relax", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "peak_kind": kind,
+                         "algorithmic_bytes_per_launch": alg_bytes},
+            "max_displacement": moved, "setup_seconds": gen_s}
+
+
 def surrogate_section(sg, torch, steps=12000, samples=20_000_000):
     """Learned kernel integral: training samples from 500 random bodies
     (seed 4, exact integrals as labels), `steps` Adam steps of batch 8192 on
@@ -325,10 +411,9 @@ def surrogate_section(sg, torch, steps=12000, samples=20_000_000):
     g.reinit(50, CFL)
     r = S.evaluate(g, net)
     g.close()
-    net.close()
     r["training"] = {"samples": info, "steps": steps, "batch": 8192, "seconds": secs,
                      "loss": [[a, b] for a, b in hist]}
-    return r
+    return r, net
 
 
 PAPER_TABLE1_MS = {  # "Performance Evaluation", Table 1 (units unstated; CPU unnamed)
@@ -608,8 +693,16 @@ def run_sg(args):
     line["table1"] = table1_section(sg, torch)
     if not args.no_batch:
         line["batch"] = batch_section(sg, torch)
+    net = None
     if not args.no_surrogate:
-        line["surrogate"] = surrogate_section(sg, torch)
+        line["surrogate"], net = surrogate_section(sg, torch)
+    if not args.no_relax:
+        trained = net is not None
+        if net is None:
+            net = sg.MLP(si.mlp_init_params(4))
+        line["relax"] = relax_section(sg, torch, net, trained, n_particles=args.relax_particles)
+    if net is not None:
+        net.close()
     if not args.no_cpu_baseline and rank == 0 and ws == 1:
         est = oracle_calibrate(args.iters, args.particles)
         frac = min(1.0, max(0.02, 15.0 / est))
@@ -638,6 +731,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-body batch measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip training and timing the surrogate")
+    ap.add_argument("--no-relax", action="store_true", help="skip the 64-body particle relaxation")
+    ap.add_argument("--relax-particles", type=int, default=100_000_000)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -220,7 +220,9 @@ typedef struct sg_batch sg_batch;
  * stencils, 4 times that for the integrals); depth: packages whose loads a
  * half-warp has in flight at once (1 or 2, at most pkgs_per_item).  The
  * sweeps are those of sg_gradient, sg_reinit(reinit_iterations, cfl) and
- * sg_kernel_integrals(integrals_mode, NULL); integrals_mode must be 0. */
+ * sg_kernel_integrals(integrals_mode, m): integrals_mode 0 is the exact sum,
+ * 1 the surrogate with fallback, whose network m is bound by
+ * sg_batch_set_surrogate. */
 typedef struct {
     int32_t pkgs_per_item;
     int32_t depth;
@@ -260,10 +262,55 @@ SG_API sg_status sg_batch_run(sg_batch *b, const sg_batch_plan *plan);
 SG_API sg_status sg_batch_autotune(sg_batch *b, sg_batch_plan *plan, int32_t reps, float *times_ms);
 
 /* Borrow body `body`'s slice of a batch field (SG_FIELD_PHI, _GX.._GZ, _W,
- * _GWX.._GWZ, _S0: [P_body][64] floats; SG_FIELD_NBR: global ids). */
+ * _GWX.._GWZ, _S0: [P_body][64] floats; SG_FIELD_NBR: [P_body][27] global
+ * ids; SG_FIELD_CELL_PKG: [nx*ny*nz] global ids of the body's background
+ * cells). */
 SG_API sg_status sg_batch_get_field(sg_batch *b, int32_t body, int32_t field, void **dev_ptr, int64_t *n_elems);
 SG_API int64_t sg_batch_n_packages(const sg_batch *b);
 SG_API const char *sg_batch_last_error(const sg_batch *b);
+
+struct sg_mlp; /* the surrogate network, declared with its calls below */
+
+/* Bind the network used by plans with integrals_mode 1 (NULL unbinds).
+ * The batch borrows it: it must outlive every run that uses it.  Its packed
+ * weights are read at each replay, so later sg_mlp_set_params or training
+ * steps take effect.  Rebinding waits for the batch's stream and drops the
+ * graphs captured with the previous network. */
+SG_API sg_status sg_batch_set_surrogate(sg_batch *b, const struct sg_mlp *m);
+
+/* Particle relaxation over a batch, the application of the grid-particle
+ * coupling (Sec. "Grid-Particle Coupling": the interpolated kernel integral
+ * acts as a surface force on particles).  Each step probes every particle as
+ * sg_probe does (trilinear phi, g, W, G of its body, n = g / |g|) and moves
+ * it by
+ *     x <- x - step h clip(phi / h, -1, 1) n
+ * (h its body's spacing), which pulls particles onto the zero level set.
+ * Particles are stored body after body; the walk is the storage order, so
+ * particles sorted by Morton key per body (sg_morton_order) give local
+ * gathers. */
+typedef struct {
+    int64_t n;              /* particles of all bodies */
+    const int64_t *offsets; /* host [n_bodies + 1]: body i owns particles [offsets[i], offsets[i+1]); offsets[0] = 0,
+                               offsets[n_bodies] = n, non-decreasing */
+    float *x, *y, *z;       /* device [n], updated in place (caller-owned) */
+    float *out[8];          /* device [n] or NULL each: phi, nx, ny, nz, W, Gx, Gy, Gz probed by the last step, before
+                               its move; must not alias the positions */
+    int32_t steps;          /* relaxation steps (0: positions unchanged) */
+    float step;             /* displacement per step in units of h, e.g. 0.1 */
+    int32_t sweeps;         /* 1: first run the plan's sweeps (as sg_batch_run); 0: probe the fields as they are */
+    int32_t reserved;
+} sg_relax;
+
+/* Run [the plan's sweeps +] `steps` relaxation steps, all captured as one
+ * CUDA graph on the first call with these arguments and replayed while they
+ * stay the same (pointers, sizes, offsets, plan).  `plan` may be NULL when
+ * sweeps = 0.  Asynchronous on the batch's stream.  Not in the paper as an
+ * API (the paper states the coupling; the batched relaxation is this
+ * library's).
+ * Errors: SG_ERR_INVALID (null arrays, bad offsets, bad plan, steps < 0),
+ * SG_ERR_CAPACITY (2^31 or more particle tiles of 256), SG_ERR_OOM,
+ * SG_ERR_CUDA. */
+SG_API sg_status sg_batch_relax(sg_batch *b, const sg_batch_plan *plan, const sg_relax *r);
 
 /* ------------------------------------------------------------------------ */
 /* Kernel-integral surrogate (not in the paper): a 27 -> 64 -> 64 -> 4       */

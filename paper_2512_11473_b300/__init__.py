@@ -52,6 +52,12 @@ class sg_batch_plan(C.Structure):
                 ("cfl", C.c_float), ("integrals_mode", C.c_int32), ("reserved", C.c_int32)]
 
 
+class sg_relax(C.Structure):
+    _fields_ = [("n", C.c_int64), ("offsets", C.POINTER(C.c_int64)), ("x", C.c_void_p), ("y", C.c_void_p),
+                ("z", C.c_void_p), ("out", C.c_void_p * 8), ("steps", C.c_int32), ("step", C.c_float),
+                ("sweeps", C.c_int32), ("reserved", C.c_int32)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -120,6 +126,8 @@ def lib():
         L.sg_batch_n_packages.argtypes = [vp]
         L.sg_batch_n_packages.restype = i64
         L.sg_batch_last_error.argtypes = [vp]
+        L.sg_batch_set_surrogate.argtypes = [vp, vp]
+        L.sg_batch_relax.argtypes = [vp, C.POINTER(sg_batch_plan), C.POINTER(sg_relax)]
         L.sg_batch_last_error.restype = C.c_char_p
         for name in declared_symbols():
             f = getattr(L, name)
@@ -396,11 +404,48 @@ class Batch:
         torch = _torch()
         p = C.c_void_p()
         n = C.c_int64()
-        if name == "nbr":
-            self._check(self._lib.sg_batch_get_field(self._h, int(body), INT_FIELDS["nbr"][0], C.byref(p), C.byref(n)))
-            return torch.as_tensor(_CudaArray(p.value, (n.value,), "<i4"), device="cuda").view(-1, 27)
+        if name in ("nbr", "cell_pkg"):
+            self._check(self._lib.sg_batch_get_field(self._h, int(body), INT_FIELDS[name][0], C.byref(p), C.byref(n)))
+            t = torch.as_tensor(_CudaArray(p.value, (n.value,), "<i4"), device="cuda")
+            return t.view(-1, 27) if name == "nbr" else t
         self._check(self._lib.sg_batch_get_field(self._h, int(body), FIELDS[name], C.byref(p), C.byref(n)))
         return torch.as_tensor(_CudaArray(p.value, (n.value,), "<f4"), device="cuda").view(-1, 64)
+
+    def set_surrogate(self, mlp):
+        """Bind the network of plans with integrals_mode=1 (None unbinds)."""
+        self._mlp = mlp  # the batch borrows it
+        self._check(self._lib.sg_batch_set_surrogate(self._h, mlp.handle if mlp is not None else None))
+
+    def relax(self, x, y, z, offsets, steps, step=0.1, plan=None, sweeps=True, out=None):
+        """[The plan's sweeps, then] `steps` relaxation steps of the particles
+        (x, y, z: float32 CUDA tensors updated in place, stored body after body,
+        body i owning [offsets[i], offsets[i+1])).  out: dict of the probe
+        outputs (names of PROBE_OUTPUTS) the last step writes."""
+        n = int(x.numel())
+        for v in (x, y, z):
+            assert v.dtype == _torch().float32 and v.is_cuda and v.is_contiguous() and v.numel() == n
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        assert off.size == self.n + 1
+        r = sg_relax()
+        r.n = n
+        self._relax_offsets = off  # kept alive for the call
+        r.offsets = off.ctypes.data_as(C.POINTER(C.c_int64))
+        r.x, r.y, r.z = x.data_ptr(), y.data_ptr(), z.data_ptr()
+        out = out or {}
+        for i, name in enumerate(PROBE_OUTPUTS):
+            t = out.get(name)
+            if t is not None:
+                assert t.dtype == _torch().float32 and t.is_cuda and t.is_contiguous() and t.numel() == n
+            r.out[i] = t.data_ptr() if t is not None else None
+        r.steps = int(steps)
+        r.step = float(step)
+        r.sweeps = 1 if sweeps else 0
+        if sweeps:
+            plan = plan if plan is not None else make_plan()
+            self._check(self._lib.sg_batch_relax(self._h, C.byref(plan), C.byref(r)))
+        else:
+            self._check(self._lib.sg_batch_relax(self._h, None, C.byref(r)))
+        return plan
 
 
 MLP_NPARAM = 6212

@@ -11,12 +11,18 @@
 // sweeps -> kernel integrals is captured once per plan into a CUDA graph and
 // replayed.  The autotuner times every (packages per item, staging depth)
 // pair and keeps the fastest.
+//
+// Relaxation ("Grid-Particle Coupling" as the surface force of particle
+// relaxation): particles of all bodies, stored body after body, are probed
+// and displaced by one kernel per step; the sweeps and every step are
+// captured into one graph.
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
 #include <vector>
 
+#include "sg_probe.cuh"
 #include "sg_rows.cuh"
 
 struct sg_batch_graph {
@@ -24,20 +30,30 @@ struct sg_batch_graph {
     cudaGraphExec_t exec;
 };
 
+struct sg_relax_graph {
+    sg_batch_plan plan;
+    sg_relax r;
+    std::vector<int64_t> offsets;
+    cudaGraphExec_t exec = nullptr;
+};
+
 struct sg_batch {
     int n = 0;
     int64_t P = 0;  // packages of all bodies, far packages included
-    std::vector<int64_t> base, npk;
+    std::vector<int64_t> base, npk, cell_base;
     std::vector<double> h;
+    std::vector<sg_grid_desc> desc;
+    const sg_mlp* mlp = nullptr;  // surrogate of plans with integrals_mode 1
     sg_allocator alloc{};
     bool user_alloc = false;
     cudaStream_t stream = nullptr;   // caller's stream: graphs run here
     cudaStream_t capture = nullptr;  // private stream used only to capture
     int device = 0;
-    sg::Buf phi, tmp, s0, phi0, f[8], nbr, faces, type, body, params, counters;
+    sg::Buf phi, tmp, s0, phi0, f[8], nbr, faces, type, body, params, counters, cells, sur, relax;
     size_t n_counters = 0;
     float params_cfl = -1.0f;
     std::vector<sg_batch_graph> graphs;
+    sg_relax_graph rx;
     std::string last_error;
 };
 
@@ -214,6 +230,64 @@ __global__ void k_batch_far_W(float* __restrict__ W, const int64_t* __restrict__
     W[base[b] * PKG3 + threadIdx.x] = threadIdx.x < PKG3 ? 1.0f : 0.0f;
 }
 
+// Per-body constants of the relaxation, in the form the single-grid probe
+// uses them, plus the body's particle range and its first tile (CTA).
+struct RelaxBody {
+    float lo[3];
+    float inv_h;   // 1/h rounded to float once
+    int dims[3];
+    float step_h;  // displacement scale times h, rounded to float once
+    int64_t cells;    // offset of the body's cells in the global cell table
+    int64_t first;    // first particle
+    int64_t end;      // one past the last particle
+    int64_t tile0;    // first tile
+    int64_t far_out;  // global id of the body's far+ package
+};
+
+constexpr int RX_THREADS = 256;  // particles per tile
+
+// One relaxation step for every particle: probe (phi, g and, with NF = 8,
+// the integrals) and move by -step h clip(phi / h, -1, 1) n.  A CTA owns one
+// tile of RX_THREADS consecutive particles of one body; its body is the last
+// whose first tile is at most blockIdx.x.
+template <int NF>
+__global__ void __launch_bounds__(RX_THREADS) k_batch_relax(const RelaxBody* __restrict__ rb, int nbody,
+                                                            const int32_t* __restrict__ cells,
+                                                            const int32_t* __restrict__ nbr, ProbeFields F,
+                                                            float* __restrict__ x, float* __restrict__ y,
+                                                            float* __restrict__ z, ProbeOut out) {
+    int lo = 0, hi = nbody - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&rb[mid].tile0) <= (int64_t)blockIdx.x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const RelaxBody B = rb[lo];
+    const int64_t q = B.first + ((int64_t)blockIdx.x - B.tile0) * RX_THREADS + threadIdx.x;
+    if (q >= B.end) return;
+    const float pos[3] = {x[q], y[q], z[q]};
+    const ProbeAt A = probe_locate(B.lo, B.inv_h, B.dims, cells + B.cells, B.far_out, pos);
+    float acc[8];
+    probe_interp<NF>(nbr, F, A, acc);
+    const float inv = probe_inv_norm(acc);
+    const float n0 = acc[1] * inv, n1 = acc[2] * inv, n2 = acc[3] * inv;
+    const float m = B.step_h * fminf(fmaxf(acc[0] * B.inv_h, -1.0f), 1.0f);
+    x[q] = fmaf(-m, n0, pos[0]);
+    y[q] = fmaf(-m, n1, pos[1]);
+    z[q] = fmaf(-m, n2, pos[2]);
+    if (out.o[0]) out.o[0][q] = acc[0];
+    if (out.o[1]) out.o[1][q] = n0;
+    if (out.o[2]) out.o[2][q] = n1;
+    if (out.o[3]) out.o[3][q] = n2;
+    if (NF == 8) {
+#pragma unroll
+        for (int f = 4; f < 8; ++f)
+            if (out.o[f]) out.o[f][q] = acc[f];
+    }
+}
+
 unsigned flat_grid(int64_t n) {
     int64_t b = (n + BT - 1) / BT;
     if (b < 1) b = 1;
@@ -263,10 +337,11 @@ bool same_plan(const sg_batch_plan& a, const sg_batch_plan& b) {
            a.cfl == b.cfl && a.integrals_mode == b.integrals_mode;
 }
 
-bool valid_plan(const sg_batch_plan* p) {
+bool valid_plan(const sg_batch* b, const sg_batch_plan* p) {
     const int ppi = p->pkgs_per_item;
     return (ppi == 1 || ppi == 2 || ppi == 4 || ppi == 8) && (p->depth == 1 || p->depth == 2) && p->depth <= ppi &&
-           p->reinit_iterations >= 0 && p->cfl > 0.0f && std::isfinite(p->cfl) && p->integrals_mode == 0;
+           p->reinit_iterations >= 0 && p->cfl > 0.0f && std::isfinite(p->cfl) &&
+           (p->integrals_mode == 0 || (p->integrals_mode == 1 && b->mlp));
 }
 
 int persistent_blocks(const void* kernel, int device) {
@@ -347,11 +422,67 @@ cudaError_t record_run(sg_batch* b, const sg_batch_plan& plan, cudaStream_t s) {
             cudaSuccess)
             return e;
     }
+    if (plan.integrals_mode == 1)
+        return launch_batch_surrogate_integrals(nbr, type, body, (const SurBody*)b->sur.p, phi, fo[4], fo[5], fo[6],
+                                                fo[7], b->P, b->mlp, b->device, s);
     const int nbi = persistent_blocks((const void*)k_batch_integrals, b->device);
     k_batch_integrals<<<nbi, BT, 0, s>>>(nbr, type, body, prm, phi, fo[4], fo[5], fo[6], fo[7], b->P, ppi, K,
                                          ctr + c++);
     note_launch();
     return cudaGetLastError();
+}
+
+// Record `steps` relaxation steps on stream s (tables already uploaded).
+cudaError_t record_relax(sg_batch* b, const sg_relax& r, int64_t tiles, cudaStream_t s) {
+    ProbeFields F;
+    F.f[0] = (const float*)b->phi.p;
+    for (int i = 1; i < 8; ++i) F.f[i] = (const float*)b->f[i].p;
+    ProbeOut o;
+    bool integ = false;
+    for (int i = 0; i < 8; ++i) {
+        o.o[i] = r.out[i];
+        if (i >= 4 && r.out[i]) integ = true;
+    }
+    const RelaxBody* rb = (const RelaxBody*)b->relax.p;
+    const int32_t* cells = (const int32_t*)b->cells.p;
+    const int32_t* nbr = (const int32_t*)b->nbr.p;
+    for (int k = 0; k < r.steps && tiles > 0; ++k) {
+        if (integ)
+            k_batch_relax<8><<<(unsigned)tiles, RX_THREADS, 0, s>>>(rb, b->n, cells, nbr, F, r.x, r.y, r.z, o);
+        else
+            k_batch_relax<4><<<(unsigned)tiles, RX_THREADS, 0, s>>>(rb, b->n, cells, nbr, F, r.x, r.y, r.z, o);
+        note_launch();
+    }
+    return cudaGetLastError();
+}
+
+bool same_relax(const sg_relax_graph& g, const sg_batch_plan& plan, const sg_relax& r, const int64_t* offsets,
+                int n) {
+    if (!g.exec || g.r.n != r.n || g.r.x != r.x || g.r.y != r.y || g.r.z != r.z || g.r.steps != r.steps ||
+        g.r.step != r.step || g.r.sweeps != r.sweeps)
+        return false;
+    for (int i = 0; i < 8; ++i)
+        if (g.r.out[i] != r.out[i]) return false;
+    if (r.sweeps && !same_plan(g.plan, plan)) return false;
+    if ((int)g.offsets.size() != n + 1) return false;
+    for (int i = 0; i <= n; ++i)
+        if (g.offsets[i] != offsets[i]) return false;
+    return true;
+}
+
+void drop_graphs(sg_batch* b, bool surrogate_only) {
+    std::vector<sg_batch_graph> keep;
+    for (auto& gr : b->graphs) {
+        if (!surrogate_only || gr.plan.integrals_mode == 1)
+            cudaGraphExecDestroy(gr.exec);
+        else
+            keep.push_back(gr);
+    }
+    b->graphs.swap(keep);
+    if (b->rx.exec && (!surrogate_only || (b->rx.r.sweeps && b->rx.plan.integrals_mode == 1))) {
+        cudaGraphExecDestroy(b->rx.exec);
+        b->rx.exec = nullptr;
+    }
 }
 
 }  // namespace
@@ -372,6 +503,8 @@ sg_status sg_batch_create(sg_grid* const* grids, int32_t n, void* stream, sg_bat
         P += grids[i]->P;
     }
     if (P >= (1LL << 31) / NB) return SG_ERR_CAPACITY;
+    int64_t n_cells = 0;
+    for (int i = 0; i < n; ++i) n_cells += grids[i]->nc;
     sg_batch* b = new (std::nothrow) sg_batch();
     if (!b) return SG_ERR_OOM;
     b->n = n;
@@ -389,7 +522,8 @@ sg_status sg_batch_create(sg_grid* const* grids, int32_t n, void* stream, sg_bat
               b_ensure(b, b->nbr, (size_t)P * NB * 4) && b_ensure(b, b->faces, (size_t)P * 8 * 4) &&
               b_ensure(b, b->type, (size_t)P) &&
               b_ensure(b, b->body, (size_t)P * 4) && b_ensure(b, b->params, (size_t)n * sizeof(BodyParams)) &&
-              b_ensure(b, b->counters, 4096);
+              b_ensure(b, b->counters, 4096) && b_ensure(b, b->cells, (size_t)n_cells * 4) &&
+              b_ensure(b, b->sur, (size_t)n * sizeof(SurBody));
     for (int i = 1; ok && i < 8; ++i) ok = b_ensure(b, b->f[i], fb);
     b->f[0] = Buf{};  // slot 0 (phi) is b->phi
     cudaError_t e = cudaSuccess;
@@ -398,13 +532,23 @@ sg_status sg_batch_create(sg_grid* const* grids, int32_t n, void* stream, sg_bat
         st = SG_ERR_OOM;
     } else {
         b->n_counters = 4096 / sizeof(unsigned);
-        int64_t off = 0;
+        int64_t off = 0, coff = 0;
+        std::vector<SurBody> sb(n);
         for (int i = 0; i < n && e == cudaSuccess; ++i) {
             sg_grid* g = grids[i];
             bases[i] = off;
             b->base.push_back(off);
+            b->cell_base.push_back(coff);
             b->npk.push_back(g->P);
             b->h.push_back(g->desc.h);
+            b->desc.push_back(g->desc);
+            sb[i] = sur_body(g->desc.h);
+            // background cells -> global package ids
+            k_batch_offset_nbr<<<flat_grid(g->nc), BT, 0, b->stream>>>((const int32_t*)g->cell_pkg.p,
+                                                                       (int32_t*)b->cells.p + coff, g->nc,
+                                                                       (int32_t)off);
+            note_launch();
+            coff += g->nc;
             e = cudaMemcpyAsync((float*)b->phi0.p + off * PKG3, g->field[SG_FIELD_PHI].p,
                                 (size_t)g->P * PKG3 * sizeof(float), cudaMemcpyDeviceToDevice, b->stream);
             if (e == cudaSuccess)
@@ -419,6 +563,8 @@ sg_status sg_batch_create(sg_grid* const* grids, int32_t n, void* stream, sg_bat
             }
             off += g->P;
         }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->sur.p, sb.data(), (size_t)n * sizeof(SurBody), cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = launch_fill_faces((const int32_t*)b->nbr.p, (int32_t*)b->faces.p, P, b->stream);
         for (int i = 1; i < 8 && e == cudaSuccess; ++i) e = cudaMemsetAsync(b->f[i].p, 0, fb, b->stream);
         if (e == cudaSuccess) {
@@ -462,8 +608,9 @@ sg_status sg_batch_create(sg_grid* const* grids, int32_t n, void* stream, sg_bat
 
 sg_status sg_batch_destroy(sg_batch* b) {
     if (!b) return SG_ERR_INVALID;
-    for (auto& gr : b->graphs) cudaGraphExecDestroy(gr.exec);
-    Buf* bufs[] = {&b->phi, &b->tmp, &b->s0, &b->phi0, &b->nbr, &b->faces, &b->type, &b->body, &b->params, &b->counters};
+    drop_graphs(b, false);
+    Buf* bufs[] = {&b->phi,  &b->tmp,    &b->s0,       &b->phi0,  &b->nbr, &b->faces, &b->type,
+                   &b->body, &b->params, &b->counters, &b->cells, &b->sur, &b->relax};
     for (Buf* x : bufs) b_free(b, *x);
     for (int i = 1; i < 8; ++i) b_free(b, b->f[i]);
     if (b->capture) cudaStreamDestroy(b->capture);
@@ -485,7 +632,7 @@ sg_status sg_batch_reset(sg_batch* b) {
 
 sg_status sg_batch_run(sg_batch* b, const sg_batch_plan* plan) {
     if (!b || !plan) return SG_ERR_INVALID;
-    if (!valid_plan(plan)) return b_fail(b, SG_ERR_INVALID, "sg_batch_run: bad plan");
+    if (!valid_plan(b, plan)) return b_fail(b, SG_ERR_INVALID, "sg_batch_run: bad plan");
     if ((size_t)plan->reinit_iterations + 4 > b->n_counters)
         return b_fail(b, SG_ERR_CAPACITY, "sg_batch_run: too many reinit iterations");
     cudaError_t e;
@@ -570,11 +717,115 @@ sg_status sg_batch_get_field(sg_batch* b, int32_t body, int32_t field, void** de
         *dev_ptr = (int32_t*)b->nbr.p + off * NB;
         *n_elems = np * NB;
         return SG_OK;
+    case SG_FIELD_CELL_PKG: {
+        const sg_grid_desc& d = b->desc[body];
+        *dev_ptr = (int32_t*)b->cells.p + b->cell_base[body];
+        *n_elems = (int64_t)d.dims[0] * d.dims[1] * d.dims[2];
+        return SG_OK;
+    }
     default:
         return b_fail(b, SG_ERR_INVALID, "sg_batch_get_field: unknown field");
     }
     *dev_ptr = base + off * PKG3;
     *n_elems = np * PKG3;
+    return SG_OK;
+}
+
+sg_status sg_batch_set_surrogate(sg_batch* b, const sg_mlp* m) {
+    if (!b) return SG_ERR_INVALID;
+    if (m != b->mlp) {
+        // captured surrogate graphs name the old network's weights
+        cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e == cudaSuccess && m) {
+            int prev = -1;
+            cudaGetDevice(&prev);
+            if (prev != b->device) cudaSetDevice(b->device);
+            e = setup_batch_surrogate();
+            if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+        }
+        if (e != cudaSuccess) return b_fail(b, SG_ERR_CUDA, std::string("set surrogate: ") + cudaGetErrorString(e));
+        drop_graphs(b, true);
+        b->mlp = m;
+    }
+    return SG_OK;
+}
+
+sg_status sg_batch_relax(sg_batch* b, const sg_batch_plan* plan, const sg_relax* r) {
+    if (!b || !r || !r->offsets || r->n < 0 || r->steps < 0 || !std::isfinite(r->step) || (r->sweeps && !plan))
+        return SG_ERR_INVALID;
+    if (r->n > 0 && (!r->x || !r->y || !r->z)) return SG_ERR_INVALID;
+    if (r->offsets[0] != 0 || r->offsets[b->n] != r->n)
+        return b_fail(b, SG_ERR_INVALID, "sg_batch_relax: offsets must run from 0 to n");
+    int64_t tiles = 0;
+    for (int i = 0; i < b->n; ++i) {
+        const int64_t c = r->offsets[i + 1] - r->offsets[i];
+        if (c < 0) return b_fail(b, SG_ERR_INVALID, "sg_batch_relax: offsets decrease");
+        tiles += (c + RX_THREADS - 1) / RX_THREADS;
+    }
+    if (tiles >= (1LL << 31)) return b_fail(b, SG_ERR_CAPACITY, "sg_batch_relax: too many particles");
+    if (r->sweeps) {
+        if (!valid_plan(b, plan)) return b_fail(b, SG_ERR_INVALID, "sg_batch_relax: bad plan");
+        if ((size_t)plan->reinit_iterations + 4 > b->n_counters)
+            return b_fail(b, SG_ERR_CAPACITY, "sg_batch_relax: too many reinit iterations");
+    }
+    cudaError_t e;
+    if (r->sweeps && plan->cfl != b->params_cfl) {
+        if ((e = upload_params(b, plan->cfl)) != cudaSuccess)
+            return b_fail(b, SG_ERR_CUDA, std::string("params: ") + cudaGetErrorString(e));
+    }
+    const sg_batch_plan none{};
+    const sg_batch_plan& pl = r->sweeps ? *plan : none;
+    if (!same_relax(b->rx, pl, *r, r->offsets, b->n)) {
+        if (b->rx.exec) {
+            cudaGraphExecDestroy(b->rx.exec);
+            b->rx.exec = nullptr;
+        }
+        std::vector<RelaxBody> hb(b->n);
+        int64_t t0 = 0;
+        for (int i = 0; i < b->n; ++i) {
+            const sg_grid_desc& d = b->desc[i];
+            RelaxBody& q = hb[i];
+            for (int a = 0; a < 3; ++a) {
+                q.lo[a] = (float)d.lo[a];
+                q.dims[a] = d.dims[a];
+            }
+            q.inv_h = (float)(1.0 / d.h);
+            q.step_h = (float)((double)r->step * d.h);
+            q.cells = b->cell_base[i];
+            q.first = r->offsets[i];
+            q.end = r->offsets[i + 1];
+            q.tile0 = t0;
+            q.far_out = b->base[i] + 1;
+            t0 += (q.end - q.first + RX_THREADS - 1) / RX_THREADS;
+        }
+        if (!b_ensure(b, b->relax, (size_t)b->n * sizeof(RelaxBody)))
+            return b_fail(b, SG_ERR_OOM, "sg_batch_relax: out of memory");
+        e = cudaMemcpyAsync(b->relax.p, hb.data(), hb.size() * sizeof(RelaxBody), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // hb goes out of scope
+        if (e != cudaSuccess) return b_fail(b, SG_ERR_CUDA, std::string("relax table: ") + cudaGetErrorString(e));
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t er = r->sweeps ? record_run(b, pl, b->capture) : cudaSuccess;
+            if (er == cudaSuccess) er = record_relax(b, *r, tiles, b->capture);
+            e = cudaStreamEndCapture(b->capture, &graph);
+            if (er != cudaSuccess) e = er;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return b_fail(b, SG_ERR_CUDA, std::string("relax capture: ") + cudaGetErrorString(e));
+        }
+        b->rx.plan = pl;
+        b->rx.r = *r;
+        b->rx.r.offsets = nullptr;
+        b->rx.offsets.assign(r->offsets, r->offsets + b->n + 1);
+        b->rx.exec = exec;
+    }
+    e = cudaGraphLaunch(b->rx.exec, b->stream);
+    if (e != cudaSuccess) return b_fail(b, SG_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
     return SG_OK;
 }
 

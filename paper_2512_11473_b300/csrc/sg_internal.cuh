@@ -119,6 +119,24 @@ cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const fl
 
 // surrogate (sg_mlp.cu)
 cudaError_t launch_surrogate_integrals(sg_grid* g, const sg_mlp* m, float* W, float* gx, float* gy, float* gz);
+// Surrogate constants of a body of spacing h: 1/h, 1/h^2, h, the curvature
+// bound |kappa| h of the fallback, and 1/eps of the Heaviside (eps = h).
+struct SurConst {
+    float inv_h, inv_h2, h, kappa_h_max;
+};
+struct SurBody {
+    SurConst C;
+    float inv_eps;
+};
+SurBody sur_body(double h);
+// Opt the batched surrogate kernel into its shared memory (once per device,
+// outside any stream capture).
+cudaError_t setup_batch_surrogate();
+// Surrogate integrals over a batch store: packages of type >= 2 take their
+// body's constants sb[body[p]]; far packages are left as they are.
+cudaError_t launch_batch_surrogate_integrals(const int32_t* nbr, const uint8_t* type, const int32_t* body,
+                                             const SurBody* sb, const float* phi, float* W, float* gx, float* gy,
+                                             float* gz, int64_t P, const sg_mlp* m, int device, cudaStream_t s);
 
 // probe (sg_probe.cu)
 struct ProbeFields {

@@ -402,9 +402,6 @@ __global__ void __launch_bounds__(TR_WARPS * 32) k_mlp_train(const unsigned char
 //            Laplacian: the exact 27-tap sum (bit-identical to mode 0)
 //   network  everything else: the tensor-core MLP
 // ---------------------------------------------------------------------------
-struct SurConst {
-    float inv_h, inv_h2, h, kappa_h_max;
-};
 
 __device__ __forceinline__ int sur_classify(const float* tile, int d, const SurConst& C, float (&v)[MLP_IN]) {
     const int i = d & 3, j = (d >> 2) & 3, k = d >> 4;
@@ -455,13 +452,19 @@ __device__ __forceinline__ void stage_tile(const int* nb27, const float* __restr
     }
 }
 
+// BATCH: packages of many bodies in one store; far packages (type < 2) are
+// skipped and each package takes its body's constants.
+template <bool BATCH>
 __global__ void __launch_bounds__(SU_THREADS) k_sur_integrals(const int32_t* __restrict__ nbr,
                                                               const float* __restrict__ phi, float* __restrict__ W,
                                                               float* __restrict__ gx, float* __restrict__ gy,
                                                               float* __restrict__ gz, int64_t P, KernelCoef K,
-                                                              float inv_eps, SurConst C,
+                                                              float inv_eps0, SurConst C0,
                                                               const unsigned char* __restrict__ packed,
-                                                              unsigned long long* __restrict__ stats) {
+                                                              unsigned long long* __restrict__ stats,
+                                                              const uint8_t* __restrict__ type,
+                                                              const int32_t* __restrict__ body,
+                                                              const SurBody* __restrict__ sb) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_nb[SU_PK][NB];
     __shared__ int s_qn;
@@ -482,7 +485,14 @@ __global__ void __launch_bounds__(SU_THREADS) k_sur_integrals(const int32_t* __r
     const int64_t rounds = (P - 2 + SU_PK - 1) / SU_PK;
     for (int64_t rd = blockIdx.x; rd < rounds; rd += gridDim.x) {
         const int64_t p = 2 + rd * SU_PK + lp;
-        const bool valid = p < P;
+        const bool valid = p < P && (!BATCH || __ldg(type + (p < P ? p : 0)) >= 2);
+        SurConst C = C0;
+        float inv_eps = inv_eps0;
+        if (BATCH && valid) {
+            const SurBody q = sb[__ldg(body + p)];
+            C = q.C;
+            inv_eps = q.inv_eps;
+        }
         if (threadIdx.x == 0) s_qn = 0;
         if (valid && d < NB) s_nb[lp][d] = __ldg(nbr + p * NB + d);
         __syncthreads();
@@ -828,18 +838,47 @@ cudaError_t launch_surrogate_integrals(sg_grid* g, const sg_mlp* m, float* W, fl
     if ((e = launch_set_far(gz, 0.0f, 0.0f, g->stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(g->stats.p, 0, 4 * sizeof(unsigned long long), g->stream)) != cudaSuccess) return e;
     if (g->P <= 2) return cudaSuccess;
-    if ((e = cudaFuncSetAttribute(k_sur_integrals, cudaFuncAttributeMaxDynamicSharedMemorySize, SU_BYTES)) !=
+    if ((e = cudaFuncSetAttribute(k_sur_integrals<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SU_BYTES)) !=
         cudaSuccess)
         return e;
     int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sur_integrals, SU_THREADS, SU_BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sur_integrals<false>, SU_THREADS, SU_BYTES);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
     const int64_t rounds = (g->P - 2 + SU_PK - 1) / SU_PK;
     int64_t blocks = (int64_t)(per_sm < 1 ? 1 : per_sm) * (sms < 1 ? 1 : sms);
     if (blocks > rounds) blocks = rounds;
-    k_sur_integrals<<<(unsigned)blocks, SU_THREADS, SU_BYTES, g->stream>>>(
+    k_sur_integrals<false><<<(unsigned)blocks, SU_THREADS, SU_BYTES, g->stream>>>(
         (const int32_t*)g->nbr.p, (const float*)g->field[SG_FIELD_PHI].p, W, gx, gy, gz, g->P, kernel_coef(),
-        (float)(1.0 / g->desc.h), sur_const(g), m->packed, (unsigned long long*)g->stats.p);
+        (float)(1.0 / g->desc.h), sur_const(g), m->packed, (unsigned long long*)g->stats.p, nullptr, nullptr,
+        nullptr);
+    note_launch();
+    return cudaGetLastError();
+}
+
+SurBody sur_body(double h) {
+    SurBody q;
+    q.C = SurConst{(float)(1.0 / h), (float)(1.0 / (h * h)), (float)h, 0.1f};
+    q.inv_eps = (float)(1.0 / h);
+    return q;
+}
+
+cudaError_t setup_batch_surrogate() {
+    return cudaFuncSetAttribute(k_sur_integrals<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SU_BYTES);
+}
+
+cudaError_t launch_batch_surrogate_integrals(const int32_t* nbr, const uint8_t* type, const int32_t* body,
+                                             const SurBody* sb, const float* phi, float* W, float* gx, float* gy,
+                                             float* gz, int64_t P, const sg_mlp* m, int device, cudaStream_t s) {
+    if (P <= 2) return cudaSuccess;
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sur_integrals<true>, SU_THREADS, SU_BYTES);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int64_t rounds = (P - 2 + SU_PK - 1) / SU_PK;
+    int64_t blocks = (int64_t)(per_sm < 1 ? 1 : per_sm) * (sms < 1 ? 1 : sms);
+    if (blocks > rounds) blocks = rounds;
+    k_sur_integrals<true><<<(unsigned)blocks, SU_THREADS, SU_BYTES, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(),
+                                                                         0.0f, SurConst{}, m->packed, nullptr, type,
+                                                                         body, sb);
     note_launch();
     return cudaGetLastError();
 }

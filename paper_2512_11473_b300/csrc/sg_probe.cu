@@ -7,7 +7,7 @@
 #include <cmath>
 #include <mutex>
 
-#include "sg_internal.cuh"
+#include "sg_probe.cuh"
 
 namespace sg {
 namespace {
@@ -17,17 +17,6 @@ constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096 keys per tile
 constexpr int RS_WARPS = RS_THREADS / 32;
-
-// Fine lattice coordinate in float32: u = (x - lo) * inv_h - 1/2 with
-// inv_h = 1/h rounded to float once, clamped to +-2^24, i0 = floor(u),
-// t = u - i0 (exact).
-__device__ __forceinline__ void lattice(float x, float lo, float inv_h, int& i0, float& t) {
-    float u = __fsub_rn(__fmul_rn(__fsub_rn(x, lo), inv_h), 0.5f);
-    u = fminf(fmaxf(u, -16777216.0f), 16777216.0f);
-    float f = floorf(u);
-    i0 = (int)f;
-    t = __fsub_rn(u, f);
-}
 
 __device__ __forceinline__ uint64_t spread3(uint64_t v) {  // bit b -> bit 3b (21 bits)
     v &= 0x1fffffull;
@@ -208,13 +197,6 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const KeyT* __restric
     }
 }
 
-__device__ __forceinline__ int64_t corner_index(const int32_t* __restrict__ nb, int sx, int sy, int sz) {
-    // index shift (Listing 2) for shifts in [0, 4] from the home package
-    int nx = (sx + PKG) >> 2, ny = (sy + PKG) >> 2, nz = (sz + PKG) >> 2;
-    int pkg = __ldg(nb + nx + 3 * ny + 9 * nz);
-    return (int64_t)pkg * PKG3 + (sx + PKG - nx * PKG) + PKG * (sy + PKG - ny * PKG) + PKG * PKG * (sz + PKG - nz * PKG);
-}
-
 __global__ void __launch_bounds__(PR_THREADS) k_probe(GridF G, const int32_t* __restrict__ cell_pkg,
                                                        const int32_t* __restrict__ nbr, ProbeFields F, int64_t n,
                                                        const float* __restrict__ x, const float* __restrict__ y,
@@ -225,32 +207,10 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe(GridF G, const int32_t* __
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = use_order ? (int64_t)__ldg(order + r) : r;
         const float pos[3] = {__ldg(x + q), __ldg(y + q), __ldg(z + q)};
-        int i0[3], l[3];
-        float t[3];
-        bool inside = true;
-        int64_t c = 0, stride = 1;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            lattice(pos[a], G.lo[a], G.inv_h, i0[a], t[a]);
-            int I = i0[a] >> 2;  // floor division by 4
-            l[a] = i0[a] & 3;
-            inside &= I >= 0 && I < G.dims[a];
-            c += (int64_t)I * stride;
-            stride *= G.dims[a];
-        }
-        const int64_t home = inside ? (int64_t)__ldg(cell_pkg + c) : 1;
-        const int32_t* nb = nbr + home * NB;
-        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll
-        for (int cr = 0; cr < 8; ++cr) {
-            const int a0 = cr & 1, a1 = (cr >> 1) & 1, a2 = (cr >> 2) & 1;
-            const float w = (a0 ? t[0] : 1.0f - t[0]) * (a1 ? t[1] : 1.0f - t[1]) * (a2 ? t[2] : 1.0f - t[2]);
-            const int64_t at = corner_index(nb, l[0] + a0, l[1] + a1, l[2] + a2);
-#pragma unroll
-            for (int f = 0; f < 8; ++f) acc[f] = fmaf(w, __ldg(F.f[f] + at), acc[f]);
-        }
-        const float gn = sqrtf(acc[1] * acc[1] + acc[2] * acc[2] + acc[3] * acc[3]);
-        const float inv = gn > 0.0f ? 1.0f / gn : 0.0f;
+        const ProbeAt A = probe_locate(G.lo, G.inv_h, G.dims, cell_pkg, 1, pos);
+        float acc[8];
+        probe_interp<8>(nbr, F, A, acc);
+        const float inv = probe_inv_norm(acc);
         if (out.o[0]) out.o[0][q] = acc[0];
         if (out.o[1]) out.o[1][q] = acc[1] * inv;
         if (out.o[2]) out.o[2][q] = acc[2] * inv;

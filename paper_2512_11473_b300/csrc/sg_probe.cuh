@@ -1,0 +1,83 @@
+// sg_probe.cuh -- per-particle probe arithmetic ("Grid-Particle Coupling"),
+// shared by the single-grid probe (sg_probe.cu) and the batched relaxation
+// (sg_batch.cu) so that both locate and interpolate identically.
+#pragma once
+#include "sg_internal.cuh"
+
+namespace sg {
+namespace {
+
+// Fine lattice coordinate in float32: u = (x - lo) * inv_h - 1/2 with
+// inv_h = 1/h rounded to float once, clamped to +-2^24, i0 = floor(u),
+// t = u - i0 (exact).
+__device__ __forceinline__ void lattice(float x, float lo, float inv_h, int& i0, float& t) {
+    float u = __fsub_rn(__fmul_rn(__fsub_rn(x, lo), inv_h), 0.5f);
+    u = fminf(fmaxf(u, -16777216.0f), 16777216.0f);
+    float f = floorf(u);
+    i0 = (int)f;
+    t = __fsub_rn(u, f);
+}
+
+__device__ __forceinline__ int64_t corner_index(const int32_t* __restrict__ nb, int sx, int sy, int sz) {
+    // index shift (Listing 2) for shifts in [0, 4] from the home package
+    int nx = (sx + PKG) >> 2, ny = (sy + PKG) >> 2, nz = (sz + PKG) >> 2;
+    int pkg = __ldg(nb + nx + 3 * ny + 9 * nz);
+    return (int64_t)pkg * PKG3 + (sx + PKG - nx * PKG) + PKG * (sy + PKG - ny * PKG) + PKG * PKG * (sz + PKG - nz * PKG);
+}
+
+// Where a particle sits: home package (the package of its home coarse cell
+// I = floor(i0 / 4), or `outside` when I leaves the domain), the local index
+// l = i0 - 4 I of the lower interpolation corner and the weights t.
+struct ProbeAt {
+    int64_t home;
+    int l[3];
+    float t[3];
+};
+
+__device__ __forceinline__ ProbeAt probe_locate(const float (&lo)[3], float inv_h, const int (&dims)[3],
+                                                const int32_t* __restrict__ cell_pkg, int64_t outside,
+                                                const float (&pos)[3]) {
+    ProbeAt A;
+    int i0[3];
+    bool inside = true;
+    int64_t c = 0, stride = 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lattice(pos[a], lo[a], inv_h, i0[a], A.t[a]);
+        int I = i0[a] >> 2;  // floor division by 4
+        A.l[a] = i0[a] & 3;
+        inside &= I >= 0 && I < dims[a];
+        c += (int64_t)I * stride;
+        stride *= dims[a];
+    }
+    A.home = inside ? (int64_t)__ldg(cell_pkg + c) : outside;
+    return A;
+}
+
+// Trilinear interpolation of the first NF probe fields (phi, gx, gy, gz, W,
+// Gx, Gy, Gz) from the 8 corners, reached from the home package by the
+// index shift.
+template <int NF>
+__device__ __forceinline__ void probe_interp(const int32_t* __restrict__ nbr, const ProbeFields& F, const ProbeAt& A,
+                                             float (&acc)[8]) {
+    const int32_t* nb = nbr + A.home * NB;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) acc[f] = 0.0f;
+#pragma unroll
+    for (int cr = 0; cr < 8; ++cr) {
+        const int a0 = cr & 1, a1 = (cr >> 1) & 1, a2 = (cr >> 2) & 1;
+        const float w = (a0 ? A.t[0] : 1.0f - A.t[0]) * (a1 ? A.t[1] : 1.0f - A.t[1]) * (a2 ? A.t[2] : 1.0f - A.t[2]);
+        const int64_t at = corner_index(nb, A.l[0] + a0, A.l[1] + a1, A.l[2] + a2);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) acc[f] = fmaf(w, __ldg(F.f[f] + at), acc[f]);
+    }
+}
+
+// n = g / |g|, or 0 where |g| = 0
+__device__ __forceinline__ float probe_inv_norm(const float (&acc)[8]) {
+    const float gn = sqrtf(acc[1] * acc[1] + acc[2] * acc[2] + acc[3] * acc[3]);
+    return gn > 0.0f ? 1.0f / gn : 0.0f;
+}
+
+}  // namespace
+}  // namespace sg
