@@ -49,7 +49,7 @@ struct sg_batch {
     cudaStream_t stream = nullptr;   // caller's stream: graphs run here
     cudaStream_t capture = nullptr;  // private stream used only to capture
     int device = 0;
-    sg::Buf phi, tmp, s0, phi0, f[8], nbr, faces, type, body, params, counters, cells, sur, relax;
+    sg::Buf phi, tmp, s0, phi0, f[8], nbr, faces, type, body, params, counters, cells, sur, relax, probe_tab;
     size_t n_counters = 0;
     float params_cfl = -1.0f;
     std::vector<sg_batch_graph> graphs;
@@ -253,7 +253,8 @@ constexpr int RX_THREADS = 256;  // particles per tile
 template <int NF>
 __global__ void __launch_bounds__(RX_THREADS) k_batch_relax(const RelaxBody* __restrict__ rb, int nbody,
                                                             const int32_t* __restrict__ cells,
-                                                            const int32_t* __restrict__ nbr, ProbeFields F,
+                                                            const int32_t* __restrict__ nbr,
+                                                            const float* __restrict__ tab,
                                                             float* __restrict__ x, float* __restrict__ y,
                                                             float* __restrict__ z, ProbeOut out) {
     int lo = 0, hi = nbody - 1;
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_batch_relax(const RelaxBody* __r
     const float pos[3] = {x[q], y[q], z[q]};
     const ProbeAt A = probe_locate(B.lo, B.inv_h, B.dims, cells + B.cells, B.far_out, pos);
     float acc[8];
-    probe_interp<NF>(nbr, F, A, acc);
+    probe_interp_packed<NF>(nbr, tab, A, acc);
     const float inv = probe_inv_norm(acc);
     const float n0 = acc[1] * inv, n1 = acc[2] * inv, n2 = acc[3] * inv;
     const float m = B.step_h * fminf(fmaxf(acc[0] * B.inv_h, -1.0f), 1.0f);
@@ -432,7 +433,8 @@ cudaError_t record_run(sg_batch* b, const sg_batch_plan& plan, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Record `steps` relaxation steps on stream s (tables already uploaded).
+// Record the packing of the probe table and `steps` relaxation steps on
+// stream s (tables already uploaded, probe table allocated).
 cudaError_t record_relax(sg_batch* b, const sg_relax& r, int64_t tiles, cudaStream_t s) {
     ProbeFields F;
     F.f[0] = (const float*)b->phi.p;
@@ -446,11 +448,15 @@ cudaError_t record_relax(sg_batch* b, const sg_relax& r, int64_t tiles, cudaStre
     const RelaxBody* rb = (const RelaxBody*)b->relax.p;
     const int32_t* cells = (const int32_t*)b->cells.p;
     const int32_t* nbr = (const int32_t*)b->nbr.p;
-    for (int k = 0; k < r.steps && tiles > 0; ++k) {
+    float* tab = (float*)b->probe_tab.p;
+    if (r.steps < 1 || tiles < 1) return cudaSuccess;
+    cudaError_t e = launch_pack_probe(F, tab, b->P * PKG3, s);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < r.steps; ++k) {
         if (integ)
-            k_batch_relax<8><<<(unsigned)tiles, RX_THREADS, 0, s>>>(rb, b->n, cells, nbr, F, r.x, r.y, r.z, o);
+            k_batch_relax<8><<<(unsigned)tiles, RX_THREADS, 0, s>>>(rb, b->n, cells, nbr, tab, r.x, r.y, r.z, o);
         else
-            k_batch_relax<4><<<(unsigned)tiles, RX_THREADS, 0, s>>>(rb, b->n, cells, nbr, F, r.x, r.y, r.z, o);
+            k_batch_relax<4><<<(unsigned)tiles, RX_THREADS, 0, s>>>(rb, b->n, cells, nbr, tab, r.x, r.y, r.z, o);
         note_launch();
     }
     return cudaGetLastError();
@@ -610,7 +616,7 @@ sg_status sg_batch_destroy(sg_batch* b) {
     if (!b) return SG_ERR_INVALID;
     drop_graphs(b, false);
     Buf* bufs[] = {&b->phi,  &b->tmp,    &b->s0,       &b->phi0,  &b->nbr, &b->faces, &b->type,
-                   &b->body, &b->params, &b->counters, &b->cells, &b->sur, &b->relax};
+                   &b->body, &b->params, &b->counters, &b->cells, &b->sur, &b->relax, &b->probe_tab};
     for (Buf* x : bufs) b_free(b, *x);
     for (int i = 1; i < 8; ++i) b_free(b, b->f[i]);
     if (b->capture) cudaStreamDestroy(b->capture);
@@ -798,7 +804,8 @@ sg_status sg_batch_relax(sg_batch* b, const sg_batch_plan* plan, const sg_relax*
             q.far_out = b->base[i] + 1;
             t0 += (q.end - q.first + RX_THREADS - 1) / RX_THREADS;
         }
-        if (!b_ensure(b, b->relax, (size_t)b->n * sizeof(RelaxBody)))
+        if (!b_ensure(b, b->relax, (size_t)b->n * sizeof(RelaxBody)) ||
+            !b_ensure(b, b->probe_tab, (size_t)b->P * PKG3 * 32))
             return b_fail(b, SG_ERR_OOM, "sg_batch_relax: out of memory");
         e = cudaMemcpyAsync(b->relax.p, hb.data(), hb.size() * sizeof(RelaxBody), cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // hb goes out of scope

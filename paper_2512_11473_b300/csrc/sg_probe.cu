@@ -197,6 +197,16 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const KeyT* __restric
     }
 }
 
+// Packed probe table: package p holds its 8 probe fields one after the
+// other, tab[512 p + 64 f + d] = field f at data point d.
+__global__ void __launch_bounds__(PR_THREADS) k_pack_probe(ProbeFields F, float* __restrict__ tab, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e >> 6, d = e & 63;
+#pragma unroll
+        for (int f = 0; f < 8; ++f) tab[p * (8 * PKG3) + f * PKG3 + d] = __ldg(F.f[f] + e);
+    }
+}
+
 __global__ void __launch_bounds__(PR_THREADS) k_probe(GridF G, const int32_t* __restrict__ cell_pkg,
                                                        const int32_t* __restrict__ nbr, ProbeFields F, int64_t n,
                                                        const float* __restrict__ x, const float* __restrict__ y,
@@ -315,6 +325,13 @@ cudaError_t morton_sort(const GridF& G, int64_t n, const float* x, const float* 
     if (bits <= 32)
         return sort_impl<uint32_t>(G, n, bits, x, y, z, keys_out, order_out, scratch, s, identity_out, unsorted_out);
     return sort_impl<uint64_t>(G, n, bits, x, y, z, keys_out, order_out, scratch, s, identity_out, unsorted_out);
+}
+
+cudaError_t launch_pack_probe(const ProbeFields& F, float* tab, int64_t n_points, cudaStream_t s) {
+    if (n_points <= 0) return cudaSuccess;
+    k_pack_probe<<<blocks_for(n_points, PR_THREADS), PR_THREADS, 0, s>>>(F, tab, n_points);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_probe(const GridF& G, const int32_t* cell_pkg, const int32_t* nbr, const ProbeFields& F,

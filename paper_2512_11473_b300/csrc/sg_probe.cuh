@@ -73,6 +73,30 @@ __device__ __forceinline__ void probe_interp(const int32_t* __restrict__ nbr, co
     }
 }
 
+// The same interpolation from the packed probe table: package p holds its 8
+// fields one after the other, field f of data point d at tab[512 p + 64 f + d],
+// so the 8 loads of a corner share one address and differ by constant
+// offsets.  Same sums in the same order as probe_interp.
+template <int NF>
+__device__ __forceinline__ void probe_interp_packed(const int32_t* __restrict__ nbr, const float* __restrict__ tab,
+                                                    const ProbeAt& A, float (&acc)[8]) {
+    const int32_t* nb = nbr + A.home * NB;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) acc[f] = 0.0f;
+#pragma unroll
+    for (int cr = 0; cr < 8; ++cr) {
+        const int a0 = cr & 1, a1 = (cr >> 1) & 1, a2 = (cr >> 2) & 1;
+        const float w = (a0 ? A.t[0] : 1.0f - A.t[0]) * (a1 ? A.t[1] : 1.0f - A.t[1]) * (a2 ? A.t[2] : 1.0f - A.t[2]);
+        const int sx = A.l[0] + a0, sy = A.l[1] + a1, sz = A.l[2] + a2;
+        const int nx = (sx + PKG) >> 2, ny = (sy + PKG) >> 2, nz = (sz + PKG) >> 2;
+        const int pkg = __ldg(nb + nx + 3 * ny + 9 * nz);
+        const float* q = tab + (int64_t)pkg * (8 * PKG3) + (sx + PKG - nx * PKG) + PKG * (sy + PKG - ny * PKG) +
+                         PKG * PKG * (sz + PKG - nz * PKG);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) acc[f] = fmaf(w, __ldg(q + f * PKG3), acc[f]);
+    }
+}
+
 // n = g / |g|, or 0 where |g| = 0
 __device__ __forceinline__ float probe_inv_norm(const float (&acc)[8]) {
     const float gn = sqrtf(acc[1] * acc[1] + acc[2] * acc[2] + acc[3] * acc[3]);
