@@ -563,10 +563,9 @@ void or_relax(const or_grid *g, const int32_t *cell_pkg, const int32_t *nbr, con
 }
 
 /* ------------------------------------------------------------------------- */
-/* Morton order of particles: key = interleave of k_a = clamp(i0_a + 4, 0,    */
-/* 4 dims_a + 7) (at most 21 bits per axis), x in the lowest bit; order =     */
-/* stable sort by (key, input index).  k_a = 4 (I_a + 1) + l_a, so each       */
-/* aligned 4x4x4 block of keys is the set of particles of one home package.   */
+/* Morton order of particles: key = interleave of k_a = clamp(i0_a + 1, 0,    */
+/* 4 dims_a + 1) (at most 21 bits per axis), x in the lowest bit; order =     */
+/* stable sort by (key, input index).                                         */
 /* ------------------------------------------------------------------------- */
 void or_morton_keys(const or_grid *g, int64_t n, const float *x, const float *y, const float *z, uint64_t *keys) {
 #pragma omp parallel for schedule(static)
@@ -577,7 +576,7 @@ void or_morton_keys(const or_grid *g, int64_t n, const float *x, const float *y,
             int64_t i0;
             double t;
             lattice(g, a, src[a][q], &i0, &t);
-            int64_t v = i0 + 4, vmax = 4 * (int64_t)g->dims[a] + 7;
+            int64_t v = i0 + 1, vmax = 4 * (int64_t)g->dims[a] + 1;
             if (v < 0) v = 0;
             if (v > vmax) v = vmax;
             k[a] = (uint64_t)v;
