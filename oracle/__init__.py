@@ -217,6 +217,21 @@ def probe(spec, cell_pkg, nbr, fields, x, y, z):
     return tuple(outs)
 
 
+def consistency_correct(spec, P, cell_pkg, pkg_cell, pkg_type, nbr, phi, trust=1.0):
+    """Consistency (sign) correction with trusted band |phi| < trust * h
+    (trust * h rounded to float32, as the device takes it).  Returns
+    (cell_pkg, nbr, phi, (points flipped, far cells moved)), all copies."""
+    cp = np.array(cell_pkg, np.int32, copy=True)
+    nb = np.array(nbr, np.int32, copy=True, order="C")
+    ph = np.array(phi, np.float64, copy=True, order="C")
+    ch = (C.c_int64 * 2)()
+    tau = float(np.float32(trust * spec.h))
+    lib().or_consistency_correct(C.byref(_grid(spec)), C.c_int64(int(P)), _p(cp),
+                                 _p(np.ascontiguousarray(pkg_cell, np.int32)),
+                                 _p(np.ascontiguousarray(pkg_type, np.uint8)), _p(nb), _p(ph), C.c_double(tau), ch)
+    return cp, nb, ph, (int(ch[0]), int(ch[1]))
+
+
 def relax(spec, cell_pkg, nbr, fields, x, y, z, steps, step=0.1):
     """Particle relaxation: `steps` times probe, then move by
     -step h clip(phi/h, -1, 1) n with float32 positions.  Returns the final

@@ -539,6 +539,142 @@ void or_probe(const or_grid *g, const int32_t *cell_pkg, const int32_t *nbr, con
 }
 
 /* ------------------------------------------------------------------------- */
+/* Consistency (sign) correction ("Consistency Correction"): the sign of phi  */
+/* is trusted only at data points with |phi| < tau, close to the surface,     */
+/* and carried from there to the rest of the domain by two diffusion steps,  */
+/* one over the data points of the packages and one over the background      */
+/* cells.  Each is a Jacobi flood over face neighbours: an unknown entry      */
+/* takes the sign of the sum of its labelled neighbours' signs, until nothing */
+/* changes.                                                                   */
+/*  - points: the trusted points start with their sign; the flood runs over  */
+/*    active packages only; then phi <- sign * |phi| where a sign is known;   */
+/*  - cells: core cells (the surface passes through them) are blocked; an    */
+/*    inner cell starts with the sign its package's points share; far cells  */
+/*    take their flooded label (package 0 inside, 1 outside) and the         */
+/*    neighbour table follows.                                               */
+/* The point step runs first: every point within h of the surface lies in a  */
+/* core cell, so the cells have no trusted sign until the points have one.   */
+/* changed[0] counts points whose sign flipped, changed[1] far cells moved.  */
+/* ------------------------------------------------------------------------- */
+#define CC_BLOCK 2
+static int face_step(const or_grid *g, int64_t c, int f, int64_t *out) {
+    const int64_t nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
+    int64_t I = c % nx, J = (c / nx) % ny, K = c / (nx * ny);
+    int a = f >> 1, d = (f & 1) ? 1 : -1;
+    if (a == 0) I += d;
+    if (a == 1) J += d;
+    if (a == 2) K += d;
+    if (I < 0 || J < 0 || K < 0 || I >= nx || J >= ny || K >= nz) return 0;
+    *out = I + nx * (J + ny * K);
+    return 1;
+}
+
+void or_consistency_correct(const or_grid *g, int64_t P, int32_t *cell_pkg, const int32_t *pkg_cell,
+                            const uint8_t *pkg_type, int32_t *nbr, double *phi, double tau, int64_t changed[2]) {
+    const int64_t nx = g->dims[0], ny = g->dims[1], nz = g->dims[2], nc = nx * ny * nz;
+    changed[0] = changed[1] = 0;
+    /* points: trusted seeds */
+    const int64_t np = P * PKG3;
+    int8_t *sg = (int8_t *)calloc((size_t)np, 1), *sn = (int8_t *)calloc((size_t)np, 1);
+    for (int64_t q = 2 * PKG3; q < np; ++q) {
+        const double v = phi[q];
+        if (fabs(v) < tau) sg[q] = v > 0.0 ? 1 : (v < 0.0 ? -1 : 0);
+    }
+    /* points: flood over the face neighbours inside active packages */
+    for (;;) {
+        int64_t moved = 0;
+        memcpy(sn, sg, (size_t)np);
+        for (int64_t p = 2; p < P; ++p) {
+            const int32_t *nb = nbr + p * 27;
+            for (int e = 0; e < PKG3; ++e) {
+                if (sg[p * PKG3 + e]) continue;
+                const int i = e % 4, j = (e / 4) % 4, k = e / 16;
+                int sum = 0;
+                for (int f = 0; f < 6; ++f) {
+                    const int a = f >> 1, d = (f & 1) ? 1 : -1;
+                    const int64_t at = shift_index(nb, i + (a == 0) * d, j + (a == 1) * d, k + (a == 2) * d);
+                    if (at / PKG3 >= 2) sum += sg[at];
+                }
+                if (sum != 0) {
+                    sn[p * PKG3 + e] = sum > 0 ? 1 : -1;
+                    ++moved;
+                }
+            }
+        }
+        int8_t *t = sg;
+        sg = sn;
+        sn = t;
+        if (!moved) break;
+    }
+    for (int64_t q = 2 * PKG3; q < np; ++q) {
+        const double v = phi[q];
+        if ((sg[q] > 0 && v < 0.0) || (sg[q] < 0 && v > 0.0)) {
+            phi[q] = -v;
+            ++changed[0];
+        }
+    }
+    /* cells: seeds from the inner packages' point signs */
+    int8_t *lab = (int8_t *)calloc((size_t)nc, 1), *nxt = (int8_t *)calloc((size_t)nc, 1);
+    for (int64_t c = 0; c < nc; ++c) {
+        const int64_t p = cell_pkg[c];
+        if (p < 2) continue;
+        if (pkg_type[p] == 2) {
+            lab[c] = CC_BLOCK;
+            continue;
+        }
+        int pos = 0, neg = 0;
+        for (int e = 0; e < PKG3; ++e) {
+            pos |= sg[p * PKG3 + e] > 0;
+            neg |= sg[p * PKG3 + e] < 0;
+        }
+        lab[c] = (pos && neg) ? CC_BLOCK : (pos ? 1 : (neg ? -1 : 0));
+    }
+    /* cells: flood */
+    for (;;) {
+        int64_t moved = 0;
+        memcpy(nxt, lab, (size_t)nc);
+        for (int64_t c = 0; c < nc; ++c) {
+            if (lab[c] != 0) continue;
+            int sum = 0;
+            for (int f = 0; f < 6; ++f) {
+                int64_t o;
+                if (face_step(g, c, f, &o) && (lab[o] == 1 || lab[o] == -1)) sum += lab[o];
+            }
+            if (sum != 0) {
+                nxt[c] = sum > 0 ? 1 : -1;
+                ++moved;
+            }
+        }
+        int8_t *t = lab;
+        lab = nxt;
+        nxt = t;
+        if (!moved) break;
+    }
+    /* far cells follow their label; neighbour entries naming far packages follow the cells */
+    for (int64_t c = 0; c < nc; ++c) {
+        if (cell_pkg[c] >= 2 || (lab[c] != 1 && lab[c] != -1)) continue;
+        const int32_t want = lab[c] < 0 ? 0 : 1;
+        if (cell_pkg[c] != want) {
+            cell_pkg[c] = want;
+            ++changed[1];
+        }
+    }
+    for (int64_t p = 2; p < P; ++p) {
+        const int64_t c = pkg_cell[p];
+        const int64_t I = c % nx, J = (c / nx) % ny, K = c / (nx * ny);
+        for (int n = 0; n < 27; ++n) {
+            const int64_t i = I + n % 3 - 1, j = J + (n / 3) % 3 - 1, k = K + n / 9 - 1;
+            if (nbr[p * 27 + n] >= 2 || i < 0 || j < 0 || k < 0 || i >= nx || j >= ny || k >= nz) continue;
+            nbr[p * 27 + n] = cell_pkg[i + nx * (j + ny * k)];
+        }
+    }
+    free(lab);
+    free(nxt);
+    free(sg);
+    free(sn);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Particle relaxation: the coupling of Sec. "Grid-Particle Coupling" used as */
 /* a surface force.  Each step probes every particle (or_probe above) and     */
 /* then moves it by -step h clip(phi/h, -1, 1) n, the position being stored   */

@@ -410,6 +410,19 @@ def relax_particles(bodies, n_total, seed=5, band_cells=2.0, jitter_h=0.5):
     return out[0], out[1], out[2], offsets
 
 
+def sign_noise_masks(P, n_cells, seed=6, frac_pkg=0.2, frac_cell=0.2):
+    """Synthetic sign noise for the consistency correction, standing in for
+    the wrong inside/outside decisions of a leaky surface: a boolean mask of
+    packages (ids >= 2) whose values away from the surface get the wrong
+    sign, and a mask of background cells whose far-package choice (inside /
+    outside) is swapped where the cell is far."""
+    st = Stream(seed)
+    pk = st.uniform53(int(P)) < frac_pkg
+    pk[:2] = False
+    cells = st.uniform53(int(n_cells)) < frac_cell
+    return pk, cells
+
+
 def box_particles(n, lo, hi, seed=0):
     """n points uniform in the axis-aligned box [lo, hi)."""
     st = Stream(seed)
