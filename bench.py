@@ -308,6 +308,47 @@ def batch_section(sg, torch, n_bodies=256, iters=20, reps=5, seed=1):
             "batch_over_single": b_rate / s_rate}
 
 
+def consistency_section(sg, torch, reps=3, frac=0.2, seed=17):
+    """Consistency (sign) correction on the h = 0.002 torus after synthetic
+    sign noise: in 20% of the packages every value at |phi| >= 2h flips sign
+    and 20% of the far cells swap inside <-> outside.  The noisy phi and cell
+    table are restored between timed calls (outside the timed region)."""
+    shape, spec = si.torus_large()
+    g = sg.Grid(spec)
+    P = g.tag_allocate(shape)
+    g.init_sdf(shape)
+    clean = g.field("phi").clone()
+    pk, cells = si.sign_noise_masks(P, spec.n_cells, seed=seed, frac_pkg=frac, frac_cell=frac)
+    phi, cp = g.field("phi"), g.field("cell_pkg")
+    flip = torch.from_numpy(pk).cuda()[:, None] & (phi.abs() >= 2.0 * spec.h)
+    phi[flip] = -phi[flip]
+    far = torch.from_numpy(cells).cuda() & (cp < 2)
+    cp[far] = 1 - cp[far]
+    noisy_phi, noisy_cp = phi.clone(), cp.clone()
+    Ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    ms, out = [], None
+    for r in range(reps + 1):
+        phi.copy_(noisy_phi)
+        cp.copy_(noisy_cp)
+        e0, e1 = Ev(), Ev()
+        e0.record()
+        out = g.consistency_correct(1.0)
+        e1.record()
+        torch.cuda.synchronize()
+        if r:
+            ms.append(e0.elapsed_time(e1))
+    restored = bool(torch.equal(g.field("phi"), clean))
+    n_pt = 64 * (P - 2)
+    t = sum(ms) / len(ms)
+    g.close()
+    return {"workload": "torus (R 0.6, r 0.2) at h = 0.002, sign noise in %d%% of packages (|phi| >= 2h) and of far "
+                        "cells, trust band |phi| < h" % int(100 * frac),
+            "packages": P, "points": n_pt, "cells": spec.n_cells, "ms": t,
+            "points_flipped": out[0], "far_cells_moved": out[1], "point_sweeps": out[2], "cell_sweeps": out[3],
+            "restored_bit_exact": restored,
+            "point_sweep_updates_per_s": n_pt * out[2] / (t * 1e-3)}
+
+
 def sort_segments(grids, X, offsets):
     """Input preparation: each body's segment of the device particles X put in
     its Morton order (the walk order of the relaxation)."""
@@ -569,6 +610,8 @@ def run_sg(args):
                 net.close()
             elif args.only == "table1":
                 r = table1_section(sg, torch)
+            elif args.only == "consistency":
+                r = consistency_section(sg, torch)
             else:
                 r = batch_section(sg, torch)
             print(json.dumps({"section": args.only, args.only: r}), flush=True)
@@ -708,6 +751,8 @@ def run_sg(args):
                        "h2d_bytes_per_step": sum(12 * b.n for b in bodies),
                        "d2h_bytes_per_step": sum(4 * len(b.out) * b.n for b in bodies)}
     line["table1"] = table1_section(sg, torch)
+    if not args.no_consistency:
+        line["consistency"] = consistency_section(sg, torch)
     if not args.no_batch:
         line["batch"] = batch_section(sg, torch)
     net = None
@@ -752,7 +797,8 @@ def main(argv=None):
     ap.add_argument("--no-relax", action="store_true", help="skip the 64-body particle relaxation")
     ap.add_argument("--relax-particles", type=int, default=100_000_000)
     ap.add_argument("--relax-bodies", type=int, default=64)
-    ap.add_argument("--only", choices=["relax", "table1", "batch"],
+    ap.add_argument("--no-consistency", action="store_true", help="skip the sign-correction measurement")
+    ap.add_argument("--only", choices=["relax", "table1", "batch", "consistency"],
                     help="run one side measurement alone and print it (no headline line)")
     args = ap.parse_args(argv)
     if args.impl == "reference":

@@ -155,6 +155,30 @@ SG_API sg_status sg_init_sdf(sg_grid *g, const sg_shape *shape);
  * Writes SG_FIELD_GX/GY/GZ.  Requires phi. */
 SG_API sg_status sg_gradient(sg_grid *g);
 
+/* Consistency (sign) correction (Sec. "Consistency Correction"): the sign
+ * of phi is trusted only where |phi| < trust h (trust h rounded to float),
+ * close to the surface, and carried from there to the rest of the domain by
+ * two diffusion steps, each a Jacobi flood over face neighbours in which an
+ * unknown entry takes the sign of the sum of its labelled neighbours'
+ * signs, run until a sweep changes nothing:
+ *   1. over the data points of the active packages, from the trusted
+ *      points; then phi <- sign |phi| wherever a sign was found;
+ *   2. over the background cells: core cells blocked, inner cells start
+ *      with the sign their package's points share; a far cell takes the
+ *      far package of its label (0 inside, 1 outside) and the neighbour
+ *      and face tables are rebuilt to match.
+ * (The paper names the cell step first; here it runs second because every
+ * data point within h of the surface lies in a core cell, so the cells have
+ * no trusted sign before the points.)  For a grid whose magnitudes are
+ * distances this restores every sign a leaky surface got wrong outside the
+ * trusted band.  out (host, may be NULL): [4] = points flipped, far cells
+ * moved, point sweeps, cell sweeps.  Derived fields (g, W, ...) are stale
+ * afterwards.  Blocks until done (it reads convergence flags).
+ * Errors: SG_ERR_INVALID (trust <= 0 or not finite), SG_ERR_STATE (no phi),
+ * SG_ERR_OOM, SG_ERR_TIMEOUT (a flood that does not settle; cannot happen
+ * for valid tables). */
+SG_API sg_status sg_consistency_correct(sg_grid *g, float trust, int64_t *out);
+
 /* The "sequential" benchmark of "Performance Evaluation": a small change to
  * every active value, phi <- phi + delta on every active package (far
  * packages untouched).  Requires phi. */

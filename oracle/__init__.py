@@ -225,7 +225,7 @@ def consistency_correct(spec, P, cell_pkg, pkg_cell, pkg_type, nbr, phi, trust=1
     nb = np.array(nbr, np.int32, copy=True, order="C")
     ph = np.array(phi, np.float64, copy=True, order="C")
     ch = (C.c_int64 * 2)()
-    tau = float(np.float32(trust * spec.h))
+    tau = float(np.float32(float(np.float32(trust)) * spec.h))  # as the library takes it
     lib().or_consistency_correct(C.byref(_grid(spec)), C.c_int64(int(P)), _p(cp),
                                  _p(np.ascontiguousarray(pkg_cell, np.int32)),
                                  _p(np.ascontiguousarray(pkg_type, np.uint8)), _p(nb), _p(ph), C.c_double(tau), ch)

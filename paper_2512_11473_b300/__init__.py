@@ -91,6 +91,7 @@ def lib():
         L.sg_gradient.argtypes = [vp]
         L.sg_laplacian.argtypes = [vp]
         L.sg_sequential_update.argtypes = [vp, C.c_float]
+        L.sg_consistency_correct.argtypes = [vp, C.c_float, C.POINTER(i64)]
         L.sg_reinit.argtypes = [vp, i32, C.c_float]
         L.sg_kernel_integrals.argtypes = [vp, i32, vp]
         L.sg_probe.argtypes = [vp, i64, vp, vp, vp] + [vp] * 8 + [i32]
@@ -264,6 +265,14 @@ class Grid:
 
     def laplacian(self):
         self._check(self._lib.sg_laplacian(self._h))
+
+    def consistency_correct(self, trust=1.0):
+        """Sign correction of phi and of the far cells (trust band |phi| <
+        trust h).  Returns (points flipped, far cells moved, point sweeps,
+        cell sweeps)."""
+        out = (C.c_int64 * 4)()
+        self._check(self._lib.sg_consistency_correct(self._h, float(trust), out))
+        return tuple(int(v) for v in out)
 
     def sequential_update(self, delta):
         """phi <- phi + delta on every active value (the paper's sequential benchmark)."""

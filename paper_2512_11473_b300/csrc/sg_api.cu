@@ -291,6 +291,26 @@ sg_status sg_gradient(sg_grid* g) {
     return SG_OK;
 }
 
+sg_status sg_consistency_correct(sg_grid* g, float trust, int64_t* out) {
+    SG_CHECK_GRID(g);
+    if (!(trust > 0.0f) || !std::isfinite(trust)) return fail(g, SG_ERR_INVALID, "sg_consistency_correct: bad trust");
+    if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_consistency_correct: phi not initialised");
+    DeviceGuard dg(g->device);
+    if (!ensure(g, g->scratch, consistency_scratch_bytes(g->P, g->nc)))
+        return fail(g, SG_ERR_OOM, "sg_consistency_correct: out of memory");
+    int64_t o[4] = {0, 0, 0, 0};
+    const cudaError_t e =
+        run_consistency(grid_ff(g), g->P, g->nc, (int32_t*)g->cell_pkg.p, (const int32_t*)g->pkg_cell.p,
+                        (const uint8_t*)g->pkg_type.p, (int32_t*)g->nbr.p, (int32_t*)g->faces.p,
+                        (float*)g->field[SG_FIELD_PHI].p, (float)((double)trust * g->desc.h), g->scratch.p,
+                        g->host_pin.p, o, g->stream);
+    if (e == cudaErrorLaunchTimeout) return fail(g, SG_ERR_TIMEOUT, "sg_consistency_correct: flood did not settle");
+    if (e != cudaSuccess) return cuda_fail(g, e, "consistency correction");
+    if (out)
+        for (int i = 0; i < 4; ++i) out[i] = o[i];
+    return SG_OK;
+}
+
 sg_status sg_sequential_update(sg_grid* g, float delta) {
     SG_CHECK_GRID(g);
     if (!std::isfinite(delta)) return fail(g, SG_ERR_INVALID, "sg_sequential_update: delta not finite");

@@ -97,6 +97,13 @@ cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* prefix,
                                int32_t* pkg_cell, uint8_t* pkg_type, int64_t nc, cudaStream_t s);
 cudaError_t launch_fill_nbr(const GridFF& G, const int32_t* cell_pkg, const int32_t* pkg_cell, int32_t* nbr,
                             int64_t P, cudaStream_t s);
+// Consistency (sign) correction of phi, cell_pkg, nbr and faces in place;
+// host-synchronising.  out: points flipped, far cells moved, point and cell
+// flood sweeps.
+size_t consistency_scratch_bytes(int64_t P, int64_t nc);
+cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cell_pkg, const int32_t* pkg_cell,
+                            const uint8_t* pkg_type, int32_t* nbr, int32_t* faces, float* phi, float tau,
+                            void* scratch, void* host_pin, int64_t out[4], cudaStream_t s);
 // faces[p][8] = the six face entries of nbr[p][27] (one 32-byte row per package)
 cudaError_t launch_fill_faces(const int32_t* nbr, int32_t* faces, int64_t P, cudaStream_t s);
 cudaError_t launch_init_sdf(const GridFF& G, const ShapeFF& S, const int32_t* pkg_cell, float* phi, float F,

@@ -1,0 +1,109 @@
+"""Consistency (sign) correction on the GPU against the oracle.
+
+Noise as in the oracle pins: in random packages every value at |phi| >= 2h
+changes sign (the point mask is taken from the oracle's values so that both
+sides flip the same points), random far cells swap inside <-> outside.  The
+device must restore its own clean grid bit for bit (phi, cell table,
+neighbour and face tables), report the same counts as the oracle, and agree
+with the oracle step-wise on the same float32 input.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import sg_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_11473_b300 import build
+    build.build()
+    import paper_2512_11473_b300 as m
+    return m
+
+
+def H(t):
+    return t.detach().cpu().numpy()
+
+
+BODIES = {
+    "sphere": lambda: si.sphere_small(),
+    "torus": lambda: (si.torus(0.5, 0.2, rot=si.random_rotation(si.Stream(3))),
+                      si.GridSpec((-0.9, -0.9, -0.9), (22, 22, 22), 0.02)),
+    "rounded_box": lambda: (si.rounded_box((0.6, 0.45, 0.3), 0.06, rot=si.random_rotation(si.Stream(5))),
+                            si.GridSpec((-1.0, -1.0, -1.0), (25, 25, 25), 0.02)),
+    "torus_h0.002": lambda: si.torus_large(),
+}
+
+
+def _setup(sg, name, seed=17, frac=0.3):
+    shape, spec = BODIES[name]()
+    g = sg.Grid(spec)
+    P = g.tag_allocate(shape)
+    g.init_sdf(shape)
+    O = oracle.build_grid(spec, shape)
+    assert P == O.P
+    clean = {k: g.field(k).clone() for k in ("phi", "cell_pkg", "nbr")}
+    pk, cells = si.sign_noise_masks(P, spec.n_cells, seed=seed, frac_pkg=frac, frac_cell=frac)
+    flip = pk[:, None] & (np.abs(O.phi) >= 2.0 * spec.h)
+    far = cells & (O.cell_pkg < 2)
+    return shape, spec, g, O, clean, flip, far
+
+
+def _apply_noise_device(g, flip, far):
+    phi = g.field("phi")
+    f = torch.from_numpy(flip).cuda()
+    phi[f] = -phi[f]
+    cp = g.field("cell_pkg")
+    m = torch.from_numpy(far).cuda()
+    cp[m] = 1 - cp[m]
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("name", ["sphere", "torus", "rounded_box", "torus_h0.002"])
+def test_consistency_restores_and_matches_oracle(sg, name):
+    shape, spec, g, O, clean, flip, far = _setup(sg, name, frac=0.3 if name != "torus_h0.002" else 0.2)
+    faces0 = H(g.field("nbr"))[:, [12, 14, 10, 16, 4, 22]]
+    _apply_noise_device(g, flip, far)
+    noisy_phi = H(g.field("phi")).astype(np.float64)
+    noisy_cp = H(g.field("cell_pkg"))
+    out = g.consistency_correct(1.0)
+    assert out[0] == int(flip.sum()) and out[1] == int(far.sum())
+    assert torch.equal(g.field("phi"), clean["phi"])
+    assert torch.equal(g.field("cell_pkg"), clean["cell_pkg"])
+    assert torch.equal(g.field("nbr"), clean["nbr"])
+    assert np.array_equal(H(g.field("nbr"))[:, [12, 14, 10, 16, 4, 22]], faces0)
+    # step-wise: the oracle on the device's noisy float32 input
+    cp2, nb2, phi2, ch = oracle.consistency_correct(spec, O.P, noisy_cp, O.pkg_cell, O.pkg_type, O.nbr, noisy_phi)
+    assert ch == (out[0], out[1])
+    assert np.array_equal(phi2.astype(np.float32), H(g.field("phi")))
+    assert np.array_equal(cp2, H(g.field("cell_pkg")))
+    assert np.array_equal(nb2, H(g.field("nbr")))
+    # the face stencils read the rebuilt face table: a gradient equals the clean grid's
+    g.gradient()
+    gx = g.field("gx").clone()
+    g2 = sg.Grid(spec)
+    g2.tag_allocate(shape)
+    g2.init_sdf(shape)
+    g2.gradient()
+    assert torch.equal(gx, g2.field("gx"))
+
+
+def test_consistency_clean_grid_unchanged(sg):
+    shape, spec, g, O, clean, _, _ = _setup(sg, "torus")
+    out = g.consistency_correct(1.0)
+    assert out[:2] == (0, 0)
+    for k, v in clean.items():
+        assert torch.equal(g.field(k), v)
+
+
+def test_consistency_bad_trust(sg):
+    shape, spec, g, O, clean, _, _ = _setup(sg, "sphere")
+    for t in (0.0, -1.0, float("nan")):
+        with pytest.raises(sg.SgError):
+            g.consistency_correct(t)
