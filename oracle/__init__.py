@@ -51,6 +51,7 @@ def lib():
     if _lib is None:
         _lib = C.CDLL(build())
         _lib.or_tag.restype = C.c_int64
+        _lib.or_tag_from.restype = C.c_int64
         _lib.or_sdf.restype = C.c_double
         _lib.or_sdf.argtypes = [C.POINTER(_Shape), C.c_double, C.c_double, C.c_double]
         _lib.or_get_threads.restype = C.c_int
@@ -128,6 +129,19 @@ def tag(spec, shape):
     ties = C.c_int64(0)
     P = lib().or_tag(C.byref(_grid(spec)), C.byref(_shape(shape)), _p(cell_pkg), _p(cell_type), C.byref(ties))
     return cell_pkg, cell_type, int(P), int(ties.value)
+
+
+def tag_from(spec, shape, coarse_spec, c_cell_pkg, c_pkg_type, c_phi):
+    """Tagging of a layer from its coarser layer (same lo, half the dims, twice
+    the spacing).  Returns (cell_pkg, cell_type, P, near_ties, evaluated)."""
+    nc = spec.n_cells
+    cell_pkg = np.empty(nc, np.int32)
+    cell_type = np.empty(nc, np.uint8)
+    ties, ev = C.c_int64(0), C.c_int64(0)
+    P = lib().or_tag_from(C.byref(_grid(spec)), C.byref(_shape(shape)), C.byref(_grid(coarse_spec)),
+                          _p(np.ascontiguousarray(c_cell_pkg, np.int32)), _p(np.ascontiguousarray(c_pkg_type, np.uint8)),
+                          _p(_f64(c_phi)), _p(cell_pkg), _p(cell_type), C.byref(ties), C.byref(ev))
+    return cell_pkg, cell_type, int(P), int(ties.value), int(ev.value)
 
 
 def tables(spec, cell_pkg, cell_type, P):
@@ -323,6 +337,34 @@ def surrogate_class(spec, nbr, phi32):
     lib().or_surrogate_class(C.byref(_grid(spec)), C.c_int64(P), _p(np.ascontiguousarray(nbr, np.int32)),
                              _p(phi32), _p(cls))
     return cls
+
+
+def coarser(spec):
+    """The layer below spec: same lo, half the dims, twice the spacing."""
+    import sg_inputs as si
+    assert all(int(d) % 2 == 0 for d in spec.dims)
+    return si.GridSpec(tuple(spec.lo), tuple(int(d) // 2 for d in spec.dims), 2.0 * spec.h)
+
+
+def build_layers(spec, shape, layers):
+    """Multi-resolution stack, coarsest first: layer 0 tagged in full, every
+    finer layer tagged from the one below it.  Returns a list of namespaces
+    (as build_grid, plus `evaluated`)."""
+    specs = [spec]
+    for _ in range(layers - 1):
+        specs.append(coarser(specs[-1]))
+    specs.reverse()
+    out = [build_grid(specs[0], shape)]
+    out[0].evaluated = specs[0].n_cells
+    for sp in specs[1:]:
+        c = out[-1]
+        cell_pkg, cell_type, P, ties, ev = tag_from(sp, shape, c.spec, c.cell_pkg, c.pkg_type, c.phi)
+        pkg_cell, pkg_type, nbr = tables(sp, cell_pkg, cell_type, P)
+        phi = init_sdf(sp, shape, P, pkg_cell)
+        out.append(types.SimpleNamespace(spec=sp, shape=shape, P=P, near_ties=ties, cell_pkg=cell_pkg,
+                                         cell_type=cell_type, pkg_cell=pkg_cell, pkg_type=pkg_type, nbr=nbr,
+                                         phi=phi, evaluated=ev))
+    return out
 
 
 def build_grid(spec, shape, far=None):

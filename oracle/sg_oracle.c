@@ -169,6 +169,8 @@ void or_sdf_many(const or_shape *s, int64_t n, const double *x, const double *y,
  * near_ties receives the number of cells with ||d| - T| < 1e-9 lc, where
  * float-float evaluation might decide differently.
  */
+static int64_t tag_inner_and_ids(const or_grid *g, int32_t *cell_pkg, uint8_t *cell_type);
+
 int64_t or_tag(const or_grid *g, const or_shape *s, int32_t *cell_pkg, uint8_t *cell_type, int64_t *near_ties) {
     const int64_t nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
     const int64_t nc = nx * ny * nz;
@@ -186,6 +188,15 @@ int64_t or_tag(const or_grid *g, const or_shape *s, int32_t *cell_pkg, uint8_t *
         cell_type[c] = fabs(d[c]) < T ? 2 : (d[c] < 0.0 ? 0 : 1);
         if (fabs(fabs(d[c]) - T) < 1e-9 * lc) ties++;
     }
+    free(d);
+    if (near_ties) *near_ties = ties;
+    return tag_inner_and_ids(g, cell_pkg, cell_type);
+}
+
+/* Steps 2-3 of the tagging on classified cells: inner cells and package ids. */
+static int64_t tag_inner_and_ids(const or_grid *g, int32_t *cell_pkg, uint8_t *cell_type) {
+    const int64_t nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
+    const int64_t nc = nx * ny * nz;
 #pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < nc; ++c) {
         if (cell_type[c] == 2) continue;
@@ -207,9 +218,47 @@ int64_t or_tag(const or_grid *g, const or_shape *s, int32_t *cell_pkg, uint8_t *
         else
             cell_pkg[c] = cell_type[c]; /* 0 inside, 1 outside */
     }
-    free(d);
-    if (near_ties) *near_ties = ties;
     return next;
+}
+
+/*
+ * Tagging of a finer layer from its coarser one ("Multi-resolution
+ * Level-set", step 1 of "Initialization Process": for successive layers only
+ * the cells covered by the coarse core cells are evaluated).  The coarse
+ * layer gc has the same lo, half the dims and twice the spacing.  A fine
+ * cell inside a coarse core cell is classified by its own distance as in
+ * or_tag; any other fine cell is far, inside when its coarse cell is far
+ * inside or is an inner cell whose level set (data point 0) is negative.
+ * evaluated receives the number of distance evaluations.
+ */
+int64_t or_tag_from(const or_grid *g, const or_shape *s, const or_grid *gc, const int32_t *c_cell_pkg,
+                    const uint8_t *c_pkg_type, const double *c_phi, int32_t *cell_pkg, uint8_t *cell_type,
+                    int64_t *near_ties, int64_t *evaluated) {
+    const int64_t nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
+    const int64_t nc = nx * ny * nz, cnx = gc->dims[0], cny = gc->dims[1];
+    const double lc = 4.0 * g->h;
+    const double T = lc * (1.0 - ldexp(1.0, -10));
+    int64_t ties = 0, evals = 0;
+#pragma omp parallel for schedule(static) reduction(+ : ties, evals)
+    for (int64_t c = 0; c < nc; ++c) {
+        int64_t I = c % nx, J = (c / nx) % ny, K = c / (nx * ny);
+        const int64_t pc = c_cell_pkg[(I / 2) + cnx * ((J / 2) + cny * (K / 2))];
+        if (pc >= 2 && c_pkg_type[pc] == 2) {
+            double x = g->lo[0] + (4.0 * (double)I + 2.0) * g->h;
+            double y = g->lo[1] + (4.0 * (double)J + 2.0) * g->h;
+            double z = g->lo[2] + (4.0 * (double)K + 2.0) * g->h;
+            const double d = or_sdf(s, x, y, z);
+            cell_type[c] = fabs(d) < T ? 2 : (d < 0.0 ? 0 : 1);
+            if (fabs(fabs(d) - T) < 1e-9 * lc) ties++;
+            evals++;
+        } else {
+            const int inside = pc < 2 ? pc == 0 : c_phi[pc * PKG3] < 0.0;
+            cell_type[c] = inside ? 0 : 1;
+        }
+    }
+    if (near_ties) *near_ties = ties;
+    if (evaluated) *evaluated = evals;
+    return tag_inner_and_ids(g, cell_pkg, cell_type);
 }
 
 /*
