@@ -349,6 +349,46 @@ def consistency_section(sg, torch, reps=3, frac=0.2, seed=17):
             "point_sweep_updates_per_s": n_pt * out[2] / (t * 1e-3)}
 
 
+def multires_section(sg, torch, reps=3):
+    """Multi-resolution initialisation of the shelled sphere at h = 1/1024:
+    a stack of six layers from 8^3 coarse cells, each tagged from the one
+    below (distances only under coarse core cells) and initialised, against
+    tagging and initialising the finest layer in full.  Both include grid
+    creation; times are wall-clock around synchronised device work."""
+    shape, spec = si.shelled_sphere()
+    L = sg.multires_layers(spec)
+
+    def stack():
+        M = sg.MultiResolution(spec, shape, layers=L)
+        torch.cuda.synchronize()
+        return M
+
+    def full():
+        g = sg.Grid(spec)
+        g.tag_allocate(shape)
+        g.init_sdf(shape)
+        torch.cuda.synchronize()
+        return g
+
+    out = {}
+    for name, fn in (("layers", stack), ("full", full)):
+        fn().close()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            obj = fn()
+            ts.append(time.perf_counter() - t0)
+            if name == "layers":
+                M = obj
+                out["evaluated"] = M.evaluated
+                out["packages"] = [g.P for g in M.grids]
+            obj.close()
+        out[name + "_ms"] = 1e3 * min(ts)
+    return {"workload": "shelled sphere (centre 0.5, radii 0.3 / 0.31) at h = 1/1024, %d layers" % L,
+            "layers": L, "cells_finest": spec.n_cells, **out,
+            "distance_evaluations_layers": int(sum(out["evaluated"])), "distance_evaluations_full": spec.n_cells}
+
+
 def sort_segments(grids, X, offsets):
     """Input preparation: each body's segment of the device particles X put in
     its Morton order (the walk order of the relaxation)."""
@@ -612,6 +652,8 @@ def run_sg(args):
                 r = table1_section(sg, torch)
             elif args.only == "consistency":
                 r = consistency_section(sg, torch)
+            elif args.only == "multires":
+                r = multires_section(sg, torch)
             else:
                 r = batch_section(sg, torch)
             print(json.dumps({"section": args.only, args.only: r}), flush=True)
@@ -753,6 +795,8 @@ def run_sg(args):
     line["table1"] = table1_section(sg, torch)
     if not args.no_consistency:
         line["consistency"] = consistency_section(sg, torch)
+    if not args.no_multires:
+        line["multires"] = multires_section(sg, torch)
     if not args.no_batch:
         line["batch"] = batch_section(sg, torch)
     net = None
@@ -798,7 +842,8 @@ def main(argv=None):
     ap.add_argument("--relax-particles", type=int, default=100_000_000)
     ap.add_argument("--relax-bodies", type=int, default=64)
     ap.add_argument("--no-consistency", action="store_true", help="skip the sign-correction measurement")
-    ap.add_argument("--only", choices=["relax", "table1", "batch", "consistency"],
+    ap.add_argument("--no-multires", action="store_true", help="skip the multi-resolution measurement")
+    ap.add_argument("--only", choices=["relax", "table1", "batch", "consistency", "multires"],
                     help="run one side measurement alone and print it (no headline line)")
     args = ap.parse_args(argv)
     if args.impl == "reference":

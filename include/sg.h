@@ -144,6 +144,31 @@ SG_API sg_status sg_destroy(sg_grid *g);
  * May be called again to re-tag; previous field contents are discarded. */
 SG_API sg_status sg_tag_allocate(sg_grid *g, const sg_shape *shape, int64_t *n_packages);
 
+/* Multi-resolution tagging (Sec. "Multi-resolution Level-set", and step 1
+ * of "Initialization Process": for successive layers only the cells covered
+ * by the coarse core cells are evaluated).  `coarse` is the layer below g:
+ * same lo, half the dims, exactly twice the spacing, tagged and initialised.
+ * A cell of g inside a coarse core cell is classified by its own distance
+ * exactly as sg_tag_allocate does; any other cell is far, inside when its
+ * coarse cell is far inside or an inner cell whose phi (data point 0) is
+ * negative.  Such a cell lies at least 1.13 cells of g from the surface, so
+ * the result equals sg_tag_allocate on g bit for bit, with distances
+ * evaluated only under coarse core cells.  n_packages as sg_tag_allocate;
+ * evaluated (may be NULL) receives the number of cells whose distance was
+ * evaluated.  Synchronises like sg_tag_allocate.
+ * Errors: SG_ERR_INVALID (null or mismatched coarse layer, bad shape),
+ * SG_ERR_STATE (coarse layer without phi), SG_ERR_OOM, SG_ERR_CAPACITY. */
+SG_API sg_status sg_tag_allocate_from(sg_grid *g, const sg_grid *coarse, const sg_shape *shape, int64_t *n_packages,
+                                      int64_t *evaluated);
+
+/* The number of layers of a multi-resolution stack ending at `finest` (the
+ * paper computes it in advance): 1 + the number of halvings of the
+ * background mesh that keep every dimension even before halving and at
+ * least min_dims after it.  Host-only arithmetic; 0 for NULL or
+ * min_dims < 1.  Layer k (0 coarsest) has spacing h 2^(L-1-k) and dims
+ * dims / 2^(L-1-k) over the same domain. */
+SG_API int32_t sg_multires_layers(const sg_grid_desc *finest, int32_t min_dims);
+
 /* Level-set values ("Initialization Process", step 4): phi at the
  * cell-centred data points lo + (4I + i + 0.5) h, evaluated in float-float
  * and rounded once; far packages hold -F and +F.  Requires a tagged grid. */

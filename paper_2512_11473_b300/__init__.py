@@ -92,6 +92,9 @@ def lib():
         L.sg_laplacian.argtypes = [vp]
         L.sg_sequential_update.argtypes = [vp, C.c_float]
         L.sg_consistency_correct.argtypes = [vp, C.c_float, C.POINTER(i64)]
+        L.sg_tag_allocate_from.argtypes = [vp, vp, C.POINTER(sg_shape), C.POINTER(i64), C.POINTER(i64)]
+        L.sg_multires_layers.argtypes = [C.POINTER(sg_grid_desc), i32]
+        L.sg_multires_layers.restype = i32
         L.sg_reinit.argtypes = [vp, i32, C.c_float]
         L.sg_kernel_integrals.argtypes = [vp, i32, vp]
         L.sg_probe.argtypes = [vp, i64, vp, vp, vp] + [vp] * 8 + [i32]
@@ -256,6 +259,15 @@ class Grid:
         self._check(self._lib.sg_tag_allocate(self._h, C.byref(_as_shape(shape)), C.byref(n)))
         self.P = int(n.value)
         return self.P
+
+    def tag_allocate_from(self, coarse, shape):
+        """Tag this layer from its coarser layer (see sg_tag_allocate_from).
+        Returns (P, cells whose distance was evaluated)."""
+        n, ev = C.c_int64(0), C.c_int64(0)
+        self._check(self._lib.sg_tag_allocate_from(self._h, coarse.handle, C.byref(_as_shape(shape)), C.byref(n),
+                                                   C.byref(ev)))
+        self.P = int(n.value)
+        return self.P, int(ev.value)
 
     def init_sdf(self, shape):
         self._check(self._lib.sg_init_sdf(self._h, C.byref(_as_shape(shape))))
@@ -533,6 +545,50 @@ def _desc(spec, far_value=0.0) -> sg_grid_desc:
     d.h = float(spec.h)
     d.far_value = float(far_value)
     return d
+
+
+def multires_layers(spec, min_dims=8) -> int:
+    """Layer count of a multi-resolution stack ending at spec (sg_multires_layers)."""
+    return int(lib().sg_multires_layers(C.byref(_desc(spec)), int(min_dims)))
+
+
+def layer_spec(spec, level, layers):
+    """Grid spec of layer `level` (0 coarsest) of a stack of `layers` ending at spec."""
+    import sg_inputs as si
+    k = layers - 1 - level
+    f = 1 << k
+    assert all(int(d) % f == 0 for d in spec.dims)
+    return si.GridSpec(tuple(spec.lo), tuple(int(d) // f for d in spec.dims), spec.h * f)
+
+
+class MultiResolution:
+    """A stack of grids over one domain, each doubling the resolution of the
+    one below ("Multi-resolution Level-set"): the coarsest layer is tagged in
+    full, every finer layer from the layer below it; each is initialised.
+    layers defaults to multires_layers(spec, min_dims)."""
+
+    def __init__(self, spec, shape, layers=None, min_dims=8, stream=None):
+        self.layers = int(layers) if layers else multires_layers(spec, min_dims)
+        self.grids, self.evaluated = [], []
+        for k in range(self.layers):
+            g = Grid(layer_spec(spec, k, self.layers), stream=stream)
+            if k == 0:
+                g.tag_allocate(shape)
+                ev = g.spec.n_cells
+            else:
+                _, ev = g.tag_allocate_from(self.grids[-1], shape)
+            g.init_sdf(shape)
+            self.grids.append(g)
+            self.evaluated.append(int(ev))
+
+    @property
+    def finest(self):
+        return self.grids[-1]
+
+    def close(self):
+        for g in self.grids:
+            g.close()
+        self.grids = []
 
 
 def morton_order_noalloc(spec, x, y, z, keys=None, order=None, stream=None):

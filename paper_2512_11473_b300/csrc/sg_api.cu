@@ -220,13 +220,14 @@ int64_t sg_n_packages(const sg_grid* g) { return g ? g->P : 0; }
 
 const char* sg_last_error(const sg_grid* g) { return g ? g->last_error.c_str() : "null grid"; }
 
-sg_status sg_tag_allocate(sg_grid* g, const sg_shape* shape, int64_t* n_packages) {
-    SG_CHECK_GRID(g);
-    if (!valid_shape(shape)) return fail(g, SG_ERR_INVALID, "sg_tag_allocate: bad shape");
-    DeviceGuard dg(g->device);
+}  // extern "C"
+
+// Tagging steps 1-5; `flags` launches step 1 (core cells and far sides) into
+// (cell_type, active) on the grid's stream.
+template <class Flags>
+static sg_status tag_common(sg_grid* g, Flags flags, int64_t* n_packages) {
     const int64_t nc = g->nc;
     const GridFF G = grid_ff(g);
-    const ShapeFF S = shape_ff(shape);
     const size_t act_bytes = ((size_t)nc * 4 + 255) & ~(size_t)255;
     if (!ensure(g, g->cell_type, (size_t)nc) || !ensure(g, g->cell_pkg, (size_t)nc * 4) ||
         !ensure(g, g->scratch, act_bytes + scan_scratch_bytes(nc) + 256))
@@ -235,7 +236,7 @@ sg_status sg_tag_allocate(sg_grid* g, const sg_shape* shape, int64_t* n_packages
     uint32_t* total = (uint32_t*)((char*)g->scratch.p + act_bytes);
     void* scan_scratch = (char*)g->scratch.p + act_bytes + 256;
     uint8_t* ct = (uint8_t*)g->cell_type.p;
-    SG_CUDA(g, launch_tag_flags(G, S, ct, active, nc, g->stream), "tag flags");
+    SG_CUDA(g, flags(ct, active), "tag flags");
     SG_CUDA(g, launch_tag_inner(G, ct, active, nc, g->stream), "tag inner");
     SG_CUDA(g, exclusive_scan_u32(active, active, nc, total, scan_scratch, g->stream), "tag scan");
     SG_CUDA(g, cudaMemcpyAsync(g->host_pin.p, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream), "tag count");
@@ -261,6 +262,73 @@ sg_status sg_tag_allocate(sg_grid* g, const sg_shape* shape, int64_t* n_packages
     g->state = 1;
     if (n_packages) *n_packages = P;
     return SG_OK;
+}
+
+extern "C" {
+
+sg_status sg_tag_allocate(sg_grid* g, const sg_shape* shape, int64_t* n_packages) {
+    SG_CHECK_GRID(g);
+    if (!valid_shape(shape)) return fail(g, SG_ERR_INVALID, "sg_tag_allocate: bad shape");
+    DeviceGuard dg(g->device);
+    const GridFF G = grid_ff(g);
+    const ShapeFF S = shape_ff(shape);
+    return tag_common(
+        g, [&](uint8_t* ct, uint32_t* active) { return launch_tag_flags(G, S, ct, active, g->nc, g->stream); },
+        n_packages);
+}
+
+sg_status sg_tag_allocate_from(sg_grid* g, const sg_grid* coarse, const sg_shape* shape, int64_t* n_packages,
+                               int64_t* evaluated) {
+    SG_CHECK_GRID(g);
+    if (!coarse || coarse == g) return fail(g, SG_ERR_INVALID, "sg_tag_allocate_from: no coarse layer");
+    if (!valid_shape(shape)) return fail(g, SG_ERR_INVALID, "sg_tag_allocate_from: bad shape");
+    if (coarse->state < 2 || !coarse->field[SG_FIELD_PHI].p)
+        return fail(g, SG_ERR_STATE, "sg_tag_allocate_from: coarse layer not initialised");
+    if (coarse->device != g->device) return fail(g, SG_ERR_INVALID, "sg_tag_allocate_from: layers on two devices");
+    bool match = coarse->desc.h == 2.0 * g->desc.h;
+    for (int a = 0; a < 3; ++a)
+        match &= coarse->desc.lo[a] == g->desc.lo[a] && 2LL * coarse->desc.dims[a] == (int64_t)g->desc.dims[a];
+    if (!match) return fail(g, SG_ERR_INVALID, "sg_tag_allocate_from: coarse layer is not this grid halved");
+    DeviceGuard dg(g->device);
+    const GridFF G = grid_ff(g);
+    const ShapeFF S = shape_ff(shape);
+    // the evaluation counter sits in the tagging scratch, beside the package count
+    const size_t act_bytes = ((size_t)g->nc * 4 + 255) & ~(size_t)255;
+    unsigned long long* ev = nullptr;
+    const sg_status st = tag_common(
+        g,
+        [&](uint8_t* ct, uint32_t* active) {
+            ev = (unsigned long long*)((char*)g->scratch.p + act_bytes + 128);
+            cudaError_t e = cudaMemsetAsync(ev, 0, sizeof(unsigned long long), g->stream);
+            if (e != cudaSuccess) return e;
+            return launch_tag_flags_from(G, S, (const int32_t*)coarse->cell_pkg.p, (const uint8_t*)coarse->pkg_type.p,
+                                         (const float*)coarse->field[SG_FIELD_PHI].p, coarse->desc.dims[0],
+                                         coarse->desc.dims[1], ct, active, g->nc, ev, g->stream);
+        },
+        n_packages);
+    if (st != SG_OK) return st;
+    if (evaluated) {
+        SG_CUDA(g, cudaMemcpyAsync((char*)g->host_pin.p + 128, ev, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                   g->stream),
+                "tag counter");
+        SG_CUDA(g, cudaStreamSynchronize(g->stream), "tag counter");
+        *evaluated = (int64_t)*(unsigned long long*)((char*)g->host_pin.p + 128);
+    }
+    return SG_OK;
+}
+
+int32_t sg_multires_layers(const sg_grid_desc* finest, int32_t min_dims) {
+    if (!finest || min_dims < 1) return 0;
+    int32_t L = 1;
+    int64_t d[3] = {finest->dims[0], finest->dims[1], finest->dims[2]};
+    for (;;) {
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) ok &= d[a] % 2 == 0 && d[a] / 2 >= min_dims;
+        if (!ok) break;
+        for (int a = 0; a < 3; ++a) d[a] /= 2;
+        ++L;
+    }
+    return L;
 }
 
 sg_status sg_init_sdf(sg_grid* g, const sg_shape* shape) {

@@ -92,6 +92,9 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uin
 // tagging / init (sg_tag.cu)
 cudaError_t launch_tag_flags(const GridFF& G, const ShapeFF& S, uint8_t* cell_type, uint32_t* active, int64_t nc,
                              cudaStream_t s);
+cudaError_t launch_tag_flags_from(const GridFF& G, const ShapeFF& S, const int32_t* c_cell_pkg,
+                                  const uint8_t* c_pkg_type, const float* c_phi, int cnx, int cny, uint8_t* cell_type,
+                                  uint32_t* active, int64_t nc, unsigned long long* evaluated, cudaStream_t s);
 cudaError_t launch_tag_inner(const GridFF& G, uint8_t* cell_type, uint32_t* active, int64_t nc, cudaStream_t s);
 cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* prefix, int32_t* cell_pkg,
                                int32_t* pkg_cell, uint8_t* pkg_type, int64_t nc, cudaStream_t s);

@@ -23,34 +23,66 @@ __device__ __forceinline__ void cell_coords(int64_t c, const int* dims, int64_t&
 // from both T and 0 in magnitude, the float decision stands (the float error
 // of these formulas is below 1e-6 (1 + |x|), the margin is 1.5e-4 (1 + |x|)),
 // otherwise it is decided on the float-float distance.
+__device__ __forceinline__ uint8_t classify_cell(const GridFF& G, const ShapeFF& S, const int64_t (&I)[3]) {
+    const float Tf = G.T.hi;
+    float xf[3];
+    float xmax = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        xf[a] = G.lo[a].hi + G.h.hi * (float)(4 * I[a] + 2);
+        xmax = fmaxf(xmax, fabsf(xf[a]));
+    }
+    const float df = f_sdf(S, xf);
+    const float margin = 1.5e-4f * (1.0f + xmax);
+    if (fabsf(fabsf(df) - Tf) > margin && fabsf(df) > margin) return fabsf(df) < Tf ? 2 : (df < 0.0f ? 0 : 1);
+    ff x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = ff_add(G.lo[a], ff_mul_f(G.h, (float)(4 * I[a] + 2)));
+    const ff d = ff_sdf(S, x);
+    return ff_lt(ff_abs(d), G.T) ? 2 : (ff_neg_p(d) ? 0 : 1);
+}
+
 __global__ void __launch_bounds__(TAG_THREADS) k_tag_flags(GridFF G, ShapeFF S, uint8_t* __restrict__ cell_type,
                                                             uint32_t* __restrict__ active, int64_t nc) {
-    const float Tf = G.T.hi;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         int64_t I[3];
         cell_coords(c, G.dims, I[0], I[1], I[2]);
-        float xf[3];
-        float xmax = 0.0f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            xf[a] = G.lo[a].hi + G.h.hi * (float)(4 * I[a] + 2);
-            xmax = fmaxf(xmax, fabsf(xf[a]));
-        }
-        const float df = f_sdf(S, xf);
-        const float margin = 1.5e-4f * (1.0f + xmax);
+        const uint8_t t = classify_cell(G, S, I);
+        cell_type[c] = t;
+        active[c] = t == 2;
+    }
+}
+
+// Step 1 of a finer layer ("Multi-resolution Level-set"): only the cells
+// covered by a core cell of the coarser layer (same lo, half the dims, twice
+// the spacing) evaluate their distance; every other cell is far, inside when
+// its coarse cell is far inside or is an inner cell whose level set (data
+// point 0) is negative.  A fine cell inside a coarse cell that is not core
+// lies at least 1.13 fine cells from the surface, so it cannot be core.
+__global__ void __launch_bounds__(TAG_THREADS) k_tag_flags_from(GridFF G, ShapeFF S, const int32_t* __restrict__ c_cell_pkg,
+                                                                 const uint8_t* __restrict__ c_pkg_type,
+                                                                 const float* __restrict__ c_phi, int cnx, int cny,
+                                                                 uint8_t* __restrict__ cell_type,
+                                                                 uint32_t* __restrict__ active, int64_t nc,
+                                                                 unsigned long long* __restrict__ evaluated) {
+    unsigned long long ev = 0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t I[3];
+        cell_coords(c, G.dims, I[0], I[1], I[2]);
+        const int64_t pc = __ldg(c_cell_pkg + (I[0] >> 1) + cnx * ((I[1] >> 1) + (int64_t)cny * (I[2] >> 1)));
         uint8_t t;
-        if (fabsf(fabsf(df) - Tf) > margin && fabsf(df) > margin) {
-            t = fabsf(df) < Tf ? 2 : (df < 0.0f ? 0 : 1);
+        if (pc >= 2 && __ldg(c_pkg_type + pc) == 2) {
+            t = classify_cell(G, S, I);
+            ++ev;
         } else {
-            ff x[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) x[a] = ff_add(G.lo[a], ff_mul_f(G.h, (float)(4 * I[a] + 2)));
-            const ff d = ff_sdf(S, x);
-            t = ff_lt(ff_abs(d), G.T) ? 2 : (ff_neg_p(d) ? 0 : 1);
+            t = (pc < 2 ? pc == 0 : __ldg(c_phi + pc * PKG3) < 0.0f) ? 0 : 1;
         }
         cell_type[c] = t;
         active[c] = t == 2;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(0xffffffffu, ev, o);
+    if ((threadIdx.x & 31) == 0 && ev) atomicAdd(evaluated, ev);
 }
 
 // Step 2: inner cells, not core and one of the 26 neighbours is core.
@@ -162,6 +194,15 @@ unsigned grid_for(int64_t n, int threads) {
 cudaError_t launch_tag_flags(const GridFF& G, const ShapeFF& S, uint8_t* cell_type, uint32_t* active, int64_t nc,
                              cudaStream_t s) {
     k_tag_flags<<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, cell_type, active, nc);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tag_flags_from(const GridFF& G, const ShapeFF& S, const int32_t* c_cell_pkg,
+                                  const uint8_t* c_pkg_type, const float* c_phi, int cnx, int cny, uint8_t* cell_type,
+                                  uint32_t* active, int64_t nc, unsigned long long* evaluated, cudaStream_t s) {
+    k_tag_flags_from<<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, c_cell_pkg, c_pkg_type, c_phi, cnx, cny,
+                                                                       cell_type, active, nc, evaluated);
     note_launch();
     return cudaGetLastError();
 }
