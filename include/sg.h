@@ -247,7 +247,10 @@ SG_API sg_status sg_kernel_integrals(sg_grid *g, int32_t mode, const void *mlp);
  * grad/|grad| (0 where |grad| = 0).  Fields not yet computed read as 0.
  * With SG_PROBE_MORTON the particles are walked in Morton order (stable
  * sort by the bit interleave of k_a = clamp(i0_a + 1, 0, 4 dims_a + 1), x in
- * the lowest bit) and results are written back in input order.
+ * the lowest bit) and results are written back in input order; an input
+ * whose sampled adjacent pairs (every 16th) are already in that order is
+ * walked as it is.  The walk only affects speed: the results are the same
+ * for any order.
  * Errors: SG_ERR_INVALID (n < 0, null positions), SG_ERR_CAPACITY
  * (n >= 2^31).  Requires phi. */
 SG_API sg_status sg_probe(sg_grid *g, int64_t n, const float *x, const float *y, const float *z, float *phi, float *nx,

@@ -493,7 +493,9 @@ sg_status sg_probe(sg_grid* g, int64_t n, const float* x, const float* y, const 
         size_t ob = ((size_t)n * 4 + 255) & ~(size_t)255;
         if (!ensure(g, g->scratch, sb + ob)) return fail(g, SG_ERR_OOM, "sg_probe: out of memory");
         int32_t* ord = (int32_t*)((char*)g->scratch.p + sb);
-        SG_CUDA(g, morton_sort(G, n, x, y, z, nullptr, ord, g->scratch.p, g->stream, false, &unsorted), "probe sort");
+        // results do not depend on the walk: a sampled check decides whether the input is walked as it is
+        SG_CUDA(g, morton_sort(G, n, x, y, z, nullptr, ord, g->scratch.p, g->stream, false, &unsorted, 16),
+                "probe sort");
         order = ord;
     }
     SG_CUDA(g, launch_probe(G, (const int32_t*)g->cell_pkg.p, (const int32_t*)g->nbr.p, F, n, x, y, z, order, unsorted,

@@ -161,9 +161,11 @@ size_t sort_scratch_bytes(int64_t n, int key_bits);
 // non-decreasing; if so the radix passes return at once and order_out is
 // the identity (written only when identity_out, else left to the caller,
 // who reads the device flag *unsorted_out: 0 = input already in order).
+// check_stride > 1: the sortedness check compares only every check_stride-th
+// adjacent pair (for callers to whom the order is a matter of speed only).
 cudaError_t morton_sort(const GridF& G, int64_t n, const float* x, const float* y, const float* z, uint64_t* keys_out,
                         int32_t* order_out, void* scratch, cudaStream_t s, bool identity_out = true,
-                        const int** unsorted_out = nullptr);
+                        const int** unsorted_out = nullptr, int check_stride = 1);
 // Packed probe table of n_points data points ([P][8][64] floats) from the 8
 // fields.
 cudaError_t launch_pack_probe(const ProbeFields& F, float* tab, int64_t n_points, cudaStream_t s);

@@ -65,6 +65,22 @@ __global__ void __launch_bounds__(RS_THREADS) k_morton_check(GridF G, int64_t n,
 
 // Keys and identity indices for the radix passes (skipped when the input is
 // already in order), and the caller's copy of the keys when asked for.
+// Sampled sortedness check: only the pairs (q, q + 1) with q a multiple of
+// `stride` are compared.  Used where the walk order is a matter of speed
+// only (the probe): an input that passes is walked as it is.
+__global__ void __launch_bounds__(RS_THREADS) k_morton_check_sampled(GridF G, int64_t n, const float* __restrict__ x,
+                                                                     const float* __restrict__ y,
+                                                                     const float* __restrict__ z, int stride,
+                                                                     int* unsorted) {
+    const int64_t pairs = (n - 1 + stride - 1) / stride;
+    bool bad = false;
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < pairs; m += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = m * stride;
+        bad |= morton_key(G, x[q], y[q], z[q]) > morton_key(G, x[q + 1], y[q + 1], z[q + 1]);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(unsorted, 1);
+}
+
 template <typename KeyT>
 __global__ void __launch_bounds__(RS_THREADS) k_morton_keys(GridF G, int64_t n, const float* __restrict__ x,
                                                             const float* __restrict__ y, const float* __restrict__ z,
@@ -243,7 +259,7 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 template <typename KeyT>
 cudaError_t sort_impl(const GridF& G, int64_t n, int key_bits, const float* x, const float* y, const float* z,
                       uint64_t* keys_out, int32_t* order_out, void* scratch, cudaStream_t s, bool identity_out,
-                      const int** unsorted_out) {
+                      const int** unsorted_out, int check_stride) {
     const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
     char* sp = (char*)scratch;
     int* unsorted = (int*)sp;
@@ -262,7 +278,11 @@ cudaError_t sort_impl(const GridF& G, int64_t n, int key_bits, const float* x, c
 
     cudaError_t e = cudaMemsetAsync(unsorted, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k_morton_check<<<blocks_for(n, RS_THREADS), RS_THREADS, 0, s>>>(G, n, x, y, z, unsorted);
+    if (check_stride > 1)
+        k_morton_check_sampled<<<blocks_for((n + check_stride - 1) / check_stride, RS_THREADS), RS_THREADS, 0, s>>>(
+            G, n, x, y, z, check_stride, unsorted);
+    else
+        k_morton_check<<<blocks_for(n, RS_THREADS), RS_THREADS, 0, s>>>(G, n, x, y, z, unsorted);
     k_morton_keys<KeyT><<<blocks_for(n, RS_THREADS), RS_THREADS, 0, s>>>(G, n, x, y, z, k0, v0, keys_out, unsorted);
     note_launch(2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -319,12 +339,14 @@ size_t sort_scratch_bytes(int64_t n, int key_bits) {
 
 cudaError_t morton_sort(const GridF& G, int64_t n, const float* x, const float* y, const float* z, uint64_t* keys_out,
                         int32_t* order_out, void* scratch, cudaStream_t s, bool identity_out,
-                        const int** unsorted_out) {
+                        const int** unsorted_out, int check_stride) {
     if (n <= 0) return cudaSuccess;
     const int bits = morton_bits(G);
     if (bits <= 32)
-        return sort_impl<uint32_t>(G, n, bits, x, y, z, keys_out, order_out, scratch, s, identity_out, unsorted_out);
-    return sort_impl<uint64_t>(G, n, bits, x, y, z, keys_out, order_out, scratch, s, identity_out, unsorted_out);
+        return sort_impl<uint32_t>(G, n, bits, x, y, z, keys_out, order_out, scratch, s, identity_out, unsorted_out,
+                                   check_stride);
+    return sort_impl<uint64_t>(G, n, bits, x, y, z, keys_out, order_out, scratch, s, identity_out, unsorted_out,
+                               check_stride);
 }
 
 cudaError_t launch_pack_probe(const ProbeFields& F, float* tab, int64_t n_points, cudaStream_t s) {
