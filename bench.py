@@ -389,6 +389,52 @@ def multires_section(sg, torch, reps=3):
             "distance_evaluations_layers": int(sum(out["evaluated"])), "distance_evaluations_full": spec.n_cells}
 
 
+def large_section(sg, torch, reps=3):
+    """The bodies at the finer spacings that give about 3M packages each
+    (torus h = 7e-4, prism h = 6e-4): each phase of the per-body chain timed
+    with CUDA events, and the sweeps' achieved bandwidth by algorithmic bytes
+    (reinit: 12 B per point + 32 B per package; gradient: 16 B per point +
+    32 B per package; integrals: 20 B per point + 108 B per package)."""
+    hbm, kind = measured_peaks()
+    Ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn, n=reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = Ev(), Ev()
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    out = {}
+    for name, (shape, spec) in (("torus", si.torus_large(h=7e-4)), ("prism", si.prism_large(h=6e-4))):
+        g = sg.Grid(spec)
+        t_tag = timed(lambda: g.tag_allocate(shape), 1)
+        P = g.P
+        n_pt = 64 * (P - 2)
+        t_init = timed(lambda: g.init_sdf(shape))
+        t_grad = timed(g.gradient)
+        t_r50 = timed(lambda: g.reinit(50, CFL), 1)
+        t_r0 = timed(lambda: g.reinit(0, CFL))
+        t_int = timed(g.kernel_integrals)
+        sweep = (t_r50 - t_r0) / 50
+        r = {"h": spec.h, "packages": P, "points": n_pt, "cells": spec.n_cells, "tag_ms": t_tag, "init_ms": t_init,
+             "gradient_ms": t_grad, "reinit50_ms": t_r50, "reinit_sweep_ms": sweep, "integrals_ms": t_int}
+        for k, ms, b in (("reinit_sweep", sweep, 12 * n_pt + 32 * (P - 2)), ("gradient", t_grad, 16 * n_pt + 32 * (P - 2)),
+                         ("integrals", t_int, 20 * n_pt + 108 * (P - 2))):
+            gbs = b / (ms * 1e-3) / 1e9
+            r[k + "_GBs"] = gbs
+            r[k + "_hbm_frac_of_" + kind] = gbs / hbm
+        r["reinit_cell_updates_per_s"] = n_pt / (sweep * 1e-3)
+        out[name] = r
+        g.close()
+    return {"workload": "torus (R 0.6, r 0.2) at h = 7e-4 and prism at h = 6e-4: tag, init, gradient, 50 reinit "
+                        "sweeps, exact integrals, per phase", **out}
+
+
 def sort_segments(grids, X, offsets):
     """Input preparation: each body's segment of the device particles X put in
     its Morton order (the walk order of the relaxation)."""
@@ -654,6 +700,8 @@ def run_sg(args):
                 r = consistency_section(sg, torch)
             elif args.only == "multires":
                 r = multires_section(sg, torch)
+            elif args.only == "large":
+                r = large_section(sg, torch)
             else:
                 r = batch_section(sg, torch)
             print(json.dumps({"section": args.only, args.only: r}), flush=True)
@@ -797,6 +845,8 @@ def run_sg(args):
         line["consistency"] = consistency_section(sg, torch)
     if not args.no_multires:
         line["multires"] = multires_section(sg, torch)
+    if not args.no_large:
+        line["large"] = large_section(sg, torch)
     if not args.no_batch:
         line["batch"] = batch_section(sg, torch)
     net = None
@@ -843,7 +893,8 @@ def main(argv=None):
     ap.add_argument("--relax-bodies", type=int, default=64)
     ap.add_argument("--no-consistency", action="store_true", help="skip the sign-correction measurement")
     ap.add_argument("--no-multires", action="store_true", help="skip the multi-resolution measurement")
-    ap.add_argument("--only", choices=["relax", "table1", "batch", "consistency", "multires"],
+    ap.add_argument("--no-large", action="store_true", help="skip the ~3M-package bodies")
+    ap.add_argument("--only", choices=["relax", "table1", "batch", "consistency", "multires", "large"],
                     help="run one side measurement alone and print it (no headline line)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
