@@ -4,10 +4,11 @@
 //
 // Face stencils: a half-warp owns one package and each lane one row of four
 // x-values (float4, row r = j + 4k).  x neighbours inside the row are in
-// registers; rows j +- 1 and k +- 1 come from lanes r -+ 1 and r -+ 4 by warp
-// shuffles; across a package face the neighbour package named by the
-// 27-entry table (Listing 2) supplies one value (x faces) or one row (y, z
-// faces).  The six face ids are read by six lanes and broadcast by shuffles.
+// registers; rows j +- 1 and k +- 1 are 16-byte loads of the package's own
+// rows (served by L1 once the half-warp has read the package); across a
+// package face the neighbour package named by the 27-entry table (Listing 2,
+// kept as a 32-byte face row) supplies one value (x faces) or one row (y, z
+// faces).
 //
 // Kernel integrals: 64 threads own a package, stage the smoothed Heaviside of
 // a 6^3 tile (package plus a one-point halo, reached by the index shift) in
@@ -30,7 +31,6 @@ KernelCoef kernel_coef();
 
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
 
 // Listing 2: shift s per axis in [-4, 7] -> (package, data index)
 __device__ __forceinline__ int64_t shift_index(const int* nb27, int sx, int sy, int sz) {
@@ -40,21 +40,6 @@ __device__ __forceinline__ int64_t shift_index(const int* nb27, int sx, int sy, 
     return (int64_t)pkg * PKG3 + dx + PKG * dy + PKG * PKG * dz;
 }
 
-__device__ __forceinline__ float4 shfl_up4(float4 v, int d) {
-    v.x = __shfl_up_sync(FULL, v.x, d, 16);
-    v.y = __shfl_up_sync(FULL, v.y, d, 16);
-    v.z = __shfl_up_sync(FULL, v.z, d, 16);
-    v.w = __shfl_up_sync(FULL, v.w, d, 16);
-    return v;
-}
-
-__device__ __forceinline__ float4 shfl_down4(float4 v, int d) {
-    v.x = __shfl_down_sync(FULL, v.x, d, 16);
-    v.y = __shfl_down_sync(FULL, v.y, d, 16);
-    v.z = __shfl_down_sync(FULL, v.z, d, 16);
-    v.w = __shfl_down_sync(FULL, v.w, d, 16);
-    return v;
-}
 
 __device__ __forceinline__ float get(const float4& v, int i) {
     return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
@@ -94,30 +79,33 @@ __device__ __forceinline__ RowSlot make_slot(int64_t p, bool valid) {
 }
 
 // Gather a lane's row and neighbours of field f.  faces[p][8] holds the six
-// face neighbours of package p (-x, +x, -y, +y, -z, +z), one 32-byte row.
-// All lanes of the warp must call this (shuffles); lanes of an invalid
-// package get zeros.
+// face neighbours of package p (-x, +x, -y, +y, -z, +z), one 32-byte row
+// read by every lane of the half-warp (one broadcast transaction).  Rows
+// j +- 1 and k +- 1 are loaded from the package itself (L1 hits: the
+// half-warp reads the whole package) or, on its boundary, from the face
+// neighbour; each lane also takes one value from the -x and +x packages.
+// Lanes of an invalid package get zeros.
 __device__ __forceinline__ Rows load_rows(const float* __restrict__ f, const int32_t* __restrict__ faces,
                                           const RowSlot& s) {
-    const int lane = threadIdx.x & 31, base = lane & 16;
     const int j = s.r & 3, k = s.r >> 2;
     const float4* __restrict__ f4 = reinterpret_cast<const float4*>(f);
-    int nid = 0;
-    if (s.valid && s.r < 6) nid = __ldg(faces + s.p * 8 + s.r);
     Rows w;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    w.c = s.valid ? __ldg(f4 + s.q4) : zero;
-    const int n_xm = __shfl_sync(FULL, nid, base + 0), n_xp = __shfl_sync(FULL, nid, base + 1);
-    const int n_ym = __shfl_sync(FULL, nid, base + 2), n_yp = __shfl_sync(FULL, nid, base + 3);
-    const int n_zm = __shfl_sync(FULL, nid, base + 4), n_zp = __shfl_sync(FULL, nid, base + 5);
-    w.xm = s.valid ? __ldg(reinterpret_cast<const float*>(f4 + (n_xm * 16 + s.r)) + 3) : 0.f;
-    w.xp = s.valid ? __ldg(reinterpret_cast<const float*>(f4 + (n_xp * 16 + s.r))) : 0.f;
-    const float4 ym = shfl_up4(w.c, 1), yp = shfl_down4(w.c, 1);
-    const float4 zm = shfl_up4(w.c, 4), zp = shfl_down4(w.c, 4);
-    w.ym = j > 0 ? ym : (s.valid ? __ldg(f4 + (n_ym * 16 + s.r + 3)) : zero);
-    w.yp = j < 3 ? yp : (s.valid ? __ldg(f4 + (n_yp * 16 + s.r - 3)) : zero);
-    w.zm = k > 0 ? zm : (s.valid ? __ldg(f4 + (n_zm * 16 + s.r + 12)) : zero);
-    w.zp = k < 3 ? zp : (s.valid ? __ldg(f4 + (n_zp * 16 + s.r - 12)) : zero);
+    if (!s.valid) {
+        w.c = w.ym = w.yp = w.zm = w.zp = zero;
+        w.xm = w.xp = 0.f;
+        return w;
+    }
+    const int4 fa = __ldg(reinterpret_cast<const int4*>(faces + s.p * 8));
+    const int2 fb = __ldg(reinterpret_cast<const int2*>(faces + s.p * 8 + 4));
+    const int q = s.q4;
+    w.c = __ldg(f4 + q);
+    w.xm = __ldg(reinterpret_cast<const float*>(f4 + (fa.x * 16 + s.r)) + 3);
+    w.xp = __ldg(reinterpret_cast<const float*>(f4 + (fa.y * 16 + s.r)));
+    w.ym = __ldg(f4 + (j > 0 ? q - 1 : fa.z * 16 + s.r + 3));
+    w.yp = __ldg(f4 + (j < 3 ? q + 1 : fa.w * 16 + s.r - 3));
+    w.zm = __ldg(f4 + (k > 0 ? q - 4 : fb.x * 16 + s.r + 12));
+    w.zp = __ldg(f4 + (k < 3 ? q + 4 : fb.y * 16 + s.r - 12));
     return w;
 }
 
