@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_reinit_s0(const float* __restric
         s0[2 * PKG3 + e] = smoothed_sign(phi[2 * PKG3 + e], h2);
 }
 
-__global__ void __launch_bounds__(ROW_THREADS) k_reinit_step(const int32_t* __restrict__ faces,
+__global__ void __launch_bounds__(ROW_THREADS, 8) k_reinit_step(const int32_t* __restrict__ faces,
                                                               const float* __restrict__ s0,
                                                               const float* __restrict__ phi_in,
                                                               float* __restrict__ phi_out, int64_t P, float cfl,
