@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(BT) k_batch_integrals(const int32_t* __restric
     __shared__ int s_item;
     __shared__ int s_nb[BT_PK][NB];
     __shared__ float s_H[BT_PK][216];
+    __shared__ unsigned s_sat[BT_PK];
     const int lp = threadIdx.x >> 6, d = threadIdx.x & 63;
     const int64_t per_item = (int64_t)BT_PK * ppi, items = (P + per_item - 1) / per_item;
     for (;;) {
@@ -192,16 +193,19 @@ __global__ void __launch_bounds__(BT) k_batch_integrals(const int32_t* __restric
             const int64_t p = item * per_item + (int64_t)k * BT_PK + lp;
             const bool valid = p < P && __ldg(type + (p < P ? p : 0)) >= 2;
             if (valid && d < NB) s_nb[lp][d] = __ldg(nbr + p * NB + d);
+            if (d == 0) s_sat[lp] = 0;
             __syncthreads();
-            float inv_eps = 0.0f;
+            unsigned bits = 0;
             if (valid) {
-                inv_eps = __ldg(&prm[__ldg(body + p)].inv_eps);
-                integrals_stage(s_nb[lp], phi, inv_eps, d, s_H[lp]);
+                const float inv_eps = __ldg(&prm[__ldg(body + p)].inv_eps);
+                bits = integrals_stage(s_nb[lp], phi, inv_eps, d, s_H[lp]);
             }
+            bits = __reduce_or_sync(0xffffffffu, bits);  // a package is two whole warps
+            if ((threadIdx.x & 31) == 0 && bits) atomicOr(&s_sat[lp], bits);
             __syncthreads();
             if (valid) {
                 float w, ax, ay, az;
-                integrals_point(s_H[lp], d, K, w, ax, ay, az);
+                if (!integrals_saturated(s_sat[lp], w, ax, ay, az)) integrals_point(s_H[lp], d, K, w, ax, ay, az);
                 const int64_t at = p * PKG3 + d;
                 W[at] = w;
                 gx[at] = ax;

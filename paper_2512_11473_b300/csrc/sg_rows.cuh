@@ -182,15 +182,32 @@ __device__ __forceinline__ float heaviside_neg(float phi, float inv_eps) {
 
 // Fill the 6^3 Heaviside tile of package p (64 threads, d = thread index in
 // the package); nb27 holds the package's neighbourhood in shared memory.
-__device__ __forceinline__ void integrals_stage(const int* nb27, const float* __restrict__ phi, float inv_eps,
-                                                int d, float* tile) {
+// Stage the smoothed Heaviside of the package's 6^3 tile; returns the
+// saturation bits of the entries this thread staged: bit 0 unless all were
+// 0, bit 1 unless all were 1 (a tile whose bits OR to 1 is all ones, to 2 all
+// zeros).
+__device__ __forceinline__ unsigned integrals_stage(const int* nb27, const float* __restrict__ phi, float inv_eps,
+                                                    int d, float* tile) {
+    unsigned bits = 0;
     for (int e = d; e < 216; e += PKG3) {
         int x = e % 6 - 1, y = (e / 6) % 6 - 1, z = e / 36 - 1;
-        tile[e] = heaviside_neg(__ldg(phi + shift_index(nb27, x, y, z)), inv_eps);
+        const float hv = heaviside_neg(__ldg(phi + shift_index(nb27, x, y, z)), inv_eps);
+        tile[e] = hv;
+        bits |= (hv != 0.0f ? 1u : 0u) | (hv != 1.0f ? 2u : 0u);
     }
+    return bits;
 }
 
 // The 27 taps around data point d of a staged tile.
+// A saturated tile (every H in it 0, or every H 1) gives W = that value and
+// G = 0 exactly (the normalised weights sum to one): the taps are skipped.
+__device__ __forceinline__ bool integrals_saturated(unsigned tile_bits, float& w, float& ax, float& ay, float& az) {
+    if (tile_bits == 3u) return false;
+    w = tile_bits == 1u ? 1.0f : 0.0f;
+    ax = ay = az = 0.0f;
+    return true;
+}
+
 __device__ __forceinline__ void integrals_point(const float* tile, int d, const KernelCoef& K, float& w,
                                                 float& ax, float& ay, float& az) {
     const int i = d & 3, j = (d >> 2) & 3, k = d >> 4;

@@ -86,16 +86,20 @@ __global__ void __launch_bounds__(SW_THREADS) k_kernel_integrals(const int32_t* 
                                                                   float inv_eps) {
     __shared__ int s_nb[SW_PKGS][NB];
     __shared__ float s_H[SW_PKGS][216];  // 6^3 tile: package plus a one-point halo
+    __shared__ unsigned s_sat[SW_PKGS];
     const int lp = threadIdx.x >> 6, d = threadIdx.x & 63;
     const int64_t p = 2 + (int64_t)blockIdx.x * SW_PKGS + lp;
     const bool valid = p < P;
     if (valid && d < NB) s_nb[lp][d] = __ldg(nbr + p * NB + d);
+    if (d == 0) s_sat[lp] = 0;
     __syncthreads();
-    if (valid) integrals_stage(s_nb[lp], phi, inv_eps, d, s_H[lp]);
+    // a package is two whole warps: OR the saturation bits per warp, then per package
+    const unsigned bits = __reduce_or_sync(0xffffffffu, valid ? integrals_stage(s_nb[lp], phi, inv_eps, d, s_H[lp]) : 0u);
+    if ((threadIdx.x & 31) == 0 && bits) atomicOr(&s_sat[lp], bits);
     __syncthreads();
     if (!valid) return;
     float w, ax, ay, az;
-    integrals_point(s_H[lp], d, K, w, ax, ay, az);
+    if (!integrals_saturated(s_sat[lp], w, ax, ay, az)) integrals_point(s_H[lp], d, K, w, ax, ay, az);
     const int64_t at = p * PKG3 + d;
     W[at] = w;
     gx[at] = ax;
