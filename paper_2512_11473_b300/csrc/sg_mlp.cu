@@ -125,10 +125,9 @@ __device__ __forceinline__ void forward_tile(const __nv_bfloat16* W, const float
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float z = acc[nt][i];
-            A1[(g + 8 * (i >> 1)) * MLP_S2 + 8 * nt + 2 * t + (i & 1)] = __float2bfloat16_rn(z * sigmoidf_(z));
-        }
+        for (int i = 0; i < 4; i += 2)
+            *reinterpret_cast<__nv_bfloat162*>(A1 + (g + 8 * (i >> 1)) * MLP_S2 + 8 * nt + 2 * t) =
+                __floats2bfloat162_rn(silu_(acc[nt][i]), silu_(acc[nt][i + 1]));
     __syncwarp();
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
@@ -139,10 +138,9 @@ __device__ __forceinline__ void forward_tile(const __nv_bfloat16* W, const float
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float z = acc[nt][i];
-            A2[(g + 8 * (i >> 1)) * MLP_S2 + 8 * nt + 2 * t + (i & 1)] = __float2bfloat16_rn(z * sigmoidf_(z));
-        }
+        for (int i = 0; i < 4; i += 2)
+            *reinterpret_cast<__nv_bfloat162*>(A2 + (g + 8 * (i >> 1)) * MLP_S2 + 8 * nt + 2 * t) =
+                __floats2bfloat162_rn(silu_(acc[nt][i]), silu_(acc[nt][i + 1]));
     __syncwarp();
     float o[1][4];
     const float c0 = 2 * t < MLP_OUT ? bias[2 * MLP_H + 2 * t] : 0.0f;

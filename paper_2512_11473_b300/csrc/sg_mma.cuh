@@ -62,7 +62,18 @@ __device__ __forceinline__ void warp_gemm(float (&acc)[NT][4], const __nv_bfloat
     }
 }
 
-__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float tanh_approx(float x) {
+    float r;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// logistic sigmoid through the hardware tanh: 1 / (1 + e^-z) = (1 + tanh(z/2)) / 2
+__device__ __forceinline__ float sigmoidf_(float z) { return fmaf(0.5f, tanh_approx(0.5f * z), 0.5f); }
+// SiLU z sigmoid(z) = h + h tanh(h) with h = z/2
+__device__ __forceinline__ float silu_(float z) {
+    const float h = 0.5f * z;
+    return fmaf(h, tanh_approx(h), h);
+}
 
 }  // namespace
 }  // namespace sg
