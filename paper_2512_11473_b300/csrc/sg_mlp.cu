@@ -111,10 +111,29 @@ __device__ __forceinline__ void load_x_tile(__nv_bfloat16* X, const __nv_bfloat1
 
 // Forward of one 16-row tile through the three layers; y = output tile
 // values in fragment layout (cols 2t, 2t+1 of rows g, g+8 of n-tile 0).
-// A1 / A2: [16][72] activation tiles of this warp.
+// SiLU of the accumulators of n-tiles 2m and 2m + 1 (columns 16m..16m+15),
+// packed as the A fragment of k-tile m of the next layer: the C layout of
+// two adjacent 16x8 tiles is the A layout of one 16x16 tile, so hidden
+// activations never leave the registers.
+__device__ __forceinline__ void silu_to_a(const float (&c0)[4], const float (&c1)[4], uint32_t (&a)[4]) {
+    __nv_bfloat162 v;
+    v = __floats2bfloat162_rn(silu_(c0[0]), silu_(c0[1]));
+    a[0] = *reinterpret_cast<uint32_t*>(&v);
+    v = __floats2bfloat162_rn(silu_(c0[2]), silu_(c0[3]));
+    a[1] = *reinterpret_cast<uint32_t*>(&v);
+    v = __floats2bfloat162_rn(silu_(c1[0]), silu_(c1[1]));
+    a[2] = *reinterpret_cast<uint32_t*>(&v);
+    v = __floats2bfloat162_rn(silu_(c1[2]), silu_(c1[3]));
+    a[3] = *reinterpret_cast<uint32_t*>(&v);
+}
+
+// One 16-row tile through the network: X [16][SX] bf16 inputs in shared
+// memory (27 values, zero padding to 32), weights W and biases as packed;
+// y = the lane's accumulator fragment of the 4 outputs (columns 2t, 2t+1 of
+// rows g and g + 8; columns >= 4 are padding).
 __device__ __forceinline__ void forward_tile(const __nv_bfloat16* W, const float* bias, const __nv_bfloat16* X,
-                                             __nv_bfloat16* A1, __nv_bfloat16* A2, float (&y)[4]) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+                                             float (&y)[4]) {
+    const int lane = threadIdx.x & 31, t = lane & 3;
     float acc[8][4];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
@@ -122,33 +141,33 @@ __device__ __forceinline__ void forward_tile(const __nv_bfloat16* W, const float
         acc[nt][0] = b0, acc[nt][1] = b1, acc[nt][2] = b0, acc[nt][3] = b1;
     }
     warp_gemm<MLP_KIN, 8>(acc, X, SX, 0, W + MLP_PK_W1T, MLP_S1, 0);
+    uint32_t a[4][4];
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int i = 0; i < 4; i += 2)
-            *reinterpret_cast<__nv_bfloat162*>(A1 + (g + 8 * (i >> 1)) * MLP_S2 + 8 * nt + 2 * t) =
-                __floats2bfloat162_rn(silu_(acc[nt][i]), silu_(acc[nt][i + 1]));
-    __syncwarp();
+    for (int m = 0; m < 4; ++m) silu_to_a(acc[2 * m], acc[2 * m + 1], a[m]);
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const float b0 = bias[MLP_H + 8 * nt + 2 * t], b1 = bias[MLP_H + 8 * nt + 2 * t + 1];
         acc[nt][0] = b0, acc[nt][1] = b1, acc[nt][2] = b0, acc[nt][3] = b1;
     }
-    warp_gemm<MLP_H, 8>(acc, A1, MLP_S2, 0, W + MLP_PK_W2, MLP_S2, 0);
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
+    for (int m = 0; m < 4; ++m)
 #pragma unroll
-        for (int i = 0; i < 4; i += 2)
-            *reinterpret_cast<__nv_bfloat162*>(A2 + (g + 8 * (i >> 1)) * MLP_S2 + 8 * nt + 2 * t) =
-                __floats2bfloat162_rn(silu_(acc[nt][i]), silu_(acc[nt][i + 1]));
-    __syncwarp();
-    float o[1][4];
+        for (int nt = 0; nt < 8; ++nt) {
+            uint32_t b[2];
+            frag_b(b, W + MLP_PK_W2, MLP_S2, 8 * nt, 16 * m);
+            mma_16816(acc[nt], a[m], b);
+        }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) silu_to_a(acc[2 * m], acc[2 * m + 1], a[m]);
     const float c0 = 2 * t < MLP_OUT ? bias[2 * MLP_H + 2 * t] : 0.0f;
     const float c1 = 2 * t + 1 < MLP_OUT ? bias[2 * MLP_H + 2 * t + 1] : 0.0f;
-    o[0][0] = c0, o[0][1] = c1, o[0][2] = c0, o[0][3] = c1;
-    warp_gemm<MLP_H, 1>(o, A2, MLP_S2, 0, W + MLP_PK_W3, MLP_S2, 0);
+    y[0] = c0, y[1] = c1, y[2] = c0, y[3] = c1;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) y[i] = o[0][i];
+    for (int m = 0; m < 4; ++m) {
+        uint32_t b[2];
+        frag_b(b, W + MLP_PK_W3, MLP_S2, 0, 16 * m);
+        mma_16816(y, a[m], b);
+    }
 }
 
 // y[n][4] = MLP(x[n][32]); one warp per 16-row tile.
@@ -159,15 +178,13 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const unsigned char* __rest
     const float* bias = reinterpret_cast<const float*>(smem + MLP_PACK_BIAS_BYTE);
     stage_weights(smem, packed, MLP_PACK_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(smem + MLP_PACK_BYTES) + warp * (16 * SX + 2 * 16 * MLP_S2);
-    __nv_bfloat16* A1 = X + 16 * SX;
-    __nv_bfloat16* A2 = A1 + 16 * MLP_S2;
+    __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(smem + MLP_PACK_BYTES) + warp * 16 * SX;
     __syncthreads();
     const int64_t tiles = (n + 15) / 16;
     for (int64_t tile = (int64_t)blockIdx.x * 4 + warp; tile < tiles; tile += (int64_t)gridDim.x * 4) {
         load_x_tile(X, x, nullptr, tile * 16, n);
         float o[4];
-        forward_tile(W, bias, X, A1, A2, o);
+        forward_tile(W, bias, X, o);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int64_t row = tile * 16 + g + 8 * (i >> 1);
@@ -431,23 +448,18 @@ constexpr int SU_THREADS = 256;
 constexpr int SU_PK = SU_THREADS / PKG3;  // packages per round
 constexpr int SU_QROWS = SU_PK * PKG3;    // queue rows (all points of a round)
 constexpr int SU_WARPS = SU_THREADS / 32;
-// dynamic shared memory: weights | phi tiles | H tiles | queue rows | queue ids | per-warp activations
+// dynamic shared memory: weights | phi tiles | H tiles | queue rows | queue ids (hidden activations stay in
+// registers, see forward_tile)
 constexpr int SU_OFF_PHI = MLP_PACK_BYTES;
 constexpr int SU_OFF_H = SU_OFF_PHI + SU_PK * 216 * 4;
 constexpr int SU_OFF_QX = SU_OFF_H + SU_PK * 216 * 4;
 constexpr int SU_OFF_QI = SU_OFF_QX + SU_QROWS * SX * 2;
-constexpr int SU_OFF_ACT = SU_OFF_QI + SU_QROWS * 8;
-constexpr int SU_BYTES = SU_OFF_ACT + SU_WARPS * 2 * 16 * MLP_S2 * 2;
+constexpr int SU_BYTES = SU_OFF_QI + SU_QROWS * 8;
 
 // Stage the phi tile (and optionally the Heaviside tile) of package p.
 __device__ __forceinline__ void stage_tile(const int* nb27, const float* __restrict__ phi, float inv_eps, int d,
                                            float* tphi, float* tH) {
-    for (int e = d; e < 216; e += PKG3) {
-        const int x = e % 6 - 1, y = (e / 6) % 6 - 1, z = e / 36 - 1;
-        const float f = __ldg(phi + shift_index(nb27, x, y, z));
-        tphi[e] = f;
-        if (tH) tH[e] = heaviside_neg(f, inv_eps);
-    }
+    stage_rows(nb27, phi, inv_eps, d, tphi, tH);
 }
 
 // BATCH: packages of many bodies in one store; far packages (type < 2) are
@@ -474,8 +486,6 @@ __global__ void __launch_bounds__(SU_THREADS) k_sur_integrals(const int32_t* __r
     __nv_bfloat16* s_qx = reinterpret_cast<__nv_bfloat16*>(smem + SU_OFF_QX);
     int64_t* s_qi = reinterpret_cast<int64_t*>(smem + SU_OFF_QI);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    __nv_bfloat16* A1 = reinterpret_cast<__nv_bfloat16*>(smem + SU_OFF_ACT) + warp * 2 * 16 * MLP_S2;
-    __nv_bfloat16* A2 = A1 + 16 * MLP_S2;
     stage_weights(smem, packed, MLP_PACK_BYTES);
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
     float* outs[4] = {W, gx, gy, gz};
@@ -531,7 +541,7 @@ __global__ void __launch_bounds__(SU_THREADS) k_sur_integrals(const int32_t* __r
                     for (int c = 8 * (lane & 3); c < 8 * (lane & 3) + 8; ++c) X[r * SX + c] = __float2bfloat16_rn(0.0f);
             __syncwarp();
             float y[4];
-            forward_tile(Wt, bias, X, A1, A2, y);
+            forward_tile(Wt, bias, X, y);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int r = tile * 16 + g + 8 * (i >> 1), col = 2 * t + (i & 1);
@@ -705,7 +715,7 @@ sg_status sg_mlp_get_params(sg_mlp* m, float* params) {
 sg_status sg_mlp_forward(sg_mlp* m, int64_t n, const void* x, float* y) {
     if (!m || n < 0 || (n > 0 && (!x || !y))) return SG_ERR_INVALID;
     if (n == 0) return SG_OK;
-    const int smem = MLP_PACK_BYTES + 4 * (16 * SX + 2 * 16 * MLP_S2) * 2;
+    const int smem = MLP_PACK_BYTES + 4 * 16 * SX * 2;
     cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) {
         unsigned blocks = cdiv(n, 64);

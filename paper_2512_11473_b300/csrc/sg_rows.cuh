@@ -186,14 +186,15 @@ __device__ __forceinline__ float heaviside_neg(float phi, float inv_eps) {
 
 // Fill the 6^3 Heaviside tile of package p (64 threads, d = thread index in
 // the package); nb27 holds the package's neighbourhood in shared memory.
-// Stage the smoothed Heaviside of the package's 6^3 tile; returns the
-// saturation bits of the entries this thread staged: bit 0 unless all were
-// 0, bit 1 unless all were 1 (a tile whose bits OR to 1 is all ones, to 2 all
-// zeros).
-__device__ __forceinline__ unsigned integrals_stage(const int* nb27, const float* __restrict__ phi, float inv_eps,
-                                                    int d, float* tile) {
-    // one x-row of the tile per thread: four interior points from one package
-    // (a 16-byte load) and the two halo points from the -x and +x packages
+// Stage the package's 6^3 tile (the package plus a one-point halo) by
+// x-rows, one row of six per thread d < 36: four interior points from one
+// package (a 16-byte load) and the two halo points from the -x and +x
+// packages of the index shift (Listing 2).  Writes phi to tphi and the
+// smoothed Heaviside to tH (either may be null); returns the saturation
+// bits of the H values this thread staged: bit 0 unless all were 0, bit 1
+// unless all were 1 (a tile whose bits OR to 1 is all ones, to 2 all zeros).
+__device__ __forceinline__ unsigned stage_rows(const int* nb27, const float* __restrict__ phi, float inv_eps, int d,
+                                               float* tphi, float* tH) {
     unsigned bits = 0;
     if (d < 36) {
         const int y = d % 6 - 1, z = d / 6 - 1;
@@ -203,16 +204,25 @@ __device__ __forceinline__ unsigned integrals_stage(const int* nb27, const float
         const float4 v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb27[nb + 1] * PKG3 + d0));
         const float vm = __ldg(phi + (int64_t)nb27[nb] * PKG3 + d0 + 3);
         const float vp = __ldg(phi + (int64_t)nb27[nb + 2] * PKG3 + d0);
-        float* t = tile + 6 * (y + 1) + 36 * (z + 1);
-        const float hv[6] = {heaviside_neg(vm, inv_eps), heaviside_neg(v.x, inv_eps), heaviside_neg(v.y, inv_eps),
-                             heaviside_neg(v.z, inv_eps), heaviside_neg(v.w, inv_eps), heaviside_neg(vp, inv_eps)};
+        const int e0 = 6 * (y + 1) + 36 * (z + 1);
+        const float f[6] = {vm, v.x, v.y, v.z, v.w, vp};
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            t[i] = hv[i];
-            bits |= (hv[i] != 0.0f ? 1u : 0u) | (hv[i] != 1.0f ? 2u : 0u);
+            if (tphi) tphi[e0 + i] = f[i];
+            if (tH) {
+                const float hv = heaviside_neg(f[i], inv_eps);
+                tH[e0 + i] = hv;
+                bits |= (hv != 0.0f ? 1u : 0u) | (hv != 1.0f ? 2u : 0u);
+            }
         }
     }
     return bits;
+}
+
+// The Heaviside tile of the kernel integrals (see stage_rows).
+__device__ __forceinline__ unsigned integrals_stage(const int* nb27, const float* __restrict__ phi, float inv_eps,
+                                                    int d, float* tile) {
+    return stage_rows(nb27, phi, inv_eps, d, nullptr, tile);
 }
 
 // The 27 taps around data point d of a staged tile.
