@@ -39,8 +39,8 @@ class _Shape(C.Structure):
 
 
 class _Grid(C.Structure):
-    _fields_ = [("lo", C.c_double * 3), ("dims", C.c_int32 * 3), ("pad", C.c_int32),
-                ("h", C.c_double), ("far_value", C.c_double)]
+    _fields_ = [("lo", C.c_double * 3), ("dims", C.c_int32 * 3), ("id_order", C.c_int32),
+                ("h", C.c_double), ("far_value", C.c_double), ("support", C.c_double), ("eps", C.c_double)]
 
 
 _lib = None
@@ -55,6 +55,9 @@ def lib():
         _lib.or_sdf.restype = C.c_double
         _lib.or_sdf.argtypes = [C.POINTER(_Shape), C.c_double, C.c_double, C.c_double]
         _lib.or_get_threads.restype = C.c_int
+        for f in ("or_wendland_r", "or_wendland_r_dq"):
+            getattr(_lib, f).restype = C.c_double
+            getattr(_lib, f).argtypes = [C.c_double, C.c_double]
         for f in ("or_wendland", "or_wendland_dq"):
             getattr(_lib, f).restype = C.c_double
             getattr(_lib, f).argtypes = [C.c_double]
@@ -91,6 +94,9 @@ def _grid(spec, far=None) -> _Grid:
     g.dims[:] = [int(v) for v in spec.dims]
     g.h = float(spec.h)
     g.far_value = far_value(spec) if far is None else float(far)
+    g.support = float(getattr(spec, "kernel_support", 0.0) or 0.0)
+    g.eps = float(getattr(spec, "heaviside_eps", 0.0) or 0.0)
+    g.id_order = int(getattr(spec, "id_order", 0) or 0)
     return g
 
 
@@ -115,6 +121,15 @@ def wendland(q):
 
 def wendland_dq(q):
     return lib().or_wendland_dq(float(q))
+
+
+def wendland_r(q, R):
+    """Wendland C2 of support R (units of h)."""
+    return lib().or_wendland_r(float(q), float(R))
+
+
+def wendland_r_dq(q, R):
+    return lib().or_wendland_r_dq(float(q), float(R))
 
 
 def heaviside(z, eps):

@@ -54,9 +54,11 @@ typedef struct {
 typedef struct {
     double lo[3];
     int32_t dims[3];
-    int32_t pad;
+    int32_t id_order; /* package ids: 0 in linear cell order, 1 in Morton order of the cells */
     double h;         /* fine spacing; coarse cell lc = 4h */
     double far_value; /* F: far packages hold -F (inside) and +F (outside) */
+    double support;   /* kernel support (a length; 0: 2h) */
+    double eps;       /* Heaviside half width (a length; 0: h) */
 } or_grid;
 
 /* ------------------------------------------------------------------------- */
@@ -163,13 +165,25 @@ void or_sdf_many(const or_shape *s, int64_t n, const double *x, const double *y,
  *       cell size" test with the threshold moved off exact lattice ties.
  * Inner: not core and one of the 26 neighbouring cells is core.
  * Package ids: 2 + number of active cells with a smaller cell index, which is
- *       the "sorted by spatial location" order with cells in linear order.
+ *       the "sorted by spatial location" order with cells in linear order;
+ *       with id_order 1, 2 + the rank of the cell in the Morton order of the
+ *       active cells (bit interleave of I, J, K, I lowest).
  * Far cells map to package 0 when d < 0 and to package 1 otherwise.
  * Returns P, the package count including the two far packages.
  * near_ties receives the number of cells with ||d| - T| < 1e-9 lc, where
  * float-float evaluation might decide differently.
  */
 static int64_t tag_inner_and_ids(const or_grid *g, int32_t *cell_pkg, uint8_t *cell_type);
+
+typedef struct {
+    uint64_t key;
+    int64_t cell;
+} or_cellkey;
+
+static int cmp_cellkey(const void *pa, const void *pb) {
+    const or_cellkey *a = (const or_cellkey *)pa, *b = (const or_cellkey *)pb;
+    return a->key < b->key ? -1 : (a->key > b->key ? 1 : 0);
+}
 
 int64_t or_tag(const or_grid *g, const or_shape *s, int32_t *cell_pkg, uint8_t *cell_type, int64_t *near_ties) {
     const int64_t nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
@@ -217,6 +231,26 @@ static int64_t tag_inner_and_ids(const or_grid *g, int32_t *cell_pkg, uint8_t *c
             cell_pkg[c] = (int32_t)next++;
         else
             cell_pkg[c] = cell_type[c]; /* 0 inside, 1 outside */
+    }
+    if (g->id_order == 1) {
+        /* ids in the Morton order of the active cells instead: sort them by
+           the bit interleave of (I, J, K), I in the lowest bit */
+        const int64_t n = next - 2;
+        or_cellkey *a = (or_cellkey *)malloc(sizeof(or_cellkey) * (size_t)(n > 0 ? n : 1));
+        int64_t m = 0;
+        for (int64_t c = 0; c < nc; ++c) {
+            if (cell_pkg[c] < 2) continue;
+            const uint64_t IJK[3] = {(uint64_t)(c % nx), (uint64_t)((c / nx) % ny), (uint64_t)(c / (nx * ny))};
+            uint64_t key = 0;
+            for (int b = 0; b < 21; ++b)
+                for (int ax = 0; ax < 3; ++ax) key |= ((IJK[ax] >> b) & 1ull) << (3 * b + ax);
+            a[m].key = key;
+            a[m].cell = c;
+            ++m;
+        }
+        qsort(a, (size_t)n, sizeof(or_cellkey), cmp_cellkey);
+        for (int64_t r = 0; r < n; ++r) cell_pkg[a[r].cell] = (int32_t)(2 + r);
+        free(a);
     }
     return next;
 }
@@ -473,6 +507,18 @@ void or_reinit(const or_grid *g, int64_t P, const int32_t *nbr, double *phi, int
 /* summed over all 125 offsets s in {-2..2}^3 (taps at |s| >= 2 weigh 0).     */
 /* Far packages: W = 1 inside, 0 outside; G^ = 0.                             */
 /* ------------------------------------------------------------------------- */
+/* Wendland C2 of support R (in units of h): (1 - q/R)^4 (1 + 4 q/R) for
+   q < R, else 0, and its derivative -20 (q / R^2) (1 - q/R)^3. */
+double or_wendland_r(double q, double R) {
+    if (q >= R) return 0.0;
+    double t = 1.0 - q / R;
+    return t * t * t * t * (1.0 + 4.0 * q / R);
+}
+double or_wendland_r_dq(double q, double R) {
+    if (q >= R) return 0.0;
+    double t = 1.0 - q / R;
+    return -20.0 * q / (R * R) * t * t * t;
+}
 double or_wendland(double q) {
     if (q >= 2.0) return 0.0;
     double t = 1.0 - 0.5 * q;
@@ -493,7 +539,9 @@ double or_heaviside(double z, double eps) {
 
 void or_kernel_integrals(const or_grid *g, int64_t P, const int32_t *nbr, const double *phi, double *W, double *Gx,
                          double *Gy, double *Gz) {
-    const double eps = g->h;
+    /* support R h (R <= 3, so that every tap lies in the 5^3 stencil) and Heaviside half width eps */
+    const double R = g->support > 0.0 ? g->support / g->h : 2.0;
+    const double eps = g->eps > 0.0 ? g->eps : g->h;
     for (int d = 0; d < PKG3; ++d) {
         W[d] = 1.0;
         W[PKG3 + d] = 0.0;
@@ -511,12 +559,12 @@ void or_kernel_integrals(const or_grid *g, int64_t P, const int32_t *nbr, const 
                         for (int sy = -2; sy <= 2; ++sy)
                             for (int sx = -2; sx <= 2; ++sx) {
                                 double q = sqrt((double)(sx * sx + sy * sy + sz * sz));
-                                double w = or_wendland(q);
+                                double w = or_wendland_r(q, R);
                                 double H = or_heaviside(-phi[shift_index(nb, i + sx, j + sy, k + sz)], eps);
                                 num += w * H;
                                 den += w;
                                 if (q > 0.0) {
-                                    double dw = or_wendland_dq(q) * H / q;
+                                    double dw = or_wendland_r_dq(q, R) * H / q;
                                     gx += dw * (double)(-sx);
                                     gy += dw * (double)(-sy);
                                     gz += dw * (double)(-sz);

@@ -92,10 +92,15 @@ class Shape:
 
 @dataclasses.dataclass
 class GridSpec:
-    """Background mesh: dims coarse cells of size lc = 4h starting at lo."""
+    """Background mesh: dims coarse cells of size lc = 4h starting at lo.
+    Optional: kernel_support (a length, 0 for 2h), heaviside_eps (a length,
+    0 for h), id_order (0 linear cell order, 1 Morton order)."""
     lo: tuple
     dims: tuple
     h: float
+    kernel_support: float = 0.0
+    heaviside_eps: float = 0.0
+    id_order: int = 0
 
     @property
     def lc(self) -> float:
