@@ -87,13 +87,25 @@ typedef struct {
     double p[8];
 } sg_shape;
 
-/* Grid description (host struct, copied).  far_value <= 0 selects F = 16h. */
+/* Grid description (host struct, copied).
+ *   lo, dims, h     background mesh of dims coarse cells of 4h from lo;
+ *   id_order        package ids in linear cell order (0, "sorted by spatial
+ *                   location" with x fastest) or in the Morton order of the
+ *                   cells (1: bit interleave of I, J, K, I lowest);
+ *   far_value       F of the far packages (-F inside, +F outside); <= 0: 16h;
+ *   kernel_support  support of the Wendland C2 kernel of the integrals, a
+ *                   length (0: 2h; at most 3h, so that every tap with a
+ *                   non-zero weight lies in the 5^3 stencil);
+ *   heaviside_eps   half width of the smoothed Heaviside, a length (0: h).
+ * The surrogate integrals are defined for the defaults (2h, h) only. */
 typedef struct {
     double lo[3];
     int32_t dims[3];
-    int32_t reserved;
-    double h;         /* fine spacing; the coarse cell is 4h */
-    double far_value; /* F */
+    int32_t id_order;
+    double h;
+    double far_value;
+    double kernel_support;
+    double heaviside_eps;
 } sg_grid_desc;
 
 /* Optional device-memory hook.  alloc returns device memory of at least

@@ -358,7 +358,9 @@ def coarser(spec):
     """The layer below spec: same lo, half the dims, twice the spacing."""
     import sg_inputs as si
     assert all(int(d) % 2 == 0 for d in spec.dims)
-    return si.GridSpec(tuple(spec.lo), tuple(int(d) // 2 for d in spec.dims), 2.0 * spec.h)
+    return si.GridSpec(tuple(spec.lo), tuple(int(d) // 2 for d in spec.dims), 2.0 * spec.h,
+                       kernel_support=2.0 * spec.kernel_support, heaviside_eps=2.0 * spec.heaviside_eps,
+                       id_order=spec.id_order)
 
 
 def build_layers(spec, shape, layers):

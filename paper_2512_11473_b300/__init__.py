@@ -43,8 +43,8 @@ class sg_shape(C.Structure):
 
 
 class sg_grid_desc(C.Structure):
-    _fields_ = [("lo", C.c_double * 3), ("dims", C.c_int32 * 3), ("reserved", C.c_int32), ("h", C.c_double),
-                ("far_value", C.c_double)]
+    _fields_ = [("lo", C.c_double * 3), ("dims", C.c_int32 * 3), ("id_order", C.c_int32), ("h", C.c_double),
+                ("far_value", C.c_double), ("kernel_support", C.c_double), ("heaviside_eps", C.c_double)]
 
 
 class sg_batch_plan(C.Structure):
@@ -193,8 +193,10 @@ class _TorchAllocator:
 class Grid:
     """A sparse narrow-band grid on one CUDA device.
 
-    ``spec`` needs ``lo`` (3 floats), ``dims`` (3 ints) and ``h``.  Calls are
-    queued on ``stream`` (default: torch's current stream at construction).
+    ``spec`` needs ``lo`` (3 floats), ``dims`` (3 ints) and ``h``, and may set
+    ``kernel_support``, ``heaviside_eps`` and ``id_order`` (see sg_grid_desc).
+    Calls are queued on ``stream`` (default: torch's current stream at
+    construction).
     """
 
     def __init__(self, spec, far_value=0.0, stream=None, torch_allocator=True):
@@ -205,11 +207,7 @@ class Grid:
         self.device = torch.cuda.current_device()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.spec = spec
-        d = sg_grid_desc()
-        d.lo[:] = [float(v) for v in spec.lo]
-        d.dims[:] = [int(v) for v in spec.dims]
-        d.h = float(spec.h)
-        d.far_value = float(far_value)
+        d = _desc(spec, far_value)
         self._alloc = _TorchAllocator(self.device) if torch_allocator else None
         h = C.c_void_p()
         st = self._lib.sg_create(C.byref(d), C.byref(self._alloc.struct) if self._alloc else None,
@@ -544,6 +542,9 @@ def _desc(spec, far_value=0.0) -> sg_grid_desc:
     d.dims[:] = [int(v) for v in spec.dims]
     d.h = float(spec.h)
     d.far_value = float(far_value)
+    d.id_order = int(getattr(spec, "id_order", 0) or 0)
+    d.kernel_support = float(getattr(spec, "kernel_support", 0.0) or 0.0)
+    d.heaviside_eps = float(getattr(spec, "heaviside_eps", 0.0) or 0.0)
     return d
 
 
@@ -558,7 +559,10 @@ def layer_spec(spec, level, layers):
     k = layers - 1 - level
     f = 1 << k
     assert all(int(d) % f == 0 for d in spec.dims)
-    return si.GridSpec(tuple(spec.lo), tuple(int(d) // f for d in spec.dims), spec.h * f)
+    # the options keep their meaning relative to each layer's spacing
+    return si.GridSpec(tuple(spec.lo), tuple(int(d) // f for d in spec.dims), spec.h * f,
+                       kernel_support=spec.kernel_support * f, heaviside_eps=spec.heaviside_eps * f,
+                       id_order=spec.id_order)
 
 
 class MultiResolution:

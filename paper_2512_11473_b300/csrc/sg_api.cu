@@ -167,6 +167,11 @@ sg_status sg_create(const sg_grid_desc* desc, const sg_allocator* alloc, void* s
     }
     if (nc >= (1LL << 31)) return SG_ERR_CAPACITY;
     if (alloc && (!alloc->alloc || !alloc->free)) return SG_ERR_INVALID;
+    if (desc->id_order != 0 && desc->id_order != 1) return SG_ERR_INVALID;
+    if (!std::isfinite(desc->kernel_support) || desc->kernel_support < 0.0 ||
+        desc->kernel_support > 3.0 * desc->h * (1.0 + 1e-12))
+        return SG_ERR_INVALID;
+    if (!std::isfinite(desc->heaviside_eps) || desc->heaviside_eps < 0.0) return SG_ERR_INVALID;
     sg_grid* g = new (std::nothrow) sg_grid();
     if (!g) return SG_ERR_OOM;
     g->desc = *desc;
@@ -255,6 +260,35 @@ static sg_status tag_common(sg_grid* g, Flags flags, int64_t* n_packages) {
     SG_CUDA(g, launch_tag_scatter(ct, active, (int32_t*)g->cell_pkg.p, (int32_t*)g->pkg_cell.p,
                                   (uint8_t*)g->pkg_type.p, nc, g->stream),
             "tag scatter");
+    if (g->desc.id_order == 1 && P > 3) {
+        // Morton package ids: sort the active cells by the Morton key of their
+        // centres (fine index 4I + 2, so the order of the cells' own keys)
+        const int64_t n = P - 2;
+        const GridF Gf = grid_f(g);
+        const size_t fb = ((size_t)n * 4 + 255) & ~(size_t)255, tb = ((size_t)P * 4 + 255) & ~(size_t)255;
+        const size_t sb = sort_scratch_bytes(n, morton_bits(Gf));
+        if (!ensure(g, g->scratch, 4 * fb + 2 * tb + sb)) {
+            g->state = 0;
+            return fail(g, SG_ERR_OOM, "sg_tag_allocate: out of device memory");
+        }
+        char* sp = (char*)g->scratch.p;
+        float* cx = (float*)sp;
+        float* cy = (float*)(sp + fb);
+        float* cz = (float*)(sp + 2 * fb);
+        int32_t* ord = (int32_t*)(sp + 3 * fb);
+        int32_t* old_cell = (int32_t*)(sp + 4 * fb);
+        uint8_t* old_type = (uint8_t*)(sp + 4 * fb + tb);
+        void* sort_scratch = sp + 4 * fb + 2 * tb;
+        SG_CUDA(g, cudaMemcpyAsync(old_cell, g->pkg_cell.p, (size_t)P * 4, cudaMemcpyDeviceToDevice, g->stream),
+                "ids copy");
+        SG_CUDA(g, cudaMemcpyAsync(old_type, g->pkg_type.p, (size_t)P, cudaMemcpyDeviceToDevice, g->stream),
+                "ids copy");
+        SG_CUDA(g, launch_cell_centres(Gf, old_cell, cx, cy, cz, n, g->stream), "ids centres");
+        SG_CUDA(g, morton_sort(Gf, n, cx, cy, cz, nullptr, ord, sort_scratch, g->stream), "ids sort");
+        SG_CUDA(g, launch_renumber(ord, old_cell, old_type, (int32_t*)g->pkg_cell.p, (uint8_t*)g->pkg_type.p,
+                                   (int32_t*)g->cell_pkg.p, n, g->stream),
+                "ids renumber");
+    }
     SG_CUDA(g, launch_fill_nbr(G, (const int32_t*)g->cell_pkg.p, (const int32_t*)g->pkg_cell.p, (int32_t*)g->nbr.p, P,
                                g->stream),
             "fill nbr");
@@ -435,6 +469,8 @@ sg_status sg_kernel_integrals(sg_grid* g, int32_t mode, const void* mlp) {
     if (!((mode == 0 && mlp == nullptr) || (mode == 1 && mlp != nullptr)))
         return fail(g, SG_ERR_INVALID, "sg_kernel_integrals: mode 0 takes no network, mode 1 needs one");
     if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_kernel_integrals: phi not initialised");
+    if (mode == 1 && !default_kernel(g->desc))
+        return fail(g, SG_ERR_INVALID, "sg_kernel_integrals: the surrogate needs kernel support 2h and eps = h");
     DeviceGuard dg(g->device);
     float* o[4];
     for (int a = 0; a < 4; ++a)
@@ -446,7 +482,7 @@ sg_status sg_kernel_integrals(sg_grid* g, int32_t mode, const void* mlp) {
         return SG_OK;
     }
     SG_CUDA(g, launch_kernel_integrals(grid_f(g), (const int32_t*)g->nbr.p, (const float*)g->field[SG_FIELD_PHI].p, o[0],
-                                       o[1], o[2], o[3], g->P, g->stream),
+                                       o[1], o[2], o[3], g->P, support_h(g->desc), heaviside_eps(g->desc), g->stream),
             "kernel integrals");
     return SG_OK;
 }

@@ -41,8 +41,10 @@ struct sg_batch {
     int n = 0;
     int64_t P = 0;  // packages of all bodies, far packages included
     std::vector<int64_t> base, npk, cell_base;
-    std::vector<double> h;
+    std::vector<double> h, eps;
     std::vector<sg_grid_desc> desc;
+    double R = 2.0;             // kernel support of every body, in units of its h
+    bool default_kernel = true;  // every body has support 2h and eps = h (the surrogate's kernel)
     const sg_mlp* mlp = nullptr;  // surrogate of plans with integrals_mode 1
     sg_allocator alloc{};
     bool user_alloc = false;
@@ -346,7 +348,7 @@ bool valid_plan(const sg_batch* b, const sg_batch_plan* p) {
     const int ppi = p->pkgs_per_item;
     return (ppi == 1 || ppi == 2 || ppi == 4 || ppi == 8) && (p->depth == 1 || p->depth == 2) && p->depth <= ppi &&
            p->reinit_iterations >= 0 && p->cfl > 0.0f && std::isfinite(p->cfl) &&
-           (p->integrals_mode == 0 || (p->integrals_mode == 1 && b->mlp));
+           (p->integrals_mode == 0 || (p->integrals_mode == 1 && b->mlp && b->default_kernel));
 }
 
 int persistent_blocks(const void* kernel, int device) {
@@ -369,7 +371,7 @@ cudaError_t upload_params(sg_batch* b, float cfl) {
         const float dt = (float)((double)cfl * h);
         q.dt = dt;
         q.cfl = (float)((double)dt / h);
-        q.inv_eps = (float)(1.0 / h);
+        q.inv_eps = (float)(1.0 / b->eps[i]);
         q.F = 0.0f;
         q.pad[0] = q.pad[1] = 0.0f;
     }
@@ -397,7 +399,7 @@ cudaError_t record_run(sg_batch* b, const sg_batch_plan& plan, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(ctr, 0, b->n_counters * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     int c = 0;
-    const KernelCoef K = kernel_coef();
+    const KernelCoef K = kernel_coef(b->R);
     if (plan.depth == 2) {
         const int nb = persistent_blocks((const void*)k_batch_gradient<2>, b->device);
         k_batch_gradient<2><<<nb, BT, 0, s>>>(faces, type, body, prm, phi, fo[1], fo[2], fo[3], b->P, ppi, ctr + c++);
@@ -510,6 +512,9 @@ sg_status sg_batch_create(sg_grid* const* grids, int32_t n, void* stream, sg_bat
         if (!grids[i]) return SG_ERR_INVALID;
         if (grids[i]->state < 2) return SG_ERR_STATE;
         if (grids[i]->device != grids[0]->device) return SG_ERR_INVALID;
+        // one tap table for all bodies: the same support in units of h, at most 2h
+        const double R = support_h(grids[i]->desc), R0 = support_h(grids[0]->desc);
+        if (R > 2.0 || std::fabs(R - R0) > 1e-12 * R0) return SG_ERR_INVALID;
         P += grids[i]->P;
     }
     if (P >= (1LL << 31) / NB) return SG_ERR_CAPACITY;
@@ -519,6 +524,7 @@ sg_status sg_batch_create(sg_grid* const* grids, int32_t n, void* stream, sg_bat
     if (!b) return SG_ERR_OOM;
     b->n = n;
     b->P = P;
+    b->R = support_h(grids[0]->desc);
     b->stream = (cudaStream_t)stream;
     b->alloc = grids[0]->alloc;
     b->user_alloc = grids[0]->user_alloc;
@@ -551,7 +557,9 @@ sg_status sg_batch_create(sg_grid* const* grids, int32_t n, void* stream, sg_bat
             b->cell_base.push_back(coff);
             b->npk.push_back(g->P);
             b->h.push_back(g->desc.h);
+            b->eps.push_back(heaviside_eps(g->desc));
             b->desc.push_back(g->desc);
+            b->default_kernel &= default_kernel(g->desc);
             sb[i] = sur_body(g->desc.h);
             // background cells -> global package ids
             k_batch_offset_nbr<<<flat_grid(g->nc), BT, 0, b->stream>>>((const int32_t*)g->cell_pkg.p,

@@ -95,6 +95,12 @@ cudaError_t launch_tag_flags(const GridFF& G, const ShapeFF& S, uint8_t* cell_ty
 cudaError_t launch_tag_flags_from(const GridFF& G, const ShapeFF& S, const int32_t* c_cell_pkg,
                                   const uint8_t* c_pkg_type, const float* c_phi, int cnx, int cny, uint8_t* cell_type,
                                   uint32_t* active, int64_t nc, unsigned long long* evaluated, cudaStream_t s);
+// Morton package ids: cell centres of the n active packages (linear ids),
+// then the move of package 2 + order[r] to id 2 + r (tables and cells).
+cudaError_t launch_cell_centres(const GridF& G, const int32_t* pkg_cell, float* x, float* y, float* z, int64_t n,
+                                cudaStream_t s);
+cudaError_t launch_renumber(const int32_t* order, const int32_t* old_cell, const uint8_t* old_type, int32_t* pkg_cell,
+                            uint8_t* pkg_type, int32_t* cell_pkg, int64_t n, cudaStream_t s);
 cudaError_t launch_tag_inner(const GridFF& G, uint8_t* cell_type, uint32_t* active, int64_t nc, cudaStream_t s);
 cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* prefix, int32_t* cell_pkg,
                                int32_t* pkg_cell, uint8_t* pkg_type, int64_t nc, cudaStream_t s);
@@ -124,8 +130,16 @@ cudaError_t launch_reinit_step(const GridF& G, const int32_t* faces, const float
 cudaError_t launch_copy_active(const float* src, float* dst, int64_t P, cudaStream_t s);
 // phi <- phi + delta on the active packages
 cudaError_t launch_sequential(float* phi, float delta, int64_t P, cudaStream_t s);
+// R: kernel support in units of h (<= 3); eps: Heaviside half width.
 cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const float* phi, float* W, float* gx,
-                                    float* gy, float* gz, int64_t P, cudaStream_t s);
+                                    float* gy, float* gz, int64_t P, double R, double eps, cudaStream_t s);
+// The kernel support of a grid in units of h and its Heaviside half width.
+inline double support_h(const sg_grid_desc& d) { return d.kernel_support > 0.0 ? d.kernel_support / d.h : 2.0; }
+inline double heaviside_eps(const sg_grid_desc& d) { return d.heaviside_eps > 0.0 ? d.heaviside_eps : d.h; }
+// The surrogate was trained for the default kernel (support 2h, eps = h).
+inline bool default_kernel(const sg_grid_desc& d) {
+    return (d.kernel_support == 0.0 || d.kernel_support == 2.0 * d.h) && (d.heaviside_eps == 0.0 || d.heaviside_eps == d.h);
+}
 
 // surrogate (sg_mlp.cu)
 cudaError_t launch_surrogate_integrals(sg_grid* g, const sg_mlp* m, float* W, float* gx, float* gy, float* gz);

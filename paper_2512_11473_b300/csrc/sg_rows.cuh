@@ -20,16 +20,17 @@
 
 namespace sg {
 
-// Kernel integrals.  Tap weights by squared distance |s|^2 in {0,1,2,3}:
-// cw = w(|s|) / sum w, ck = w'(|s|) / |s| / sum w (taps at |s| >= 2 vanish).
+// Kernel integrals.  Tap weights by squared distance |s|^2 in {0..12} (the
+// 5^3 stencil): cw = w(|s|) / sum w, ck = w'(|s|) / |s| / sum w, for the
+// Wendland C2 of support R h, w(q) = (1 - q/R)^4 (1 + 4q/R) (0 at q >= R).
 struct KernelCoef {
-    float cw[4];
-    float ck[4];
+    float cw[13];
+    float ck[13];
 };
 
-// host: tap coefficients of the Wendland C2 kernel (support 2h) normalised by
-// the discrete sum of its 27 non-zero taps
-KernelCoef kernel_coef();
+// host: the tap coefficients for support R h (R <= 3), normalised by the
+// discrete sum of the taps
+KernelCoef kernel_coef(double R = 2.0);
 
 namespace {
 
@@ -217,6 +218,58 @@ __device__ __forceinline__ unsigned stage_rows(const int* nb27, const float* __r
         }
     }
     return bits;
+}
+
+// Supports above 2h reach two points: the package's 8^3 tile (a two-point
+// halo) is staged by x-rows, one per thread (64 rows of eight: four interior
+// points by a 16-byte load, two from the -x and two from the +x package by
+// 8-byte loads).  Returns saturation bits as stage_rows.
+__device__ __forceinline__ unsigned stage_rows_wide(const int* nb27, const float* __restrict__ phi, float inv_eps,
+                                                    int d, float* tH) {
+    const int y = d % 8 - 2, z = d / 8 - 2;
+    const int oy = ((y + 4) >> 2) - 1, oz = ((z + 4) >> 2) - 1;
+    const int d0 = 4 * (y - 4 * oy) + 16 * (z - 4 * oz);
+    const int nb = 3 * (oy + 1) + 9 * (oz + 1);
+    const float2 m = __ldg(reinterpret_cast<const float2*>(phi + (int64_t)nb27[nb] * PKG3 + d0 + 2));
+    const float4 v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb27[nb + 1] * PKG3 + d0));
+    const float2 pp = __ldg(reinterpret_cast<const float2*>(phi + (int64_t)nb27[nb + 2] * PKG3 + d0));
+    const float f[8] = {m.x, m.y, v.x, v.y, v.z, v.w, pp.x, pp.y};
+    float* t = tH + 8 * (y + 2) + 64 * (z + 2);
+    unsigned bits = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float hv = heaviside_neg(f[i], inv_eps);
+        t[i] = hv;
+        bits |= (hv != 0.0f ? 1u : 0u) | (hv != 1.0f ? 2u : 0u);
+    }
+    return bits;
+}
+
+// The 5^3 tap sums of data point d from an 8^3 tile (taps with |s|^2 >= 9
+// carry no weight for supports up to 3h).
+__device__ __forceinline__ void integrals_point_wide(const float* tile, int d, const KernelCoef& K, float& w,
+                                                     float& ax, float& ay, float& az) {
+    const int i = d & 3, j = (d >> 2) & 3, k = d >> 4;
+    const float* H = tile + (i + 2) + 8 * (j + 2) + 64 * (k + 2);
+    w = 0.0f;
+    ax = ay = az = 0.0f;
+#pragma unroll
+    for (int sz = -2; sz <= 2; ++sz)
+#pragma unroll
+        for (int sy = -2; sy <= 2; ++sy)
+#pragma unroll
+            for (int sx = -2; sx <= 2; ++sx) {
+                const int q2 = sx * sx + sy * sy + sz * sz;
+                if (q2 >= 9) continue;
+                const float h = H[sx + 8 * sy + 64 * sz];
+                w = fmaf(K.cw[q2], h, w);
+                if (q2 > 0) {
+                    const float kh = K.ck[q2] * h;
+                    if (sx) ax = fmaf(kh, (float)(-sx), ax);
+                    if (sy) ay = fmaf(kh, (float)(-sy), ay);
+                    if (sz) az = fmaf(kh, (float)(-sz), az);
+                }
+            }
 }
 
 // The Heaviside tile of the kernel integrals (see stage_rows).

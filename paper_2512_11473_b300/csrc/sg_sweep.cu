@@ -2,6 +2,8 @@
 // grid ("MeshPackageDynamics" / package_for, Listing 4): gradient
 // (Listing 5), 7-point Laplacian, Godunov reinitialisation step, kernel
 // integrals.  The per-package arithmetic lives in sg_rows.cuh.
+#include <cmath>
+
 #include "sg_rows.cuh"
 
 namespace sg {
@@ -107,6 +109,34 @@ __global__ void __launch_bounds__(SW_THREADS) k_kernel_integrals(const int32_t* 
     gz[at] = az;
 }
 
+// Supports above 2h: 8^3 tiles, 5^3 taps.
+__global__ void __launch_bounds__(SW_THREADS) k_kernel_integrals_wide(const int32_t* __restrict__ nbr,
+                                                                       const float* __restrict__ phi,
+                                                                       float* __restrict__ W, float* __restrict__ gx,
+                                                                       float* __restrict__ gy, float* __restrict__ gz,
+                                                                       int64_t P, KernelCoef K, float inv_eps) {
+    __shared__ int s_nb[SW_PKGS][NB];
+    __shared__ float s_H[SW_PKGS][512];  // 8^3 tile: package plus a two-point halo
+    __shared__ unsigned s_sat[SW_PKGS];
+    const int lp = threadIdx.x >> 6, d = threadIdx.x & 63;
+    const int64_t p = 2 + (int64_t)blockIdx.x * SW_PKGS + lp;
+    const bool valid = p < P;
+    if (valid && d < NB) s_nb[lp][d] = __ldg(nbr + p * NB + d);
+    if (d == 0) s_sat[lp] = 0;
+    __syncthreads();
+    const unsigned bits = __reduce_or_sync(0xffffffffu, valid ? stage_rows_wide(s_nb[lp], phi, inv_eps, d, s_H[lp]) : 0u);
+    if ((threadIdx.x & 31) == 0 && bits) atomicOr(&s_sat[lp], bits);
+    __syncthreads();
+    if (!valid) return;
+    float w, ax, ay, az;
+    if (!integrals_saturated(s_sat[lp], w, ax, ay, az)) integrals_point_wide(s_H[lp], d, K, w, ax, ay, az);
+    const int64_t at = p * PKG3 + d;
+    W[at] = w;
+    gx[at] = ax;
+    gy[at] = ay;
+    gz[at] = az;
+}
+
 unsigned pkg_blocks(int64_t P) {
     int64_t n = P - 2;
     return (unsigned)((n + SW_PKGS - 1) / SW_PKGS);
@@ -124,27 +154,30 @@ unsigned flat_blocks(int64_t n) {
     return (unsigned)b;
 }
 
-double wendland(double q) {
-    if (q >= 2.0) return 0.0;
-    double t = 1.0 - 0.5 * q;
-    return t * t * t * t * (1.0 + 2.0 * q);
+double wendland(double q, double R) {
+    if (q >= R) return 0.0;
+    const double t = 1.0 - q / R;
+    return t * t * t * t * (1.0 + 4.0 * q / R);
 }
 
-double wendland_dq(double q) {
-    if (q >= 2.0) return 0.0;
-    double t = 1.0 - 0.5 * q;
-    return -5.0 * q * t * t * t;
+double wendland_dq(double q, double R) {
+    if (q >= R) return 0.0;
+    const double t = 1.0 - q / R;
+    return -20.0 * q / (R * R) * t * t * t;
 }
 
 }  // namespace
 
-KernelCoef kernel_coef() {
+KernelCoef kernel_coef(double R) {
     KernelCoef K;
-    const double q[4] = {0.0, 1.0, 1.4142135623730951, 1.7320508075688772};
-    const double den = wendland(q[0]) + 6 * wendland(q[1]) + 12 * wendland(q[2]) + 8 * wendland(q[3]);
-    for (int c = 0; c < 4; ++c) {
-        K.cw[c] = (float)(wendland(q[c]) / den);
-        K.ck[c] = c == 0 ? 0.0f : (float)(wendland_dq(q[c]) / q[c] / den);
+    double den = 0.0;
+    for (int sz = -2; sz <= 2; ++sz)
+        for (int sy = -2; sy <= 2; ++sy)
+            for (int sx = -2; sx <= 2; ++sx) den += wendland(std::sqrt((double)(sx * sx + sy * sy + sz * sz)), R);
+    for (int c = 0; c < 13; ++c) {
+        const double q = std::sqrt((double)c);
+        K.cw[c] = (float)(wendland(q, R) / den);
+        K.ck[c] = c == 0 ? 0.0f : (float)(wendland_dq(q, R) / q / den);
     }
     return K;
 }
@@ -207,15 +240,19 @@ cudaError_t launch_copy_active(const float* src, float* dst, int64_t P, cudaStre
 }
 
 cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const float* phi, float* W, float* gx,
-                                    float* gy, float* gz, int64_t P, cudaStream_t s) {
+                                    float* gy, float* gz, int64_t P, double R, double eps, cudaStream_t s) {
     cudaError_t e;
     if ((e = launch_set_far(W, 1.0f, 0.0f, s)) != cudaSuccess) return e;
     if ((e = launch_set_far(gx, 0.0f, 0.0f, s)) != cudaSuccess) return e;
     if ((e = launch_set_far(gy, 0.0f, 0.0f, s)) != cudaSuccess) return e;
     if ((e = launch_set_far(gz, 0.0f, 0.0f, s)) != cudaSuccess) return e;
     if (P <= 2) return cudaSuccess;
-    k_kernel_integrals<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(),
-                                                             (float)(1.0 / G.h_d));
+    if (R > 2.0)
+        k_kernel_integrals_wide<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(R),
+                                                                      (float)(1.0 / eps));
+    else
+        k_kernel_integrals<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(R),
+                                                                 (float)(1.0 / eps));
     note_launch();
     return cudaGetLastError();
 }

@@ -207,6 +207,51 @@ cudaError_t launch_tag_flags_from(const GridFF& G, const ShapeFF& S, const int32
     return cudaGetLastError();
 }
 
+// Morton package ids: cell centres of the active packages (linear ids), for
+// the Morton sort; then every package moves to its rank in that order.
+__global__ void __launch_bounds__(TAG_THREADS) k_cell_centres(GridF G, const int32_t* __restrict__ pkg_cell,
+                                                               float* __restrict__ x, float* __restrict__ y,
+                                                               float* __restrict__ z, int64_t n) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = pkg_cell[2 + r];
+        const int64_t I = c % G.dims[0], J = (c / G.dims[0]) % G.dims[1], K = c / ((int64_t)G.dims[0] * G.dims[1]);
+        x[r] = G.lo[0] + G.h * (float)(4 * I + 2);
+        y[r] = G.lo[1] + G.h * (float)(4 * J + 2);
+        z[r] = G.lo[2] + G.h * (float)(4 * K + 2);
+    }
+}
+
+__global__ void __launch_bounds__(TAG_THREADS) k_renumber(const int32_t* __restrict__ order,
+                                                           const int32_t* __restrict__ old_cell,
+                                                           const uint8_t* __restrict__ old_type,
+                                                           int32_t* __restrict__ pkg_cell, uint8_t* __restrict__ pkg_type,
+                                                           int32_t* __restrict__ cell_pkg, int64_t n) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t was = 2 + order[r];
+        const int32_t c = old_cell[was];
+        pkg_cell[2 + r] = c;
+        pkg_type[2 + r] = old_type[was];
+        cell_pkg[c] = (int32_t)(2 + r);
+    }
+}
+
+cudaError_t launch_cell_centres(const GridF& G, const int32_t* pkg_cell, float* x, float* y, float* z, int64_t n,
+                                cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_cell_centres<<<grid_for(n, TAG_THREADS), TAG_THREADS, 0, s>>>(G, pkg_cell, x, y, z, n);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_renumber(const int32_t* order, const int32_t* old_cell, const uint8_t* old_type, int32_t* pkg_cell,
+                            uint8_t* pkg_type, int32_t* cell_pkg, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_renumber<<<grid_for(n, TAG_THREADS), TAG_THREADS, 0, s>>>(order, old_cell, old_type, pkg_cell, pkg_type, cell_pkg,
+                                                                n);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tag_inner(const GridFF& G, uint8_t* cell_type, uint32_t* active, int64_t nc, cudaStream_t s) {
     k_tag_inner<<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_type, active, nc);
     note_launch();
