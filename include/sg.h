@@ -476,8 +476,24 @@ SG_API int64_t sg_n_packages(const sg_grid *g);
 SG_API sg_status sg_set_stream(sg_grid *g, void *stream);
 
 /* Synchronise the grid's stream and return the sticky device error status
- * (SG_OK, SG_ERR_DEVICE or SG_ERR_TIMEOUT) or SG_ERR_CUDA. */
+ * (SG_OK, SG_ERR_DEVICE or SG_ERR_TIMEOUT) or SG_ERR_CUDA.  The word stays
+ * set until sg_clear_error. */
 SG_API sg_status sg_status_sync(sg_grid *g);
+
+/* Check the tables of a tagged grid on the device (asynchronous; the result
+ * is the sticky word read by sg_status_sync): every package and neighbour
+ * id in range, far packages their own neighbours (Sec. "Neighbourhood"),
+ * each active package its own centre entry and its cell's package, every
+ * neighbour entry the package of that neighbour cell (the outside far
+ * package beyond the domain), the face rows copies of the neighbour rows,
+ * every cell's package naming it back.  Every read is bounds-checked before
+ * use, so tables edited through sg_get_field pointers can be checked before
+ * a sweep reads them.  Sets SG_ERR_DEVICE on any inconsistency.
+ * Errors: SG_ERR_STATE (not tagged). */
+SG_API sg_status sg_check_tables(sg_grid *g);
+
+/* Reset the sticky device error word (queued on the grid's stream). */
+SG_API sg_status sg_clear_error(sg_grid *g);
 
 /* Message of the last failed call on this grid ("" if none). */
 SG_API const char *sg_last_error(const sg_grid *g);

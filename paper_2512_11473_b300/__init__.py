@@ -104,6 +104,8 @@ def lib():
         L.sg_n_packages.argtypes = [vp]
         L.sg_n_packages.restype = i64
         L.sg_set_stream.argtypes = [vp, vp]
+        L.sg_check_tables.argtypes = [vp]
+        L.sg_clear_error.argtypes = [vp]
         L.sg_status_sync.argtypes = [vp]
         L.sg_last_error.argtypes = [vp]
         L.sg_last_error.restype = C.c_char_p
@@ -250,6 +252,14 @@ class Grid:
     def sync(self):
         """Synchronise the stream; raise on a sticky device error."""
         self._check(self._lib.sg_status_sync(self._h))
+
+    def check_tables(self):
+        """Queue the device check of the cell, package, neighbour and face
+        tables; a later sync() raises if they disagree."""
+        self._check(self._lib.sg_check_tables(self._h))
+
+    def clear_error(self):
+        self._check(self._lib.sg_clear_error(self._h))
 
     # -- the hot path --------------------------------------------------------
     def tag_allocate(self, shape) -> int:

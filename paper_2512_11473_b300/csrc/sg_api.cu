@@ -577,6 +577,24 @@ sg_status sg_get_field(sg_grid* g, int32_t field, void** dev_ptr, int64_t* n_ele
     }
 }
 
+sg_status sg_check_tables(sg_grid* g) {
+    SG_CHECK_GRID(g);
+    if (g->state < 1) return fail(g, SG_ERR_STATE, "sg_check_tables: grid not tagged");
+    DeviceGuard dg(g->device);
+    SG_CUDA(g, launch_check_tables(grid_ff(g), (const int32_t*)g->cell_pkg.p, (const int32_t*)g->pkg_cell.p,
+                                   (const uint8_t*)g->pkg_type.p, (const int32_t*)g->nbr.p, (const int32_t*)g->faces.p,
+                                   g->P, g->nc, (int*)g->err.p, g->stream),
+            "check tables");
+    return SG_OK;
+}
+
+sg_status sg_clear_error(sg_grid* g) {
+    SG_CHECK_GRID(g);
+    DeviceGuard dg(g->device);
+    SG_CUDA(g, cudaMemsetAsync(g->err.p, 0, sizeof(int32_t), g->stream), "clear error");
+    return SG_OK;
+}
+
 sg_status sg_status_sync(sg_grid* g) {
     SG_CHECK_GRID(g);
     DeviceGuard dg(g->device);

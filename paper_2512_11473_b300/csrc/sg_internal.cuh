@@ -95,6 +95,11 @@ cudaError_t launch_tag_flags(const GridFF& G, const ShapeFF& S, uint8_t* cell_ty
 cudaError_t launch_tag_flags_from(const GridFF& G, const ShapeFF& S, const int32_t* c_cell_pkg,
                                   const uint8_t* c_pkg_type, const float* c_phi, int cnx, int cny, uint8_t* cell_type,
                                   uint32_t* active, int64_t nc, unsigned long long* evaluated, cudaStream_t s);
+// Consistency of the cell, package, neighbour and face tables; sets
+// ERR_BAD_INDEX in *err on any inconsistency (reads are bounds-checked).
+cudaError_t launch_check_tables(const GridFF& G, const int32_t* cell_pkg, const int32_t* pkg_cell,
+                                const uint8_t* pkg_type, const int32_t* nbr, const int32_t* faces, int64_t P,
+                                int64_t nc, int* err, cudaStream_t s);
 // Morton package ids: cell centres of the n active packages (linear ids),
 // then the move of package 2 + order[r] to id 2 + r (tables and cells).
 cudaError_t launch_cell_centres(const GridF& G, const int32_t* pkg_cell, float* x, float* y, float* z, int64_t n,

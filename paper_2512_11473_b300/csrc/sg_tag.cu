@@ -164,6 +164,55 @@ __global__ void __launch_bounds__(TAG_THREADS) k_fill_faces(const int32_t* __res
     }
 }
 
+// Table check: every id in range, far packages their own neighbours, each
+// active package its own centre entry and its cell's package, every
+// neighbour entry the package of that neighbour cell (1 outside the domain),
+// the face rows copies of the neighbour rows, every cell's package in range
+// and naming it back.  Every read is bounds-checked first; an inconsistency
+// sets ERR_BAD_INDEX in *err.
+__global__ void __launch_bounds__(TAG_THREADS) k_check_tables(GridFF G, const int32_t* __restrict__ cell_pkg,
+                                                               const int32_t* __restrict__ pkg_cell,
+                                                               const uint8_t* __restrict__ pkg_type,
+                                                               const int32_t* __restrict__ nbr,
+                                                               const int32_t* __restrict__ faces, int64_t P,
+                                                               int64_t nc, int* err) {
+    const int face_n[6] = {12, 14, 10, 16, 4, 22};
+    const int64_t nx = G.dims[0], ny = G.dims[1], nz = G.dims[2];
+    bool bad = false;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P + nc; e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < P) {
+            const int64_t p = e;
+            const int32_t* row = nbr + p * NB;
+            for (int n = 0; n < NB; ++n) bad |= row[n] < 0 || row[n] >= P || (p < 2 && row[n] != p);
+            if (p >= 2) {
+                bad |= row[13] != p || pkg_type[p] < 2 || pkg_type[p] > 3;
+                const int64_t c = pkg_cell[p];
+                if (c < 0 || c >= nc) {
+                    bad = true;
+                } else {
+                    bad |= cell_pkg[c] != p;
+                    const int64_t I = c % nx, J = (c / nx) % ny, K = c / (nx * ny);
+                    for (int n = 0; n < NB; ++n) {
+                        const int64_t a = I + n % 3 - 1, b = J + (n / 3) % 3 - 1, k = K + n / 9 - 1;
+                        const bool in = a >= 0 && b >= 0 && k >= 0 && a < nx && b < ny && k < nz;
+                        bad |= row[n] != (in ? cell_pkg[a + nx * (b + ny * k)] : 1);
+                    }
+                }
+            }
+            for (int f = 0; f < 6; ++f) bad |= faces[p * 8 + f] != row[face_n[f]];
+            bad |= faces[p * 8 + 6] != 0 || faces[p * 8 + 7] != 0;
+        } else {
+            const int64_t c = e - P;
+            const int64_t v = cell_pkg[c];
+            if (v < 0 || v >= P)
+                bad = true;
+            else if (v >= 2)
+                bad |= pkg_cell[v] != c;
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, ERR_BAD_INDEX);
+}
+
 // Step 4: phi at cell-centred data points, float-float, rounded once.
 __global__ void __launch_bounds__(TAG_THREADS) k_init_sdf(GridFF G, ShapeFF S, const int32_t* __restrict__ pkg_cell,
                                                            float* __restrict__ phi, int64_t P) {
@@ -233,6 +282,15 @@ __global__ void __launch_bounds__(TAG_THREADS) k_renumber(const int32_t* __restr
         pkg_type[2 + r] = old_type[was];
         cell_pkg[c] = (int32_t)(2 + r);
     }
+}
+
+cudaError_t launch_check_tables(const GridFF& G, const int32_t* cell_pkg, const int32_t* pkg_cell,
+                                const uint8_t* pkg_type, const int32_t* nbr, const int32_t* faces, int64_t P,
+                                int64_t nc, int* err, cudaStream_t s) {
+    k_check_tables<<<grid_for(P + nc, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_pkg, pkg_cell, pkg_type, nbr, faces,
+                                                                         P, nc, err);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cell_centres(const GridF& G, const int32_t* pkg_cell, float* x, float* y, float* z, int64_t n,

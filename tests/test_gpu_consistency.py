@@ -78,6 +78,8 @@ def test_consistency_restores_and_matches_oracle(sg, name):
     assert torch.equal(g.field("cell_pkg"), clean["cell_pkg"])
     assert torch.equal(g.field("nbr"), clean["nbr"])
     assert np.array_equal(H(g.field("nbr"))[:, [12, 14, 10, 16, 4, 22]], faces0)
+    g.check_tables()  # the rebuilt neighbour and face tables agree with the cells
+    g.sync()
     # step-wise: the oracle on the device's noisy float32 input
     cp2, nb2, phi2, ch = oracle.consistency_correct(spec, O.P, noisy_cp, O.pkg_cell, O.pkg_type, O.nbr, noisy_phi)
     assert ch == (out[0], out[1])

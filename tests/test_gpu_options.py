@@ -143,3 +143,37 @@ def test_batch_with_eps_equals_single(sg):
     for i, w in enumerate(ref):
         assert torch.equal(b.field(i, "W"), w)
     b.close()
+
+
+def test_check_tables_and_sticky_error(sg):
+    """Tables edited through borrowed pointers: the device check finds an
+    out-of-range neighbour id, a neighbour entry that names the wrong package
+    and a cell whose package does not name it back; the word stays set until
+    cleared.  No sweep runs on an edited table."""
+    shape, spec = si.sphere_small()
+    g = sg.Grid(spec)
+    P = g.tag_allocate(shape)
+    g.check_tables()
+    g.sync()
+    nbr, cp = g.field("nbr"), g.field("cell_pkg")
+    act = torch.nonzero(cp >= 2).flatten()
+    for edit in ("range", "neighbour", "cell"):
+        nb0, cp0 = nbr.clone(), cp.clone()
+        if edit == "range":
+            nbr[5, 3] = P + 7
+        elif edit == "neighbour":
+            nbr[5, 3] = 5 if int(nbr[5, 3]) != 5 else 6
+        else:
+            c = int(act[10])
+            cp[c] = int(cp[int(act[11])])
+        g.check_tables()
+        with pytest.raises(sg.SgError):
+            g.sync()
+        with pytest.raises(sg.SgError):  # sticky
+            g.sync()
+        nbr.copy_(nb0)
+        cp.copy_(cp0)
+        g.clear_error()
+        g.check_tables()
+        g.sync()
+    g.close()
