@@ -201,7 +201,7 @@ class Grid:
     construction).
     """
 
-    def __init__(self, spec, far_value=0.0, stream=None, torch_allocator=True):
+    def __init__(self, spec, far_value=0.0, stream=None, torch_allocator=True, allocator=None):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2512_11473_b300 needs a CUDA device")
@@ -210,7 +210,8 @@ class Grid:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.spec = spec
         d = _desc(spec, far_value)
-        self._alloc = _TorchAllocator(self.device) if torch_allocator else None
+        # allocator: any object with an sg_allocator ``struct`` (kept alive here)
+        self._alloc = allocator if allocator is not None else (_TorchAllocator(self.device) if torch_allocator else None)
         h = C.c_void_p()
         st = self._lib.sg_create(C.byref(d), C.byref(self._alloc.struct) if self._alloc else None,
                                  C.c_void_p(self.stream.cuda_stream), C.byref(h))

@@ -177,3 +177,59 @@ def test_check_tables_and_sticky_error(sg):
         g.check_tables()
         g.sync()
     g.close()
+
+
+class _Budget:
+    """A device-memory hook that refuses any allocation past a byte budget."""
+
+    def __init__(self, sg, budget):
+        self.budget, self.used, self.sizes = budget, 0, {}
+
+        def _alloc(nbytes, stream, ctx):
+            if self.used + nbytes > self.budget:
+                return None
+            p = torch.cuda.caching_allocator_alloc(int(nbytes), device=0, stream=stream or 0)
+            self.used += nbytes
+            self.sizes[p] = nbytes
+            return p
+
+        def _free(ptr, nbytes, stream, ctx):
+            self.used -= self.sizes.pop(ptr, 0)
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc_fn, self.free_fn = sg.ALLOC_FN(_alloc), sg.FREE_FN(_free)
+        self.struct = sg.sg_allocator(self.alloc_fn, self.free_fn, None)
+
+
+def test_allocator_failure_is_reported(sg):
+    """An allocator that runs dry gives SG_ERR_OOM, the grid keeps its previous
+    state, later calls succeed once memory is there, and every byte is
+    returned at the end."""
+    shape, spec = si.sphere_small()
+    B = _Budget(sg, 4096)
+    g = sg.Grid(spec, allocator=B)
+    with pytest.raises(sg.SgError) as e:
+        g.tag_allocate(shape)  # cell tables do not fit
+    assert e.value.status == 2
+    with pytest.raises(sg.SgError) as e:
+        g.init_sdf(shape)  # still untagged
+    assert e.value.status == 4
+    B.budget = 1 << 30
+    P = g.tag_allocate(shape)
+    assert P == 1634
+    B.budget = B.used + 1000  # the level set (P x 64 floats) does not fit
+    with pytest.raises(sg.SgError) as e:
+        g.init_sdf(shape)
+    assert e.value.status == 2
+    B.budget = 1 << 30
+    g.init_sdf(shape)
+    g.gradient()
+    ref = sg.Grid(spec)
+    ref.tag_allocate(shape)
+    ref.init_sdf(shape)
+    ref.gradient()
+    assert torch.equal(g.field("gx"), ref.field("gx"))
+    ref.close()
+    g.close()
+    torch.cuda.synchronize()
+    assert B.used == 0 and not B.sizes
