@@ -119,6 +119,16 @@ ShapeFF shape_ff(const sg_shape* s) {
         S.pf[i] = (float)s->p[i];
     }
     S.plain = plain ? 1 : 0;
+    // prism edges (a -> b: vertex 0 -> 1, 1 -> 2, 2 -> 0) and orientation
+    const double* t = s->p;
+    for (int k = 0; k < 3; ++k) {
+        const int a = 2 * k, b = (2 * k + 2) % 6;
+        const double ex = t[b] - t[a], ey = t[b + 1] - t[a + 1], l2 = ex * ex + ey * ey;
+        S.seg[3 * k] = split(ex);
+        S.seg[3 * k + 1] = split(ey);
+        S.seg[3 * k + 2] = split(l2 > 0.0 ? 1.0 / l2 : 0.0);
+    }
+    S.orient = (t[2] - t[0]) * (t[5] - t[1]) - (t[3] - t[1]) * (t[4] - t[0]) > 0.0 ? 1 : -1;
     return S;
 }
 

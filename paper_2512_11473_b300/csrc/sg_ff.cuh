@@ -112,6 +112,10 @@ struct ShapeFF {
     ff rot[9];  // row-major, local -> world
     ff p[8];
     float cf[3], rf[9], pf[8];  // the same in float, for the float pre-filter
+    // prism: per edge k (a -> b: 0 -> 1, 1 -> 2, 2 -> 0) e = b - a and
+    // 1 / |e|^2 (seg[3k .. 3k+2]), and the sign of the triangle's orientation
+    ff seg[9];
+    int orient;
 };
 
 // local coordinates q = R^T (x - centre)
@@ -122,30 +126,69 @@ __device__ __forceinline__ void ff_to_local(const ShapeFF& s, const ff x[3], ff 
         q[i] = ff_add(ff_add(ff_mul(s.rot[i], d[0]), ff_mul(s.rot[3 + i], d[1])), ff_mul(s.rot[6 + i], d[2]));
 }
 
-// squared distance from p to the segment a-b, all in the plane
-__device__ __forceinline__ ff ff_seg_dist2(ff px, ff py, ff ax, ff ay, ff bx, ff by) {
-    ff ex = ff_sub(bx, ax), ey = ff_sub(by, ay);
+
+__device__ __forceinline__ ff ff_cross(ff ax, ff ay, ff bx, ff by) { return ff_sub(ff_mul(ax, by), ff_mul(ay, bx)); }
+
+// squared distance from p to the edge from a along e, with 1 / |e|^2 given
+__device__ __forceinline__ ff ff_edge_dist2(ff px, ff py, ff ax, ff ay, ff ex, ff ey, ff inv_len2) {
     ff wx = ff_sub(px, ax), wy = ff_sub(py, ay);
-    ff t = ff_clamp01(ff_div(ff_add(ff_mul(wx, ex), ff_mul(wy, ey)), ff_add(ff_sqr(ex), ff_sqr(ey))));
+    ff t = ff_clamp01(ff_mul(ff_add(ff_mul(wx, ex), ff_mul(wy, ey)), inv_len2));
     ff dx = ff_sub(wx, ff_mul(t, ex)), dy = ff_sub(wy, ff_mul(t, ey));
     return ff_add(ff_sqr(dx), ff_sqr(dy));
 }
 
-__device__ __forceinline__ ff ff_cross(ff ax, ff ay, ff bx, ff by) { return ff_sub(ff_mul(ax, by), ff_mul(ay, bx)); }
+__device__ __forceinline__ float f_seg_dist2(float px, float py, float ax, float ay, float bx, float by);
 
-__device__ inline ff ff_triangle_sdf(ff px, ff py, const ff* t) {
-    ff d2 = ff_seg_dist2(px, py, t[0], t[1], t[2], t[3]);
-    d2 = ff_min(d2, ff_seg_dist2(px, py, t[2], t[3], t[4], t[5]));
-    d2 = ff_min(d2, ff_seg_dist2(px, py, t[4], t[5], t[0], t[1]));
-    ff orient = ff_cross(ff_sub(t[2], t[0]), ff_sub(t[3], t[1]), ff_sub(t[4], t[0]), ff_sub(t[5], t[1]));
-    ff c0 = ff_cross(ff_sub(t[2], t[0]), ff_sub(t[3], t[1]), ff_sub(px, t[0]), ff_sub(py, t[1]));
-    ff c1 = ff_cross(ff_sub(t[4], t[2]), ff_sub(t[5], t[3]), ff_sub(px, t[2]), ff_sub(py, t[3]));
-    ff c2 = ff_cross(ff_sub(t[0], t[4]), ff_sub(t[1], t[5]), ff_sub(px, t[4]), ff_sub(py, t[5]));
-    const ff zero{0.0f, 0.0f};
-    bool inside = ff_gt(orient, zero) ? (ff_gt(c0, zero) && ff_gt(c1, zero) && ff_gt(c2, zero))
-                                      : (ff_lt(c0, zero) && ff_lt(c1, zero) && ff_lt(c2, zero));
-    ff d = ff_sqrt(d2);
-    return inside ? ff_neg(d) : d;
+// Signed distance to a triangle (negative inside) in float-float.  A float
+// pass first bounds each edge's squared distance (error below
+// 2 |d| delta + delta^2 + 2.4e-7 d^2 with delta = 1e-6 (1 + |p|), generous
+// for these few operations on inputs rounded to float): only the edges that
+// can hold the minimum are evaluated in float-float.  The inside test is
+// decided by float cross products when all three are clear of zero by their
+// error bound, else in float-float.
+__device__ inline ff ff_triangle_sdf(ff px, ff py, const ShapeFF& s) {
+    const ff* t = s.p;
+    const float* tf = s.pf;
+    const float fx = px.hi, fy = py.hi;
+    const float scale = 1.0f + fabsf(fx) + fabsf(fy), delta = 1e-6f * scale;
+    float d[3], hi[3];
+    d[0] = f_seg_dist2(fx, fy, tf[0], tf[1], tf[2], tf[3]);
+    d[1] = f_seg_dist2(fx, fy, tf[2], tf[3], tf[4], tf[5]);
+    d[2] = f_seg_dist2(fx, fy, tf[4], tf[5], tf[0], tf[1]);
+    float tol[3], up = INFINITY;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        tol[k] = 2.0f * sqrtf(d[k]) * delta + delta * delta + 2.4e-7f * d[k];
+        hi[k] = d[k] + tol[k];
+        up = fminf(up, hi[k]);
+    }
+    ff d2{INFINITY, 0.0f};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (d[k] - tol[k] > up) continue;  // cannot be the nearest edge
+        const int a = 2 * k;
+        d2 = ff_min(d2, ff_edge_dist2(px, py, t[a], t[a + 1], s.seg[3 * k], s.seg[3 * k + 1], s.seg[3 * k + 2]));
+    }
+    const float ctol = 8e-6f * scale * scale;
+    float c[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int a = 2 * k, b = (2 * k + 2) % 6;
+        c[k] = (tf[b] - tf[a]) * (fy - tf[a + 1]) - (tf[b + 1] - tf[a + 1]) * (fx - tf[a]);
+    }
+    bool inside;
+    if (fabsf(c[0]) > ctol && fabsf(c[1]) > ctol && fabsf(c[2]) > ctol) {
+        inside = s.orient > 0 ? (c[0] > 0.0f && c[1] > 0.0f && c[2] > 0.0f) : (c[0] < 0.0f && c[1] < 0.0f && c[2] < 0.0f);
+    } else {
+        ff c0 = ff_cross(ff_sub(t[2], t[0]), ff_sub(t[3], t[1]), ff_sub(px, t[0]), ff_sub(py, t[1]));
+        ff c1 = ff_cross(ff_sub(t[4], t[2]), ff_sub(t[5], t[3]), ff_sub(px, t[2]), ff_sub(py, t[3]));
+        ff c2 = ff_cross(ff_sub(t[0], t[4]), ff_sub(t[1], t[5]), ff_sub(px, t[4]), ff_sub(py, t[5]));
+        const ff zero{0.0f, 0.0f};
+        inside = s.orient > 0 ? (ff_gt(c0, zero) && ff_gt(c1, zero) && ff_gt(c2, zero))
+                              : (ff_lt(c0, zero) && ff_lt(c1, zero) && ff_lt(c2, zero));
+    }
+    ff dd = ff_sqrt(d2);
+    return inside ? ff_neg(dd) : dd;
 }
 
 // Exact signed distance (negative inside) of each primitive, in float-float.
@@ -172,7 +215,7 @@ __device__ inline ff ff_sdf(const ShapeFF& s, const ff x[3]) {
         return ff_sub(ff_sqrt(ff_add(ff_sqr(a), ff_sqr(q[2]))), s.p[1]);
     }
     case SHAPE_PRISM: {
-        ff w0 = ff_triangle_sdf(q[0], q[1], s.p);
+        ff w0 = ff_triangle_sdf(q[0], q[1], s);
         ff zc = ff_mul_f(ff_add(s.p[6], s.p[7]), 0.5f);
         ff hz = ff_mul_f(ff_sub(s.p[7], s.p[6]), 0.5f);
         ff w1 = ff_sub(ff_abs(ff_sub(q[2], zc)), hz);
