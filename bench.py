@@ -773,7 +773,7 @@ def run_sg(args):
     hbm, peak_kind = measured_peaks()
     achieved = alg_bytes / (sweep_ms[big.name] * 1e-3) / 1e9
     csrc = os.path.join(ROOT, "paper_2512_11473_b300", "csrc")
-    prof = profile_traffic([os.path.join(csrc, "sg_sweep.cu"), os.path.join(csrc, "sg_rows.cuh")],
+    prof = profile_traffic([os.path.join(csrc, "sg_reinit.cu"), os.path.join(csrc, "sg_rows.cuh")],
                            "reinit_step_torus_h0.002.md")
     traffic = None
     if prof is not None:

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "sg_probe.cuh"
+#include "sg_integrals.cuh"
 #include "sg_rows.cuh"
 
 struct sg_batch_graph {

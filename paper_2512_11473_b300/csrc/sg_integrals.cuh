@@ -1,0 +1,167 @@
+// sg_integrals.cuh -- kernel-integral device code shared by the exact
+// integrals (sg_sweep.cu), the batched sweeps (sg_batch.cu) and the
+// surrogate's staging and fallback (sg_mlp.cu).
+//
+// Kernel integrals: 64 threads own a package, stage the smoothed Heaviside of
+// a 6^3 tile (package plus a one-point halo) in shared memory, one x-row of
+// six per thread (four interior points from one package by a 16-byte load,
+// the two halo points from the -x and +x packages of the index shift), and
+// sum the 27 non-zero taps from there; supports above 2h use 8^3 tiles and
+// the 5^3 taps.
+#pragma once
+#include "sg_internal.cuh"
+
+namespace sg {
+
+// Kernel integrals.  Tap weights by squared distance |s|^2 in {0..12} (the
+// 5^3 stencil): cw = w(|s|) / sum w, ck = w'(|s|) / |s| / sum w, for the
+// Wendland C2 of support R h, w(q) = (1 - q/R)^4 (1 + 4q/R) (0 at q >= R).
+struct KernelCoef {
+    float cw[13];
+    float ck[13];
+};
+
+// host: the tap coefficients for support R h (R <= 3), normalised by the
+// discrete sum of the taps
+KernelCoef kernel_coef(double R = 2.0);
+
+namespace {
+
+__device__ __forceinline__ float heaviside_neg(float phi, float inv_eps) {
+    // H(z) at z = -phi with half width eps: 0 below -eps, 1 above eps,
+    // 1/2 (1 + z/eps + sin(pi z/eps)/pi) between; the sine is the hardware
+    // approximation (absolute error about 5e-7 on [-pi, pi], far below the
+    // 1e-5 the integrals are held to)
+    float t = -phi * inv_eps;
+    if (t < -1.0f) return 0.0f;
+    if (t > 1.0f) return 1.0f;
+    return 0.5f * (1.0f + t + __sinf(3.14159265358979323846f * t) * 0.318309886183790672f);
+}
+
+// Stage the package's 6^3 tile (the package plus a one-point halo) by
+// x-rows, one row of six per thread d < 36: four interior points from one
+// package (a 16-byte load) and the two halo points from the -x and +x
+// packages of the index shift (Listing 2).  Writes phi to tphi and the
+// smoothed Heaviside to tH (either may be null); returns the saturation
+// bits of the H values this thread staged: bit 0 unless all were 0, bit 1
+// unless all were 1 (a tile whose bits OR to 1 is all ones, to 2 all zeros).
+__device__ __forceinline__ unsigned stage_rows(const int* nb27, const float* __restrict__ phi, float inv_eps, int d,
+                                               float* tphi, float* tH) {
+    unsigned bits = 0;
+    if (d < 36) {
+        const int y = d % 6 - 1, z = d / 6 - 1;
+        const int oy = ((y + 4) >> 2) - 1, oz = ((z + 4) >> 2) - 1;
+        const int d0 = 4 * (y - 4 * oy) + 16 * (z - 4 * oz);
+        const int nb = 3 * (oy + 1) + 9 * (oz + 1);
+        const float4 v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb27[nb + 1] * PKG3 + d0));
+        const float vm = __ldg(phi + (int64_t)nb27[nb] * PKG3 + d0 + 3);
+        const float vp = __ldg(phi + (int64_t)nb27[nb + 2] * PKG3 + d0);
+        const int e0 = 6 * (y + 1) + 36 * (z + 1);
+        const float f[6] = {vm, v.x, v.y, v.z, v.w, vp};
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            if (tphi) tphi[e0 + i] = f[i];
+            if (tH) {
+                const float hv = heaviside_neg(f[i], inv_eps);
+                tH[e0 + i] = hv;
+                bits |= (hv != 0.0f ? 1u : 0u) | (hv != 1.0f ? 2u : 0u);
+            }
+        }
+    }
+    return bits;
+}
+
+// Supports above 2h reach two points: the package's 8^3 tile (a two-point
+// halo) is staged by x-rows, one per thread (64 rows of eight: four interior
+// points by a 16-byte load, two from the -x and two from the +x package by
+// 8-byte loads).  Returns saturation bits as stage_rows.
+__device__ __forceinline__ unsigned stage_rows_wide(const int* nb27, const float* __restrict__ phi, float inv_eps,
+                                                    int d, float* tH) {
+    const int y = d % 8 - 2, z = d / 8 - 2;
+    const int oy = ((y + 4) >> 2) - 1, oz = ((z + 4) >> 2) - 1;
+    const int d0 = 4 * (y - 4 * oy) + 16 * (z - 4 * oz);
+    const int nb = 3 * (oy + 1) + 9 * (oz + 1);
+    const float2 m = __ldg(reinterpret_cast<const float2*>(phi + (int64_t)nb27[nb] * PKG3 + d0 + 2));
+    const float4 v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb27[nb + 1] * PKG3 + d0));
+    const float2 pp = __ldg(reinterpret_cast<const float2*>(phi + (int64_t)nb27[nb + 2] * PKG3 + d0));
+    const float f[8] = {m.x, m.y, v.x, v.y, v.z, v.w, pp.x, pp.y};
+    float* t = tH + 8 * (y + 2) + 64 * (z + 2);
+    unsigned bits = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float hv = heaviside_neg(f[i], inv_eps);
+        t[i] = hv;
+        bits |= (hv != 0.0f ? 1u : 0u) | (hv != 1.0f ? 2u : 0u);
+    }
+    return bits;
+}
+
+// The 5^3 tap sums of data point d from an 8^3 tile (taps with |s|^2 >= 9
+// carry no weight for supports up to 3h).
+__device__ __forceinline__ void integrals_point_wide(const float* tile, int d, const KernelCoef& K, float& w,
+                                                     float& ax, float& ay, float& az) {
+    const int i = d & 3, j = (d >> 2) & 3, k = d >> 4;
+    const float* H = tile + (i + 2) + 8 * (j + 2) + 64 * (k + 2);
+    w = 0.0f;
+    ax = ay = az = 0.0f;
+#pragma unroll
+    for (int sz = -2; sz <= 2; ++sz)
+#pragma unroll
+        for (int sy = -2; sy <= 2; ++sy)
+#pragma unroll
+            for (int sx = -2; sx <= 2; ++sx) {
+                const int q2 = sx * sx + sy * sy + sz * sz;
+                if (q2 >= 9) continue;
+                const float h = H[sx + 8 * sy + 64 * sz];
+                w = fmaf(K.cw[q2], h, w);
+                if (q2 > 0) {
+                    const float kh = K.ck[q2] * h;
+                    if (sx) ax = fmaf(kh, (float)(-sx), ax);
+                    if (sy) ay = fmaf(kh, (float)(-sy), ay);
+                    if (sz) az = fmaf(kh, (float)(-sz), az);
+                }
+            }
+}
+
+// The Heaviside tile of the kernel integrals (see stage_rows).
+__device__ __forceinline__ unsigned integrals_stage(const int* nb27, const float* __restrict__ phi, float inv_eps,
+                                                    int d, float* tile) {
+    return stage_rows(nb27, phi, inv_eps, d, nullptr, tile);
+}
+
+// The 27 taps around data point d of a staged tile.
+// A saturated tile (every H in it 0, or every H 1) gives W = that value and
+// G = 0 exactly (the normalised weights sum to one): the taps are skipped.
+__device__ __forceinline__ bool integrals_saturated(unsigned tile_bits, float& w, float& ax, float& ay, float& az) {
+    if (tile_bits == 3u) return false;
+    w = tile_bits == 1u ? 1.0f : 0.0f;
+    ax = ay = az = 0.0f;
+    return true;
+}
+
+__device__ __forceinline__ void integrals_point(const float* tile, int d, const KernelCoef& K, float& w,
+                                                float& ax, float& ay, float& az) {
+    const int i = d & 3, j = (d >> 2) & 3, k = d >> 4;
+    const float* H = tile + (i + 1) + 6 * (j + 1) + 36 * (k + 1);
+    w = 0.0f;
+    ax = ay = az = 0.0f;
+#pragma unroll
+    for (int sz = -1; sz <= 1; ++sz)
+#pragma unroll
+        for (int sy = -1; sy <= 1; ++sy)
+#pragma unroll
+            for (int sx = -1; sx <= 1; ++sx) {
+                const int q2 = sx * sx + sy * sy + sz * sz;
+                const float h = H[sx + 6 * sy + 36 * sz];
+                w = fmaf(K.cw[q2], h, w);
+                if (q2 > 0) {
+                    const float kh = K.ck[q2] * h;
+                    if (sx) ax = fmaf(kh, (float)(-sx), ax);
+                    if (sy) ay = fmaf(kh, (float)(-sy), ay);
+                    if (sz) az = fmaf(kh, (float)(-sz), az);
+                }
+            }
+}
+
+}  // namespace
+}  // namespace sg

@@ -22,6 +22,7 @@
 
 #include "sg_mlp.cuh"
 #include "sg_mma.cuh"
+#include "sg_integrals.cuh"
 #include "sg_rows.cuh"
 
 struct sg_mlp {

@@ -1,0 +1,56 @@
+// sg_reinit.cu -- the Godunov reinitialisation of one grid: the smoothed
+// sign of the level set at call entry and one Jacobi sweep over the active
+// packages (a half-warp per package, a float4 row per lane, the row code of
+// sg_rows.cuh shared with the batched sweeps).
+#include "sg_rows.cuh"
+
+namespace sg {
+namespace {
+
+constexpr int SW_THREADS = 256;
+
+unsigned flat_blocks(int64_t n) {
+    int64_t b = (n + SW_THREADS - 1) / SW_THREADS;
+    if (b < 1) b = 1;
+    if (b > 148 * 64) b = 148 * 64;
+    return (unsigned)b;
+}
+
+__global__ void __launch_bounds__(SW_THREADS) k_reinit_s0(const float* __restrict__ phi, float* __restrict__ s0,
+                                                           int64_t n_act, float h2) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_act; e += (int64_t)gridDim.x * blockDim.x)
+        s0[2 * PKG3 + e] = smoothed_sign(phi[2 * PKG3 + e], h2);
+}
+
+__global__ void __launch_bounds__(ROW_THREADS, 8) k_reinit_step(const int32_t* __restrict__ faces,
+                                                              const float* __restrict__ s0,
+                                                              const float* __restrict__ phi_in,
+                                                              float* __restrict__ phi_out, int64_t P, float cfl,
+                                                              float dt) {
+    const RowSlot s = row_slot(P);
+    const float4 sg = s.valid ? __ldg(reinterpret_cast<const float4*>(s0) + s.q4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const Rows w = load_rows(phi_in, faces, s);
+    if (!s.valid) return;
+    reinterpret_cast<float4*>(phi_out)[s.q4] = reinit_row(w, sg, cfl, dt);
+}
+
+}  // namespace
+
+cudaError_t launch_reinit_s0(const GridF& G, const float* phi, float* s0, int64_t P, cudaStream_t s) {
+    if (P <= 2) return cudaSuccess;
+    int64_t n = (P - 2) * PKG3;
+    k_reinit_s0<<<flat_blocks(n), SW_THREADS, 0, s>>>(phi, s0, n, (float)(G.h_d * G.h_d));
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reinit_step(const GridF& G, const int32_t* faces, const float* s0, const float* phi_in,
+                               float* phi_out, float dt, int64_t P, cudaStream_t s) {
+    if (P <= 2) return cudaSuccess;
+    // dt sqrt(G) = (dt / h) sqrt(h^2 G) and dt / h is the CFL number
+    k_reinit_step<<<row_blocks(P), ROW_THREADS, 0, s>>>(faces, s0, phi_in, phi_out, P, (float)(dt / G.h_d), dt);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace sg

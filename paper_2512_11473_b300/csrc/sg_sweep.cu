@@ -1,23 +1,19 @@
 // sg_sweep.cu -- per-package stencil sweeps over the active packages of one
 // grid ("MeshPackageDynamics" / package_for, Listing 4): gradient
-// (Listing 5), 7-point Laplacian, Godunov reinitialisation step, kernel
-// integrals.  The per-package arithmetic lives in sg_rows.cuh.
+// (Listing 5), 7-point Laplacian, the sequential update, kernel integrals.
+// The per-package arithmetic lives in sg_rows.cuh and sg_integrals.cuh; the
+// reinitialisation sweep has its own file, sg_reinit.cu.
 #include <cmath>
 
+#include "sg_integrals.cuh"
 #include "sg_rows.cuh"
 
 namespace sg {
 namespace {
 
-constexpr int ROW_THREADS = 256;
-constexpr int ROW_PKGS = ROW_THREADS / 16;  // packages per CTA (a half-warp each)
 constexpr int SW_THREADS = 256;
 constexpr int SW_PKGS = SW_THREADS / PKG3;  // packages per CTA (64 threads each)
 
-__device__ __forceinline__ RowSlot row_slot(int64_t P) {
-    const int64_t p = 2 + (int64_t)blockIdx.x * ROW_PKGS + (threadIdx.x >> 4);
-    return make_slot(p, p < P);
-}
 
 __global__ void __launch_bounds__(SW_THREADS) k_set_far(float* f, float v_in, float v_out) {
     f[threadIdx.x] = threadIdx.x < PKG3 ? v_in : v_out;
@@ -43,24 +39,6 @@ __global__ void __launch_bounds__(ROW_THREADS) k_laplacian(const int32_t* __rest
     const Rows w = load_rows(phi, faces, s);
     if (!s.valid) return;
     reinterpret_cast<float4*>(lap)[s.q4] = laplacian_row(w, inv_h2);
-}
-
-__global__ void __launch_bounds__(SW_THREADS) k_reinit_s0(const float* __restrict__ phi, float* __restrict__ s0,
-                                                           int64_t n_act, float h2) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_act; e += (int64_t)gridDim.x * blockDim.x)
-        s0[2 * PKG3 + e] = smoothed_sign(phi[2 * PKG3 + e], h2);
-}
-
-__global__ void __launch_bounds__(ROW_THREADS, 8) k_reinit_step(const int32_t* __restrict__ faces,
-                                                              const float* __restrict__ s0,
-                                                              const float* __restrict__ phi_in,
-                                                              float* __restrict__ phi_out, int64_t P, float cfl,
-                                                              float dt) {
-    const RowSlot s = row_slot(P);
-    const float4 sg = s.valid ? __ldg(reinterpret_cast<const float4*>(s0) + s.q4) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const Rows w = load_rows(phi_in, faces, s);
-    if (!s.valid) return;
-    reinterpret_cast<float4*>(phi_out)[s.q4] = reinit_row(w, sg, cfl, dt);
 }
 
 // One float4 row per thread, grid-stride over the active packages.
@@ -142,10 +120,6 @@ unsigned pkg_blocks(int64_t P) {
     return (unsigned)((n + SW_PKGS - 1) / SW_PKGS);
 }
 
-unsigned row_blocks(int64_t P) {
-    int64_t n = P - 2;
-    return (unsigned)((n + ROW_PKGS - 1) / ROW_PKGS);
-}
 
 unsigned flat_blocks(int64_t n) {
     int64_t b = (n + SW_THREADS - 1) / SW_THREADS;
@@ -200,23 +174,6 @@ cudaError_t launch_laplacian(const GridF& G, const int32_t* faces, const float* 
                              cudaStream_t s) {
     if (P <= 2) return cudaSuccess;
     k_laplacian<<<row_blocks(P), ROW_THREADS, 0, s>>>(faces, phi, lap, P, (float)(1.0 / (G.h_d * G.h_d)));
-    note_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_reinit_s0(const GridF& G, const float* phi, float* s0, int64_t P, cudaStream_t s) {
-    if (P <= 2) return cudaSuccess;
-    int64_t n = (P - 2) * PKG3;
-    k_reinit_s0<<<flat_blocks(n), SW_THREADS, 0, s>>>(phi, s0, n, (float)(G.h_d * G.h_d));
-    note_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_reinit_step(const GridF& G, const int32_t* faces, const float* s0, const float* phi_in,
-                               float* phi_out, float dt, int64_t P, cudaStream_t s) {
-    if (P <= 2) return cudaSuccess;
-    // dt sqrt(G) = (dt / h) sqrt(h^2 G) and dt / h is the CFL number
-    k_reinit_step<<<row_blocks(P), ROW_THREADS, 0, s>>>(faces, s0, phi_in, phi_out, P, (float)(dt / G.h_d), dt);
     note_launch();
     return cudaGetLastError();
 }
