@@ -68,23 +68,22 @@ __device__ __forceinline__ ff ff_mul_f(ff x, float b) {
 
 __device__ __forceinline__ ff ff_sqr(ff x) { return ff_mul(x, x); }
 
-__device__ __forceinline__ ff ff_div(ff x, ff y) {
-    float q1 = __fdiv_rn(x.hi, y.hi);
-    ff r = ff_sub(x, ff_mul_f(y, q1));
-    float q2 = __fdiv_rn(r.hi, y.hi);
-    r = ff_sub(r, ff_mul_f(y, q2));
-    float q3 = __fdiv_rn(r.hi, y.hi);
-    ff q = fast_two_sum(q1, q2);
-    return ff_add(q, ff_make(q3));
-}
-
-// sqrt(x) for x >= 0: s = sqrtf(hi), then s + (x - s^2) / (2 s).
+// sqrt(x) for x >= 0, after Karp and Markstein ("High-precision division
+// and square root", 1997): a reciprocal square root r of hi refined by one
+// Newton step, a float root s = hi r corrected once, then
+// sqrt(x) = s + (x - s^2) r / 2 with x - s^2 formed exactly (two_prod and
+// Sterbenz); relative error about 2^-46.
 __device__ __forceinline__ ff ff_sqrt(ff x) {
     if (!(x.hi > 0.0f)) return ff{0.0f, 0.0f};
-    float s = __fsqrt_rn(x.hi);
-    ff r = ff_sub(x, two_prod(s, s));
-    float c = __fdiv_rn(r.hi, __fmul_rn(2.0f, s));
-    return fast_two_sum(s, c);
+    if (x.hi < 0x1p-100f) return ff{__fsqrt_rn(x.hi), 0.0f};  // far below any grid length; keeps rsqrtf normal
+    float r = rsqrtf(x.hi);
+    r = __fmul_rn(r, __fmaf_rn(__fmul_rn(-0.5f, x.hi), __fmul_rn(r, r), 1.5f));
+    const float hr = __fmul_rn(0.5f, r);
+    float s = __fmul_rn(x.hi, r);
+    s = __fmaf_rn(__fmaf_rn(-s, s, x.hi), hr, s);
+    const ff p = two_prod(s, s);
+    const float d = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p.hi), p.lo), x.lo);
+    return fast_two_sum(s, __fmul_rn(d, hr));
 }
 
 __device__ __forceinline__ bool ff_lt(ff a, ff b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
@@ -191,8 +190,9 @@ __device__ inline ff ff_triangle_sdf(ff px, ff py, const ShapeFF& s) {
     return inside ? ff_neg(dd) : dd;
 }
 
-// Exact signed distance (negative inside) of each primitive, in float-float.
-__device__ inline ff ff_sdf(const ShapeFF& s, const ff x[3]) {
+// Exact signed distance (negative inside) of primitive K, in float-float.
+template <int K>
+__device__ inline ff ff_sdf_k(const ShapeFF& s, const ff x[3]) {
     ff q[3];
     if (s.plain) {
         q[0] = x[0], q[1] = x[1], q[2] = x[2];
@@ -200,7 +200,7 @@ __device__ inline ff ff_sdf(const ShapeFF& s, const ff x[3]) {
         ff_to_local(s, x, q);
     }
     const ff zero{0.0f, 0.0f};
-    switch (s.kind) {
+    switch (K) {
     case SHAPE_SPHERE:
         return ff_sub(ff_sqrt(ff_add(ff_add(ff_sqr(q[0]), ff_sqr(q[1])), ff_sqr(q[2]))), s.p[0]);
     case SHAPE_PLANE:
@@ -251,7 +251,8 @@ __device__ __forceinline__ float f_seg_dist2(float px, float py, float ax, float
     return dx * dx + dy * dy;
 }
 
-__device__ inline float f_sdf(const ShapeFF& s, const float x[3]) {
+template <int K>
+__device__ inline float f_sdf_k(const ShapeFF& s, const float x[3]) {
     float q[3];
     if (s.plain) {
         q[0] = x[0], q[1] = x[1], q[2] = x[2];
@@ -261,7 +262,7 @@ __device__ inline float f_sdf(const ShapeFF& s, const float x[3]) {
         for (int i = 0; i < 3; ++i) q[i] = s.rf[i] * d0 + s.rf[3 + i] * d1 + s.rf[6 + i] * d2;
     }
     const float* p = s.pf;
-    switch (s.kind) {
+    switch (K) {
     case SHAPE_SPHERE:
         return sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) - p[0];
     case SHAPE_PLANE:

@@ -12,10 +12,28 @@ namespace {
 
 constexpr int TAG_THREADS = 256;
 
+// Launch the instantiation of a shape-templated kernel for kind `kind` (the
+// statement `launch` names it with template argument K).
+#define SG_SHAPE_DISPATCH(kind, launch)                         \
+    do {                                                        \
+        switch (kind) {                                         \
+        case SHAPE_SPHERE: { constexpr int K = SHAPE_SPHERE; launch; } break;           \
+        case SHAPE_PLANE: { constexpr int K = SHAPE_PLANE; launch; } break;             \
+        case SHAPE_TORUS: { constexpr int K = SHAPE_TORUS; launch; } break;             \
+        case SHAPE_PRISM: { constexpr int K = SHAPE_PRISM; launch; } break;             \
+        case SHAPE_ROUNDED_BOX: { constexpr int K = SHAPE_ROUNDED_BOX; launch; } break; \
+        default: { constexpr int K = SHAPE_SHELL; launch; } break;                      \
+        }                                                       \
+    } while (0)
+
+// Cell (I, J, K) of linear index c = I + nx (J + ny K).  Grids hold fewer
+// than 2^31 cells, so two 32-bit divisions suffice.
 __device__ __forceinline__ void cell_coords(int64_t c, const int* dims, int64_t& I, int64_t& J, int64_t& K) {
-    I = c % dims[0];
-    J = (c / dims[0]) % dims[1];
-    K = c / ((int64_t)dims[0] * dims[1]);
+    const uint32_t u = (uint32_t)c, nx = (uint32_t)dims[0], ny = (uint32_t)dims[1];
+    const uint32_t q = u / nx, k = q / ny;
+    I = u - q * nx;
+    J = q - k * ny;
+    K = k;
 }
 
 // Step 1: core cells, |d(centre)| < T; far cells keep the sign of d.  The
@@ -23,31 +41,33 @@ __device__ __forceinline__ void cell_coords(int64_t c, const int* dims, int64_t&
 // from both T and 0 in magnitude, the float decision stands (the float error
 // of these formulas is below 1e-6 (1 + |x|), the margin is 1.5e-4 (1 + |x|)),
 // otherwise it is decided on the float-float distance.
+template <int K>
 __device__ __forceinline__ uint8_t classify_cell(const GridFF& G, const ShapeFF& S, const int64_t (&I)[3]) {
     const float Tf = G.T.hi;
     float xf[3];
     float xmax = 0.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        xf[a] = G.lo[a].hi + G.h.hi * (float)(4 * I[a] + 2);
+        xf[a] = G.lo[a].hi + G.h.hi * (float)(4 * (int)I[a] + 2);
         xmax = fmaxf(xmax, fabsf(xf[a]));
     }
-    const float df = f_sdf(S, xf);
+    const float df = f_sdf_k<K>(S, xf);
     const float margin = 1.5e-4f * (1.0f + xmax);
     if (fabsf(fabsf(df) - Tf) > margin && fabsf(df) > margin) return fabsf(df) < Tf ? 2 : (df < 0.0f ? 0 : 1);
     ff x[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) x[a] = ff_add(G.lo[a], ff_mul_f(G.h, (float)(4 * I[a] + 2)));
-    const ff d = ff_sdf(S, x);
+    for (int a = 0; a < 3; ++a) x[a] = ff_add(G.lo[a], ff_mul_f(G.h, (float)(4 * (int)I[a] + 2)));
+    const ff d = ff_sdf_k<K>(S, x);
     return ff_lt(ff_abs(d), G.T) ? 2 : (ff_neg_p(d) ? 0 : 1);
 }
 
+template <int K>
 __global__ void __launch_bounds__(TAG_THREADS) k_tag_flags(GridFF G, ShapeFF S, uint8_t* __restrict__ cell_type,
                                                             uint32_t* __restrict__ active, int64_t nc) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         int64_t I[3];
         cell_coords(c, G.dims, I[0], I[1], I[2]);
-        const uint8_t t = classify_cell(G, S, I);
+        const uint8_t t = classify_cell<K>(G, S, I);
         cell_type[c] = t;
         active[c] = t == 2;
     }
@@ -59,6 +79,7 @@ __global__ void __launch_bounds__(TAG_THREADS) k_tag_flags(GridFF G, ShapeFF S, 
 // its coarse cell is far inside or is an inner cell whose level set (data
 // point 0) is negative.  A fine cell inside a coarse cell that is not core
 // lies at least 1.13 fine cells from the surface, so it cannot be core.
+template <int K>
 __global__ void __launch_bounds__(TAG_THREADS) k_tag_flags_from(GridFF G, ShapeFF S, const int32_t* __restrict__ c_cell_pkg,
                                                                  const uint8_t* __restrict__ c_pkg_type,
                                                                  const float* __restrict__ c_phi, int cnx, int cny,
@@ -72,7 +93,7 @@ __global__ void __launch_bounds__(TAG_THREADS) k_tag_flags_from(GridFF G, ShapeF
         const int64_t pc = __ldg(c_cell_pkg + (I[0] >> 1) + cnx * ((I[1] >> 1) + (int64_t)cny * (I[2] >> 1)));
         uint8_t t;
         if (pc >= 2 && __ldg(c_pkg_type + pc) == 2) {
-            t = classify_cell(G, S, I);
+            t = classify_cell<K>(G, S, I);
             ++ev;
         } else {
             t = (pc < 2 ? pc == 0 : __ldg(c_phi + pc * PKG3) < 0.0f) ? 0 : 1;
@@ -94,12 +115,13 @@ __global__ void __launch_bounds__(TAG_THREADS) k_tag_inner(GridFF G, uint8_t* ce
         int64_t I, J, K;
         cell_coords(c, G.dims, I, J, K);
         bool found = false;
+        // indices stay in 32 bits: the grid has fewer than 2^31 cells
         for (int dk = -1; dk <= 1; ++dk)
             for (int dj = -1; dj <= 1; ++dj)
                 for (int di = -1; di <= 1; ++di) {
-                    int64_t a = I + di, b = J + dj, e = K + dk;
+                    const int a = (int)I + di, b = (int)J + dj, e = (int)K + dk;
                     if (a < 0 || b < 0 || e < 0 || a >= nx || b >= ny || e >= nz) continue;
-                    found |= cell_type[a + nx * (b + (int64_t)ny * e)] == 2;
+                    found |= cell_type[a + nx * (b + ny * e)] == 2;
                 }
         if (found) {
             cell_type[c] = 3;  // other threads only test for == 2, unaffected
@@ -147,9 +169,9 @@ __global__ void __launch_bounds__(TAG_THREADS) k_fill_nbr(GridFF G, const int32_
         }
         int64_t I, J, K;
         cell_coords(pkg_cell[p], G.dims, I, J, K);
-        int64_t a = I + (n % 3) - 1, b = J + (n / 3) % 3 - 1, c = K + n / 9 - 1;
-        bool in = a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz;
-        nbr[e] = in ? cell_pkg[a + nx * (b + (int64_t)ny * c)] : 1;
+        const int a = (int)I + (n % 3) - 1, b = (int)J + (n / 3) % 3 - 1, c = (int)K + n / 9 - 1;
+        const bool in = a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz;
+        nbr[e] = in ? cell_pkg[a + nx * (b + ny * c)] : 1;
     }
 }
 
@@ -214,7 +236,8 @@ __global__ void __launch_bounds__(TAG_THREADS) k_check_tables(GridFF G, const in
 }
 
 // Step 4: phi at cell-centred data points, float-float, rounded once.
-__global__ void __launch_bounds__(TAG_THREADS) k_init_sdf(GridFF G, ShapeFF S, const int32_t* __restrict__ pkg_cell,
+template <int K>
+__global__ void __launch_bounds__(TAG_THREADS, K == SHAPE_PRISM ? 4 : 8) k_init_sdf(GridFF G, ShapeFF S, const int32_t* __restrict__ pkg_cell,
                                                            float* __restrict__ phi, int64_t P) {
     const int64_t total = (P - 2) * PKG3;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -223,11 +246,11 @@ __global__ void __launch_bounds__(TAG_THREADS) k_init_sdf(GridFF G, ShapeFF S, c
         int d = (int)(e & (PKG3 - 1));
         int64_t I[3];
         cell_coords(pkg_cell[p], G.dims, I[0], I[1], I[2]);
-        int l[3] = {d & 3, (d >> 2) & 3, d >> 4};
+        const int l[3] = {d & 3, (d >> 2) & 3, d >> 4};
         ff x[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) x[a] = ff_add(G.lo[a], ff_mul_f(G.h, (float)(4 * I[a] + l[a]) + 0.5f));
-        phi[p * PKG3 + d] = ff_to_float(ff_sdf(S, x));
+        for (int a = 0; a < 3; ++a) x[a] = ff_add(G.lo[a], ff_mul_f(G.h, (float)(4 * (int)I[a] + l[a]) + 0.5f));
+        phi[p * PKG3 + d] = ff_to_float(ff_sdf_k<K>(S, x));
     }
 }
 
@@ -242,7 +265,7 @@ unsigned grid_for(int64_t n, int threads) {
 
 cudaError_t launch_tag_flags(const GridFF& G, const ShapeFF& S, uint8_t* cell_type, uint32_t* active, int64_t nc,
                              cudaStream_t s) {
-    k_tag_flags<<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, cell_type, active, nc);
+    SG_SHAPE_DISPATCH(S.kind, (k_tag_flags<K><<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, cell_type, active, nc)));
     note_launch();
     return cudaGetLastError();
 }
@@ -250,8 +273,8 @@ cudaError_t launch_tag_flags(const GridFF& G, const ShapeFF& S, uint8_t* cell_ty
 cudaError_t launch_tag_flags_from(const GridFF& G, const ShapeFF& S, const int32_t* c_cell_pkg,
                                   const uint8_t* c_pkg_type, const float* c_phi, int cnx, int cny, uint8_t* cell_type,
                                   uint32_t* active, int64_t nc, unsigned long long* evaluated, cudaStream_t s) {
-    k_tag_flags_from<<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, c_cell_pkg, c_pkg_type, c_phi, cnx, cny,
-                                                                       cell_type, active, nc, evaluated);
+    SG_SHAPE_DISPATCH(S.kind, (k_tag_flags_from<K><<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(
+                                  G, S, c_cell_pkg, c_pkg_type, c_phi, cnx, cny, cell_type, active, nc, evaluated)));
     note_launch();
     return cudaGetLastError();
 }
@@ -342,7 +365,8 @@ cudaError_t launch_init_sdf(const GridFF& G, const ShapeFF& S, const int32_t* pk
     cudaError_t e = launch_set_far(phi, -F, F, s);
     if (e != cudaSuccess) return e;
     if (P > 2) {
-        k_init_sdf<<<grid_for((P - 2) * PKG3, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, pkg_cell, phi, P);
+        SG_SHAPE_DISPATCH(S.kind, (k_init_sdf<K><<<grid_for((P - 2) * PKG3, TAG_THREADS), TAG_THREADS, 0, s>>>(
+                                      G, S, pkg_cell, phi, P)));
         note_launch();
     }
     return cudaGetLastError();
