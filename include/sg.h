@@ -260,7 +260,7 @@ SG_API sg_status sg_kernel_integrals(sg_grid *g, int32_t mode, const void *mlp);
  * With SG_PROBE_MORTON the particles are walked in Morton order (stable
  * sort by the bit interleave of k_a = clamp(i0_a + 1, 0, 4 dims_a + 1), x in
  * the lowest bit) and results are written back in input order; an input
- * whose sampled adjacent pairs (every 16th) are already in that order is
+ * whose sampled adjacent pairs (one in 128) are already in that order is
  * walked as it is.  The walk only affects speed: the results are the same
  * for any order.
  * Errors: SG_ERR_INVALID (n < 0, null positions), SG_ERR_CAPACITY

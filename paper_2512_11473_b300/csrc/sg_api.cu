@@ -129,6 +129,8 @@ ShapeFF shape_ff(const sg_shape* s) {
         S.seg[3 * k + 2] = split(l2 > 0.0 ? 1.0 / l2 : 0.0);
     }
     S.orient = (t[2] - t[0]) * (t[5] - t[1]) - (t[3] - t[1]) * (t[4] - t[0]) > 0.0 ? 1 : -1;
+    S.zc = split(0.5 * (t[6] + t[7]));
+    S.hz = split(0.5 * (t[7] - t[6]));
     return S;
 }
 
@@ -539,8 +541,9 @@ sg_status sg_probe(sg_grid* g, int64_t n, const float* x, const float* y, const 
         size_t ob = ((size_t)n * 4 + 255) & ~(size_t)255;
         if (!ensure(g, g->scratch, sb + ob)) return fail(g, SG_ERR_OOM, "sg_probe: out of memory");
         int32_t* ord = (int32_t*)((char*)g->scratch.p + sb);
-        // results do not depend on the walk: a sampled check decides whether the input is walked as it is
-        SG_CUDA(g, morton_sort(G, n, x, y, z, nullptr, ord, g->scratch.p, g->stream, false, &unsorted, 16),
+        // results do not depend on the walk: a sampled check (one pair in 128, so that it reads about one
+        // 32-byte sector of the positions in 16) decides whether the input is walked as it is
+        SG_CUDA(g, morton_sort(G, n, x, y, z, nullptr, ord, g->scratch.p, g->stream, false, &unsorted, 128),
                 "probe sort");
         order = ord;
     }

@@ -115,6 +115,7 @@ struct ShapeFF {
     // 1 / |e|^2 (seg[3k .. 3k+2]), and the sign of the triangle's orientation
     ff seg[9];
     int orient;
+    ff zc, hz;  // prism: centre and half height of the z extent
 };
 
 // local coordinates q = R^T (x - centre)
@@ -136,7 +137,15 @@ __device__ __forceinline__ ff ff_edge_dist2(ff px, ff py, ff ax, ff ay, ff ex, f
     return ff_add(ff_sqr(dx), ff_sqr(dy));
 }
 
-__device__ __forceinline__ float f_seg_dist2(float px, float py, float ax, float ay, float bx, float by);
+__device__ __forceinline__ float f_edge_dist2(float px, float py, float ax, float ay, float ex, float ey, float inv_len2);
+
+// upper estimate of sqrt(x) for x >= 0 (hardware approximation, relative
+// error below 2^-22, inflated by 2^-20)
+__device__ __forceinline__ float f_sqrt_up(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r * 1.000001f;
+}
 
 // Signed distance to a triangle (negative inside) in float-float.  A float
 // pass first bounds each edge's squared distance (error below
@@ -151,13 +160,13 @@ __device__ inline ff ff_triangle_sdf(ff px, ff py, const ShapeFF& s) {
     const float fx = px.hi, fy = py.hi;
     const float scale = 1.0f + fabsf(fx) + fabsf(fy), delta = 1e-6f * scale;
     float d[3], hi[3];
-    d[0] = f_seg_dist2(fx, fy, tf[0], tf[1], tf[2], tf[3]);
-    d[1] = f_seg_dist2(fx, fy, tf[2], tf[3], tf[4], tf[5]);
-    d[2] = f_seg_dist2(fx, fy, tf[4], tf[5], tf[0], tf[1]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        d[k] = f_edge_dist2(fx, fy, tf[2 * k], tf[2 * k + 1], s.seg[3 * k].hi, s.seg[3 * k + 1].hi, s.seg[3 * k + 2].hi);
     float tol[3], up = INFINITY;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        tol[k] = 2.0f * sqrtf(d[k]) * delta + delta * delta + 2.4e-7f * d[k];
+        tol[k] = 2.0f * f_sqrt_up(d[k]) * delta + delta * delta + 2.4e-7f * d[k];
         hi[k] = d[k] + tol[k];
         up = fminf(up, hi[k]);
     }
@@ -215,13 +224,12 @@ __device__ inline ff ff_sdf_k(const ShapeFF& s, const ff x[3]) {
         return ff_sub(ff_sqrt(ff_add(ff_sqr(a), ff_sqr(q[2]))), s.p[1]);
     }
     case SHAPE_PRISM: {
-        ff w0 = ff_triangle_sdf(q[0], q[1], s);
-        ff zc = ff_mul_f(ff_add(s.p[6], s.p[7]), 0.5f);
-        ff hz = ff_mul_f(ff_sub(s.p[7], s.p[6]), 0.5f);
-        ff w1 = ff_sub(ff_abs(ff_sub(q[2], zc)), hz);
-        ff in = ff_min(ff_max(w0, w1), zero);
-        ff a = ff_max(w0, zero), b = ff_max(w1, zero);
-        return ff_add(in, ff_sqrt(ff_add(ff_sqr(a), ff_sqr(b))));
+        const ff w0 = ff_triangle_sdf(q[0], q[1], s);
+        const ff w1 = ff_sub(ff_abs(ff_sub(q[2], s.zc)), s.hz);
+        // max(w0, w1) where at most one is positive, else the distance to
+        // the rim sqrt(w0^2 + w1^2)
+        if (!(ff_gt(w0, zero) && ff_gt(w1, zero))) return ff_max(w0, w1);
+        return ff_sqrt(ff_add(ff_sqr(w0), ff_sqr(w1)));
     }
     case SHAPE_ROUNDED_BOX: {
         ff r = s.p[3];
@@ -244,9 +252,11 @@ __device__ inline ff ff_sdf_k(const ShapeFF& s, const ff x[3]) {
 // predicate: decisions far from the thresholds are taken here, the rest in
 // float-float.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float f_seg_dist2(float px, float py, float ax, float ay, float bx, float by) {
-    const float ex = bx - ax, ey = by - ay, wx = px - ax, wy = py - ay;
-    const float t = fminf(fmaxf((wx * ex + wy * ey) / (ex * ex + ey * ey), 0.0f), 1.0f);
+// squared distance from p to the edge from a along e, with 1 / |e|^2 given
+// (an error in the clamped parameter t changes the distance to second order)
+__device__ __forceinline__ float f_edge_dist2(float px, float py, float ax, float ay, float ex, float ey, float inv_len2) {
+    const float wx = px - ax, wy = py - ay;
+    const float t = fminf(fmaxf((wx * ex + wy * ey) * inv_len2, 0.0f), 1.0f);
     const float dx = wx - t * ex, dy = wy - t * ey;
     return dx * dx + dy * dy;
 }
@@ -274,9 +284,11 @@ __device__ inline float f_sdf_k(const ShapeFF& s, const float x[3]) {
         return sqrtf(a * a + q[2] * q[2]) - p[1];
     }
     case SHAPE_PRISM: {
-        float d2 = f_seg_dist2(q[0], q[1], p[0], p[1], p[2], p[3]);
-        d2 = fminf(d2, f_seg_dist2(q[0], q[1], p[2], p[3], p[4], p[5]));
-        d2 = fminf(d2, f_seg_dist2(q[0], q[1], p[4], p[5], p[0], p[1]));
+        float d2 = INFINITY;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            d2 = fminf(d2, f_edge_dist2(q[0], q[1], p[2 * k], p[2 * k + 1], s.seg[3 * k].hi, s.seg[3 * k + 1].hi,
+                                        s.seg[3 * k + 2].hi));
         const float orient = (p[2] - p[0]) * (p[5] - p[1]) - (p[3] - p[1]) * (p[4] - p[0]);
         const float c0 = (p[2] - p[0]) * (q[1] - p[1]) - (p[3] - p[1]) * (q[0] - p[0]);
         const float c1 = (p[4] - p[2]) * (q[1] - p[3]) - (p[5] - p[3]) * (q[0] - p[2]);

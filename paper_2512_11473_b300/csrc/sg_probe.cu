@@ -110,16 +110,19 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const KeyT* __restrict__
                                                         uint32_t* __restrict__ hist, int64_t nb, const int* run) {
     if (*run == 0) return;  // keys already in order
     __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int64_t tile = blockIdx.x; tile < nb; tile += gridDim.x) {
+        h[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t base = tile * RS_TILE;
 #pragma unroll 4
-    for (int r = 0; r < RS_ITEMS; ++r) {
-        int64_t i = base + r * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+        for (int r = 0; r < RS_ITEMS; ++r) {
+            int64_t i = base + r * RS_THREADS + threadIdx.x;
+            if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        hist[(int64_t)threadIdx.x * nb + tile] = h[threadIdx.x];
+        __syncthreads();
     }
-    __syncthreads();
-    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
 // Stable scatter of one 8-bit digit.  Warp w ranks its own contiguous 512
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const KeyT* __restrict__
 // keys are staged in shared memory in digit order and written out so that
 // each digit's run is one contiguous global range.
 template <typename KeyT>
-__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin,
+__global__ void __launch_bounds__(RS_THREADS, 2) k_rs_scatter(const KeyT* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            KeyT* __restrict__ kout, uint32_t* __restrict__ vout,
                                                            int64_t n, int shift, const uint32_t* __restrict__ offs,
                                                            int64_t nb, const int* run) {
@@ -142,74 +145,79 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const KeyT* __restric
     __shared__ uint32_t s_wsum[RS_WARPS];
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
-    const int tile_n = (int)min((int64_t)RS_TILE, n - tile0);
-    const int wbase = warp * (RS_TILE / RS_WARPS);
+    // blocks loop over the tiles (a bounded grid, so that a launch whose
+    // run flag is clear ends at once)
+    for (int64_t tile = blockIdx.x; tile < nb; tile += gridDim.x) {
+        const int64_t tile0 = tile * RS_TILE;
+        const int tile_n = (int)min((int64_t)RS_TILE, n - tile0);
+        const int wbase = warp * (RS_TILE / RS_WARPS);
 
 #pragma unroll
-    for (int w = 0; w < RS_WARPS; ++w) s_cnt[w][t] = 0;
-    KeyT key[RS_ITEMS];
-    uint32_t val[RS_ITEMS], rank[RS_ITEMS];
+        for (int w = 0; w < RS_WARPS; ++w) s_cnt[w][t] = 0;
+        KeyT key[RS_ITEMS];
+        uint32_t val[RS_ITEMS], rank[RS_ITEMS];
 #pragma unroll
-    for (int r = 0; r < RS_ITEMS; ++r) {
-        const int i = wbase + 32 * r + lane;
-        key[r] = i < tile_n ? kin[tile0 + i] : (KeyT)0;
-        val[r] = i < tile_n ? vin[tile0 + i] : 0u;
-    }
-    __syncthreads();
-    const uint32_t lt = (1u << lane) - 1u;
-#pragma unroll
-    for (int r = 0; r < RS_ITEMS; ++r) {
-        const bool valid = wbase + 32 * r + lane < tile_n;
-        const uint32_t dg = valid ? ((uint32_t)(key[r] >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-        const uint32_t below = __popc(peers & lt);
-        const uint32_t before = valid ? s_cnt[warp][dg] : 0u;
-        __syncwarp();
-        if (valid && below == 0) s_cnt[warp][dg] = before + __popc(peers);
-        __syncwarp();
-        rank[r] = before + below;
-    }
-    __syncthreads();
-    {  // per digit t: exclusive prefix over warps, then over digits
-        uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < RS_WARPS; ++w) {
-            const uint32_t c = s_cnt[w][t];
-            s_cnt[w][t] = run;
-            run += c;
+        for (int r = 0; r < RS_ITEMS; ++r) {
+            const int i = wbase + 32 * r + lane;
+            key[r] = i < tile_n ? kin[tile0 + i] : (KeyT)0;
+            val[r] = i < tile_n ? vin[tile0 + i] : 0u;
         }
-        uint32_t incl = run;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
-        }
-        if (lane == 31) s_wsum[warp] = incl;
         __syncthreads();
-        uint32_t wpre = 0;
+        const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-        for (int w = 0; w < RS_WARPS; ++w) wpre += w < warp ? s_wsum[w] : 0u;
-        const uint32_t start = wpre + incl - run;
-        s_start[t] = start;
-        s_goff[t] = offs[(int64_t)t * nb + blockIdx.x] - start;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < RS_ITEMS; ++r) {
-        if (wbase + 32 * r + lane < tile_n) {
-            const uint32_t dg = (uint32_t)(key[r] >> shift) & 255u;
-            const uint32_t pos = s_start[dg] + s_cnt[warp][dg] + rank[r];
-            s_k[pos] = key[r];
-            s_v[pos] = val[r];
+        for (int r = 0; r < RS_ITEMS; ++r) {
+            const bool valid = wbase + 32 * r + lane < tile_n;
+            const uint32_t dg = valid ? ((uint32_t)(key[r] >> shift) & 255u) : 256u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+            const uint32_t below = __popc(peers & lt);
+            const uint32_t before = valid ? s_cnt[warp][dg] : 0u;
+            __syncwarp();
+            if (valid && below == 0) s_cnt[warp][dg] = before + __popc(peers);
+            __syncwarp();
+            rank[r] = before + below;
         }
-    }
-    __syncthreads();
-    for (int j = t; j < tile_n; j += RS_THREADS) {
-        const KeyT k = s_k[j];
-        const uint32_t g = s_goff[(uint32_t)(k >> shift) & 255u] + (uint32_t)j;
-        kout[g] = k;
-        vout[g] = s_v[j];
+        __syncthreads();
+        {  // per digit t: exclusive prefix over warps, then over digits
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < RS_WARPS; ++w) {
+                const uint32_t c = s_cnt[w][t];
+                s_cnt[w][t] = run;
+                run += c;
+            }
+            uint32_t incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            if (lane == 31) s_wsum[warp] = incl;
+            __syncthreads();
+            uint32_t wpre = 0;
+#pragma unroll
+            for (int w = 0; w < RS_WARPS; ++w) wpre += w < warp ? s_wsum[w] : 0u;
+            const uint32_t start = wpre + incl - run;
+            s_start[t] = start;
+            s_goff[t] = offs[(int64_t)t * nb + tile] - start;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < RS_ITEMS; ++r) {
+            if (wbase + 32 * r + lane < tile_n) {
+                const uint32_t dg = (uint32_t)(key[r] >> shift) & 255u;
+                const uint32_t pos = s_start[dg] + s_cnt[warp][dg] + rank[r];
+                s_k[pos] = key[r];
+                s_v[pos] = val[r];
+            }
+        }
+        __syncthreads();
+        for (int j = t; j < tile_n; j += RS_THREADS) {
+            const KeyT k = s_k[j];
+            const uint32_t g = s_goff[(uint32_t)(k >> shift) & 255u] + (uint32_t)j;
+            kout[g] = k;
+            vout[g] = s_v[j];
+        }
+        __syncthreads();
     }
 }
 
@@ -283,7 +291,9 @@ cudaError_t sort_impl(const GridF& G, int64_t n, int key_bits, const float* x, c
             G, n, x, y, z, check_stride, unsorted);
     else
         k_morton_check<<<blocks_for(n, RS_THREADS), RS_THREADS, 0, s>>>(G, n, x, y, z, unsorted);
-    k_morton_keys<KeyT><<<blocks_for(n, RS_THREADS), RS_THREADS, 0, s>>>(G, n, x, y, z, k0, v0, keys_out, unsorted);
+    // grid-stride kernels that may find nothing to do: a bounded grid ends at once
+    const unsigned small_grid = blocks_for(n, RS_THREADS) < 148 * 8 ? blocks_for(n, RS_THREADS) : 148 * 8;
+    k_morton_keys<KeyT><<<small_grid, RS_THREADS, 0, s>>>(G, n, x, y, z, k0, v0, keys_out, unsorted);
     note_launch(2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int passes = (key_bits + 7) / 8;
@@ -296,13 +306,15 @@ cudaError_t sort_impl(const GridF& G, int64_t n, int key_bits, const float* x, c
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         uint32_t* vout = (p == passes - 1) ? (uint32_t*)order_out : V[1 - cur];
-        k_rs_hist<KeyT><<<(unsigned)nb, RS_THREADS, 0, s>>>(K[cur], n, shift, hist, nb, unsorted);
+        k_rs_hist<KeyT><<<(unsigned)(nb < 148 * 8 ? nb : 148 * 8), RS_THREADS, 0, s>>>(K[cur], n, shift, hist, nb,
+                                                                                          unsorted);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = exclusive_scan_u32(hist, hist, 256 * nb, nullptr, scan_scratch, s, unsorted)) != cudaSuccess)
             return e;
-        k_rs_scatter<KeyT><<<(unsigned)nb, RS_THREADS, smem, s>>>(K[cur], V[cur], K[1 - cur], vout, n, shift, hist,
-                                                                  nb, unsorted);
+        // two blocks of the scatter fit on an SM (128 registers, 42-74 KB of shared memory)
+        k_rs_scatter<KeyT><<<(unsigned)(nb < 148 * 2 ? nb : 148 * 2), RS_THREADS, smem, s>>>(
+            K[cur], V[cur], K[1 - cur], vout, n, shift, hist, nb, unsorted);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         cur = 1 - cur;
@@ -311,7 +323,7 @@ cudaError_t sort_impl(const GridF& G, int64_t n, int key_bits, const float* x, c
         if ((e = cudaMemcpyAsync(order_out, V[0], n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
             return e;
     } else if (identity_out) {
-        k_identity_if_sorted<<<blocks_for(n, RS_THREADS), RS_THREADS, 0, s>>>(unsorted, order_out, n);
+        k_identity_if_sorted<<<small_grid, RS_THREADS, 0, s>>>(unsorted, order_out, n);
         note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

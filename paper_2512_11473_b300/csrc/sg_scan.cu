@@ -11,6 +11,7 @@ constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 constexpr int SPINE_THREADS = 1024;
+constexpr int64_t SCAN_GRID = 148 * 8;  // 8 blocks of 256 on each of the 148 SMs
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
     const int lane = threadIdx.x & 31;
@@ -44,22 +45,27 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
     return r;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n,
+// Tile sums; blocks loop over the tiles (a grid of at most SCAN_GRID blocks,
+// so that a launch whose `go` flag is clear ends at once).
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n, int64_t nb,
                                                                uint32_t* __restrict__ partial, const int* go) {
     if (go && *go == 0) return;
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
-    uint32_t s = 0;
-#pragma unroll
-    for (int r = 0; r < SCAN_ITEMS; ++r)
-        if (base + r < n) s += in[base + r];
     __shared__ uint32_t red[SCAN_THREADS / 32];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        uint32_t v = threadIdx.x < SCAN_THREADS / 32 ? red[threadIdx.x] : 0u;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (threadIdx.x == 0) partial[blockIdx.x] = v;
+    for (int64_t tile = blockIdx.x; tile < nb; tile += gridDim.x) {
+        const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+        uint32_t s = 0;
+#pragma unroll
+        for (int r = 0; r < SCAN_ITEMS; ++r)
+            if (base + r < n) s += in[base + r];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            uint32_t v = threadIdx.x < SCAN_THREADS / 32 ? red[threadIdx.x] : 0u;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (threadIdx.x == 0) partial[tile] = v;
+        }
+        __syncthreads();
     }
 }
 
@@ -83,23 +89,25 @@ __global__ void __launch_bounds__(SPINE_THREADS) k_scan_spine(uint32_t* __restri
     if (threadIdx.x == 0 && total) *total = carry_s;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* in, uint32_t* out, int64_t n,
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* in, uint32_t* out, int64_t n, int64_t nb,
                                                              const uint32_t* __restrict__ partial, const int* go) {
     if (go && *go == 0) return;
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
-    uint32_t v[SCAN_ITEMS];
-    uint32_t s = 0;
+    for (int64_t tile = blockIdx.x; tile < nb; tile += gridDim.x) {
+        const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+        uint32_t v[SCAN_ITEMS];
+        uint32_t s = 0;
 #pragma unroll
-    for (int r = 0; r < SCAN_ITEMS; ++r) {
-        v[r] = base + r < n ? in[base + r] : 0u;
-        s += v[r];
-    }
-    uint32_t tot;
-    uint32_t run = block_excl_scan<SCAN_THREADS>(s, &tot) + partial[blockIdx.x];
+        for (int r = 0; r < SCAN_ITEMS; ++r) {
+            v[r] = base + r < n ? in[base + r] : 0u;
+            s += v[r];
+        }
+        uint32_t tot;
+        uint32_t run = block_excl_scan<SCAN_THREADS>(s, &tot) + partial[tile];
 #pragma unroll
-    for (int r = 0; r < SCAN_ITEMS; ++r) {
-        if (base + r < n) out[base + r] = run;
-        run += v[r];
+        for (int r = 0; r < SCAN_ITEMS; ++r) {
+            if (base + r < n) out[base + r] = run;
+            run += v[r];
+        }
     }
 }
 
@@ -118,11 +126,12 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uin
     }
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     uint32_t* partial = (uint32_t*)scratch;
-    k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, partial, go);
+    const unsigned grid = (unsigned)(nb < SCAN_GRID ? nb : SCAN_GRID);
+    k_scan_reduce<<<grid, SCAN_THREADS, 0, s>>>(in, n, nb, partial, go);
     note_launch();
     k_scan_spine<<<1, SPINE_THREADS, 0, s>>>(partial, nb, total, go);
     note_launch();
-    k_scan_down<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, partial, go);
+    k_scan_down<<<grid, SCAN_THREADS, 0, s>>>(in, out, n, nb, partial, go);
     note_launch();
     return cudaGetLastError();
 }
