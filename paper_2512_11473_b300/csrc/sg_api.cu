@@ -239,23 +239,31 @@ const char* sg_last_error(const sg_grid* g) { return g ? g->last_error.c_str() :
 
 }  // extern "C"
 
+// Scratch of the tagging: three 32-cell bit-mask arrays (core, active, and
+// the per-word populations scanned in place), the package count and the
+// multi-resolution evaluation counter, and the scan's own scratch.
+static size_t tag_mask_bytes(int64_t nc) { return ((size_t)((nc + 31) >> 5) * 4 + 255) & ~(size_t)255; }
+static size_t tag_count_offset(int64_t nc) { return 3 * tag_mask_bytes(nc); }
+
 // Tagging steps 1-5; `flags` launches step 1 (core cells and far sides) into
-// (cell_type, active) on the grid's stream.
+// (cell_type, core mask) on the grid's stream.
 template <class Flags>
 static sg_status tag_common(sg_grid* g, Flags flags, int64_t* n_packages) {
-    const int64_t nc = g->nc;
+    const int64_t nc = g->nc, nw = (nc + 31) >> 5;
     const GridFF G = grid_ff(g);
-    const size_t act_bytes = ((size_t)nc * 4 + 255) & ~(size_t)255;
+    const size_t mb = tag_mask_bytes(nc), cnt = tag_count_offset(nc);
     if (!ensure(g, g->cell_type, (size_t)nc) || !ensure(g, g->cell_pkg, (size_t)nc * 4) ||
-        !ensure(g, g->scratch, act_bytes + scan_scratch_bytes(nc) + 256))
+        !ensure(g, g->scratch, cnt + 256 + scan_scratch_bytes(nw)))
         return fail(g, SG_ERR_OOM, "sg_tag_allocate: out of device memory");
-    uint32_t* active = (uint32_t*)g->scratch.p;
-    uint32_t* total = (uint32_t*)((char*)g->scratch.p + act_bytes);
-    void* scan_scratch = (char*)g->scratch.p + act_bytes + 256;
+    uint32_t* core = (uint32_t*)g->scratch.p;
+    uint32_t* act = (uint32_t*)((char*)g->scratch.p + mb);
+    uint32_t* count = (uint32_t*)((char*)g->scratch.p + 2 * mb);
+    uint32_t* total = (uint32_t*)((char*)g->scratch.p + cnt);
+    void* scan_scratch = (char*)g->scratch.p + cnt + 256;
     uint8_t* ct = (uint8_t*)g->cell_type.p;
-    SG_CUDA(g, flags(ct, active), "tag flags");
-    SG_CUDA(g, launch_tag_inner(G, ct, active, nc, g->stream), "tag inner");
-    SG_CUDA(g, exclusive_scan_u32(active, active, nc, total, scan_scratch, g->stream), "tag scan");
+    SG_CUDA(g, flags(ct, core), "tag flags");
+    SG_CUDA(g, launch_tag_inner(G, ct, core, act, count, nc, g->stream), "tag inner");
+    SG_CUDA(g, exclusive_scan_u32(count, count, nw, total, scan_scratch, g->stream), "tag scan");
     SG_CUDA(g, cudaMemcpyAsync(g->host_pin.p, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream), "tag count");
     SG_CUDA(g, cudaStreamSynchronize(g->stream), "tag sync");
     const int64_t P = 2 + (int64_t)*(uint32_t*)g->host_pin.p;
@@ -269,7 +277,7 @@ static sg_status tag_common(sg_grid* g, Flags flags, int64_t* n_packages) {
         return fail(g, SG_ERR_OOM, "sg_tag_allocate: out of device memory");
     }
     g->P = P;
-    SG_CUDA(g, launch_tag_scatter(ct, active, (int32_t*)g->cell_pkg.p, (int32_t*)g->pkg_cell.p,
+    SG_CUDA(g, launch_tag_scatter(ct, act, count, (int32_t*)g->cell_pkg.p, (int32_t*)g->pkg_cell.p,
                                   (uint8_t*)g->pkg_type.p, nc, g->stream),
             "tag scatter");
     if (g->desc.id_order == 1 && P > 3) {
@@ -319,7 +327,7 @@ sg_status sg_tag_allocate(sg_grid* g, const sg_shape* shape, int64_t* n_packages
     const GridFF G = grid_ff(g);
     const ShapeFF S = shape_ff(shape);
     return tag_common(
-        g, [&](uint8_t* ct, uint32_t* active) { return launch_tag_flags(G, S, ct, active, g->nc, g->stream); },
+        g, [&](uint8_t* ct, uint32_t* core) { return launch_tag_flags(G, S, ct, core, g->nc, g->stream); },
         n_packages);
 }
 
@@ -339,17 +347,16 @@ sg_status sg_tag_allocate_from(sg_grid* g, const sg_grid* coarse, const sg_shape
     const GridFF G = grid_ff(g);
     const ShapeFF S = shape_ff(shape);
     // the evaluation counter sits in the tagging scratch, beside the package count
-    const size_t act_bytes = ((size_t)g->nc * 4 + 255) & ~(size_t)255;
     unsigned long long* ev = nullptr;
     const sg_status st = tag_common(
         g,
-        [&](uint8_t* ct, uint32_t* active) {
-            ev = (unsigned long long*)((char*)g->scratch.p + act_bytes + 128);
+        [&](uint8_t* ct, uint32_t* core) {
+            ev = (unsigned long long*)((char*)g->scratch.p + tag_count_offset(g->nc) + 128);
             cudaError_t e = cudaMemsetAsync(ev, 0, sizeof(unsigned long long), g->stream);
             if (e != cudaSuccess) return e;
             return launch_tag_flags_from(G, S, (const int32_t*)coarse->cell_pkg.p, (const uint8_t*)coarse->pkg_type.p,
                                          (const float*)coarse->field[SG_FIELD_PHI].p, coarse->desc.dims[0],
-                                         coarse->desc.dims[1], ct, active, g->nc, ev, g->stream);
+                                         coarse->desc.dims[1], ct, core, g->nc, ev, g->stream);
         },
         n_packages);
     if (st != SG_OK) return st;

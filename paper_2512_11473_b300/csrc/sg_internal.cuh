@@ -90,11 +90,13 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uin
                                cudaStream_t s, const int* run = nullptr);
 
 // tagging / init (sg_tag.cu)
-cudaError_t launch_tag_flags(const GridFF& G, const ShapeFF& S, uint8_t* cell_type, uint32_t* active, int64_t nc,
+// Step 1: cell_type[nc] and the core mask (bit i of core_bits[w] = cell
+// 32 w + i is core).
+cudaError_t launch_tag_flags(const GridFF& G, const ShapeFF& S, uint8_t* cell_type, uint32_t* core_bits, int64_t nc,
                              cudaStream_t s);
 cudaError_t launch_tag_flags_from(const GridFF& G, const ShapeFF& S, const int32_t* c_cell_pkg,
                                   const uint8_t* c_pkg_type, const float* c_phi, int cnx, int cny, uint8_t* cell_type,
-                                  uint32_t* active, int64_t nc, unsigned long long* evaluated, cudaStream_t s);
+                                  uint32_t* core_bits, int64_t nc, unsigned long long* evaluated, cudaStream_t s);
 // Consistency of the cell, package, neighbour and face tables; sets
 // ERR_BAD_INDEX in *err on any inconsistency (reads are bounds-checked).
 cudaError_t launch_check_tables(const GridFF& G, const int32_t* cell_pkg, const int32_t* pkg_cell,
@@ -106,9 +108,12 @@ cudaError_t launch_cell_centres(const GridF& G, const int32_t* pkg_cell, float* 
                                 cudaStream_t s);
 cudaError_t launch_renumber(const int32_t* order, const int32_t* old_cell, const uint8_t* old_type, int32_t* pkg_cell,
                             uint8_t* pkg_type, int32_t* cell_pkg, int64_t n, cudaStream_t s);
-cudaError_t launch_tag_inner(const GridFF& G, uint8_t* cell_type, uint32_t* active, int64_t nc, cudaStream_t s);
-cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* prefix, int32_t* cell_pkg,
-                               int32_t* pkg_cell, uint8_t* pkg_type, int64_t nc, cudaStream_t s);
+// Step 2: inner cells (type 3), the active mask and its population per
+// 32-cell word; step 3: ids from the scanned populations.
+cudaError_t launch_tag_inner(const GridFF& G, uint8_t* cell_type, const uint32_t* core_bits, uint32_t* act_bits,
+                             uint32_t* count, int64_t nc, cudaStream_t s);
+cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* act_bits, const uint32_t* prefix,
+                               int32_t* cell_pkg, int32_t* pkg_cell, uint8_t* pkg_type, int64_t nc, cudaStream_t s);
 cudaError_t launch_fill_nbr(const GridFF& G, const int32_t* cell_pkg, const int32_t* pkg_cell, int32_t* nbr,
                             int64_t P, cudaStream_t s);
 // Consistency (sign) correction of phi, cell_pkg, nbr and faces in place;

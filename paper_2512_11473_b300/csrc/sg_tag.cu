@@ -61,15 +61,24 @@ __device__ __forceinline__ uint8_t classify_cell(const GridFF& G, const ShapeFF&
     return ff_lt(ff_abs(d), G.T) ? 2 : (ff_neg_p(d) ? 0 : 1);
 }
 
+// Step 1 over all cells; bit i of core_bits[w] flags cell 32 w + i core.
+// A warp classifies 32 consecutive cells (its first cell a multiple of 32).
 template <int K>
 __global__ void __launch_bounds__(TAG_THREADS) k_tag_flags(GridFF G, ShapeFF S, uint8_t* __restrict__ cell_type,
-                                                            uint32_t* __restrict__ active, int64_t nc) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
-        int64_t I[3];
-        cell_coords(c, G.dims, I[0], I[1], I[2]);
-        const uint8_t t = classify_cell<K>(G, S, I);
-        cell_type[c] = t;
-        active[c] = t == 2;
+                                                            uint32_t* __restrict__ core_bits, int64_t nc) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < nc;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = base + lane;
+        uint8_t t = 0;
+        if (c < nc) {
+            int64_t I[3];
+            cell_coords(c, G.dims, I[0], I[1], I[2]);
+            t = classify_cell<K>(G, S, I);
+            cell_type[c] = t;
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, c < nc && t == 2);
+        if (lane == 0) core_bits[base >> 5] = m;
     }
 }
 
@@ -84,54 +93,104 @@ __global__ void __launch_bounds__(TAG_THREADS) k_tag_flags_from(GridFF G, ShapeF
                                                                  const uint8_t* __restrict__ c_pkg_type,
                                                                  const float* __restrict__ c_phi, int cnx, int cny,
                                                                  uint8_t* __restrict__ cell_type,
-                                                                 uint32_t* __restrict__ active, int64_t nc,
+                                                                 uint32_t* __restrict__ core_bits, int64_t nc,
                                                                  unsigned long long* __restrict__ evaluated) {
     unsigned long long ev = 0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
-        int64_t I[3];
-        cell_coords(c, G.dims, I[0], I[1], I[2]);
-        const int64_t pc = __ldg(c_cell_pkg + (I[0] >> 1) + cnx * ((I[1] >> 1) + (int64_t)cny * (I[2] >> 1)));
-        uint8_t t;
-        if (pc >= 2 && __ldg(c_pkg_type + pc) == 2) {
-            t = classify_cell<K>(G, S, I);
-            ++ev;
-        } else {
-            t = (pc < 2 ? pc == 0 : __ldg(c_phi + pc * PKG3) < 0.0f) ? 0 : 1;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < nc;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = base + lane;
+        uint8_t t = 0;
+        if (c < nc) {
+            int64_t I[3];
+            cell_coords(c, G.dims, I[0], I[1], I[2]);
+            const int64_t pc = __ldg(c_cell_pkg + (I[0] >> 1) + cnx * ((I[1] >> 1) + (int64_t)cny * (I[2] >> 1)));
+            if (pc >= 2 && __ldg(c_pkg_type + pc) == 2) {
+                t = classify_cell<K>(G, S, I);
+                ++ev;
+            } else {
+                t = (pc < 2 ? pc == 0 : __ldg(c_phi + pc * PKG3) < 0.0f) ? 0 : 1;
+            }
+            cell_type[c] = t;
         }
-        cell_type[c] = t;
-        active[c] = t == 2;
+        const uint32_t m = __ballot_sync(0xffffffffu, c < nc && t == 2);
+        if (lane == 0) core_bits[base >> 5] = m;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ev += __shfl_down_sync(0xffffffffu, ev, o);
     if ((threadIdx.x & 31) == 0 && ev) atomicAdd(evaluated, ev);
 }
 
-// Step 2: inner cells, not core and one of the 26 neighbours is core.
-__global__ void __launch_bounds__(TAG_THREADS) k_tag_inner(GridFF G, uint8_t* cell_type,
-                                                            uint32_t* __restrict__ active, int64_t nc) {
+// Bits of cells s .. s + 31 of a bit mask (zero outside its nw words).
+__device__ __forceinline__ uint32_t bit_window(const uint32_t* __restrict__ bits, int64_t nw, int64_t s) {
+    const int64_t q = s >> 5;  // floor division, also for s < 0
+    const uint32_t lo = (q >= 0 && q < nw) ? bits[q] : 0u;
+    const uint32_t hi = (q + 1 >= 0 && q + 1 < nw) ? bits[q + 1] : 0u;
+    return __funnelshift_r(lo, hi, (int)(s & 31));
+}
+
+// Step 2: inner cells, not core and one of the 26 neighbours is core, on
+// bit masks: a thread takes the 32 cells of word w, gathers the core bits
+// of their 27-cell neighbourhoods as 27 shifted windows of the core mask
+// (cell c + dx + nx dy + nx ny dz at bit i for cell c = 32 w + i), each
+// window cleared where its move leaves the domain (cells in the first or
+// last column, row or plane).  Writes the active mask (core or inner), its
+// population per word and type 3 for the inner cells.
+__global__ void __launch_bounds__(TAG_THREADS) k_tag_inner(GridFF G, uint8_t* __restrict__ cell_type,
+                                                            const uint32_t* __restrict__ core,
+                                                            uint32_t* __restrict__ act, uint32_t* __restrict__ count,
+                                                            int64_t nc) {
     const int nx = G.dims[0], ny = G.dims[1], nz = G.dims[2];
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
-        if (cell_type[c] == 2) continue;
+    const int64_t nw = (nc + 31) >> 5, plane = (int64_t)nx * ny;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c0 = w << 5;
+        const int nvalid = (int)min((int64_t)32, nc - c0);
         int64_t I, J, K;
-        cell_coords(c, G.dims, I, J, K);
-        bool found = false;
-        // indices stay in 32 bits: the grid has fewer than 2^31 cells
-        for (int dk = -1; dk <= 1; ++dk)
-            for (int dj = -1; dj <= 1; ++dj)
-                for (int di = -1; di <= 1; ++di) {
-                    const int a = (int)I + di, b = (int)J + dj, e = (int)K + dk;
-                    if (a < 0 || b < 0 || e < 0 || a >= nx || b >= ny || e >= nz) continue;
-                    found |= cell_type[a + nx * (b + ny * e)] == 2;
+        cell_coords(c0, G.dims, I, J, K);
+        int i = (int)I, j = (int)J, k = (int)K;
+        uint32_t xl = 0, xh = 0, yl = 0, yh = 0, zl = 0, zh = 0;
+        for (int b = 0; b < nvalid; ++b) {
+            const uint32_t bit = 1u << b;
+            xl |= i == 0 ? bit : 0u;
+            xh |= i == nx - 1 ? bit : 0u;
+            yl |= j == 0 ? bit : 0u;
+            yh |= j == ny - 1 ? bit : 0u;
+            zl |= k == 0 ? bit : 0u;
+            zh |= k == nz - 1 ? bit : 0u;
+            if (++i == nx) {
+                i = 0;
+                if (++j == ny) {
+                    j = 0;
+                    ++k;
                 }
-        if (found) {
-            cell_type[c] = 3;  // other threads only test for == 2, unaffected
-            active[c] = 1;
+            }
         }
+        uint32_t near = 0;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+            const uint32_t mz = dz < 0 ? ~zl : (dz > 0 ? ~zh : ~0u);
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const uint32_t m = mz & (dy < 0 ? ~yl : (dy > 0 ? ~yh : ~0u));
+                const int64_t s = c0 + dy * (int64_t)nx + dz * plane;
+                near |= m & ((bit_window(core, nw, s - 1) & ~xl) | bit_window(core, nw, s) |
+                             (bit_window(core, nw, s + 1) & ~xh));
+            }
+        }
+        const uint32_t valid = nvalid == 32 ? 0xffffffffu : (1u << nvalid) - 1u;
+        const uint32_t cw = core[w];
+        const uint32_t inner = near & ~cw & valid;
+        act[w] = cw | inner;
+        count[w] = __popc(cw | inner);
+        for (uint32_t m = inner; m; m &= m - 1) cell_type[c0 + __ffs(m) - 1] = 3;
     }
 }
 
-// Step 3: ids in increasing cell index = 2 + exclusive prefix of active.
+// Step 3: ids in increasing cell index = 2 + number of active cells before
+// c: the scanned population of the words before c's word plus the active
+// bits below c's bit.
 __global__ void __launch_bounds__(TAG_THREADS) k_tag_scatter(const uint8_t* __restrict__ cell_type,
+                                                              const uint32_t* __restrict__ act,
                                                               const uint32_t* __restrict__ prefix,
                                                               int32_t* __restrict__ cell_pkg,
                                                               int32_t* __restrict__ pkg_cell,
@@ -143,7 +202,9 @@ __global__ void __launch_bounds__(TAG_THREADS) k_tag_scatter(const uint8_t* __re
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         uint8_t t = cell_type[c];
         if (t >= 2) {
-            int32_t id = 2 + (int32_t)prefix[c];
+            const int64_t w = c >> 5;
+            const uint32_t below = act[w] & ((1u << (c & 31)) - 1u);
+            const int32_t id = 2 + (int32_t)(prefix[w] + __popc(below));
             cell_pkg[c] = id;
             pkg_cell[id] = (int32_t)c;
             pkg_type[id] = t;
@@ -263,18 +324,19 @@ unsigned grid_for(int64_t n, int threads) {
 
 }  // namespace
 
-cudaError_t launch_tag_flags(const GridFF& G, const ShapeFF& S, uint8_t* cell_type, uint32_t* active, int64_t nc,
+cudaError_t launch_tag_flags(const GridFF& G, const ShapeFF& S, uint8_t* cell_type, uint32_t* core_bits, int64_t nc,
                              cudaStream_t s) {
-    SG_SHAPE_DISPATCH(S.kind, (k_tag_flags<K><<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, cell_type, active, nc)));
+    SG_SHAPE_DISPATCH(S.kind, (k_tag_flags<K><<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, cell_type, core_bits,
+                                                                                                nc)));
     note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_tag_flags_from(const GridFF& G, const ShapeFF& S, const int32_t* c_cell_pkg,
                                   const uint8_t* c_pkg_type, const float* c_phi, int cnx, int cny, uint8_t* cell_type,
-                                  uint32_t* active, int64_t nc, unsigned long long* evaluated, cudaStream_t s) {
+                                  uint32_t* core_bits, int64_t nc, unsigned long long* evaluated, cudaStream_t s) {
     SG_SHAPE_DISPATCH(S.kind, (k_tag_flags_from<K><<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(
-                                  G, S, c_cell_pkg, c_pkg_type, c_phi, cnx, cny, cell_type, active, nc, evaluated)));
+                                  G, S, c_cell_pkg, c_pkg_type, c_phi, cnx, cny, cell_type, core_bits, nc, evaluated)));
     note_launch();
     return cudaGetLastError();
 }
@@ -333,16 +395,18 @@ cudaError_t launch_renumber(const int32_t* order, const int32_t* old_cell, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_tag_inner(const GridFF& G, uint8_t* cell_type, uint32_t* active, int64_t nc, cudaStream_t s) {
-    k_tag_inner<<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_type, active, nc);
+cudaError_t launch_tag_inner(const GridFF& G, uint8_t* cell_type, const uint32_t* core_bits, uint32_t* act_bits,
+                             uint32_t* count, int64_t nc, cudaStream_t s) {
+    const int64_t nw = (nc + 31) >> 5;
+    k_tag_inner<<<grid_for(nw, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_type, core_bits, act_bits, count, nc);
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* prefix, int32_t* cell_pkg,
-                               int32_t* pkg_cell, uint8_t* pkg_type, int64_t nc, cudaStream_t s) {
-    k_tag_scatter<<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(cell_type, prefix, cell_pkg, pkg_cell, pkg_type,
-                                                                     nc);
+cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* act_bits, const uint32_t* prefix,
+                               int32_t* cell_pkg, int32_t* pkg_cell, uint8_t* pkg_type, int64_t nc, cudaStream_t s) {
+    k_tag_scatter<<<grid_for(nc, TAG_THREADS), TAG_THREADS, 0, s>>>(cell_type, act_bits, prefix, cell_pkg, pkg_cell,
+                                                                     pkg_type, nc);
     note_launch();
     return cudaGetLastError();
 }
