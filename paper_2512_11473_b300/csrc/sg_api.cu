@@ -473,8 +473,12 @@ sg_status sg_reinit(sg_grid* g, int32_t iterations, float cfl) {
     SG_CUDA(g, launch_reinit_s0(G, phi, s0, g->P, g->stream), "reinit s0");
     float* a = phi;
     float* b = tmp;
+    // sweeps alternate their direction, the first against the S0 pass, so
+    // that each starts on the packages whose phi and S0 the previous pass
+    // left in L2 (the results do not depend on the order: a sweep reads only
+    // the previous iterate)
     for (int32_t it = 0; it < iterations; ++it) {
-        SG_CUDA(g, launch_reinit_step(G, faces, s0, a, b, dt, g->P, g->stream), "reinit step");
+        SG_CUDA(g, launch_reinit_step(G, faces, s0, a, b, dt, g->P, (it & 1) == 0, g->stream), "reinit step");
         float* t = a;
         a = b;
         b = t;

@@ -26,8 +26,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 8) k_reinit_step(const int32_t* _
                                                               const float* __restrict__ s0,
                                                               const float* __restrict__ phi_in,
                                                               float* __restrict__ phi_out, int64_t P, float cfl,
-                                                              float dt) {
-    const RowSlot s = row_slot(P);
+                                                              float dt, int reverse) {
+    const RowSlot s = row_slot_dir(P, reverse);
     const float4 sg = s.valid ? __ldg(reinterpret_cast<const float4*>(s0) + s.q4) : make_float4(0.f, 0.f, 0.f, 0.f);
     const Rows w = load_rows(phi_in, faces, s);
     if (!s.valid) return;
@@ -45,10 +45,11 @@ cudaError_t launch_reinit_s0(const GridF& G, const float* phi, float* s0, int64_
 }
 
 cudaError_t launch_reinit_step(const GridF& G, const int32_t* faces, const float* s0, const float* phi_in,
-                               float* phi_out, float dt, int64_t P, cudaStream_t s) {
+                               float* phi_out, float dt, int64_t P, int reverse, cudaStream_t s) {
     if (P <= 2) return cudaSuccess;
     // dt sqrt(G) = (dt / h) sqrt(h^2 G) and dt / h is the CFL number
-    k_reinit_step<<<row_blocks(P), ROW_THREADS, 0, s>>>(faces, s0, phi_in, phi_out, P, (float)(dt / G.h_d), dt);
+    k_reinit_step<<<row_blocks(P), ROW_THREADS, 0, s>>>(faces, s0, phi_in, phi_out, P, (float)(dt / G.h_d), dt,
+                                                        reverse);
     note_launch();
     return cudaGetLastError();
 }

@@ -167,6 +167,16 @@ __device__ __forceinline__ RowSlot row_slot(int64_t P) {
     return make_slot(p, p < P);
 }
 
+// The same with the CTAs taken in reverse order when `reverse` is set (CTA
+// b owns the packages of CTA gridDim.x - 1 - b): a sweep that follows one
+// in the other direction starts on the packages whose data the previous
+// sweep touched last, still in L2.
+__device__ __forceinline__ RowSlot row_slot_dir(int64_t P, int reverse) {
+    const int64_t b = reverse ? (int64_t)gridDim.x - 1 - blockIdx.x : (int64_t)blockIdx.x;
+    const int64_t p = 2 + b * ROW_PKGS + (threadIdx.x >> 4);
+    return make_slot(p, p < P);
+}
+
 inline unsigned row_blocks(int64_t P) { return (unsigned)((P - 2 + ROW_PKGS - 1) / ROW_PKGS); }
 
 }  // namespace
