@@ -18,13 +18,6 @@ __device__ __forceinline__ void lattice(float x, float lo, float inv_h, int& i0,
     t = __fsub_rn(u, f);
 }
 
-__device__ __forceinline__ int64_t corner_index(const int32_t* __restrict__ nb, int sx, int sy, int sz) {
-    // index shift (Listing 2) for shifts in [0, 4] from the home package
-    int nx = (sx + PKG) >> 2, ny = (sy + PKG) >> 2, nz = (sz + PKG) >> 2;
-    int pkg = __ldg(nb + nx + 3 * ny + 9 * nz);
-    return (int64_t)pkg * PKG3 + (sx + PKG - nx * PKG) + PKG * (sy + PKG - ny * PKG) + PKG * PKG * (sz + PKG - nz * PKG);
-}
-
 // Where a particle sits: home package (the package of its home coarse cell
 // I = floor(i0 / 4), or `outside` when I leaves the domain), the local index
 // l = i0 - 4 I of the lower interpolation corner and the weights t.
@@ -56,18 +49,32 @@ __device__ __forceinline__ ProbeAt probe_locate(const float (&lo)[3], float inv_
 
 // Trilinear interpolation of the first NF probe fields (phi, gx, gy, gz, W,
 // Gx, Gy, Gz) from the 8 corners, reached from the home package by the
-// index shift.
+// index shift.  Per axis the lower corner l lies in the home package's
+// column and the upper one, l + 1, in the next package when l = 3, so a
+// corner's neighbourhood slot is 13 + (up_x + 3 up_y + 9 up_z) and the home
+// package itself needs no table read.  (32-bit element offsets measured
+// slower: 1.34 against 1.15 ms for 50M probes on the torus.)
 template <int NF>
 __device__ __forceinline__ void probe_interp(const int32_t* __restrict__ nbr, const ProbeFields& F, const ProbeAt& A,
                                              float (&acc)[8]) {
     const int32_t* nb = nbr + A.home * NB;
+    int up[3], lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        up[a] = A.l[a] == 3 ? 1 : 0;
+        lo[a] = A.l[a];
+        hi[a] = up[a] ? 0 : A.l[a] + 1;
+    }
 #pragma unroll
     for (int f = 0; f < 8; ++f) acc[f] = 0.0f;
 #pragma unroll
     for (int cr = 0; cr < 8; ++cr) {
         const int a0 = cr & 1, a1 = (cr >> 1) & 1, a2 = (cr >> 2) & 1;
         const float w = (a0 ? A.t[0] : 1.0f - A.t[0]) * (a1 ? A.t[1] : 1.0f - A.t[1]) * (a2 ? A.t[2] : 1.0f - A.t[2]);
-        const int64_t at = corner_index(nb, A.l[0] + a0, A.l[1] + a1, A.l[2] + a2);
+        const int slot = (a0 ? up[0] : 0) + 3 * (a1 ? up[1] : 0) + 9 * (a2 ? up[2] : 0);
+        const int64_t pkg = slot == 0 ? A.home : (int64_t)__ldg(nb + 13 + slot);
+        const int64_t at =
+            pkg * PKG3 + ((a0 ? hi[0] : lo[0]) + PKG * (a1 ? hi[1] : lo[1]) + PKG * PKG * (a2 ? hi[2] : lo[2]));
 #pragma unroll
         for (int f = 0; f < NF; ++f) acc[f] = fmaf(w, __ldg(F.f[f] + at), acc[f]);
     }
@@ -81,17 +88,23 @@ template <int NF>
 __device__ __forceinline__ void probe_interp_packed(const int32_t* __restrict__ nbr, const float* __restrict__ tab,
                                                     const ProbeAt& A, float (&acc)[8]) {
     const int32_t* nb = nbr + A.home * NB;
+    int up[3], lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        up[a] = A.l[a] == 3 ? 1 : 0;
+        lo[a] = A.l[a];
+        hi[a] = up[a] ? 0 : A.l[a] + 1;
+    }
 #pragma unroll
     for (int f = 0; f < 8; ++f) acc[f] = 0.0f;
 #pragma unroll
     for (int cr = 0; cr < 8; ++cr) {
         const int a0 = cr & 1, a1 = (cr >> 1) & 1, a2 = (cr >> 2) & 1;
         const float w = (a0 ? A.t[0] : 1.0f - A.t[0]) * (a1 ? A.t[1] : 1.0f - A.t[1]) * (a2 ? A.t[2] : 1.0f - A.t[2]);
-        const int sx = A.l[0] + a0, sy = A.l[1] + a1, sz = A.l[2] + a2;
-        const int nx = (sx + PKG) >> 2, ny = (sy + PKG) >> 2, nz = (sz + PKG) >> 2;
-        const int pkg = __ldg(nb + nx + 3 * ny + 9 * nz);
-        const float* q = tab + (int64_t)pkg * (8 * PKG3) + (sx + PKG - nx * PKG) + PKG * (sy + PKG - ny * PKG) +
-                         PKG * PKG * (sz + PKG - nz * PKG);
+        const int slot = (a0 ? up[0] : 0) + 3 * (a1 ? up[1] : 0) + 9 * (a2 ? up[2] : 0);
+        const int64_t pkg = slot == 0 ? A.home : (int64_t)__ldg(nb + 13 + slot);
+        const float* q = tab + pkg * (8 * PKG3) + (a0 ? hi[0] : lo[0]) + PKG * (a1 ? hi[1] : lo[1]) +
+                         PKG * PKG * (a2 ? hi[2] : lo[2]);
 #pragma unroll
         for (int f = 0; f < NF; ++f) acc[f] = fmaf(w, __ldg(q + f * PKG3), acc[f]);
     }

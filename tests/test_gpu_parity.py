@@ -72,6 +72,32 @@ def test_tag_allocate_bit_exact(sg, name):
     g.sync()
 
 
+# Background grids whose rows, planes and total cell count fall across the
+# 32-cell words of the tagging bit masks in every way: one-cell axes, rows of
+# 31 and 33 cells, a plane of exactly 64 cells, and a count that is not a
+# multiple of 32.
+ODD_DIMS = [(1, 5, 7), (2, 33, 3), (31, 3, 17), (33, 1, 40), (8, 8, 9), (64, 1, 3), (7, 31, 1), (1, 1, 97)]
+
+
+@pytest.mark.parametrize("dims", ODD_DIMS)
+def test_tag_bit_mask_word_edges(sg, dims):
+    h = 0.02
+    lo = tuple(-2.0 * h * n for n in dims)  # the domain is centred on the origin
+    spec = si.GridSpec(lo, dims, h)
+    # a sphere through the middle of the box: core cells on every word edge
+    shape = si.sphere(0.9 * 2.0 * h * max(min(dims), 2))
+    g = sg.Grid(spec)
+    P = g.tag_allocate(shape)
+    cp, ct, P_o, ties = oracle.tag(spec, shape)
+    assert ties == 0
+    assert P == P_o
+    assert np.array_equal(H(g.field("cell_pkg")), cp)
+    pc, pt, nbr = oracle.tables(spec, cp, ct, P_o)
+    assert np.array_equal(H(g.field("pkg_cell")), pc)
+    assert np.array_equal(H(g.field("pkg_type")), pt)
+    assert np.array_equal(H(g.field("nbr")), nbr)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_init_sdf_within_tolerance(sg, name):
     g, O, P, shape, spec = build_both(sg, name)
