@@ -59,32 +59,56 @@ __global__ void __launch_bounds__(SW_THREADS) k_copy(const float* __restrict__ s
         dst[e] = src[e];
 }
 
+// 16 packages per CTA: the 36 rows of each package's 6^3 Heaviside tile are
+// staged by all threads, then each thread sums the taps of one package row
+// of four points (the loads of neighbouring points are shared) and writes
+// four outputs per field as 16-byte stores.
+constexpr int IN_PKGS = 16;
+
 __global__ void __launch_bounds__(SW_THREADS) k_kernel_integrals(const int32_t* __restrict__ nbr,
                                                                   const float* __restrict__ phi, float* __restrict__ W,
                                                                   float* __restrict__ gx, float* __restrict__ gy,
                                                                   float* __restrict__ gz, int64_t P, KernelCoef K,
                                                                   float inv_eps) {
-    __shared__ int s_nb[SW_PKGS][NB];
-    __shared__ float s_H[SW_PKGS][216];  // 6^3 tile: package plus a one-point halo
-    __shared__ unsigned s_sat[SW_PKGS];
-    const int lp = threadIdx.x >> 6, d = threadIdx.x & 63;
-    const int64_t p = 2 + (int64_t)blockIdx.x * SW_PKGS + lp;
-    const bool valid = p < P;
-    if (valid && d < NB) s_nb[lp][d] = __ldg(nbr + p * NB + d);
-    if (d == 0) s_sat[lp] = 0;
+    __shared__ int s_nb[IN_PKGS][NB];
+    __shared__ __align__(16) float s_H[IN_PKGS][216];  // 6^3 tile: package plus a one-point halo
+    __shared__ unsigned s_sat[IN_PKGS];
+    const int64_t p0 = 2 + (int64_t)blockIdx.x * IN_PKGS;
+    const int n_pk = (int)min((int64_t)IN_PKGS, P - p0);
+    for (int e = threadIdx.x; e < IN_PKGS * NB; e += SW_THREADS) {
+        const int lp = e / NB;
+        if (lp < n_pk) s_nb[lp][e - lp * NB] = __ldg(nbr + (p0 + lp) * NB + (e - lp * NB));
+    }
+    if (threadIdx.x < IN_PKGS) s_sat[threadIdx.x] = 0;
     __syncthreads();
-    // a package is two whole warps: OR the saturation bits per warp, then per package
-    const unsigned bits = __reduce_or_sync(0xffffffffu, valid ? integrals_stage(s_nb[lp], phi, inv_eps, d, s_H[lp]) : 0u);
-    if ((threadIdx.x & 31) == 0 && bits) atomicOr(&s_sat[lp], bits);
+    for (int e = threadIdx.x; e < IN_PKGS * 36; e += SW_THREADS) {
+        const int lp = e / 36;
+        if (lp < n_pk) {
+            const unsigned bits = integrals_stage(s_nb[lp], phi, inv_eps, e - lp * 36, s_H[lp]);
+            if (bits) atomicOr(&s_sat[lp], bits);
+        }
+    }
     __syncthreads();
-    if (!valid) return;
-    float w, ax, ay, az;
-    if (!integrals_saturated(s_sat[lp], w, ax, ay, az)) integrals_point(s_H[lp], d, K, w, ax, ay, az);
-    const int64_t at = p * PKG3 + d;
-    W[at] = w;
-    gx[at] = ax;
-    gy[at] = ay;
-    gz[at] = az;
+    const int lp = threadIdx.x >> 4, r = threadIdx.x & 15;
+    if (lp >= n_pk) return;
+    float4 ow, ox, oy, oz;
+    float w[4], ax[4], ay[4], az[4];
+    if (!integrals_saturated(s_sat[lp], w[0], ax[0], ay[0], az[0])) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) integrals_point(s_H[lp], 4 * r + i, K, w[i], ax[i], ay[i], az[i]);
+    } else {
+#pragma unroll
+        for (int i = 1; i < 4; ++i) w[i] = w[0], ax[i] = ax[0], ay[i] = ay[0], az[i] = az[0];
+    }
+    ow = make_float4(w[0], w[1], w[2], w[3]);
+    ox = make_float4(ax[0], ax[1], ax[2], ax[3]);
+    oy = make_float4(ay[0], ay[1], ay[2], ay[3]);
+    oz = make_float4(az[0], az[1], az[2], az[3]);
+    const int64_t q4 = (p0 + lp) * 16 + r;
+    reinterpret_cast<float4*>(W)[q4] = ow;
+    reinterpret_cast<float4*>(gx)[q4] = ox;
+    reinterpret_cast<float4*>(gy)[q4] = oy;
+    reinterpret_cast<float4*>(gz)[q4] = oz;
 }
 
 // Supports above 2h: 8^3 tiles, 5^3 taps.
@@ -208,8 +232,8 @@ cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const fl
         k_kernel_integrals_wide<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(R),
                                                                       (float)(1.0 / eps));
     else
-        k_kernel_integrals<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(R),
-                                                                 (float)(1.0 / eps));
+        k_kernel_integrals<<<(unsigned)((P - 2 + IN_PKGS - 1) / IN_PKGS), SW_THREADS, 0, s>>>(
+            nbr, phi, W, gx, gy, gz, P, kernel_coef(R), (float)(1.0 / eps));
     note_launch();
     return cudaGetLastError();
 }
