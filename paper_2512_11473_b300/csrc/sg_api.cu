@@ -390,8 +390,9 @@ sg_status sg_init_sdf(sg_grid* g, const sg_shape* shape) {
     if (g->state < 1) return fail(g, SG_ERR_STATE, "sg_init_sdf: grid not tagged");
     DeviceGuard dg(g->device);
     float* phi = field_ptr(g, SG_FIELD_PHI, false);
-    if (!phi) return fail(g, SG_ERR_OOM, "sg_init_sdf: out of device memory");
-    SG_CUDA(g, launch_init_sdf(grid_ff(g), shape_ff(shape), (const int32_t*)g->pkg_cell.p, phi, (float)g->F, g->P,
+    const GridFF G = grid_ff(g);
+    if (!phi || !ensure(g, g->scratch, init_table_bytes(G))) return fail(g, SG_ERR_OOM, "sg_init_sdf: out of device memory");
+    SG_CUDA(g, launch_init_sdf(G, shape_ff(shape), (const int32_t*)g->pkg_cell.p, phi, (float)g->F, g->P, g->scratch.p,
                                g->stream),
             "init sdf");
     g->state = 2;

@@ -125,8 +125,11 @@ cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cel
                             void* scratch, void* host_pin, int64_t out[4], cudaStream_t s);
 // faces[p][8] = the six face entries of nbr[p][27] (one 32-byte row per package)
 cudaError_t launch_fill_faces(const int32_t* nbr, int32_t* faces, int64_t P, cudaStream_t s);
+// Level set at the data points; table: scratch of init_table_bytes(G) for
+// the tabulated lattice coordinates.
 cudaError_t launch_init_sdf(const GridFF& G, const ShapeFF& S, const int32_t* pkg_cell, float* phi, float F,
-                            int64_t P, cudaStream_t s);
+                            int64_t P, void* table, cudaStream_t s);
+inline size_t init_table_bytes(const GridFF& G) { return (size_t)4 * (G.dims[0] + G.dims[1] + G.dims[2]) * 8; }
 
 // sweeps (sg_sweep.cu)
 cudaError_t launch_set_far(float* f, float v_in, float v_out, cudaStream_t s);

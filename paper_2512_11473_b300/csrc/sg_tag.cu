@@ -297,10 +297,24 @@ __global__ void __launch_bounds__(TAG_THREADS) k_check_tables(GridFF G, const in
 }
 
 // Step 4: phi at cell-centred data points, float-float, rounded once.
+// The fine lattice coordinates lo_a + (e + 1/2) h, e = 4 I + l in
+// [0, 4 dims_a), of the three axes in float-float, one after the other:
+// the data points' coordinates, tabulated once per call.
+__global__ void __launch_bounds__(TAG_THREADS) k_coord_table(GridFF G, ff* __restrict__ tab) {
+    const int n0 = 4 * G.dims[0], n1 = 4 * G.dims[1], n = n0 + n1 + 4 * G.dims[2];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int a = e < n0 ? 0 : (e < n0 + n1 ? 1 : 2);
+        const int m = e - (a == 0 ? 0 : (a == 1 ? n0 : n0 + n1));
+        tab[e] = ff_add(G.lo[a], ff_mul_f(G.h, (float)m + 0.5f));
+    }
+}
+
 template <int K>
 __global__ void __launch_bounds__(TAG_THREADS, K == SHAPE_PRISM ? 4 : 8) k_init_sdf(GridFF G, ShapeFF S, const int32_t* __restrict__ pkg_cell,
-                                                           float* __restrict__ phi, int64_t P) {
+                                                           const ff* __restrict__ tab, float* __restrict__ phi,
+                                                           int64_t P) {
     const int64_t total = (P - 2) * PKG3;
+    const int off[3] = {0, 4 * G.dims[0], 4 * (G.dims[0] + G.dims[1])};
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         int64_t p = 2 + e / PKG3;
@@ -310,7 +324,10 @@ __global__ void __launch_bounds__(TAG_THREADS, K == SHAPE_PRISM ? 4 : 8) k_init_
         const int l[3] = {d & 3, (d >> 2) & 3, d >> 4};
         ff x[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) x[a] = ff_add(G.lo[a], ff_mul_f(G.h, (float)(4 * (int)I[a] + l[a]) + 0.5f));
+        for (int a = 0; a < 3; ++a) {
+            const float2 v = __ldg(reinterpret_cast<const float2*>(tab) + off[a] + 4 * (int)I[a] + l[a]);
+            x[a] = ff{v.x, v.y};
+        }
         phi[p * PKG3 + d] = ff_to_float(ff_sdf_k<K>(S, x));
     }
 }
@@ -425,12 +442,16 @@ cudaError_t launch_fill_faces(const int32_t* nbr, int32_t* faces, int64_t P, cud
 }
 
 cudaError_t launch_init_sdf(const GridFF& G, const ShapeFF& S, const int32_t* pkg_cell, float* phi, float F,
-                            int64_t P, cudaStream_t s) {
+                            int64_t P, void* table, cudaStream_t s) {
     cudaError_t e = launch_set_far(phi, -F, F, s);
     if (e != cudaSuccess) return e;
     if (P > 2) {
+        const int n = 4 * (G.dims[0] + G.dims[1] + G.dims[2]);
+        k_coord_table<<<(n + TAG_THREADS - 1) / TAG_THREADS, TAG_THREADS, 0, s>>>(G, (ff*)table);
+        note_launch();
+        const ff* tab = (const ff*)table;
         SG_SHAPE_DISPATCH(S.kind, (k_init_sdf<K><<<grid_for((P - 2) * PKG3, TAG_THREADS), TAG_THREADS, 0, s>>>(
-                                      G, S, pkg_cell, phi, P)));
+                                      G, S, pkg_cell, tab, phi, P)));
         note_launch();
     }
     return cudaGetLastError();
