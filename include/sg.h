@@ -280,8 +280,8 @@ SG_API sg_status sg_morton_order(sg_grid *g, int64_t n, const float *x, const fl
 typedef struct sg_batch sg_batch;
 
 /* How a batch run is scheduled.  pkgs_per_item: packages each half-warp
- * takes per work item (1, 2, 4 or 8; a CTA takes 16 times that for the face
- * stencils, 4 times that for the integrals); depth: packages whose loads a
+ * takes per work item (1, 2, 4 or 8; a CTA takes 16 times that, for the
+ * face stencils and the integrals alike); depth: packages whose loads a
  * half-warp has in flight at once (1 or 2, at most pkgs_per_item).  The
  * sweeps are those of sg_gradient, sg_reinit(reinit_iterations, cfl) and
  * sg_kernel_integrals(integrals_mode, m): integrals_mode 0 is the exact sum,

@@ -75,8 +75,7 @@ struct BodyParams {
 };
 
 constexpr int BT = 256;       // threads per CTA
-constexpr int BT_HW = BT / 16;  // half-warps (row kernels: packages per slot)
-constexpr int BT_PK = BT / PKG3;  // packages per slot of the integrals kernel
+constexpr int BT_HW = BT / 16;  // half-warps (row kernels and integrals: packages per slot)
 
 __device__ __forceinline__ int64_t next_item(unsigned* counter, int* s_item) {
     __syncthreads();
@@ -174,49 +173,59 @@ __global__ void __launch_bounds__(BT) k_batch_s0(const uint8_t* __restrict__ typ
     }
 }
 
-// Kernel integrals over the global store: a work item is 4 * ppi packages,
-// 64 threads per package.
+// Kernel integrals over the global store, as the single-grid kernel: a CTA
+// per 16 consecutive packages (the batch's store is one package array), all
+// threads staging the 16 Heaviside tiles, then each thread summing one
+// package row of four points.  Far packages are skipped; each package takes
+// the Heaviside width of its body.
 __global__ void __launch_bounds__(BT) k_batch_integrals(const int32_t* __restrict__ nbr, const uint8_t* __restrict__ type,
                                                         const int32_t* __restrict__ body,
                                                         const BodyParams* __restrict__ prm,
                                                         const float* __restrict__ phi, float* __restrict__ W,
                                                         float* __restrict__ gx, float* __restrict__ gy,
-                                                        float* __restrict__ gz, int64_t P, int ppi, KernelCoef K,
-                                                        unsigned* counter) {
-    __shared__ int s_item;
-    __shared__ int s_nb[BT_PK][NB];
-    __shared__ float s_H[BT_PK][216];
-    __shared__ unsigned s_sat[BT_PK];
-    const int lp = threadIdx.x >> 6, d = threadIdx.x & 63;
-    const int64_t per_item = (int64_t)BT_PK * ppi, items = (P + per_item - 1) / per_item;
-    for (;;) {
-        const int64_t item = next_item(counter, &s_item);
-        if (item >= items) break;
-        for (int k = 0; k < ppi; ++k) {
-            const int64_t p = item * per_item + (int64_t)k * BT_PK + lp;
-            const bool valid = p < P && __ldg(type + (p < P ? p : 0)) >= 2;
-            if (valid && d < NB) s_nb[lp][d] = __ldg(nbr + p * NB + d);
-            if (d == 0) s_sat[lp] = 0;
-            __syncthreads();
-            unsigned bits = 0;
-            if (valid) {
-                const float inv_eps = __ldg(&prm[__ldg(body + p)].inv_eps);
-                bits = integrals_stage(s_nb[lp], phi, inv_eps, d, s_H[lp]);
-            }
-            bits = __reduce_or_sync(0xffffffffu, bits);  // a package is two whole warps
-            if ((threadIdx.x & 31) == 0 && bits) atomicOr(&s_sat[lp], bits);
-            __syncthreads();
-            if (valid) {
-                float w, ax, ay, az;
-                if (!integrals_saturated(s_sat[lp], w, ax, ay, az)) integrals_point(s_H[lp], d, K, w, ax, ay, az);
-                const int64_t at = p * PKG3 + d;
-                W[at] = w;
-                gx[at] = ax;
-                gy[at] = ay;
-                gz[at] = az;
-            }
+                                                        float* __restrict__ gz, int64_t P, KernelCoef K) {
+    __shared__ int s_nb[BT_HW][NB];
+    __shared__ float s_H[BT_HW][216];
+    __shared__ unsigned s_sat[BT_HW];
+    __shared__ float s_ieps[BT_HW];
+    __shared__ int s_ok[BT_HW];
+    const int64_t p0 = (int64_t)blockIdx.x * BT_HW;
+    if (threadIdx.x < BT_HW) {
+        const int64_t p = p0 + threadIdx.x;
+        const bool ok = p < P && __ldg(type + p) >= 2;
+        s_ok[threadIdx.x] = ok;
+        s_sat[threadIdx.x] = 0;
+        s_ieps[threadIdx.x] = ok ? __ldg(&prm[__ldg(body + p)].inv_eps) : 0.0f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < BT_HW * NB; e += BT) {
+        const int lp = e / NB;
+        if (s_ok[lp]) s_nb[lp][e - lp * NB] = __ldg(nbr + (p0 + lp) * NB + (e - lp * NB));
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < BT_HW * 36; e += BT) {
+        const int lp = e / 36;
+        if (s_ok[lp]) {
+            const unsigned bits = integrals_stage(s_nb[lp], phi, s_ieps[lp], e - lp * 36, s_H[lp]);
+            if (bits) atomicOr(&s_sat[lp], bits);
         }
     }
+    __syncthreads();
+    const int lp = threadIdx.x >> 4, r = threadIdx.x & 15;
+    if (!s_ok[lp]) return;
+    float w[4], ax[4], ay[4], az[4];
+    if (!integrals_saturated(s_sat[lp], w[0], ax[0], ay[0], az[0])) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) integrals_point(s_H[lp], 4 * r + i, K, w[i], ax[i], ay[i], az[i]);
+    } else {
+#pragma unroll
+        for (int i = 1; i < 4; ++i) w[i] = w[0], ax[i] = ax[0], ay[i] = ay[0], az[i] = az[0];
+    }
+    const int64_t q4 = (p0 + lp) * 16 + r;
+    reinterpret_cast<float4*>(W)[q4] = make_float4(w[0], w[1], w[2], w[3]);
+    reinterpret_cast<float4*>(gx)[q4] = make_float4(ax[0], ax[1], ax[2], ax[3]);
+    reinterpret_cast<float4*>(gy)[q4] = make_float4(ay[0], ay[1], ay[2], ay[3]);
+    reinterpret_cast<float4*>(gz)[q4] = make_float4(az[0], az[1], az[2], az[3]);
 }
 
 __global__ void k_batch_offset_nbr(const int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t n,
@@ -433,9 +442,9 @@ cudaError_t record_run(sg_batch* b, const sg_batch_plan& plan, cudaStream_t s) {
     if (plan.integrals_mode == 1)
         return launch_batch_surrogate_integrals(nbr, type, body, (const SurBody*)b->sur.p, phi, fo[4], fo[5], fo[6],
                                                 fo[7], b->P, b->mlp, b->device, s);
-    const int nbi = persistent_blocks((const void*)k_batch_integrals, b->device);
-    k_batch_integrals<<<nbi, BT, 0, s>>>(nbr, type, body, prm, phi, fo[4], fo[5], fo[6], fo[7], b->P, ppi, K,
-                                         ctr + c++);
+    // a plain grid: the integrals' per-package work is even, so they need no work counter
+    k_batch_integrals<<<(unsigned)((b->P + BT_HW - 1) / BT_HW), BT, 0, s>>>(nbr, type, body, prm, phi, fo[4], fo[5],
+                                                                           fo[6], fo[7], b->P, K);
     note_launch();
     return cudaGetLastError();
 }
