@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(BT) k_batch_integrals(const int32_t* __restric
                                                         float* __restrict__ gx, float* __restrict__ gy,
                                                         float* __restrict__ gz, int64_t P, KernelCoef K) {
     __shared__ int s_nb[BT_HW][NB];
-    __shared__ float s_H[BT_HW][216];
+    __shared__ float s_H[BT_HW][TILE_N];
     __shared__ unsigned s_sat[BT_HW];
     __shared__ float s_ieps[BT_HW];
     __shared__ int s_ok[BT_HW];

@@ -25,6 +25,16 @@ struct KernelCoef {
 // discrete sum of the taps
 KernelCoef kernel_coef(double R = 2.0);
 
+// A package's 6^3 tile (the package plus a one-point halo) in shared
+// memory: rows of 6 along x, planes of 40 (6 x 6 padded), 241 floats per
+// package.  When 16 threads of a package take one row (j, k) each and a warp
+// holds two packages, every tap load falls on 32 distinct banks: the rows
+// 6 j + 40 k cover the even banks, the odd tile size puts the second
+// package on the odd ones (6 x 36 x 216 gave 3-way conflicts).
+constexpr int TILE_Y = 6;
+constexpr int TILE_Z = 40;
+constexpr int TILE_N = 241;
+
 namespace {
 
 __device__ __forceinline__ float heaviside_neg(float phi, float inv_eps) {
@@ -56,7 +66,7 @@ __device__ __forceinline__ unsigned stage_rows(const int* nb27, const float* __r
         const float4 v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb27[nb + 1] * PKG3 + d0));
         const float vm = __ldg(phi + (int64_t)nb27[nb] * PKG3 + d0 + 3);
         const float vp = __ldg(phi + (int64_t)nb27[nb + 2] * PKG3 + d0);
-        const int e0 = 6 * (y + 1) + 36 * (z + 1);
+        const int e0 = TILE_Y * (y + 1) + TILE_Z * (z + 1);
         const float f[6] = {vm, v.x, v.y, v.z, v.w, vp};
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
@@ -151,7 +161,7 @@ __device__ __forceinline__ bool integrals_saturated(unsigned tile_bits, float& w
 __device__ __forceinline__ void integrals_point(const float* tile, int d, const KernelCoef& K, float& w,
                                                 float& ax, float& ay, float& az) {
     const int i = d & 3, j = (d >> 2) & 3, k = d >> 4;
-    const float* H = tile + (i + 1) + 6 * (j + 1) + 36 * (k + 1);
+    const float* H = tile + (i + 1) + TILE_Y * (j + 1) + TILE_Z * (k + 1);
     w = 0.0f;
     ax = ay = az = 0.0f;
 #pragma unroll
@@ -160,7 +170,7 @@ __device__ __forceinline__ void integrals_point(const float* tile, int d, const 
         float h0[3], a[3], b[3];
 #pragma unroll
         for (int sy = -1; sy <= 1; ++sy) {
-            const float* row = H + 6 * sy + 36 * sz;
+            const float* row = H + TILE_Y * sy + TILE_Z * sz;
             const float m = row[-1], p = row[1];
             h0[sy + 1] = row[0];
             a[sy + 1] = m + p;

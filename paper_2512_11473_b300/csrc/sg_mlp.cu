@@ -421,12 +421,12 @@ __global__ void __launch_bounds__(TR_WARPS * 32) k_mlp_train(const unsigned char
 
 __device__ __forceinline__ int sur_classify(const float* tile, int d, const SurConst& C, float (&v)[MLP_IN]) {
     const int i = d & 3, j = (d >> 2) & 3, k = d >> 4;
-    const int e0 = (i + 1) + 6 * (j + 1) + 36 * (k + 1);
+    const int e0 = (i + 1) + TILE_Y * (j + 1) + TILE_Z * (k + 1);
     bool all_in = true, all_out = true;
 #pragma unroll
     for (int n = 0; n < MLP_IN; ++n) {
         const int sx = n % 3 - 1, sy = (n / 3) % 3 - 1, sz = n / 9 - 1;
-        const float f = tile[e0 + sx + 6 * sy + 36 * sz];
+        const float f = tile[e0 + sx + TILE_Y * sy + TILE_Z * sz];
         const float tt = __fmul_rn(-f, C.inv_h);  // the Heaviside argument z / eps
         all_in &= tt > 1.0f;
         all_out &= tt < -1.0f;
@@ -438,8 +438,8 @@ __device__ __forceinline__ int sur_classify(const float* tile, int d, const SurC
     if (fabsf(__fmul_rn(c, C.inv_h)) < 1.0f) return SG_SUR_FALLBACK;
     const float c2 = __fmul_rn(2.0f, c);
     float a = __fadd_rn(__fsub_rn(tile[e0 + 1], c2), tile[e0 - 1]);
-    a = __fadd_rn(a, __fadd_rn(__fsub_rn(tile[e0 + 6], c2), tile[e0 - 6]));
-    a = __fadd_rn(a, __fadd_rn(__fsub_rn(tile[e0 + 36], c2), tile[e0 - 36]));
+    a = __fadd_rn(a, __fadd_rn(__fsub_rn(tile[e0 + TILE_Y], c2), tile[e0 - TILE_Y]));
+    a = __fadd_rn(a, __fadd_rn(__fsub_rn(tile[e0 + TILE_Z], c2), tile[e0 - TILE_Z]));
     const float kap = __fmul_rn(a, C.inv_h2);
     if (__fmul_rn(fabsf(kap), C.h) > C.kappa_h_max) return SG_SUR_FALLBACK;
     return SG_SUR_NETWORK;
@@ -452,10 +452,11 @@ constexpr int SU_WARPS = SU_THREADS / 32;
 // dynamic shared memory: weights | phi tiles | H tiles | queue rows | queue ids (hidden activations stay in
 // registers, see forward_tile)
 constexpr int SU_OFF_PHI = MLP_PACK_BYTES;
-constexpr int SU_OFF_H = SU_OFF_PHI + SU_PK * 216 * 4;
-constexpr int SU_OFF_QX = SU_OFF_H + SU_PK * 216 * 4;
+constexpr int SU_OFF_H = SU_OFF_PHI + SU_PK * TILE_N * 4;
+constexpr int SU_OFF_QX = SU_OFF_H + SU_PK * TILE_N * 4;
 constexpr int SU_OFF_QI = SU_OFF_QX + SU_QROWS * SX * 2;
 constexpr int SU_BYTES = SU_OFF_QI + SU_QROWS * 8;
+static_assert(SU_OFF_H % 16 == 0 && SU_OFF_QX % 16 == 0 && SU_OFF_QI % 16 == 0, "16-byte aligned regions");
 
 // Stage the phi tile (and optionally the Heaviside tile) of package p.
 __device__ __forceinline__ void stage_tile(const int* nb27, const float* __restrict__ phi, float inv_eps, int d,
@@ -505,11 +506,11 @@ __global__ void __launch_bounds__(SU_THREADS) k_sur_integrals(const int32_t* __r
         if (threadIdx.x == 0) s_qn = 0;
         if (valid && d < NB) s_nb[lp][d] = __ldg(nbr + p * NB + d);
         __syncthreads();
-        if (valid) stage_tile(s_nb[lp], phi, inv_eps, d, s_phi + lp * 216, s_H + lp * 216);
+        if (valid) stage_tile(s_nb[lp], phi, inv_eps, d, s_phi + lp * TILE_N, s_H + lp * TILE_N);
         __syncthreads();
         if (valid) {
             float v[MLP_IN];
-            const int cls = sur_classify(s_phi + lp * 216, d, C, v);
+            const int cls = sur_classify(s_phi + lp * TILE_N, d, C, v);
             atomicAdd(&s_cnt[cls], 1u);
             const int64_t at = p * PKG3 + d;
             if (cls == SG_SUR_NETWORK) {
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(SU_THREADS) k_sur_integrals(const int32_t* __r
                 s_qi[q] = at;
             } else if (cls == SG_SUR_FALLBACK) {
                 float w, ax, ay, az;
-                integrals_point(s_H + lp * 216, d, K, w, ax, ay, az);
+                integrals_point(s_H + lp * TILE_N, d, K, w, ax, ay, az);
                 W[at] = w;
                 gx[at] = ax;
                 gy[at] = ay;
@@ -560,7 +561,7 @@ __global__ void __launch_bounds__(SU_THREADS) k_sur_classify(const int32_t* __re
                                                              const float* __restrict__ phi, int64_t P, SurConst C,
                                                              uint8_t* __restrict__ cls) {
     __shared__ int s_nb[SU_PK][NB];
-    __shared__ float s_phi[SU_PK][216];
+    __shared__ float s_phi[SU_PK][TILE_N];
     const int lp = threadIdx.x >> 6, d = threadIdx.x & 63;
     const int64_t p = (int64_t)blockIdx.x * SU_PK + lp;
     const bool act = p >= 2 && p < P;
@@ -594,7 +595,7 @@ __global__ void __launch_bounds__(SU_THREADS) k_sur_samples(const int32_t* __res
                                                             const float* __restrict__ gy, const float* __restrict__ gz,
                                                             __nv_bfloat16* __restrict__ xo, float* __restrict__ to) {
     __shared__ int s_nb[SU_PK][NB];
-    __shared__ float s_phi[SU_PK][216];
+    __shared__ float s_phi[SU_PK][TILE_N];
     __shared__ unsigned s_ball[SU_PK][2];
     const int lp = threadIdx.x >> 6, d = threadIdx.x & 63, lane = threadIdx.x & 31;
     const int64_t p = (int64_t)blockIdx.x * SU_PK + lp;

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_kernel_integrals(const int32_t* 
                                                                   float* __restrict__ gz, int64_t P, KernelCoef K,
                                                                   float inv_eps) {
     __shared__ int s_nb[IN_PKGS][NB];
-    __shared__ __align__(16) float s_H[IN_PKGS][216];  // 6^3 tile: package plus a one-point halo
+    __shared__ float s_H[IN_PKGS][TILE_N];  // 6^3 tile: package plus a one-point halo
     __shared__ unsigned s_sat[IN_PKGS];
     const int64_t p0 = 2 + (int64_t)blockIdx.x * IN_PKGS;
     const int n_pk = (int)min((int64_t)IN_PKGS, P - p0);
