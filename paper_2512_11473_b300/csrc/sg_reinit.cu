@@ -23,13 +23,17 @@ __global__ void __launch_bounds__(SW_THREADS) k_reinit_s0(const float* __restric
 }
 
 __global__ void __launch_bounds__(ROW_THREADS, 8) k_reinit_step(const int32_t* __restrict__ faces,
-                                                              const float* __restrict__ s0,
-                                                              const float* __restrict__ phi_in,
+                                                              const float* s0, const float* phi_in,
                                                               float* __restrict__ phi_out, int64_t P, float cfl,
                                                               float dt, int reverse) {
+    // Sweeps are launched as programmatic dependents of the previous sweep:
+    // wait until it has completed (its phi is our input, and we overwrite its
+    // input), then let the next sweep's CTAs launch as this one drains.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const RowSlot s = row_slot_dir(P, reverse);
-    const float4 sg = s.valid ? __ldg(reinterpret_cast<const float4*>(s0) + s.q4) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const Rows w = load_rows(phi_in, faces, s);
+    const float4 sg = s.valid ? __ldca(reinterpret_cast<const float4*>(s0) + s.q4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const Rows w = load_rows_t<true>(phi_in, faces, s);
     if (!s.valid) return;
     reinterpret_cast<float4*>(phi_out)[s.q4] = reinit_row(w, sg, cfl, dt);
 }
@@ -48,10 +52,19 @@ cudaError_t launch_reinit_step(const GridF& G, const int32_t* faces, const float
                                float* phi_out, float dt, int64_t P, int reverse, cudaStream_t s) {
     if (P <= 2) return cudaSuccess;
     // dt sqrt(G) = (dt / h) sqrt(h^2 G) and dt / h is the CFL number
-    k_reinit_step<<<row_blocks(P), ROW_THREADS, 0, s>>>(faces, s0, phi_in, phi_out, P, (float)(dt / G.h_d), dt,
-                                                        reverse);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(row_blocks(P));
+    cfg.blockDim = dim3(ROW_THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_reinit_step, faces, s0, phi_in, phi_out, P,
+                                             (float)(dt / G.h_d), dt, reverse);
     note_launch();
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace sg

@@ -74,10 +74,18 @@ __device__ __forceinline__ RowSlot make_slot(int64_t p, bool valid) {
 // half-warp reads the whole package) or, on its boundary, from the face
 // neighbour; each lane also takes one value from the -x and +x packages.
 // Lanes of an invalid package get zeros.
-__device__ __forceinline__ Rows load_rows(const float* __restrict__ f, const int32_t* __restrict__ faces,
-                                          const RowSlot& s) {
+// Loads of field values: read-only for the whole kernel (the non-coherent
+// path), or written by a grid this kernel was launched to depend on (plain
+// loads, visible once the dependency wait has returned).
+template <bool Dependent>
+__device__ __forceinline__ float4 ld_f4(const float4* p) { return Dependent ? __ldca(p) : __ldg(p); }
+template <bool Dependent>
+__device__ __forceinline__ float ld_f1(const float* p) { return Dependent ? __ldca(p) : __ldg(p); }
+
+template <bool Dependent>
+__device__ __forceinline__ Rows load_rows_t(const float* f, const int32_t* __restrict__ faces, const RowSlot& s) {
     const int j = s.r & 3, k = s.r >> 2;
-    const float4* __restrict__ f4 = reinterpret_cast<const float4*>(f);
+    const float4* f4 = reinterpret_cast<const float4*>(f);
     Rows w;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     if (!s.valid) {
@@ -88,14 +96,19 @@ __device__ __forceinline__ Rows load_rows(const float* __restrict__ f, const int
     const int4 fa = __ldg(reinterpret_cast<const int4*>(faces + s.p * 8));
     const int2 fb = __ldg(reinterpret_cast<const int2*>(faces + s.p * 8 + 4));
     const int q = s.q4;
-    w.c = __ldg(f4 + q);
-    w.xm = __ldg(reinterpret_cast<const float*>(f4 + (fa.x * 16 + s.r)) + 3);
-    w.xp = __ldg(reinterpret_cast<const float*>(f4 + (fa.y * 16 + s.r)));
-    w.ym = __ldg(f4 + (j > 0 ? q - 1 : fa.z * 16 + s.r + 3));
-    w.yp = __ldg(f4 + (j < 3 ? q + 1 : fa.w * 16 + s.r - 3));
-    w.zm = __ldg(f4 + (k > 0 ? q - 4 : fb.x * 16 + s.r + 12));
-    w.zp = __ldg(f4 + (k < 3 ? q + 4 : fb.y * 16 + s.r - 12));
+    w.c = ld_f4<Dependent>(f4 + q);
+    w.xm = ld_f1<Dependent>(reinterpret_cast<const float*>(f4 + (fa.x * 16 + s.r)) + 3);
+    w.xp = ld_f1<Dependent>(reinterpret_cast<const float*>(f4 + (fa.y * 16 + s.r)));
+    w.ym = ld_f4<Dependent>(f4 + (j > 0 ? q - 1 : fa.z * 16 + s.r + 3));
+    w.yp = ld_f4<Dependent>(f4 + (j < 3 ? q + 1 : fa.w * 16 + s.r - 3));
+    w.zm = ld_f4<Dependent>(f4 + (k > 0 ? q - 4 : fb.x * 16 + s.r + 12));
+    w.zp = ld_f4<Dependent>(f4 + (k < 3 ? q + 4 : fb.y * 16 + s.r - 12));
     return w;
+}
+
+__device__ __forceinline__ Rows load_rows(const float* __restrict__ f, const int32_t* __restrict__ faces,
+                                          const RowSlot& s) {
+    return load_rows_t<false>(f, faces, s);
 }
 
 __device__ __forceinline__ float row_xm(const Rows& w, int i) { return i > 0 ? get(w.c, i - 1) : w.xm; }
