@@ -261,47 +261,55 @@ struct RelaxBody {
 };
 
 constexpr int RX_THREADS = 256;  // particles per tile
+constexpr int RX_TILES = 16;     // consecutive tiles a CTA walks
 
 // One relaxation step for every particle: probe (phi, g and, with NF = 8,
 // the integrals) and move by -step h clip(phi / h, -1, 1) n.  A CTA owns one
 // tile of RX_THREADS consecutive particles of one body; its body is the last
 // whose first tile is at most blockIdx.x.
 template <int NF>
+// A CTA walks RX_TILES consecutive 256-particle tiles (of one body or of
+// consecutive bodies), so that a warp's successive particles are near each
+// other in the Morton walk and hit the packages L1 holds.
 __global__ void __launch_bounds__(RX_THREADS) k_batch_relax(const RelaxBody* __restrict__ rb, int nbody,
-                                                            const int32_t* __restrict__ cells,
+                                                            int64_t tiles, const int32_t* __restrict__ cells,
                                                             const int32_t* __restrict__ nbr,
                                                             const float* __restrict__ tab,
                                                             float* __restrict__ x, float* __restrict__ y,
                                                             float* __restrict__ z, ProbeOut out) {
+    const int64_t t0 = (int64_t)blockIdx.x * RX_TILES, t1 = min(tiles, t0 + RX_TILES);
     int lo = 0, hi = nbody - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(&rb[mid].tile0) <= (int64_t)blockIdx.x)
+        if (__ldg(&rb[mid].tile0) <= t0)
             lo = mid;
         else
             hi = mid - 1;
     }
-    const RelaxBody B = rb[lo];
-    const int64_t q = B.first + ((int64_t)blockIdx.x - B.tile0) * RX_THREADS + threadIdx.x;
-    if (q >= B.end) return;
-    const float pos[3] = {x[q], y[q], z[q]};
-    const ProbeAt A = probe_locate(B.lo, B.inv_h, B.dims, cells + B.cells, B.far_out, pos);
-    float acc[8];
-    probe_interp_packed<NF>(nbr, tab, A, acc);
-    const float inv = probe_inv_norm(acc);
-    const float n0 = acc[1] * inv, n1 = acc[2] * inv, n2 = acc[3] * inv;
-    const float m = B.step_h * fminf(fmaxf(acc[0] * B.inv_h, -1.0f), 1.0f);
-    x[q] = fmaf(-m, n0, pos[0]);
-    y[q] = fmaf(-m, n1, pos[1]);
-    z[q] = fmaf(-m, n2, pos[2]);
-    if (out.o[0]) out.o[0][q] = acc[0];
-    if (out.o[1]) out.o[1][q] = n0;
-    if (out.o[2]) out.o[2][q] = n1;
-    if (out.o[3]) out.o[3][q] = n2;
-    if (NF == 8) {
+    for (int64_t t = t0; t < t1; ++t) {
+        while (lo + 1 < nbody && __ldg(&rb[lo + 1].tile0) <= t) ++lo;  // the body of tile t
+        const RelaxBody B = rb[lo];
+        const int64_t q = B.first + (t - B.tile0) * RX_THREADS + threadIdx.x;
+        if (q >= B.end) continue;
+        const float pos[3] = {x[q], y[q], z[q]};
+        const ProbeAt A = probe_locate(B.lo, B.inv_h, B.dims, cells + B.cells, B.far_out, pos);
+        float acc[8];
+        probe_interp_packed<NF>(nbr, tab, A, acc);
+        const float inv = probe_inv_norm(acc);
+        const float n0 = acc[1] * inv, n1 = acc[2] * inv, n2 = acc[3] * inv;
+        const float m = B.step_h * fminf(fmaxf(acc[0] * B.inv_h, -1.0f), 1.0f);
+        x[q] = fmaf(-m, n0, pos[0]);
+        y[q] = fmaf(-m, n1, pos[1]);
+        z[q] = fmaf(-m, n2, pos[2]);
+        if (out.o[0]) out.o[0][q] = acc[0];
+        if (out.o[1]) out.o[1][q] = n0;
+        if (out.o[2]) out.o[2][q] = n1;
+        if (out.o[3]) out.o[3][q] = n2;
+        if (NF == 8) {
 #pragma unroll
-        for (int f = 4; f < 8; ++f)
-            if (out.o[f]) out.o[f][q] = acc[f];
+            for (int f = 4; f < 8; ++f)
+                if (out.o[f]) out.o[f][q] = acc[f];
+        }
     }
 }
 
@@ -468,11 +476,12 @@ cudaError_t record_relax(sg_batch* b, const sg_relax& r, int64_t tiles, cudaStre
     if (r.steps < 1 || tiles < 1) return cudaSuccess;
     cudaError_t e = launch_pack_probe(F, tab, b->P * PKG3, s);
     if (e != cudaSuccess) return e;
+    const unsigned ctas = (unsigned)((tiles + RX_TILES - 1) / RX_TILES);
     for (int k = 0; k < r.steps; ++k) {
         if (integ)
-            k_batch_relax<8><<<(unsigned)tiles, RX_THREADS, 0, s>>>(rb, b->n, cells, nbr, tab, r.x, r.y, r.z, o);
+            k_batch_relax<8><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, o);
         else
-            k_batch_relax<4><<<(unsigned)tiles, RX_THREADS, 0, s>>>(rb, b->n, cells, nbr, tab, r.x, r.y, r.z, o);
+            k_batch_relax<4><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, o);
         note_launch();
     }
     return cudaGetLastError();
