@@ -134,12 +134,20 @@ ShapeFF shape_ff(const sg_shape* s) {
     return S;
 }
 
+bool field_fresh(const sg_grid* g, int f) {
+    const Buf& b = g->field[f];
+    return !b.p || b.bytes < (size_t)g->P * PKG3 * sizeof(float) || g->stale[f];
+}
+
+// A field of the current tagging; a buffer that is new, or kept from an
+// earlier tagging, is zero-filled when the caller reads before writing.
 float* field_ptr(sg_grid* g, int f, bool zero_new) {
     const size_t bytes = (size_t)g->P * PKG3 * sizeof(float);
+    const bool fresh = field_fresh(g, f);
     Buf& b = g->field[f];
-    if (b.p && b.bytes >= bytes) return (float*)b.p;
     if (!ensure(g, b, bytes)) return nullptr;
-    if (zero_new && cudaMemsetAsync(b.p, 0, bytes, g->stream) != cudaSuccess) return nullptr;
+    if (fresh && zero_new && cudaMemsetAsync(b.p, 0, bytes, g->stream) != cudaSuccess) return nullptr;
+    g->stale[f] = false;
     return (float*)b.p;
 }
 
@@ -268,9 +276,10 @@ static sg_status tag_common(sg_grid* g, Flags flags, int64_t* n_packages) {
     SG_CUDA(g, cudaStreamSynchronize(g->stream), "tag sync");
     const int64_t P = 2 + (int64_t)*(uint32_t*)g->host_pin.p;
     if (P >= (1LL << 31) / NB) return fail(g, SG_ERR_CAPACITY, "sg_tag_allocate: too many packages");
-    // the package arrays and every field are sized by P: start afresh
-    for (int f = 0; f < SG_N_FLOAT_FIELDS; ++f) grid_free(g, g->field[f]);
-    grid_free(g, g->phi_tmp);
+    // every field is sized by P and its values belong to the old tagging: the
+    // buffers are kept (they grow when P does) and treated as new, so that a
+    // re-tagged grid allocates nothing once its buffers are large enough
+    for (int f = 0; f < SG_N_FLOAT_FIELDS; ++f) g->stale[f] = true;
     if (!ensure(g, g->pkg_cell, (size_t)P * 4) || !ensure(g, g->pkg_type, (size_t)P) ||
         !ensure(g, g->nbr, (size_t)P * NB * 4) || !ensure(g, g->faces, (size_t)P * 8 * 4)) {
         g->state = 0;
@@ -539,7 +548,7 @@ sg_status sg_probe(sg_grid* g, int64_t n, const float* x, const float* y, const 
     const int src[8] = {SG_FIELD_PHI, SG_FIELD_GX, SG_FIELD_GY, SG_FIELD_GZ,
                         SG_FIELD_W,   SG_FIELD_GWX, SG_FIELD_GWY, SG_FIELD_GWZ};
     for (int f = 0; f < 8; ++f) {
-        bool fresh = !g->field[src[f]].p;
+        const bool fresh = field_fresh(g, src[f]);
         F.f[f] = field_ptr(g, src[f], true);
         if (!F.f[f]) return fail(g, SG_ERR_OOM, "sg_probe: out of memory");
         if (fresh && src[f] == SG_FIELD_W) SG_CUDA(g, launch_set_far((float*)F.f[f], 1.0f, 0.0f, g->stream), "probe W far");
@@ -571,7 +580,7 @@ sg_status sg_get_field(sg_grid* g, int32_t field, void** dev_ptr, int64_t* n_ele
     DeviceGuard dg(g->device);
     if (field >= 0 && field < SG_N_FLOAT_FIELDS) {
         if (g->state < 1) return fail(g, SG_ERR_STATE, "sg_get_field: grid not tagged");
-        bool fresh = !g->field[field].p;
+        const bool fresh = field_fresh(g, field);
         float* p = field_ptr(g, field, true);
         if (!p) return fail(g, SG_ERR_OOM, "sg_get_field: out of memory");
         if (fresh && field == SG_FIELD_W) SG_CUDA(g, launch_set_far(p, 1.0f, 0.0f, g->stream), "field W far");

@@ -58,6 +58,7 @@ struct sg_grid {
     sg::Buf cell_pkg, cell_type, pkg_cell, pkg_type, nbr;
     sg::Buf faces;  // int32 [P][8]: the six face neighbours (-x,+x,-y,+y,-z,+z), then 2 zeros
     sg::Buf field[SG_N_FLOAT_FIELDS];
+    bool stale[SG_N_FLOAT_FIELDS] = {};  // buffer kept from an earlier tagging: treated as new
     sg::Buf phi_tmp;
     sg::Buf err;       // int32 sticky device error word
     sg::Buf scratch;   // reusable temporary space (scans, sort)
@@ -78,6 +79,7 @@ bool ensure(sg_grid* g, Buf& b, size_t bytes);  // (re)allocates when too small
 sg_status fail(sg_grid* g, sg_status st, const std::string& msg);
 sg_status cuda_fail(sg_grid* g, cudaError_t e, const char* where);
 float* field_ptr(sg_grid* g, int f, bool zero_new);
+bool field_fresh(const sg_grid* g, int f);  // field_ptr would hand out a new (or stale) buffer
 GridF grid_f(const sg_grid* g);
 GridFF grid_ff(const sg_grid* g);
 ShapeFF shape_ff(const sg_shape* s);

@@ -788,7 +788,7 @@ sg_status sg_surrogate_samples(sg_grid* g, uint64_t seed, float keep, int64_t ca
     if (!g || !count || cap < 0 || !(keep >= 0.0f && keep <= 1.0f) || (cap > 0 && (!x_bf16 || !t)))
         return SG_ERR_INVALID;
     if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_surrogate_samples: phi not initialised");
-    if (!g->field[SG_FIELD_W].p) return fail(g, SG_ERR_STATE, "sg_surrogate_samples: no exact integrals");
+    if (field_fresh(g, SG_FIELD_W)) return fail(g, SG_ERR_STATE, "sg_surrogate_samples: no exact integrals");
     const int64_t P = g->P;
     const size_t cb = ((size_t)P * 4 + 255) & ~(size_t)255;
     if (!ensure(g, g->scratch, 2 * cb + scan_scratch_bytes(P) + 256))

@@ -371,6 +371,40 @@ def test_retag_matches_fresh(sg):
     assert np.max(np.abs(H(g.field("phi")).astype(np.float64) - O.phi)) <= 1e-4 * spec.h
 
 
+@pytest.mark.parametrize("order", ["larger_first", "smaller_first"])
+def test_retag_keeps_no_old_values(sg, order):
+    """A re-tagged grid keeps its buffers but none of their values: fields not
+    yet computed read as a fresh grid's (zeros, W = 1 / 0 in the far
+    packages), and every computed field equals a fresh grid's bit for bit."""
+    big, spec = CASES["torus_rot"]
+    small = si.sphere(0.3)
+    first, second = (big, small) if order == "larger_first" else (small, big)
+    g = sg.Grid(spec)
+    g.tag_allocate(first)
+    g.init_sdf(first)
+    g.gradient()
+    g.reinit(3, 0.5)
+    g.kernel_integrals()
+    g.probe(*(torch.zeros(10, device="cuda") for _ in range(3)))
+    g.tag_allocate(second)
+    g.init_sdf(second)
+    f = sg.Grid(spec)
+    f.tag_allocate(second)
+    f.init_sdf(second)
+    for name in ("gx", "gy", "gz", "W", "Gx", "Gy", "Gz"):
+        assert torch.equal(g.field(name), f.field(name)), name
+    w = H(g.field("W"))
+    assert np.all(w[0] == 1.0) and np.all(w[1] == 0.0) and np.all(w[2:] == 0.0)
+    for grid in (g, f):
+        grid.gradient()
+        grid.reinit(3, 0.5)
+        grid.kernel_integrals()
+    for name in ("phi", "gx", "gy", "gz", "W", "Gx", "Gy", "Gz"):
+        assert torch.equal(g.field(name), f.field(name)), name
+    g.sync()
+    f.sync()
+
+
 def test_deterministic(sg):
     shape, spec = CASES["box_rot"]
     outs = []
