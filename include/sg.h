@@ -153,7 +153,9 @@ SG_API sg_status sg_destroy(sg_grid *g);
  * neighbours is core; ids follow the cell index.  Fills cell_pkg, pkg_cell,
  * pkg_type and nbr and writes P (including the 2 far packages) to
  * *n_packages.  Synchronises the stream (P sizes the package arrays).
- * May be called again to re-tag; previous field contents are discarded. */
+ * May be called again to re-tag; previous field contents are discarded (the
+ * field buffers are kept and reused when large enough, so a grid re-tagged
+ * with a package count it has seen before allocates nothing). */
 SG_API sg_status sg_tag_allocate(sg_grid *g, const sg_shape *shape, int64_t *n_packages);
 
 /* Multi-resolution tagging (Sec. "Multi-resolution Level-set", and step 1
@@ -465,8 +467,8 @@ SG_API sg_status sg_morton_order_noalloc(const sg_grid_desc *desc, int64_t n, co
                                          const float *z, uint64_t *keys, int32_t *order, void *stream);
 
 /* Borrow the device pointer and element count of a field; valid until the
- * grid is destroyed or re-tagged.  A float field that was never written is
- * allocated and zeroed on first request. */
+ * grid is destroyed or re-tagged.  A float field not written since the last
+ * tagging reads as zeros on first request (W: 1 in the inside far package). */
 SG_API sg_status sg_get_field(sg_grid *g, int32_t field, void **dev_ptr, int64_t *n_elems);
 
 /* Number of packages P (including the far packages); 0 before tagging. */
