@@ -8,6 +8,7 @@
 #include <mutex>
 
 #include "sg_probe.cuh"
+#include <algorithm>
 
 namespace sg {
 namespace {
@@ -377,7 +378,10 @@ cudaError_t launch_probe(const GridF& G, const int32_t* cell_pkg, const int32_t*
                          int64_t n, const float* x, const float* y, const float* z, const int32_t* order,
                          const int* unsorted, const ProbeOut& out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_probe<<<blocks_for(n, PR_THREADS), PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, unsorted, out);
+    // up to 148 x 128 CTAs, each a contiguous stretch of about 2.6k particles
+    // at 50M (9,472 CTAs measured 2% slower on the torus)
+    const int64_t ctas = std::min<int64_t>((n + PR_THREADS - 1) / PR_THREADS, 148 * 128);
+    k_probe<<<(unsigned)ctas, PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, unsorted, out);
     note_launch();
     return cudaGetLastError();
 }
