@@ -479,15 +479,17 @@ sg_status sg_reinit(sg_grid* g, int32_t iterations, float cfl) {
     const int32_t* faces = (const int32_t*)g->faces.p;
     SG_CUDA(g, launch_set_far(s0, -1.0f, 1.0f, g->stream), "reinit far");
     SG_CUDA(g, launch_set_far(tmp, -(float)g->F, (float)g->F, g->stream), "reinit far");
-    SG_CUDA(g, launch_reinit_s0(G, phi, s0, g->P, g->stream), "reinit s0");
+    // the first sweep forms S0 from phi at call entry; with no sweep a pass of its own does
+    if (iterations == 0) SG_CUDA(g, launch_reinit_s0(G, phi, s0, g->P, g->stream), "reinit s0");
     float* a = phi;
     float* b = tmp;
-    // sweeps alternate their direction, the first against the S0 pass, so
-    // that each starts on the packages whose phi and S0 the previous pass
-    // left in L2 (the results do not depend on the order: a sweep reads only
-    // the previous iterate)
+    // sweeps alternate their direction, the first against the pass before the
+    // call, so that each starts on the packages whose phi and S0 the previous
+    // pass left in L2 (the results do not depend on the order: a sweep reads
+    // only the previous iterate)
     for (int32_t it = 0; it < iterations; ++it) {
-        SG_CUDA(g, launch_reinit_step(G, faces, s0, a, b, dt, g->P, (it & 1) == 0, g->stream), "reinit step");
+        SG_CUDA(g, launch_reinit_step(G, faces, s0, a, b, dt, g->P, (it & 1) == 0, it == 0, g->stream),
+                "reinit step");
         float* t = a;
         a = b;
         b = t;

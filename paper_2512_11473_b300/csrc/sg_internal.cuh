@@ -142,9 +142,10 @@ cudaError_t launch_gradient(const GridF& G, const int32_t* faces, const float* p
 cudaError_t launch_laplacian(const GridF& G, const int32_t* faces, const float* phi, float* lap, int64_t P,
                              cudaStream_t s);
 cudaError_t launch_reinit_s0(const GridF& G, const float* phi, float* s0, int64_t P, cudaStream_t s);
-// One Jacobi sweep; `reverse` walks the packages from the last CTA down.
-cudaError_t launch_reinit_step(const GridF& G, const int32_t* faces, const float* s0, const float* phi_in,
-                               float* phi_out, float dt, int64_t P, int reverse, cudaStream_t s);
+// One Jacobi sweep; `reverse` walks the packages from the last CTA down;
+// `first` forms S0 from phi_in and stores it instead of reading it.
+cudaError_t launch_reinit_step(const GridF& G, const int32_t* faces, float* s0, const float* phi_in,
+                               float* phi_out, float dt, int64_t P, int reverse, int first, cudaStream_t s);
 cudaError_t launch_copy_active(const float* src, float* dst, int64_t P, cudaStream_t s);
 // phi <- phi + delta on the active packages
 cudaError_t launch_sequential(float* phi, float delta, int64_t P, cudaStream_t s);
