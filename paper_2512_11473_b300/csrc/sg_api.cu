@@ -414,7 +414,9 @@ sg_status sg_gradient(sg_grid* g) {
     float* o[3];
     for (int a = 0; a < 3; ++a)
         if (!(o[a] = field_ptr(g, SG_FIELD_GX + a, false))) return fail(g, SG_ERR_OOM, "sg_gradient: out of memory");
-    for (int a = 0; a < 3; ++a) SG_CUDA(g, launch_set_far(o[a], 0.0f, 0.0f, g->stream), "gradient far");
+    // the gradient kernel writes the far packages itself; with none active it is not launched
+    if (g->P <= 2)
+        for (int a = 0; a < 3; ++a) SG_CUDA(g, launch_set_far(o[a], 0.0f, 0.0f, g->stream), "gradient far");
     SG_CUDA(g, launch_gradient(grid_f(g), (const int32_t*)g->faces.p, (const float*)g->field[SG_FIELD_PHI].p, o[0], o[1],
                                o[2], g->P, g->stream),
             "gradient");
@@ -477,10 +479,14 @@ sg_status sg_reinit(sg_grid* g, int32_t iterations, float cfl) {
     const GridF G = grid_f(g);
     const float dt = (float)((double)cfl * g->desc.h);
     const int32_t* faces = (const int32_t*)g->faces.p;
-    SG_CUDA(g, launch_set_far(s0, -1.0f, 1.0f, g->stream), "reinit far");
-    SG_CUDA(g, launch_set_far(tmp, -(float)g->F, (float)g->F, g->stream), "reinit far");
-    // the first sweep forms S0 from phi at call entry; with no sweep a pass of its own does
-    if (iterations == 0) SG_CUDA(g, launch_reinit_s0(G, phi, s0, g->P, g->stream), "reinit s0");
+    // the first sweep forms S0 from phi at call entry and writes the far
+    // packages of S0 and of the second buffer; with no sweep (or no active
+    // package) passes of their own do
+    if (iterations == 0 || g->P <= 2) {
+        SG_CUDA(g, launch_set_far(s0, -1.0f, 1.0f, g->stream), "reinit far");
+        SG_CUDA(g, launch_set_far(tmp, -(float)g->F, (float)g->F, g->stream), "reinit far");
+        SG_CUDA(g, launch_reinit_s0(G, phi, s0, g->P, g->stream), "reinit s0");
+    }
     float* a = phi;
     float* b = tmp;
     // sweeps alternate their direction, the first against the pass before the

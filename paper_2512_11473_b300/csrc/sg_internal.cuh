@@ -69,6 +69,13 @@ struct sg_grid {
 
 namespace sg {
 
+// The two far packages of a field (far- then far+, 64 points each), written
+// by CTA 0 of the kernel that computes the field (blocks of at least 128
+// threads), so that no launch of its own is needed.
+__device__ __forceinline__ void write_far(float* f, float v_in, float v_out) {
+    if (blockIdx.x == 0 && threadIdx.x < 2 * PKG3) f[threadIdx.x] = threadIdx.x < PKG3 ? v_in : v_out;
+}
+
 // process-wide count of kernels launched by the library (sg_api.cu)
 void note_launch(int n = 1);
 

@@ -35,6 +35,10 @@ __global__ void __launch_bounds__(ROW_THREADS, 8) k_reinit_step(const int32_t* _
     // input), then let the next sweep's CTAs launch as this one drains.
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (FIRST) {  // far packages of S0 (the sign) and of the output (phi's far values)
+        write_far(s0, -1.0f, 1.0f);
+        if (blockIdx.x == 0 && threadIdx.x < 2 * PKG3) phi_out[threadIdx.x] = __ldca(phi_in + threadIdx.x);
+    }
     const RowSlot s = row_slot_dir(P, reverse);
     const Rows w = load_rows_t<true>(phi_in, faces, s);
     float4 sg = make_float4(0.f, 0.f, 0.f, 0.f);

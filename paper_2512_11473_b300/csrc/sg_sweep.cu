@@ -22,6 +22,9 @@ __global__ void __launch_bounds__(SW_THREADS) k_set_far(float* f, float v_in, fl
 __global__ void __launch_bounds__(ROW_THREADS) k_gradient(const int32_t* __restrict__ faces, const float* __restrict__ phi,
                                                            float* __restrict__ gx, float* __restrict__ gy,
                                                            float* __restrict__ gz, int64_t P, float inv2h) {
+    write_far(gx, 0.0f, 0.0f);
+    write_far(gy, 0.0f, 0.0f);
+    write_far(gz, 0.0f, 0.0f);
     const RowSlot s = row_slot(P);
     const Rows w = load_rows(phi, faces, s);
     if (!s.valid) return;
@@ -73,6 +76,10 @@ __global__ void __launch_bounds__(SW_THREADS) k_kernel_integrals(const int32_t* 
     __shared__ int s_nb[IN_PKGS][NB];
     __shared__ float s_H[IN_PKGS][TILE_N];  // 6^3 tile: package plus a one-point halo
     __shared__ unsigned s_sat[IN_PKGS];
+    write_far(W, 1.0f, 0.0f);
+    write_far(gx, 0.0f, 0.0f);
+    write_far(gy, 0.0f, 0.0f);
+    write_far(gz, 0.0f, 0.0f);
     const int64_t p0 = 2 + (int64_t)blockIdx.x * IN_PKGS;
     const int n_pk = (int)min((int64_t)IN_PKGS, P - p0);
     for (int e = threadIdx.x; e < IN_PKGS * NB; e += SW_THREADS) {
@@ -223,10 +230,12 @@ cudaError_t launch_copy_active(const float* src, float* dst, int64_t P, cudaStre
 cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const float* phi, float* W, float* gx,
                                     float* gy, float* gz, int64_t P, double R, double eps, cudaStream_t s) {
     cudaError_t e;
-    if ((e = launch_set_far(W, 1.0f, 0.0f, s)) != cudaSuccess) return e;
-    if ((e = launch_set_far(gx, 0.0f, 0.0f, s)) != cudaSuccess) return e;
-    if ((e = launch_set_far(gy, 0.0f, 0.0f, s)) != cudaSuccess) return e;
-    if ((e = launch_set_far(gz, 0.0f, 0.0f, s)) != cudaSuccess) return e;
+    if (P <= 2 || R > 2.0) {  // the narrow kernel writes the far packages itself
+        if ((e = launch_set_far(W, 1.0f, 0.0f, s)) != cudaSuccess) return e;
+        if ((e = launch_set_far(gx, 0.0f, 0.0f, s)) != cudaSuccess) return e;
+        if ((e = launch_set_far(gy, 0.0f, 0.0f, s)) != cudaSuccess) return e;
+        if ((e = launch_set_far(gz, 0.0f, 0.0f, s)) != cudaSuccess) return e;
+    }
     if (P <= 2) return cudaSuccess;
     if (R > 2.0)
         k_kernel_integrals_wide<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(R),

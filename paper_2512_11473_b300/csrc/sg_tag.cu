@@ -323,7 +323,8 @@ __global__ void __launch_bounds__(TAG_THREADS) k_coord_table(GridFF G, ff* __res
 template <int K>
 __global__ void __launch_bounds__(TAG_THREADS, K == SHAPE_PRISM ? 4 : 8) k_init_sdf(GridFF G, ShapeFF S, const int32_t* __restrict__ pkg_cell,
                                                            const ff* __restrict__ tab, float* __restrict__ phi,
-                                                           int64_t P) {
+                                                           int64_t P, float F) {
+    write_far(phi, -F, F);
     const int64_t total = (P - 2) * PKG3;
     const int off[3] = {0, 4 * G.dims[0], 4 * (G.dims[0] + G.dims[1])};
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -454,17 +455,14 @@ cudaError_t launch_fill_faces(const int32_t* nbr, int32_t* faces, int64_t P, cud
 
 cudaError_t launch_init_sdf(const GridFF& G, const ShapeFF& S, const int32_t* pkg_cell, float* phi, float F,
                             int64_t P, void* table, cudaStream_t s) {
-    cudaError_t e = launch_set_far(phi, -F, F, s);
-    if (e != cudaSuccess) return e;
-    if (P > 2) {
-        const int n = 4 * (G.dims[0] + G.dims[1] + G.dims[2]);
-        k_coord_table<<<(n + TAG_THREADS - 1) / TAG_THREADS, TAG_THREADS, 0, s>>>(G, (ff*)table);
-        note_launch();
-        const ff* tab = (const ff*)table;
-        SG_SHAPE_DISPATCH(S.kind, (k_init_sdf<K><<<grid_for((P - 2) * PKG3, TAG_THREADS), TAG_THREADS, 0, s>>>(
-                                      G, S, pkg_cell, tab, phi, P)));
-        note_launch();
-    }
+    if (P <= 2) return launch_set_far(phi, -F, F, s);  // otherwise the init kernel writes the far packages
+    const int n = 4 * (G.dims[0] + G.dims[1] + G.dims[2]);
+    k_coord_table<<<(n + TAG_THREADS - 1) / TAG_THREADS, TAG_THREADS, 0, s>>>(G, (ff*)table);
+    note_launch();
+    const ff* tab = (const ff*)table;
+    SG_SHAPE_DISPATCH(S.kind, (k_init_sdf<K><<<grid_for((P - 2) * PKG3, TAG_THREADS), TAG_THREADS, 0, s>>>(
+                                  G, S, pkg_cell, tab, phi, P, F)));
+    note_launch();
     return cudaGetLastError();
 }
 
