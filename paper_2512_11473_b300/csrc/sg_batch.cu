@@ -120,8 +120,12 @@ __global__ void __launch_bounds__(BT) k_batch_gradient(const int32_t* __restrict
     }
 }
 
+// Reinit sweep over the global store: a work item is 16 * ppi packages, each
+// half-warp takes ppi of them, DEPTH at a time; a package's body constants
+// are read with its sign, ahead of the rows.  DEPTH 1 is bounded to 40
+// registers (6 CTAs per SM), which it fits without spills.
 template <int DEPTH>
-__global__ void __launch_bounds__(BT) k_batch_reinit(const int32_t* __restrict__ faces, const uint8_t* __restrict__ type,
+__global__ void __launch_bounds__(BT, DEPTH == 1 ? 6 : 1) k_batch_reinit(const int32_t* __restrict__ faces, const uint8_t* __restrict__ type,
                                                      const int32_t* __restrict__ body,
                                                      const BodyParams* __restrict__ prm, const float* __restrict__ s0,
                                                      const float* __restrict__ phi_in, float* __restrict__ phi_out,
@@ -135,10 +139,15 @@ __global__ void __launch_bounds__(BT) k_batch_reinit(const int32_t* __restrict__
             RowSlot sl[DEPTH];
             Rows w[DEPTH];
             float4 sg[DEPTH];
+            float cfl[DEPTH], dtv[DEPTH];
 #pragma unroll
             for (int d = 0; d < DEPTH; ++d) {
                 const int64_t p = item * per_item + (int64_t)(k + d) * BT_HW + (threadIdx.x >> 4);
-                sl[d] = make_slot(p, p < P && k + d < ppi && __ldg(type + (p < P ? p : 0)) >= 2);
+                const int64_t pc = p < P ? p : 0;
+                sl[d] = make_slot(p, p < P && k + d < ppi && __ldg(type + pc) >= 2);
+                const BodyParams* bp = prm + __ldg(body + pc);
+                cfl[d] = __ldg(&bp->cfl);
+                dtv[d] = __ldg(&bp->dt);
                 sg[d] = sl[d].valid ? __ldg(reinterpret_cast<const float4*>(s0) + sl[d].q4)
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
             }
@@ -147,8 +156,7 @@ __global__ void __launch_bounds__(BT) k_batch_reinit(const int32_t* __restrict__
 #pragma unroll
             for (int d = 0; d < DEPTH; ++d) {
                 if (!sl[d].valid) continue;
-                const BodyParams* bp = prm + __ldg(body + sl[d].p);
-                reinterpret_cast<float4*>(phi_out)[sl[d].q4] = reinit_row(w[d], sg[d], __ldg(&bp->cfl), __ldg(&bp->dt));
+                reinterpret_cast<float4*>(phi_out)[sl[d].q4] = reinit_row(w[d], sg[d], cfl[d], dtv[d]);
             }
         }
     }
