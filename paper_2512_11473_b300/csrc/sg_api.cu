@@ -318,9 +318,10 @@ static sg_status tag_common(sg_grid* g, Flags flags, int64_t* n_packages) {
                                    (int32_t*)g->cell_pkg.p, n, g->stream),
                 "ids renumber");
     }
-    SG_CUDA(g, launch_fill_nbr(G, (const int32_t*)g->cell_pkg.p, (const int32_t*)g->pkg_cell.p, (int32_t*)g->nbr.p,
-                               (int32_t*)g->faces.p, P, g->stream),
+    SG_CUDA(g, launch_fill_nbr(G, (const int32_t*)g->cell_pkg.p, (const int32_t*)g->pkg_cell.p, (int32_t*)g->nbr.p, P,
+                               g->stream),
             "fill nbr");
+    SG_CUDA(g, launch_fill_faces((const int32_t*)g->nbr.p, (int32_t*)g->faces.p, P, g->stream), "fill faces");
     g->state = 1;
     if (n_packages) *n_packages = P;
     return SG_OK;

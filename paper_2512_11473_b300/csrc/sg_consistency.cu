@@ -260,7 +260,8 @@ cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cel
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the neighbour and face tables name far packages by their cells
-    if ((e = launch_fill_nbr(G, cell_pkg, pkg_cell, nbr, faces, P, s)) != cudaSuccess) return e;
+    if ((e = launch_fill_nbr(G, cell_pkg, pkg_cell, nbr, P, s)) != cudaSuccess) return e;
+    if ((e = launch_fill_faces(nbr, faces, P, s)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(hcnt, cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return e;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;

@@ -123,10 +123,8 @@ cudaError_t launch_tag_inner(const GridFF& G, uint8_t* cell_type, const uint32_t
                              uint32_t* count, int64_t nc, cudaStream_t s);
 cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* act_bits, const uint32_t* prefix,
                                int32_t* cell_pkg, int32_t* pkg_cell, uint8_t* pkg_type, int64_t nc, cudaStream_t s);
-// The 27-entry neighbourhood table, and with faces != null the face table
-// in the same pass.
 cudaError_t launch_fill_nbr(const GridFF& G, const int32_t* cell_pkg, const int32_t* pkg_cell, int32_t* nbr,
-                            int32_t* faces, int64_t P, cudaStream_t s);
+                            int64_t P, cudaStream_t s);
 // Consistency (sign) correction of phi, cell_pkg, nbr and faces in place;
 // host-synchronising.  out: points flipped, far cells moved, point and cell
 // flood sweeps.

@@ -215,35 +215,24 @@ __global__ void __launch_bounds__(TAG_THREADS) k_tag_scatter(const uint8_t* __re
 }
 
 // Step 5: neighbourhood; outside the domain -> package 1; far packages self.
-// With faces != null the compact face table is written in the same pass:
-// faces[p][0..5] = the entries 12, 14, 10, 16, 4, 22 (-x, +x, -y, +y, -z,
-// +z), faces[p][6..7] = 0.
 __global__ void __launch_bounds__(TAG_THREADS) k_fill_nbr(GridFF G, const int32_t* __restrict__ cell_pkg,
                                                            const int32_t* __restrict__ pkg_cell,
-                                                           int32_t* __restrict__ nbr, int32_t* __restrict__ faces,
-                                                           int64_t P) {
+                                                           int32_t* __restrict__ nbr, int64_t P) {
     const int nx = G.dims[0], ny = G.dims[1], nz = G.dims[2];
     const int64_t total = P * NB;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         int64_t p = e / NB;
         int n = (int)(e - p * NB);
-        int32_t v;
         if (p < 2) {
-            v = (int32_t)p;
-        } else {
-            int64_t I, J, K;
-            cell_coords(pkg_cell[p], G.dims, I, J, K);
-            const int a = (int)I + (n % 3) - 1, b = (int)J + (n / 3) % 3 - 1, c = (int)K + n / 9 - 1;
-            const bool in = a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz;
-            v = in ? cell_pkg[a + nx * (b + ny * c)] : 1;
+            nbr[e] = (int32_t)p;
+            continue;
         }
-        nbr[e] = v;
-        if (faces) {
-            const int slot = n == 12 ? 0 : n == 14 ? 1 : n == 10 ? 2 : n == 16 ? 3 : n == 4 ? 4 : n == 22 ? 5 : -1;
-            if (slot >= 0) faces[p * 8 + slot] = v;
-            if (n < 2) faces[p * 8 + 6 + n] = 0;
-        }
+        int64_t I, J, K;
+        cell_coords(pkg_cell[p], G.dims, I, J, K);
+        const int a = (int)I + (n % 3) - 1, b = (int)J + (n / 3) % 3 - 1, c = (int)K + n / 9 - 1;
+        const bool in = a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz;
+        nbr[e] = in ? cell_pkg[a + nx * (b + ny * c)] : 1;
     }
 }
 
@@ -441,8 +430,8 @@ cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* act_bit
 }
 
 cudaError_t launch_fill_nbr(const GridFF& G, const int32_t* cell_pkg, const int32_t* pkg_cell, int32_t* nbr,
-                            int32_t* faces, int64_t P, cudaStream_t s) {
-    k_fill_nbr<<<grid_for(P * NB, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_pkg, pkg_cell, nbr, faces, P);
+                            int64_t P, cudaStream_t s) {
+    k_fill_nbr<<<grid_for(P * NB, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_pkg, pkg_cell, nbr, P);
     note_launch();
     return cudaGetLastError();
 }
