@@ -199,6 +199,28 @@ __device__ inline ff ff_triangle_sdf(ff px, ff py, const ShapeFF& s) {
     return inside ? ff_neg(dd) : dd;
 }
 
+// The torus and the prism split into a part of the local (x, y) alone, the
+// same for every point of a column along the local z axis, and a finish
+// with z: the torus's in-plane distance to its core circle
+// a = |(x, y)| - R, then sqrt(a^2 + z^2) - r; the prism's triangle distance
+// w0, then its combination with the slab distance w1 = |z - zc| - hz.
+template <int K>
+__device__ __forceinline__ ff ff_column_k(const ShapeFF& s, ff qx, ff qy) {
+    if (K == SHAPE_TORUS) return ff_sub(ff_sqrt(ff_add(ff_sqr(qx), ff_sqr(qy))), s.p[0]);
+    return ff_triangle_sdf(qx, qy, s);
+}
+
+template <int K>
+__device__ __forceinline__ ff ff_finish_k(const ShapeFF& s, ff col, ff qz) {
+    if (K == SHAPE_TORUS) return ff_sub(ff_sqrt(ff_add(ff_sqr(col), ff_sqr(qz))), s.p[1]);
+    const ff zero{0.0f, 0.0f};
+    const ff w1 = ff_sub(ff_abs(ff_sub(qz, s.zc)), s.hz);
+    // max(w0, w1) where at most one is positive, else the distance to the
+    // rim sqrt(w0^2 + w1^2)
+    if (!(ff_gt(col, zero) && ff_gt(w1, zero))) return ff_max(col, w1);
+    return ff_sqrt(ff_add(ff_sqr(col), ff_sqr(w1)));
+}
+
 // Exact signed distance (negative inside) of primitive K, in float-float.
 template <int K>
 __device__ inline ff ff_sdf_k(const ShapeFF& s, const ff x[3]) {
@@ -219,18 +241,9 @@ __device__ inline ff ff_sdf_k(const ShapeFF& s, const ff x[3]) {
         ff mid = ff_mul_f(ff_add(s.p[0], s.p[1]), 0.5f), half = ff_mul_f(ff_sub(s.p[1], s.p[0]), 0.5f);
         return ff_sub(ff_abs(ff_sub(r, mid)), half);
     }
-    case SHAPE_TORUS: {
-        ff a = ff_sub(ff_sqrt(ff_add(ff_sqr(q[0]), ff_sqr(q[1]))), s.p[0]);
-        return ff_sub(ff_sqrt(ff_add(ff_sqr(a), ff_sqr(q[2]))), s.p[1]);
-    }
-    case SHAPE_PRISM: {
-        const ff w0 = ff_triangle_sdf(q[0], q[1], s);
-        const ff w1 = ff_sub(ff_abs(ff_sub(q[2], s.zc)), s.hz);
-        // max(w0, w1) where at most one is positive, else the distance to
-        // the rim sqrt(w0^2 + w1^2)
-        if (!(ff_gt(w0, zero) && ff_gt(w1, zero))) return ff_max(w0, w1);
-        return ff_sqrt(ff_add(ff_sqr(w0), ff_sqr(w1)));
-    }
+    case SHAPE_TORUS:
+    case SHAPE_PRISM:
+        return ff_finish_k<K>(s, ff_column_k<K>(s, q[0], q[1]), q[2]);
     case SHAPE_ROUNDED_BOX: {
         ff r = s.p[3];
         ff o = zero, m = ff{-INFINITY, 0.0f};

@@ -333,6 +333,35 @@ __global__ void __launch_bounds__(TAG_THREADS, K == SHAPE_PRISM ? 4 : 8) k_init_
     }
 }
 
+// Plain torus and prism (no rotation, centre at the origin): a thread per
+// package column (i, j) forms the column part of the distance once and
+// finishes it at the column's four points along z (the same operations per
+// point as k_init_sdf).
+template <int K>
+__global__ void __launch_bounds__(TAG_THREADS, K == SHAPE_PRISM ? 4 : 8) k_init_sdf_col(GridFF G, ShapeFF S,
+                                                               const int32_t* __restrict__ pkg_cell,
+                                                               const ff* __restrict__ tab, float* __restrict__ phi,
+                                                               int64_t P, float F) {
+    write_far(phi, -F, F);
+    const int64_t total = (P - 2) * 16;
+    const int off[3] = {0, 4 * G.dims[0], 4 * (G.dims[0] + G.dims[1])};
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = 2 + e / 16;
+        const int c = (int)(e & 15), i = c & 3, j = c >> 2;
+        int64_t I[3];
+        cell_coords(pkg_cell[p], G.dims, I[0], I[1], I[2]);
+        const float2 vx = __ldg(reinterpret_cast<const float2*>(tab) + off[0] + 4 * (int)I[0] + i);
+        const float2 vy = __ldg(reinterpret_cast<const float2*>(tab) + off[1] + 4 * (int)I[1] + j);
+        const ff col = ff_column_k<K>(S, ff{vx.x, vx.y}, ff{vy.x, vy.y});
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 vz = __ldg(reinterpret_cast<const float2*>(tab) + off[2] + 4 * (int)I[2] + k);
+            phi[p * PKG3 + i + 4 * j + 16 * k] = ff_to_float(ff_finish_k<K>(S, col, ff{vz.x, vz.y}));
+        }
+    }
+}
+
 unsigned grid_for(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -449,8 +478,15 @@ cudaError_t launch_init_sdf(const GridFF& G, const ShapeFF& S, const int32_t* pk
     k_coord_table<<<(n + TAG_THREADS - 1) / TAG_THREADS, TAG_THREADS, 0, s>>>(G, (ff*)table);
     note_launch();
     const ff* tab = (const ff*)table;
-    SG_SHAPE_DISPATCH(S.kind, (k_init_sdf<K><<<grid_for((P - 2) * PKG3, TAG_THREADS), TAG_THREADS, 0, s>>>(
-                                  G, S, pkg_cell, tab, phi, P, F)));
+    if (S.plain && S.kind == SHAPE_TORUS)
+        k_init_sdf_col<SHAPE_TORUS><<<grid_for((P - 2) * 16, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, pkg_cell, tab,
+                                                                                              phi, P, F);
+    else if (S.plain && S.kind == SHAPE_PRISM)
+        k_init_sdf_col<SHAPE_PRISM><<<grid_for((P - 2) * 16, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, pkg_cell, tab,
+                                                                                              phi, P, F);
+    else
+        SG_SHAPE_DISPATCH(S.kind, (k_init_sdf<K><<<grid_for((P - 2) * PKG3, TAG_THREADS), TAG_THREADS, 0, s>>>(
+                                      G, S, pkg_cell, tab, phi, P, F)));
     note_launch();
     return cudaGetLastError();
 }
