@@ -215,24 +215,33 @@ __global__ void __launch_bounds__(TAG_THREADS) k_tag_scatter(const uint8_t* __re
 }
 
 // Step 5: neighbourhood; outside the domain -> package 1; far packages self.
+// A thread takes one row (dy, dz) of three entries of a package: the
+// package's cell coordinates once per row, the three x-neighbours from one
+// stretch of cell_pkg, and 12 contiguous bytes of the table.
 __global__ void __launch_bounds__(TAG_THREADS) k_fill_nbr(GridFF G, const int32_t* __restrict__ cell_pkg,
                                                            const int32_t* __restrict__ pkg_cell,
                                                            int32_t* __restrict__ nbr, int64_t P) {
     const int nx = G.dims[0], ny = G.dims[1], nz = G.dims[2];
-    const int64_t total = P * NB;
+    const int64_t total = P * 9;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t p = e / NB;
-        int n = (int)(e - p * NB);
+        const int64_t p = e / 9;
+        const int row = (int)(e - p * 9);  // row = (dy + 1) + 3 (dz + 1)
+        int32_t* out = nbr + p * NB + 3 * row;
         if (p < 2) {
-            nbr[e] = (int32_t)p;
+            out[0] = out[1] = out[2] = (int32_t)p;
             continue;
         }
         int64_t I, J, K;
         cell_coords(pkg_cell[p], G.dims, I, J, K);
-        const int a = (int)I + (n % 3) - 1, b = (int)J + (n / 3) % 3 - 1, c = (int)K + n / 9 - 1;
-        const bool in = a >= 0 && b >= 0 && c >= 0 && a < nx && b < ny && c < nz;
-        nbr[e] = in ? cell_pkg[a + nx * (b + ny * c)] : 1;
+        const int b = (int)J + row % 3 - 1, c = (int)K + row / 3 - 1;
+        const bool in_yz = b >= 0 && c >= 0 && b < ny && c < nz;
+        const int64_t base = (int64_t)nx * (b + (int64_t)ny * c);
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int a = (int)I + dx;
+            out[dx + 1] = in_yz && a >= 0 && a < nx ? cell_pkg[base + a] : 1;
+        }
     }
 }
 
@@ -460,7 +469,7 @@ cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* act_bit
 
 cudaError_t launch_fill_nbr(const GridFF& G, const int32_t* cell_pkg, const int32_t* pkg_cell, int32_t* nbr,
                             int64_t P, cudaStream_t s) {
-    k_fill_nbr<<<grid_for(P * NB, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_pkg, pkg_cell, nbr, P);
+    k_fill_nbr<<<grid_for(P * 9, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_pkg, pkg_cell, nbr, P);
     note_launch();
     return cudaGetLastError();
 }

@@ -179,6 +179,29 @@ def test_reinit_stepwise(sg, name, distort):
     assert np.array_equal(states[1][:2], start32[:2].astype(np.float64))
 
 
+@pytest.mark.parametrize("name", ["sphere_small", "torus_rot"])
+def test_reinit_smoothed_sign(sg, name):
+    """S0 of a call: formed by its first sweep, or by a pass of its own when
+    the call has no sweep; both the same floats, near the oracle's
+    phi / sqrt(phi^2 + h^2), with -1 / +1 in the far packages."""
+    shape, spec = CASES[name]
+    O = oracle.build_grid(spec, shape)
+    start32 = _distorted(spec, O, O.phi).astype(np.float32)
+    got = []
+    for iters in (0, 1, 4):
+        g = sg.Grid(spec)
+        g.tag_allocate(shape)
+        g.init_sdf(shape)
+        g.field("phi").copy_(torch.from_numpy(start32).cuda())
+        g.reinit(iters, 0.5)
+        got.append(H(g.field("S0")))
+        g.sync()
+    assert np.array_equal(got[0], got[1]) and np.array_equal(got[0], got[2])
+    assert np.all(got[0][0] == -1.0) and np.all(got[0][1] == 1.0)
+    ref = oracle.reinit_s0(spec, start32.astype(np.float64))
+    assert np.max(np.abs(got[0][2:].astype(np.float64) - ref[2:])) <= 4 * EPS32
+
+
 @pytest.mark.parametrize("iters", [20, 7])
 def test_reinit_end_to_end_sphere_small(sg, iters):
     shape, spec = si.sphere_small()
