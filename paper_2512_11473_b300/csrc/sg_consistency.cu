@@ -137,7 +137,9 @@ __global__ void __launch_bounds__(CC_THREADS) k_cc_flood_cells(const int8_t* __r
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         int8_t s = src[c];
         if (s == 0) {
-            const int I = (int)(c % nx), J = (int)((c / nx) % ny), K = (int)(c / ((int64_t)nx * ny));
+            // 32-bit index arithmetic: grids hold fewer than 2^31 cells
+            const uint32_t u = (uint32_t)c, q = u / (uint32_t)nx, kk = q / (uint32_t)ny;
+            const int I = (int)(u - q * (uint32_t)nx), J = (int)(q - kk * (uint32_t)ny), K = (int)kk;
             const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
             int sum = 0;
             int8_t v;
