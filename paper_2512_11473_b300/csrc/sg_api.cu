@@ -461,7 +461,7 @@ sg_status sg_laplacian(sg_grid* g) {
     DeviceGuard dg(g->device);
     float* lap = field_ptr(g, SG_FIELD_LAP, false);
     if (!lap) return fail(g, SG_ERR_OOM, "sg_laplacian: out of memory");
-    SG_CUDA(g, launch_set_far(lap, 0.0f, 0.0f, g->stream), "laplacian far");
+    if (g->P <= 2) SG_CUDA(g, launch_set_far(lap, 0.0f, 0.0f, g->stream), "laplacian far");  // else the kernel writes them
     SG_CUDA(g, launch_laplacian(grid_f(g), (const int32_t*)g->faces.p, (const float*)g->field[SG_FIELD_PHI].p, lap, g->P,
                                 g->stream),
             "laplacian");

@@ -35,9 +35,12 @@ __global__ void __launch_bounds__(ROW_THREADS) k_gradient(const int32_t* __restr
     reinterpret_cast<float4*>(gz)[s.q4] = oz;
 }
 
-__global__ void __launch_bounds__(ROW_THREADS) k_laplacian(const int32_t* __restrict__ faces,
-                                                            const float* __restrict__ phi, float* __restrict__ lap,
-                                                            int64_t P, float inv_h2) {
+// 32-register launch bounds (8 CTAs of 256 per SM) as for the reinit sweep;
+// the far packages of the output are written by the first CTA.
+__global__ void __launch_bounds__(ROW_THREADS, 8) k_laplacian(const int32_t* __restrict__ faces,
+                                                               const float* __restrict__ phi, float* __restrict__ lap,
+                                                               int64_t P, float inv_h2) {
+    write_far(lap, 0.0f, 0.0f);
     const RowSlot s = row_slot(P);
     const Rows w = load_rows(phi, faces, s);
     if (!s.valid) return;
