@@ -733,7 +733,7 @@ def run_sg(args):
             elif args.only == "large":
                 r = large_section(sg, torch)
             else:
-                r = batch_section(sg, torch)
+                r = batch_section(sg, torch, n_bodies=args.batch_bodies)
             print(json.dumps({"section": args.only, args.only: r}), flush=True)
         return 0
 
@@ -888,7 +888,7 @@ def run_sg(args):
     if not args.no_large:
         line["large"] = large_section(sg, torch)
     if not args.no_batch:
-        line["batch"] = batch_section(sg, torch)
+        line["batch"] = batch_section(sg, torch, n_bodies=args.batch_bodies)
     net = None
     if not args.no_surrogate:
         line["surrogate"], net = surrogate_section(sg, torch)
@@ -927,6 +927,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-body batch measurement")
+    ap.add_argument("--batch-bodies", type=int, default=256,
+                    help="bodies in the batch measurement (the first n of the 256-body set)")
     ap.add_argument("--no-surrogate", action="store_true", help="skip training and timing the surrogate")
     ap.add_argument("--no-relax", action="store_true", help="skip the 64-body particle relaxation")
     ap.add_argument("--relax-particles", type=int, default=100_000_000)

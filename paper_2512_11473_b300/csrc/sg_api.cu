@@ -429,7 +429,7 @@ sg_status sg_consistency_correct(sg_grid* g, float trust, int64_t* out) {
     if (!(trust > 0.0f) || !std::isfinite(trust)) return fail(g, SG_ERR_INVALID, "sg_consistency_correct: bad trust");
     if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_consistency_correct: phi not initialised");
     DeviceGuard dg(g->device);
-    if (!ensure(g, g->scratch, consistency_scratch_bytes(g->P, g->nc)))
+    if (!ensure(g, g->scratch, consistency_scratch_bytes(g->P, g->desc.dims)))
         return fail(g, SG_ERR_OOM, "sg_consistency_correct: out of memory");
     int64_t o[4] = {0, 0, 0, 0};
     const cudaError_t e =

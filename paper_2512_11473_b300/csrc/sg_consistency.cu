@@ -12,6 +12,11 @@
 //    inside, 1 outside) and the neighbour table is rebuilt.
 // The point step runs first: every data point within h of the surface lies
 // in a core cell, so the cells have no trusted sign until the points have.
+// Labels are kept as bit planes (a 64-bit word per package for the points,
+// 32-cell words of the mesh's x-rows for the cells) and a sweep counts the
+// + and - neighbours of every bit with bit-sliced adders: a few dozen word
+// operations per 64 or 32 entries, the same labels sweep by sweep as the
+// entry-by-entry rule.
 #include "sg_internal.cuh"
 
 namespace sg {
@@ -32,62 +37,117 @@ __device__ __forceinline__ void flag_if_any(bool changed, int* flag) {
     if (any && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
 
-// trusted points keep their sign; every other entry starts unknown
-__global__ void __launch_bounds__(CC_THREADS) k_cc_seed_points(const float* __restrict__ phi, int8_t* __restrict__ sg,
-                                                                int64_t n_act, float tau) {
+// Both floods run on bit planes of labels, `plus` and `minus`.  Points: a
+// package's 64 data points are the bits of one 64-bit word (bit d = i + 4j +
+// 16k), so a plane is P words, seen as 2P 32-bit halves by the kernels that
+// work point by point.
+
+// count of set inputs per bit, bit-sliced: n = n0 + 2 n1 + 4 n2 (at most 6)
+template <class W>
+__device__ __forceinline__ void count6(W a1, W a2, W a3, W a4, W a5, W a6, W& n0, W& n1, W& n2) {
+    const W x1 = a1 ^ a2, s1 = x1 ^ a3, c1 = (a1 & a2) | (a3 & x1);
+    const W x2 = a4 ^ a5, s2 = x2 ^ a6, c2 = (a4 & a5) | (a6 & x2);
+    n0 = s1 ^ s2;
+    const W k = s1 & s2, x3 = c1 ^ c2;
+    n1 = x3 ^ k;
+    n2 = (c1 & c2) | (k & x3);
+}
+
+// From the per-bit counts of + and - neighbours (bit-sliced, three bits
+// each) the bits where + outnumbers - (gt) and where - outnumbers + (lt):
+// the sign of the sum of the neighbours' signs.
+template <class W>
+__device__ __forceinline__ void majority(const W (&pa)[6], const W (&ma)[6], W& gt, W& lt) {
+    W p0, p1, p2, m0, m1, m2;
+    count6(pa[0], pa[1], pa[2], pa[3], pa[4], pa[5], p0, p1, p2);
+    count6(ma[0], ma[1], ma[2], ma[3], ma[4], ma[5], m0, m1, m2);
+    const W e2 = ~(p2 ^ m2), e1 = ~(p1 ^ m1);
+    gt = (p2 & ~m2) | (e2 & ((p1 & ~m1) | (e1 & p0 & ~m0)));
+    lt = (m2 & ~p2) | (e2 & ((m1 & ~p1) | (e1 & m0 & ~p0)));
+}
+
+// trusted points (|phi| < tau, phi != 0) start with their sign, every other
+// point unknown; a warp forms one 32-bit half of a package's words by ballots
+__global__ void __launch_bounds__(CC_THREADS) k_cc_seed_points(const float* __restrict__ phi,
+                                                                uint32_t* __restrict__ plus,
+                                                                uint32_t* __restrict__ minus, int64_t n_act,
+                                                                float tau) {
+    // n_act and the grid stride are multiples of 32: a warp is in or out as a whole
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_act; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = 2 * PKG3 + e;
         const float v = phi[q];
-        sg[q] = fabsf(v) < tau ? (int8_t)(v > 0.0f ? 1 : (v < 0.0f ? -1 : 0)) : (int8_t)0;
+        const bool trusted = fabsf(v) < tau;
+        const unsigned po = __ballot_sync(0xffffffffu, trusted && v > 0.0f);
+        const unsigned mo = __ballot_sync(0xffffffffu, trusted && v < 0.0f);
+        if ((threadIdx.x & 31) == 0) {
+            plus[q >> 5] = po;
+            minus[q >> 5] = mo;
+        }
     }
 }
 
-// one Jacobi sweep of the point flood; neighbours across a package face come
-// from the face table, neighbours in far packages do not count
+// The six face-neighbour words of a package word v (bit d = i + 4j + 16k):
+// bit d of the result is the neighbour's bit, from v inside the package and
+// from the neighbour package's word (0 for a far package) across a face.
+__device__ __forceinline__ void point_neighbours(uint64_t v, const uint64_t (&nb)[6], uint64_t (&out)[6]) {
+    constexpr uint64_t I0 = 0x1111111111111111ull, I3 = 0x8888888888888888ull;  // i = 0, i = 3
+    constexpr uint64_t J0 = 0x000F000F000F000Full, J3 = 0xF000F000F000F000ull;  // j = 0, j = 3
+    out[0] = ((v << 1) & ~I0) | ((nb[0] >> 3) & I0);    // -x: d - 1, or d + 3 of the -x package
+    out[1] = ((v >> 1) & ~I3) | ((nb[1] << 3) & I3);    // +x: d + 1, or d - 3 of the +x package
+    out[2] = ((v << 4) & ~J0) | ((nb[2] >> 12) & J0);   // -y: d - 4, or d + 12
+    out[3] = ((v >> 4) & ~J3) | ((nb[3] << 12) & J3);   // +y: d + 4, or d - 12
+    out[4] = (v << 16) | (nb[4] >> 48);                 // -z: d - 16, or d + 48
+    out[5] = (v >> 16) | (nb[5] << 48);                 // +z: d + 16, or d - 48
+}
+
+// one Jacobi sweep of the point flood, a thread per active package: an
+// unknown point takes the sign of the sum of its labelled face neighbours'
+// signs; neighbours across a package face come from the face table, those
+// in far packages do not count
 __global__ void __launch_bounds__(CC_THREADS) k_cc_flood_points(const int32_t* __restrict__ faces,
-                                                                 const int8_t* __restrict__ src,
-                                                                 int8_t* __restrict__ dst, int64_t n_act, int* flag) {
+                                                                 const uint64_t* __restrict__ p_in,
+                                                                 const uint64_t* __restrict__ m_in,
+                                                                 uint64_t* __restrict__ p_out,
+                                                                 uint64_t* __restrict__ m_out, int64_t P, int* flag) {
     bool changed = false;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_act; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = 2 * PKG3 + e, p = q >> 6;
-        const int d = (int)(q & 63);
-        int8_t s = src[q];
-        if (s == 0) {
-            const int i = d & 3, j = (d >> 2) & 3, k = d >> 4;
-            const int32_t* fc = faces + p * 8;
-            int sum = 0;
-            int64_t pp;
-            pp = i > 0 ? p : __ldg(fc + 0);
-            if (pp >= 2) sum += src[pp * PKG3 + (i > 0 ? d - 1 : d + 3)];
-            pp = i < 3 ? p : __ldg(fc + 1);
-            if (pp >= 2) sum += src[pp * PKG3 + (i < 3 ? d + 1 : d - 3)];
-            pp = j > 0 ? p : __ldg(fc + 2);
-            if (pp >= 2) sum += src[pp * PKG3 + (j > 0 ? d - 4 : d + 12)];
-            pp = j < 3 ? p : __ldg(fc + 3);
-            if (pp >= 2) sum += src[pp * PKG3 + (j < 3 ? d + 4 : d - 12)];
-            pp = k > 0 ? p : __ldg(fc + 4);
-            if (pp >= 2) sum += src[pp * PKG3 + (k > 0 ? d - 16 : d + 48)];
-            pp = k < 3 ? p : __ldg(fc + 5);
-            if (pp >= 2) sum += src[pp * PKG3 + (k < 3 ? d + 16 : d - 48)];
-            if (sum != 0) {
-                s = sum > 0 ? 1 : -1;
-                changed = true;
+    for (int64_t p = 2 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t Pw = p_in[p], Mw = m_in[p], U = ~(Pw | Mw);
+        uint64_t Pn = Pw, Mn = Mw;
+        if (U) {
+            const int4 f0 = __ldg(reinterpret_cast<const int4*>(faces + p * 8));
+            const int2 f1 = __ldg(reinterpret_cast<const int2*>(faces + p * 8 + 4));
+            const int32_t fc[6] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y};
+            uint64_t pn[6], mn[6];
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+                pn[a] = fc[a] >= 2 ? p_in[fc[a]] : 0ull;
+                mn[a] = fc[a] >= 2 ? m_in[fc[a]] : 0ull;
             }
+            uint64_t pa[6], ma[6], gt, lt;
+            point_neighbours(Pw, pn, pa);
+            point_neighbours(Mw, mn, ma);
+            majority(pa, ma, gt, lt);
+            Pn |= U & gt;
+            Mn |= U & lt;
+            changed |= (U & (gt | lt)) != 0ull;
         }
-        dst[q] = s;
+        p_out[p] = Pn;
+        m_out[p] = Mn;
     }
     flag_if_any(changed, flag);
 }
 
 // phi <- sign |phi| where the flood found a sign; counts the flips
-__global__ void __launch_bounds__(CC_THREADS) k_cc_apply(float* __restrict__ phi, const int8_t* __restrict__ sg,
-                                                          int64_t n_act, unsigned long long* count) {
+__global__ void __launch_bounds__(CC_THREADS) k_cc_apply(float* __restrict__ phi, const uint32_t* __restrict__ plus,
+                                                          const uint32_t* __restrict__ minus, int64_t n_act,
+                                                          unsigned long long* count) {
     unsigned long long c = 0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_act; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = 2 * PKG3 + e;
-        const int8_t s = sg[q];
+        const uint32_t bit = 1u << (q & 31);
+        const bool pos = (plus[q >> 5] & bit) != 0u, neg = (minus[q >> 5] & bit) != 0u;
         const float v = phi[q];
-        if ((s > 0 && v < 0.0f) || (s < 0 && v > 0.0f)) {
+        if ((pos && v < 0.0f) || (neg && v > 0.0f)) {
             phi[q] = -v;
             ++c;
         }
@@ -97,80 +157,107 @@ __global__ void __launch_bounds__(CC_THREADS) k_cc_apply(float* __restrict__ phi
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
-// cell labels: core cells blocked, inner cells from their package's signs
-__global__ void __launch_bounds__(CC_THREADS) k_cc_seed_cells(const int32_t* __restrict__ cell_pkg,
+// The label of one background cell at the start of the cell flood: 0 for a
+// far cell (unknown), CC_BLOCK for a core cell or an inner cell whose points
+// carry both signs, else the sign its package's points share (or 0).
+__device__ __forceinline__ int cell_label(const int32_t* __restrict__ cell_pkg, const uint8_t* __restrict__ pkg_type,
+                                          const uint64_t* __restrict__ pt_plus, const uint64_t* __restrict__ pt_minus,
+                                          int64_t c) {
+    const int64_t p = cell_pkg[c];
+    if (p < 2) return 0;
+    if (pkg_type[p] == 2) return CC_BLOCK;
+    const bool pos = pt_plus[p] != 0ull, neg = pt_minus[p] != 0ull;
+    return (pos && neg) ? CC_BLOCK : (pos ? 1 : (neg ? -1 : 0));
+}
+
+// The cell flood runs on bit planes: each x-row of the background mesh is
+// cut into nwx = ceil(nx / 32) words, bit b of word x of row r = J + ny K
+// standing for cell I = 32 x + b (bits at I >= nx are 0 in every plane).
+// `open` marks the cells that are not blocked, `plus` and `minus` the
+// labelled ones.  Seeding: a lane per bit (rows padded to whole words, so a
+// warp covers one word), the three words formed by ballots.
+__global__ void __launch_bounds__(CC_THREADS) k_cc_seed_words(const int32_t* __restrict__ cell_pkg,
                                                                const uint8_t* __restrict__ pkg_type,
-                                                               const int8_t* __restrict__ sg, int8_t* __restrict__ lab,
-                                                               int64_t nc) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = cell_pkg[c];
-        int8_t l = 0;
-        if (p >= 2) {
-            if (pkg_type[p] == 2) {
-                l = CC_BLOCK;
-            } else {
-                // bytes are 0x01 (+), 0xff (-) or 0: bit 7 marks -, bit 0 without bit 7 marks +
-                const uint4* r = reinterpret_cast<const uint4*>(sg + p * PKG3);
-                unsigned pos = 0, neg = 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint4 v = r[k];
-                    const unsigned w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        neg |= w[m] & 0x80808080u;
-                        pos |= w[m] & 0x01010101u & ~((w[m] >> 7) & 0x01010101u);
-                    }
-                }
-                l = (pos && neg) ? CC_BLOCK : (pos ? 1 : (neg ? -1 : 0));
-            }
+                                                               const uint64_t* __restrict__ pt_plus,
+                                                               const uint64_t* __restrict__ pt_minus,
+                                                               uint32_t* __restrict__ open,
+                                                               uint32_t* __restrict__ plus, uint32_t* __restrict__ minus,
+                                                               int nx, int nwx, int64_t n_lanes) {
+    // n_lanes and the grid stride are multiples of 32: a warp is in or out as a whole
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_lanes; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row_lanes = 32 * (int64_t)nwx, r = t / row_lanes;
+        const int I = (int)(t - r * row_lanes);
+        const int l = I < nx ? cell_label(cell_pkg, pkg_type, pt_plus, pt_minus, (int64_t)I + (int64_t)nx * r) : CC_BLOCK;
+        const unsigned po = __ballot_sync(0xffffffffu, l == 1);
+        const unsigned mo = __ballot_sync(0xffffffffu, l == -1);
+        const unsigned op = __ballot_sync(0xffffffffu, l != CC_BLOCK);
+        if ((threadIdx.x & 31) == 0) {
+            const int64_t w = t >> 5;
+            open[w] = op;
+            plus[w] = po;
+            minus[w] = mo;
         }
-        lab[c] = l;
     }
 }
 
-// one Jacobi sweep of the cell flood over the background mesh
-__global__ void __launch_bounds__(CC_THREADS) k_cc_flood_cells(const int8_t* __restrict__ src, int8_t* __restrict__ dst,
-                                                                int nx, int ny, int nz, int* flag) {
-    const int64_t nc = (int64_t)nx * ny * nz;
+// one Jacobi sweep of the cell flood, a thread per word: an unknown open
+// cell takes + where more of its face neighbours are + than -, - where more
+// are -, exactly as the sign of the sum of their signs (blocked and unknown
+// neighbours count 0; neighbours outside the mesh do not exist)
+__global__ void __launch_bounds__(CC_THREADS) k_cc_flood_words(const uint32_t* __restrict__ open,
+                                                                const uint32_t* __restrict__ p_in,
+                                                                const uint32_t* __restrict__ m_in,
+                                                                uint32_t* __restrict__ p_out, uint32_t* __restrict__ m_out,
+                                                                int nwx, int ny, int nz, int* flag) {
+    const int64_t nw = (int64_t)nwx * ny * nz;
     bool changed = false;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
-        int8_t s = src[c];
-        if (s == 0) {
-            // 32-bit index arithmetic: grids hold fewer than 2^31 cells
-            const uint32_t u = (uint32_t)c, q = u / (uint32_t)nx, kk = q / (uint32_t)ny;
-            const int I = (int)(u - q * (uint32_t)nx), J = (int)(q - kk * (uint32_t)ny), K = (int)kk;
-            const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
-            int sum = 0;
-            int8_t v;
-            if (I > 0 && ((v = src[c - sx]) == 1 || v == -1)) sum += v;
-            if (I < nx - 1 && ((v = src[c + sx]) == 1 || v == -1)) sum += v;
-            if (J > 0 && ((v = src[c - sy]) == 1 || v == -1)) sum += v;
-            if (J < ny - 1 && ((v = src[c + sy]) == 1 || v == -1)) sum += v;
-            if (K > 0 && ((v = src[c - sz]) == 1 || v == -1)) sum += v;
-            if (K < nz - 1 && ((v = src[c + sz]) == 1 || v == -1)) sum += v;
-            if (sum != 0) {
-                s = sum > 0 ? 1 : -1;
-                changed = true;
-            }
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t P = p_in[w], M = m_in[w];
+        const uint32_t U = open[w] & ~(P | M);
+        uint32_t Pn = P, Mn = M;
+        if (U) {
+            // 32-bit index arithmetic: nw <= nx ny nz < 2^31
+            const uint32_t u = (uint32_t)w, r = u / (uint32_t)nwx, x = u - r * (uint32_t)nwx;
+            const uint32_t K = r / (uint32_t)ny, J = r - K * (uint32_t)ny;
+            const int64_t sy = nwx, sz = (int64_t)nwx * ny;
+            const bool xl = x > 0, xr = x + 1 < (uint32_t)nwx, yl = J > 0, yr = J + 1 < (uint32_t)ny, zl = K > 0,
+                       zr = K + 1 < (uint32_t)nz;
+            const uint32_t Pl = xl ? p_in[w - 1] : 0u, Pr = xr ? p_in[w + 1] : 0u;
+            const uint32_t Ml = xl ? m_in[w - 1] : 0u, Mr = xr ? m_in[w + 1] : 0u;
+            const uint32_t pa[6] = {(P << 1) | (Pl >> 31), (P >> 1) | (Pr << 31), yl ? p_in[w - sy] : 0u,
+                                    yr ? p_in[w + sy] : 0u, zl ? p_in[w - sz] : 0u, zr ? p_in[w + sz] : 0u};
+            const uint32_t ma[6] = {(M << 1) | (Ml >> 31), (M >> 1) | (Mr << 31), yl ? m_in[w - sy] : 0u,
+                                    yr ? m_in[w + sy] : 0u, zl ? m_in[w - sz] : 0u, zr ? m_in[w + sz] : 0u};
+            uint32_t gt, lt;
+            majority(pa, ma, gt, lt);
+            Pn |= U & gt;
+            Mn |= U & lt;
+            changed |= (U & (gt | lt)) != 0u;
         }
-        dst[c] = s;
+        p_out[w] = Pn;
+        m_out[w] = Mn;
     }
     flag_if_any(changed, flag);
 }
 
 // far cells take their label's far package; counts the moves
-__global__ void __launch_bounds__(CC_THREADS) k_cc_far(int32_t* __restrict__ cell_pkg, const int8_t* __restrict__ lab,
-                                                        int64_t nc, unsigned long long* count) {
+__global__ void __launch_bounds__(CC_THREADS) k_cc_far(int32_t* __restrict__ cell_pkg, const uint32_t* __restrict__ plus,
+                                                        const uint32_t* __restrict__ minus, int nx, int nwx, int64_t nc,
+                                                        unsigned long long* count) {
     unsigned long long c = 0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t p = cell_pkg[e];
-        const int8_t l = lab[e];
-        if (p < 2 && (l == 1 || l == -1)) {
-            const int32_t want = l < 0 ? 0 : 1;
-            if (p != want) {
-                cell_pkg[e] = want;
-                ++c;
+        if (p < 2) {
+            const uint32_t u = (uint32_t)e, r = u / (uint32_t)nx, I = u - r * (uint32_t)nx;
+            const int64_t w = (int64_t)r * nwx + (I >> 5);
+            const uint32_t bit = 1u << (I & 31);
+            const int l = (plus[w] & bit) ? 1 : ((minus[w] & bit) ? -1 : 0);
+            if (l != 0) {
+                const int32_t want = l < 0 ? 0 : 1;
+                if (p != want) {
+                    cell_pkg[e] = want;
+                    ++c;
+                }
             }
         }
     }
@@ -183,15 +270,15 @@ __global__ void __launch_bounds__(CC_THREADS) k_cc_far(int32_t* __restrict__ cel
 // on the fixed point.  Host-synchronising.
 constexpr int CC_BATCH = 8;
 
-template <class Sweep>
-cudaError_t flood(Sweep sweep, int8_t*& a, int8_t*& b, int* dflag, int* hflag, int64_t max_sweeps, int64_t& sweeps,
+template <class Sweep, class T>
+cudaError_t flood(Sweep sweep, T*& a, T*& b, int* dflag, int* hflag, int64_t max_sweeps, int64_t& sweeps,
                   cudaStream_t s) {
     for (;;) {
         cudaError_t e = cudaMemsetAsync(dflag, 0, CC_BATCH * sizeof(int), s);
         for (int k = 0; k < CC_BATCH && e == cudaSuccess; ++k) {
             sweep(a, b, dflag + k);
             e = cudaGetLastError();
-            int8_t* t = a;
+            T* t = a;
             a = b;
             b = t;
             ++sweeps;
@@ -206,59 +293,69 @@ cudaError_t flood(Sweep sweep, int8_t*& a, int8_t*& b, int* dflag, int* hflag, i
 
 size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// words of one bit plane of the cell flood
+int64_t plane_words(const int32_t dims[3]) { return (int64_t)((dims[0] + 31) / 32) * dims[1] * dims[2]; }
+
 }  // namespace
 
-size_t consistency_scratch_bytes(int64_t P, int64_t nc) {
-    return 2 * al256((size_t)P * PKG3) + 2 * al256((size_t)nc) + 256;
+size_t consistency_scratch_bytes(int64_t P, const int32_t dims[3]) {
+    const size_t plane = (size_t)plane_words(dims) * sizeof(uint32_t);
+    return 2 * al256(2 * (size_t)P * sizeof(uint64_t)) + al256(plane) + 2 * al256(2 * plane) + 256;
 }
 
 cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cell_pkg, const int32_t* pkg_cell,
                             const uint8_t* pkg_type, int32_t* nbr, int32_t* faces, float* phi, float tau,
                             void* scratch, void* host_pin, int64_t out[4], cudaStream_t s) {
     char* sp = (char*)scratch;
-    int8_t* sa = (int8_t*)sp;
-    sp += al256((size_t)P * PKG3);
-    int8_t* sb = (int8_t*)sp;
-    sp += al256((size_t)P * PKG3);
-    int8_t* la = (int8_t*)sp;
-    sp += al256((size_t)nc);
-    int8_t* lb = (int8_t*)sp;
-    sp += al256((size_t)nc);
+    uint64_t* sa = (uint64_t*)sp;  // point planes: plus (P words), then minus (P words)
+    sp += al256(2 * (size_t)P * sizeof(uint64_t));
+    uint64_t* sb = (uint64_t*)sp;
+    sp += al256(2 * (size_t)P * sizeof(uint64_t));
+    const int nx = G.dims[0], ny = G.dims[1], nz = G.dims[2], nwx = (nx + 31) / 32;
+    const int64_t nw = plane_words(G.dims);
+    uint32_t* open = (uint32_t*)sp;
+    sp += al256((size_t)nw * sizeof(uint32_t));
+    uint32_t* la = (uint32_t*)sp;  // plus plane, then minus plane
+    sp += al256(2 * (size_t)nw * sizeof(uint32_t));
+    uint32_t* lb = (uint32_t*)sp;
+    sp += al256(2 * (size_t)nw * sizeof(uint32_t));
     int* dflag = (int*)sp;                                               // CC_BATCH ints
     unsigned long long* cnt = (unsigned long long*)(sp + 64);            // 2 counters
     int* hflag = (int*)host_pin;                                         // CC_BATCH ints
     unsigned long long* hcnt = (unsigned long long*)((char*)host_pin + 64);  // 2 counters
     const int64_t n_act = (P - 2) * PKG3;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(sa, 0, (size_t)P * PKG3, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(sb, 0, (size_t)P * PKG3, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(sa, 0, 2 * (size_t)P * sizeof(uint64_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(sb, 0, 2 * (size_t)P * sizeof(uint64_t), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     int64_t sweeps_pt = 0, sweeps_cell = 0;
     if (n_act > 0) {
-        k_cc_seed_points<<<cc_blocks(n_act), CC_THREADS, 0, s>>>(phi, sa, n_act, tau);
+        k_cc_seed_points<<<cc_blocks(n_act), CC_THREADS, 0, s>>>(phi, (uint32_t*)sa, (uint32_t*)(sa + P), n_act, tau);
         note_launch();
-        const unsigned nb = cc_blocks(n_act);
+        const unsigned nb = cc_blocks(P - 2);
         e = flood(
-            [&](const int8_t* src, int8_t* dst, int* flag) {
-                k_cc_flood_points<<<nb, CC_THREADS, 0, s>>>(faces, src, dst, n_act, flag);
+            [&](const uint64_t* src, uint64_t* dst, int* flag) {
+                k_cc_flood_points<<<nb, CC_THREADS, 0, s>>>(faces, src, src + P, dst, dst + P, P, flag);
                 note_launch();
             },
             sa, sb, dflag, hflag, n_act + 1, sweeps_pt, s);
         if (e != cudaSuccess) return e;
-        k_cc_apply<<<cc_blocks(n_act), CC_THREADS, 0, s>>>(phi, sa, n_act, cnt);
+        k_cc_apply<<<cc_blocks(n_act), CC_THREADS, 0, s>>>(phi, (const uint32_t*)sa, (const uint32_t*)(sa + P), n_act,
+                                                            cnt);
         note_launch();
     }
-    k_cc_seed_cells<<<cc_blocks(nc), CC_THREADS, 0, s>>>(cell_pkg, pkg_type, sa, la, nc);
+    k_cc_seed_words<<<cc_blocks(32 * nw), CC_THREADS, 0, s>>>(cell_pkg, pkg_type, sa, sa + P, open, la, la + nw, nx, nwx,
+                                                              32 * nw);
     note_launch();
-    const unsigned cb = cc_blocks(nc);
+    const unsigned cb = cc_blocks(nw);
     e = flood(
-        [&](const int8_t* src, int8_t* dst, int* flag) {
-            k_cc_flood_cells<<<cb, CC_THREADS, 0, s>>>(src, dst, G.dims[0], G.dims[1], G.dims[2], flag);
+        [&](const uint32_t* src, uint32_t* dst, int* flag) {
+            k_cc_flood_words<<<cb, CC_THREADS, 0, s>>>(open, src, src + nw, dst, dst + nw, nwx, ny, nz, flag);
             note_launch();
         },
         la, lb, dflag, hflag, nc + 1, sweeps_cell, s);
     if (e != cudaSuccess) return e;
-    k_cc_far<<<cc_blocks(nc), CC_THREADS, 0, s>>>(cell_pkg, la, nc, cnt + 1);
+    k_cc_far<<<cc_blocks(nc), CC_THREADS, 0, s>>>(cell_pkg, la, la + nw, nx, nwx, nc, cnt + 1);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the neighbour and face tables name far packages by their cells

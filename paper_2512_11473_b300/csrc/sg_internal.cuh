@@ -128,7 +128,7 @@ cudaError_t launch_fill_nbr(const GridFF& G, const int32_t* cell_pkg, const int3
 // Consistency (sign) correction of phi, cell_pkg, nbr and faces in place;
 // host-synchronising.  out: points flipped, far cells moved, point and cell
 // flood sweeps.
-size_t consistency_scratch_bytes(int64_t P, int64_t nc);
+size_t consistency_scratch_bytes(int64_t P, const int32_t dims[3]);
 cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cell_pkg, const int32_t* pkg_cell,
                             const uint8_t* pkg_type, int32_t* nbr, int32_t* faces, float* phi, float tau,
                             void* scratch, void* host_pin, int64_t out[4], cudaStream_t s);

@@ -38,6 +38,9 @@ BODIES = {
     "rounded_box": lambda: (si.rounded_box((0.6, 0.45, 0.3), 0.06, rot=si.random_rotation(si.Stream(5))),
                             si.GridSpec((-1.0, -1.0, -1.0), (25, 25, 25), 0.02)),
     "torus_h0.002": lambda: si.torus_large(),
+    # x-rows of exactly two 32-cell words: the cell flood's bit planes without padding bits
+    "sphere_64x40x33": lambda: (si.sphere(0.5, centre=(0.05, -0.03, 0.02)),
+                                si.GridSpec((-1.6, -1.0, -0.8), (64, 40, 33), 0.0125)),
 }
 
 
@@ -65,7 +68,7 @@ def _apply_noise_device(g, flip, far):
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("name", ["sphere", "torus", "rounded_box", "torus_h0.002"])
+@pytest.mark.parametrize("name", ["sphere", "torus", "rounded_box", "sphere_64x40x33", "torus_h0.002"])
 def test_consistency_restores_and_matches_oracle(sg, name):
     shape, spec, g, O, clean, flip, far = _setup(sg, name, frac=0.3 if name != "torus_h0.002" else 0.2)
     faces0 = H(g.field("nbr"))[:, [12, 14, 10, 16, 4, 22]]
