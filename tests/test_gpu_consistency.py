@@ -41,6 +41,9 @@ BODIES = {
     # x-rows of exactly two 32-cell words: the cell flood's bit planes without padding bits
     "sphere_64x40x33": lambda: (si.sphere(0.5, centre=(0.05, -0.03, 0.02)),
                                 si.GridSpec((-1.6, -1.0, -0.8), (64, 40, 33), 0.0125)),
+    # x-rows of 10 words (300 cells, the last one 12 bits wide)
+    "sphere_300x20x20": lambda: (si.sphere(0.1, centre=(0.31, 0.005, -0.004)),
+                                 si.GridSpec((-3.0, -0.2, -0.2), (300, 20, 20), 0.005)),
 }
 
 
@@ -68,7 +71,8 @@ def _apply_noise_device(g, flip, far):
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("name", ["sphere", "torus", "rounded_box", "sphere_64x40x33", "torus_h0.002"])
+@pytest.mark.parametrize("name", ["sphere", "torus", "rounded_box", "sphere_64x40x33", "sphere_300x20x20",
+                                  "torus_h0.002"])
 def test_consistency_restores_and_matches_oracle(sg, name):
     shape, spec, g, O, clean, flip, far = _setup(sg, name, frac=0.3 if name != "torus_h0.002" else 0.2)
     faces0 = H(g.field("nbr"))[:, [12, 14, 10, 16, 4, 22]]
