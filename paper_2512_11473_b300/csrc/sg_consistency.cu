@@ -137,20 +137,33 @@ __global__ void __launch_bounds__(CC_THREADS) k_cc_flood_points(const int32_t* _
     flag_if_any(changed, flag);
 }
 
-// phi <- sign |phi| where the flood found a sign; counts the flips
-__global__ void __launch_bounds__(CC_THREADS) k_cc_apply(float* __restrict__ phi, const uint32_t* __restrict__ plus,
-                                                          const uint32_t* __restrict__ minus, int64_t n_act,
+// phi <- sign |phi| where the flood found a sign; counts the flips.  A
+// thread per row of four points (one float4 of phi, four bits of each
+// plane); rows without a label are not read.
+__device__ __forceinline__ float apply_sign(float v, uint32_t pos, uint32_t neg, unsigned long long& c) {
+    if ((pos && v < 0.0f) || (neg && v > 0.0f)) {
+        ++c;
+        return -v;
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(CC_THREADS) k_cc_apply(float4* __restrict__ phi4, const uint32_t* __restrict__ plus,
+                                                          const uint32_t* __restrict__ minus, int64_t n_rows,
                                                           unsigned long long* count) {
     unsigned long long c = 0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_act; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = 2 * PKG3 + e;
-        const uint32_t bit = 1u << (q & 31);
-        const bool pos = (plus[q >> 5] & bit) != 0u, neg = (minus[q >> 5] & bit) != 0u;
-        const float v = phi[q];
-        if ((pos && v < 0.0f) || (neg && v > 0.0f)) {
-            phi[q] = -v;
-            ++c;
-        }
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_rows; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = 2 * PKG3 + 4 * e;  // first point of the row
+        const uint32_t sh = (uint32_t)q & 31u;
+        const uint32_t pb = (plus[q >> 5] >> sh) & 0xFu, mb = (minus[q >> 5] >> sh) & 0xFu;
+        if ((pb | mb) == 0u) continue;
+        const float4 v = phi4[q >> 2];
+        float4 o;
+        o.x = apply_sign(v.x, pb & 1u, mb & 1u, c);
+        o.y = apply_sign(v.y, pb & 2u, mb & 2u, c);
+        o.z = apply_sign(v.z, pb & 4u, mb & 4u, c);
+        o.w = apply_sign(v.w, pb & 8u, mb & 8u, c);
+        if (o.x != v.x || o.y != v.y || o.z != v.z || o.w != v.w) phi4[q >> 2] = o;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
@@ -340,8 +353,8 @@ cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cel
             },
             sa, sb, dflag, hflag, n_act + 1, sweeps_pt, s);
         if (e != cudaSuccess) return e;
-        k_cc_apply<<<cc_blocks(n_act), CC_THREADS, 0, s>>>(phi, (const uint32_t*)sa, (const uint32_t*)(sa + P), n_act,
-                                                            cnt);
+        k_cc_apply<<<cc_blocks(n_act / 4), CC_THREADS, 0, s>>>(reinterpret_cast<float4*>(phi), (const uint32_t*)sa,
+                                                                (const uint32_t*)(sa + P), n_act / 4, cnt);
         note_launch();
     }
     k_cc_seed_words<<<cc_blocks(32 * nw), CC_THREADS, 0, s>>>(cell_pkg, pkg_type, sa, sa + P, open, la, la + nw, nx, nwx,
