@@ -211,7 +211,8 @@ SG_API sg_status sg_gradient(sg_grid *g);
  * no trusted sign before the points.)  For a grid whose magnitudes are
  * distances this restores every sign a leaky surface got wrong outside the
  * trusted band.  out (host, may be NULL): [4] = points flipped, far cells
- * moved, point sweeps, cell sweeps.  Derived fields (g, W, ...) are stale
+ * moved, point sweeps, cell sweeps (each count ends with the first sweep
+ * that changes nothing).  Derived fields (g, W, ...) are stale
  * afterwards.  Blocks until done (it reads convergence flags).
  * Errors: SG_ERR_INVALID (trust <= 0 or not finite), SG_ERR_STATE (no phi),
  * SG_ERR_OOM, SG_ERR_TIMEOUT (a flood that does not settle; cannot happen

@@ -17,6 +17,8 @@
 // + and - neighbours of every bit with bit-sliced adders: a few dozen word
 // operations per 64 or 32 entries, the same labels sweep by sweep as the
 // entry-by-entry rule.
+#include <algorithm>
+
 #include "sg_internal.cuh"
 
 namespace sg {
@@ -100,40 +102,54 @@ __device__ __forceinline__ void point_neighbours(uint64_t v, const uint64_t (&nb
     out[5] = (v >> 16) | (nb[5] << 48);                 // +z: d + 16, or d - 48
 }
 
-// one Jacobi sweep of the point flood, a thread per active package: an
-// unknown point takes the sign of the sum of its labelled face neighbours'
-// signs; neighbours across a package face come from the face table, those
-// in far packages do not count
+// Label loads: plain in the one-sweep kernels, from L2 (ld.global.cg) in
+// the persistent ones, where another SM may have rewritten a line this SM
+// still holds in L1 since an earlier sweep.
+template <bool L2, class W>
+__device__ __forceinline__ W ld_lab(const W* p) { return L2 ? __ldcg(p) : *p; }
+
+// One package of a point sweep: an unknown point takes the sign of the sum
+// of its labelled face neighbours' signs; neighbours across a package face
+// come from the face table, those in far packages do not count.  Returns
+// whether a label was set.
+template <bool L2>
+__device__ __forceinline__ bool point_sweep_one(const int32_t* __restrict__ faces, const uint64_t* p_in,
+                                                const uint64_t* m_in, uint64_t* p_out, uint64_t* m_out, int64_t p) {
+    const uint64_t Pw = ld_lab<L2>(p_in + p), Mw = ld_lab<L2>(m_in + p), U = ~(Pw | Mw);
+    uint64_t Pn = Pw, Mn = Mw;
+    bool changed = false;
+    if (U) {
+        const int4 f0 = __ldg(reinterpret_cast<const int4*>(faces + p * 8));
+        const int2 f1 = __ldg(reinterpret_cast<const int2*>(faces + p * 8 + 4));
+        const int32_t fc[6] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y};
+        uint64_t pn[6], mn[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            pn[a] = fc[a] >= 2 ? ld_lab<L2>(p_in + fc[a]) : 0ull;
+            mn[a] = fc[a] >= 2 ? ld_lab<L2>(m_in + fc[a]) : 0ull;
+        }
+        uint64_t pa[6], ma[6], gt, lt;
+        point_neighbours(Pw, pn, pa);
+        point_neighbours(Mw, mn, ma);
+        majority(pa, ma, gt, lt);
+        Pn |= U & gt;
+        Mn |= U & lt;
+        changed = (U & (gt | lt)) != 0ull;
+    }
+    p_out[p] = Pn;
+    m_out[p] = Mn;
+    return changed;
+}
+
+// one Jacobi sweep of the point flood, a thread per active package
 __global__ void __launch_bounds__(CC_THREADS) k_cc_flood_points(const int32_t* __restrict__ faces,
                                                                  const uint64_t* __restrict__ p_in,
                                                                  const uint64_t* __restrict__ m_in,
                                                                  uint64_t* __restrict__ p_out,
                                                                  uint64_t* __restrict__ m_out, int64_t P, int* flag) {
     bool changed = false;
-    for (int64_t p = 2 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t Pw = p_in[p], Mw = m_in[p], U = ~(Pw | Mw);
-        uint64_t Pn = Pw, Mn = Mw;
-        if (U) {
-            const int4 f0 = __ldg(reinterpret_cast<const int4*>(faces + p * 8));
-            const int2 f1 = __ldg(reinterpret_cast<const int2*>(faces + p * 8 + 4));
-            const int32_t fc[6] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y};
-            uint64_t pn[6], mn[6];
-#pragma unroll
-            for (int a = 0; a < 6; ++a) {
-                pn[a] = fc[a] >= 2 ? p_in[fc[a]] : 0ull;
-                mn[a] = fc[a] >= 2 ? m_in[fc[a]] : 0ull;
-            }
-            uint64_t pa[6], ma[6], gt, lt;
-            point_neighbours(Pw, pn, pa);
-            point_neighbours(Mw, mn, ma);
-            majority(pa, ma, gt, lt);
-            Pn |= U & gt;
-            Mn |= U & lt;
-            changed |= (U & (gt | lt)) != 0ull;
-        }
-        p_out[p] = Pn;
-        m_out[p] = Mn;
-    }
+    for (int64_t p = 2 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x)
+        changed |= point_sweep_one<false>(faces, p_in, m_in, p_out, m_out, p);
     flag_if_any(changed, flag);
 }
 
@@ -213,10 +229,46 @@ __global__ void __launch_bounds__(CC_THREADS) k_cc_seed_words(const int32_t* __r
     }
 }
 
-// one Jacobi sweep of the cell flood, a thread per word: an unknown open
-// cell takes + where more of its face neighbours are + than -, - where more
-// are -, exactly as the sign of the sum of their signs (blocked and unknown
-// neighbours count 0; neighbours outside the mesh do not exist)
+// One word of a cell sweep: an unknown open cell takes + where more of its
+// face neighbours are + than -, - where more are -, exactly as the sign of
+// the sum of their signs (blocked and unknown neighbours count 0;
+// neighbours outside the mesh do not exist).  Returns whether a label was
+// set.
+template <bool L2>
+__device__ __forceinline__ bool cell_sweep_one(const uint32_t* __restrict__ open, const uint32_t* p_in,
+                                               const uint32_t* m_in, uint32_t* p_out, uint32_t* m_out, int64_t w,
+                                               int nwx, int ny, int nz) {
+    const uint32_t P = ld_lab<L2>(p_in + w), M = ld_lab<L2>(m_in + w);
+    const uint32_t U = __ldg(open + w) & ~(P | M);
+    uint32_t Pn = P, Mn = M;
+    bool changed = false;
+    if (U) {
+        // 32-bit index arithmetic: nw <= nx ny nz < 2^31
+        const uint32_t u = (uint32_t)w, r = u / (uint32_t)nwx, x = u - r * (uint32_t)nwx;
+        const uint32_t K = r / (uint32_t)ny, J = r - K * (uint32_t)ny;
+        const int64_t sy = nwx, sz = (int64_t)nwx * ny;
+        const bool xl = x > 0, xr = x + 1 < (uint32_t)nwx, yl = J > 0, yr = J + 1 < (uint32_t)ny, zl = K > 0,
+                   zr = K + 1 < (uint32_t)nz;
+        const uint32_t Pl = xl ? ld_lab<L2>(p_in + w - 1) : 0u, Pr = xr ? ld_lab<L2>(p_in + w + 1) : 0u;
+        const uint32_t Ml = xl ? ld_lab<L2>(m_in + w - 1) : 0u, Mr = xr ? ld_lab<L2>(m_in + w + 1) : 0u;
+        const uint32_t pa[6] = {(P << 1) | (Pl >> 31), (P >> 1) | (Pr << 31),
+                                yl ? ld_lab<L2>(p_in + w - sy) : 0u, yr ? ld_lab<L2>(p_in + w + sy) : 0u,
+                                zl ? ld_lab<L2>(p_in + w - sz) : 0u, zr ? ld_lab<L2>(p_in + w + sz) : 0u};
+        const uint32_t ma[6] = {(M << 1) | (Ml >> 31), (M >> 1) | (Mr << 31),
+                                yl ? ld_lab<L2>(m_in + w - sy) : 0u, yr ? ld_lab<L2>(m_in + w + sy) : 0u,
+                                zl ? ld_lab<L2>(m_in + w - sz) : 0u, zr ? ld_lab<L2>(m_in + w + sz) : 0u};
+        uint32_t gt, lt;
+        majority(pa, ma, gt, lt);
+        Pn |= U & gt;
+        Mn |= U & lt;
+        changed = (U & (gt | lt)) != 0u;
+    }
+    p_out[w] = Pn;
+    m_out[w] = Mn;
+    return changed;
+}
+
+// one Jacobi sweep of the cell flood, a thread per word
 __global__ void __launch_bounds__(CC_THREADS) k_cc_flood_words(const uint32_t* __restrict__ open,
                                                                 const uint32_t* __restrict__ p_in,
                                                                 const uint32_t* __restrict__ m_in,
@@ -224,33 +276,112 @@ __global__ void __launch_bounds__(CC_THREADS) k_cc_flood_words(const uint32_t* _
                                                                 int nwx, int ny, int nz, int* flag) {
     const int64_t nw = (int64_t)nwx * ny * nz;
     bool changed = false;
-    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t P = p_in[w], M = m_in[w];
-        const uint32_t U = open[w] & ~(P | M);
-        uint32_t Pn = P, Mn = M;
-        if (U) {
-            // 32-bit index arithmetic: nw <= nx ny nz < 2^31
-            const uint32_t u = (uint32_t)w, r = u / (uint32_t)nwx, x = u - r * (uint32_t)nwx;
-            const uint32_t K = r / (uint32_t)ny, J = r - K * (uint32_t)ny;
-            const int64_t sy = nwx, sz = (int64_t)nwx * ny;
-            const bool xl = x > 0, xr = x + 1 < (uint32_t)nwx, yl = J > 0, yr = J + 1 < (uint32_t)ny, zl = K > 0,
-                       zr = K + 1 < (uint32_t)nz;
-            const uint32_t Pl = xl ? p_in[w - 1] : 0u, Pr = xr ? p_in[w + 1] : 0u;
-            const uint32_t Ml = xl ? m_in[w - 1] : 0u, Mr = xr ? m_in[w + 1] : 0u;
-            const uint32_t pa[6] = {(P << 1) | (Pl >> 31), (P >> 1) | (Pr << 31), yl ? p_in[w - sy] : 0u,
-                                    yr ? p_in[w + sy] : 0u, zl ? p_in[w - sz] : 0u, zr ? p_in[w + sz] : 0u};
-            const uint32_t ma[6] = {(M << 1) | (Ml >> 31), (M >> 1) | (Mr << 31), yl ? m_in[w - sy] : 0u,
-                                    yr ? m_in[w + sy] : 0u, zl ? m_in[w - sz] : 0u, zr ? m_in[w + sz] : 0u};
-            uint32_t gt, lt;
-            majority(pa, ma, gt, lt);
-            Pn |= U & gt;
-            Mn |= U & lt;
-            changed |= (U & (gt | lt)) != 0u;
-        }
-        p_out[w] = Pn;
-        m_out[w] = Mn;
-    }
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x)
+        changed |= cell_sweep_one<false>(open, p_in, m_in, p_out, m_out, w, nwx, ny, nz);
     flag_if_any(changed, flag);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent floods: every sweep of a flood in one cooperative launch (all
+// CTAs resident), the sweeps separated by a grid barrier of the library's
+// own whose waits are bounded: a CTA that waits longer than CC_SPIN_LIMIT
+// polls sets `err` and returns, and the others then give up at their next
+// barrier, so the launch always ends.  `chg` rotates over three slots: the
+// slot of sweep s is final after barrier s, read by every CTA, and cleared
+// (as slot s + 2) by CTA 0 after barrier s + 1, when every CTA has read it.
+struct FloodSync {
+    unsigned arrive;   // CTAs arrived at the current barrier
+    unsigned gen;      // barriers completed
+    int chg[3];        // per-sweep change flags
+    int err;           // 1: a barrier wait gave up, 2: no fixed point within the sweep bound
+    int sweeps;        // sweeps up to and including the first that changed nothing
+};
+constexpr unsigned CC_SPIN_LIMIT = 1u << 21;  // polls of at least 100 ns: about 0.2 s and more
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// all CTAs of the launch; false when a wait gave up (then `err` is set)
+__device__ bool grid_barrier(FloodSync* fs, unsigned& gen) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned target = gen + 1;
+        __threadfence();  // this CTA's label stores and flag updates before its arrival
+        if (atomicAdd(&fs->arrive, 1u) == gridDim.x - 1) {
+            atomicExch(&fs->arrive, 0u);  // reset before the release: no CTA arrives again before it
+            __threadfence();
+            atomicExch(&fs->gen, target);
+        } else {
+            unsigned polls = 0;
+            while (ld_acquire(&fs->gen) != target) {
+                if (++polls > CC_SPIN_LIMIT) {
+                    atomicExch(&fs->err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        gen = target;
+        s_ok = ok && ld_acquire((const unsigned*)&fs->err) == 0u;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// after barrier `sw`: whether the flood goes on (CTA 0 records the end)
+__device__ __forceinline__ bool flood_continues(FloodSync* fs, int64_t sw) {
+    const unsigned c = ld_acquire((const unsigned*)&fs->chg[sw % 3]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        fs->chg[(sw + 2) % 3] = 0;
+        if (c == 0u) fs->sweeps = (int)(sw + 1);
+    }
+    return c != 0u;
+}
+
+// a = plus plane then minus plane (P words each), b the same; the fixed
+// point ends in both
+__global__ void __launch_bounds__(CC_THREADS) k_cc_flood_points_coop(const int32_t* __restrict__ faces, uint64_t* a,
+                                                                      uint64_t* b, int64_t P, int64_t max_sweeps,
+                                                                      FloodSync* fs) {
+    unsigned gen = 0;
+    for (int64_t sw = 0; sw < max_sweeps; ++sw) {
+        const uint64_t* src = (sw & 1) ? b : a;
+        uint64_t* dst = (sw & 1) ? a : b;
+        bool changed = false;
+        for (int64_t p = 2 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P;
+             p += (int64_t)gridDim.x * blockDim.x)
+            changed |= point_sweep_one<true>(faces, src, src + P, dst, dst + P, p);
+        flag_if_any(changed, &fs->chg[sw % 3]);
+        if (!grid_barrier(fs, gen)) return;
+        if (!flood_continues(fs, sw)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&fs->err, 2);
+}
+
+// a = plus plane then minus plane (nw words each), b the same
+__global__ void __launch_bounds__(CC_THREADS) k_cc_flood_words_coop(const uint32_t* __restrict__ open, uint32_t* a,
+                                                                     uint32_t* b, int nwx, int ny, int nz,
+                                                                     int64_t max_sweeps, FloodSync* fs) {
+    const int64_t nw = (int64_t)nwx * ny * nz;
+    unsigned gen = 0;
+    for (int64_t sw = 0; sw < max_sweeps; ++sw) {
+        const uint32_t* src = (sw & 1) ? b : a;
+        uint32_t* dst = (sw & 1) ? a : b;
+        bool changed = false;
+        for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x)
+            changed |= cell_sweep_one<true>(open, src, src + nw, dst, dst + nw, w, nwx, ny, nz);
+        flag_if_any(changed, &fs->chg[sw % 3]);
+        if (!grid_barrier(fs, gen)) return;
+        if (!flood_continues(fs, sw)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&fs->err, 2);
 }
 
 // far cells take their label's far package; counts the moves
@@ -309,6 +440,38 @@ size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 // words of one bit plane of the cell flood
 int64_t plane_words(const int32_t dims[3]) { return (int64_t)((dims[0] + 31) / 32) * dims[1] * dims[2]; }
 
+// CTAs of a cooperative launch of `kernel`: all resident at once (the
+// occupancy on every SM), no more than the entries need; 0 when the device
+// cannot launch cooperatively
+int coop_blocks(const void* kernel, int64_t n, int device) {
+    int coop = 0, per_sm = 0, sms = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, CC_THREADS, 0) != cudaSuccess || per_sm < 1)
+        return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1) return 0;
+    const int64_t need = (n + CC_THREADS - 1) / CC_THREADS;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)per_sm * sms));
+}
+
+// One persistent flood: reset the sync block, launch, read back its end
+// state (host-synchronising).  Gives cudaErrorLaunchTimeout when a barrier
+// wait gave up or no fixed point came within the sweep bound.
+template <class... Args>
+cudaError_t run_coop_flood(void (*kernel)(Args...), int blocks, FloodSync* fs, FloodSync* hfs, int64_t& sweeps,
+                           cudaStream_t s, Args... args) {
+    cudaError_t e = cudaMemsetAsync(fs, 0, sizeof(FloodSync), s);
+    if (e != cudaSuccess) return e;
+    void* argv[] = {(void*)&args...};
+    e = cudaLaunchCooperativeKernel((const void*)kernel, dim3((unsigned)blocks), dim3(CC_THREADS), argv, 0, s);
+    note_launch();
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(hfs, fs, sizeof(FloodSync), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (hfs->err != 0) return cudaErrorLaunchTimeout;
+    sweeps = hfs->sweeps;
+    return cudaSuccess;
+}
+
 }  // namespace
 
 size_t consistency_scratch_bytes(int64_t P, const int32_t dims[3]) {
@@ -332,10 +495,15 @@ cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cel
     sp += al256(2 * (size_t)nw * sizeof(uint32_t));
     uint32_t* lb = (uint32_t*)sp;
     sp += al256(2 * (size_t)nw * sizeof(uint32_t));
-    int* dflag = (int*)sp;                                               // CC_BATCH ints
+    int* dflag = (int*)sp;                                               // CC_BATCH ints, or
+    FloodSync* fs = (FloodSync*)sp;                                      // the persistent floods' sync block
     unsigned long long* cnt = (unsigned long long*)(sp + 64);            // 2 counters
-    int* hflag = (int*)host_pin;                                         // CC_BATCH ints
+    int* hflag = (int*)host_pin;                                         // the same on the host
+    FloodSync* hfs = (FloodSync*)host_pin;
     unsigned long long* hcnt = (unsigned long long*)((char*)host_pin + 64);  // 2 counters
+    static_assert(sizeof(FloodSync) <= 64 && CC_BATCH * sizeof(int) <= 64, "sync block and flags fit 64 bytes");
+    int device = 0;
+    cudaGetDevice(&device);
     const int64_t n_act = (P - 2) * PKG3;
     cudaError_t e;
     if ((e = cudaMemsetAsync(sa, 0, 2 * (size_t)P * sizeof(uint64_t), s)) != cudaSuccess) return e;
@@ -345,13 +513,19 @@ cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cel
     if (n_act > 0) {
         k_cc_seed_points<<<cc_blocks(n_act), CC_THREADS, 0, s>>>(phi, (uint32_t*)sa, (uint32_t*)(sa + P), n_act, tau);
         note_launch();
-        const unsigned nb = cc_blocks(P - 2);
-        e = flood(
-            [&](const uint64_t* src, uint64_t* dst, int* flag) {
-                k_cc_flood_points<<<nb, CC_THREADS, 0, s>>>(faces, src, src + P, dst, dst + P, P, flag);
-                note_launch();
-            },
-            sa, sb, dflag, hflag, n_act + 1, sweeps_pt, s);
+        const int cbp = coop_blocks((const void*)k_cc_flood_points_coop, P - 2, device);
+        if (cbp > 0) {
+            e = run_coop_flood(k_cc_flood_points_coop, cbp, fs, hfs, sweeps_pt, s, (const int32_t*)faces, sa, sb, P,
+                               n_act + 1, fs);
+        } else {
+            const unsigned nb = cc_blocks(P - 2);
+            e = flood(
+                [&](const uint64_t* src, uint64_t* dst, int* flag) {
+                    k_cc_flood_points<<<nb, CC_THREADS, 0, s>>>(faces, src, src + P, dst, dst + P, P, flag);
+                    note_launch();
+                },
+                sa, sb, dflag, hflag, n_act + 1, sweeps_pt, s);
+        }
         if (e != cudaSuccess) return e;
         k_cc_apply<<<cc_blocks(n_act / 4), CC_THREADS, 0, s>>>(reinterpret_cast<float4*>(phi), (const uint32_t*)sa,
                                                                 (const uint32_t*)(sa + P), n_act / 4, cnt);
@@ -360,13 +534,19 @@ cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cel
     k_cc_seed_words<<<cc_blocks(32 * nw), CC_THREADS, 0, s>>>(cell_pkg, pkg_type, sa, sa + P, open, la, la + nw, nx, nwx,
                                                               32 * nw);
     note_launch();
-    const unsigned cb = cc_blocks(nw);
-    e = flood(
-        [&](const uint32_t* src, uint32_t* dst, int* flag) {
-            k_cc_flood_words<<<cb, CC_THREADS, 0, s>>>(open, src, src + nw, dst, dst + nw, nwx, ny, nz, flag);
-            note_launch();
-        },
-        la, lb, dflag, hflag, nc + 1, sweeps_cell, s);
+    const int cbw = coop_blocks((const void*)k_cc_flood_words_coop, nw, device);
+    if (cbw > 0) {
+        e = run_coop_flood(k_cc_flood_words_coop, cbw, fs, hfs, sweeps_cell, s, (const uint32_t*)open, la, lb, nwx, ny,
+                           nz, nc + 1, fs);
+    } else {
+        const unsigned cb = cc_blocks(nw);
+        e = flood(
+            [&](const uint32_t* src, uint32_t* dst, int* flag) {
+                k_cc_flood_words<<<cb, CC_THREADS, 0, s>>>(open, src, src + nw, dst, dst + nw, nwx, ny, nz, flag);
+                note_launch();
+            },
+            la, lb, dflag, hflag, nc + 1, sweeps_cell, s);
+    }
     if (e != cudaSuccess) return e;
     k_cc_far<<<cc_blocks(nc), CC_THREADS, 0, s>>>(cell_pkg, la, la + nw, nx, nwx, nc, cnt + 1);
     note_launch();
