@@ -215,8 +215,10 @@ SG_API sg_status sg_gradient(sg_grid *g);
  * that changes nothing).  Derived fields (g, W, ...) are stale
  * afterwards.  Blocks until done (it reads convergence flags).
  * Errors: SG_ERR_INVALID (trust <= 0 or not finite), SG_ERR_STATE (no phi),
- * SG_ERR_OOM, SG_ERR_TIMEOUT (a flood that does not settle; cannot happen
- * for valid tables). */
+ * SG_ERR_OOM, SG_ERR_TIMEOUT (a flood that does not settle, which cannot
+ * happen for valid tables, or a grid-barrier wait of a persistent flood
+ * that gave up after its bounded number of polls; phi is then unchanged if
+ * it was the point flood). */
 SG_API sg_status sg_consistency_correct(sg_grid *g, float trust, int64_t *out);
 
 /* The "sequential" benchmark of "Performance Evaluation": a small change to
