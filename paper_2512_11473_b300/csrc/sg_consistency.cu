@@ -324,7 +324,7 @@ __device__ bool grid_barrier(FloodSync* fs, unsigned& gen) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(100);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -440,9 +440,11 @@ size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 // words of one bit plane of the cell flood
 int64_t plane_words(const int32_t dims[3]) { return (int64_t)((dims[0] + 31) / 32) * dims[1] * dims[2]; }
 
-// CTAs of a cooperative launch of `kernel`: all resident at once (the
-// occupancy on every SM), no more than the entries need; 0 when the device
-// cannot launch cooperatively
+// CTAs of a cooperative launch of `kernel`: all resident at once, at most
+// three per SM (fewer CTAs at each barrier; on the h = 0.002 torus 1, 2, 3
+// and 4 per SM took 1.63, 1.35, 1.34 and about 1.4 ms for the correction),
+// no more than the entries need; 0 when the device cannot launch
+// cooperatively
 int coop_blocks(const void* kernel, int64_t n, int device) {
     int coop = 0, per_sm = 0, sms = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop) return 0;
@@ -450,7 +452,7 @@ int coop_blocks(const void* kernel, int64_t n, int device) {
         return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1) return 0;
     const int64_t need = (n + CC_THREADS - 1) / CC_THREADS;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)per_sm * sms));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)std::min(per_sm, 3) * sms));
 }
 
 // One persistent flood: reset the sync block, launch, read back its end
