@@ -221,6 +221,16 @@ SG_API sg_status sg_gradient(sg_grid *g);
  * it was the point flood). */
 SG_API sg_status sg_consistency_correct(sg_grid *g, float trust, int64_t *out);
 
+/* Testing hook for the bounded waits of the persistent floods: runs
+ * sg_consistency_correct(g, trust, NULL) with one CTA counted at every grid
+ * barrier that never arrives, so the first barrier (of the point flood, or
+ * of the cell flood when there are no active points) cannot complete: every
+ * CTA gives up after its bounded number of polls (about a second) and the
+ * call returns SG_ERR_TIMEOUT with phi and the tables unchanged and the
+ * grid usable.  Errors: as sg_consistency_correct, SG_ERR_DEVICE (a device
+ * without cooperative launch, where the floods do not wait on one another). */
+SG_API sg_status sg_debug_consistency_absent_cta(sg_grid *g, float trust);
+
 /* The "sequential" benchmark of "Performance Evaluation": a small change to
  * every active value, phi <- phi + delta on every active package (far
  * packages untouched).  Requires phi. */

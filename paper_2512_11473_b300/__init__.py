@@ -92,6 +92,7 @@ def lib():
         L.sg_laplacian.argtypes = [vp]
         L.sg_sequential_update.argtypes = [vp, C.c_float]
         L.sg_consistency_correct.argtypes = [vp, C.c_float, C.POINTER(i64)]
+        L.sg_debug_consistency_absent_cta.argtypes = [vp, C.c_float]
         L.sg_tag_allocate_from.argtypes = [vp, vp, C.POINTER(sg_shape), C.POINTER(i64), C.POINTER(i64)]
         L.sg_multires_layers.argtypes = [C.POINTER(sg_grid_desc), i32]
         L.sg_multires_layers.restype = i32
@@ -294,6 +295,12 @@ class Grid:
         out = (C.c_int64 * 4)()
         self._check(self._lib.sg_consistency_correct(self._h, float(trust), out))
         return tuple(int(v) for v in out)
+
+    def debug_consistency_absent_cta(self, trust=1.0):
+        """Testing hook: the correction with a CTA that never reaches the
+        floods' grid barriers; raises SgError (SG_ERR_TIMEOUT) once the
+        bounded waits give up, with phi and the tables unchanged."""
+        self._check(self._lib.sg_debug_consistency_absent_cta(self._h, float(trust)))
 
     def sequential_update(self, delta):
         """phi <- phi + delta on every active value (the paper's sequential benchmark)."""

@@ -424,7 +424,7 @@ sg_status sg_gradient(sg_grid* g) {
     return SG_OK;
 }
 
-sg_status sg_consistency_correct(sg_grid* g, float trust, int64_t* out) {
+static sg_status consistency(sg_grid* g, float trust, int64_t* out, unsigned absent) {
     SG_CHECK_GRID(g);
     if (!(trust > 0.0f) || !std::isfinite(trust)) return fail(g, SG_ERR_INVALID, "sg_consistency_correct: bad trust");
     if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_consistency_correct: phi not initialised");
@@ -436,12 +436,21 @@ sg_status sg_consistency_correct(sg_grid* g, float trust, int64_t* out) {
         run_consistency(grid_ff(g), g->P, g->nc, (int32_t*)g->cell_pkg.p, (const int32_t*)g->pkg_cell.p,
                         (const uint8_t*)g->pkg_type.p, (int32_t*)g->nbr.p, (int32_t*)g->faces.p,
                         (float*)g->field[SG_FIELD_PHI].p, (float)((double)trust * g->desc.h), g->scratch.p,
-                        g->host_pin.p, o, g->stream);
-    if (e == cudaErrorLaunchTimeout) return fail(g, SG_ERR_TIMEOUT, "sg_consistency_correct: flood did not settle");
+                        g->host_pin.p, o, g->stream, absent);
+    if (e == cudaErrorLaunchTimeout) return fail(g, SG_ERR_TIMEOUT, "sg_consistency_correct: flood did not settle or a barrier wait gave up");
     if (e != cudaSuccess) return cuda_fail(g, e, "consistency correction");
     if (out)
         for (int i = 0; i < 4; ++i) out[i] = o[i];
     return SG_OK;
+}
+
+sg_status sg_consistency_correct(sg_grid* g, float trust, int64_t* out) { return consistency(g, trust, out, 0); }
+
+sg_status sg_debug_consistency_absent_cta(sg_grid* g, float trust) {
+    SG_CHECK_GRID(g);
+    if (!consistency_persistent(g->device))
+        return fail(g, SG_ERR_DEVICE, "sg_debug_consistency_absent_cta: no cooperative launch on this device");
+    return consistency(g, trust, nullptr, 1);
 }
 
 sg_status sg_sequential_update(sg_grid* g, float delta) {

@@ -295,6 +295,7 @@ struct FloodSync {
     int chg[3];        // per-sweep change flags
     int err;           // 1: a barrier wait gave up, 2: no fixed point within the sweep bound
     int sweeps;        // sweeps up to and including the first that changed nothing
+    unsigned absent;   // CTAs counted at every barrier that never arrive: 0, or 1 to test the bounded waits
 };
 constexpr unsigned CC_SPIN_LIMIT = 1u << 21;  // polls of at least 100 ns: about 0.2 s and more
 
@@ -312,7 +313,7 @@ __device__ bool grid_barrier(FloodSync* fs, unsigned& gen) {
         int ok = 1;
         const unsigned target = gen + 1;
         __threadfence();  // this CTA's label stores and flag updates before its arrival
-        if (atomicAdd(&fs->arrive, 1u) == gridDim.x - 1) {
+        if (atomicAdd(&fs->arrive, 1u) == gridDim.x - 1 + fs->absent) {
             atomicExch(&fs->arrive, 0u);  // reset before the release: no CTA arrives again before it
             __threadfence();
             atomicExch(&fs->gen, target);
@@ -460,9 +461,11 @@ int coop_blocks(const void* kernel, int64_t n, int device) {
 // state (host-synchronising).  Gives cudaErrorLaunchTimeout when a barrier
 // wait gave up or no fixed point came within the sweep bound.
 template <class... Args>
-cudaError_t run_coop_flood(void (*kernel)(Args...), int blocks, FloodSync* fs, FloodSync* hfs, int64_t& sweeps,
-                           cudaStream_t s, Args... args) {
-    cudaError_t e = cudaMemsetAsync(fs, 0, sizeof(FloodSync), s);
+cudaError_t run_coop_flood(void (*kernel)(Args...), int blocks, FloodSync* fs, FloodSync* hfs, unsigned absent,
+                           int64_t& sweeps, cudaStream_t s, Args... args) {
+    *hfs = FloodSync{};  // pinned; free: the stream was synchronised after the last read-back
+    hfs->absent = absent;
+    cudaError_t e = cudaMemcpyAsync(fs, hfs, sizeof(FloodSync), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     void* argv[] = {(void*)&args...};
     e = cudaLaunchCooperativeKernel((const void*)kernel, dim3((unsigned)blocks), dim3(CC_THREADS), argv, 0, s);
@@ -477,6 +480,11 @@ cudaError_t run_coop_flood(void (*kernel)(Args...), int blocks, FloodSync* fs, F
 
 }  // namespace
 
+bool consistency_persistent(int device) {
+    int coop = 0;
+    return cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) == cudaSuccess && coop != 0;
+}
+
 size_t consistency_scratch_bytes(int64_t P, const int32_t dims[3]) {
     const size_t plane = (size_t)plane_words(dims) * sizeof(uint32_t);
     return 2 * al256(2 * (size_t)P * sizeof(uint64_t)) + al256(plane) + 2 * al256(2 * plane) + 256;
@@ -484,7 +492,7 @@ size_t consistency_scratch_bytes(int64_t P, const int32_t dims[3]) {
 
 cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cell_pkg, const int32_t* pkg_cell,
                             const uint8_t* pkg_type, int32_t* nbr, int32_t* faces, float* phi, float tau,
-                            void* scratch, void* host_pin, int64_t out[4], cudaStream_t s) {
+                            void* scratch, void* host_pin, int64_t out[4], cudaStream_t s, unsigned absent) {
     char* sp = (char*)scratch;
     uint64_t* sa = (uint64_t*)sp;  // point planes: plus (P words), then minus (P words)
     sp += al256(2 * (size_t)P * sizeof(uint64_t));
@@ -518,7 +526,7 @@ cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cel
         note_launch();
         const int cbp = coop_blocks((const void*)k_cc_flood_points_coop, P - 2, device);
         if (cbp > 0) {
-            e = run_coop_flood(k_cc_flood_points_coop, cbp, fs, hfs, sweeps_pt, s, (const int32_t*)faces, sa, sb, P,
+            e = run_coop_flood(k_cc_flood_points_coop, cbp, fs, hfs, absent, sweeps_pt, s, (const int32_t*)faces, sa, sb, P,
                                n_act + 1, fs);
         } else {
             const unsigned nb = cc_blocks(P - 2);
@@ -539,7 +547,7 @@ cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cel
     note_launch();
     const int cbw = coop_blocks((const void*)k_cc_flood_words_coop, nw, device);
     if (cbw > 0) {
-        e = run_coop_flood(k_cc_flood_words_coop, cbw, fs, hfs, sweeps_cell, s, (const uint32_t*)open, la, lb, nwx, ny,
+        e = run_coop_flood(k_cc_flood_words_coop, cbw, fs, hfs, absent, sweeps_cell, s, (const uint32_t*)open, la, lb, nwx, ny,
                            nz, nc + 1, fs);
     } else {
         const unsigned cb = cc_blocks(nw);

@@ -116,3 +116,24 @@ def test_consistency_bad_trust(sg):
     for t in (0.0, -1.0, float("nan")):
         with pytest.raises(sg.SgError):
             g.consistency_correct(t)
+
+
+def test_flood_barrier_wait_gives_up(sg):
+    """A CTA that never reaches the persistent floods' grid barrier: the
+    bounded waits give up, the call reports SG_ERR_TIMEOUT, nothing changed,
+    and the grid (and the context) still work."""
+    shape, spec = BODIES["sphere"]()
+    g = sg.Grid(spec)
+    g.tag_allocate(shape)
+    g.init_sdf(shape)
+    before = {k: g.field(k).clone() for k in ("phi", "cell_pkg", "nbr")}
+    with pytest.raises(sg.SgError) as e:
+        g.debug_consistency_absent_cta(1.0)
+    assert e.value.status == sg.SG_ERR_TIMEOUT
+    for k, v in before.items():
+        assert torch.equal(g.field(k), v), k
+    out = g.consistency_correct(1.0)
+    assert out[:2] == (0, 0)
+    for k, v in before.items():
+        assert torch.equal(g.field(k), v), k
+    g.close()
