@@ -246,18 +246,22 @@ def probe(spec, cell_pkg, nbr, fields, x, y, z):
     return tuple(outs)
 
 
-def consistency_correct(spec, P, cell_pkg, pkg_cell, pkg_type, nbr, phi, trust=1.0):
+def consistency_correct(spec, P, cell_pkg, pkg_cell, pkg_type, nbr, phi, trust=1.0, sweeps=False):
     """Consistency (sign) correction with trusted band |phi| < trust * h
     (trust * h rounded to float32, as the device takes it).  Returns
-    (cell_pkg, nbr, phi, (points flipped, far cells moved)), all copies."""
+    (cell_pkg, nbr, phi, (points flipped, far cells moved)), all copies, and
+    with sweeps=True also (point sweeps, cell sweeps), each up to and
+    including the first sweep that labels nothing."""
     cp = np.array(cell_pkg, np.int32, copy=True)
     nb = np.array(nbr, np.int32, copy=True, order="C")
     ph = np.array(phi, np.float64, copy=True, order="C")
-    ch = (C.c_int64 * 2)()
+    ch = (C.c_int64 * 4)()
     tau = float(np.float32(float(np.float32(trust)) * spec.h))  # as the library takes it
     lib().or_consistency_correct(C.byref(_grid(spec)), C.c_int64(int(P)), _p(cp),
                                  _p(np.ascontiguousarray(pkg_cell, np.int32)),
                                  _p(np.ascontiguousarray(pkg_type, np.uint8)), _p(nb), _p(ph), C.c_double(tau), ch)
+    if sweeps:
+        return cp, nb, ph, (int(ch[0]), int(ch[1])), (int(ch[2]), int(ch[3]))
     return cp, nb, ph, (int(ch[0]), int(ch[1]))
 
 

@@ -651,7 +651,9 @@ void or_probe(const or_grid *g, const int32_t *cell_pkg, const int32_t *nbr, con
 /*    neighbour table follows.                                               */
 /* The point step runs first: every point within h of the surface lies in a  */
 /* core cell, so the cells have no trusted sign until the points have one.   */
-/* changed[0] counts points whose sign flipped, changed[1] far cells moved.  */
+/* changed[0] counts points whose sign flipped, changed[1] far cells moved, */
+/* changed[2] and changed[3] the point and cell sweeps, each up to and       */
+/* including the first sweep that labels nothing.                            */
 /* ------------------------------------------------------------------------- */
 #define CC_BLOCK 2
 static int face_step(const or_grid *g, int64_t c, int f, int64_t *out) {
@@ -667,9 +669,9 @@ static int face_step(const or_grid *g, int64_t c, int f, int64_t *out) {
 }
 
 void or_consistency_correct(const or_grid *g, int64_t P, int32_t *cell_pkg, const int32_t *pkg_cell,
-                            const uint8_t *pkg_type, int32_t *nbr, double *phi, double tau, int64_t changed[2]) {
+                            const uint8_t *pkg_type, int32_t *nbr, double *phi, double tau, int64_t changed[4]) {
     const int64_t nx = g->dims[0], ny = g->dims[1], nz = g->dims[2], nc = nx * ny * nz;
-    changed[0] = changed[1] = 0;
+    changed[0] = changed[1] = changed[2] = changed[3] = 0;
     /* points: trusted seeds */
     const int64_t np = P * PKG3;
     int8_t *sg = (int8_t *)calloc((size_t)np, 1), *sn = (int8_t *)calloc((size_t)np, 1);
@@ -680,6 +682,7 @@ void or_consistency_correct(const or_grid *g, int64_t P, int32_t *cell_pkg, cons
     /* points: flood over the face neighbours inside active packages */
     for (;;) {
         int64_t moved = 0;
+        ++changed[2];
         memcpy(sn, sg, (size_t)np);
         for (int64_t p = 2; p < P; ++p) {
             const int32_t *nb = nbr + p * 27;
@@ -729,6 +732,7 @@ void or_consistency_correct(const or_grid *g, int64_t P, int32_t *cell_pkg, cons
     /* cells: flood */
     for (;;) {
         int64_t moved = 0;
+        ++changed[3];
         memcpy(nxt, lab, (size_t)nc);
         for (int64_t c = 0; c < nc; ++c) {
             if (lab[c] != 0) continue;

@@ -412,7 +412,8 @@ __global__ void __launch_bounds__(CC_THREADS) k_cc_far(int32_t* __restrict__ cel
 }
 
 // Jacobi sweeps in batches of CC_BATCH until one changes nothing; `a` ends
-// on the fixed point.  Host-synchronising.
+// on the fixed point and `sweeps` counts up to the first sweep that changed
+// nothing.  Host-synchronising.
 constexpr int CC_BATCH = 8;
 
 template <class Sweep, class T>
@@ -431,7 +432,12 @@ cudaError_t flood(Sweep sweep, T*& a, T*& b, int* dflag, int* hflag, int64_t max
         if (e == cudaSuccess) e = cudaMemcpyAsync(hflag, dflag, CC_BATCH * sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
-        if (hflag[CC_BATCH - 1] == 0) return cudaSuccess;
+        if (hflag[CC_BATCH - 1] == 0) {  // count up to the first sweep that changed nothing
+            int k = 0;
+            while (hflag[k] != 0) ++k;
+            sweeps -= CC_BATCH - 1 - k;
+            return cudaSuccess;
+        }
         if (sweeps > max_sweeps) return cudaErrorLaunchTimeout;  // cannot happen: every sweep labels an entry
     }
 }

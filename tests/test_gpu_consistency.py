@@ -88,8 +88,10 @@ def test_consistency_restores_and_matches_oracle(sg, name):
     g.check_tables()  # the rebuilt neighbour and face tables agree with the cells
     g.sync()
     # step-wise: the oracle on the device's noisy float32 input
-    cp2, nb2, phi2, ch = oracle.consistency_correct(spec, O.P, noisy_cp, O.pkg_cell, O.pkg_type, O.nbr, noisy_phi)
+    cp2, nb2, phi2, ch, sw = oracle.consistency_correct(spec, O.P, noisy_cp, O.pkg_cell, O.pkg_type, O.nbr,
+                                                        noisy_phi, sweeps=True)
     assert ch == (out[0], out[1])
+    assert sw == (out[2], out[3])  # the same floods, sweep for sweep
     assert np.array_equal(phi2.astype(np.float32), H(g.field("phi")))
     assert np.array_equal(cp2, H(g.field("cell_pkg")))
     assert np.array_equal(nb2, H(g.field("nbr")))

@@ -88,3 +88,65 @@ def test_consistency_trusted_band_is_kept():
     phi[p, e] = -phi[p, e]
     _, _, phi2, ch = oracle.consistency_correct(spec, G.P, G.cell_pkg, G.pkg_cell, G.pkg_type, G.nbr, phi)
     assert phi2[p, e] == phi[p, e]
+
+
+def _flood_depth(n, edges_a, edges_b, seeds, passable):
+    """1 + the largest graph distance from the seeds over passable entries
+    (multi-source breadth-first search on the face-neighbour graph): the
+    number of Jacobi sweeps of a flood whose fronts never meet, the last one
+    labelling nothing."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import dijkstra
+    keep = passable[edges_a] & passable[edges_b]
+    A = coo_matrix((np.ones(int(keep.sum())), (edges_a[keep], edges_b[keep])), shape=(n, n)).tocsr()
+    d = dijkstra(A, directed=False, indices=np.flatnonzero(seeds), unweighted=True, min_only=True)
+    d = d[passable & np.isfinite(d)]
+    return 1 + int(d.max())
+
+
+@pytest.mark.parametrize("name", sorted(BODIES))
+def test_consistency_sweep_counts_are_flood_depths(name):
+    """On a clean grid the two floods' sweep counts equal one plus the
+    largest breadth-first distance from their seeds: the points from the
+    trusted band through the active packages, the cells from the inner
+    cells through the far cells (core cells block)."""
+    shape, spec = BODIES[name]()
+    G = oracle.build_grid(spec, shape)
+    *_, ch, sw = oracle.consistency_correct(spec, G.P, G.cell_pkg, G.pkg_cell, G.pkg_type, G.nbr, G.phi, sweeps=True)
+    assert ch == (0, 0)
+    # points: graph over the active packages' data points, face neighbours from the 27-entry table
+    P, h = G.P, spec.h
+    tau = float(np.float32(float(np.float32(1.0)) * h))
+    d = np.arange(64)
+    i, j, k = d % 4, (d // 4) % 4, d // 16
+    ea, eb = [], []
+    for axis in range(3):
+        loc = (i, j, k)[axis]
+        up = loc == 3  # the +axis neighbour lies in the next package
+        step = (1, 4, 16)[axis]
+        slot = 13 + (1, 3, 9)[axis]
+        for p in range(2, P):
+            inner = ~up
+            ea.append(p * 64 + d[inner])
+            eb.append(p * 64 + d[inner] + step)
+            q = G.nbr[p, slot]
+            if q >= 2:
+                ea.append(p * 64 + d[up])
+                eb.append(q * 64 + d[up] - 3 * step)
+    ea, eb = np.concatenate(ea), np.concatenate(eb)
+    n = P * 64
+    phi = G.phi.reshape(-1)
+    active = np.zeros(n, bool)
+    active[128:] = True
+    seeds = active & (np.abs(phi) < tau) & (phi != 0)
+    assert sw[0] == _flood_depth(n, ea, eb, seeds, active)
+    # cells: graph over the background mesh, core cells removed
+    nx, ny, nz = spec.dims
+    c = np.arange(nx * ny * nz).reshape(nz, ny, nx)
+    pairs = [(c[:, :, :-1], c[:, :, 1:]), (c[:, :-1, :], c[:, 1:, :]), (c[:-1, :, :], c[1:, :, :])]
+    ca = np.concatenate([a.ravel() for a, _ in pairs])
+    cb = np.concatenate([b.ravel() for _, b in pairs])
+    cp = G.cell_pkg
+    core = (cp >= 2) & (G.pkg_type[np.maximum(cp, 0)] == 2)
+    seeds_c = (cp >= 2) & ~core
+    assert sw[1] == _flood_depth(cp.size, ca, cb, seeds_c, ~core)
