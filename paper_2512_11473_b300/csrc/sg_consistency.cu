@@ -450,7 +450,7 @@ int64_t plane_words(const int32_t dims[3]) { return (int64_t)((dims[0] + 31) / 3
 // CTAs of a cooperative launch of `kernel`: all resident at once, at most
 // three per SM (fewer CTAs at each barrier; on the h = 0.002 torus 1, 2
 // and 3 per SM took 1.63, 1.35 and 1.34 ms for the correction, 4 per SM
-// 1.46 ms with 100 ns between polls),
+// 1.57 ms, and 1.46 ms with 100 ns between polls),
 // no more than the entries need; 0 when the device cannot launch
 // cooperatively
 int coop_blocks(const void* kernel, int64_t n, int device) {
