@@ -61,6 +61,7 @@ def lib():
         for f in ("or_wendland", "or_wendland_dq"):
             getattr(_lib, f).restype = C.c_double
             getattr(_lib, f).argtypes = [C.c_double]
+        _lib.or_lattice_ties.restype = C.c_int64
         _lib.or_heaviside.restype = C.c_double
         _lib.or_heaviside.argtypes = [C.c_double, C.c_double]
     return _lib
@@ -289,6 +290,15 @@ def morton_keys(spec, x, y, z):
     return keys
 
 
+def lattice_ties(spec, x, y, z, tol=1e-9):
+    """Number of particles with a lattice coordinate u = (x - lo)/h - 1/2
+    within tol of an integer on some axis: their cell decision rests on the
+    last bits of the arithmetic."""
+    x, y, z = (np.ascontiguousarray(v, np.float32) for v in (x, y, z))
+    return int(lib().or_lattice_ties(C.byref(_grid(spec)), C.c_int64(x.size), _p(x), _p(y), _p(z),
+                                     C.c_double(tol)))
+
+
 def morton_order(keys):
     keys = np.ascontiguousarray(keys, np.uint64)
     order = np.empty(keys.size, np.int64)
@@ -347,15 +357,18 @@ def surrogate_inputs(spec, nbr, phi):
     return x
 
 
-def surrogate_class(spec, nbr, phi32):
-    """Classes (0 in, 1 out, 2 fallback, 3 network; 255 far) decided in float
-    from the device's float phi, as the device decides them."""
+def surrogate_class(spec, nbr, phi32, ties=False):
+    """Classes (0 in, 1 out, 2 fallback, 3 network; 255 far) of the float
+    field phi32, decided on its real values in double precision.  With
+    ties=True also returns the number of points whose |kappa| h lies within
+    1e-9 (relative) of the 0.1 bound."""
     phi32 = np.ascontiguousarray(phi32, np.float32)
     P = phi32.shape[0]
     cls = np.empty((P, 64), np.uint8)
+    nt = C.c_int64(0)
     lib().or_surrogate_class(C.byref(_grid(spec)), C.c_int64(P), _p(np.ascontiguousarray(nbr, np.int32)),
-                             _p(phi32), _p(cls))
-    return cls
+                             _p(phi32), _p(cls), C.byref(nt))
+    return (cls, int(nt.value)) if ties else cls
 
 
 def coarser(spec):

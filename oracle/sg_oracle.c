@@ -581,22 +581,45 @@ void or_kernel_integrals(const or_grid *g, int64_t P, const int32_t *nbr, const 
 
 /* ------------------------------------------------------------------------- */
 /* Particle probe ("Grid-Particle Coupling"): trilinear interpolation.        */
-/* The fine lattice coordinate is decided in float32 exactly as the device    */
-/* does it:  u = (x - (float)lo) * (float)(1/h) - 0.5f, clamped to +-2^24,    */
-/* i0 = floor(u).  Home cell I = floor(i0 / 4), local l0 = i0 - 4I.  Corners  */
+/* The fine lattice coordinate of a float32 position x is the plain           */
+/* definition in double precision: u = (x - lo) / h - 1/2, i0 = floor(u),     */
+/* t = u - i0 (u clamped to +-2^40 so that far-away particles stay           */
+/* representable).  Home cell I = floor(i0 / 4), local l0 = i0 - 4I.  Corners */
 /* l0 + {0,1} are reached from the home package by the index shift; a home    */
-/* cell outside the domain is the outside far package.  Weights t = u - i0.   */
+/* cell outside the domain is the outside far package.                        */
 /* Outputs (in input order): phi, normal n = g/|g| (0 when |g| = 0), W, G^.   */
 /* ------------------------------------------------------------------------- */
-static void lattice(const or_grid *g, int a, float x, int64_t *i0, double *t) {
-    float lo = (float)g->lo[a], inv_h = (float)(1.0 / g->h);
-    float u = (x - lo) * inv_h - 0.5f;
-    const float lim = 16777216.0f;
+static double lattice_u(const or_grid *g, int a, float x) {
+    double u = ((double)x - g->lo[a]) / g->h - 0.5;
+    const double lim = 1099511627776.0; /* 2^40 */
     if (u < -lim) u = -lim;
     if (u > lim) u = lim;
-    float f = floorf(u);
+    return u;
+}
+
+static void lattice(const or_grid *g, int a, float x, int64_t *i0, double *t) {
+    const double u = lattice_u(g, a, x);
+    const double f = floor(u);
     *i0 = (int64_t)f;
-    *t = (double)u - (double)f;
+    *t = u - f;
+}
+
+/* Particles with some lattice coordinate u within tol of an integer: their  */
+/* cell decision rests on the last bits of the arithmetic (the counterpart of */
+/* the tagging threshold test); a caller comparing decisions asserts none.    */
+int64_t or_lattice_ties(const or_grid *g, int64_t n, const float *x, const float *y, const float *z, double tol) {
+    int64_t ties = 0;
+#pragma omp parallel for schedule(static) reduction(+ : ties)
+    for (int64_t q = 0; q < n; ++q) {
+        const float p[3] = {x[q], y[q], z[q]};
+        int tie = 0;
+        for (int a = 0; a < 3; ++a) {
+            const double u = lattice_u(g, a, p[a]);
+            if (fabs(u - nearbyint(u)) < tol) tie = 1;
+        }
+        ties += tie;
+    }
+    return ties;
 }
 
 void or_probe(const or_grid *g, const int32_t *cell_pkg, const int32_t *nbr, const double *const fields[8], int64_t n,
@@ -972,15 +995,25 @@ void or_surrogate_inputs(const or_grid *g, int64_t P, const int32_t *nbr, const 
     }
 }
 
-/* Classes of the surrogate integral, decided in float exactly as the device
- * decides them (same operations, same order, no contraction): 0 every tap
- * inside (-phi_s / h > 1), 1 every tap outside (< -1), 2 fallback
- * (|phi / h| < 1 or |kappa| h > 0.1, kappa the 7-point Laplacian in float),
- * 3 network.  phi is the device's float field; far packages get 255. */
-void or_surrogate_class(const or_grid *g, int64_t P, const int32_t *nbr, const float *phi, uint8_t *cls) {
-    const float inv_h = (float)(1.0 / g->h), inv_h2 = (float)(1.0 / (g->h * g->h)), h = (float)g->h;
+/* Classes of the surrogate integral (a reading: the network stands in for    */
+/* the kernel integral of "Integral with SPH Smoothing Kernel and Grid-       */
+/* Particle Coupling"), decided on the real values of the float field phi:    */
+/*   0  every one of the 27 taps is inside at or beyond the Heaviside's half  */
+/*      width (-phi_s / h >= 1), where it saturates: W = 1 and G^ = 0;        */
+/*   1  every tap outside (phi_s / h >= 1): W = 0, G^ = 0;                     */
+/*   2  fallback: |phi / h| < 1 at the point, or |kappa| h > 0.1 with kappa    */
+/*      the 7-point Laplacian (phi_+x + phi_-x + ... - 6 phi) / h^2;           */
+/*   3  network.                                                              */
+/* Comparisons are taken in double precision on the float values widened;    */
+/* the tap and |phi| tests are exact, the curvature test is exact up to       */
+/* the rounding of the Laplacian's sum, and *ties counts points whose         */
+/* |kappa| h lies within 1e-9 (relative) of 0.1.  Far packages get 255.       */
+void or_surrogate_class(const or_grid *g, int64_t P, const int32_t *nbr, const float *phi, uint8_t *cls,
+                        int64_t *ties) {
+    const double h = g->h;
+    int64_t nt = 0;
     for (int d = 0; d < 2 * PKG3; ++d) cls[d] = 255;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) reduction(+ : nt)
     for (int64_t p = 2; p < P; ++p) {
         const int32_t *nb = nbr + p * 27;
         for (int d = 0; d < PKG3; ++d) {
@@ -988,10 +1021,9 @@ void or_surrogate_class(const or_grid *g, int64_t P, const int32_t *nbr, const f
             int all_in = 1, all_out = 1;
             for (int n = 0; n < 27; ++n) {
                 int sx = n % 3 - 1, sy = (n / 3) % 3 - 1, sz = n / 9 - 1;
-                float f = phi[shift_index(nb, i + sx, j + sy, k + sz)];
-                float t = (-f) * inv_h;
-                all_in &= t > 1.0f;
-                all_out &= t < -1.0f;
+                double f = (double)phi[shift_index(nb, i + sx, j + sy, k + sz)];
+                all_in &= -f >= h; /* -phi_s / h >= 1 with h > 0, compared without rounding */
+                all_out &= f >= h;
             }
             uint8_t c;
             if (all_in)
@@ -999,14 +1031,15 @@ void or_surrogate_class(const or_grid *g, int64_t P, const int32_t *nbr, const f
             else if (all_out)
                 c = 1;
             else {
-                float v = phi[shift_index(nb, i, j, k)];
-                float c2 = 2.0f * v;
-                float a = (phi[shift_index(nb, i + 1, j, k)] - c2) + phi[shift_index(nb, i - 1, j, k)];
-                a = a + ((phi[shift_index(nb, i, j + 1, k)] - c2) + phi[shift_index(nb, i, j - 1, k)]);
-                a = a + ((phi[shift_index(nb, i, j, k + 1)] - c2) + phi[shift_index(nb, i, j, k - 1)]);
-                float kap = a * inv_h2;
-                float r = v * inv_h;
-                if (fabsf(r) < 1.0f || fabsf(kap) * h > 0.1f)
+                double v = (double)phi[shift_index(nb, i, j, k)];
+                double a = (double)phi[shift_index(nb, i + 1, j, k)] + (double)phi[shift_index(nb, i - 1, j, k)] +
+                           (double)phi[shift_index(nb, i, j + 1, k)] + (double)phi[shift_index(nb, i, j - 1, k)] +
+                           (double)phi[shift_index(nb, i, j, k + 1)] + (double)phi[shift_index(nb, i, j, k - 1)] -
+                           6.0 * v;
+                double kap = a / (h * h);
+                double kh = fabs(kap) * h;
+                if (fabs(kh - 0.1) < 1e-10) ++nt;
+                if (fabs(v) < h || kh > 0.1) /* |phi / h| < 1, compared without rounding */
                     c = 2;
                 else
                     c = 3;
@@ -1014,4 +1047,5 @@ void or_surrogate_class(const or_grid *g, int64_t P, const int32_t *nbr, const f
             cls[p * PKG3 + d] = c;
         }
     }
+    if (ties) *ties = nt;
 }

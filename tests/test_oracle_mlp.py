@@ -91,3 +91,54 @@ def test_integrals_are_a_function_of_the_clipped_inputs():
     w = np.array([oracle.wendland(math.sqrt(q)) for q in q2])
     H = 0.5 * (1.0 - x - np.sin(np.pi * x) / np.pi)
     assert np.max(np.abs(H @ w / w.sum() - W)) < 1e-14
+
+
+def _all_active_grid():
+    """A dyadic grid (h = 1/32) on which every background cell is active, so
+    that every tap of every interior data point is a data point."""
+    spec = si.GridSpec((-0.375, -0.375, -0.375), (6, 6, 6), 1.0 / 32)
+    G = oracle.build_grid(spec, si.sphere(0.25, (0.0, 0.0, 0.0)))
+    assert G.P == 2 + 6 ** 3
+    nx = spec.dims[0]
+    pc = G.pkg_cell.astype(np.int64)
+    I, J, K = pc % nx, (pc // nx) % nx, pc // (nx * nx)
+    d = np.arange(64)
+    X = [spec.lo[a] + (4 * c[:, None] + l + 0.5) * spec.h for a, (c, l) in
+         enumerate(((I, d % 4), (J, (d // 4) % 4), (K, d // 16)))]
+    return spec, G, X
+
+
+def test_surrogate_class_trivial_at_the_half_width():
+    """The Heaviside saturates at |phi| >= h: a field of exactly +h (-h) is
+    trivially outside (inside); a field one float below h in magnitude is
+    fallback (|phi| < h at the point)."""
+    spec, G, _ = _all_active_grid()
+    h = np.float32(spec.h)
+    assert float(h) == spec.h
+    act = slice(2, None)
+    for val, want in ((h, 1), (-h, 0), (2 * h, 1), (np.nextafter(h, np.float32(0)), 2),
+                      (-np.nextafter(h, np.float32(0)), 2)):
+        phi = np.full((G.P, 64), val, np.float32)
+        cls = oracle.surrogate_class(spec, G.nbr, phi)
+        assert np.all(cls[act] == want), (val, want)
+        assert np.all(cls[:2] == 255)
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_surrogate_class_curvature_bound(sign):
+    """phi = s (1.5 h + 0.7 (x - x0) + kappa |x - x0|^2 / 6): the 7-point
+    Laplacian of a quadratic is exact, kappa; the centre value 1.5 h is not
+    fallback by |phi|, the tap at -x (0.8 h + ...) keeps the point
+    non-trivial.  |kappa| h just above 0.1 is fallback, just below network."""
+    spec, G, X = _all_active_grid()
+    h = spec.h
+    p0, d0 = 2 + 2 + 6 * (2 + 6 * 2), 1 + 4 * 2 + 16 * 1  # a data point deep inside the all-active grid
+    x0 = [X[a][p0, d0] for a in range(3)]
+    r2 = sum((X[a] - x0[a]) ** 2 for a in range(3))
+    for kh, want in ((0.1 * (1 + 1e-3), 2), (0.1 * (1 - 1e-3), 3), (-0.1 * (1 + 1e-3), 2),
+                     (-0.1 * (1 - 1e-3), 3), (0.0, 3)):
+        kap = kh / h
+        phi = (sign * (1.5 * h + 0.7 * (X[0] - x0[0]) + kap * r2 / 6.0)).astype(np.float32)
+        cls, ties = oracle.surrogate_class(spec, G.nbr, phi, ties=True)
+        assert cls[p0, d0] == want, (kh, sign, cls[p0, d0])
+        assert ties == 0

@@ -8,6 +8,7 @@ points and closed-form single steps of the reinitialisation, and linear
 reproduction of the trilinear probe.
 """
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -28,6 +29,21 @@ def tiny_sphere(h=0.0625, radius=0.55, n=8, centre=(0.03, -0.02, 0.05)):
 # ----------------------------------------------------------------------------
 # Signed distance functions
 # ----------------------------------------------------------------------------
+def exact_lattice(v, lo, h):
+    """Fine lattice index and weight of float32 coordinates v, from the
+    definition u = (x - lo)/h - 1/2, i0 = floor(u), t = u - i0 evaluated in
+    exact rational arithmetic (the binary values of v, lo and h)."""
+    i0 = np.empty(len(v), np.int64)
+    t = np.empty(len(v))
+    Lo, H = Fraction(float(lo)), Fraction(float(h))
+    for q, x in enumerate(np.asarray(v, np.float32)):
+        u = (Fraction(float(x)) - Lo) / H - Fraction(1, 2)
+        f = math.floor(u)
+        i0[q] = f
+        t[q] = float(u - f)
+    return i0, t
+
+
 def test_sdf_sphere_closed_form():
     s = si.sphere(0.7, centre=(0.1, 0.2, -0.3))
     d = oracle.sdf(s, [0.1, 1.1, 0.1], [0.2, 0.2, 0.2 + 0.7], [-0.3, -0.3, -0.3])
@@ -286,10 +302,9 @@ def test_dense_twin_probe(tiny):
     nx, ny, nz = spec.dims
     i0, t = [], []
     for a, v in enumerate((x, y, z)):
-        u = (v - np.float32(spec.lo[a])) * np.float32(1.0 / h) - np.float32(0.5)
-        f = np.floor(u.astype(np.float32))
-        i0.append(f.astype(np.int64))
-        t.append(u.astype(np.float64) - f.astype(np.float64))
+        ia, ta = exact_lattice(v, spec.lo[a], h)
+        i0.append(ia)
+        t.append(ta)
     I = [v // 4 for v in i0]
     inside = (I[0] >= 0) & (I[1] >= 0) & (I[2] >= 0) & (I[0] < nx) & (I[1] < ny) & (I[2] < nz)
     cidx = np.clip(I[0], 0, nx - 1) + nx * (np.clip(I[1], 0, ny - 1) + ny * np.clip(I[2], 0, nz - 1))
@@ -617,17 +632,37 @@ def test_probe_reproduces_linear_field():
     fields = [G.phi, *oracle.gradient(spec, G.nbr, G.phi), *oracle.kernel_integrals(spec, G.nbr, G.phi)]
     x, y, z = si.box_particles(4000, (-0.15,) * 3, (0.15,) * 3, seed=3)
     out = oracle.probe(spec, G.cell_pkg, G.nbr, fields, x, y, z)
-    # the lattice coordinate u is decided in float32; the probe interpolates at
-    # the point lo + (u + 0.5) h that u represents exactly
-    pts = np.stack([(np.asarray(v, np.float32) - np.float32(spec.lo[a])) * np.float32(1.0 / spec.h) - np.float32(0.5)
-                    for a, v in enumerate((x, y, z))], 1).astype(np.float64)
-    pts = np.asarray(spec.lo)[None, :] + (pts + 0.5) * spec.h
+    # interpolation reproduces a linear field at the particle's own position
+    pts = np.stack([np.asarray(v, np.float32).astype(np.float64) for v in (x, y, z)], 1)
     exact = (pts - p0) @ n
     ok = np.abs(exact) < 4 * spec.h  # all eight corners in the interior of the band
     assert ok.sum() > 1000
     assert np.max(np.abs(out[0][ok] - exact[ok])) < 1e-13
     for a in range(3):
         assert np.max(np.abs(out[1 + a][ok] - n[a])) < 1e-12
+
+
+def test_probe_quadratic_field_picks_the_enclosing_cell():
+    """Trilinear interpolation of f = X^2 (X the data point's x coordinate)
+    between the corners of the cell that encloses the particle overshoots by
+    exactly h^2 t (1 - t), t in [0, 1); corners one cell off would extrapolate
+    and undershoot.  So this pins the cell decision and the weight t against
+    exact rational arithmetic, not against the oracle's own formula."""
+    spec = si.GridSpec((-0.3, -0.3, -0.3), (6, 6, 6), 0.025)
+    G = oracle.build_grid(spec, si.sphere(0.2, (0.0, 0.0, 0.0)))
+    assert G.P == 2 + 6 ** 3  # every cell active: all corners below are data points
+    X = spec.lo[0] + (_fine_coords(G)[0] + 0.5) * spec.h
+    fx = X * X
+    zero = np.zeros_like(fx)
+    fields = [fx, zero, zero, zero, zero, zero, zero, zero]
+    x, y, z = si.box_particles(3000, (-0.28,) * 3, (0.28,) * 3, seed=11)
+    out = oracle.probe(spec, G.cell_pkg, G.nbr, fields, x, y, z)[0]
+    i0, t = exact_lattice(x, spec.lo[0], spec.h)
+    xs = np.asarray(x, np.float32).astype(np.float64)
+    expect = xs * xs + spec.h ** 2 * t * (1.0 - t)
+    assert oracle.lattice_ties(spec, x, y, z) == 0
+    assert np.all((t >= 0) & (t < 1))
+    assert np.max(np.abs(out - expect)) < 1e-12
 
 
 def test_probe_at_data_points_and_far():
@@ -670,8 +705,7 @@ def test_morton_keys_bit_loop():
     for q in range(0, 300, 7):
         k = []
         for a, v in enumerate((x[q], y[q], z[q])):
-            u = (np.float32(v) - np.float32(spec.lo[a])) * np.float32(1.0 / spec.h) - np.float32(0.5)
-            i0 = int(np.floor(np.float32(u)))
+            i0 = int(exact_lattice([v], spec.lo[a], spec.h)[0][0])
             k.append(min(max(i0 + 1, 0), 4 * spec.dims[a] + 1))
         ref = 0
         for b in range(21):
