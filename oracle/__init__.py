@@ -290,13 +290,42 @@ def morton_keys(spec, x, y, z):
     return keys
 
 
-def lattice_ties(spec, x, y, z, tol=1e-9):
+def lattice_ties(spec, x, y, z, tol=1e-9, mask=False):
     """Number of particles with a lattice coordinate u = (x - lo)/h - 1/2
     within tol of an integer on some axis: their cell decision rests on the
-    last bits of the arithmetic."""
+    last bits of the arithmetic.  With mask=True also returns a uint8 array,
+    bit a set where axis a is tied."""
     x, y, z = (np.ascontiguousarray(v, np.float32) for v in (x, y, z))
-    return int(lib().or_lattice_ties(C.byref(_grid(spec)), C.c_int64(x.size), _p(x), _p(y), _p(z),
-                                     C.c_double(tol)))
+    m = np.zeros(x.size, np.uint8) if mask else None
+    n = int(lib().or_lattice_ties(C.byref(_grid(spec)), C.c_int64(x.size), _p(x), _p(y), _p(z), C.c_double(tol),
+                                  _p(m) if mask else None))
+    return (n, m) if mask else n
+
+
+def morton_keys_accept(spec, x, y, z, keys):
+    """Whether the given Morton keys are the oracle's: equal for every
+    particle away from lattice planes; a particle within 1e-9 of a plane on
+    some axes (two cell decisions are then both correct) may carry the key of
+    either side of each such plane, judged by moving that coordinate one
+    float step down or up.  Returns (ok, number of tied particles)."""
+    x, y, z = (np.ascontiguousarray(v, np.float32) for v in (x, y, z))
+    keys = np.asarray(keys).view(np.uint64)
+    n_t, m = lattice_ties(spec, x, y, z, mask=True)
+    ref = morton_keys(spec, x, y, z)
+    free = m == 0
+    if not np.array_equal(keys[free], ref[free]):
+        return False, n_t
+    for q in np.nonzero(~free)[0]:
+        cands = set()
+        for c in range(8):
+            p = [x[q], y[q], z[q]]
+            for a in range(3):
+                if m[q] >> a & 1:
+                    p[a] = np.nextafter(p[a], np.float32(-np.inf if (c >> a) & 1 else np.inf))
+            cands.add(int(morton_keys(spec, *(np.array([v], np.float32) for v in p))[0]))
+        if int(keys[q]) not in cands:
+            return False, n_t
+    return True, n_t
 
 
 def morton_order(keys):

@@ -606,18 +606,21 @@ static void lattice(const or_grid *g, int a, float x, int64_t *i0, double *t) {
 
 /* Particles with some lattice coordinate u within tol of an integer: their  */
 /* cell decision rests on the last bits of the arithmetic (the counterpart of */
-/* the tagging threshold test); a caller comparing decisions asserts none.    */
-int64_t or_lattice_ties(const or_grid *g, int64_t n, const float *x, const float *y, const float *z, double tol) {
+/* the tagging threshold test).  mask (optional) receives bit a set where     */
+/* axis a is tied; returns the number of particles with any tied axis.        */
+int64_t or_lattice_ties(const or_grid *g, int64_t n, const float *x, const float *y, const float *z, double tol,
+                        uint8_t *mask) {
     int64_t ties = 0;
 #pragma omp parallel for schedule(static) reduction(+ : ties)
     for (int64_t q = 0; q < n; ++q) {
         const float p[3] = {x[q], y[q], z[q]};
-        int tie = 0;
+        uint8_t tie = 0;
         for (int a = 0; a < 3; ++a) {
             const double u = lattice_u(g, a, p[a]);
-            if (fabs(u - nearbyint(u)) < tol) tie = 1;
+            if (fabs(u - nearbyint(u)) < tol) tie |= (uint8_t)(1u << a);
         }
-        ties += tie;
+        if (mask) mask[q] = tie;
+        ties += tie != 0;
     }
     return ties;
 }

@@ -25,11 +25,7 @@ struct DeviceGuard {
     }
 };
 
-ff split(double v) {
-    float hi = (float)v;
-    float lo = (float)(v - (double)hi);
-    return ff{hi, lo};
-}
+ff split(double v) { return split_ff(v); }
 
 }  // namespace
 
@@ -86,6 +82,7 @@ GridF grid_f(const sg_grid* g) {
     G.h_d = g->desc.h;
     G.F = (float)g->F;
     G.inv_h = (float)(1.0 / g->desc.h);
+    set_lattice(G.lat_c, G.lat_ih, g->desc.lo, g->desc.h);
     return G;
 }
 

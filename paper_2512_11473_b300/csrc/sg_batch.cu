@@ -257,8 +257,9 @@ __global__ void k_batch_far_W(float* __restrict__ W, const int64_t* __restrict__
 // Per-body constants of the relaxation, in the form the single-grid probe
 // uses them, plus the body's particle range and its first tile (CTA).
 struct RelaxBody {
-    float lo[3];
-    float inv_h;   // 1/h rounded to float once
+    ff lat_c[3];   // lattice constants of the probe (lo/h + 1/2, float-float)
+    ff lat_ih;     // 1/h, float-float
+    float inv_h;   // 1/h rounded to float once (the displacement's clip)
     int dims[3];
     float step_h;  // displacement scale times h, rounded to float once
     int64_t cells;    // offset of the body's cells in the global cell table
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_batch_relax(const RelaxBody* __r
         const int64_t q = B.first + (t - B.tile0) * RX_THREADS + threadIdx.x;
         if (q >= B.end) continue;
         const float pos[3] = {x[q], y[q], z[q]};
-        const ProbeAt A = probe_locate(B.lo, B.inv_h, B.dims, cells + B.cells, B.far_out, pos);
+        const ProbeAt A = probe_locate(B.lat_c, B.lat_ih, B.dims, cells + B.cells, B.far_out, pos);
         float acc[8];
         probe_interp_packed<NF>(nbr, tab, A, acc);
         const float inv = probe_inv_norm(acc);
@@ -830,10 +831,8 @@ sg_status sg_batch_relax(sg_batch* b, const sg_batch_plan* plan, const sg_relax*
         for (int i = 0; i < b->n; ++i) {
             const sg_grid_desc& d = b->desc[i];
             RelaxBody& q = hb[i];
-            for (int a = 0; a < 3; ++a) {
-                q.lo[a] = (float)d.lo[a];
-                q.dims[a] = d.dims[a];
-            }
+            for (int a = 0; a < 3; ++a) q.dims[a] = d.dims[a];
+            set_lattice(q.lat_c, q.lat_ih, d.lo, d.h);
             q.inv_h = (float)(1.0 / d.h);
             q.step_h = (float)((double)r->step * d.h);
             q.cells = b->cell_base[i];

@@ -31,8 +31,23 @@ struct GridF {
     int dims[3];
     float F;
     double h_d;   // h in double, for host-side constants
-    float inv_h;  // 1/h rounded to float once (the probe's lattice coordinate)
+    float inv_h;  // 1/h rounded to float once
+    ff lat_c[3];  // lo / h + 1/2 per axis, float-float (the probe's lattice coordinate)
+    ff lat_ih;    // 1 / h, float-float
 };
+
+// v as a float-float pair (host side): hi = v rounded to float, lo = the rest.
+inline ff split_ff(double v) {
+    const float hi = (float)v;
+    return ff{hi, (float)(v - (double)hi)};
+}
+
+// Constants of the probe's lattice coordinate u = (x - lo)/h - 1/2, written
+// as u = x (1/h) - (lo/h + 1/2).
+inline void set_lattice(ff (&c)[3], ff& ih, const double lo[3], double h) {
+    for (int a = 0; a < 3; ++a) c[a] = split_ff(lo[a] / h + 0.5);
+    ih = split_ff(1.0 / h);
+}
 
 // Scalars of the tagging/init kernels, in float-float.
 struct GridFF {
@@ -170,10 +185,14 @@ inline bool default_kernel(const sg_grid_desc& d) {
 
 // surrogate (sg_mlp.cu)
 cudaError_t launch_surrogate_integrals(sg_grid* g, const sg_mlp* m, float* W, float* gx, float* gy, float* gz);
-// Surrogate constants of a body of spacing h: 1/h, 1/h^2, h, the curvature
-// bound |kappa| h of the fallback, and 1/eps of the Heaviside (eps = h).
+// Surrogate constants of a body of spacing h: 1/h (the network inputs),
+// h_up = the least float >= h (a float f has |f| >= h exactly when
+// |f| >= h_up, and |f| < h when |f| < h_up), and the curvature bound
+// 0.1 h of the fallback's Laplacian numerator, in float and float-float;
+// 1/eps of the Heaviside (eps = h).
 struct SurConst {
-    float inv_h, inv_h2, h, kappa_h_max;
+    float inv_h, h_up, kap_thr;
+    ff kap_thr_ff;
 };
 struct SurBody {
     SurConst C;

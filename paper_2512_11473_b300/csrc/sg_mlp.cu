@@ -419,6 +419,32 @@ __global__ void __launch_bounds__(TR_WARPS * 32) k_mlp_train(const unsigned char
 //   network  everything else: the tensor-core MLP
 // ---------------------------------------------------------------------------
 
+// |kappa| h > 0.1 with kappa the 7-point Laplacian (sum of the six face
+// neighbours - 6 phi) / h^2, i.e. |a| > 0.1 h for the numerator a, decided
+// as on the real values: the float sum a is within 7 roundings, 2^-21 S, of
+// the exact one (S the float sum of the terms' magnitudes); only when |a|
+// falls within 2^-19 S of the bound is the numerator re-formed in
+// float-float (error about 2^-44 S).
+__device__ __forceinline__ bool curvature_exceeds(float xp, float xm, float yp, float ym, float zp, float zm, float c,
+                                                  const SurConst& C) {
+    const float a = __fadd_rn(__fadd_rn(__fadd_rn(xp, xm), __fadd_rn(yp, ym)),
+                              __fsub_rn(__fadd_rn(zp, zm), __fmul_rn(6.0f, c)));
+    const float S = __fadd_rn(__fadd_rn(__fadd_rn(fabsf(xp), fabsf(xm)), __fadd_rn(fabsf(yp), fabsf(ym))),
+                              __fadd_rn(__fadd_rn(fabsf(zp), fabsf(zm)), __fmul_rn(6.0f, fabsf(c))));
+    const float d = __fsub_rn(fabsf(a), C.kap_thr);
+    if (fabsf(d) > __fmul_rn(0x1p-19f, S) + __fmul_rn(0x1p-22f, C.kap_thr)) return d > 0.0f;
+    ff s = ff_add(two_sum(xp, xm), two_sum(yp, ym));
+    s = ff_add(s, two_sum(zp, zm));
+    s = ff_add(s, two_prod(-6.0f, c));  // -6 phi exactly
+    if (s.hi < 0.0f) s = ff_neg(s);
+    return ff_gt(s, C.kap_thr_ff);
+}
+
+// Class of a data point from the 6^3 phi tile around its package, on the
+// real values of the float phi (the same decisions as an exact evaluation):
+// trivial where every tap has |phi_s| >= h on one side (the Heaviside
+// saturates), fallback where |phi| < h or |kappa| h > 0.1, network else.
+// v receives the inputs clip(phi_s / h, -1, 1).
 __device__ __forceinline__ int sur_classify(const float* tile, int d, const SurConst& C, float (&v)[MLP_IN]) {
     const int i = d & 3, j = (d >> 2) & 3, k = d >> 4;
     const int e0 = (i + 1) + TILE_Y * (j + 1) + TILE_Z * (k + 1);
@@ -427,21 +453,17 @@ __device__ __forceinline__ int sur_classify(const float* tile, int d, const SurC
     for (int n = 0; n < MLP_IN; ++n) {
         const int sx = n % 3 - 1, sy = (n / 3) % 3 - 1, sz = n / 9 - 1;
         const float f = tile[e0 + sx + TILE_Y * sy + TILE_Z * sz];
-        const float tt = __fmul_rn(-f, C.inv_h);  // the Heaviside argument z / eps
-        all_in &= tt > 1.0f;
-        all_out &= tt < -1.0f;
+        all_in &= -f >= C.h_up;
+        all_out &= f >= C.h_up;
         v[n] = fminf(fmaxf(__fmul_rn(f, C.inv_h), -1.0f), 1.0f);
     }
     if (all_in) return SG_SUR_TRIVIAL_IN;
     if (all_out) return SG_SUR_TRIVIAL_OUT;
     const float c = tile[e0];
-    if (fabsf(__fmul_rn(c, C.inv_h)) < 1.0f) return SG_SUR_FALLBACK;
-    const float c2 = __fmul_rn(2.0f, c);
-    float a = __fadd_rn(__fsub_rn(tile[e0 + 1], c2), tile[e0 - 1]);
-    a = __fadd_rn(a, __fadd_rn(__fsub_rn(tile[e0 + TILE_Y], c2), tile[e0 - TILE_Y]));
-    a = __fadd_rn(a, __fadd_rn(__fsub_rn(tile[e0 + TILE_Z], c2), tile[e0 - TILE_Z]));
-    const float kap = __fmul_rn(a, C.inv_h2);
-    if (__fmul_rn(fabsf(kap), C.h) > C.kappa_h_max) return SG_SUR_FALLBACK;
+    if (fabsf(c) < C.h_up) return SG_SUR_FALLBACK;
+    if (curvature_exceeds(tile[e0 + 1], tile[e0 - 1], tile[e0 + TILE_Y], tile[e0 - TILE_Y], tile[e0 + TILE_Z],
+                          tile[e0 - TILE_Z], c, C))
+        return SG_SUR_FALLBACK;
     return SG_SUR_NETWORK;
 }
 
@@ -626,10 +648,21 @@ __global__ void __launch_bounds__(SU_THREADS) k_sur_samples(const int32_t* __res
     to[row * 4 + 3] = gz[pt];
 }
 
-SurConst sur_const(const sg_grid* g) {
-    const double h = g->desc.h;
-    return SurConst{(float)(1.0 / h), (float)(1.0 / (h * h)), (float)h, 0.1f};
+// The fallback's curvature bound |kappa| h > 0.1.
+constexpr double SUR_KAPPA_H_MAX = 0.1;
+
+SurConst sur_const_h(double h) {
+    SurConst C;
+    C.inv_h = (float)(1.0 / h);
+    float up = (float)h;
+    if ((double)up < h) up = std::nextafter(up, INFINITY);
+    C.h_up = up;
+    C.kap_thr = (float)(SUR_KAPPA_H_MAX * h);
+    C.kap_thr_ff = split_ff(SUR_KAPPA_H_MAX * h);
+    return C;
 }
+
+SurConst sur_const(const sg_grid* g) { return sur_const_h(g->desc.h); }
 
 unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
@@ -867,7 +900,7 @@ cudaError_t launch_surrogate_integrals(sg_grid* g, const sg_mlp* m, float* W, fl
 
 SurBody sur_body(double h) {
     SurBody q;
-    q.C = SurConst{(float)(1.0 / h), (float)(1.0 / (h * h)), (float)h, 0.1f};
+    q.C = sur_const_h(h);
     q.inv_eps = (float)(1.0 / h);
     return q;
 }

@@ -36,7 +36,7 @@ __device__ __forceinline__ uint64_t morton_key(const GridF& G, float x, float y,
     for (int a = 0; a < 3; ++a) {
         int i0;
         float t;
-        lattice(pos[a], G.lo[a], G.inv_h, i0, t);
+        lattice(pos[a], G.lat_c[a], G.lat_ih, i0, t);
         int k = i0 + 1;
         k = k < 0 ? 0 : (k > 4 * G.dims[a] + 1 ? 4 * G.dims[a] + 1 : k);
         key |= spread3((uint64_t)k) << a;
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe(GridF G, const int32_t* __
     for (int64_t r = (int64_t)blockIdx.x * per + threadIdx.x; r < r1; r += blockDim.x) {
         const int64_t q = use_order ? (int64_t)__ldg(order + r) : r;
         const float pos[3] = {__ldg(x + q), __ldg(y + q), __ldg(z + q)};
-        const ProbeAt A = probe_locate(G.lo, G.inv_h, G.dims, cell_pkg, 1, pos);
+        const ProbeAt A = probe_locate(G.lat_c, G.lat_ih, G.dims, cell_pkg, 1, pos);
         float acc[8];
         probe_interp<8>(nbr, F, A, acc);
         const float inv = probe_inv_norm(acc);
@@ -436,6 +436,7 @@ extern "C" sg_status sg_morton_order_noalloc(const sg_grid_desc* desc, int64_t n
     G.h_d = desc->h;
     G.F = 0.0f;
     G.inv_h = (float)(1.0 / desc->h);
+    set_lattice(G.lat_c, G.lat_ih, desc->lo, desc->h);
     if (sort_scratch_bytes(n, morton_bits(G)) > sizeof(g_noalloc_scratch)) return SG_ERR_CAPACITY;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {

@@ -7,15 +7,27 @@
 namespace sg {
 namespace {
 
-// Fine lattice coordinate in float32: u = (x - lo) * inv_h - 1/2 with
-// inv_h = 1/h rounded to float once, clamped to +-2^24, i0 = floor(u),
-// t = u - i0 (exact).
-__device__ __forceinline__ void lattice(float x, float lo, float inv_h, int& i0, float& t) {
-    float u = __fsub_rn(__fmul_rn(__fsub_rn(x, lo), inv_h), 0.5f);
-    u = fminf(fmaxf(u, -16777216.0f), 16777216.0f);
-    float f = floorf(u);
+// Fine lattice coordinate u = (x - lo)/h - 1/2 = x (1/h) - (lo/h + 1/2) in
+// float-float, about 44 significant bits: ih = 1/h and c = lo/h + 1/2 are
+// float-float constants, x ih.hi is formed exactly (TwoProduct) and c.hi is
+// subtracted exactly (TwoSum).  i0 = floor(u) then agrees with the exact
+// decision unless u lies within about 1e-10 of an integer, and t = u - i0
+// is correct to float rounding.  i0 is clamped to +-2^24 (t = 0 there:
+// the particle is far outside any domain).
+__device__ __forceinline__ void lattice(float x, const ff& c, const ff& ih, int& i0, float& t) {
+    const ff p = two_prod(x, ih.hi);
+    const ff s = two_sum(p.hi, -c.hi);
+    const float e = __fadd_rn(__fadd_rn(s.lo, p.lo), __fsub_rn(__fmul_rn(x, ih.lo), c.lo));
+    const ff u = two_sum(s.hi, e);
+    float f = floorf(u.hi);
+    if (f == u.hi && u.lo < 0.0f) f = __fsub_rn(f, 1.0f);  // an integer hi with the rest below it
+    float tt = __fadd_rn(__fsub_rn(u.hi, f), u.lo);       // u.hi - f is exact
+    if (!(fabsf(f) < 16777216.0f)) {
+        f = fminf(fmaxf(f, -16777216.0f), 16777216.0f);
+        tt = 0.0f;
+    }
     i0 = (int)f;
-    t = __fsub_rn(u, f);
+    t = tt;
 }
 
 // Where a particle sits: home package (the package of its home coarse cell
@@ -27,7 +39,7 @@ struct ProbeAt {
     float t[3];
 };
 
-__device__ __forceinline__ ProbeAt probe_locate(const float (&lo)[3], float inv_h, const int (&dims)[3],
+__device__ __forceinline__ ProbeAt probe_locate(const ff (&lat_c)[3], const ff& lat_ih, const int (&dims)[3],
                                                 const int32_t* __restrict__ cell_pkg, int64_t outside,
                                                 const float (&pos)[3]) {
     ProbeAt A;
@@ -36,7 +48,7 @@ __device__ __forceinline__ ProbeAt probe_locate(const float (&lo)[3], float inv_
     int64_t c = 0, stride = 1;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        lattice(pos[a], lo[a], inv_h, i0[a], A.t[a]);
+        lattice(pos[a], lat_c[a], lat_ih, i0[a], A.t[a]);
         int I = i0[a] >> 2;  // floor division by 4
         A.l[a] = i0[a] & 3;
         inside &= I >= 0 && I < dims[a];

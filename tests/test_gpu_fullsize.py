@@ -103,8 +103,10 @@ def test_full_probe_50m_sampled(body, sg):
     sample = np.sort(rng.choice(N_PARTICLES, 1_000_000, replace=False))
     si_t = torch.from_numpy(sample).cuda()
     xs, ys, zs = (H(v[si_t]) for v in X)
-    # keys of the sample against the oracle's definition
-    assert np.array_equal(H(keys[o[si_t]]).view(np.uint64), oracle.morton_keys(spec, xs, ys, zs))
+    # keys of the sample against the oracle's definition (a particle within
+    # 1e-9 of a lattice plane may carry either side's key)
+    ok, n_tied = oracle.morton_keys_accept(spec, xs, ys, zs, H(keys[o[si_t]]))
+    assert ok and n_tied <= 10
     fields = [H(g.field(f)).astype(np.float64) for f in ("phi", "gx", "gy", "gz", "W", "Gx", "Gy", "Gz")]
     ref = oracle.probe(spec, O.cell_pkg, O.nbr, fields, xs, ys, zs)
     got = {k: H(v[si_t]).astype(np.float64) for k, v in out.items()}

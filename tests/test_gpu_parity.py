@@ -260,8 +260,8 @@ def _fields_host(g):
     return [H(g.field(f)).astype(np.float64) for f in ("phi", "gx", "gy", "gz", "W", "Gx", "Gy", "Gz")]
 
 
-def _probe_compare(got, ref):
-    assert np.max(np.abs(got["phi"] - ref[0])) <= 1e-5
+def _probe_compare(got, ref, h):
+    assert np.max(np.abs(got["phi"] - ref[0])) <= 1e-4 * h
     for k, name in enumerate(("W", "Gx", "Gy", "Gz")):
         assert np.max(np.abs(got[name] - ref[4 + k])) <= 1e-5, name
     gref = np.sqrt(ref[1] ** 2 + ref[2] ** 2 + ref[3] ** 2)
@@ -287,7 +287,7 @@ def test_probe_sphere_small(sg):
     ref = oracle.probe(spec, O.cell_pkg, O.nbr, fields, x, y, z)
     for morton in (True, False):
         got = {k: H(v).astype(np.float64) for k, v in g.probe(X, Y, Z, morton=morton).items()}
-        _probe_compare(got, ref)
+        _probe_compare(got, ref, spec.h)
 
 
 def test_probe_permutation_and_order_invariance(sg):
@@ -308,7 +308,19 @@ def test_probe_permutation_and_order_invariance(sg):
         assert torch.equal(a[k][perm], c[k])
     O = oracle.build_grid(spec, shape)
     ref = oracle.probe(spec, O.cell_pkg, O.nbr, _fields_host(g), x, y, z)
-    _probe_compare({k: H(v).astype(np.float64) for k, v in a.items()}, ref)
+    _probe_compare({k: H(v).astype(np.float64) for k, v in a.items()}, ref, spec.h)
+
+
+def _keys_and_order_match(spec, x, y, z, keys, order):
+    """Keys bit-exact against the oracle's definition (a particle within 1e-9
+    of a lattice plane may carry either side's key: both decisions are
+    correct there, and such particles must be rare), and the order the
+    stable sort of those keys by (key, input index)."""
+    k = H(keys).view(np.uint64)
+    ok, n_tied = oracle.morton_keys_accept(spec, x, y, z, k)
+    assert ok
+    assert n_tied <= max(1, len(x) // 100_000)
+    assert np.array_equal(H(order).astype(np.int64), oracle.morton_order(k))
 
 
 @pytest.mark.parametrize("n", [1, 4095, 4096, 4097, 100_003])
@@ -325,9 +337,7 @@ def test_morton_order_bit_exact(sg, n):
         y[n // 2:n // 2 + 5] = y[0]
         z[n // 2:n // 2 + 5] = z[0]
     keys, order = g.morton_order(*(torch.from_numpy(v).cuda() for v in (x, y, z)))
-    rk = oracle.morton_keys(spec, x, y, z)
-    assert np.array_equal(H(keys).view(np.uint64), rk)
-    assert np.array_equal(H(order).astype(np.int64), oracle.morton_order(rk))
+    _keys_and_order_match(spec, x, y, z, keys, order)
 
 
 def test_morton_sort_64bit_keys(sg):
@@ -338,10 +348,8 @@ def test_morton_sort_64bit_keys(sg):
     g.tag_allocate(shape)
     x, y, z = si.box_particles(20_000, spec.lo, spec.hi(), seed=9)
     keys, order = g.morton_order(*(torch.from_numpy(v).cuda() for v in (x, y, z)))
-    rk = oracle.morton_keys(spec, x, y, z)
-    assert int(rk.max()) >= 2 ** 32
-    assert np.array_equal(H(keys).view(np.uint64), rk)
-    assert np.array_equal(H(order).astype(np.int64), oracle.morton_order(rk))
+    assert int(oracle.morton_keys(spec, x, y, z).max()) >= 2 ** 32
+    _keys_and_order_match(spec, x, y, z, keys, order)
 
 
 # --------------------------------------------------------------------------
@@ -510,6 +518,7 @@ def test_morton_sorted_input_fast_path(sg):
     D = [torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (xs, ys, zs)]
     keys, order = g.morton_order(*D)
     assert np.array_equal(H(order), np.arange(len(xs)))
+    assert oracle.lattice_ties(spec, xs, ys, zs) == 0  # the input order was the oracle's
     assert np.array_equal(H(keys).view(np.uint64), rk[ro])
     a = g.probe(*D, morton=True)
     b = g.probe(*D, morton=False)
@@ -523,8 +532,7 @@ def test_morton_sorted_input_fast_path(sg):
         v[i], v[j] = v[j], v[i]
     D2 = [torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (xs2, ys2, zs2)]
     keys2, order2 = g.morton_order(*D2)
-    rk2 = oracle.morton_keys(spec, xs2, ys2, zs2)
-    assert np.array_equal(H(order2).astype(np.int64), oracle.morton_order(rk2))
+    _keys_and_order_match(spec, xs2, ys2, zs2, keys2, order2)
     c = g.probe(*D2, morton=True)
     d = g.probe(*D2, morton=False)
     for k in c:

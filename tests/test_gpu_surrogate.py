@@ -70,7 +70,7 @@ def test_gradient_matches_oracle(sg, n):
     assert np.linalg.norm(g - gref) <= 2e-2 * np.linalg.norm(gref)
     # per block: every layer's gradient, not only the large ones
     for a, b in ((0, 1728), (1728, 1792), (1792, 5888), (5888, 5952), (5952, 6208), (6208, 6212)):
-        assert np.linalg.norm(g[a:b] - gref[a:b]) <= 5e-2 * np.linalg.norm(gref[a:b]) + 1e-9
+        assert np.linalg.norm(g[a:b] - gref[a:b]) <= 2e-2 * np.linalg.norm(gref[a:b]) + 1e-9
 
 
 def test_gradient_with_index_rows(sg):
@@ -135,7 +135,8 @@ def test_classification_matches_oracle(sg, name):
     g = _grid(sg, shape, spec)
     cls = g.surrogate_classify().cpu().numpy()
     phi = g.field("phi").cpu().numpy()
-    ref = oracle.surrogate_class(spec, g.field("nbr").cpu().numpy(), phi)
+    ref, ties = oracle.surrogate_class(spec, g.field("nbr").cpu().numpy(), phi, ties=True)
+    assert ties == 0
     assert np.array_equal(cls, ref)
     assert set(np.unique(cls[2:])) <= {0, 1, 2, 3} and (cls[2:] == 3).sum() > 0
 
