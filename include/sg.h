@@ -259,7 +259,12 @@ SG_API sg_status sg_reinit(sg_grid *g, int32_t iterations, float cfl);
  *   G^ = h grad W = sum_s w'(|s|) (-s/|s|) H(-phi(x+sh)) / sum_s w(|s|).
  * Far packages: W = 1 inside, 0 outside, G^ = 0.  Writes SG_FIELD_W and
  * SG_FIELD_GWX/GWY/GWZ.  Mode 0 takes mlp = NULL; mode 1 (surrogate with
- * exact fallback, see SG_SUR_*) takes an sg_mlp*.
+ * exact fallback, see SG_SUR_*) takes an sg_mlp*: one pass classifies every
+ * point and writes the trivial and fallback values and a list of network
+ * points, a second runs the network over the list in 128-row tensor-core
+ * tiles (a product that never completes within its bounded wait sets the
+ * device error word: sg_status_sync returns SG_ERR_TIMEOUT).  The grid
+ * keeps the list's buffer (4 bytes per data point) for later calls.
  * Errors: SG_ERR_INVALID for an unknown mode or a missing or extra network.
  * Requires phi. */
 SG_API sg_status sg_kernel_integrals(sg_grid *g, int32_t mode, const void *mlp);
@@ -267,9 +272,12 @@ SG_API sg_status sg_kernel_integrals(sg_grid *g, int32_t mode, const void *mlp);
 /* Particle probe ("Grid-Particle Coupling"): trilinear interpolation of phi,
  * grad phi, W and G^ at n particles.  x, y, z are device arrays of n floats;
  * the eight outputs are device arrays of n floats in input order (any may
- * be NULL to skip it).  The lattice coordinate is taken in float32:
- * u = (x - lo) * (1/h) - 0.5 with 1/h rounded to float once, clamped to +-2^24, i0 = floor(u), t = u - i0, home
- * cell floor(i0/4) (the outside far package when outside the domain),
+ * be NULL to skip it).  The lattice coordinate u = (x - lo)/h - 1/2 of the
+ * float position is formed in float-float (x (1/h) - (lo/h + 1/2), about 44
+ * bits), so i0 = floor(u) is the exact decision unless u lies within about
+ * 1e-10 of an integer, and t = u - i0 is correct to float rounding; i0 is
+ * clamped to +-2^24 (far outside any domain).  Home cell floor(i0/4) (the
+ * outside far package when outside the domain),
  * corners reached through the home package's neighbourhood.  The normal is
  * grad/|grad| (0 where |grad| = 0).  Fields not yet computed read as 0.
  * With SG_PROBE_MORTON the particles are walked in Morton order (stable
@@ -394,15 +402,27 @@ SG_API sg_status sg_batch_relax(sg_batch *b, const sg_batch_plan *plan, const sg
 /* ------------------------------------------------------------------------ */
 /* Kernel-integral surrogate (not in the paper): a 27 -> 64 -> 64 -> 4       */
 /* multilayer perceptron with SiLU hidden activations, BF16 weights and      */
-/* activations, FP32 accumulation and FP32 master weights.                   */
+/* activations, FP32 accumulation (tcgen05 tensor cores, accumulators in     */
+/* tensor memory) and FP32 master weights.  It stands in for the kernel      */
+/* integral of "Integral with SPH Smoothing Kernel and Grid-Particle         */
+/* Coupling" at the points the classes below leave to it.                    */
 /* ------------------------------------------------------------------------ */
 typedef struct sg_mlp sg_mlp;
 
 /* Parameter vector (FP32, host): W1[64][27], b1[64], W2[64][64], b2[64],
  * W3[4][64], b3[4] (row = output unit).  Inputs are bf16 rows of 32 values:
- * v_n = clip(phi(x + s h) / h, -1, 1) for the 27 offsets s in {-1,0,1}^3,
- * n = (sx+1) + 3 (sy+1) + 9 (sz+1), then 5 zeros.  Outputs per row:
- * (W, Gx, Gy, Gz) as defined by sg_kernel_integrals. */
+ * 27 inputs then 5 zeros.  The surrogate integrals feed the network the 27
+ * values v = clip(sign phi(x + s h) / h, -1, 1) of a point in its canonical
+ * frame: sign = -1 where phi(x) < 0; axes reversed where the central
+ * difference sign (phi(x + h e_a) - phi(x - h e_a)) is negative; axes
+ * ordered by decreasing |difference| (equal magnitudes keep the lower axis
+ * first); input n' = (s'x+1) + 3 (s'y+1) + 9 (s'z+1) at the canonical
+ * offset s'.  Outputs (W', G'x, G'y, G'z) in that frame are carried back:
+ * W = W' (1 - W' where sign = -1), component k of G' belongs to the k-th
+ * ordered axis, negated where that axis was reversed or sign = -1.  The
+ * tap weights depend on |s| alone and H(-z) = 1 - H(z), so this is a
+ * symmetry of the exact integrals; the network learns one 48th of their
+ * input space. */
 #define SG_MLP_NPARAM 6212
 #define SG_MLP_ROW 32
 
@@ -412,29 +432,38 @@ SG_API sg_status sg_mlp_create(const float *params, void *stream, sg_mlp **out);
 SG_API sg_status sg_mlp_destroy(sg_mlp *m);
 /* Replace the parameters (copied; Adam moments and step count reset). */
 SG_API sg_status sg_mlp_set_params(sg_mlp *m, const float *params);
-/* Read the FP32 master parameters back (synchronises the stream). */
+/* Read the FP32 master parameters back (synchronises the stream).  Returns
+ * SG_ERR_TIMEOUT when a tensor-core product of an earlier call on this
+ * network never signalled completion (each wait is bounded; the kernel then
+ * frees its tensor memory and returns). */
 SG_API sg_status sg_mlp_get_params(sg_mlp *m, float *params);
-/* y[n][4] = network(x[n][SG_MLP_ROW]); device arrays owned by the caller. */
+/* y[n][4] = network(x[n][SG_MLP_ROW]) on the rows as given; device arrays
+ * owned by the caller (16-byte aligned). */
 SG_API sg_status sg_mlp_forward(sg_mlp *m, int64_t n, const void *x_bf16, float *y);
 /* Gradient of L = mean over rows and the 4 outputs of (y - t)^2 with respect
  * to every parameter, written to grad[SG_MLP_NPARAM] (device, FP32); rows
  * idx[0..n) of x and t (idx NULL: rows 0..n); *loss (device, may be NULL)
- * receives L.  Uses the BF16 copy of the current parameters. */
+ * receives L.  Uses the BF16 copy of the current parameters.  Each CTA of
+ * 128 rows forms its partial gradient; the partials are summed in CTA order,
+ * so the result does not depend on scheduling. */
 SG_API sg_status sg_mlp_loss_grad(sg_mlp *m, int64_t n, const void *x_bf16, const float *t, const int32_t *idx,
                                   float *grad, float *loss);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with
- * learning rate lr on the batch of rows idx[0..batch) (or 0..batch). */
+ * learning rate lr on the batch of rows idx[0..batch) (or 0..batch); the
+ * gradient is formed as by sg_mlp_loss_grad, so training is reproducible. */
 SG_API sg_status sg_mlp_train_step(sg_mlp *m, int64_t batch, const void *x_bf16, const float *t,
                                    const int32_t *idx, float lr, float *loss);
 SG_API const char *sg_mlp_last_error(const sg_mlp *m);
 
-/* Classes of a data point for sg_kernel_integrals mode 1 (decided in float
- * from the grid's phi with explicitly rounded operations):
- *   SG_SUR_TRIVIAL_IN / _OUT: every one of the 27 taps saturates the
- *     smoothed Heaviside (-phi_s / h > 1, resp. < -1): W = 1 / 0, G = 0;
- *   SG_SUR_FALLBACK: |phi / h| < 1, or |kappa| h > 0.1 with kappa the 7-point
+/* Classes of a data point for sg_kernel_integrals mode 1, decided on the
+ * real values of the grid's float phi (the same decisions as an exact
+ * evaluation; the curvature test is exact up to its float-float sum):
+ *   SG_SUR_TRIVIAL_IN / _OUT: every one of the 27 taps has -phi_s >= h
+ *     (resp. phi_s >= h), where the smoothed Heaviside saturates: W = 1 / 0,
+ *     G = 0;
+ *   SG_SUR_FALLBACK: |phi| < h, or |kappa| h > 0.1 with kappa the 7-point
  *     Laplacian of phi: the exact 27-tap sum of mode 0, bit for bit;
- *   SG_SUR_NETWORK: the network on the 27 clipped inputs. */
+ *   SG_SUR_NETWORK: the network on the point's canonical inputs. */
 enum { SG_SUR_TRIVIAL_IN = 0, SG_SUR_TRIVIAL_OUT = 1, SG_SUR_FALLBACK = 2, SG_SUR_NETWORK = 3 };
 
 /* Class of every data point: cls[P*64] (device, caller-owned); far packages
@@ -444,8 +473,9 @@ SG_API sg_status sg_surrogate_classify(sg_grid *g, uint8_t *cls);
 /* Training samples of a grid whose exact integrals (mode 0) are current:
  * every SG_SUR_NETWORK point whose SplitMix64 hash of (seed, point index)
  * falls below `keep` (a fraction in [0, 1]), in point order: x rows of
- * SG_MLP_ROW bf16 inputs and t rows of (W, Gx, Gy, Gz).  At most cap rows are
- * written; *count receives the number of points selected (synchronises). */
+ * SG_MLP_ROW bf16 canonical inputs and t rows of the exact (W, Gx, Gy, Gz)
+ * carried into the point's canonical frame.  At most cap rows are written;
+ * *count receives the number of points selected (synchronises). */
 SG_API sg_status sg_surrogate_samples(sg_grid *g, uint64_t seed, float keep, int64_t cap, void *x_bf16, float *t,
                                       int64_t *count);
 

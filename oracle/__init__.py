@@ -386,6 +386,40 @@ def surrogate_inputs(spec, nbr, phi):
     return x
 
 
+def surrogate_canonical(spec, nbr, phi32):
+    """Canonical inputs (P, 64, 27) and frame codes (P, 64) of every data
+    point of the float field phi32 (see or_surrogate_canonical)."""
+    phi32 = np.ascontiguousarray(phi32, np.float32)
+    P = phi32.shape[0]
+    x = np.zeros((P, 64, MLP_IN))
+    code = np.zeros((P, 64), np.int32)
+    lib().or_surrogate_canonical(C.byref(_grid(spec)), C.c_int64(P), _p(np.ascontiguousarray(nbr, np.int32)),
+                                 _p(phi32), _p(x), _p(code))
+    return x, code
+
+
+_PERMS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+
+
+def surrogate_uncanon(code, y):
+    """Outputs (W', G'_0, G'_1, G'_2) in the canonical frames `code` -> (W, G^)
+    of the points: W = 1 - W' where the frame negated phi; component k of G'
+    belongs to original axis p[k], negated where that axis was reversed or
+    phi negated."""
+    code = np.asarray(code).reshape(-1)
+    y = np.asarray(y, np.float64).reshape(-1, 4)
+    flip = (code & 1) == 1
+    out = np.empty_like(y)
+    out[:, 0] = np.where(flip, 1.0 - y[:, 0], y[:, 0])
+    for r, c in enumerate(code):
+        q = _PERMS[c >> 4]
+        for k in range(3):
+            a = q[k]
+            neg = bool((c >> (1 + a)) & 1) != bool(flip[r])
+            out[r, 1 + a] = -y[r, 1 + k] if neg else y[r, 1 + k]
+    return out
+
+
 def surrogate_class(spec, nbr, phi32, ties=False):
     """Classes (0 in, 1 out, 2 fallback, 3 network; 255 far) of the float
     field phi32, decided on its real values in double precision.  With

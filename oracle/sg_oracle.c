@@ -998,6 +998,65 @@ void or_surrogate_inputs(const or_grid *g, int64_t P, const int32_t *nbr, const 
     }
 }
 
+/* Canonical frame of a surrogate input (not in the paper; it follows from    */
+/* the definitions of W and G^).  The tap weights depend on |s| alone and H   */
+/* is antisymmetric, H(-z) = 1 - H(z), so negating phi maps (W, G^) to         */
+/* (1 - W, -G^) and a signed permutation T of the axes maps G^ to T G^.  The   */
+/* frame of a point: sign = -1 when phi(x) < 0 (else 1); g_a = sign (phi(x +   */
+/* h e_a) - phi(x - h e_a)), exact in double; axis a reversed when g_a < 0;    */
+/* axes ordered by decreasing |g_a|, equal magnitudes keeping the lower axis   */
+/* first: canonical axis k is original axis p[k].  The canonical input at      */
+/* canonical offset s' is sign phi(x + s h) / h (clipped to [-1, 1]) with      */
+/* s[p[k]] = (reversed p[k] ? -1 : 1) s'[k].  code = (sign < 0) | reversed    */
+/* axes << 1 | index of (p[0], p[1], p[2]) among the six permutations in      */
+/* lexicographic order << 4.  x receives 27 canonical inputs per point.       */
+void or_surrogate_canonical(const or_grid *g, int64_t P, const int32_t *nbr, const float *phi, double *x,
+                            int32_t *code) {
+    static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    const double h = g->h;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 2; p < P; ++p) {
+        const int32_t *nb = nbr + p * 27;
+        for (int d = 0; d < PKG3; ++d) {
+            const int i = d & 3, j = (d >> 2) & 3, k = d >> 4;
+            double f[27];
+            for (int n = 0; n < 27; ++n)
+                f[n] = (double)phi[shift_index(nb, i + n % 3 - 1, j + (n / 3) % 3 - 1, k + n / 9 - 1)];
+            const double sign = f[13] < 0.0 ? -1.0 : 1.0;
+            const double ga[3] = {sign * (f[14] - f[12]), sign * (f[16] - f[10]), sign * (f[22] - f[4])};
+            int rev = 0;
+            for (int a = 0; a < 3; ++a)
+                if (ga[a] < 0.0) rev |= 1 << a;
+            int pi = 0;
+            for (int c = 0; c < 6; ++c) { /* the ordering with no later axis strictly larger than an earlier one */
+                const int *q = perms[c];
+                int good = 1;
+                for (int u = 0; u < 3; ++u)
+                    for (int w = u + 1; w < 3; ++w) {
+                        const double mu = fabs(ga[q[u]]), mw = fabs(ga[q[w]]);
+                        if (mw > mu || (mw == mu && q[w] < q[u])) good = 0;
+                    }
+                if (good) {
+                    pi = c;
+                    break;
+                }
+            }
+            const int *q = perms[pi];
+            for (int m = 0; m < 27; ++m) {
+                const int sp[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
+                int so[3];
+                for (int kk = 0; kk < 3; ++kk) so[q[kk]] = ((rev >> q[kk]) & 1 ? -1 : 1) * sp[kk];
+                const int n = (so[0] + 1) + 3 * (so[1] + 1) + 9 * (so[2] + 1);
+                double v = sign * f[n] / h;
+                if (v < -1.0) v = -1.0;
+                if (v > 1.0) v = 1.0;
+                x[(p * PKG3 + d) * 27 + m] = v;
+            }
+            code[p * PKG3 + d] = (sign < 0.0 ? 1 : 0) | (rev << 1) | (pi << 4);
+        }
+    }
+}
+
 /* Classes of the surrogate integral (a reading: the network stands in for    */
 /* the kernel integral of "Integral with SPH Smoothing Kernel and Grid-       */
 /* Particle Coupling"), decided on the real values of the float field phi:    */

@@ -12,7 +12,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsg.so")
 SOURCES = ["sg_api.cu", "sg_scan.cu", "sg_tag.cu", "sg_sweep.cu", "sg_probe.cu", "sg_batch.cu", "sg_mlp.cu",
            "sg_consistency.cu", "sg_reinit.cu"]
-HEADERS = ["sg_internal.cuh", "sg_ff.cuh", "sg_rows.cuh", "sg_integrals.cuh", "sg_probe.cuh", "sg_mma.cuh", "sg_mlp.cuh"]
+HEADERS = ["sg_internal.cuh", "sg_ff.cuh", "sg_rows.cuh", "sg_integrals.cuh", "sg_probe.cuh", "sg_umma.cuh", "sg_mlp.cuh",
+           "sg_sur.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

@@ -224,7 +224,7 @@ sg_status sg_destroy(sg_grid* g) {
     SG_CHECK_GRID(g);
     DeviceGuard dg(g->device);
     Buf* bufs[] = {&g->cell_pkg, &g->cell_type, &g->pkg_cell, &g->pkg_type, &g->nbr, &g->faces,
-                   &g->phi_tmp,  &g->err,       &g->scratch,  &g->stats};
+                   &g->phi_tmp,  &g->err,       &g->scratch,  &g->stats,    &g->sur_work};
     for (Buf* b : bufs) grid_free(g, *b);
     for (int f = 0; f < SG_N_FLOAT_FIELDS; ++f) grid_free(g, g->field[f]);
     if (g->host_pin.p) cudaFreeHost(g->host_pin.p);
@@ -524,8 +524,10 @@ sg_status sg_kernel_integrals(sg_grid* g, int32_t mode, const void* mlp) {
         if (!(o[a] = field_ptr(g, SG_FIELD_W + a, false)))
             return fail(g, SG_ERR_OOM, "sg_kernel_integrals: out of memory");
     if (mode == 1) {
-        if (!ensure(g, g->stats, 256)) return fail(g, SG_ERR_OOM, "sg_kernel_integrals: out of memory");
-        SG_CUDA(g, launch_surrogate_integrals(g, (const sg_mlp*)mlp, o[0], o[1], o[2], o[3]), "surrogate integrals");
+        if (!ensure(g, g->stats, 256) || !ensure(g, g->sur_work, sur_work_bytes(g->P)))
+            return fail(g, SG_ERR_OOM, "sg_kernel_integrals: out of memory");
+        SG_CUDA(g, launch_surrogate_integrals(g, (const sg_mlp*)mlp, g->sur_work.p, o[0], o[1], o[2], o[3]),
+                "surrogate integrals");
         return SG_OK;
     }
     SG_CUDA(g, launch_kernel_integrals(grid_f(g), (const int32_t*)g->nbr.p, (const float*)g->field[SG_FIELD_PHI].p, o[0],

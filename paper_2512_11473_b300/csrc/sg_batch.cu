@@ -24,6 +24,7 @@
 
 #include "sg_probe.cuh"
 #include "sg_integrals.cuh"
+#include "sg_mlp.cuh"
 #include "sg_rows.cuh"
 
 struct sg_batch_graph {
@@ -53,6 +54,7 @@ struct sg_batch {
     cudaStream_t capture = nullptr;  // private stream used only to capture
     int device = 0;
     sg::Buf phi, tmp, s0, phi0, f[8], nbr, faces, type, body, params, counters, cells, sur, relax, probe_tab;
+    sg::Buf sur_work;  // list of network points of the surrogate integrals
     size_t n_counters = 0;
     float params_cfl = -1.0f;
     std::vector<sg_batch_graph> graphs;
@@ -458,7 +460,7 @@ cudaError_t record_run(sg_batch* b, const sg_batch_plan& plan, cudaStream_t s) {
     }
     if (plan.integrals_mode == 1)
         return launch_batch_surrogate_integrals(nbr, type, body, (const SurBody*)b->sur.p, phi, fo[4], fo[5], fo[6],
-                                                fo[7], b->P, b->mlp, b->device, s);
+                                                fo[7], b->P, b->mlp, b->sur_work.p, mlp_err(b->mlp), b->device, s);
     // a plain grid: the integrals' per-package work is even, so they need no work counter
     k_batch_integrals<<<(unsigned)((b->P + BT_HW - 1) / BT_HW), BT, 0, s>>>(nbr, type, body, prm, phi, fo[4], fo[5],
                                                                            fo[6], fo[7], b->P, K);
@@ -656,7 +658,7 @@ sg_status sg_batch_destroy(sg_batch* b) {
     if (!b) return SG_ERR_INVALID;
     drop_graphs(b, false);
     Buf* bufs[] = {&b->phi,  &b->tmp,    &b->s0,       &b->phi0,  &b->nbr, &b->faces, &b->type,
-                   &b->body, &b->params, &b->counters, &b->cells, &b->sur, &b->relax, &b->probe_tab};
+                   &b->body, &b->params, &b->counters, &b->cells, &b->sur, &b->relax, &b->probe_tab, &b->sur_work};
     for (Buf* x : bufs) b_free(b, *x);
     for (int i = 1; i < 8; ++i) b_free(b, b->f[i]);
     if (b->capture) cudaStreamDestroy(b->capture);
@@ -790,6 +792,8 @@ sg_status sg_batch_set_surrogate(sg_batch* b, const sg_mlp* m) {
             if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
         }
         if (e != cudaSuccess) return b_fail(b, SG_ERR_CUDA, std::string("set surrogate: ") + cudaGetErrorString(e));
+        if (m && !b_ensure(b, b->sur_work, sur_work_bytes(b->P)))
+            return b_fail(b, SG_ERR_OOM, "set surrogate: out of memory");
         drop_graphs(b, true);
         b->mlp = m;
     }

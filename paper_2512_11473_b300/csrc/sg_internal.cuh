@@ -78,6 +78,7 @@ struct sg_grid {
     sg::Buf err;       // int32 sticky device error word
     sg::Buf scratch;   // reusable temporary space (scans, sort)
     sg::Buf stats;     // class counts of the last surrogate integral call
+    sg::Buf sur_work;  // list of network points of the surrogate integrals
     sg::Buf host_pin;  // pinned host word for read-backs
     std::string last_error;
 };
@@ -183,8 +184,11 @@ inline bool default_kernel(const sg_grid_desc& d) {
     return (d.kernel_support == 0.0 || d.kernel_support == 2.0 * d.h) && (d.heaviside_eps == 0.0 || d.heaviside_eps == d.h);
 }
 
-// surrogate (sg_mlp.cu)
-cudaError_t launch_surrogate_integrals(sg_grid* g, const sg_mlp* m, float* W, float* gx, float* gy, float* gz);
+// surrogate (sg_mlp.cu).  Work space of the two-pass surrogate integrals of
+// P packages: a list counter and the list of network points.
+size_t sur_work_bytes(int64_t P);
+cudaError_t launch_surrogate_integrals(sg_grid* g, const sg_mlp* m, void* work, float* W, float* gx, float* gy,
+                                       float* gz);
 // Surrogate constants of a body of spacing h: 1/h (the network inputs),
 // h_up = the least float >= h (a float f has |f| >= h exactly when
 // |f| >= h_up, and |f| < h when |f| < h_up), and the curvature bound
@@ -206,7 +210,8 @@ cudaError_t setup_batch_surrogate();
 // body's constants sb[body[p]]; far packages are left as they are.
 cudaError_t launch_batch_surrogate_integrals(const int32_t* nbr, const uint8_t* type, const int32_t* body,
                                              const SurBody* sb, const float* phi, float* W, float* gx, float* gy,
-                                             float* gz, int64_t P, const sg_mlp* m, int device, cudaStream_t s);
+                                             float* gz, int64_t P, const sg_mlp* m, void* work, int* err, int device,
+                                             cudaStream_t s);
 
 // probe (sg_probe.cu)
 struct ProbeFields {

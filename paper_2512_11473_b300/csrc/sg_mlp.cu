@@ -1,35 +1,44 @@
-// sg_mlp.cu -- the kernel-integral surrogate network: 27 inputs -> 64 -> 64 ->
-// 4 outputs, SiLU hidden activations, BF16 weights and activations, FP32
-// accumulation on the tensor cores (sg_mma.cuh), FP32 master weights and Adam
-// (Kingma & Ba 2015).  Not in the paper: the learned stand-in for the kernel
-// integral of "Integral with SPH Smoothing Kernel and Grid-Particle Coupling".
+// sg_mlp.cu -- the kernel-integral surrogate network on the fifth-generation
+// tensor cores: 27 inputs -> 64 -> 64 -> 4 outputs, SiLU hidden activations,
+// BF16 weights and activations, FP32 accumulation in tensor memory, FP32
+// master weights and Adam (Kingma & Ba 2015).  Not in the paper: the learned
+// stand-in for the kernel integral of "Integral with SPH Smoothing Kernel and
+// Grid-Particle Coupling".
 //
-// Canonical parameter vector (FP32, shared with the host):
-//   W1[64][27], b1[64], W2[64][64], b2[64], W3[4][64], b3[4]   (6212 values)
-// Packed device copy (what the kernels stage in shared memory), BF16 with
-// padded rows so that fragment loads hit distinct banks:
-//   W1t[64][40]  W1 with inputs padded to 32     (B operand of layer 1)
-//   W2 [64][72]                                  (B operand of layer 2)
-//   W3 [8][72]   rows 4..7 zero                  (B operand of layer 3)
-//   W2T[64][72]  transpose of W2                 (B operand of dh1 = dz2 W2)
-//   W3T[64][24]  transpose of W3, outputs padded (B operand of dh2 = dy W3)
-//   then b1[64], b2[64], b3[8] in FP32.
+// Every product is a tcgen05.mma of M = 128 rows (one row per thread of a
+// 128-thread CTA), operands K-major in shared memory (sg_umma.cuh), issued by
+// one thread, completion signalled through an mbarrier:
+//   forward   Z1 = X W1^T, Z2 = A1 W2^T, Y = A2 W3^T           (N = 64, 64, 16)
+//   backward  dA2 = dY W3, dA1 = dZ2 W2                         (N = 64)
+//   gradients [dZ1^T; dZ2^T] [X | A1] (one product, K = the 128 rows): the
+//             diagonal blocks are dW1 and dW2, and a column of ones among X's
+//             padding columns yields the bias gradients db1 and db2.
+// Each CTA writes its partial gradient; a second kernel sums the partials in
+// CTA order (training is reproducible), takes the Adam step and repacks the
+// BF16 weights.
+//
+// Surrogate integrals (sg_kernel_integrals mode 1) run in two passes: pass A
+// stages each package's tiles, classifies every data point, writes the
+// trivial constants and the exact fallback sums (the code of mode 0) and
+// appends network points to a list; pass B takes the list in 128-row tiles,
+// gathers and canonicalises the inputs (sg_sur.cuh) and runs the network.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
 #include <vector>
 
-#include "sg_mlp.cuh"
-#include "sg_mma.cuh"
-#include "sg_integrals.cuh"
-#include "sg_rows.cuh"
+#include "sg_sur.cuh"
 
 struct sg_mlp {
     cudaStream_t stream = nullptr;
     int device = 0;
-    float *master = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+    float *master = nullptr, *m = nullptr, *v = nullptr;
     unsigned char* packed = nullptr;
+    float* part = nullptr;  // per-CTA partial gradients [ctas][MLP_NPARAM] and losses [ctas]
+    int64_t part_ctas = 0;
+    int* err = nullptr;  // device error word (ERR_TIMEOUT)
     int64_t step = 0;
     std::string last_error;
 };
@@ -37,546 +46,679 @@ struct sg_mlp {
 namespace sg {
 namespace {
 
-constexpr int TR_WARPS = 4;
-constexpr int TR_ROWS = 16 * TR_WARPS;  // samples per CTA of the training kernel
-constexpr int SX = MLP_KIN + 8;         // row stride of input tiles (40)
-constexpr int SY = 24;                  // row stride of output-gradient tiles
+constexpr int TC_ROWS = 128;               // rows of a tile = threads of a tensor-core CTA
+constexpr uint32_t WAIT_POLLS = 1u << 20;  // bounded waits for a product (each poll is itself bounded)
 
-// canonical index -> packed placement
-__global__ void k_mlp_pack(const float* __restrict__ master, unsigned char* __restrict__ packed) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= MLP_NPARAM) return;
-    __nv_bfloat16* w = reinterpret_cast<__nv_bfloat16*>(packed);
-    float* bias = reinterpret_cast<float*>(packed + MLP_PACK_BIAS_BYTE);
-    const float v = master[k];
+// ---------------------------------------------------------------------------
+// Parameters: canonical vector <-> packed operands
+// ---------------------------------------------------------------------------
+
+// Place canonical parameter k (value v) in the packed copy.
+__device__ __forceinline__ void pack_param(int k, float v, unsigned char* __restrict__ packed) {
+    using umma::kmajor_byte;
     const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    float* bias = reinterpret_cast<float*>(packed + PK_BIAS);
+    auto put = [&](int off, uint32_t byte) { *reinterpret_cast<__nv_bfloat16*>(packed + off + byte) = b; };
     if (k < MLP_OFF_B1) {
         const int o = k / MLP_IN, i = k % MLP_IN;
-        w[MLP_PK_W1T + o * MLP_S1 + i] = b;
+        put(PK_W1, kmajor_byte(o, i, MLP_K1));
+        if (MLP_SPLIT) put(PK_W1, kmajor_byte(o, MLP_IN + i, MLP_K1));  // the low parts meet the same weight
     } else if (k < MLP_OFF_W2) {
         bias[k - MLP_OFF_B1] = v;
     } else if (k < MLP_OFF_B2) {
         const int o = (k - MLP_OFF_W2) / MLP_H, i = (k - MLP_OFF_W2) % MLP_H;
-        w[MLP_PK_W2 + o * MLP_S2 + i] = b;
-        w[MLP_PK_W2T + i * MLP_S2 + o] = b;
+        put(PK_W2, kmajor_byte(o, i, MLP_H));
+        put(PK_W2T, kmajor_byte(i, o, MLP_H));
     } else if (k < MLP_OFF_W3) {
         bias[MLP_H + k - MLP_OFF_B2] = v;
     } else if (k < MLP_OFF_B3) {
         const int o = (k - MLP_OFF_W3) / MLP_H, i = (k - MLP_OFF_W3) % MLP_H;
-        w[MLP_PK_W3 + o * MLP_S2 + i] = b;
-        w[MLP_PK_W3T + i * MLP_S3T + o] = b;
+        put(PK_W3, kmajor_byte(o, i, MLP_H));
+        put(PK_W3T, kmajor_byte(i, o, MLP_N3));
     } else {
         bias[2 * MLP_H + k - MLP_OFF_B3] = v;
     }
 }
 
-__global__ void k_adam(float* __restrict__ master, float* __restrict__ grad, float* __restrict__ m,
-                       float* __restrict__ v, float lr, float beta1, float beta2, float eps, float c1, float c2) {
+__global__ void k_mlp_pack(const float* __restrict__ master, unsigned char* __restrict__ packed) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= MLP_NPARAM) return;
-    const float g = grad[k];
-    const float mk = beta1 * m[k] + (1.0f - beta1) * g;
-    const float vk = beta2 * v[k] + (1.0f - beta2) * g * g;
-    m[k] = mk;
-    v[k] = vk;
-    master[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
-    grad[k] = 0.0f;
+    if (k < MLP_NPARAM) pack_param(k, master[k], packed);
 }
 
-// Copy the packed weights (bytes, multiple of 16) into shared memory.
-__device__ __forceinline__ void stage_weights(unsigned char* dst, const unsigned char* __restrict__ src, int bytes) {
+// Sum of the per-CTA partials in CTA order: the gradient (and loss) of the
+// whole batch, independent of scheduling.
+__global__ void k_mlp_grad_sum(const float* __restrict__ part, int ctas, float* __restrict__ grad,
+                               float* __restrict__ loss) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < MLP_NPARAM) {
+        float g = 0.0f;
+        for (int c = 0; c < ctas; ++c) g += part[(int64_t)c * MLP_NPARAM + k];
+        grad[k] = g;
+    }
+    if (k == 0 && loss) {
+        float l = 0.0f;
+        for (int c = 0; c < ctas; ++c) l += part[(int64_t)ctas * MLP_NPARAM + c];
+        *loss = l;
+    }
+}
+
+// Ordered sum of the partials, bias-corrected Adam step on the master
+// weights, repacking of the BF16 copy.
+__global__ void k_mlp_adam(const float* __restrict__ part, int ctas, float* __restrict__ master, float* __restrict__ m,
+                           float* __restrict__ v, unsigned char* __restrict__ packed, float lr, float beta1,
+                           float beta2, float eps, float c1, float c2, float* __restrict__ loss) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < MLP_NPARAM) {
+        float g = 0.0f;
+        for (int c = 0; c < ctas; ++c) g += part[(int64_t)c * MLP_NPARAM + k];
+        const float mk = beta1 * m[k] + (1.0f - beta1) * g;
+        const float vk = beta2 * v[k] + (1.0f - beta2) * g * g;
+        m[k] = mk;
+        v[k] = vk;
+        const float w = master[k] - lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+        master[k] = w;
+        pack_param(k, w, packed);
+    }
+    if (k == 0 && loss) {
+        float l = 0.0f;
+        for (int c = 0; c < ctas; ++c) l += part[(int64_t)ctas * MLP_NPARAM + c];
+        *loss = l;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core tile machinery
+// ---------------------------------------------------------------------------
+struct Tc {
+    uint32_t tmem;   // TMEM base address of the CTA's columns
+    uint64_t* bar;   // completion barrier of the products
+    uint32_t phase;  // parity of the next completion
+    bool ok;         // every wait so far completed (uniform over the CTA)
+};
+
+// Warp 0 allocates ncols TMEM columns, thread 0 initialises the barrier.
+__device__ __forceinline__ Tc tc_begin(uint64_t* bar, uint32_t* slot, uint32_t ncols) {
+    if (threadIdx.x < 32) umma::tmem_alloc(slot, ncols);
+    if (threadIdx.x == 0) umma::mbar_init(bar, 1);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    Tc t;
+    t.tmem = *slot;
+    t.bar = bar;
+    t.phase = 0;
+    t.ok = true;
+    return t;
+}
+
+// Make this thread's shared-memory operand stores visible to the tensor
+// core and order its TMEM reads before the next product.
+__device__ __forceinline__ void tc_publish() {
+    umma::fence_smem_to_async();
+    umma::fence_before_sync();
+    __syncthreads();
+}
+
+// D (TMEM columns from tcol) = A B^T, A and B K-major with K columns, N
+// columns of D; thread 0 issues the K / 16 products and commits.
+__device__ __forceinline__ void tc_gemm(const Tc& t, uint32_t tcol, const unsigned char* A, const unsigned char* B,
+                                        int K, int N) {
+    if (threadIdx.x == 0) {
+        umma::fence_after_sync();
+        const uint32_t id = umma::idesc_bf16(TC_ROWS, N), sa = umma::smem_u32(A), sb = umma::smem_u32(B);
+        for (int k = 0; k < K; k += 16)
+            umma::mma(t.tmem + tcol, umma::kslice_desc(sa, K, k), umma::kslice_desc(sb, K, k), id, k > 0 ? 1u : 0u);
+        umma::commit(t.bar);
+    }
+}
+
+// Every thread waits for the products committed last.
+__device__ __forceinline__ bool tc_wait(Tc& t) {
+    const bool done = umma::mbar_wait(t.bar, t.phase, WAIT_POLLS);
+    t.ok = __syncthreads_and(done) != 0;
+    if (t.ok) t.phase ^= 1u;
+    umma::fence_after_sync();
+    return t.ok;
+}
+
+// Free the TMEM columns; after a wait that gave up, first wait (bounded) for
+// the product still in flight and raise ERR_TIMEOUT.
+__device__ __forceinline__ void tc_end(Tc& t, uint32_t ncols, int* err) {
+    if (!t.ok && threadIdx.x == 0) {
+        umma::mbar_wait(t.bar, t.phase, WAIT_POLLS);
+        if (err) atomicOr(err, ERR_TIMEOUT);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    if (threadIdx.x < 32) umma::tmem_dealloc(t.tmem, ncols);
+}
+
+__device__ __forceinline__ uint32_t lane_col(const Tc& t, int col) {
+    return umma::tmem_lane_addr(t.tmem, threadIdx.x >> 5, col);
+}
+
+// 32 consecutive accumulator columns of this thread's row.
+__device__ __forceinline__ void tc_ld32(const Tc& t, int col, float (&v)[32]) {
+    float a[16], b[16];
+    umma::tmem_ld16(lane_col(t, col), a);
+    umma::tmem_ld16(lane_col(t, col + 16), b);
+    umma::tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = a[i], v[16 + i] = b[i];
+}
+
+// Hidden layer out of TMEM: row r of the 64 columns at tcol, plus bias,
+// SiLU, rounded to BF16 into the K-major operand A ([128][64]).
+__device__ __forceinline__ void tc_hidden(const Tc& t, int tcol, const float* bias, unsigned char* A) {
+    const int r = threadIdx.x;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float v[32];
+        tc_ld32(t, tcol + 32 * h, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = silu_(v[i] + bias[32 * h + i]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(A + umma::kmajor_byte(r, 32 * h + 8 * q, MLP_H)) = umma::pack8_bf16(v + 8 * q);
+    }
+}
+
+// The three layers of one 128-row tile: T holds the K-major input rows
+// ([128][K1]) and is reused for the hidden activations ([128][64]); y gets
+// this thread's four outputs.  W is the packed forward part in shared memory.
+__device__ __forceinline__ void tc_forward(Tc& t, const unsigned char* W, unsigned char* T, float (&y)[4]) {
+    const float* bias = reinterpret_cast<const float*>(W + PK_BIAS);
+    tc_publish();
+    tc_gemm(t, 0, T, W + PK_W1, MLP_K1, MLP_H);
+    if (!tc_wait(t)) return;
+    tc_hidden(t, 0, bias, T);  // layer 1 has read the inputs
+    tc_publish();
+    tc_gemm(t, 0, T, W + PK_W2, MLP_H, MLP_H);
+    if (!tc_wait(t)) return;
+    tc_hidden(t, 0, bias + MLP_H, T);
+    tc_publish();
+    tc_gemm(t, 0, T, W + PK_W3, MLP_H, MLP_N3);
+    if (!tc_wait(t)) return;
+    float v[16];
+    umma::tmem_ld16(lane_col(t, 0), v);
+    umma::tmem_wait_ld();
+#pragma unroll
+    for (int o = 0; o < MLP_OUT; ++o) y[o] = v[o] + bias[2 * MLP_H + o];
+}
+
+__device__ __forceinline__ void stage_bytes(unsigned char* dst, const unsigned char* __restrict__ src, int bytes) {
     const uint4* s = reinterpret_cast<const uint4*>(src);
     uint4* d = reinterpret_cast<uint4*>(dst);
     for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = __ldg(s + i);
 }
 
-// Rows of a 16-row input tile: lane pairs load one 64-byte row (27 values
-// plus zero padding, bf16).  Rows past n are zero.
-__device__ __forceinline__ void load_x_tile(__nv_bfloat16* X, const __nv_bfloat16* __restrict__ x,
-                                            const int32_t* __restrict__ idx, int64_t row0, int64_t n) {
-    const int lane = threadIdx.x & 31;
+constexpr int FWD_T = PK_FWD_BYTES;               // tile operand after the forward weights
+constexpr int FWD_BYTES = FWD_T + TC_ROWS * MLP_H * 2;  // (input rows need at most as much as A)
+static_assert(MLP_K1 <= MLP_H, "the input tile fits the activation tile");
+
+// y[n][4] = network(x[n][K1]) on raw input rows.
+__global__ void __launch_bounds__(TC_ROWS) k_mlp_forward(const unsigned char* __restrict__ packed, int64_t n,
+                                                          const __nv_bfloat16* __restrict__ x, float* __restrict__ y,
+                                                          int* err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t slot;
+    stage_bytes(smem, packed, PK_FWD_BYTES);
+    unsigned char* T = smem + FWD_T;
+    Tc t = tc_begin(&bar, &slot, 64);
+    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    for (int64_t tile = blockIdx.x; tile < tiles && t.ok; tile += gridDim.x) {
+        const int64_t row = tile * TC_ROWS + threadIdx.x;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int q = lane + 32 * h;  // 64 quarter-rows of 16 bytes
-        const int r = q >> 2, c = q & 3;
-        const int64_t row = row0 + r;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (row < n) {
-            const int64_t src = idx ? (int64_t)__ldg(idx + row) : row;
-            v = __ldg(reinterpret_cast<const uint4*>(x + src * MLP_KIN) + c);
+        for (int c = 0; c < MLP_K1 / 8; ++c) {
+            const uint4 v = row < n ? __ldg(reinterpret_cast<const uint4*>(x + row * MLP_K1) + c) : make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4*>(T + umma::kmajor_byte(threadIdx.x, 8 * c, MLP_K1)) = v;
         }
-        *reinterpret_cast<uint4*>(X + r * SX + 8 * c) = v;
-    }
-    __syncwarp();
-}
-
-// Forward of one 16-row tile through the three layers; y = output tile
-// values in fragment layout (cols 2t, 2t+1 of rows g, g+8 of n-tile 0).
-// SiLU of the accumulators of n-tiles 2m and 2m + 1 (columns 16m..16m+15),
-// packed as the A fragment of k-tile m of the next layer: the C layout of
-// two adjacent 16x8 tiles is the A layout of one 16x16 tile, so hidden
-// activations never leave the registers.
-__device__ __forceinline__ void silu_to_a(const float (&c0)[4], const float (&c1)[4], uint32_t (&a)[4]) {
-    __nv_bfloat162 v;
-    v = __floats2bfloat162_rn(silu_(c0[0]), silu_(c0[1]));
-    a[0] = *reinterpret_cast<uint32_t*>(&v);
-    v = __floats2bfloat162_rn(silu_(c0[2]), silu_(c0[3]));
-    a[1] = *reinterpret_cast<uint32_t*>(&v);
-    v = __floats2bfloat162_rn(silu_(c1[0]), silu_(c1[1]));
-    a[2] = *reinterpret_cast<uint32_t*>(&v);
-    v = __floats2bfloat162_rn(silu_(c1[2]), silu_(c1[3]));
-    a[3] = *reinterpret_cast<uint32_t*>(&v);
-}
-
-// One 16-row tile through the network: X [16][SX] bf16 inputs in shared
-// memory (27 values, zero padding to 32), weights W and biases as packed;
-// y = the lane's accumulator fragment of the 4 outputs (columns 2t, 2t+1 of
-// rows g and g + 8; columns >= 4 are padding).
-__device__ __forceinline__ void forward_tile(const __nv_bfloat16* W, const float* bias, const __nv_bfloat16* X,
-                                             float (&y)[4]) {
-    const int lane = threadIdx.x & 31, t = lane & 3;
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const float b0 = bias[8 * nt + 2 * t], b1 = bias[8 * nt + 2 * t + 1];
-        acc[nt][0] = b0, acc[nt][1] = b1, acc[nt][2] = b0, acc[nt][3] = b1;
-    }
-    warp_gemm<MLP_KIN, 8>(acc, X, SX, 0, W + MLP_PK_W1T, MLP_S1, 0);
-    uint32_t a[4][4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) silu_to_a(acc[2 * m], acc[2 * m + 1], a[m]);
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const float b0 = bias[MLP_H + 8 * nt + 2 * t], b1 = bias[MLP_H + 8 * nt + 2 * t + 1];
-        acc[nt][0] = b0, acc[nt][1] = b1, acc[nt][2] = b0, acc[nt][3] = b1;
-    }
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            uint32_t b[2];
-            frag_b(b, W + MLP_PK_W2, MLP_S2, 8 * nt, 16 * m);
-            mma_16816(acc[nt], a[m], b);
-        }
-#pragma unroll
-    for (int m = 0; m < 4; ++m) silu_to_a(acc[2 * m], acc[2 * m + 1], a[m]);
-    const float c0 = 2 * t < MLP_OUT ? bias[2 * MLP_H + 2 * t] : 0.0f;
-    const float c1 = 2 * t + 1 < MLP_OUT ? bias[2 * MLP_H + 2 * t + 1] : 0.0f;
-    y[0] = c0, y[1] = c1, y[2] = c0, y[3] = c1;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        uint32_t b[2];
-        frag_b(b, W + MLP_PK_W3, MLP_S2, 0, 16 * m);
-        mma_16816(y, a[m], b);
-    }
-}
-
-// y[n][4] = MLP(x[n][32]); one warp per 16-row tile.
-__global__ void __launch_bounds__(128) k_mlp_forward(const unsigned char* __restrict__ packed, int64_t n,
-                                                      const __nv_bfloat16* __restrict__ x, float* __restrict__ y) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __nv_bfloat16* W = reinterpret_cast<__nv_bfloat16*>(smem);
-    const float* bias = reinterpret_cast<const float*>(smem + MLP_PACK_BIAS_BYTE);
-    stage_weights(smem, packed, MLP_PACK_BYTES);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(smem + MLP_PACK_BYTES) + warp * 16 * SX;
-    __syncthreads();
-    const int64_t tiles = (n + 15) / 16;
-    for (int64_t tile = (int64_t)blockIdx.x * 4 + warp; tile < tiles; tile += (int64_t)gridDim.x * 4) {
-        load_x_tile(X, x, nullptr, tile * 16, n);
         float o[4];
-        forward_tile(W, bias, X, o);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int64_t row = tile * 16 + g + 8 * (i >> 1);
-            const int col = 2 * t + (i & 1);
-            if (row < n && col < MLP_OUT) y[row * MLP_OUT + col] = o[i];
-        }
-        __syncwarp();
+        tc_forward(t, smem, T, o);
+        if (t.ok && row < n) *reinterpret_cast<float4*>(y + row * MLP_OUT) = make_float4(o[0], o[1], o[2], o[3]);
     }
-}
-
-// Shared-memory plan of the training kernel (bytes).
-constexpr int TR_W = MLP_PACK_BYTES;                                   // weights + biases
-constexpr int TR_WARP_BF16 = 16 * SX + 4 * 16 * MLP_S2 + 16 * SY;      // X, A1, A2, DZ2, (spare), DY
-constexpr int TR_WARP_F32 = 2 * 16 * MLP_H;                            // SiLU'(z1), SiLU'(z2)
-constexpr int TR_T_ROWS = MLP_KIN + 3 * MLP_H + 16 + MLP_H;            // XT, A1T, A2T, DZ2T, DYT, DZ1T rows
-constexpr int TR_TS = TR_ROWS + 8;                                     // transposed row stride (72)
-constexpr int TR_BYTES = TR_W + TR_WARPS * (TR_WARP_BF16 * 2 + TR_WARP_F32 * 4) + TR_T_ROWS * TR_TS * 2 + 64;
-
-// Gradient of the mean squared error of one batch (rows idx[0..n) or 0..n)
-// with respect to every canonical parameter, added into grad; the loss is
-// added into *loss.  A CTA takes 64 samples (one 16-row tile per warp), runs
-// forward and backward per tile on the tensor cores, then forms the weight
-// gradients as K = 64 products of the transposed tiles.
-__global__ void __launch_bounds__(TR_WARPS * 32) k_mlp_train(const unsigned char* __restrict__ packed, int64_t n,
-                                                            const __nv_bfloat16* __restrict__ x,
-                                                            const float* __restrict__ tgt,
-                                                            const int32_t* __restrict__ idx, float scale,
-                                                            float* __restrict__ grad, float* __restrict__ loss) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __nv_bfloat16* W = reinterpret_cast<__nv_bfloat16*>(smem);
-    const float* bias = reinterpret_cast<const float*>(smem + MLP_PACK_BIAS_BYTE);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    __nv_bfloat16* wb = reinterpret_cast<__nv_bfloat16*>(smem + TR_W) + warp * TR_WARP_BF16;
-    __nv_bfloat16* X = wb;
-    __nv_bfloat16* A1 = X + 16 * SX;
-    __nv_bfloat16* A2 = A1 + 16 * MLP_S2;
-    __nv_bfloat16* DZ2 = A2 + 16 * MLP_S2;
-    __nv_bfloat16* DY = DZ2 + 2 * 16 * MLP_S2;
-    float* D1 = reinterpret_cast<float*>(smem + TR_W + TR_WARPS * TR_WARP_BF16 * 2) + warp * TR_WARP_F32;
-    float* D2 = D1 + 16 * MLP_H;
-    __nv_bfloat16* T0 =
-        reinterpret_cast<__nv_bfloat16*>(smem + TR_W + TR_WARPS * (TR_WARP_BF16 * 2 + TR_WARP_F32 * 4));
-    __nv_bfloat16* XT = T0;                           // [32][72]
-    __nv_bfloat16* A1T = XT + MLP_KIN * TR_TS;        // [64][72]
-    __nv_bfloat16* A2T = A1T + MLP_H * TR_TS;         // [64][72]
-    __nv_bfloat16* DZ2T = A2T + MLP_H * TR_TS;        // [64][72]
-    __nv_bfloat16* DYT = DZ2T + MLP_H * TR_TS;        // [16][72]
-    __nv_bfloat16* DZ1T = DYT + 16 * TR_TS;           // [64][72]
-
-    stage_weights(smem, packed, MLP_PACK_BYTES);
-    // zero the padded output-gradient tiles (cols 4..15 must stay zero)
-    for (int i = lane; i < 16 * SY; i += 32) DY[i] = __float2bfloat16_rn(0.0f);
-    for (int i = threadIdx.x; i < 16 * TR_TS; i += blockDim.x) DYT[i] = __float2bfloat16_rn(0.0f);
-    __syncthreads();
-
-    const int64_t row0 = (int64_t)blockIdx.x * TR_ROWS + 16 * warp;
-    const int col0 = 16 * warp;  // this warp's sample columns in the transposed tiles
-    load_x_tile(X, x, idx, row0, n);
-    for (int i = lane; i < 16 * MLP_KIN; i += 32) {
-        const int r = i / MLP_KIN, c = i % MLP_KIN;
-        XT[c * TR_TS + col0 + r] = X[r * SX + c];
-    }
-    // ---- forward, keeping SiLU'(z) ----
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const float b0 = bias[8 * nt + 2 * t], b1 = bias[8 * nt + 2 * t + 1];
-        acc[nt][0] = b0, acc[nt][1] = b1, acc[nt][2] = b0, acc[nt][3] = b1;
-    }
-    warp_gemm<MLP_KIN, 8>(acc, X, SX, 0, W + MLP_PK_W1T, MLP_S1, 0);
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = g + 8 * (i >> 1), c = 8 * nt + 2 * t + (i & 1);
-            const float z = acc[nt][i], s = sigmoidf_(z);
-            const __nv_bfloat16 a = __float2bfloat16_rn(z * s);
-            A1[r * MLP_S2 + c] = a;
-            A1T[c * TR_TS + col0 + r] = a;
-            D1[r * MLP_H + c] = s * (1.0f + z * (1.0f - s));
-        }
-    __syncwarp();
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const float b0 = bias[MLP_H + 8 * nt + 2 * t], b1 = bias[MLP_H + 8 * nt + 2 * t + 1];
-        acc[nt][0] = b0, acc[nt][1] = b1, acc[nt][2] = b0, acc[nt][3] = b1;
-    }
-    warp_gemm<MLP_H, 8>(acc, A1, MLP_S2, 0, W + MLP_PK_W2, MLP_S2, 0);
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = g + 8 * (i >> 1), c = 8 * nt + 2 * t + (i & 1);
-            const float z = acc[nt][i], s = sigmoidf_(z);
-            const __nv_bfloat16 a = __float2bfloat16_rn(z * s);
-            A2[r * MLP_S2 + c] = a;
-            A2T[c * TR_TS + col0 + r] = a;
-            D2[r * MLP_H + c] = s * (1.0f + z * (1.0f - s));
-        }
-    __syncwarp();
-    float o[1][4];
-    {
-        const float c0 = 2 * t < MLP_OUT ? bias[2 * MLP_H + 2 * t] : 0.0f;
-        const float c1 = 2 * t + 1 < MLP_OUT ? bias[2 * MLP_H + 2 * t + 1] : 0.0f;
-        o[0][0] = c0, o[0][1] = c1, o[0][2] = c0, o[0][3] = c1;
-    }
-    warp_gemm<MLP_H, 1>(o, A2, MLP_S2, 0, W + MLP_PK_W3, MLP_S2, 0);
-    // ---- loss and dL/dy ----
-    float lsum = 0.0f;
-    float dys[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int r = g + 8 * (i >> 1), c = 2 * t + (i & 1);
-        const int64_t row = row0 + r;
-        float dy = 0.0f;
-        if (row < n && c < MLP_OUT) {
-            const int64_t src = idx ? (int64_t)__ldg(idx + row) : row;
-            const float e = o[0][i] - __ldg(tgt + src * MLP_OUT + c);
-            lsum += e * e * scale;
-            dy = 2.0f * e * scale;
-        }
-        dys[i] = dy;
-        const __nv_bfloat16 b = __float2bfloat16_rn(dy);
-        DY[r * SY + c] = b;
-        DYT[c * TR_TS + col0 + r] = b;
-    }
-    __syncwarp();
-    // bias gradient of layer 3: column sums of dy (over g, i.e. lane bits 2..4)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        float s = dys[j] + dys[j + 2];
-        for (int off = 4; off < 32; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (g == 0 && 2 * t + j < MLP_OUT) atomicAdd(grad + MLP_OFF_B3 + 2 * t + j, s);
-    }
-    for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
-    if (lane == 0 && loss) atomicAdd(loss, lsum);
-    // ---- dh2 = dy W3, dz2 = dh2 SiLU'(z2) ----
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-    warp_gemm<16, 8>(acc, DY, SY, 0, W + MLP_PK_W3T, MLP_S3T, 0);
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        float bs[2] = {0.0f, 0.0f};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = g + 8 * (i >> 1), c = 8 * nt + 2 * t + (i & 1);
-            const float dz = acc[nt][i] * D2[r * MLP_H + c];
-            bs[i & 1] += dz;
-            const __nv_bfloat16 b = __float2bfloat16_rn(dz);
-            DZ2[r * MLP_S2 + c] = b;
-            DZ2T[c * TR_TS + col0 + r] = b;
-        }
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            float s = bs[j];
-            for (int off = 4; off < 32; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (g == 0) atomicAdd(grad + MLP_OFF_B2 + 8 * nt + 2 * t + j, s);
-        }
-    }
-    __syncwarp();
-    // ---- dh1 = dz2 W2, dz1 = dh1 SiLU'(z1) ----
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-    warp_gemm<MLP_H, 8>(acc, DZ2, MLP_S2, 0, W + MLP_PK_W2T, MLP_S2, 0);
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        float bs[2] = {0.0f, 0.0f};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = g + 8 * (i >> 1), c = 8 * nt + 2 * t + (i & 1);
-            const float dz = acc[nt][i] * D1[r * MLP_H + c];
-            bs[i & 1] += dz;
-            DZ1T[c * TR_TS + col0 + r] = __float2bfloat16_rn(dz);
-        }
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            float s = bs[j];
-            for (int off = 4; off < 32; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (g == 0) atomicAdd(grad + MLP_OFF_B1 + 8 * nt + 2 * t + j, s);
-        }
-    }
-    __syncthreads();
-    // ---- weight gradients over the CTA's 64 samples (K = 64) ----
-    // dW1[o][i] = sum_s dz1[s][o] x[s][i]; dW2[o][i] = sum_s dz2[s][o] a1[s][i]
-    {
-        float a4[4][4];
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) a4[nt][0] = a4[nt][1] = a4[nt][2] = a4[nt][3] = 0.0f;
-        warp_gemm<TR_ROWS, 4>(a4, DZ1T, TR_TS, 16 * warp, XT, TR_TS, 0);
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int o_ = 16 * warp + g + 8 * (i >> 1), in = 8 * nt + 2 * t + (i & 1);
-                if (in < MLP_IN) atomicAdd(grad + MLP_OFF_W1 + o_ * MLP_IN + in, a4[nt][i]);
-            }
-    }
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-    warp_gemm<TR_ROWS, 8>(acc, DZ2T, TR_TS, 16 * warp, A1T, TR_TS, 0);
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int o_ = 16 * warp + g + 8 * (i >> 1), in = 8 * nt + 2 * t + (i & 1);
-            atomicAdd(grad + MLP_OFF_W2 + o_ * MLP_H + in, acc[nt][i]);
-        }
-    // dW3[o][i] = sum_s dy[s][o] a2[s][i] (rows o < 4 of a 16-row tile), split by warps over i
-    {
-        float a2[2][4];
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) a2[nt][0] = a2[nt][1] = a2[nt][2] = a2[nt][3] = 0.0f;
-        warp_gemm<TR_ROWS, 2>(a2, DYT, TR_TS, 0, A2T, TR_TS, 16 * warp);
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int o_ = g + 8 * (i >> 1), in = 16 * warp + 8 * nt + 2 * t + (i & 1);
-                if (o_ < MLP_OUT) atomicAdd(grad + MLP_OFF_W3 + o_ * MLP_H + in, a2[nt][i]);
-            }
-    }
+    tc_end(t, 64, err);
 }
 
 // ---------------------------------------------------------------------------
-// Surrogate kernel integrals.  Per data point, from the 6^3 tile of phi around
-// its package (float, the same rounding on host and device):
-//   inputs   v_n = clip(phi_s / h, -1, 1)                   (27 offsets s)
-//   trivial  every tap saturates the Heaviside on one side: W = 1 or 0, G = 0
-//   fallback |phi / h| < 1, or |kappa| h > 0.1 with kappa the 7-point
-//            Laplacian: the exact 27-tap sum (bit-identical to mode 0)
-//   network  everything else: the tensor-core MLP
+// Training: forward, backward and the partial gradient of 128 rows per CTA.
 // ---------------------------------------------------------------------------
+constexpr int NG = MLP_K1 + MLP_H;  // rows of the gradient product's B operand: X^T then A1^T
+constexpr int ONES = MLP_K1 - 1;    // a padding input column: its B row holds ones (bias gradients)
+static_assert(NG % 16 == 0 && NG <= 256, "gradient product width");
+constexpr int TR_X = (PK_BYTES + 127) / 128 * 128;
+constexpr int TR_A1 = TR_X + TC_ROWS * MLP_K1 * 2;
+constexpr int TR_A2 = TR_A1 + TC_ROWS * MLP_H * 2;
+constexpr int TR_DY = TR_A2 + TC_ROWS * MLP_H * 2;
+constexpr int TR_DZ2 = TR_DY + TC_ROWS * MLP_N3 * 2;
+constexpr int TR_AG = TR_DZ2 + TC_ROWS * MLP_H * 2;  // [128 features][128 rows]: dZ1^T then dZ2^T
+constexpr int TR_BG = TR_AG + 128 * TC_ROWS * 2;     // [NG][128 rows]
+constexpr int TR_RED = TR_BG + NG * TC_ROWS * 2;
+constexpr int TR_BYTES = TR_RED + TC_ROWS * 4;
+// TMEM columns of the training kernel
+constexpr int TM_Z1 = 0, TM_Z2 = 64, TM_Y = 128, TM_DA = 192, TM_G = 0;
 
-// |kappa| h > 0.1 with kappa the 7-point Laplacian (sum of the six face
-// neighbours - 6 phi) / h^2, i.e. |a| > 0.1 h for the numerator a, decided
-// as on the real values: the float sum a is within 7 roundings, 2^-21 S, of
-// the exact one (S the float sum of the terms' magnitudes); only when |a|
-// falls within 2^-19 S of the bound is the numerator re-formed in
-// float-float (error about 2^-44 S).
-__device__ __forceinline__ bool curvature_exceeds(float xp, float xm, float yp, float ym, float zp, float zm, float c,
-                                                  const SurConst& C) {
-    const float a = __fadd_rn(__fadd_rn(__fadd_rn(xp, xm), __fadd_rn(yp, ym)),
-                              __fsub_rn(__fadd_rn(zp, zm), __fmul_rn(6.0f, c)));
-    const float S = __fadd_rn(__fadd_rn(__fadd_rn(fabsf(xp), fabsf(xm)), __fadd_rn(fabsf(yp), fabsf(ym))),
-                              __fadd_rn(__fadd_rn(fabsf(zp), fabsf(zm)), __fmul_rn(6.0f, fabsf(c))));
-    const float d = __fsub_rn(fabsf(a), C.kap_thr);
-    if (fabsf(d) > __fmul_rn(0x1p-19f, S) + __fmul_rn(0x1p-22f, C.kap_thr)) return d > 0.0f;
-    ff s = ff_add(two_sum(xp, xm), two_sum(yp, ym));
-    s = ff_add(s, two_sum(zp, zm));
-    s = ff_add(s, two_prod(-6.0f, c));  // -6 phi exactly
-    if (s.hi < 0.0f) s = ff_neg(s);
-    return ff_gt(s, C.kap_thr_ff);
+__device__ __forceinline__ void put_bf16(unsigned char* base, uint32_t byte, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(base + byte) = __float2bfloat16_rn(v);
+}
+__device__ __forceinline__ float get_bf16(const unsigned char* base, uint32_t byte) {
+    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(base + byte));
 }
 
-// Class of a data point from the 6^3 phi tile around its package, on the
-// real values of the float phi (the same decisions as an exact evaluation):
-// trivial where every tap has |phi_s| >= h on one side (the Heaviside
-// saturates), fallback where |phi| < h or |kappa| h > 0.1, network else.
-// v receives the inputs clip(phi_s / h, -1, 1).
-__device__ __forceinline__ int sur_classify(const float* tile, int d, const SurConst& C, float (&v)[MLP_IN]) {
-    const int i = d & 3, j = (d >> 2) & 3, k = d >> 4;
-    const int e0 = (i + 1) + TILE_Y * (j + 1) + TILE_Z * (k + 1);
-    bool all_in = true, all_out = true;
+// Gradient of L = scale * sum over rows and outputs of (y - t)^2 for rows
+// idx[0..n) (or 0..n): CTA c writes part[c][MLP_NPARAM] and its loss share
+// part[gridDim.x * MLP_NPARAM + c].
+__global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* __restrict__ packed, int64_t n,
+                                                           const __nv_bfloat16* __restrict__ x,
+                                                           const float* __restrict__ tgt,
+                                                           const int32_t* __restrict__ idx, float scale,
+                                                           float* __restrict__ part, int* err) {
+    using umma::kmajor_byte;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t slot;
+    const unsigned char* W = smem;
+    const float* bias = reinterpret_cast<const float*>(smem + PK_BIAS);
+    unsigned char *X = smem + TR_X, *A1 = smem + TR_A1, *A2 = smem + TR_A2, *DY = smem + TR_DY,
+                  *DZ2 = smem + TR_DZ2, *AG = smem + TR_AG, *BG = smem + TR_BG;
+    float* red = reinterpret_cast<float*>(smem + TR_RED);
+    stage_bytes(smem, packed, PK_BYTES);
+    const int r = threadIdx.x;
+    const int64_t row = (int64_t)blockIdx.x * TC_ROWS + r;
+    const bool valid = row < n;
+    const int64_t src = valid ? (idx ? (int64_t)__ldg(idx + row) : row) : 0;
+    // inputs: X (K-major rows) and X^T (rows 0..K1-1 of the gradient product's B; row ONES = 1)
+    {
+        __align__(16) __nv_bfloat16 xr[MLP_K1];
+#pragma unroll
+        for (int c = 0; c < MLP_K1 / 8; ++c) {
+            const uint4 v = valid ? __ldg(reinterpret_cast<const uint4*>(x + src * MLP_K1) + c) : make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4*>(X + kmajor_byte(r, 8 * c, MLP_K1)) = v;
+            *reinterpret_cast<uint4*>(xr + 8 * c) = v;
+        }
+#pragma unroll
+        for (int c = 0; c < MLP_K1; ++c)
+            *reinterpret_cast<__nv_bfloat16*>(BG + kmajor_byte(c, r, TC_ROWS)) =
+                c == ONES ? __float2bfloat16_rn(1.0f) : xr[c];
+    }
+    Tc t = tc_begin(&bar, &slot, 256);
+    float* pg = part + (int64_t)blockIdx.x * MLP_NPARAM;
+    do {
+        // layer 1
+        tc_publish();
+        tc_gemm(t, TM_Z1, X, W + PK_W1, MLP_K1, MLP_H);
+        if (!tc_wait(t)) break;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tc_ld32(t, TM_Z1 + 32 * h, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = silu_(v[i] + bias[32 * h + i]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<uint4*>(A1 + kmajor_byte(r, 32 * h + 8 * q, MLP_H)) = umma::pack8_bf16(v + 8 * q);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) put_bf16(BG, kmajor_byte(MLP_K1 + 32 * h + i, r, TC_ROWS), v[i]);
+        }
+        // layer 2
+        tc_publish();
+        tc_gemm(t, TM_Z2, A1, W + PK_W2, MLP_H, MLP_H);
+        if (!tc_wait(t)) break;
+        tc_hidden(t, TM_Z2, bias + MLP_H, A2);
+        // layer 3, loss, dY
+        tc_publish();
+        tc_gemm(t, TM_Y, A2, W + PK_W3, MLP_H, MLP_N3);
+        if (!tc_wait(t)) break;
+        {
+            float v[16], dy[16];
+            umma::tmem_ld16(lane_col(t, TM_Y), v);
+            umma::tmem_wait_ld();
+            float l = 0.0f;
+#pragma unroll
+            for (int o = 0; o < 16; ++o) dy[o] = 0.0f;
+#pragma unroll
+            for (int o = 0; o < MLP_OUT; ++o) {
+                if (valid) {
+                    const float e = v[o] + bias[2 * MLP_H + o] - __ldg(tgt + src * MLP_OUT + o);
+                    l += e * e * scale;
+                    dy[o] = 2.0f * e * scale;
+                }
+            }
+            red[r] = l;
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                *reinterpret_cast<uint4*>(DY + kmajor_byte(r, 8 * q, MLP_N3)) = umma::pack8_bf16(dy + 8 * q);
+        }
+        // dA2 = dY W3, dZ2 = dA2 SiLU'(z2)
+        tc_publish();
+        tc_gemm(t, TM_DA, DY, W + PK_W3T, MLP_N3, MLP_H);
+        if (!tc_wait(t)) break;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float da[32], z[32];
+            tc_ld32(t, TM_DA + 32 * h, da);
+            tc_ld32(t, TM_Z2 + 32 * h, z);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const float zz = z[i] + bias[MLP_H + 32 * h + i], s = sigmoidf_(zz);
+                da[i] *= s * (1.0f + zz * (1.0f - s));
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<uint4*>(DZ2 + kmajor_byte(r, 32 * h + 8 * q, MLP_H)) = umma::pack8_bf16(da + 8 * q);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) put_bf16(AG, kmajor_byte(MLP_H + 32 * h + i, r, TC_ROWS), da[i]);
+        }
+        // dA1 = dZ2 W2, dZ1 = dA1 SiLU'(z1)
+        tc_publish();
+        tc_gemm(t, TM_DA, DZ2, W + PK_W2T, MLP_H, MLP_H);
+        if (!tc_wait(t)) break;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float da[32], z[32];
+            tc_ld32(t, TM_DA + 32 * h, da);
+            tc_ld32(t, TM_Z1 + 32 * h, z);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const float zz = z[i] + bias[32 * h + i], s = sigmoidf_(zz);
+                put_bf16(AG, kmajor_byte(32 * h + i, r, TC_ROWS), da[i] * (s * (1.0f + zz * (1.0f - s))));
+            }
+        }
+        // [dZ1^T; dZ2^T] [X | A1]: dW1, db1 (rows 0..63), dW2, db2 (rows 64..127)
+        tc_publish();
+        tc_gemm(t, TM_G, AG, BG, TC_ROWS, NG);
+        if (!tc_wait(t)) break;
+        {
+            const int m = r;  // gradient row: hidden unit m of layer 1, or m - 64 of layer 2
+#pragma unroll
+            for (int c0 = 0; c0 < NG; c0 += 32) {
+                float v[32];
+                tc_ld32(t, TM_G + c0, v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int c = c0 + i;
+                    if (m < MLP_H) {
+                        if (c < MLP_IN) pg[MLP_OFF_W1 + m * MLP_IN + c] = v[i];
+                        if (c == ONES) pg[MLP_OFF_B1 + m] = v[i];
+                    } else {
+                        if (c >= MLP_K1) pg[MLP_OFF_W2 + (m - MLP_H) * MLP_H + (c - MLP_K1)] = v[i];
+                        if (c == ONES) pg[MLP_OFF_B2 + (m - MLP_H)] = v[i];
+                    }
+                }
+                if (MLP_SPLIT && m < MLP_H) {
+                    // columns 27..53 carry the low parts of the same inputs
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int c = c0 + i;
+                        if (c >= MLP_IN && c < 2 * MLP_IN) pg[MLP_OFF_W1 + m * MLP_IN + (c - MLP_IN)] += v[i];
+                    }
+                }
+            }
+        }
+    } while (false);
+    __syncthreads();
+    if (t.ok) {
+        // dW3 = dY^T A2 and db3 on the CUDA cores (4 x 65 sums over the rows, in row order)
+        for (int e = r; e < MLP_OUT * (MLP_H + 1); e += TC_ROWS) {
+            const int o = e / (MLP_H + 1), i = e % (MLP_H + 1);
+            float s = 0.0f;
+            for (int k = 0; k < TC_ROWS; ++k) {
+                const float dy = get_bf16(DY, kmajor_byte(k, o, MLP_N3));
+                s += i < MLP_H ? dy * get_bf16(A2, kmajor_byte(k, i, MLP_H)) : dy;
+            }
+            if (i < MLP_H)
+                pg[MLP_OFF_W3 + o * MLP_H + i] = s;
+            else
+                pg[MLP_OFF_B3 + o] = s;
+        }
+        if (r == 0) {
+            float l = 0.0f;
+            for (int k = 0; k < TC_ROWS; ++k) l += red[k];
+            part[(int64_t)gridDim.x * MLP_NPARAM + blockIdx.x] = l;
+        }
+    }
+    tc_end(t, 256, err);
+}
+
+// ---------------------------------------------------------------------------
+// Surrogate integrals, pass A: classes, trivial constants, exact fallback,
+// list of network points.
+// ---------------------------------------------------------------------------
+constexpr int SA_THREADS = 256;
+constexpr int SA_PKGS = 16;  // packages per CTA (16 threads per package, a row of four points each)
+
+template <bool BATCH>
+__global__ void __launch_bounds__(SA_THREADS) k_sur_a(const int32_t* __restrict__ nbr, const float* __restrict__ phi,
+                                                      float* __restrict__ W, float* __restrict__ gx,
+                                                      float* __restrict__ gy, float* __restrict__ gz, int64_t P,
+                                                      KernelCoef K, float inv_eps0, SurConst C0,
+                                                      const uint8_t* __restrict__ type,
+                                                      const int32_t* __restrict__ body,
+                                                      const SurBody* __restrict__ sb, int32_t* __restrict__ list,
+                                                      unsigned* __restrict__ count,
+                                                      unsigned long long* __restrict__ stats) {
+    __shared__ int s_nb[SA_PKGS][NB];
+    __shared__ float s_phi[SA_PKGS][TILE_N];
+    __shared__ float s_H[SA_PKGS][TILE_N];
+    __shared__ unsigned s_sat[SA_PKGS];
+    __shared__ unsigned s_triv[SA_PKGS];  // bit 0: every tile value >= h (all points trivially outside), bit 1: <= -h
+    __shared__ SurConst s_C[SA_PKGS];
+    __shared__ float s_ie[SA_PKGS];
+    __shared__ bool s_ok[SA_PKGS];
+    __shared__ unsigned s_cnt[4];
+    const int64_t p0 = 2 + (int64_t)blockIdx.x * SA_PKGS;
+    if (threadIdx.x < SA_PKGS) {
+        const int64_t p = p0 + threadIdx.x;
+        bool ok = p < P;
+        SurConst C = C0;
+        float ie = inv_eps0;
+        if (BATCH && ok) {
+            ok = __ldg(type + p) >= 2;
+            if (ok) {
+                const SurBody q = sb[__ldg(body + p)];
+                C = q.C;
+                ie = q.inv_eps;
+            }
+        }
+        s_ok[threadIdx.x] = ok;
+        s_C[threadIdx.x] = C;
+        s_ie[threadIdx.x] = ie;
+        s_sat[threadIdx.x] = 0;
+        s_triv[threadIdx.x] = 3u;
+    }
+    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < SA_PKGS * NB; e += SA_THREADS) {
+        const int lp = e / NB;
+        if (s_ok[lp]) s_nb[lp][e - lp * NB] = __ldg(nbr + (p0 + lp) * NB + (e - lp * NB));
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < SA_PKGS * 36; e += SA_THREADS) {
+        const int lp = e / 36;
+        if (s_ok[lp]) {
+            const unsigned bits = stage_rows(s_nb[lp], phi, s_ie[lp], e - lp * 36, s_phi[lp], s_H[lp]);
+            if (bits) atomicOr(&s_sat[lp], bits);
+        }
+    }
+    __syncthreads();
+    // whole-package classes: a tile whose every value has |phi| >= h on one side makes every
+    // point's 27 taps trivial (the same exact comparison as sur_class_at)
+    for (int e = threadIdx.x; e < SA_PKGS * 36; e += SA_THREADS) {
+        const int lp = e / 36, rr = e - lp * 36;
+        if (s_ok[lp]) {
+            const float* row = s_phi[lp] + TILE_Y * (rr % 6) + TILE_Z * (rr / 6);
+            const float hu = s_C[lp].h_up;
+            bool out = true, in = true;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                out &= row[i] >= hu;
+                in &= -row[i] >= hu;
+            }
+            const unsigned keep = (out ? 1u : 0u) | (in ? 2u : 0u);
+            if (keep != 3u) atomicAnd(&s_triv[lp], keep);
+        }
+    }
+    __syncthreads();
+    const int lp = threadIdx.x >> 4, rw = threadIdx.x & 15, lane = threadIdx.x & 31;
+    const bool ok = s_ok[lp];
+    const int64_t pt0 = (p0 + lp) * PKG3 + 4 * rw;
+    float w[4], ax[4], ay[4], az[4];
+    unsigned net = 0;
+    if (ok) {
+        const SurConst C = s_C[lp];
+        const unsigned triv = s_triv[lp];
+        unsigned cnt[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int d = 4 * rw + i;
+            const int cls = (triv & 1u)   ? SG_SUR_TRIVIAL_OUT
+                            : (triv & 2u) ? SG_SUR_TRIVIAL_IN
+                                          : sur_class_at(s_phi[lp], tile_e0(d), C);
+            ++cnt[cls];
+            w[i] = cls == SG_SUR_TRIVIAL_IN ? 1.0f : 0.0f;
+            ax[i] = ay[i] = az[i] = 0.0f;
+            if (cls == SG_SUR_FALLBACK) {  // the exact sum exactly as mode 0 forms it
+                if (!integrals_saturated(s_sat[lp], w[i], ax[i], ay[i], az[i]))
+                    integrals_point(s_H[lp], d, K, w[i], ax[i], ay[i], az[i]);
+            } else if (cls == SG_SUR_NETWORK) {
+                net |= 1u << i;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (cnt[c]) atomicAdd(&s_cnt[c], cnt[c]);
+        reinterpret_cast<float4*>(W)[pt0 >> 2] = make_float4(w[0], w[1], w[2], w[3]);
+        reinterpret_cast<float4*>(gx)[pt0 >> 2] = make_float4(ax[0], ax[1], ax[2], ax[3]);
+        reinterpret_cast<float4*>(gy)[pt0 >> 2] = make_float4(ay[0], ay[1], ay[2], ay[3]);
+        reinterpret_cast<float4*>(gz)[pt0 >> 2] = make_float4(az[0], az[1], az[2], az[3]);
+    }
+    // network points: one list reservation per warp
+    const unsigned c = __popc(net);
+    unsigned incl = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned base = 0;
+    if (lane == 31 && total) base = atomicAdd(count, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    unsigned at = base + incl - c;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if (net >> i & 1) list[at++] = (int32_t)(pt0 + i);
+    __syncthreads();
+    if (stats && threadIdx.x < 4 && s_cnt[threadIdx.x])
+        atomicAdd(stats + threadIdx.x, (unsigned long long)s_cnt[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// Surrogate integrals, pass B: the network over the list, 128 rows a tile.
+// ---------------------------------------------------------------------------
+constexpr int SB_POS = PK_FWD_BYTES;                   // canonical input positions [48][27] bytes
+constexpr int SB_T = SB_POS + 1408;                    // tile operand
+constexpr int SB_BYTES = SB_T + TC_ROWS * MLP_H * 2;
+static_assert(SB_T % 128 == 0, "tile alignment");
+
+// The 27 phi values around data point q = 64 p + d, through the index
+// shift of package p.
+__device__ __forceinline__ void gather27(const int32_t* __restrict__ nbr, const float* __restrict__ phi, int64_t q,
+                                         float (&f)[MLP_IN]) {
+    const int64_t p = q >> 6;
+    const int d = (int)(q & 63), i = d & 3, j = (d >> 2) & 3, k = d >> 4;
 #pragma unroll
     for (int n = 0; n < MLP_IN; ++n) {
-        const int sx = n % 3 - 1, sy = (n / 3) % 3 - 1, sz = n / 9 - 1;
-        const float f = tile[e0 + sx + TILE_Y * sy + TILE_Z * sz];
-        all_in &= -f >= C.h_up;
-        all_out &= f >= C.h_up;
-        v[n] = fminf(fmaxf(__fmul_rn(f, C.inv_h), -1.0f), 1.0f);
+        const int ii = i + n % 3 - 1, jj = j + (n / 3) % 3 - 1, kk = k + n / 9 - 1;
+        const int ox = ((ii + 4) >> 2) - 1, oy = ((jj + 4) >> 2) - 1, oz = ((kk + 4) >> 2) - 1;
+        const int slot = 13 + ox + 3 * oy + 9 * oz;
+        const int64_t pk = slot == 13 ? p : (int64_t)__ldg(nbr + p * NB + slot);
+        f[n] = __ldg(phi + pk * PKG3 + (ii - 4 * ox) + PKG * (jj - 4 * oy) + PKG * PKG * (kk - 4 * oz));
     }
-    if (all_in) return SG_SUR_TRIVIAL_IN;
-    if (all_out) return SG_SUR_TRIVIAL_OUT;
-    const float c = tile[e0];
-    if (fabsf(c) < C.h_up) return SG_SUR_FALLBACK;
-    if (curvature_exceeds(tile[e0 + 1], tile[e0 - 1], tile[e0 + TILE_Y], tile[e0 - TILE_Y], tile[e0 + TILE_Z],
-                          tile[e0 - TILE_Z], c, C))
-        return SG_SUR_FALLBACK;
-    return SG_SUR_NETWORK;
 }
 
-constexpr int SU_THREADS = 256;
-constexpr int SU_PK = SU_THREADS / PKG3;  // packages per round
-constexpr int SU_QROWS = SU_PK * PKG3;    // queue rows (all points of a round)
-constexpr int SU_WARPS = SU_THREADS / 32;
-// dynamic shared memory: weights | phi tiles | H tiles | queue rows | queue ids (hidden activations stay in
-// registers, see forward_tile)
-constexpr int SU_OFF_PHI = MLP_PACK_BYTES;
-constexpr int SU_OFF_H = SU_OFF_PHI + SU_PK * TILE_N * 4;
-constexpr int SU_OFF_QX = SU_OFF_H + SU_PK * TILE_N * 4;
-constexpr int SU_OFF_QI = SU_OFF_QX + SU_QROWS * SX * 2;
-constexpr int SU_BYTES = SU_OFF_QI + SU_QROWS * 8;
-static_assert(SU_OFF_H % 16 == 0 && SU_OFF_QX % 16 == 0 && SU_OFF_QI % 16 == 0, "16-byte aligned regions");
-
-// Stage the phi tile (and optionally the Heaviside tile) of package p.
-__device__ __forceinline__ void stage_tile(const int* nb27, const float* __restrict__ phi, float inv_eps, int d,
-                                           float* tphi, float* tH) {
-    stage_rows(nb27, phi, inv_eps, d, tphi, tH);
+// Canonical input row of a point into the tile operand T (row r); returns
+// the transform code.
+__device__ __forceinline__ int canon_row(const float (&f)[MLP_IN], float inv_h, const uint8_t* pos, unsigned char* T,
+                                         int r) {
+    const int code = canon_code(f[13], f[14], f[12], f[16], f[10], f[22], f[4]);
+    const float sgn = (code & 1) ? -1.0f : 1.0f;
+    const uint8_t* ps = pos + (code >> 1) * MLP_IN;
+#pragma unroll
+    for (int c = MLP_SPLIT ? 2 * MLP_IN : MLP_IN; c < MLP_K1; ++c) put_bf16(T, umma::kmajor_byte(r, c, MLP_K1), 0.0f);
+#pragma unroll
+    for (int n = 0; n < MLP_IN; ++n) {
+        const float v = fminf(fmaxf(__fmul_rn(sgn * f[n], inv_h), -1.0f), 1.0f);
+        const int c = ps[n];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        *reinterpret_cast<__nv_bfloat16*>(T + umma::kmajor_byte(r, c, MLP_K1)) = hi;
+        if (MLP_SPLIT) put_bf16(T, umma::kmajor_byte(r, MLP_IN + c, MLP_K1), v - __bfloat162float(hi));
+    }
+    return code;
 }
 
-// BATCH: packages of many bodies in one store; far packages (type < 2) are
-// skipped and each package takes its body's constants.
+// Canonical positions of the 27 inputs under each of the 48 (reflection,
+// permutation) pairs: pos[(rb | perm << 3) * 27 + n].
+__device__ __forceinline__ void build_pos(uint8_t* pos) {
+    for (int e = threadIdx.x; e < 48 * MLP_IN; e += blockDim.x) {
+        const int combo = e / MLP_IN, n = e % MLP_IN;
+        pos[e] = (uint8_t)canon_pos(n, combo & 7, combo >> 3);
+    }
+}
+
 template <bool BATCH>
-__global__ void __launch_bounds__(SU_THREADS) k_sur_integrals(const int32_t* __restrict__ nbr,
-                                                              const float* __restrict__ phi, float* __restrict__ W,
-                                                              float* __restrict__ gx, float* __restrict__ gy,
-                                                              float* __restrict__ gz, int64_t P, KernelCoef K,
-                                                              float inv_eps0, SurConst C0,
-                                                              const unsigned char* __restrict__ packed,
-                                                              unsigned long long* __restrict__ stats,
-                                                              const uint8_t* __restrict__ type,
-                                                              const int32_t* __restrict__ body,
-                                                              const SurBody* __restrict__ sb) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_nb[SU_PK][NB];
-    __shared__ int s_qn;
-    __shared__ unsigned s_cnt[4];
-    const __nv_bfloat16* Wt = reinterpret_cast<const __nv_bfloat16*>(smem);
-    const float* bias = reinterpret_cast<const float*>(smem + MLP_PACK_BIAS_BYTE);
-    float* s_phi = reinterpret_cast<float*>(smem + SU_OFF_PHI);
-    float* s_H = reinterpret_cast<float*>(smem + SU_OFF_H);
-    __nv_bfloat16* s_qx = reinterpret_cast<__nv_bfloat16*>(smem + SU_OFF_QX);
-    int64_t* s_qi = reinterpret_cast<int64_t*>(smem + SU_OFF_QI);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    stage_weights(smem, packed, MLP_PACK_BYTES);
-    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
-    float* outs[4] = {W, gx, gy, gz};
-    const int lp = threadIdx.x >> 6, d = threadIdx.x & 63;
-    const int64_t rounds = (P - 2 + SU_PK - 1) / SU_PK;
-    for (int64_t rd = blockIdx.x; rd < rounds; rd += gridDim.x) {
-        const int64_t p = 2 + rd * SU_PK + lp;
-        const bool valid = p < P && (!BATCH || __ldg(type + (p < P ? p : 0)) >= 2);
-        SurConst C = C0;
-        float inv_eps = inv_eps0;
-        if (BATCH && valid) {
-            const SurBody q = sb[__ldg(body + p)];
-            C = q.C;
-            inv_eps = q.inv_eps;
-        }
-        if (threadIdx.x == 0) s_qn = 0;
-        if (valid && d < NB) s_nb[lp][d] = __ldg(nbr + p * NB + d);
-        __syncthreads();
-        if (valid) stage_tile(s_nb[lp], phi, inv_eps, d, s_phi + lp * TILE_N, s_H + lp * TILE_N);
-        __syncthreads();
+__global__ void __launch_bounds__(TC_ROWS) k_sur_b(const int32_t* __restrict__ nbr, const float* __restrict__ phi,
+                                                   float* __restrict__ W, float* __restrict__ gx,
+                                                   float* __restrict__ gy, float* __restrict__ gz, float inv_h0,
+                                                   const int32_t* __restrict__ body, const SurBody* __restrict__ sb,
+                                                   const int32_t* __restrict__ list, const unsigned* __restrict__ count,
+                                                   const unsigned char* __restrict__ packed, int* err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t slot;
+    stage_bytes(smem, packed, PK_FWD_BYTES);
+    uint8_t* pos = smem + SB_POS;
+    build_pos(pos);
+    unsigned char* T = smem + SB_T;
+    Tc t = tc_begin(&bar, &slot, 64);
+    const int64_t n = (int64_t)*count;
+    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    for (int64_t tile = blockIdx.x; tile < tiles && t.ok; tile += gridDim.x) {
+        const int64_t row = tile * TC_ROWS + threadIdx.x;
+        const bool valid = row < n;
+        int64_t q = 0;
+        int code = 0;
         if (valid) {
-            float v[MLP_IN];
-            const int cls = sur_classify(s_phi + lp * TILE_N, d, C, v);
-            atomicAdd(&s_cnt[cls], 1u);
-            const int64_t at = p * PKG3 + d;
-            if (cls == SG_SUR_NETWORK) {
-                const int q = atomicAdd(&s_qn, 1);
-                __nv_bfloat16* row = s_qx + q * SX;
+            q = (int64_t)__ldg(list + row);
+            float f[MLP_IN];
+            gather27(nbr, phi, q, f);
+            const float inv_h = BATCH ? sb[__ldg(body + (q >> 6))].C.inv_h : inv_h0;
+            code = canon_row(f, inv_h, pos, T, threadIdx.x);
+        } else {
 #pragma unroll
-                for (int n = 0; n < MLP_KIN; ++n) row[n] = __float2bfloat16_rn(n < MLP_IN ? v[n] : 0.0f);
-                s_qi[q] = at;
-            } else if (cls == SG_SUR_FALLBACK) {
-                float w, ax, ay, az;
-                integrals_point(s_H + lp * TILE_N, d, K, w, ax, ay, az);
-                W[at] = w;
-                gx[at] = ax;
-                gy[at] = ay;
-                gz[at] = az;
-            } else {
-                W[at] = cls == SG_SUR_TRIVIAL_IN ? 1.0f : 0.0f;
-                gx[at] = 0.0f;
-                gy[at] = 0.0f;
-                gz[at] = 0.0f;
-            }
+            for (int c = 0; c < MLP_K1 / 8; ++c)
+                *reinterpret_cast<uint4*>(T + umma::kmajor_byte(threadIdx.x, 8 * c, MLP_K1)) = make_uint4(0, 0, 0, 0);
         }
-        __syncthreads();
-        const int qn = s_qn;
-        for (int tile = warp; tile * 16 < qn; tile += SU_WARPS) {
-            __nv_bfloat16* X = s_qx + tile * 16 * SX;
-            // rows past the queue end are zeroed so that the tile is defined
-            for (int r = qn - tile * 16 + (lane >> 2); r < 16; r += 8)
-                if (r >= 0)
-                    for (int c = 8 * (lane & 3); c < 8 * (lane & 3) + 8; ++c) X[r * SX + c] = __float2bfloat16_rn(0.0f);
-            __syncwarp();
-            float y[4];
-            forward_tile(Wt, bias, X, y);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = tile * 16 + g + 8 * (i >> 1), col = 2 * t + (i & 1);
-                if (r < qn && col < MLP_OUT) outs[col][s_qi[r]] = y[i];
-            }
-            __syncwarp();
+        float y[4], o[4];
+        tc_forward(t, smem, T, y);
+        if (t.ok && valid) {
+            uncanon_outputs(code, y, o);
+            W[q] = o[0];
+            gx[q] = o[1];
+            gy[q] = o[2];
+            gz[q] = o[3];
         }
-        __syncthreads();
     }
-    if (stats && threadIdx.x < 4) atomicAdd(stats + threadIdx.x, (unsigned long long)s_cnt[threadIdx.x]);
+    tc_end(t, 64, err);
 }
+
+// ---------------------------------------------------------------------------
+// Classes and training samples
+// ---------------------------------------------------------------------------
+constexpr int SU_THREADS = 256;
+constexpr int SU_PK = SU_THREADS / PKG3;  // packages per CTA
 
 // class of every data point (255 for far packages)
 __global__ void __launch_bounds__(SU_THREADS) k_sur_classify(const int32_t* __restrict__ nbr,
@@ -589,12 +731,9 @@ __global__ void __launch_bounds__(SU_THREADS) k_sur_classify(const int32_t* __re
     const bool act = p >= 2 && p < P;
     if (act && d < NB) s_nb[lp][d] = __ldg(nbr + p * NB + d);
     __syncthreads();
-    if (act) stage_tile(s_nb[lp], phi, 0.0f, d, s_phi[lp], nullptr);
+    if (act) stage_rows(s_nb[lp], phi, 0.0f, d, s_phi[lp], nullptr);
     __syncthreads();
-    if (p < P) {
-        float v[MLP_IN];
-        cls[p * PKG3 + d] = act ? (uint8_t)sur_classify(s_phi[lp], d, C, v) : (uint8_t)255;
-    }
+    if (p < P) cls[p * PKG3 + d] = act ? (uint8_t)sur_class_at(s_phi[lp], tile_e0(d), C) : (uint8_t)255;
 }
 
 __device__ __forceinline__ bool keep_sample(uint64_t seed, int64_t pt, uint32_t keep24) {
@@ -606,8 +745,10 @@ __device__ __forceinline__ bool keep_sample(uint64_t seed, int64_t pt, uint32_t 
     return (uint32_t)(z >> 40) < keep24;
 }
 
-// Training samples: network-class points kept by the hash, in point order.
-// Pass 1 (offsets == nullptr) counts per package; pass 2 writes the rows.
+// Training samples: network-class points kept by the hash, in point order,
+// as canonical input rows and canonical targets (the exact W, G^ carried
+// into the point's canonical frame).  Pass 1 (offsets == nullptr) counts per
+// package; pass 2 writes the rows.
 __global__ void __launch_bounds__(SU_THREADS) k_sur_samples(const int32_t* __restrict__ nbr,
                                                             const float* __restrict__ phi, int64_t P, SurConst C,
                                                             uint64_t seed, uint32_t keep24,
@@ -619,16 +760,18 @@ __global__ void __launch_bounds__(SU_THREADS) k_sur_samples(const int32_t* __res
     __shared__ int s_nb[SU_PK][NB];
     __shared__ float s_phi[SU_PK][TILE_N];
     __shared__ unsigned s_ball[SU_PK][2];
+    __shared__ uint8_t s_pos[48 * MLP_IN];
     const int lp = threadIdx.x >> 6, d = threadIdx.x & 63, lane = threadIdx.x & 31;
     const int64_t p = (int64_t)blockIdx.x * SU_PK + lp;
     const bool act = p >= 2 && p < P;
     if (act && d < NB) s_nb[lp][d] = __ldg(nbr + p * NB + d);
+    if (offsets) build_pos(s_pos);
     __syncthreads();
-    if (act) stage_tile(s_nb[lp], phi, 0.0f, d, s_phi[lp], nullptr);
+    if (act) stage_rows(s_nb[lp], phi, 0.0f, d, s_phi[lp], nullptr);
     __syncthreads();
-    float v[MLP_IN];
+    const int e0 = tile_e0(d);
     const int64_t pt = p * PKG3 + d;
-    const bool take = act && sur_classify(s_phi[lp], d, C, v) == SG_SUR_NETWORK && keep_sample(seed, pt, keep24);
+    const bool take = act && sur_class_at(s_phi[lp], e0, C) == SG_SUR_NETWORK && keep_sample(seed, pt, keep24);
     const unsigned ball = __ballot_sync(0xffffffffu, take);
     if (lane == 0) s_ball[lp][d >> 5] = ball;
     __syncthreads();
@@ -640,12 +783,34 @@ __global__ void __launch_bounds__(SU_THREADS) k_sur_samples(const int32_t* __res
     const int rank = __popc(ball & ((1u << lane) - 1u)) + (d >= 32 ? __popc(s_ball[lp][0]) : 0);
     const int64_t row = (int64_t)offsets[p] + rank;
     if (row >= cap) return;
+    const float* tl = s_phi[lp];
+    float f[MLP_IN];
 #pragma unroll
-    for (int n = 0; n < MLP_KIN; ++n) xo[row * MLP_KIN + n] = __float2bfloat16_rn(n < MLP_IN ? v[n] : 0.0f);
-    to[row * 4 + 0] = W[pt];
-    to[row * 4 + 1] = gx[pt];
-    to[row * 4 + 2] = gy[pt];
-    to[row * 4 + 3] = gz[pt];
+    for (int n = 0; n < MLP_IN; ++n) f[n] = tl[e0 + (n % 3 - 1) + TILE_Y * ((n / 3) % 3 - 1) + TILE_Z * (n / 9 - 1)];
+    const int code = canon_code(f[13], f[14], f[12], f[16], f[10], f[22], f[4]);
+    const float sgn = (code & 1) ? -1.0f : 1.0f;
+    const uint8_t* ps = s_pos + (code >> 1) * MLP_IN;
+    float xr[MLP_K1];
+#pragma unroll
+    for (int c = 0; c < MLP_K1; ++c) xr[c] = 0.0f;
+#pragma unroll
+    for (int n = 0; n < MLP_IN; ++n) {
+        const float v = fminf(fmaxf(__fmul_rn(sgn * f[n], C.inv_h), -1.0f), 1.0f);
+        const int c = ps[n];
+        xr[c] = v;  // dynamic index: a local-memory row, written once per sample
+    }
+#pragma unroll
+    for (int c = 0; c < MLP_IN; ++c) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(xr[c]);
+        xo[row * MLP_K1 + c] = hi;
+        if (MLP_SPLIT) xo[row * MLP_K1 + MLP_IN + c] = __float2bfloat16_rn(xr[c] - __bfloat162float(hi));
+    }
+#pragma unroll
+    for (int c = MLP_SPLIT ? 2 * MLP_IN : MLP_IN; c < MLP_K1; ++c) xo[row * MLP_K1 + c] = __float2bfloat16_rn(0.0f);
+    const float ex[4] = {W[pt], gx[pt], gy[pt], gz[pt]};
+    float tc[4];
+    canon_targets(code, ex, tc);
+    *reinterpret_cast<float4*>(to + row * 4) = make_float4(tc[0], tc[1], tc[2], tc[3]);
 }
 
 // The fallback's curvature bound |kappa| h > 0.1.
@@ -671,9 +836,54 @@ sg_status m_fail(sg_mlp* m, sg_status st, const std::string& msg) {
     return st;
 }
 
+// Persistent grid of a tensor-core kernel: the CTAs that fit on every SM
+// at once by registers, shared memory, threads and the 512 TMEM columns
+// (ncols per CTA), so that no CTA waits for another's columns.
+unsigned tc_grid(const void* fn, int smem, uint32_t ncols, int device, int64_t tiles) {
+    cudaFuncAttributes fa{};
+    int sms = 0, smem_sm = 0, regs_sm = 0;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) cudaGetLastError();
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, device);
+    int per_sm = (int)(512 / ncols);
+    per_sm = std::min(per_sm, 2048 / TC_ROWS);
+    const int regs = (std::max(fa.numRegs, 1) + 7) / 8 * 8;
+    if (regs_sm > 0) per_sm = std::min(per_sm, regs_sm / (regs * TC_ROWS));
+    if (smem_sm > 0) per_sm = std::min(per_sm, smem_sm / (smem + (int)fa.sharedSizeBytes + 1024));
+    int64_t b = (int64_t)std::max(per_sm, 1) * std::max(sms, 1);
+    if (tiles > 0 && b > tiles) b = tiles;
+    return (unsigned)std::max<int64_t>(b, 1);
+}
+
+// Partial-gradient buffer for `ctas` CTAs.
+bool ensure_part(sg_mlp* m, int64_t ctas) {
+    if (m->part && m->part_ctas >= ctas) return true;
+    if (m->part) cudaFree(m->part);
+    m->part = nullptr;
+    m->part_ctas = 0;
+    if (cudaMalloc(&m->part, (size_t)ctas * (MLP_NPARAM + 1) * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        m->part = nullptr;
+        return false;
+    }
+    m->part_ctas = ctas;
+    return true;
+}
+
+cudaError_t launch_train(sg_mlp* m, int64_t n, const void* x, const float* t, const int32_t* idx) {
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_BYTES);
+    if (e != cudaSuccess) return e;
+    k_mlp_train<<<cdiv(n, TC_ROWS), TC_ROWS, TR_BYTES, m->stream>>>(m->packed, n, (const __nv_bfloat16*)x, t, idx,
+                                                                    1.0f / (float)(n * MLP_OUT), m->part, m->err);
+    note_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 const unsigned char* mlp_packed(const sg_mlp* m) { return m->packed; }
+int* mlp_err(const sg_mlp* m) { return m->err; }
 
 }  // namespace sg
 
@@ -689,22 +899,14 @@ sg_status sg_mlp_create(const float* params, void* stream, sg_mlp** out) {
     m->stream = (cudaStream_t)stream;
     cudaGetDevice(&m->device);
     const size_t pb = MLP_NPARAM * sizeof(float);
-    cudaError_t e = cudaMalloc(&m->master, 4 * pb);
-    if (e != cudaSuccess) {
+    if (cudaMalloc(&m->master, 3 * pb + 256) != cudaSuccess || cudaMalloc(&m->packed, PK_BYTES) != cudaSuccess) {
         cudaGetLastError();
-        delete m;
+        sg_mlp_destroy(m);
         return SG_ERR_OOM;
     }
     m->m = m->master + MLP_NPARAM;
     m->v = m->m + MLP_NPARAM;
-    m->grad = m->v + MLP_NPARAM;
-    e = cudaMalloc(&m->packed, MLP_PACK_BYTES);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(m->master);
-        delete m;
-        return SG_ERR_OOM;
-    }
+    m->err = reinterpret_cast<int*>(m->v + MLP_NPARAM);
     sg_status st = sg_mlp_set_params(m, params);
     if (st != SG_OK) {
         sg_mlp_destroy(m);
@@ -718,6 +920,7 @@ sg_status sg_mlp_destroy(sg_mlp* m) {
     if (!m) return SG_ERR_INVALID;
     if (m->master) cudaFree(m->master);
     if (m->packed) cudaFree(m->packed);
+    if (m->part) cudaFree(m->part);
     delete m;
     return SG_OK;
 }
@@ -726,8 +929,8 @@ sg_status sg_mlp_set_params(sg_mlp* m, const float* params) {
     if (!m || !params) return SG_ERR_INVALID;
     const size_t pb = MLP_NPARAM * sizeof(float);
     cudaError_t e = cudaMemcpyAsync(m->master, params, pb, cudaMemcpyHostToDevice, m->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(m->m, 0, 3 * pb, m->stream);  // moments and gradient
-    if (e == cudaSuccess) e = cudaMemsetAsync(m->packed, 0, MLP_PACK_BYTES, m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->m, 0, 2 * pb + sizeof(int), m->stream);  // moments, error word
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->packed, 0, PK_BYTES, m->stream);         // padding stays zero
     if (e == cudaSuccess) {
         k_mlp_pack<<<cdiv(MLP_NPARAM, 256), 256, 0, m->stream>>>(m->master, m->packed);
         note_launch();
@@ -741,21 +944,23 @@ sg_status sg_mlp_set_params(sg_mlp* m, const float* params) {
 
 sg_status sg_mlp_get_params(sg_mlp* m, float* params) {
     if (!m || !params) return SG_ERR_INVALID;
+    int err = 0;
     cudaError_t e = cudaMemcpyAsync(params, m->master, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return m_fail(m, SG_ERR_CUDA, std::string("get_params: ") + cudaGetErrorString(e));
+    if (err) return m_fail(m, SG_ERR_TIMEOUT, "a tensor-core product did not complete in time");
     return SG_OK;
 }
 
 sg_status sg_mlp_forward(sg_mlp* m, int64_t n, const void* x, float* y) {
     if (!m || n < 0 || (n > 0 && (!x || !y))) return SG_ERR_INVALID;
     if (n == 0) return SG_OK;
-    const int smem = MLP_PACK_BYTES + 4 * 16 * SX * 2;
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, FWD_BYTES);
     if (e == cudaSuccess) {
-        unsigned blocks = cdiv(n, 64);
-        if (blocks > 148 * 8) blocks = 148 * 8;
-        k_mlp_forward<<<blocks, 128, smem, m->stream>>>(m->packed, n, (const __nv_bfloat16*)x, y);
+        k_mlp_forward<<<tc_grid((const void*)k_mlp_forward, FWD_BYTES, 64, m->device, tiles), TC_ROWS, FWD_BYTES,
+                        m->stream>>>(m->packed, n, (const __nv_bfloat16*)x, y, m->err);
         note_launch();
         e = cudaGetLastError();
     }
@@ -766,12 +971,11 @@ sg_status sg_mlp_forward(sg_mlp* m, int64_t n, const void* x, float* y) {
 sg_status sg_mlp_loss_grad(sg_mlp* m, int64_t n, const void* x, const float* t, const int32_t* idx, float* grad,
                            float* loss) {
     if (!m || n < 1 || !x || !t || !grad) return SG_ERR_INVALID;
-    cudaError_t e = cudaMemsetAsync(grad, 0, MLP_NPARAM * sizeof(float), m->stream);
-    if (e == cudaSuccess && loss) e = cudaMemsetAsync(loss, 0, sizeof(float), m->stream);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_BYTES);
+    const int64_t ctas = (n + TC_ROWS - 1) / TC_ROWS;
+    if (!ensure_part(m, ctas)) return m_fail(m, SG_ERR_OOM, "loss_grad: out of memory");
+    cudaError_t e = launch_train(m, n, x, t, idx);
     if (e == cudaSuccess) {
-        k_mlp_train<<<cdiv(n, TR_ROWS), TR_WARPS * 32, TR_BYTES, m->stream>>>(
-            m->packed, n, (const __nv_bfloat16*)x, t, idx, 1.0f / (float)(n * MLP_OUT), grad, loss);
+        k_mlp_grad_sum<<<cdiv(MLP_NPARAM, 256), 256, 0, m->stream>>>(m->part, (int)ctas, grad, loss);
         note_launch();
         e = cudaGetLastError();
     }
@@ -782,20 +986,16 @@ sg_status sg_mlp_loss_grad(sg_mlp* m, int64_t n, const void* x, const float* t, 
 sg_status sg_mlp_train_step(sg_mlp* m, int64_t batch, const void* x, const float* t, const int32_t* idx, float lr,
                             float* loss) {
     if (!m || batch < 1 || !x || !t || !(lr >= 0.0f)) return SG_ERR_INVALID;
-    cudaError_t e = cudaSuccess;
-    if (loss) e = cudaMemsetAsync(loss, 0, sizeof(float), m->stream);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_BYTES);
+    const int64_t ctas = (batch + TC_ROWS - 1) / TC_ROWS;
+    if (!ensure_part(m, ctas)) return m_fail(m, SG_ERR_OOM, "train_step: out of memory");
+    cudaError_t e = launch_train(m, batch, x, t, idx);
     if (e == cudaSuccess) {
-        // the gradient buffer is zero here: k_adam clears it after every step
-        k_mlp_train<<<cdiv(batch, TR_ROWS), TR_WARPS * 32, TR_BYTES, m->stream>>>(
-            m->packed, batch, (const __nv_bfloat16*)x, t, idx, 1.0f / (float)(batch * MLP_OUT), m->grad, loss);
         m->step += 1;
         const double b1 = 0.9, b2 = 0.999;
         const float c1 = (float)(1.0 - std::pow(b1, (double)m->step)), c2 = (float)(1.0 - std::pow(b2, (double)m->step));
-        k_adam<<<cdiv(MLP_NPARAM, 256), 256, 0, m->stream>>>(m->master, m->grad, m->m, m->v, lr, (float)b1, (float)b2,
-                                                             1e-8f, c1, c2);
-        k_mlp_pack<<<cdiv(MLP_NPARAM, 256), 256, 0, m->stream>>>(m->master, m->packed);
-        note_launch(3);
+        k_mlp_adam<<<cdiv(MLP_NPARAM, 256), 256, 0, m->stream>>>(m->part, (int)ctas, m->master, m->m, m->v, m->packed,
+                                                                lr, (float)b1, (float)b2, 1e-8f, c1, c2, loss);
+        note_launch();
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return m_fail(m, SG_ERR_CUDA, std::string("train_step: ") + cudaGetErrorString(e));
@@ -873,7 +1073,10 @@ sg_status sg_surrogate_stats(sg_grid* g, int64_t* counts) {
 
 namespace sg {
 
-cudaError_t launch_surrogate_integrals(sg_grid* g, const sg_mlp* m, float* W, float* gx, float* gy, float* gz) {
+size_t sur_work_bytes(int64_t P) { return 256 + ((size_t)(P > 2 ? P - 2 : 0) * PKG3 * 4 + 255) / 256 * 256; }
+
+cudaError_t launch_surrogate_integrals(sg_grid* g, const sg_mlp* m, void* work, float* W, float* gx, float* gy,
+                                       float* gz) {
     cudaError_t e;
     if ((e = launch_set_far(W, 1.0f, 0.0f, g->stream)) != cudaSuccess) return e;
     if ((e = launch_set_far(gx, 0.0f, 0.0f, g->stream)) != cudaSuccess) return e;
@@ -881,20 +1084,21 @@ cudaError_t launch_surrogate_integrals(sg_grid* g, const sg_mlp* m, float* W, fl
     if ((e = launch_set_far(gz, 0.0f, 0.0f, g->stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(g->stats.p, 0, 4 * sizeof(unsigned long long), g->stream)) != cudaSuccess) return e;
     if (g->P <= 2) return cudaSuccess;
-    if ((e = cudaFuncSetAttribute(k_sur_integrals<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SU_BYTES)) !=
+    unsigned* count = (unsigned*)work;
+    int32_t* list = (int32_t*)((char*)work + 256);
+    if ((e = cudaMemsetAsync(count, 0, sizeof(unsigned), g->stream)) != cudaSuccess) return e;
+    const int32_t* nbr = (const int32_t*)g->nbr.p;
+    const float* phi = (const float*)g->field[SG_FIELD_PHI].p;
+    k_sur_a<false><<<cdiv(g->P - 2, SA_PKGS), SA_THREADS, 0, g->stream>>>(
+        nbr, phi, W, gx, gy, gz, g->P, kernel_coef(), (float)(1.0 / g->desc.h), sur_const(g), nullptr, nullptr,
+        nullptr, list, count, (unsigned long long*)g->stats.p);
+    if ((e = cudaFuncSetAttribute(k_sur_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SB_BYTES)) !=
         cudaSuccess)
         return e;
-    int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sur_integrals<false>, SU_THREADS, SU_BYTES);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-    const int64_t rounds = (g->P - 2 + SU_PK - 1) / SU_PK;
-    int64_t blocks = (int64_t)(per_sm < 1 ? 1 : per_sm) * (sms < 1 ? 1 : sms);
-    if (blocks > rounds) blocks = rounds;
-    k_sur_integrals<false><<<(unsigned)blocks, SU_THREADS, SU_BYTES, g->stream>>>(
-        (const int32_t*)g->nbr.p, (const float*)g->field[SG_FIELD_PHI].p, W, gx, gy, gz, g->P, kernel_coef(),
-        (float)(1.0 / g->desc.h), sur_const(g), m->packed, (unsigned long long*)g->stats.p, nullptr, nullptr,
-        nullptr);
-    note_launch();
+    k_sur_b<false><<<tc_grid((const void*)k_sur_b<false>, SB_BYTES, 64, g->device, 0), TC_ROWS, SB_BYTES, g->stream>>>(
+        nbr, phi, W, gx, gy, gz, (float)(1.0 / g->desc.h), nullptr, nullptr, list, count, m->packed,
+        (int*)g->err.p);
+    note_launch(2);
     return cudaGetLastError();
 }
 
@@ -906,23 +1110,23 @@ SurBody sur_body(double h) {
 }
 
 cudaError_t setup_batch_surrogate() {
-    return cudaFuncSetAttribute(k_sur_integrals<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SU_BYTES);
+    return cudaFuncSetAttribute(k_sur_b<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SB_BYTES);
 }
 
 cudaError_t launch_batch_surrogate_integrals(const int32_t* nbr, const uint8_t* type, const int32_t* body,
                                              const SurBody* sb, const float* phi, float* W, float* gx, float* gy,
-                                             float* gz, int64_t P, const sg_mlp* m, int device, cudaStream_t s) {
+                                             float* gz, int64_t P, const sg_mlp* m, void* work, int* err, int device,
+                                             cudaStream_t s) {
     if (P <= 2) return cudaSuccess;
-    int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sur_integrals<true>, SU_THREADS, SU_BYTES);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    const int64_t rounds = (P - 2 + SU_PK - 1) / SU_PK;
-    int64_t blocks = (int64_t)(per_sm < 1 ? 1 : per_sm) * (sms < 1 ? 1 : sms);
-    if (blocks > rounds) blocks = rounds;
-    k_sur_integrals<true><<<(unsigned)blocks, SU_THREADS, SU_BYTES, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(),
-                                                                         0.0f, SurConst{}, m->packed, nullptr, type,
-                                                                         body, sb);
-    note_launch();
+    unsigned* count = (unsigned*)work;
+    int32_t* list = (int32_t*)((char*)work + 256);
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    k_sur_a<true><<<cdiv(P - 2, SA_PKGS), SA_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(), 0.0f,
+                                                              SurConst{}, type, body, sb, list, count, nullptr);
+    k_sur_b<true><<<tc_grid((const void*)k_sur_b<true>, SB_BYTES, 64, device, 0), TC_ROWS, SB_BYTES, s>>>(
+        nbr, phi, W, gx, gy, gz, 0.0f, body, sb, list, count, m->packed, err);
+    note_launch(2);
     return cudaGetLastError();
 }
 

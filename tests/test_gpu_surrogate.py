@@ -1,9 +1,10 @@
 """The surrogate network and the surrogate kernel integrals on the GPU.
 
 Forward and gradients against the FP64 oracle on the same BF16-rounded
-weights and inputs; classification against the oracle's float replica;
+weights and inputs; classification against the oracle's FP64 decision;
 trivial and fallback points against the exact integrals; network points
-against the oracle network; sample gathering; a short training run.
+against the oracle network on the oracle's canonical inputs; sample
+gathering in the canonical frame; reproducible training.
 """
 import numpy as np
 import pytest
@@ -100,6 +101,22 @@ def test_train_step_matches_oracle_adam(sg):
     assert np.max(np.abs(got - p)) <= 1e-6
 
 
+def test_training_is_reproducible(sg):
+    """The partial gradients of the CTAs are summed in a fixed order: two
+    trainings from the same start on the same batches end bit for bit equal."""
+    x, t = _data(6, 4096)
+    X = rows32(x)
+    T = torch.from_numpy(t.astype(np.float32)).cuda()
+    idx = torch.from_numpy(np.random.default_rng(2).permutation(4096)[:2500].astype(np.int32)).cuda()
+    out = []
+    for _ in range(2):
+        net = sg.MLP(si.mlp_init_params(17))
+        for s in range(20):
+            net.train_step(X, T, idx if s % 2 else None, 2e-3)
+        out.append(net.get_params())
+    assert np.array_equal(out[0], out[1])
+
+
 def test_training_reduces_loss(sg):
     net = sg.MLP(si.mlp_init_params(15))
     x, t = _data(5, 8192)
@@ -162,18 +179,20 @@ def test_surrogate_integrals(sg, name):
     assert torch.all(g.field("W")[tin] == 1) and torch.all(g.field("W")[tout] == 0)
     for f in ("Gx", "Gy", "Gz"):
         assert torch.all(g.field(f)[tin | tout] == 0)
-    # network points against the oracle network on the same inputs
-    phi = g.field("phi").cpu().numpy().astype(np.float64)
-    xin = oracle.surrogate_inputs(spec, g.field("nbr").cpu().numpy(), phi)
+    # network points against the oracle network on the oracle's canonical inputs, carried back
+    phi = g.field("phi").cpu().numpy()
+    xin, code = oracle.surrogate_canonical(spec, g.field("nbr").cpu().numpy(), phi)
     net_pts = (cls == 3).cpu().numpy()
     xr = bf16_round(xin[net_pts].astype(np.float32))
-    ref = oracle.mlp_forward(bf16_round(par), xr)
+    ref = oracle.surrogate_uncanon(code[net_pts], oracle.mlp_forward(bf16_round(par), xr))
     got = np.stack([g.field(f).cpu().numpy()[net_pts] for f in ("W", "Gx", "Gy", "Gz")], 1)
     scale = np.abs(ref).max()
     assert np.max(np.abs(got - ref)) <= 2e-2 * scale
 
 
 def test_surrogate_samples(sg):
+    """Samples are the network points in point order: canonical inputs (the
+    oracle's frame, BF16) and the exact integrals carried into that frame."""
     shape, spec = CASES["torus_rot"]
     g = _grid(sg, shape, spec)
     g.kernel_integrals()
@@ -181,12 +200,15 @@ def test_surrogate_samples(sg):
     cls = g.surrogate_classify().cpu().numpy()
     sel = cls == 3
     assert n == sel.sum() == x.shape[0]
-    phi = g.field("phi").cpu().numpy().astype(np.float64)
-    xin = oracle.surrogate_inputs(spec, g.field("nbr").cpu().numpy(), phi)[sel]
+    xin, code = oracle.surrogate_canonical(spec, g.field("nbr").cpu().numpy(), g.field("phi").cpu().numpy())
+    xin, code = xin[sel], code[sel]
     assert np.max(np.abs(x.float().cpu().numpy()[:, :27] - bf16_round(xin.astype(np.float32)))) <= 1e-6
     assert torch.all(x[:, 27:] == 0)
-    W = g.field("W").cpu().numpy()[sel]
-    assert np.array_equal(t[:, 0].cpu().numpy(), W)
+    exact = np.stack([g.field(f).cpu().numpy()[sel] for f in ("W", "Gx", "Gy", "Gz")], 1).astype(np.float64)
+    back = oracle.surrogate_uncanon(code, t.cpu().numpy())
+    assert np.max(np.abs(back - exact)) <= 1e-7
+    # the frame permutes and negates the components of G^: their magnitudes are kept exactly
+    assert np.array_equal(np.sort(np.abs(t[:, 1:].cpu().numpy()), 1), np.sort(np.abs(exact[:, 1:]), 1).astype(np.float32))
     # sub-sampling keeps a deterministic subset of about the requested size
     x2, t2, n2 = g.surrogate_samples(seed=4, keep=0.25)
     x3, t3, n3 = g.surrogate_samples(seed=4, keep=0.25)

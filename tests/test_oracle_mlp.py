@@ -142,3 +142,42 @@ def test_surrogate_class_curvature_bound(sign):
         cls, ties = oracle.surrogate_class(spec, G.nbr, phi, ties=True)
         assert cls[p0, d0] == want, (kh, sign, cls[p0, d0])
         assert ties == 0
+
+
+def _integrals_of_inputs(x):
+    """(W, G^) of rows of 27 clipped inputs v by the definitions: W = sum of
+    w_s H(-v_s) over the sum of w_s, G^ = sum of w'(|s|) (-s/|s|) H(-v_s)
+    over the same sum, H(z) = (1 + z + sin(pi z)/pi) / 2."""
+    s = np.array([(n % 3 - 1, (n // 3) % 3 - 1, n // 9 - 1) for n in range(27)], np.float64)
+    q = np.sqrt((s ** 2).sum(1))
+    w = np.array([oracle.wendland(v) for v in q])
+    dw = np.array([oracle.wendland_dq(v) / v if v > 0 else 0.0 for v in q])
+    H = 0.5 * (1.0 - x - np.sin(np.pi * x) / np.pi)
+    W = H @ w / w.sum()
+    G = H @ (dw[:, None] * -s) / w.sum()
+    return np.concatenate([W[:, None], G], 1)
+
+
+@pytest.mark.parametrize("case", ["sphere", "torus_rot"])
+def test_surrogate_canonical_frame_is_a_symmetry(case):
+    """The integrals of the canonical inputs, carried back by the frame,
+    equal the integrals of the point (so the sign, reflection and
+    permutation of every frame are a symmetry of W and G^); the canonical
+    centre value is >= 0 and the canonical central differences are >= 0."""
+    if case == "sphere":
+        shape, spec = si.sphere_small()
+    else:
+        shape = si.torus(0.45, 0.15, rot=si.random_rotation(si.Stream(21)))
+        spec = si.GridSpec((-0.8,) * 3, (20, 20, 20), 0.02)
+    G = oracle.build_grid(spec, shape)
+    phi32 = G.phi.astype(np.float32)
+    x, code = oracle.surrogate_canonical(spec, G.nbr, phi32)
+    ref = np.stack(oracle.kernel_integrals(spec, G.nbr, phi32.astype(np.float64)), -1)[2:].reshape(-1, 4)
+    xc = x[2:].reshape(-1, 27)
+    got = oracle.surrogate_uncanon(code[2:].reshape(-1), _integrals_of_inputs(xc))
+    assert np.max(np.abs(got - ref)) < 1e-13
+    assert np.all(xc[:, 13] >= 0)
+    for a, (plus, minus) in enumerate(((14, 12), (16, 10), (22, 4))):
+        assert np.all(xc[:, plus] - xc[:, minus] >= 0), a
+    # every one of the 48 frames occurs on these bodies except where symmetry forbids; many do
+    assert len(np.unique(code[2:] >> 1)) >= 24
