@@ -63,6 +63,22 @@ def combine_over_ranks(seconds: float, units: float, backend_device=None):
     return float(t.item()), float(u.item())
 
 
+def partition_bodies(weights, world):
+    """Independent bodies over `world` ranks by package count, greedy
+    largest-first (each body, heaviest first, goes to the least-loaded rank;
+    ties to the lower rank): no rank exchanges data with another.  The
+    heaviest rank carries at most the mean load plus the heaviest body.
+    Returns one list of body indices per rank, each in increasing order."""
+    order = sorted(range(len(weights)), key=lambda i: (-float(weights[i]), i))
+    loads = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (loads[k], k))
+        parts[r].append(i)
+        loads[r] += float(weights[i])
+    return [sorted(p) for p in parts]
+
+
 def barrier():
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
@@ -281,10 +297,16 @@ def batch_section(sg, torch, n_bodies=256, iters=20, reps=5, seed=1):
     rotations, package counts log-uniform in [1e2, 1e5]) swept together by
     one autotuned batch plan, against one sphere of equal package count
     through the single-grid calls.  Both time the same sweeps per run:
-    gradient, smoothed sign, `iters` reinit sweeps, exact integrals."""
+    gradient, smoothed sign, `iters` reinit sweeps, exact integrals.  With
+    several ranks the bodies are partitioned by package count
+    (partition_bodies) and every rank runs its share as its own batch; times
+    are the maximum over ranks, points the sum."""
+    ws, rank, _ = dist_env()
     bodies = si.random_bodies(n_bodies, seed=seed)
+    mine = partition_bodies([t for _, _, t in bodies], ws)[rank] if ws > 1 else list(range(n_bodies))
     grids = []
-    for shape, spec, _ in bodies:
+    for b in mine:
+        shape, spec, _ = bodies[b]
         g = sg.Grid(spec)
         g.tag_allocate(shape)
         g.init_sdf(shape)
@@ -298,6 +320,7 @@ def batch_section(sg, torch, n_bodies=256, iters=20, reps=5, seed=1):
     Ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     batch.run(plan)
     torch.cuda.synchronize()
+    barrier()
     e0, e1 = Ev(), Ev()
     e0.record()
     for _ in range(reps):
@@ -306,6 +329,8 @@ def batch_section(sg, torch, n_bodies=256, iters=20, reps=5, seed=1):
     torch.cuda.synchronize()
     batch_ms = e0.elapsed_time(e1) / reps
     batch.close()
+    sweeps = iters + 2
+    b_sec, b_pts = combine_over_ranks(batch_ms * 1e-3, float(n_pt), "cuda")
 
     shape, spec = sphere_with_packages(P_tot)
     g = sg.Grid(spec)
@@ -319,6 +344,7 @@ def batch_section(sg, torch, n_bodies=256, iters=20, reps=5, seed=1):
 
     single()
     torch.cuda.synchronize()
+    barrier()
     e0.record()
     for _ in range(reps):
         single()
@@ -327,15 +353,19 @@ def batch_section(sg, torch, n_bodies=256, iters=20, reps=5, seed=1):
     single_ms = e0.elapsed_time(e1) / reps
     n1 = 64 * (P1 - 2)
     g.close()
-    sweeps = iters + 2
-    b_rate = n_pt * sweeps / (batch_ms * 1e-3)
-    s_rate = n1 * sweeps / (single_ms * 1e-3)
-    return {"bodies": n_bodies, "packages": P_tot, "points": n_pt, "sweeps_per_run": sweeps,
-            "plan": {"pkgs_per_item": plan.pkgs_per_item, "depth": plan.depth},
-            "autotune_ms": {"%d,%d" % k: v for k, v in times.items()},
-            "run_ms": batch_ms, "cell_updates_per_s": b_rate,
-            "single_body": {"packages": P1, "points": n1, "run_ms": single_ms, "cell_updates_per_s": s_rate},
-            "batch_over_single": b_rate / s_rate}
+    s_sec, s_pts = combine_over_ranks(single_ms * 1e-3, float(n1), "cuda")
+    b_rate = b_pts * sweeps / b_sec
+    s_rate = s_pts * sweeps / s_sec
+    out = {"bodies": n_bodies, "packages": P_tot, "points": n_pt, "sweeps_per_run": sweeps,
+           "plan": {"pkgs_per_item": plan.pkgs_per_item, "depth": plan.depth},
+           "autotune_ms": {"%d,%d" % k: v for k, v in times.items()},
+           "run_ms": batch_ms, "cell_updates_per_s": b_rate,
+           "single_body": {"packages": P1, "points": n1, "run_ms": single_ms, "cell_updates_per_s": s_rate},
+           "batch_over_single": b_rate / s_rate}
+    if ws > 1:
+        out["partition"] = {"ranks": ws, "rule": "greedy largest-first by target package count, no collective",
+                            "bodies_rank0": len(mine) if rank == 0 else None, "run_ms_max_over_ranks": 1e3 * b_sec}
+    return out
 
 
 def consistency_section(sg, torch, reps=3, frac=0.2, seed=17):
@@ -488,14 +518,18 @@ def relax_section(sg, torch, net, trained, n_particles=100_000_000, steps=50, n_
     -0.1 h clip(phi/h, -1, 1) n.  Positions are restored between timed
     replays (outside the timed region)."""
     t0 = time.perf_counter()
+    ws, rank, _ = dist_env()
     bodies = si.random_bodies(n_bodies, seed=seed)
+    mine = partition_bodies([t for _, _, t in bodies], ws)[rank] if ws > 1 else list(range(n_bodies))
     grids = []
-    for shape, spec, _ in bodies:
+    for b in mine:
+        shape, spec, _ = bodies[b]
         g = sg.Grid(spec)
         g.tag_allocate(shape)
         g.init_sdf(shape)
         grids.append(g)
-    x, y, z, off = si.relax_particles(bodies, n_particles, seed=5)
+    x, y, z, off = si.relax_particles(bodies, n_particles, seed=5, subset=mine)
+    n_mine = int(off[-1])
     gen_s = time.perf_counter() - t0
     X0 = [torch.from_numpy(v).cuda() for v in (x, y, z)]
     del x, y, z
@@ -517,6 +551,8 @@ def relax_section(sg, torch, net, trained, n_particles=100_000_000, steps=50, n_
             batch.reset()
             for v, v0 in zip(X, X0):
                 v.copy_(v0)
+            torch.cuda.synchronize()
+            barrier()
             e0, e1 = Ev(), Ev()
             e0.record()
             batch.relax(*X, off, steps, 0.1, plan=plan, sweeps=sweeps, out=out)
@@ -528,12 +564,15 @@ def relax_section(sg, torch, net, trained, n_particles=100_000_000, steps=50, n_
 
     full_ms = timed(True)
     relax_ms = timed(False)
+    full_s, pts = combine_over_ranks(full_ms * 1e-3, float(n_mine), "cuda")
+    relax_s, _ = combine_over_ranks(relax_ms * 1e-3, float(n_mine), "cuda")
+    full_ms, relax_ms = 1e3 * full_s, 1e3 * relax_s
     # moved distance after the 50 steps, a check that the run relaxed something
     moved = float(torch.sqrt(sum((a - b) ** 2 for a, b in zip(X, X0))).max())
     batch.close()
     step_ms = relax_ms / steps
     n_out = len(out)
-    alg_bytes = n_particles * (24 + 4 * n_out) + 32 * 64 * P_act
+    alg_bytes = n_mine * (24 + 4 * n_out) + 32 * 64 * P_act  # this rank's launch
     hbm, kind = measured_peaks()
     achieved = alg_bytes / (step_ms * 1e-3) / 1e9
     return {"workload": "%d mixed bodies (first %d of the 256-body batch, seed %d), %d particles near their surfaces, "
@@ -543,8 +582,10 @@ def relax_section(sg, torch, net, trained, n_particles=100_000_000, steps=50, n_
             "plan": {"pkgs_per_item": plan.pkgs_per_item, "depth": plan.depth},
             "surrogate_weights": "trained (surrogate section)" if trained else "random-init (surrogate not trained)",
             "graph_ms": full_ms, "relax_only_ms": relax_ms, "sweeps_ms": full_ms - relax_ms, "step_ms": step_ms,
-            "particle_steps_per_s": n_particles * steps / (relax_ms * 1e-3),
-            "pipeline_particle_steps_per_s": n_particles * steps / (full_ms * 1e-3),
+            "particle_steps_per_s": pts * steps / (relax_ms * 1e-3),
+            "pipeline_particle_steps_per_s": pts * steps / (full_ms * 1e-3),
+            "partition": ({"ranks": ws, "rule": "greedy largest-first by target package count, no collective"}
+                          if ws > 1 else None),
             "roofline": {"kernel": "k_batch_relax", "bound": "hbm", "achieved": achieved, "peak": hbm,
                          "unit": "GB/s", "frac": achieved / hbm, "peak_kind": kind,
                          "algorithmic_bytes_per_launch": alg_bytes},

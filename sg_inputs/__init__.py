@@ -388,30 +388,35 @@ def body_band_particles(shape: Shape, n, half_width, seed=0, jitter=0.0):
     return tuple(np.ascontiguousarray(w[:, a], dtype=np.float32) for a in range(3))
 
 
-def relax_particles(bodies, n_total, seed=5, band_cells=2.0, jitter_h=0.5):
+def relax_particles(bodies, n_total, seed=5, band_cells=2.0, jitter_h=0.5, subset=None):
     """Particles of a batch relaxation: n_total points over the bodies of
     ``random_bodies``, body b getting a share proportional to its target
     package count (so particles per package are about equal), sampled by
     ``body_band_particles`` with half-width band_cells coarse cells, jitter
     jitter_h fine cells and seed seed + b, stored body after body.
-    Returns (x, y, z, offsets) with offsets[b] the first particle of body b."""
+    subset: indices of the bodies to generate (their shares stay those of the
+    whole set, so that the bodies of a partition get the particles they have
+    in the whole run).  Returns (x, y, z, offsets) with offsets[k] the first
+    particle of the k-th generated body."""
     tgt = np.array([t for _, _, t in bodies], dtype=np.float64)
     share = np.floor(n_total * tgt / tgt.sum()).astype(np.int64)
     rest = int(n_total - share.sum())
     share[:rest] += 1
-    offsets = np.zeros(len(bodies) + 1, dtype=np.int64)
-    offsets[1:] = np.cumsum(share)
-    out = [np.empty(int(n_total), dtype=np.float32) for _ in range(3)]
+    which = list(range(len(bodies))) if subset is None else [int(b) for b in subset]
+    offsets = np.zeros(len(which) + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(share[which])
+    out = [np.empty(int(offsets[-1]), dtype=np.float32) for _ in range(3)]
 
-    def one(b):  # bodies draw from their own streams: any schedule gives the same arrays
+    def one(k):  # bodies draw from their own streams: any schedule gives the same arrays
+        b = which[k]
         shape, spec, _ = bodies[b]
         v = body_band_particles(shape, int(share[b]), band_cells * spec.lc, seed=seed + b, jitter=jitter_h * spec.h)
         for a in range(3):
-            out[a][offsets[b]:offsets[b + 1]] = v[a]
+            out[a][offsets[k]:offsets[k + 1]] = v[a]
 
     import concurrent.futures as cf
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
-        list(ex.map(one, range(len(bodies))))
+        list(ex.map(one, range(len(which))))
     return out[0], out[1], out[2], offsets
 
 
