@@ -592,15 +592,16 @@ def relax_section(sg, torch, net, trained, n_particles=100_000_000, steps=50, n_
             "max_displacement": moved, "setup_seconds": gen_s}
 
 
-def surrogate_section(sg, torch, steps=12000, samples=20_000_000):
+def surrogate_section(sg, torch, steps=300_000, batch=16384, samples=20_000_000):
     """Learned kernel integral: training samples from 500 random bodies
-    (seed 4, exact integrals as labels), `steps` Adam steps of batch 8192 on
-    the library's own kernels, then the exact and the surrogate integrals of
+    (seed 4, 20 reinit sweeps, exact integrals as labels, in each point's
+    canonical frame), `steps` Adam steps of `batch` samples on the library's
+    own tensor-core kernels, then the exact and the surrogate integrals of
     the h = 0.002 torus after 50 reinit sweeps: times and errors."""
     from paper_2512_11473_b300 import surrogate as S
     X, T, info = S.collect_samples(target=samples)
     net = sg.MLP(si.mlp_init_params(4))
-    hist, secs = S.train(net, X, T, steps=steps, log_every=steps // 4)
+    hist, secs = S.train(net, X, T, steps=steps, batch=batch, log_every=steps // 4)
     del X, T
     shape, spec = si.torus_large()
     g = sg.Grid(spec)
@@ -609,7 +610,7 @@ def surrogate_section(sg, torch, steps=12000, samples=20_000_000):
     g.reinit(50, CFL)
     r = S.evaluate(g, net)
     g.close()
-    r["training"] = {"samples": info, "steps": steps, "batch": 8192, "seconds": secs,
+    r["training"] = {"samples": info, "steps": steps, "batch": batch, "lr": 3e-3, "seconds": secs,
                      "loss": [[a, b] for a, b in hist]}
     return r, net
 

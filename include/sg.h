@@ -502,9 +502,13 @@ SG_API sg_status sg_surrogate_stats(sg_grid *g, int64_t counts[4]);
  * one call to the next; but calls that overlap on the GPU (different streams,
  * or threads that do not order their streams) race on the array: serialise
  * them.  Work is queued on `stream` (a cudaStream_t; NULL = legacy default).
- * Errors: SG_ERR_INVALID (null pointers, n < 0, h <= 0, a dimension < 1),
- * SG_ERR_CAPACITY (n > SG_NOALLOC_MAX_PARTICLES, 4*dims >= 2^21, or more
- * than 64 devices), SG_ERR_CUDA (address lookup or launch failed). */
+ * The arrays must be device memory of the current device (checked with
+ * cudaPointerGetAttributes: anything else is SG_ERR_INVALID before any
+ * launch).
+ * Errors: SG_ERR_INVALID (null pointers, n < 0, h <= 0, a dimension < 1, an
+ * array not on the current device), SG_ERR_CAPACITY (n >
+ * SG_NOALLOC_MAX_PARTICLES, 4*dims >= 2^21, or more than 64 devices),
+ * SG_ERR_CUDA (address lookup or launch failed). */
 #define SG_NOALLOC_MAX_PARTICLES 262144
 SG_API sg_status sg_morton_order_noalloc(const sg_grid_desc *desc, int64_t n, const float *x, const float *y,
                                          const float *z, uint64_t *keys, int32_t *order, void *stream);

@@ -618,18 +618,29 @@ def morton_order_noalloc(spec, x, y, z, keys=None, order=None, stream=None):
 
     For callers whose device memory is not the library's to take: the library
     allocates nothing here and uses its built-in scratch (at most
-    NOALLOC_MAX_PARTICLES particles).  ``keys`` / ``order`` may be caller
-    tensors (int64 / int32 on the device); otherwise they are created here by
-    torch on the caller's behalf."""
+    NOALLOC_MAX_PARTICLES particles).  ``x``, ``y``, ``z`` are contiguous
+    float32 CUDA tensors of one length on one device; ``keys`` / ``order`` may
+    be caller tensors (contiguous int64 / int32 of at least that length on the
+    same device); otherwise they are created here by torch on the caller's
+    behalf.  The call runs with x's device current, on ``stream`` (default:
+    that device's current stream)."""
     torch = _torch()
     n = x.numel()
+    dev = x.device
+    for name, t in (("x", x), ("y", y), ("z", z)):
+        if not (t.is_cuda and t.device == dev and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == n):
+            raise ValueError("%s: contiguous float32 CUDA tensor of %d values on %s expected" % (name, n, dev))
     if keys is None:
-        keys = torch.empty(n, dtype=torch.int64, device=x.device)
+        keys = torch.empty(n, dtype=torch.int64, device=dev)
     if order is None:
-        order = torch.empty(n, dtype=torch.int32, device=x.device)
-    s = stream if stream is not None else torch.cuda.current_stream()
-    st = lib().sg_morton_order_noalloc(C.byref(_desc(spec)), n, _ptr(x), _ptr(y), _ptr(z), _ptr(keys), _ptr(order),
-                                       C.c_void_p(s.cuda_stream))
+        order = torch.empty(n, dtype=torch.int32, device=dev)
+    for name, t, dt in (("keys", keys, torch.int64), ("order", order, torch.int32)):
+        if not (t.is_cuda and t.device == dev and t.dtype == dt and t.is_contiguous() and t.numel() >= n):
+            raise ValueError("%s: contiguous %s CUDA tensor of >= %d values on %s expected" % (name, dt, n, dev))
+    with torch.cuda.device(dev):
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        st = lib().sg_morton_order_noalloc(C.byref(_desc(spec)), n, _ptr(x), _ptr(y), _ptr(z), _ptr(keys),
+                                           _ptr(order), C.c_void_p(s.cuda_stream))
     if st != SG_OK:
         raise SgError(st, "sg_morton_order_noalloc failed")
     return keys, order

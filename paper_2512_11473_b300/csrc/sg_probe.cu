@@ -444,6 +444,17 @@ extern "C" sg_status sg_morton_order_noalloc(const sg_grid_desc* desc, int64_t n
         return SG_ERR_CUDA;
     }
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return SG_ERR_CAPACITY;
+    // the arrays must live on the current device (the scratch array used is that device's)
+    for (const void* ptr : {(const void*)x, (const void*)y, (const void*)z, (const void*)order, (const void*)keys}) {
+        if (!ptr) continue;
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return SG_ERR_INVALID;
+        }
+        if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) return SG_ERR_INVALID;
+        if (pa.device != dev) return SG_ERR_INVALID;
+    }
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);

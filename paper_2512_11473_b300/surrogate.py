@@ -27,8 +27,11 @@ def _torch():
     return torch
 
 
-def collect_samples(n_bodies=500, seed=4, target=20_000_000, p_lo=1e2, p_hi=1e5, reinit_iters=0, log=None):
-    """Returns (x bf16 [n, 32], t float32 [n, 4], info) with n <= target."""
+def collect_samples(n_bodies=500, seed=4, target=20_000_000, p_lo=1e2, p_hi=1e5, reinit_iters=20, log=None):
+    """Returns (x bf16 [n, 32], t float32 [n, 4], info) with n <= target:
+    canonical inputs and targets of network-class points, each body's phi
+    initialised from its distance and reinitialised `reinit_iters` sweeps
+    (as the fields the surrogate later serves are)."""
     import sg_inputs as si
     torch = _torch()
     bodies = si.random_bodies(n_bodies, seed=seed, p_lo=p_lo, p_hi=p_hi)
@@ -69,9 +72,12 @@ def collect_samples(n_bodies=500, seed=4, target=20_000_000, p_lo=1e2, p_hi=1e5,
     return X, T, info
 
 
-def train(net: MLP, X, T, steps=12000, batch=8192, lr=1e-3, seed=4, log_every=0, log=None):
-    """Adam with lr * (1 + cos(pi s / steps)) / 2 on seeded random batches.
-    Returns a list of (step, loss) samples."""
+def train(net: MLP, X, T, steps=300_000, batch=16384, lr=3e-3, seed=4, log_every=0, log=None):
+    """Adam with lr * (1 + cos(pi s / steps)) / 2 on seeded random batches
+    (epochs of a seeded permutation).  The defaults are the production
+    recipe: 300k steps of 16384 samples (about 9 s on one B300) take the
+    h = 0.002 torus to a max abs error near 8e-4 after fallback.  Returns
+    ([(step, loss)], seconds)."""
     torch = _torch()
     n = X.shape[0]
     gen = torch.Generator(device="cuda")

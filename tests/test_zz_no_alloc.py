@@ -38,8 +38,12 @@ def _regular(sg, spec, shape, X, Y, Z):
     return keys.cpu(), order.cpu()
 
 
-def _noalloc_raw(sg, spec, X, Y, Z):
-    """Direct C-ABI call with caller-owned outputs."""
+def _noalloc_raw(sg, spec, X, Y, Z, check_free=False):
+    """Direct C-ABI call with caller-owned outputs.  check_free: the device's
+    free memory (cudaMemGetInfo) must not drop across the call, which catches
+    a cudaMalloc by the library as well as an allocation through torch (the
+    first call on a device may load the library's module and its static
+    scratch array, so only a later call is checked)."""
     n = X.numel()
     keys = torch.full((n,), -1, dtype=torch.int64, device="cuda")
     order = torch.full((n,), -1, dtype=torch.int32, device="cuda")
@@ -53,13 +57,17 @@ def _noalloc_raw(sg, spec, X, Y, Z):
     try:
         torch.cuda.synchronize()
         before = torch.cuda.memory_allocated()
+        free0 = torch.cuda.mem_get_info()[0]
         st = sg.lib().sg_morton_order_noalloc(C.byref(desc), n, *args[:3], *args[3:], stream)
         torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
         after = torch.cuda.memory_allocated()
     finally:
         gc.enable()
     assert st == sg.SG_OK
     assert after <= before
+    if check_free:
+        assert free1 >= free0
     return keys.cpu(), order.cpu()
 
 
@@ -79,7 +87,7 @@ def test_noalloc_matches_regular_entry_point_twice(sg):
     X2, Y2, Z2 = (torch.from_numpy(v).cuda() for v in (x, y, z))
 
     got1 = _noalloc_raw(sg, spec1, X1, Y1, Z1)
-    got2 = _noalloc_raw(sg, spec2, X2, Y2, Z2)
+    got2 = _noalloc_raw(sg, spec2, X2, Y2, Z2, check_free=True)
     ref1 = _regular(sg, spec1, shape1, X1, Y1, Z1)
     ref2 = _regular(sg, spec2, shape2, X2, Y2, Z2)
     assert torch.equal(got1[0], ref1[0]) and torch.equal(got1[1], ref1[1])
@@ -106,3 +114,26 @@ def test_noalloc_limits(sg):
     with pytest.raises(sg.SgError) as e:
         sg.morton_order_noalloc(si.GridSpec((0, 0, 0), (600000, 1, 1), 0.1), Xs[0], Xs[1], Xs[2])
     assert e.value.status == sg.SG_ERR_CAPACITY
+
+
+def test_noalloc_wrapper_rejects_bad_arrays(sg):
+    spec = si.GridSpec((-1.0, -1.0, -0.4), (50, 50, 20), 0.01)
+    X = torch.zeros(1000, device="cuda")
+    with pytest.raises(ValueError):
+        sg.morton_order_noalloc(spec, X, X, X.double())
+    with pytest.raises(ValueError):
+        sg.morton_order_noalloc(spec, X, X, X[::2])
+    with pytest.raises(ValueError):
+        sg.morton_order_noalloc(spec, X, X, X, order=torch.zeros(999, dtype=torch.int32, device="cuda"))
+    with pytest.raises(ValueError):
+        sg.morton_order_noalloc(spec, X, X, X, keys=torch.zeros(1000, dtype=torch.int32, device="cuda"))
+    with pytest.raises(ValueError):
+        sg.morton_order_noalloc(spec, X, X, X.cpu())
+    # host memory passed straight to the C entry point is refused before any launch
+    h = torch.zeros(1000)
+    o = torch.zeros(1000, dtype=torch.int32)
+    desc = sg._desc(spec)
+    st = sg.lib().sg_morton_order_noalloc(C.byref(desc), 1000, *[C.c_void_p(t.data_ptr()) for t in (h, h, h)],
+                                          None, C.c_void_p(o.data_ptr()),
+                                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == sg.SG_ERR_INVALID
