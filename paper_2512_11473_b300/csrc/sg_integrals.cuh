@@ -41,11 +41,13 @@ __device__ __forceinline__ float heaviside_neg(float phi, float inv_eps) {
     // H(z) at z = -phi with half width eps: 0 below -eps, 1 above eps,
     // 1/2 (1 + z/eps + sin(pi z/eps)/pi) between; the sine is the hardware
     // approximation (absolute error about 5e-7 on [-pi, pi], far below the
-    // 1e-5 the integrals are held to)
-    float t = -phi * inv_eps;
+    // 1e-5 the integrals are held to).  Every operation is an explicitly
+    // rounded one, so that all kernels that stage H agree bit for bit.
+    const float t = __fmul_rn(-phi, inv_eps);
     if (t < -1.0f) return 0.0f;
     if (t > 1.0f) return 1.0f;
-    return 0.5f * (1.0f + t + __sinf(3.14159265358979323846f * t) * 0.318309886183790672f);
+    const float sn = __sinf(__fmul_rn(3.14159265358979323846f, t));
+    return __fmul_rn(0.5f, __fmaf_rn(sn, 0.318309886183790672f, __fadd_rn(1.0f, t)));
 }
 
 // Stage the package's 6^3 tile (the package plus a one-point halo) by
@@ -187,6 +189,47 @@ __device__ __forceinline__ void integrals_point(const float* tile, int d, const 
         if (sz != 0) {
             const float kz = fmaf(K.ck[s2 + 2], sa, fmaf(K.ck[s2 + 1], t, K.ck[s2] * h0[1]));
             az = sz < 0 ? az + kz : az - kz;
+        }
+    }
+}
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+
+// Points d and d + 1 (x-neighbours of one package row) at once: the sums of
+// integrals_point, operation for operation, on pairs of floats (each lane of
+// a paired instruction is the same rounded operation), so both points come
+// out bit for bit as integrals_point gives them.
+__device__ __forceinline__ void integrals_point2(const float* tile, int d, const KernelCoef& K, float2& w, float2& ax,
+                                                 float2& ay, float2& az) {
+    const int i = d & 3, j = (d >> 2) & 3, k = d >> 4;
+    const float* H = tile + (i + 1) + TILE_Y * (j + 1) + TILE_Z * (k + 1);
+    w = ax = ay = az = f2(0.0f);
+#pragma unroll
+    for (int sz = -1; sz <= 1; ++sz) {
+        const int s2 = sz * sz;
+        float2 h0[3], a[3], b[3];
+#pragma unroll
+        for (int sy = -1; sy <= 1; ++sy) {
+            const float* row = H + TILE_Y * sy + TILE_Z * sz;
+            const float r0 = row[-1], r1 = row[0], r2 = row[1], r3 = row[2];
+            const float2 m = make_float2(r0, r1), p = make_float2(r2, r3);
+            h0[sy + 1] = make_float2(r1, r2);
+            a[sy + 1] = __fadd2_rn(m, p);
+            b[sy + 1] = __fadd2_rn(m, neg2(p));
+        }
+        const float2 t = __fadd2_rn(a[1], __fadd2_rn(h0[0], h0[2])), sa = __fadd2_rn(a[0], a[2]);
+        w = __ffma2_rn(f2(K.cw[s2]), h0[1], w);
+        w = __ffma2_rn(f2(K.cw[s2 + 1]), t, w);
+        w = __ffma2_rn(f2(K.cw[s2 + 2]), sa, w);
+        ax = __ffma2_rn(f2(K.ck[s2 + 1]), b[1], ax);
+        ax = __ffma2_rn(f2(K.ck[s2 + 2]), __fadd2_rn(b[0], b[2]), ax);
+        ay = __ffma2_rn(f2(K.ck[s2 + 1]), __fadd2_rn(h0[0], neg2(h0[2])), ay);
+        ay = __ffma2_rn(f2(K.ck[s2 + 2]), __fadd2_rn(a[0], neg2(a[2])), ay);
+        if (sz != 0) {
+            const float2 kz = __ffma2_rn(f2(K.ck[s2 + 2]), sa,
+                                         __ffma2_rn(f2(K.ck[s2 + 1]), t, __fmul2_rn(f2(K.ck[s2]), h0[1])));
+            az = sz < 0 ? __fadd2_rn(az, kz) : __fadd2_rn(az, neg2(kz));
         }
     }
 }

@@ -3,6 +3,7 @@
 // (Listing 5), 7-point Laplacian, the sequential update, kernel integrals.
 // The per-package arithmetic lives in sg_rows.cuh and sg_integrals.cuh; the
 // reinitialisation sweep has its own file, sg_reinit.cu.
+#include <algorithm>
 #include <cmath>
 
 #include "sg_integrals.cuh"
@@ -65,60 +66,102 @@ __global__ void __launch_bounds__(SW_THREADS) k_copy(const float* __restrict__ s
         dst[e] = src[e];
 }
 
-// 16 packages per CTA: the 36 rows of each package's 6^3 Heaviside tile are
-// staged by all threads, then each thread sums the taps of one package row
-// of four points (the loads of neighbouring points are shared) and writes
-// four outputs per field as 16-byte stores.
-constexpr int IN_PKGS = 16;
+// Each warp takes pairs of packages in turn (a persistent loop): it stages
+// the two packages' smoothed Heaviside tiles (6^3: the package plus a
+// one-point halo; 72 rows of six, a 16-byte interior load and two halo
+// values per row, rows fixed per lane so their index arithmetic is done
+// once), then each half-warp sums the taps of one package, a row of four
+// points per lane, as two x-neighbour pairs on paired FP32 instructions,
+// and writes four outputs per field as 16-byte stores.  Warps never wait for
+// one another; a tile that is all 0 or all 1 writes W = that value and G = 0
+// without the taps.
+constexpr int IW_WARPS = 8;  // warps per CTA
+constexpr int IW_ROWS = 72;  // staged rows per package pair
 
-__global__ void __launch_bounds__(SW_THREADS) k_kernel_integrals(const int32_t* __restrict__ nbr,
-                                                                  const float* __restrict__ phi, float* __restrict__ W,
-                                                                  float* __restrict__ gx, float* __restrict__ gy,
-                                                                  float* __restrict__ gz, int64_t P, KernelCoef K,
-                                                                  float inv_eps) {
-    __shared__ int s_nb[IN_PKGS][NB];
-    __shared__ float s_H[IN_PKGS][TILE_N];  // 6^3 tile: package plus a one-point halo
-    __shared__ unsigned s_sat[IN_PKGS];
+__global__ void __launch_bounds__(IW_WARPS * 32, 4) k_kernel_integrals(const int32_t* __restrict__ nbr,
+                                                                     const float* __restrict__ phi,
+                                                                     float* __restrict__ W, float* __restrict__ gx,
+                                                                     float* __restrict__ gy, float* __restrict__ gz,
+                                                                     int64_t P, KernelCoef K, float inv_eps) {
+    __shared__ float s_H[IW_WARPS][2][TILE_N];
+    __shared__ int s_nb[IW_WARPS][2][NB];
     write_far(W, 1.0f, 0.0f);
     write_far(gx, 0.0f, 0.0f);
     write_far(gy, 0.0f, 0.0f);
     write_far(gz, 0.0f, 0.0f);
-    const int64_t p0 = 2 + (int64_t)blockIdx.x * IN_PKGS;
-    const int n_pk = (int)min((int64_t)IN_PKGS, P - p0);
-    for (int e = threadIdx.x; e < IN_PKGS * NB; e += SW_THREADS) {
-        const int lp = e / NB;
-        if (lp < n_pk) s_nb[lp][e - lp * NB] = __ldg(nbr + (p0 + lp) * NB + (e - lp * NB));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float(*tH)[TILE_N] = s_H[warp];
+    int(*tnb)[NB] = s_nb[warp];
+    // staging rows of this lane: e = lane, lane + 32, lane + 64 (< 72): package e / 36, row e % 36
+    int r_pk[3], r_nb[3], r_d0[3], r_e0[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int e = lane + 32 * q, rr = e % 36;
+        const int y = rr % 6 - 1, z = rr / 6 - 1;
+        const int oy = ((y + 4) >> 2) - 1, oz = ((z + 4) >> 2) - 1;
+        r_pk[q] = e < IW_ROWS ? e / 36 : -1;
+        r_nb[q] = 3 * (oy + 1) + 9 * (oz + 1);
+        r_d0[q] = 4 * (y - 4 * oy) + 16 * (z - 4 * oz);
+        r_e0[q] = TILE_Y * (y + 1) + TILE_Z * (z + 1);
     }
-    if (threadIdx.x < IN_PKGS) s_sat[threadIdx.x] = 0;
-    __syncthreads();
-    for (int e = threadIdx.x; e < IN_PKGS * 36; e += SW_THREADS) {
-        const int lp = e / 36;
-        if (lp < n_pk) {
-            const unsigned bits = integrals_stage(s_nb[lp], phi, inv_eps, e - lp * 36, s_H[lp]);
-            if (bits) atomicOr(&s_sat[lp], bits);
+    const int half = lane >> 4, r = lane & 15;
+    const int64_t pairs = (P - 2 + 1) / 2;
+    for (int64_t pr = (int64_t)blockIdx.x * IW_WARPS + warp; pr < pairs; pr += (int64_t)gridDim.x * IW_WARPS) {
+        const int64_t p0 = 2 + 2 * pr;
+        const bool two = p0 + 1 < P;
+        if (lane < NB) {
+            tnb[0][lane] = __ldg(nbr + p0 * NB + lane);
+            if (two) tnb[1][lane] = __ldg(nbr + (p0 + 1) * NB + lane);
         }
-    }
-    __syncthreads();
-    const int lp = threadIdx.x >> 4, r = threadIdx.x & 15;
-    if (lp >= n_pk) return;
-    float4 ow, ox, oy, oz;
-    float w[4], ax[4], ay[4], az[4];
-    if (!integrals_saturated(s_sat[lp], w[0], ax[0], ay[0], az[0])) {
+        __syncwarp();
+        unsigned bits[2] = {0u, 0u};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) integrals_point(s_H[lp], 4 * r + i, K, w[i], ax[i], ay[i], az[i]);
-    } else {
+        for (int q = 0; q < 3; ++q) {
+            const int pk = r_pk[q];
+            if (pk < 0 || (pk == 1 && !two)) continue;
+            const int* nb = tnb[pk];
+            const float4 v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb[r_nb[q] + 1] * PKG3 + r_d0[q]));
+            const float vm = __ldg(phi + (int64_t)nb[r_nb[q]] * PKG3 + r_d0[q] + 3);
+            const float vp = __ldg(phi + (int64_t)nb[r_nb[q] + 2] * PKG3 + r_d0[q]);
+            const float f[6] = {vm, v.x, v.y, v.z, v.w, vp};
+            float* t = tH[pk] + r_e0[q];
+            unsigned b = 0;
 #pragma unroll
-        for (int i = 1; i < 4; ++i) w[i] = w[0], ax[i] = ax[0], ay[i] = ay[0], az[i] = az[0];
+            for (int i = 0; i < 6; ++i) {
+                const float hv = heaviside_neg(f[i], inv_eps);
+                t[i] = hv;
+                b |= (hv != 0.0f ? 1u : 0u) | (hv != 1.0f ? 2u : 0u);
+            }
+            bits[pk] |= b;
+        }
+        bits[0] = __reduce_or_sync(0xffffffffu, bits[0]);
+        bits[1] = __reduce_or_sync(0xffffffffu, bits[1]);
+        __syncwarp();
+        if (half == 0 || two) {
+            const int64_t p = p0 + half;
+            float w[4], ax[4], ay[4], az[4];
+            if (!integrals_saturated(bits[half], w[0], ax[0], ay[0], az[0])) {
+#pragma unroll
+                for (int pp = 0; pp < 2; ++pp) {
+                    float2 w2, x2, y2, z2;
+                    integrals_point2(tH[half], 4 * r + 2 * pp, K, w2, x2, y2, z2);
+                    w[2 * pp] = w2.x, w[2 * pp + 1] = w2.y;
+                    ax[2 * pp] = x2.x, ax[2 * pp + 1] = x2.y;
+                    ay[2 * pp] = y2.x, ay[2 * pp + 1] = y2.y;
+                    az[2 * pp] = z2.x, az[2 * pp + 1] = z2.y;
+                }
+            } else {
+#pragma unroll
+                for (int i = 1; i < 4; ++i) w[i] = w[0], ax[i] = ax[0], ay[i] = ay[0], az[i] = az[0];
+            }
+            const int64_t q4 = p * 16 + r;
+            reinterpret_cast<float4*>(W)[q4] = make_float4(w[0], w[1], w[2], w[3]);
+            reinterpret_cast<float4*>(gx)[q4] = make_float4(ax[0], ax[1], ax[2], ax[3]);
+            reinterpret_cast<float4*>(gy)[q4] = make_float4(ay[0], ay[1], ay[2], ay[3]);
+            reinterpret_cast<float4*>(gz)[q4] = make_float4(az[0], az[1], az[2], az[3]);
+        }
+        __syncwarp();  // the next pair's staging overwrites the tiles
     }
-    ow = make_float4(w[0], w[1], w[2], w[3]);
-    ox = make_float4(ax[0], ax[1], ax[2], ax[3]);
-    oy = make_float4(ay[0], ay[1], ay[2], ay[3]);
-    oz = make_float4(az[0], az[1], az[2], az[3]);
-    const int64_t q4 = (p0 + lp) * 16 + r;
-    reinterpret_cast<float4*>(W)[q4] = ow;
-    reinterpret_cast<float4*>(gx)[q4] = ox;
-    reinterpret_cast<float4*>(gy)[q4] = oy;
-    reinterpret_cast<float4*>(gz)[q4] = oz;
 }
 
 // Supports above 2h: 8^3 tiles, 5^3 taps.
@@ -230,6 +273,27 @@ cudaError_t launch_copy_active(const float* src, float* dst, int64_t P, cudaStre
     return cudaGetLastError();
 }
 
+// Persistent grid of k_kernel_integrals: the CTAs resident on every SM at
+// once, at most one warp per package pair.
+unsigned integrals_grid(int64_t P) {
+    static int per_sm = 0, sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kernel_integrals, IW_WARPS * 32, 0) !=
+                cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    const int64_t pairs = (P - 2 + 1) / 2;
+    const int64_t need = (pairs + IW_WARPS - 1) / IW_WARPS;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)per_sm * sms));
+}
+
 cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const float* phi, float* W, float* gx,
                                     float* gy, float* gz, int64_t P, double R, double eps, cudaStream_t s) {
     cudaError_t e;
@@ -244,8 +308,8 @@ cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const fl
         k_kernel_integrals_wide<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(R),
                                                                       (float)(1.0 / eps));
     else
-        k_kernel_integrals<<<(unsigned)((P - 2 + IN_PKGS - 1) / IN_PKGS), SW_THREADS, 0, s>>>(
-            nbr, phi, W, gx, gy, gz, P, kernel_coef(R), (float)(1.0 / eps));
+        k_kernel_integrals<<<integrals_grid(P), IW_WARPS * 32, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(R),
+                                                                       (float)(1.0 / eps));
     note_launch();
     return cudaGetLastError();
 }
