@@ -217,18 +217,29 @@ SG_API sg_status sg_gradient(sg_grid *g);
  * Errors: SG_ERR_INVALID (trust <= 0 or not finite), SG_ERR_STATE (no phi),
  * SG_ERR_OOM, SG_ERR_TIMEOUT (a flood that does not settle, which cannot
  * happen for valid tables, or a grid-barrier wait of a persistent flood
- * that gave up after its bounded number of polls; phi is then unchanged if
- * it was the point flood). */
+ * that gave up after its bounded number of polls; phi and the tables are
+ * then unchanged). */
 SG_API sg_status sg_consistency_correct(sg_grid *g, float trust, int64_t *out);
 
-/* Testing hook for the bounded waits of the persistent floods: runs
- * sg_consistency_correct(g, trust, NULL) with one CTA counted at every grid
- * barrier that never arrives, so the first barrier (of the point flood, or
- * of the cell flood when there are no active points) cannot complete: every
- * CTA gives up after its bounded number of polls (about a second) and the
- * call returns SG_ERR_TIMEOUT with phi and the tables unchanged and the
- * grid usable.  Errors: as sg_consistency_correct, SG_ERR_DEVICE (a device
- * without cooperative launch, where the floods do not wait on one another). */
+/* Testing hooks of sg_consistency_correct (out as there, may be NULL):
+ *   SG_DEBUG_CC_ABSENT_POINTS / _CELLS: one CTA is counted at every grid
+ *     barrier of the point (cell) flood and never arrives, so that flood's
+ *     first barrier cannot complete: every CTA gives up after its 2^21 polls
+ *     (at least 67 ms; 0.54 s measured on a B300) and the call returns
+ *     SG_ERR_TIMEOUT with phi and the tables unchanged (the corrections are
+ *     applied only after both floods settled) and the grid usable;
+ *   SG_DEBUG_CC_PER_SWEEP: the floods run as one launch per sweep with the
+ *     host reading the flags (the path of devices without cooperative
+ *     launch) instead of one persistent launch each.
+ * Errors: as sg_consistency_correct; SG_ERR_INVALID (unknown flags, or an
+ * absent CTA with SG_DEBUG_CC_PER_SWEEP); SG_ERR_DEVICE (an absent CTA on a
+ * device without cooperative launch, where the floods do not wait on one
+ * another). */
+#define SG_DEBUG_CC_ABSENT_POINTS 1
+#define SG_DEBUG_CC_ABSENT_CELLS 2
+#define SG_DEBUG_CC_PER_SWEEP 4
+SG_API sg_status sg_debug_consistency(sg_grid *g, float trust, int32_t flags, int64_t *out);
+/* sg_debug_consistency with SG_DEBUG_CC_ABSENT_POINTS | SG_DEBUG_CC_ABSENT_CELLS. */
 SG_API sg_status sg_debug_consistency_absent_cta(sg_grid *g, float trust);
 
 /* The "sequential" benchmark of "Performance Evaluation": a small change to

@@ -27,6 +27,7 @@ STATUS_NAMES = ["SG_OK", "SG_ERR_INVALID", "SG_ERR_OOM", "SG_ERR_CUDA", "SG_ERR_
 FIELDS = {"phi": 0, "gx": 1, "gy": 2, "gz": 3, "W": 4, "Gx": 5, "Gy": 6, "Gz": 7, "lap": 8, "S0": 9}
 INT_FIELDS = {"cell_pkg": (100, "<i4"), "pkg_cell": (101, "<i4"), "pkg_type": (102, "|u1"), "nbr": (103, "<i4")}
 PROBE_MORTON = 1
+DEBUG_CC_ABSENT_POINTS, DEBUG_CC_ABSENT_CELLS, DEBUG_CC_PER_SWEEP = 1, 2, 4
 PROBE_OUTPUTS = ("phi", "nx", "ny", "nz", "W", "Gx", "Gy", "Gz")
 
 
@@ -93,6 +94,7 @@ def lib():
         L.sg_sequential_update.argtypes = [vp, C.c_float]
         L.sg_consistency_correct.argtypes = [vp, C.c_float, C.POINTER(i64)]
         L.sg_debug_consistency_absent_cta.argtypes = [vp, C.c_float]
+        L.sg_debug_consistency.argtypes = [vp, C.c_float, C.c_int32, C.POINTER(i64)]
         L.sg_tag_allocate_from.argtypes = [vp, vp, C.POINTER(sg_shape), C.POINTER(i64), C.POINTER(i64)]
         L.sg_multires_layers.argtypes = [C.POINTER(sg_grid_desc), i32]
         L.sg_multires_layers.restype = i32
@@ -301,6 +303,14 @@ class Grid:
         floods' grid barriers; raises SgError (SG_ERR_TIMEOUT) once the
         bounded waits give up, with phi and the tables unchanged."""
         self._check(self._lib.sg_debug_consistency_absent_cta(self._h, float(trust)))
+
+    def debug_consistency(self, trust=1.0, flags=0):
+        """Testing hook: the correction with SG_DEBUG_CC_* flags (an absent CTA
+        in the point or cell flood, or the per-sweep floods).  Returns the
+        counts as consistency_correct."""
+        out = (C.c_int64 * 4)()
+        self._check(self._lib.sg_debug_consistency(self._h, float(trust), int(flags), out))
+        return tuple(int(v) for v in out)
 
     def sequential_update(self, delta):
         """phi <- phi + delta on every active value (the paper's sequential benchmark)."""

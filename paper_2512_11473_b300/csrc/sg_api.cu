@@ -421,7 +421,7 @@ sg_status sg_gradient(sg_grid* g) {
     return SG_OK;
 }
 
-static sg_status consistency(sg_grid* g, float trust, int64_t* out, unsigned absent) {
+static sg_status consistency(sg_grid* g, float trust, int64_t* out, unsigned debug) {
     SG_CHECK_GRID(g);
     if (!(trust > 0.0f) || !std::isfinite(trust)) return fail(g, SG_ERR_INVALID, "sg_consistency_correct: bad trust");
     if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_consistency_correct: phi not initialised");
@@ -433,7 +433,7 @@ static sg_status consistency(sg_grid* g, float trust, int64_t* out, unsigned abs
         run_consistency(grid_ff(g), g->P, g->nc, (int32_t*)g->cell_pkg.p, (const int32_t*)g->pkg_cell.p,
                         (const uint8_t*)g->pkg_type.p, (int32_t*)g->nbr.p, (int32_t*)g->faces.p,
                         (float*)g->field[SG_FIELD_PHI].p, (float)((double)trust * g->desc.h), g->scratch.p,
-                        g->host_pin.p, o, g->stream, absent);
+                        g->host_pin.p, o, g->stream, debug);
     if (e == cudaErrorLaunchTimeout) return fail(g, SG_ERR_TIMEOUT, "sg_consistency_correct: flood did not settle or a barrier wait gave up");
     if (e != cudaSuccess) return cuda_fail(g, e, "consistency correction");
     if (out)
@@ -443,11 +443,21 @@ static sg_status consistency(sg_grid* g, float trust, int64_t* out, unsigned abs
 
 sg_status sg_consistency_correct(sg_grid* g, float trust, int64_t* out) { return consistency(g, trust, out, 0); }
 
-sg_status sg_debug_consistency_absent_cta(sg_grid* g, float trust) {
+sg_status sg_debug_consistency(sg_grid* g, float trust, int32_t flags, int64_t* out) {
     SG_CHECK_GRID(g);
-    if (!consistency_persistent(g->device))
-        return fail(g, SG_ERR_DEVICE, "sg_debug_consistency_absent_cta: no cooperative launch on this device");
-    return consistency(g, trust, nullptr, 1);
+    const unsigned all = SG_DEBUG_CC_ABSENT_POINTS | SG_DEBUG_CC_ABSENT_CELLS | SG_DEBUG_CC_PER_SWEEP;
+    if (flags < 0 || ((unsigned)flags & ~all))
+        return fail(g, SG_ERR_INVALID, "sg_debug_consistency: unknown flags");
+    const unsigned absent = (unsigned)flags & (SG_DEBUG_CC_ABSENT_POINTS | SG_DEBUG_CC_ABSENT_CELLS);
+    if (absent && ((unsigned)flags & SG_DEBUG_CC_PER_SWEEP))
+        return fail(g, SG_ERR_INVALID, "sg_debug_consistency: an absent CTA needs the persistent floods");
+    if (absent && !consistency_persistent(g->device))
+        return fail(g, SG_ERR_DEVICE, "sg_debug_consistency: no cooperative launch on this device");
+    return consistency(g, trust, out, (unsigned)flags);
+}
+
+sg_status sg_debug_consistency_absent_cta(sg_grid* g, float trust) {
+    return sg_debug_consistency(g, trust, SG_DEBUG_CC_ABSENT_POINTS | SG_DEBUG_CC_ABSENT_CELLS, nullptr);
 }
 
 sg_status sg_sequential_update(sg_grid* g, float delta) {

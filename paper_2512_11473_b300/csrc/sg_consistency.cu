@@ -297,7 +297,10 @@ struct FloodSync {
     int sweeps;        // sweeps up to and including the first that changed nothing
     unsigned absent;   // CTAs counted at every barrier that never arrive: 0, or 1 to test the bounded waits
 };
-constexpr unsigned CC_SPIN_LIMIT = 1u << 21;  // polls of at least 100 ns: about 0.2 s and more
+// 2^21 polls, each a load of the barrier word and a __nanosleep(32): at least
+// 67 ms; 0.54 s measured on a B300 for the small sphere (the give-up is timed
+// by the consistency tests)
+constexpr unsigned CC_SPIN_LIMIT = 1u << 21;
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
@@ -498,7 +501,10 @@ size_t consistency_scratch_bytes(int64_t P, const int32_t dims[3]) {
 
 cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cell_pkg, const int32_t* pkg_cell,
                             const uint8_t* pkg_type, int32_t* nbr, int32_t* faces, float* phi, float tau,
-                            void* scratch, void* host_pin, int64_t out[4], cudaStream_t s, unsigned absent) {
+                            void* scratch, void* host_pin, int64_t out[4], cudaStream_t s, unsigned debug) {
+    const unsigned absent_pt = debug & SG_DEBUG_CC_ABSENT_POINTS ? 1u : 0u;
+    const unsigned absent_cell = debug & SG_DEBUG_CC_ABSENT_CELLS ? 1u : 0u;
+    const bool per_sweep = (debug & SG_DEBUG_CC_PER_SWEEP) != 0;
     char* sp = (char*)scratch;
     uint64_t* sa = (uint64_t*)sp;  // point planes: plus (P words), then minus (P words)
     sp += al256(2 * (size_t)P * sizeof(uint64_t));
@@ -530,10 +536,10 @@ cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cel
     if (n_act > 0) {
         k_cc_seed_points<<<cc_blocks(n_act), CC_THREADS, 0, s>>>(phi, (uint32_t*)sa, (uint32_t*)(sa + P), n_act, tau);
         note_launch();
-        const int cbp = coop_blocks((const void*)k_cc_flood_points_coop, P - 2, device);
+        const int cbp = per_sweep ? 0 : coop_blocks((const void*)k_cc_flood_points_coop, P - 2, device);
         if (cbp > 0) {
-            e = run_coop_flood(k_cc_flood_points_coop, cbp, fs, hfs, absent, sweeps_pt, s, (const int32_t*)faces, sa, sb, P,
-                               n_act + 1, fs);
+            e = run_coop_flood(k_cc_flood_points_coop, cbp, fs, hfs, absent_pt, sweeps_pt, s, (const int32_t*)faces, sa, sb,
+                               P, n_act + 1, fs);
         } else {
             const unsigned nb = cc_blocks(P - 2);
             e = flood(
@@ -544,17 +550,14 @@ cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cel
                 sa, sb, dflag, hflag, n_act + 1, sweeps_pt, s);
         }
         if (e != cudaSuccess) return e;
-        k_cc_apply<<<cc_blocks(n_act / 4), CC_THREADS, 0, s>>>(reinterpret_cast<float4*>(phi), (const uint32_t*)sa,
-                                                                (const uint32_t*)(sa + P), n_act / 4, cnt);
-        note_launch();
     }
     k_cc_seed_words<<<cc_blocks(32 * nw), CC_THREADS, 0, s>>>(cell_pkg, pkg_type, sa, sa + P, open, la, la + nw, nx, nwx,
                                                               32 * nw);
     note_launch();
-    const int cbw = coop_blocks((const void*)k_cc_flood_words_coop, nw, device);
+    const int cbw = per_sweep ? 0 : coop_blocks((const void*)k_cc_flood_words_coop, nw, device);
     if (cbw > 0) {
-        e = run_coop_flood(k_cc_flood_words_coop, cbw, fs, hfs, absent, sweeps_cell, s, (const uint32_t*)open, la, lb, nwx, ny,
-                           nz, nc + 1, fs);
+        e = run_coop_flood(k_cc_flood_words_coop, cbw, fs, hfs, absent_cell, sweeps_cell, s, (const uint32_t*)open, la, lb,
+                           nwx, ny, nz, nc + 1, fs);
     } else {
         const unsigned cb = cc_blocks(nw);
         e = flood(
@@ -565,6 +568,14 @@ cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cel
             la, lb, dflag, hflag, nc + 1, sweeps_cell, s);
     }
     if (e != cudaSuccess) return e;
+    // both floods settled: only now are phi and the tables changed, so that a
+    // flood that gives up leaves the grid as it was (the cell flood reads the
+    // point labels, never phi)
+    if (n_act > 0) {
+        k_cc_apply<<<cc_blocks(n_act / 4), CC_THREADS, 0, s>>>(reinterpret_cast<float4*>(phi), (const uint32_t*)sa,
+                                                                (const uint32_t*)(sa + P), n_act / 4, cnt);
+        note_launch();
+    }
     k_cc_far<<<cc_blocks(nc), CC_THREADS, 0, s>>>(cell_pkg, la, la + nw, nx, nwx, nc, cnt + 1);
     note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

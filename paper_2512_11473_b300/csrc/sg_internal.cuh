@@ -148,7 +148,7 @@ size_t consistency_scratch_bytes(int64_t P, const int32_t dims[3]);
 cudaError_t run_consistency(const GridFF& G, int64_t P, int64_t nc, int32_t* cell_pkg, const int32_t* pkg_cell,
                             const uint8_t* pkg_type, int32_t* nbr, int32_t* faces, float* phi, float tau,
                             void* scratch, void* host_pin, int64_t out[4], cudaStream_t s,
-                            unsigned absent = 0);
+                            unsigned debug = 0);
 // whether the device can run the persistent (cooperative) floods
 bool consistency_persistent(int device);
 // faces[p][8] = the six face entries of nbr[p][27] (one 32-byte row per package)

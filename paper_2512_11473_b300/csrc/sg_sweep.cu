@@ -77,21 +77,24 @@ __global__ void __launch_bounds__(SW_THREADS) k_copy(const float* __restrict__ s
 // without the taps.
 constexpr int IW_WARPS = 8;  // warps per CTA
 constexpr int IW_ROWS = 72;  // staged rows per package pair
+#ifndef SG_IW_MIN_CTAS
+#define SG_IW_MIN_CTAS 4
+#endif
 
-__global__ void __launch_bounds__(IW_WARPS * 32, 4) k_kernel_integrals(const int32_t* __restrict__ nbr,
+__global__ void __launch_bounds__(IW_WARPS * 32, SG_IW_MIN_CTAS) k_kernel_integrals(const int32_t* __restrict__ nbr,
                                                                      const float* __restrict__ phi,
                                                                      float* __restrict__ W, float* __restrict__ gx,
                                                                      float* __restrict__ gy, float* __restrict__ gz,
                                                                      int64_t P, KernelCoef K, float inv_eps) {
     __shared__ float s_H[IW_WARPS][2][TILE_N];
-    __shared__ int s_nb[IW_WARPS][2][NB];
+    __shared__ int s_nb[IW_WARPS][2][32];  // rows of 27, padded: the two packages' rows start on bank 0
     write_far(W, 1.0f, 0.0f);
     write_far(gx, 0.0f, 0.0f);
     write_far(gy, 0.0f, 0.0f);
     write_far(gz, 0.0f, 0.0f);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float(*tH)[TILE_N] = s_H[warp];
-    int(*tnb)[NB] = s_nb[warp];
+    int(*tnb)[32] = s_nb[warp];
     // staging rows of this lane: e = lane, lane + 32, lane + 64 (< 72): package e / 36, row e % 36
     int r_pk[3], r_nb[3], r_d0[3], r_e0[3];
 #pragma unroll
@@ -106,14 +109,27 @@ __global__ void __launch_bounds__(IW_WARPS * 32, 4) k_kernel_integrals(const int
     }
     const int half = lane >> 4, r = lane & 15;
     const int64_t pairs = (P - 2 + 1) / 2;
-    for (int64_t pr = (int64_t)blockIdx.x * IW_WARPS + warp; pr < pairs; pr += (int64_t)gridDim.x * IW_WARPS) {
+    const int64_t stride = (int64_t)gridDim.x * IW_WARPS;
+    // the neighbourhood rows of the next pair are loaded while this pair's taps are summed
+    int nb_next[2] = {0, 0};
+    int64_t pr = (int64_t)blockIdx.x * IW_WARPS + warp;
+    if (pr < pairs && lane < NB) {
+        nb_next[0] = __ldg(nbr + (2 + 2 * pr) * NB + lane);
+        if (3 + 2 * pr < P) nb_next[1] = __ldg(nbr + (3 + 2 * pr) * NB + lane);
+    }
+    for (; pr < pairs; pr += stride) {
         const int64_t p0 = 2 + 2 * pr;
         const bool two = p0 + 1 < P;
         if (lane < NB) {
-            tnb[0][lane] = __ldg(nbr + p0 * NB + lane);
-            if (two) tnb[1][lane] = __ldg(nbr + (p0 + 1) * NB + lane);
+            tnb[0][lane] = nb_next[0];
+            tnb[1][lane] = nb_next[1];
         }
         __syncwarp();
+        const int64_t pn = pr + stride;
+        if (pn < pairs && lane < NB) {
+            nb_next[0] = __ldg(nbr + (2 + 2 * pn) * NB + lane);
+            if (3 + 2 * pn < P) nb_next[1] = __ldg(nbr + (3 + 2 * pn) * NB + lane);
+        }
         unsigned bits[2] = {0u, 0u};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {

@@ -123,14 +123,21 @@ def test_consistency_bad_trust(sg):
 def test_flood_barrier_wait_gives_up(sg):
     """A CTA that never reaches the persistent floods' grid barrier: the
     bounded waits give up, the call reports SG_ERR_TIMEOUT, nothing changed,
-    and the grid (and the context) still work."""
+    and the grid (and the context) still work.  The give-up time is measured
+    (2^21 polls of at least 32 ns each: no less than 67 ms)."""
+    import time
     shape, spec = BODIES["sphere"]()
     g = sg.Grid(spec)
     g.tag_allocate(shape)
     g.init_sdf(shape)
     before = {k: g.field(k).clone() for k in ("phi", "cell_pkg", "nbr")}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     with pytest.raises(sg.SgError) as e:
         g.debug_consistency_absent_cta(1.0)
+    dt = time.perf_counter() - t0
+    print("barrier wait gave up after %.3f s" % dt)
+    assert 0.05 < dt < 10.0
     assert e.value.status == sg.SG_ERR_TIMEOUT
     for k, v in before.items():
         assert torch.equal(g.field(k), v), k
@@ -139,3 +146,50 @@ def test_flood_barrier_wait_gives_up(sg):
     for k, v in before.items():
         assert torch.equal(g.field(k), v), k
     g.close()
+
+
+def test_cell_flood_give_up_leaves_grid_unchanged(sg):
+    """The point flood settles, the cell flood's barrier cannot complete: the
+    call reports SG_ERR_TIMEOUT and neither phi nor the tables changed (the
+    signs are applied only after both floods settled)."""
+    shape, spec, g, O, clean, flip, far = _setup(sg, "sphere")
+    _apply_noise_device(g, flip, far)
+    noisy = {k: g.field(k).clone() for k in ("phi", "cell_pkg", "nbr")}
+    with pytest.raises(sg.SgError) as e:
+        g.debug_consistency(1.0, sg.DEBUG_CC_ABSENT_CELLS)
+    assert e.value.status == sg.SG_ERR_TIMEOUT
+    for k, v in noisy.items():
+        assert torch.equal(g.field(k), v), k
+    out = g.consistency_correct(1.0)  # and the grid still corrects
+    assert out[0] == int(flip.sum()) and out[1] == int(far.sum())
+    for k, v in clean.items():
+        assert torch.equal(g.field(k), v), k
+
+
+@pytest.mark.parametrize("name", ["sphere", "sphere_64x40x33", "torus"])
+def test_per_sweep_floods_match_persistent_and_oracle(sg, name):
+    """The floods of devices without cooperative launch (a launch per sweep,
+    flags read by the host in batches): the same corrected grid, counts and
+    sweep counts as the persistent floods and as the oracle."""
+    shape, spec, g, O, clean, flip, far = _setup(sg, name)
+    _apply_noise_device(g, flip, far)
+    noisy_phi = H(g.field("phi")).astype(np.float64)
+    noisy_cp = H(g.field("cell_pkg"))
+    out = g.debug_consistency(1.0, sg.DEBUG_CC_PER_SWEEP)
+    for k, v in clean.items():
+        assert torch.equal(g.field(k), v), k
+    cp2, nb2, phi2, ch, sw = oracle.consistency_correct(spec, O.P, noisy_cp, O.pkg_cell, O.pkg_type, O.nbr,
+                                                        noisy_phi, sweeps=True)
+    assert ch == (out[0], out[1])
+    assert sw == (out[2], out[3])
+    # the persistent path on the same noise
+    _apply_noise_device(g, flip, far)
+    assert g.consistency_correct(1.0) == out
+
+
+def test_debug_consistency_flags(sg):
+    shape, spec, g, O, clean, _, _ = _setup(sg, "sphere")
+    for bad in (8, -1, sg.DEBUG_CC_ABSENT_POINTS | sg.DEBUG_CC_PER_SWEEP):
+        with pytest.raises(sg.SgError) as e:
+            g.debug_consistency(1.0, bad)
+        assert e.value.status == sg.SG_ERR_INVALID
