@@ -942,7 +942,7 @@ def run_sg(args):
         line["batch"] = batch_section(sg, torch, n_bodies=args.batch_bodies)
     net = None
     if not args.no_surrogate:
-        line["surrogate"], net = surrogate_section(sg, torch)
+        line["surrogate"], net = surrogate_section(sg, torch, steps=args.sur_steps)
     if not args.no_relax:
         trained = net is not None
         if net is None:
@@ -981,6 +981,8 @@ def main(argv=None):
     ap.add_argument("--batch-bodies", type=int, default=256,
                     help="bodies in the batch measurement (the first n of the 256-body set)")
     ap.add_argument("--no-surrogate", action="store_true", help="skip training and timing the surrogate")
+    ap.add_argument("--sur-steps", type=int, default=300_000,
+                    help="Adam steps of the surrogate training (fewer only for profiling runs)")
     ap.add_argument("--no-relax", action="store_true", help="skip the 64-body particle relaxation")
     ap.add_argument("--relax-particles", type=int, default=100_000_000)
     ap.add_argument("--relax-bodies", type=int, default=64)
