@@ -494,6 +494,22 @@ SG_API sg_status sg_surrogate_samples(sg_grid *g, uint64_t seed, float keep, int
  * call on this grid (synchronises). */
 SG_API sg_status sg_surrogate_stats(sg_grid *g, int64_t counts[4]);
 
+/* Checkpoint restore (the paper's "Data Transfer": registered variables
+ * synchronised to the host for output, and back).  A checkpoint is the
+ * tagging's tables and the fields, read through sg_get_field; sg_restore
+ * puts the tables back into a grid created with the same description:
+ * P packages (far included), cell_pkg[nx ny nz], pkg_cell[P], pkg_type[P],
+ * nbr[P][27] and optionally phi[P][64], all host arrays, copied (the call
+ * synchronises).  The face table is rebuilt from nbr and every table is
+ * checked as sg_check_tables does; the grid is then tagged (state 1), or
+ * ready for the sweeps and the probe when phi is given.  Other fields
+ * (gradient, integrals) are written through sg_get_field afterwards.  The
+ * grid's earlier fields are dropped.
+ * Errors: SG_ERR_INVALID (P < 2, a null table, or tables that are not
+ * consistent: the grid is then untagged), SG_ERR_CAPACITY, SG_ERR_OOM. */
+SG_API sg_status sg_restore(sg_grid *g, int64_t P, const int32_t *cell_pkg, const int32_t *pkg_cell,
+                            const uint8_t *pkg_type, const int32_t *nbr, const float *phi);
+
 /* Allocation-free variant of sg_morton_order.  The paper has no counterpart;
  * this entry point exists for callers that cannot let a library allocate
  * device memory: applications that hand (nearly) all of the device memory to

@@ -108,6 +108,7 @@ def lib():
         L.sg_n_packages.restype = i64
         L.sg_set_stream.argtypes = [vp, vp]
         L.sg_check_tables.argtypes = [vp]
+        L.sg_restore.argtypes = [vp, i64, vp, vp, vp, vp, vp]
         L.sg_clear_error.argtypes = [vp]
         L.sg_status_sync.argtypes = [vp]
         L.sg_last_error.argtypes = [vp]
@@ -391,6 +392,34 @@ class Grid:
     def n_packages(self) -> int:
         return int(self._lib.sg_n_packages(self._h))
 
+    # -- checkpoint ------------------------------------------------------------
+    def checkpoint(self, fields=("phi", "gx", "gy", "gz", "W", "Gx", "Gy", "Gz")):
+        """Host copy of the grid: the tagging's tables and the named float
+        fields (numpy arrays), for save_checkpoint / restore."""
+        ck = {"P": np.int64(self.P)}
+        for name in ("cell_pkg", "pkg_cell", "pkg_type", "nbr"):
+            ck[name] = self.field(name).cpu().numpy().copy()
+        for name in fields:
+            ck[name] = self.field(name).cpu().numpy().copy()
+        return ck
+
+    def restore(self, ck):
+        """Put a checkpoint back (a grid created with the same description):
+        tables and phi through sg_restore (checked), the other fields through
+        their device views."""
+        torch = _torch()
+        arrs = {k: np.ascontiguousarray(ck[k]) for k in ("cell_pkg", "pkg_cell", "pkg_type", "nbr")}
+        assert arrs["cell_pkg"].dtype == np.int32 and arrs["nbr"].dtype == np.int32
+        phi = np.ascontiguousarray(ck["phi"], np.float32) if "phi" in ck else None
+        self._check(self._lib.sg_restore(self._h, int(ck["P"]), *(arrs[k].ctypes.data_as(C.c_void_p)
+                                                                 for k in ("cell_pkg", "pkg_cell", "pkg_type", "nbr")),
+                                         phi.ctypes.data_as(C.c_void_p) if phi is not None else None))
+        self.P = int(ck["P"])
+        for name in FIELDS:
+            if name != "phi" and name in ck:
+                self.field(name).copy_(torch.from_numpy(np.ascontiguousarray(ck[name], np.float32)))
+        torch.cuda.synchronize()
+
 
 BATCH_CANDIDATES = ((1, 1), (2, 1), (2, 2), (4, 1), (4, 2), (8, 1), (8, 2))
 
@@ -621,6 +650,30 @@ class MultiResolution:
         for g in self.grids:
             g.close()
         self.grids = []
+
+
+def save_checkpoint(path, grid=None, mlp=None):
+    """One .npz file with a grid's checkpoint (Grid.checkpoint) and/or a
+    network's parameters: the FP32 master vector and its BF16 rounding (the
+    values the tensor cores use), as raw arrays."""
+    out = {}
+    if grid is not None:
+        out.update({"grid_" + k: v for k, v in grid.checkpoint().items()})
+    if mlp is not None:
+        par = mlp.get_params()
+        out["mlp_master"] = par
+        out["mlp_bf16"] = (par.view(np.uint32) + 0x7FFF + ((par.view(np.uint32) >> 16) & 1) >> 16).astype(np.uint16)
+    np.savez(path, **out)
+
+
+def load_checkpoint(path, grid=None, mlp=None):
+    """Restore what save_checkpoint wrote into a grid (of the same
+    description) and/or a network."""
+    d = np.load(path)
+    if grid is not None:
+        grid.restore({k[5:]: d[k] for k in d.files if k.startswith("grid_")})
+    if mlp is not None:
+        mlp.set_params(d["mlp_master"])
 
 
 def morton_order_noalloc(spec, x, y, z, keys=None, order=None, stream=None):

@@ -637,6 +637,49 @@ sg_status sg_get_field(sg_grid* g, int32_t field, void** dev_ptr, int64_t* n_ele
     }
 }
 
+sg_status sg_restore(sg_grid* g, int64_t P, const int32_t* cell_pkg, const int32_t* pkg_cell, const uint8_t* pkg_type,
+                     const int32_t* nbr, const float* phi) {
+    SG_CHECK_GRID(g);
+    if (P < 2 || !cell_pkg || !pkg_cell || !pkg_type || !nbr)
+        return fail(g, SG_ERR_INVALID, "sg_restore: P < 2 or a null table");
+    if (P >= (1LL << 31) / NB) return fail(g, SG_ERR_CAPACITY, "sg_restore: too many packages");
+    DeviceGuard dg(g->device);
+    for (int f = 0; f < SG_N_FLOAT_FIELDS; ++f) g->stale[f] = true;
+    if (!ensure(g, g->cell_pkg, (size_t)g->nc * 4) || !ensure(g, g->pkg_cell, (size_t)P * 4) ||
+        !ensure(g, g->pkg_type, (size_t)P) || !ensure(g, g->nbr, (size_t)P * NB * 4) ||
+        !ensure(g, g->faces, (size_t)P * 8 * 4)) {
+        g->state = 0;
+        return fail(g, SG_ERR_OOM, "sg_restore: out of device memory");
+    }
+    g->P = P;
+    g->state = 1;
+    SG_CUDA(g, cudaMemcpyAsync(g->cell_pkg.p, cell_pkg, (size_t)g->nc * 4, cudaMemcpyHostToDevice, g->stream), "restore");
+    SG_CUDA(g, cudaMemcpyAsync(g->pkg_cell.p, pkg_cell, (size_t)P * 4, cudaMemcpyHostToDevice, g->stream), "restore");
+    SG_CUDA(g, cudaMemcpyAsync(g->pkg_type.p, pkg_type, (size_t)P, cudaMemcpyHostToDevice, g->stream), "restore");
+    SG_CUDA(g, cudaMemcpyAsync(g->nbr.p, nbr, (size_t)P * NB * 4, cudaMemcpyHostToDevice, g->stream), "restore");
+    SG_CUDA(g, launch_fill_faces((const int32_t*)g->nbr.p, (int32_t*)g->faces.p, P, g->stream), "restore faces");
+    // a checkpoint is input: the tables are checked (bounds and consistency) before the grid is used
+    SG_CUDA(g, cudaMemsetAsync(g->err.p, 0, sizeof(int32_t), g->stream), "restore");
+    SG_CUDA(g, launch_check_tables(grid_ff(g), (const int32_t*)g->cell_pkg.p, (const int32_t*)g->pkg_cell.p,
+                                   (const uint8_t*)g->pkg_type.p, (const int32_t*)g->nbr.p, (const int32_t*)g->faces.p,
+                                   g->P, g->nc, (int*)g->err.p, g->stream),
+            "restore check");
+    if (phi) {
+        float* d = field_ptr(g, SG_FIELD_PHI, false);
+        if (!d) return fail(g, SG_ERR_OOM, "sg_restore: out of device memory");
+        SG_CUDA(g, cudaMemcpyAsync(d, phi, (size_t)P * PKG3 * 4, cudaMemcpyHostToDevice, g->stream), "restore phi");
+    }
+    SG_CUDA(g, cudaMemcpyAsync(g->host_pin.p, g->err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream), "restore");
+    SG_CUDA(g, cudaStreamSynchronize(g->stream), "restore sync");  // the host arrays may be temporary
+    if (*(int32_t*)g->host_pin.p) {
+        g->state = 0;
+        SG_CUDA(g, cudaMemsetAsync(g->err.p, 0, sizeof(int32_t), g->stream), "restore");
+        return fail(g, SG_ERR_INVALID, "sg_restore: the tables are not consistent");
+    }
+    g->state = phi ? 2 : 1;
+    return SG_OK;
+}
+
 sg_status sg_check_tables(sg_grid* g) {
     SG_CHECK_GRID(g);
     if (g->state < 1) return fail(g, SG_ERR_STATE, "sg_check_tables: grid not tagged");

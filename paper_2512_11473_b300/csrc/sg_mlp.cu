@@ -129,23 +129,53 @@ __global__ void k_mlp_adam(const float* __restrict__ part, int ctas, float* __re
 // ---------------------------------------------------------------------------
 // Tensor-core tile machinery
 // ---------------------------------------------------------------------------
+// The threads that work one tile: the whole CTA of 128 threads (group 0,
+// synchronised by __syncthreads), or one of the 128-thread warpgroups of a
+// larger CTA (group g >= 0 with named barrier 1 + g).
 struct Tc {
-    uint32_t tmem;   // TMEM base address of the CTA's columns
-    uint64_t* bar;   // completion barrier of the products
+    uint32_t tmem;   // TMEM address of the group's columns
+    uint64_t* bar;   // completion barrier of the group's products
     uint32_t phase;  // parity of the next completion
-    bool ok;         // every wait so far completed (uniform over the CTA)
+    bool ok;         // every wait so far completed (uniform over the group)
+    int group;       // -1: the whole CTA; else the warpgroup, named barrier 1 + group
 };
 
-// Warp 0 allocates ncols TMEM columns, thread 0 initialises the barrier.
-__device__ __forceinline__ Tc tc_begin(uint64_t* bar, uint32_t* slot, uint32_t ncols) {
+__device__ __forceinline__ int tc_row() { return threadIdx.x & (TC_ROWS - 1); }
+
+__device__ __forceinline__ void tc_sync(const Tc& t) {
+    if (t.group < 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + t.group), "r"(TC_ROWS) : "memory");
+}
+
+__device__ __forceinline__ bool tc_sync_and(const Tc& t, bool v) {
+    if (t.group < 0) return __syncthreads_and(v) != 0;
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(r)
+        : "r"(v ? 1u : 0u), "r"(1 + t.group), "r"(TC_ROWS)
+        : "memory");
+    return r != 0;
+}
+
+// Warp 0 allocates ncols TMEM columns for the whole CTA and thread 0
+// initialises one barrier per group (bars[0 .. groups)); group g (or the
+// whole CTA, groups = 0) then uses columns [g ncols / groups, ...).
+__device__ __forceinline__ Tc tc_begin(uint64_t* bars, uint32_t* slot, uint32_t ncols, int groups = 0) {
     if (threadIdx.x < 32) umma::tmem_alloc(slot, ncols);
-    if (threadIdx.x == 0) umma::mbar_init(bar, 1);
+    if (threadIdx.x == 0)
+        for (int g = 0; g < (groups > 0 ? groups : 1); ++g) umma::mbar_init(bars + g, 1);
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
     Tc t;
-    t.tmem = *slot;
-    t.bar = bar;
+    t.group = groups > 0 ? (int)(threadIdx.x / TC_ROWS) : -1;
+    const int g = t.group < 0 ? 0 : t.group;
+    t.tmem = *slot + (uint32_t)(groups > 0 ? g * (int)(ncols / groups) : 0);
+    t.bar = bars + g;
     t.phase = 0;
     t.ok = true;
     return t;
@@ -153,17 +183,18 @@ __device__ __forceinline__ Tc tc_begin(uint64_t* bar, uint32_t* slot, uint32_t n
 
 // Make this thread's shared-memory operand stores visible to the tensor
 // core and order its TMEM reads before the next product.
-__device__ __forceinline__ void tc_publish() {
+__device__ __forceinline__ void tc_publish(const Tc& t) {
     umma::fence_smem_to_async();
     umma::fence_before_sync();
-    __syncthreads();
+    tc_sync(t);
 }
 
 // D (TMEM columns from tcol) = A B^T, A and B K-major with K columns, N
-// columns of D; thread 0 issues the K / 16 products and commits.
+// columns of D; the group's first thread issues the K / 16 products and
+// commits.
 __device__ __forceinline__ void tc_gemm(const Tc& t, uint32_t tcol, const unsigned char* A, const unsigned char* B,
                                         int K, int N) {
-    if (threadIdx.x == 0) {
+    if (tc_row() == 0) {
         umma::fence_after_sync();
         const uint32_t id = umma::idesc_bf16(TC_ROWS, N), sa = umma::smem_u32(A), sb = umma::smem_u32(B);
         for (int k = 0; k < K; k += 16)
@@ -172,26 +203,27 @@ __device__ __forceinline__ void tc_gemm(const Tc& t, uint32_t tcol, const unsign
     }
 }
 
-// Every thread waits for the products committed last.
+// Every thread of the group waits for the products committed last.
 __device__ __forceinline__ bool tc_wait(Tc& t) {
     const bool done = umma::mbar_wait(t.bar, t.phase, WAIT_POLLS);
-    t.ok = __syncthreads_and(done) != 0;
+    t.ok = tc_sync_and(t, done);
     if (t.ok) t.phase ^= 1u;
     umma::fence_after_sync();
     return t.ok;
 }
 
-// Free the TMEM columns; after a wait that gave up, first wait (bounded) for
-// the product still in flight and raise ERR_TIMEOUT.
-__device__ __forceinline__ void tc_end(Tc& t, uint32_t ncols, int* err) {
-    if (!t.ok && threadIdx.x == 0) {
+// Free the CTA's TMEM columns (every group done); after a wait that gave up,
+// first wait (bounded) for the group's product still in flight and raise
+// ERR_TIMEOUT.
+__device__ __forceinline__ void tc_end(Tc& t, uint32_t slot_base, uint32_t ncols, int* err) {
+    if (!t.ok && tc_row() == 0) {
         umma::mbar_wait(t.bar, t.phase, WAIT_POLLS);
         if (err) atomicOr(err, ERR_TIMEOUT);
     }
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
-    if (threadIdx.x < 32) umma::tmem_dealloc(t.tmem, ncols);
+    if (threadIdx.x < 32) umma::tmem_dealloc(slot_base, ncols);
 }
 
 __device__ __forceinline__ uint32_t lane_col(const Tc& t, int col) {
@@ -211,7 +243,7 @@ __device__ __forceinline__ void tc_ld32(const Tc& t, int col, float (&v)[32]) {
 // Hidden layer out of TMEM: row r of the 64 columns at tcol, plus bias,
 // SiLU, rounded to BF16 into the K-major operand A ([128][64]).
 __device__ __forceinline__ void tc_hidden(const Tc& t, int tcol, const float* bias, unsigned char* A) {
-    const int r = threadIdx.x;
+    const int r = tc_row();
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         float v[32];
@@ -229,15 +261,15 @@ __device__ __forceinline__ void tc_hidden(const Tc& t, int tcol, const float* bi
 // this thread's four outputs.  W is the packed forward part in shared memory.
 __device__ __forceinline__ void tc_forward(Tc& t, const unsigned char* W, unsigned char* T, float (&y)[4]) {
     const float* bias = reinterpret_cast<const float*>(W + PK_BIAS);
-    tc_publish();
+    tc_publish(t);
     tc_gemm(t, 0, T, W + PK_W1, MLP_K1, MLP_H);
     if (!tc_wait(t)) return;
     tc_hidden(t, 0, bias, T);  // layer 1 has read the inputs
-    tc_publish();
+    tc_publish(t);
     tc_gemm(t, 0, T, W + PK_W2, MLP_H, MLP_H);
     if (!tc_wait(t)) return;
     tc_hidden(t, 0, bias + MLP_H, T);
-    tc_publish();
+    tc_publish(t);
     tc_gemm(t, 0, T, W + PK_W3, MLP_H, MLP_N3);
     if (!tc_wait(t)) return;
     float v[16];
@@ -267,6 +299,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_mlp_forward(const unsigned char* __
     stage_bytes(smem, packed, PK_FWD_BYTES);
     unsigned char* T = smem + FWD_T;
     Tc t = tc_begin(&bar, &slot, 64);
+    const uint32_t tbase = t.tmem;
     const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
     for (int64_t tile = blockIdx.x; tile < tiles && t.ok; tile += gridDim.x) {
         const int64_t row = tile * TC_ROWS + threadIdx.x;
@@ -279,7 +312,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_mlp_forward(const unsigned char* __
         tc_forward(t, smem, T, o);
         if (t.ok && row < n) *reinterpret_cast<float4*>(y + row * MLP_OUT) = make_float4(o[0], o[1], o[2], o[3]);
     }
-    tc_end(t, 64, err);
+    tc_end(t, tbase, 64, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -344,10 +377,11 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* _
                 c == ONES ? __float2bfloat16_rn(1.0f) : xr[c];
     }
     Tc t = tc_begin(&bar, &slot, 256);
+    const uint32_t tbase = t.tmem;
     float* pg = part + (int64_t)blockIdx.x * MLP_NPARAM;
     do {
         // layer 1
-        tc_publish();
+        tc_publish(t);
         tc_gemm(t, TM_Z1, X, W + PK_W1, MLP_K1, MLP_H);
         if (!tc_wait(t)) break;
 #pragma unroll
@@ -363,12 +397,12 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* _
             for (int i = 0; i < 32; ++i) put_bf16(BG, kmajor_byte(MLP_K1 + 32 * h + i, r, TC_ROWS), v[i]);
         }
         // layer 2
-        tc_publish();
+        tc_publish(t);
         tc_gemm(t, TM_Z2, A1, W + PK_W2, MLP_H, MLP_H);
         if (!tc_wait(t)) break;
         tc_hidden(t, TM_Z2, bias + MLP_H, A2);
         // layer 3, loss, dY
-        tc_publish();
+        tc_publish(t);
         tc_gemm(t, TM_Y, A2, W + PK_W3, MLP_H, MLP_N3);
         if (!tc_wait(t)) break;
         {
@@ -392,7 +426,7 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* _
                 *reinterpret_cast<uint4*>(DY + kmajor_byte(r, 8 * q, MLP_N3)) = umma::pack8_bf16(dy + 8 * q);
         }
         // dA2 = dY W3, dZ2 = dA2 SiLU'(z2)
-        tc_publish();
+        tc_publish(t);
         tc_gemm(t, TM_DA, DY, W + PK_W3T, MLP_N3, MLP_H);
         if (!tc_wait(t)) break;
 #pragma unroll
@@ -412,7 +446,7 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* _
             for (int i = 0; i < 32; ++i) put_bf16(AG, kmajor_byte(MLP_H + 32 * h + i, r, TC_ROWS), da[i]);
         }
         // dA1 = dZ2 W2, dZ1 = dA1 SiLU'(z1)
-        tc_publish();
+        tc_publish(t);
         tc_gemm(t, TM_DA, DZ2, W + PK_W2T, MLP_H, MLP_H);
         if (!tc_wait(t)) break;
 #pragma unroll
@@ -427,7 +461,7 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* _
             }
         }
         // [dZ1^T; dZ2^T] [X | A1]: dW1, db1 (rows 0..63), dW2, db2 (rows 64..127)
-        tc_publish();
+        tc_publish(t);
         tc_gemm(t, TM_G, AG, BG, TC_ROWS, NG);
         if (!tc_wait(t)) break;
         {
@@ -479,7 +513,7 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* _
             part[(int64_t)gridDim.x * MLP_NPARAM + blockIdx.x] = l;
         }
     }
-    tc_end(t, 256, err);
+    tc_end(t, tbase, 256, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -504,6 +538,7 @@ __global__ void __launch_bounds__(SA_THREADS) k_sur_a(const int32_t* __restrict_
     __shared__ float s_H[SA_PKGS][TILE_N];
     __shared__ unsigned s_sat[SA_PKGS];
     __shared__ unsigned s_triv[SA_PKGS];  // bit 0: every tile value >= h (all points trivially outside), bit 1: <= -h
+    __shared__ uint16_t s_mask[SA_PKGS][36];  // per tile row: bit i of the low byte: value i >= h; high byte: <= -h
     __shared__ SurConst s_C[SA_PKGS];
     __shared__ float s_ie[SA_PKGS];
     __shared__ bool s_ok[SA_PKGS];
@@ -535,29 +570,50 @@ __global__ void __launch_bounds__(SA_THREADS) k_sur_a(const int32_t* __restrict_
         if (s_ok[lp]) s_nb[lp][e - lp * NB] = __ldg(nbr + (p0 + lp) * NB + (e - lp * NB));
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < SA_PKGS * 36; e += SA_THREADS) {
-        const int lp = e / 36;
+    // staging, one tile row of six per thread (a warp's 32 consecutive rows
+    // span at most two packages: their saturation bits and whole-package
+    // class flags are reduced over the warp per package, one atomic each).
+    // Whole-package classes: a tile whose every value has |phi| >= h on one
+    // side makes every point's 27 taps trivial (the exact comparison of
+    // sur_class_at), decided here from the values in registers.
+    for (int e = threadIdx.x; e < SA_PKGS * 36; e += SA_THREADS) {  // uniform per warp
+        const int lp = e / 36, lp0 = (e - (threadIdx.x & 31)) / 36;
+        unsigned bits = 0, keep = 3u;
         if (s_ok[lp]) {
-            const unsigned bits = stage_rows(s_nb[lp], phi, s_ie[lp], e - lp * 36, s_phi[lp], s_H[lp]);
-            if (bits) atomicOr(&s_sat[lp], bits);
-        }
-    }
-    __syncthreads();
-    // whole-package classes: a tile whose every value has |phi| >= h on one side makes every
-    // point's 27 taps trivial (the same exact comparison as sur_class_at)
-    for (int e = threadIdx.x; e < SA_PKGS * 36; e += SA_THREADS) {
-        const int lp = e / 36, rr = e - lp * 36;
-        if (s_ok[lp]) {
-            const float* row = s_phi[lp] + TILE_Y * (rr % 6) + TILE_Z * (rr / 6);
-            const float hu = s_C[lp].h_up;
-            bool out = true, in = true;
+            const int d = e - lp * 36;
+            const int* nb27 = s_nb[lp];
+            const int y = d % 6 - 1, z = d / 6 - 1;
+            const int oy = ((y + 4) >> 2) - 1, oz = ((z + 4) >> 2) - 1;
+            const int d0 = 4 * (y - 4 * oy) + 16 * (z - 4 * oz);
+            const int nb = 3 * (oy + 1) + 9 * (oz + 1);
+            const float4 v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb27[nb + 1] * PKG3 + d0));
+            const float vm = __ldg(phi + (int64_t)nb27[nb] * PKG3 + d0 + 3);
+            const float vp = __ldg(phi + (int64_t)nb27[nb + 2] * PKG3 + d0);
+            const int e0 = TILE_Y * (y + 1) + TILE_Z * (z + 1);
+            const float f[6] = {vm, v.x, v.y, v.z, v.w, vp};
+            const float hu = s_C[lp].h_up, ie = s_ie[lp];
+            unsigned mo = 0, mi = 0;
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
-                out &= row[i] >= hu;
-                in &= -row[i] >= hu;
+                s_phi[lp][e0 + i] = f[i];
+                const float hv = heaviside_neg(f[i], ie);
+                s_H[lp][e0 + i] = hv;
+                bits |= (hv != 0.0f ? 1u : 0u) | (hv != 1.0f ? 2u : 0u);
+                mo |= (f[i] >= hu ? 1u : 0u) << i;
+                mi |= (-f[i] >= hu ? 1u : 0u) << i;
             }
-            const unsigned keep = (out ? 1u : 0u) | (in ? 2u : 0u);
-            if (keep != 3u) atomicAnd(&s_triv[lp], keep);
+            s_mask[lp][d] = (uint16_t)(mo | (mi << 8));
+            keep = (mo == 0x3Fu ? 1u : 0u) | (mi == 0x3Fu ? 2u : 0u);
+        }
+        const unsigned b0 = __reduce_or_sync(0xffffffffu, lp == lp0 ? bits : 0u);
+        const unsigned b1 = __reduce_or_sync(0xffffffffu, lp == lp0 ? 0u : bits);
+        const unsigned k0 = __reduce_and_sync(0xffffffffu, lp == lp0 ? keep : 3u);
+        const unsigned k1 = __reduce_and_sync(0xffffffffu, lp == lp0 ? 3u : keep);
+        if ((threadIdx.x & 31) == 0) {
+            if (b0) atomicOr(&s_sat[lp0], b0);
+            if (b1) atomicOr(&s_sat[lp0 + 1], b1);
+            if (k0 != 3u) atomicAnd(&s_triv[lp0], k0);
+            if (k1 != 3u) atomicAnd(&s_triv[lp0 + 1], k1);
         }
     }
     __syncthreads();
@@ -566,16 +622,35 @@ __global__ void __launch_bounds__(SA_THREADS) k_sur_a(const int32_t* __restrict_
     const int64_t pt0 = (p0 + lp) * PKG3 + 4 * rw;
     float w[4], ax[4], ay[4], az[4];
     unsigned net = 0;
+    unsigned cnt[4] = {0, 0, 0, 0};
     if (ok) {
         const SurConst C = s_C[lp];
         const unsigned triv = s_triv[lp];
-        unsigned cnt[4] = {0, 0, 0, 0};
+        // the 27-tap trivial tests of the row's four points from the 3 x 3
+        // tile rows around it: point x is trivially outside (inside) when
+        // bits x .. x + 2 of the AND of those rows' masks are set
+        unsigned m = 0xFFFFu;
+        if (!triv) {
+            const int j = rw & 3, k = rw >> 2;
+#pragma unroll
+            for (int sz = 0; sz < 3; ++sz)
+#pragma unroll
+                for (int sy = 0; sy < 3; ++sy) m &= s_mask[lp][(j + sy) + 6 * (k + sz)];
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int d = 4 * rw + i;
-            const int cls = (triv & 1u)   ? SG_SUR_TRIVIAL_OUT
-                            : (triv & 2u) ? SG_SUR_TRIVIAL_IN
-                                          : sur_class_at(s_phi[lp], tile_e0(d), C);
+            int cls;
+            if (triv & 1u)
+                cls = SG_SUR_TRIVIAL_OUT;
+            else if (triv & 2u)
+                cls = SG_SUR_TRIVIAL_IN;
+            else if (((m >> (8 + i)) & 7u) == 7u)
+                cls = SG_SUR_TRIVIAL_IN;
+            else if (((m >> i) & 7u) == 7u)
+                cls = SG_SUR_TRIVIAL_OUT;
+            else
+                cls = sur_fallback_at(s_phi[lp], tile_e0(d), C) ? SG_SUR_FALLBACK : SG_SUR_NETWORK;
             ++cnt[cls];
             w[i] = cls == SG_SUR_TRIVIAL_IN ? 1.0f : 0.0f;
             ax[i] = ay[i] = az[i] = 0.0f;
@@ -586,13 +661,16 @@ __global__ void __launch_bounds__(SA_THREADS) k_sur_a(const int32_t* __restrict_
                 net |= 1u << i;
             }
         }
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (cnt[c]) atomicAdd(&s_cnt[c], cnt[c]);
         reinterpret_cast<float4*>(W)[pt0 >> 2] = make_float4(w[0], w[1], w[2], w[3]);
         reinterpret_cast<float4*>(gx)[pt0 >> 2] = make_float4(ax[0], ax[1], ax[2], ax[3]);
         reinterpret_cast<float4*>(gy)[pt0 >> 2] = make_float4(ay[0], ay[1], ay[2], ay[3]);
         reinterpret_cast<float4*>(gz)[pt0 >> 2] = make_float4(az[0], az[1], az[2], az[3]);
+    }
+    // class counts: one shared atomic per warp and class
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned v = __reduce_add_sync(0xffffffffu, cnt[k]);
+        if (lane == 0 && v) atomicAdd(&s_cnt[k], v);
     }
     // network points: one list reservation per warp
     const unsigned c = __popc(net);
@@ -618,9 +696,13 @@ __global__ void __launch_bounds__(SA_THREADS) k_sur_a(const int32_t* __restrict_
 // ---------------------------------------------------------------------------
 // Surrogate integrals, pass B: the network over the list, 128 rows a tile.
 // ---------------------------------------------------------------------------
+// 128-row tile streams (warpgroups) per CTA: two, sharing one copy of the
+// weights, measured 347 against 334 us for one on the h = 0.002 torus (at
+// the 64 registers that four CTAs of two groups allow, the kernel spills)
+constexpr int SB_GROUPS = 1;
 constexpr int SB_POS = PK_FWD_BYTES;                   // canonical input positions [48][27] bytes
-constexpr int SB_T = SB_POS + 1408;                    // tile operand
-constexpr int SB_BYTES = SB_T + TC_ROWS * MLP_H * 2;
+constexpr int SB_T = SB_POS + 1408;                    // tile operands, one per group
+constexpr int SB_BYTES = SB_T + SB_GROUPS * TC_ROWS * MLP_H * 2;
 static_assert(SB_T % 128 == 0, "tile alignment");
 
 // The 27 phi values around data point q = 64 p + d, through the index
@@ -668,25 +750,34 @@ __device__ __forceinline__ void build_pos(uint8_t* pos) {
     }
 }
 
+// SB_GROUPS warpgroups per CTA, each a stream of 128-row tiles with its own
+// tensor-memory columns, barrier and tile operand, sharing one copy of the
+// weights.
 template <bool BATCH>
-__global__ void __launch_bounds__(TC_ROWS) k_sur_b(const int32_t* __restrict__ nbr, const float* __restrict__ phi,
-                                                   float* __restrict__ W, float* __restrict__ gx,
-                                                   float* __restrict__ gy, float* __restrict__ gz, float inv_h0,
-                                                   const int32_t* __restrict__ body, const SurBody* __restrict__ sb,
-                                                   const int32_t* __restrict__ list, const unsigned* __restrict__ count,
-                                                   const unsigned char* __restrict__ packed, int* err) {
+__global__ void __launch_bounds__(SB_GROUPS * TC_ROWS) k_sur_b(const int32_t* __restrict__ nbr,
+                                                               const float* __restrict__ phi, float* __restrict__ W,
+                                                               float* __restrict__ gx, float* __restrict__ gy,
+                                                               float* __restrict__ gz, float inv_h0,
+                                                               const int32_t* __restrict__ body,
+                                                               const SurBody* __restrict__ sb,
+                                                               const int32_t* __restrict__ list,
+                                                               const unsigned* __restrict__ count,
+                                                               const unsigned char* __restrict__ packed, int* err) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bars[SB_GROUPS];
     __shared__ uint32_t slot;
     stage_bytes(smem, packed, PK_FWD_BYTES);
     uint8_t* pos = smem + SB_POS;
     build_pos(pos);
-    unsigned char* T = smem + SB_T;
-    Tc t = tc_begin(&bar, &slot, 64);
+    Tc t = tc_begin(bars, &slot, 64 * SB_GROUPS, SB_GROUPS > 1 ? SB_GROUPS : 0);  // one group: the whole CTA
+    const uint32_t tbase = slot;
+    unsigned char* T = smem + SB_T + (t.group > 0 ? t.group : 0) * TC_ROWS * MLP_H * 2;
+    const int r = tc_row();
     const int64_t n = (int64_t)*count;
     const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
-    for (int64_t tile = blockIdx.x; tile < tiles && t.ok; tile += gridDim.x) {
-        const int64_t row = tile * TC_ROWS + threadIdx.x;
+    for (int64_t tile = (int64_t)blockIdx.x * SB_GROUPS + (t.group > 0 ? t.group : 0); tile < tiles && t.ok;
+         tile += (int64_t)gridDim.x * SB_GROUPS) {
+        const int64_t row = tile * TC_ROWS + r;
         const bool valid = row < n;
         int64_t q = 0;
         int code = 0;
@@ -695,11 +786,11 @@ __global__ void __launch_bounds__(TC_ROWS) k_sur_b(const int32_t* __restrict__ n
             float f[MLP_IN];
             gather27(nbr, phi, q, f);
             const float inv_h = BATCH ? sb[__ldg(body + (q >> 6))].C.inv_h : inv_h0;
-            code = canon_row(f, inv_h, pos, T, threadIdx.x);
+            code = canon_row(f, inv_h, pos, T, r);
         } else {
 #pragma unroll
             for (int c = 0; c < MLP_K1 / 8; ++c)
-                *reinterpret_cast<uint4*>(T + umma::kmajor_byte(threadIdx.x, 8 * c, MLP_K1)) = make_uint4(0, 0, 0, 0);
+                *reinterpret_cast<uint4*>(T + umma::kmajor_byte(r, 8 * c, MLP_K1)) = make_uint4(0, 0, 0, 0);
         }
         float y[4], o[4];
         tc_forward(t, smem, T, y);
@@ -711,7 +802,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_sur_b(const int32_t* __restrict__ n
             gz[q] = o[3];
         }
     }
-    tc_end(t, 64, err);
+    tc_end(t, tbase, 64 * SB_GROUPS, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -839,7 +930,7 @@ sg_status m_fail(sg_mlp* m, sg_status st, const std::string& msg) {
 // Persistent grid of a tensor-core kernel: the CTAs that fit on every SM
 // at once by registers, shared memory, threads and the 512 TMEM columns
 // (ncols per CTA), so that no CTA waits for another's columns.
-unsigned tc_grid(const void* fn, int smem, uint32_t ncols, int device, int64_t tiles) {
+unsigned tc_grid(const void* fn, int smem, uint32_t ncols, int device, int64_t tiles, int threads = TC_ROWS) {
     cudaFuncAttributes fa{};
     int sms = 0, smem_sm = 0, regs_sm = 0;
     if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) cudaGetLastError();
@@ -847,9 +938,9 @@ unsigned tc_grid(const void* fn, int smem, uint32_t ncols, int device, int64_t t
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
     cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, device);
     int per_sm = (int)(512 / ncols);
-    per_sm = std::min(per_sm, 2048 / TC_ROWS);
+    per_sm = std::min(per_sm, 2048 / threads);
     const int regs = (std::max(fa.numRegs, 1) + 7) / 8 * 8;
-    if (regs_sm > 0) per_sm = std::min(per_sm, regs_sm / (regs * TC_ROWS));
+    if (regs_sm > 0) per_sm = std::min(per_sm, regs_sm / (regs * threads));
     if (smem_sm > 0) per_sm = std::min(per_sm, smem_sm / (smem + (int)fa.sharedSizeBytes + 1024));
     int64_t b = (int64_t)std::max(per_sm, 1) * std::max(sms, 1);
     if (tiles > 0 && b > tiles) b = tiles;
@@ -1095,7 +1186,8 @@ cudaError_t launch_surrogate_integrals(sg_grid* g, const sg_mlp* m, void* work, 
     if ((e = cudaFuncSetAttribute(k_sur_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SB_BYTES)) !=
         cudaSuccess)
         return e;
-    k_sur_b<false><<<tc_grid((const void*)k_sur_b<false>, SB_BYTES, 64, g->device, 0), TC_ROWS, SB_BYTES, g->stream>>>(
+    k_sur_b<false><<<tc_grid((const void*)k_sur_b<false>, SB_BYTES, 64 * SB_GROUPS, g->device, 0, SB_GROUPS * TC_ROWS),
+                     SB_GROUPS * TC_ROWS, SB_BYTES, g->stream>>>(
         nbr, phi, W, gx, gy, gz, (float)(1.0 / g->desc.h), nullptr, nullptr, list, count, m->packed,
         (int*)g->err.p);
     note_launch(2);
@@ -1124,7 +1216,8 @@ cudaError_t launch_batch_surrogate_integrals(const int32_t* nbr, const uint8_t* 
     if (e != cudaSuccess) return e;
     k_sur_a<true><<<cdiv(P - 2, SA_PKGS), SA_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(), 0.0f,
                                                               SurConst{}, type, body, sb, list, count, nullptr);
-    k_sur_b<true><<<tc_grid((const void*)k_sur_b<true>, SB_BYTES, 64, device, 0), TC_ROWS, SB_BYTES, s>>>(
+    k_sur_b<true><<<tc_grid((const void*)k_sur_b<true>, SB_BYTES, 64 * SB_GROUPS, device, 0, SB_GROUPS * TC_ROWS),
+                    SB_GROUPS * TC_ROWS, SB_BYTES, s>>>(
         nbr, phi, W, gx, gy, gz, 0.0f, body, sb, list, count, m->packed, err);
     note_launch(2);
     return cudaGetLastError();

@@ -83,6 +83,15 @@ __device__ __forceinline__ int sur_class_at(const float* tile, int e0, const Sur
     return SG_SUR_NETWORK;
 }
 
+// The fallback test of a point that is not trivial: |phi| < h, or
+// |kappa| h > 0.1 (the last two steps of sur_class_at).
+__device__ __forceinline__ bool sur_fallback_at(const float* tile, int e0, const SurConst& C) {
+    const float c = tile[e0];
+    if (fabsf(c) < C.h_up) return true;
+    return curvature_exceeds(tile[e0 + 1], tile[e0 - 1], tile[e0 + TILE_Y], tile[e0 - TILE_Y], tile[e0 + TILE_Z],
+                             tile[e0 - TILE_Z], c, C);
+}
+
 __device__ __forceinline__ int tile_e0(int d) { return ((d & 3) + 1) + TILE_Y * (((d >> 2) & 3) + 1) + TILE_Z * ((d >> 4) + 1); }
 
 // ---------------------------------------------------------------------------
