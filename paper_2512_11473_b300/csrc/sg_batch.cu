@@ -131,12 +131,17 @@ __global__ void __launch_bounds__(BT, DEPTH == 1 ? 6 : 1) k_batch_reinit(const i
                                                      const int32_t* __restrict__ body,
                                                      const BodyParams* __restrict__ prm, const float* __restrict__ s0,
                                                      const float* __restrict__ phi_in, float* __restrict__ phi_out,
-                                                     int64_t P, int ppi, unsigned* counter) {
+                                                     int64_t P, int ppi, unsigned* counter, int reverse) {
     __shared__ int s_item;
     const int64_t per_item = (int64_t)BT_HW * ppi, items = (P + per_item - 1) / per_item;
     for (;;) {
-        const int64_t item = next_item(counter, &s_item);
+        int64_t item = next_item(counter, &s_item);
         if (item >= items) break;
+        // every other sweep walks the store backwards (the first one, after the
+        // forward smoothed-sign pass, among them), so that it starts on the
+        // packages the previous pass left in L2 (the Jacobi results do not
+        // depend on the order)
+        if (reverse) item = items - 1 - item;
         for (int k = 0; k < ppi; k += DEPTH) {
             RowSlot sl[DEPTH];
             Rows w[DEPTH];
@@ -445,9 +450,9 @@ cudaError_t record_run(sg_batch* b, const sg_batch_plan& plan, cudaStream_t s) {
     const int nbr1 = persistent_blocks((const void*)k_batch_reinit<1>, b->device);
     for (int it = 0; it < iters; ++it) {
         if (plan.depth == 2)
-            k_batch_reinit<2><<<nbr2, BT, 0, s>>>(faces, type, body, prm, s0, a, o, b->P, ppi, ctr + c++);
+            k_batch_reinit<2><<<nbr2, BT, 0, s>>>(faces, type, body, prm, s0, a, o, b->P, ppi, ctr + c++, (it & 1) ^ 1);
         else
-            k_batch_reinit<1><<<nbr1, BT, 0, s>>>(faces, type, body, prm, s0, a, o, b->P, ppi, ctr + c++);
+            k_batch_reinit<1><<<nbr1, BT, 0, s>>>(faces, type, body, prm, s0, a, o, b->P, ppi, ctr + c++, (it & 1) ^ 1);
         note_launch();
         float* t = a;
         a = o;
