@@ -248,8 +248,7 @@ __device__ __forceinline__ void tc_hidden(const Tc& t, int tcol, const float* bi
     for (int h = 0; h < 2; ++h) {
         float v[32];
         tc_ld32(t, tcol + 32 * h, v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = silu_(v[i] + bias[32 * h + i]);
+        silu32_bias(v, bias + 32 * h);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             *reinterpret_cast<uint4*>(A + umma::kmajor_byte(r, 32 * h + 8 * q, MLP_H)) = umma::pack8_bf16(v + 8 * q);
@@ -388,8 +387,7 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* _
         for (int h = 0; h < 2; ++h) {
             float v[32];
             tc_ld32(t, TM_Z1 + 32 * h, v);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = silu_(v[i] + bias[32 * h + i]);
+            silu32_bias(v, bias + 32 * h);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 *reinterpret_cast<uint4*>(A1 + kmajor_byte(r, 32 * h + 8 * q, MLP_H)) = umma::pack8_bf16(v + 8 * q);
@@ -520,177 +518,234 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* _
 // Surrogate integrals, pass A: classes, trivial constants, exact fallback,
 // list of network points.
 // ---------------------------------------------------------------------------
-constexpr int SA_THREADS = 256;
-constexpr int SA_PKGS = 16;  // packages per CTA (16 threads per package, a row of four points each)
+constexpr int SA_WARPS = 8;  // warps per CTA
+#ifndef SG_SA_MIN_CTAS
+#define SG_SA_MIN_CTAS 4
+#endif
 
+// The structure of the exact kernel (k_kernel_integrals): each warp takes
+// pairs of packages in turn and stages their Heaviside tiles by x-rows; it
+// also keeps the phi tiles (for the curvature) and a row mask per tile row
+// (bit i of the low byte: value i >= h, of the high byte: -value >= h, the
+// exact comparisons of sur_class_at).  A package whose whole tile lies at
+// |phi| >= h on one side is trivial without per-point work; otherwise each
+// lane classifies its row of four points from the AND of the 3 x 3 masks
+// around it and the fallback test.  Trivial points get the exact constants,
+// fallback points the exact sums exactly as mode 0 forms them, and network
+// points (written 0 here) go on the list, one reservation per warp.  With
+// BATCH, packages of type < 2 are skipped and every package takes its body's
+// constants.
 template <bool BATCH>
-__global__ void __launch_bounds__(SA_THREADS) k_sur_a(const int32_t* __restrict__ nbr, const float* __restrict__ phi,
-                                                      float* __restrict__ W, float* __restrict__ gx,
-                                                      float* __restrict__ gy, float* __restrict__ gz, int64_t P,
-                                                      KernelCoef K, float inv_eps0, SurConst C0,
-                                                      const uint8_t* __restrict__ type,
-                                                      const int32_t* __restrict__ body,
-                                                      const SurBody* __restrict__ sb, int32_t* __restrict__ list,
-                                                      unsigned* __restrict__ count,
-                                                      unsigned long long* __restrict__ stats) {
-    __shared__ int s_nb[SA_PKGS][NB];
-    __shared__ float s_phi[SA_PKGS][TILE_N];
-    __shared__ float s_H[SA_PKGS][TILE_N];
-    __shared__ unsigned s_sat[SA_PKGS];
-    __shared__ unsigned s_triv[SA_PKGS];  // bit 0: every tile value >= h (all points trivially outside), bit 1: <= -h
-    __shared__ uint16_t s_mask[SA_PKGS][36];  // per tile row: bit i of the low byte: value i >= h; high byte: <= -h
-    __shared__ SurConst s_C[SA_PKGS];
-    __shared__ float s_ie[SA_PKGS];
-    __shared__ bool s_ok[SA_PKGS];
+__global__ void __launch_bounds__(SA_WARPS * 32, SG_SA_MIN_CTAS)
+    k_sur_a(const int32_t* __restrict__ nbr, const float* __restrict__ phi, float* __restrict__ W,
+            float* __restrict__ gx, float* __restrict__ gy, float* __restrict__ gz, int64_t P, KernelCoef K,
+            SurBody B0, const uint8_t* __restrict__ type, const int32_t* __restrict__ body,
+            const SurBody* __restrict__ sb, int32_t* __restrict__ list, unsigned* __restrict__ count,
+            unsigned long long* __restrict__ stats) {
+    __shared__ float s_H[SA_WARPS][2][TILE_N];
+    __shared__ float s_phi[SA_WARPS][2][TILE_N];
+    __shared__ uint16_t s_mask[SA_WARPS][2][36];
+    __shared__ int s_nb[SA_WARPS][2][32];
+    __shared__ SurBody s_B[SA_WARPS][2];
     __shared__ unsigned s_cnt[4];
-    const int64_t p0 = 2 + (int64_t)blockIdx.x * SA_PKGS;
-    if (threadIdx.x < SA_PKGS) {
-        const int64_t p = p0 + threadIdx.x;
-        bool ok = p < P;
-        SurConst C = C0;
-        float ie = inv_eps0;
-        if (BATCH && ok) {
-            ok = __ldg(type + p) >= 2;
-            if (ok) {
-                const SurBody q = sb[__ldg(body + p)];
-                C = q.C;
-                ie = q.inv_eps;
-            }
-        }
-        s_ok[threadIdx.x] = ok;
-        s_C[threadIdx.x] = C;
-        s_ie[threadIdx.x] = ie;
-        s_sat[threadIdx.x] = 0;
-        s_triv[threadIdx.x] = 3u;
-    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (int e = threadIdx.x; e < SA_PKGS * NB; e += SA_THREADS) {
-        const int lp = e / NB;
-        if (s_ok[lp]) s_nb[lp][e - lp * NB] = __ldg(nbr + (p0 + lp) * NB + (e - lp * NB));
+    float(*tH)[TILE_N] = s_H[warp];
+    float(*tP)[TILE_N] = s_phi[warp];
+    uint16_t(*tM)[36] = s_mask[warp];
+    int(*tnb)[32] = s_nb[warp];
+    // staging rows of this lane: e = lane, lane + 32, lane + 64 (< 72): package e / 36, row e % 36
+    int r_pk[3], r_rr[3], r_nb[3], r_d0[3], r_e0[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int e = lane + 32 * q, rr = e % 36;
+        const int y = rr % 6 - 1, z = rr / 6 - 1;
+        const int oy = ((y + 4) >> 2) - 1, oz = ((z + 4) >> 2) - 1;
+        r_pk[q] = e < 72 ? e / 36 : -1;
+        r_rr[q] = rr;
+        r_nb[q] = 3 * (oy + 1) + 9 * (oz + 1);
+        r_d0[q] = 4 * (y - 4 * oy) + 16 * (z - 4 * oz);
+        r_e0[q] = TILE_Y * (y + 1) + TILE_Z * (z + 1);
     }
-    __syncthreads();
-    // staging, one tile row of six per thread (a warp's 32 consecutive rows
-    // span at most two packages: their saturation bits and whole-package
-    // class flags are reduced over the warp per package, one atomic each).
-    // Whole-package classes: a tile whose every value has |phi| >= h on one
-    // side makes every point's 27 taps trivial (the exact comparison of
-    // sur_class_at), decided here from the values in registers.
-    for (int e = threadIdx.x; e < SA_PKGS * 36; e += SA_THREADS) {  // uniform per warp
-        const int lp = e / 36, lp0 = (e - (threadIdx.x & 31)) / 36;
-        unsigned bits = 0, keep = 3u;
-        if (s_ok[lp]) {
-            const int d = e - lp * 36;
-            const int* nb27 = s_nb[lp];
-            const int y = d % 6 - 1, z = d / 6 - 1;
-            const int oy = ((y + 4) >> 2) - 1, oz = ((z + 4) >> 2) - 1;
-            const int d0 = 4 * (y - 4 * oy) + 16 * (z - 4 * oz);
-            const int nb = 3 * (oy + 1) + 9 * (oz + 1);
-            const float4 v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb27[nb + 1] * PKG3 + d0));
-            const float vm = __ldg(phi + (int64_t)nb27[nb] * PKG3 + d0 + 3);
-            const float vp = __ldg(phi + (int64_t)nb27[nb + 2] * PKG3 + d0);
-            const int e0 = TILE_Y * (y + 1) + TILE_Z * (z + 1);
+    const int half = lane >> 4, r = lane & 15;
+    const int j = r & 3, k = r >> 2;
+    const int64_t pairs = (P - 2 + 1) / 2;
+    const int64_t stride = (int64_t)gridDim.x * SA_WARPS;
+    unsigned cnt[4] = {0, 0, 0, 0};
+    int nb_next[2] = {0, 0};
+    int64_t pr = (int64_t)blockIdx.x * SA_WARPS + warp;
+    if (pr < pairs && lane < NB) {
+        nb_next[0] = __ldg(nbr + (2 + 2 * pr) * NB + lane);
+        if (3 + 2 * pr < P) nb_next[1] = __ldg(nbr + (3 + 2 * pr) * NB + lane);
+    }
+    for (; pr < pairs; pr += stride) {
+        const int64_t p0 = 2 + 2 * pr;
+        const bool two = p0 + 1 < P;
+        bool ok = lane < 2 && (lane == 0 || two);
+        if (lane < 2) {
+            SurBody b = B0;
+            if (BATCH && ok) {
+                ok = __ldg(type + p0 + lane) >= 2;
+                if (ok) b = sb[__ldg(body + p0 + lane)];
+            }
+            s_B[warp][lane] = b;
+        }
+        const unsigned okm = __ballot_sync(0xffffffffu, ok);
+        if (lane < NB) {
+            tnb[0][lane] = nb_next[0];
+            tnb[1][lane] = nb_next[1];
+        }
+        __syncwarp();
+        const int64_t pn = pr + stride;
+        if (pn < pairs && lane < NB) {
+            nb_next[0] = __ldg(nbr + (2 + 2 * pn) * NB + lane);
+            if (3 + 2 * pn < P) nb_next[1] = __ldg(nbr + (3 + 2 * pn) * NB + lane);
+        }
+        unsigned bits[2] = {0u, 0u}, keep[2] = {3u, 3u};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int pk = r_pk[q];
+            if (pk < 0 || !((okm >> pk) & 1u)) continue;
+            const int* nb = tnb[pk];
+            const float4 v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb[r_nb[q] + 1] * PKG3 + r_d0[q]));
+            const float vm = __ldg(phi + (int64_t)nb[r_nb[q]] * PKG3 + r_d0[q] + 3);
+            const float vp = __ldg(phi + (int64_t)nb[r_nb[q] + 2] * PKG3 + r_d0[q]);
             const float f[6] = {vm, v.x, v.y, v.z, v.w, vp};
-            const float hu = s_C[lp].h_up, ie = s_ie[lp];
-            unsigned mo = 0, mi = 0;
+            const float ie = s_B[warp][pk].inv_eps, hu = s_B[warp][pk].C.h_up;
+            float* t = tH[pk] + r_e0[q];
+            float* tp = tP[pk] + r_e0[q];
+            unsigned b = 0, mo = 0, mi = 0;
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
-                s_phi[lp][e0 + i] = f[i];
                 const float hv = heaviside_neg(f[i], ie);
-                s_H[lp][e0 + i] = hv;
-                bits |= (hv != 0.0f ? 1u : 0u) | (hv != 1.0f ? 2u : 0u);
+                t[i] = hv;
+                tp[i] = f[i];
+                b |= (hv != 0.0f ? 1u : 0u) | (hv != 1.0f ? 2u : 0u);
                 mo |= (f[i] >= hu ? 1u : 0u) << i;
                 mi |= (-f[i] >= hu ? 1u : 0u) << i;
             }
-            s_mask[lp][d] = (uint16_t)(mo | (mi << 8));
-            keep = (mo == 0x3Fu ? 1u : 0u) | (mi == 0x3Fu ? 2u : 0u);
+            tM[pk][r_rr[q]] = (uint16_t)(mo | (mi << 8));
+            bits[pk] |= b;
+            keep[pk] &= (mo == 0x3Fu ? 1u : 0u) | (mi == 0x3Fu ? 2u : 0u);
         }
-        const unsigned b0 = __reduce_or_sync(0xffffffffu, lp == lp0 ? bits : 0u);
-        const unsigned b1 = __reduce_or_sync(0xffffffffu, lp == lp0 ? 0u : bits);
-        const unsigned k0 = __reduce_and_sync(0xffffffffu, lp == lp0 ? keep : 3u);
-        const unsigned k1 = __reduce_and_sync(0xffffffffu, lp == lp0 ? 3u : keep);
-        if ((threadIdx.x & 31) == 0) {
-            if (b0) atomicOr(&s_sat[lp0], b0);
-            if (b1) atomicOr(&s_sat[lp0 + 1], b1);
-            if (k0 != 3u) atomicAnd(&s_triv[lp0], k0);
-            if (k1 != 3u) atomicAnd(&s_triv[lp0 + 1], k1);
-        }
-    }
-    __syncthreads();
-    const int lp = threadIdx.x >> 4, rw = threadIdx.x & 15, lane = threadIdx.x & 31;
-    const bool ok = s_ok[lp];
-    const int64_t pt0 = (p0 + lp) * PKG3 + 4 * rw;
-    float w[4], ax[4], ay[4], az[4];
-    unsigned net = 0;
-    unsigned cnt[4] = {0, 0, 0, 0};
-    if (ok) {
-        const SurConst C = s_C[lp];
-        const unsigned triv = s_triv[lp];
-        // the 27-tap trivial tests of the row's four points from the 3 x 3
-        // tile rows around it: point x is trivially outside (inside) when
-        // bits x .. x + 2 of the AND of those rows' masks are set
-        unsigned m = 0xFFFFu;
-        if (!triv) {
-            const int j = rw & 3, k = rw >> 2;
+        bits[0] = __reduce_or_sync(0xffffffffu, bits[0]);
+        bits[1] = __reduce_or_sync(0xffffffffu, bits[1]);
+        keep[0] = __reduce_and_sync(0xffffffffu, keep[0]);
+        keep[1] = __reduce_and_sync(0xffffffffu, keep[1]);
+        __syncwarp();
+        unsigned net = 0;
+        const int64_t pt0 = (p0 + half) * PKG3 + 4 * r;
+        if ((okm >> half) & 1u) {
+            const unsigned triv = keep[half];
+            const SurConst C = s_B[warp][half].C;
+            unsigned fb = 0;
+            int cls[4];
+            if (triv) {
 #pragma unroll
-            for (int sz = 0; sz < 3; ++sz)
+                for (int i = 0; i < 4; ++i) cls[i] = (triv & 1u) ? SG_SUR_TRIVIAL_OUT : SG_SUR_TRIVIAL_IN;
+            } else {
+                // the 27-tap trivial tests of the row's four points from the
+                // 3 x 3 tile rows around it: point x is trivially outside
+                // (inside) when bits x .. x + 2 of the AND of those masks are set
+                unsigned m = 0xFFFFu;
 #pragma unroll
-                for (int sy = 0; sy < 3; ++sy) m &= s_mask[lp][(j + sy) + 6 * (k + sz)];
-        }
+                for (int sz = 0; sz < 3; ++sz)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int d = 4 * rw + i;
-            int cls;
-            if (triv & 1u)
-                cls = SG_SUR_TRIVIAL_OUT;
-            else if (triv & 2u)
-                cls = SG_SUR_TRIVIAL_IN;
-            else if (((m >> (8 + i)) & 7u) == 7u)
-                cls = SG_SUR_TRIVIAL_IN;
-            else if (((m >> i) & 7u) == 7u)
-                cls = SG_SUR_TRIVIAL_OUT;
-            else
-                cls = sur_fallback_at(s_phi[lp], tile_e0(d), C) ? SG_SUR_FALLBACK : SG_SUR_NETWORK;
-            ++cnt[cls];
-            w[i] = cls == SG_SUR_TRIVIAL_IN ? 1.0f : 0.0f;
-            ax[i] = ay[i] = az[i] = 0.0f;
-            if (cls == SG_SUR_FALLBACK) {  // the exact sum exactly as mode 0 forms it
-                if (!integrals_saturated(s_sat[lp], w[i], ax[i], ay[i], az[i]))
-                    integrals_point(s_H[lp], d, K, w[i], ax[i], ay[i], az[i]);
-            } else if (cls == SG_SUR_NETWORK) {
-                net |= 1u << i;
+                    for (int sy = 0; sy < 3; ++sy) m &= tM[half][(j + sy) + 6 * (k + sz)];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int d = 4 * r + i;
+                    if (((m >> (8 + i)) & 7u) == 7u)
+                        cls[i] = SG_SUR_TRIVIAL_IN;
+                    else if (((m >> i) & 7u) == 7u)
+                        cls[i] = SG_SUR_TRIVIAL_OUT;
+                    else
+                        cls[i] = sur_fallback_at(tP[half], tile_e0(d), C) ? SG_SUR_FALLBACK : SG_SUR_NETWORK;
+                    fb |= (cls[i] == SG_SUR_FALLBACK ? 1u : 0u) << i;
+                    net |= (cls[i] == SG_SUR_NETWORK ? 1u : 0u) << i;
+                }
             }
+            float w[4], ax[4], ay[4], az[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                w[i] = cls[i] == SG_SUR_TRIVIAL_IN ? 1.0f : 0.0f;
+                ax[i] = ay[i] = az[i] = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) cnt[c] += cls[i] == c ? 1u : 0u;
+            }
+            if (fb) {  // the exact sums exactly as mode 0 forms them
+                float sw, sx, sy, sz;
+                if (integrals_saturated(bits[half], sw, sx, sy, sz)) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if ((fb >> i) & 1u) w[i] = sw, ax[i] = sx, ay[i] = sy, az[i] = sz;
+                } else {
+#pragma unroll
+                    for (int pp = 0; pp < 2; ++pp) {
+                        if (!((fb >> (2 * pp)) & 3u)) continue;
+                        float2 w2, x2, y2, z2;
+                        integrals_point2(tH[half], 4 * r + 2 * pp, K, w2, x2, y2, z2);
+                        if ((fb >> (2 * pp)) & 1u) w[2 * pp] = w2.x, ax[2 * pp] = x2.x, ay[2 * pp] = y2.x, az[2 * pp] = z2.x;
+                        if ((fb >> (2 * pp + 1)) & 1u)
+                            w[2 * pp + 1] = w2.y, ax[2 * pp + 1] = x2.y, ay[2 * pp + 1] = y2.y, az[2 * pp + 1] = z2.y;
+                    }
+                }
+            }
+            const int64_t q4 = pt0 >> 2;
+            reinterpret_cast<float4*>(W)[q4] = make_float4(w[0], w[1], w[2], w[3]);
+            reinterpret_cast<float4*>(gx)[q4] = make_float4(ax[0], ax[1], ax[2], ax[3]);
+            reinterpret_cast<float4*>(gy)[q4] = make_float4(ay[0], ay[1], ay[2], ay[3]);
+            reinterpret_cast<float4*>(gz)[q4] = make_float4(az[0], az[1], az[2], az[3]);
         }
-        reinterpret_cast<float4*>(W)[pt0 >> 2] = make_float4(w[0], w[1], w[2], w[3]);
-        reinterpret_cast<float4*>(gx)[pt0 >> 2] = make_float4(ax[0], ax[1], ax[2], ax[3]);
-        reinterpret_cast<float4*>(gy)[pt0 >> 2] = make_float4(ay[0], ay[1], ay[2], ay[3]);
-        reinterpret_cast<float4*>(gz)[pt0 >> 2] = make_float4(az[0], az[1], az[2], az[3]);
-    }
-    // class counts: one shared atomic per warp and class
+        // network points: one list reservation per warp
+        const unsigned c = __popc(net);
+        unsigned incl = c;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const unsigned v = __reduce_add_sync(0xffffffffu, cnt[k]);
-        if (lane == 0 && v) atomicAdd(&s_cnt[k], v);
-    }
-    // network points: one list reservation per warp
-    const unsigned c = __popc(net);
-    unsigned incl = c;
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total) {
+            unsigned base = 0;
+            if (lane == 31) base = atomicAdd(count, total);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            unsigned at = base + incl - c;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const unsigned v = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += v;
+            for (int i = 0; i < 4; ++i)
+                if ((net >> i) & 1u) list[at++] = (int32_t)(pt0 + i);
+        }
+        __syncwarp();  // the next pair's staging overwrites the tiles
     }
-    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned base = 0;
-    if (lane == 31 && total) base = atomicAdd(count, total);
-    base = __shfl_sync(0xffffffffu, base, 31);
-    unsigned at = base + incl - c;
+    // class counts: a shared atomic per warp and class, one global atomic per CTA and class
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-        if (net >> i & 1) list[at++] = (int32_t)(pt0 + i);
+    for (int c = 0; c < 4; ++c) {
+        const unsigned v = __reduce_add_sync(0xffffffffu, cnt[c]);
+        if (lane == 0 && v) atomicAdd(&s_cnt[c], v);
+    }
     __syncthreads();
     if (stats && threadIdx.x < 4 && s_cnt[threadIdx.x])
         atomicAdd(stats + threadIdx.x, (unsigned long long)s_cnt[threadIdx.x]);
+}
+
+// Persistent grid of pass A: the CTAs that fit on all SMs at once.
+template <bool BATCH>
+unsigned sur_a_grid(int64_t P, int device) {
+    static int per_sm = 0, sms = 0;  // per instantiation, on the first device asked (all alike here)
+    if (!sms) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sur_a<BATCH>, SA_WARPS * 32, 0) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    }
+    const int64_t pairs = (P - 2 + 1) / 2;
+    int64_t b = (int64_t)std::max(per_sm, 1) * std::max(sms, 1);
+    const int64_t need = (pairs + SA_WARPS - 1) / SA_WARPS;
+    if (b > need) b = need;
+    return (unsigned)std::max<int64_t>(b, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -1180,9 +1235,9 @@ cudaError_t launch_surrogate_integrals(sg_grid* g, const sg_mlp* m, void* work, 
     if ((e = cudaMemsetAsync(count, 0, sizeof(unsigned), g->stream)) != cudaSuccess) return e;
     const int32_t* nbr = (const int32_t*)g->nbr.p;
     const float* phi = (const float*)g->field[SG_FIELD_PHI].p;
-    k_sur_a<false><<<cdiv(g->P - 2, SA_PKGS), SA_THREADS, 0, g->stream>>>(
-        nbr, phi, W, gx, gy, gz, g->P, kernel_coef(), (float)(1.0 / g->desc.h), sur_const(g), nullptr, nullptr,
-        nullptr, list, count, (unsigned long long*)g->stats.p);
+    k_sur_a<false><<<sur_a_grid<false>(g->P, g->device), SA_WARPS * 32, 0, g->stream>>>(
+        nbr, phi, W, gx, gy, gz, g->P, kernel_coef(), sur_body(g->desc.h), nullptr, nullptr, nullptr, list, count,
+        (unsigned long long*)g->stats.p);
     if ((e = cudaFuncSetAttribute(k_sur_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SB_BYTES)) !=
         cudaSuccess)
         return e;
@@ -1214,8 +1269,8 @@ cudaError_t launch_batch_surrogate_integrals(const int32_t* nbr, const uint8_t* 
     int32_t* list = (int32_t*)((char*)work + 256);
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    k_sur_a<true><<<cdiv(P - 2, SA_PKGS), SA_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(), 0.0f,
-                                                              SurConst{}, type, body, sb, list, count, nullptr);
+    k_sur_a<true><<<sur_a_grid<true>(P, device), SA_WARPS * 32, 0, s>>>(
+        nbr, phi, W, gx, gy, gz, P, kernel_coef(), SurBody{}, type, body, sb, list, count, nullptr);
     k_sur_b<true><<<tc_grid((const void*)k_sur_b<true>, SB_BYTES, 64 * SB_GROUPS, device, 0, SB_GROUPS * TC_ROWS),
                     SB_GROUPS * TC_ROWS, SB_BYTES, s>>>(
         nbr, phi, W, gx, gy, gz, 0.0f, body, sb, list, count, m->packed, err);

@@ -36,6 +36,23 @@ __device__ __forceinline__ float silu_(float z) {
     return fmaf(h, tanh_approx(h), h);
 }
 
+// silu_(v + b) of two values at once on paired FP32 instructions (each lane
+// the same rounded operations as the scalar form, so the same bits)
+__device__ __forceinline__ float2 silu2_bias(float2 v, float2 b) {
+    const float2 h = __fmul2_rn(make_float2(0.5f, 0.5f), __fadd2_rn(v, b));
+    return __ffma2_rn(h, make_float2(tanh_approx(h.x), tanh_approx(h.y)), h);
+}
+
+// v[i] = silu_(v[i] + bias[i]) for 32 consecutive columns (bias 8-byte aligned)
+__device__ __forceinline__ void silu32_bias(float (&v)[32], const float* bias) {
+#pragma unroll
+    for (int i = 0; i < 32; i += 2) {
+        const float2 s = silu2_bias(make_float2(v[i], v[i + 1]), *reinterpret_cast<const float2*>(bias + i));
+        v[i] = s.x;
+        v[i + 1] = s.y;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Class decision (see SurConst): exact on the real values of the float phi.
 // ---------------------------------------------------------------------------
@@ -102,9 +119,10 @@ __device__ __forceinline__ int tile_e0(int d) { return ((d & 3) + 1) + TILE_Y * 
 //               canonical axis k is original axis perm_axis(perm, k)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int perm_axis(int perm, int k) {
-    // (0,1,2) (0,2,1) (1,0,2) (1,2,0) (2,0,1) (2,1,0), two bits per entry
-    constexpr uint32_t tab[6] = {0x24u, 0x18u, 0x21u, 0x09u, 0x12u, 0x06u};
-    return (int)((tab[perm] >> (2 * k)) & 3u);
+    // (0,1,2) (0,2,1) (1,0,2) (1,2,0) (2,0,1) (2,1,0): two bits per entry,
+    // six bits per permutation, in one register-held constant
+    constexpr uint64_t tab = 0x24ull | 0x18ull << 6 | 0x21ull << 12 | 0x09ull << 18 | 0x12ull << 24 | 0x06ull << 30;
+    return (int)((tab >> (6 * perm + 2 * k)) & 3u);
 }
 
 // Index of the permutation (p0, p1, 3 - p0 - p1).
@@ -139,11 +157,21 @@ __device__ __forceinline__ int canon_code(float c, float xp, float xm, float yp,
         if (flip) g[a] = ff_neg(g[a]);
         if (g[a].hi < 0.0f) rb |= 1 << a;
     }
-    // stable sort of the axes by decreasing |g| (equal magnitudes keep the lower axis first)
-    int p0 = 0, p1 = 1, p2 = 2, t;
-    if (ff_abs_gt(g[p1], g[p0])) t = p0, p0 = p1, p1 = t;
-    if (ff_abs_gt(g[p2], g[p1])) t = p1, p1 = p2, p2 = t;
-    if (ff_abs_gt(g[p1], g[p0])) t = p0, p0 = p1, p1 = t;
+    // stable sort of the axes by decreasing |g| (equal magnitudes keep the
+    // lower axis first), the values moving with their axes
+    ff ga = g[0], gb = g[1], gc = g[2];
+    int p0 = 0, p1 = 1, p2 = 2;
+    if (ff_abs_gt(gb, ga)) {
+        const ff u = ga; ga = gb; gb = u;
+        const int v = p0; p0 = p1; p1 = v;
+    }
+    if (ff_abs_gt(gc, gb)) {
+        const ff u = gb; gb = gc; gc = u;
+        const int v = p1; p1 = p2; p2 = v;
+    }
+    if (ff_abs_gt(gb, ga)) {
+        const int v = p0; p0 = p1; p1 = v;
+    }
     (void)p2;
     return (flip ? 1 : 0) | (rb << 1) | (perm_index(p0, p1) << 4);
 }
@@ -153,11 +181,14 @@ __device__ __forceinline__ void uncanon_outputs(int code, const float (&y)[4], f
     const bool flip = code & 1;
     const int rb = (code >> 1) & 7, perm = code >> 4;
     o[0] = flip ? __fsub_rn(1.0f, y[0]) : y[0];
+    // output axis b takes the canonical component k with perm_axis(perm, k)
+    // = b (selects, so that o stays in registers)
+    const int a0 = perm_axis(perm, 0), a1 = perm_axis(perm, 1);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int a = perm_axis(perm, k);
-        const bool neg = ((rb >> a) & 1) != flip;
-        o[1 + a] = neg ? -y[1 + k] : y[1 + k];
+    for (int b = 0; b < 3; ++b) {
+        const float v = a0 == b ? y[1] : (a1 == b ? y[2] : y[3]);
+        const bool neg = ((rb >> b) & 1) != flip;
+        o[1 + b] = neg ? -v : v;
     }
 }
 
