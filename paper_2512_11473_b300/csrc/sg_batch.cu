@@ -493,11 +493,16 @@ cudaError_t record_relax(sg_batch* b, const sg_relax& r, int64_t tiles, cudaStre
     cudaError_t e = launch_pack_probe(F, tab, b->P * PKG3, s);
     if (e != cudaSuccess) return e;
     const unsigned ctas = (unsigned)((tiles + RX_TILES - 1) / RX_TILES);
+    // the outputs kept are the last step's: the steps before it interpolate
+    // only what the move needs (phi and g) and write only the positions
+    const ProbeOut none{};
     for (int k = 0; k < r.steps; ++k) {
-        if (integ)
+        const bool last = k == r.steps - 1;
+        if (last && integ)
             k_batch_relax<8><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, o);
         else
-            k_batch_relax<4><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, o);
+            k_batch_relax<4><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z,
+                                                          last ? o : none);
         note_launch();
     }
     return cudaGetLastError();
