@@ -555,18 +555,21 @@ __global__ void __launch_bounds__(SA_WARPS * 32, SG_SA_MIN_CTAS)
     float(*tP)[TILE_N] = s_phi[warp];
     uint16_t(*tM)[36] = s_mask[warp];
     int(*tnb)[32] = s_nb[warp];
-    // staging rows of this lane: e = lane, lane + 32, lane + 64 (< 72): package e / 36, row e % 36
-    int r_pk[3], r_rr[3], r_nb[3], r_d0[3], r_e0[3];
+    // staging rows of this lane: e = lane, lane + 32, lane + 64 (< 72):
+    // package e / 36, row e % 36; each row's indices packed in one word
+    // (package + 1: 2 bits, row: 6, neighbour slot: 5, first element in the
+    // package: 6, tile offset: 8)
+    unsigned r_w[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const int e = lane + 32 * q, rr = e % 36;
         const int y = rr % 6 - 1, z = rr / 6 - 1;
         const int oy = ((y + 4) >> 2) - 1, oz = ((z + 4) >> 2) - 1;
-        r_pk[q] = e < 72 ? e / 36 : -1;
-        r_rr[q] = rr;
-        r_nb[q] = 3 * (oy + 1) + 9 * (oz + 1);
-        r_d0[q] = 4 * (y - 4 * oy) + 16 * (z - 4 * oz);
-        r_e0[q] = TILE_Y * (y + 1) + TILE_Z * (z + 1);
+        const unsigned pk1 = e < 72 ? (unsigned)(e / 36 + 1) : 0u;
+        const unsigned nbs = (unsigned)(3 * (oy + 1) + 9 * (oz + 1));
+        const unsigned d0 = (unsigned)(4 * (y - 4 * oy) + 16 * (z - 4 * oz));
+        const unsigned e0 = (unsigned)(TILE_Y * (y + 1) + TILE_Z * (z + 1));
+        r_w[q] = pk1 | (unsigned)rr << 2 | nbs << 8 | d0 << 13 | e0 << 19;
     }
     const int half = lane >> 4, r = lane & 15;
     const int j = r & 3, k = r >> 2;
@@ -605,16 +608,18 @@ __global__ void __launch_bounds__(SA_WARPS * 32, SG_SA_MIN_CTAS)
         unsigned bits[2] = {0u, 0u}, keep[2] = {3u, 3u};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            const int pk = r_pk[q];
+            const unsigned wq = r_w[q];
+            const int pk = (int)(wq & 3u) - 1, rr = (int)((wq >> 2) & 63u), nbs = (int)((wq >> 8) & 31u);
+            const int d0 = (int)((wq >> 13) & 63u), e0 = (int)(wq >> 19);
             if (pk < 0 || !((okm >> pk) & 1u)) continue;
             const int* nb = tnb[pk];
-            const float4 v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb[r_nb[q] + 1] * PKG3 + r_d0[q]));
-            const float vm = __ldg(phi + (int64_t)nb[r_nb[q]] * PKG3 + r_d0[q] + 3);
-            const float vp = __ldg(phi + (int64_t)nb[r_nb[q] + 2] * PKG3 + r_d0[q]);
+            const float4 v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb[nbs + 1] * PKG3 + d0));
+            const float vm = __ldg(phi + (int64_t)nb[nbs] * PKG3 + d0 + 3);
+            const float vp = __ldg(phi + (int64_t)nb[nbs + 2] * PKG3 + d0);
             const float f[6] = {vm, v.x, v.y, v.z, v.w, vp};
             const float ie = s_B[warp][pk].inv_eps, hu = s_B[warp][pk].C.h_up;
-            float* t = tH[pk] + r_e0[q];
-            float* tp = tP[pk] + r_e0[q];
+            float* t = tH[pk] + e0;
+            float* tp = tP[pk] + e0;
             unsigned b = 0, mo = 0, mi = 0;
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
@@ -625,7 +630,7 @@ __global__ void __launch_bounds__(SA_WARPS * 32, SG_SA_MIN_CTAS)
                 mo |= (f[i] >= hu ? 1u : 0u) << i;
                 mi |= (-f[i] >= hu ? 1u : 0u) << i;
             }
-            tM[pk][r_rr[q]] = (uint16_t)(mo | (mi << 8));
+            tM[pk][rr] = (uint16_t)(mo | (mi << 8));
             bits[pk] |= b;
             keep[pk] &= (mo == 0x3Fu ? 1u : 0u) | (mi == 0x3Fu ? 2u : 0u);
         }
@@ -638,41 +643,51 @@ __global__ void __launch_bounds__(SA_WARPS * 32, SG_SA_MIN_CTAS)
         const int64_t pt0 = (p0 + half) * PKG3 + 4 * r;
         if ((okm >> half) & 1u) {
             const unsigned triv = keep[half];
-            const SurConst C = s_B[warp][half].C;
-            unsigned fb = 0;
-            int cls[4];
+            // classes of the row's four points as bit masks (bit i: point i)
+            unsigned tin = 0, fb = 0;
             if (triv) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) cls[i] = (triv & 1u) ? SG_SUR_TRIVIAL_OUT : SG_SUR_TRIVIAL_IN;
+                tin = (triv & 2u) ? 0xFu : 0u;
             } else {
-                // the 27-tap trivial tests of the row's four points from the
-                // 3 x 3 tile rows around it: point x is trivially outside
-                // (inside) when bits x .. x + 2 of the AND of those masks are set
-                unsigned m = 0xFFFFu;
+                // the 27-tap trivial tests from the 3 x 3 tile rows around
+                // the row: point i is trivially outside (inside) when bits
+                // i .. i + 2 of the AND of those masks are set; |phi| < h at
+                // the point itself when neither bit i + 1 of its own row is
+                const SurConst C = s_B[warp][half].C;
+                unsigned m = 0xFFFFu, mc = 0;
 #pragma unroll
                 for (int sz = 0; sz < 3; ++sz)
 #pragma unroll
-                    for (int sy = 0; sy < 3; ++sy) m &= tM[half][(j + sy) + 6 * (k + sz)];
+                    for (int sy = 0; sy < 3; ++sy) {
+                        const unsigned v = tM[half][(j + sy) + 6 * (k + sz)];
+                        m &= v;
+                        if (sz == 1 && sy == 1) mc = v;
+                    }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const int d = 4 * r + i;
-                    if (((m >> (8 + i)) & 7u) == 7u)
-                        cls[i] = SG_SUR_TRIVIAL_IN;
-                    else if (((m >> i) & 7u) == 7u)
-                        cls[i] = SG_SUR_TRIVIAL_OUT;
-                    else
-                        cls[i] = sur_fallback_at(tP[half], tile_e0(d), C) ? SG_SUR_FALLBACK : SG_SUR_NETWORK;
-                    fb |= (cls[i] == SG_SUR_FALLBACK ? 1u : 0u) << i;
-                    net |= (cls[i] == SG_SUR_NETWORK ? 1u : 0u) << i;
+                    if (((m >> (8 + i)) & 7u) == 7u) {
+                        tin |= 1u << i;
+                    } else if (((m >> i) & 7u) != 7u) {
+                        const int e0 = tile_e0(4 * r + i);
+                        const float* tl = tP[half];
+                        const bool f = !((mc >> (i + 1)) & 0x101u) ||
+                                       curvature_exceeds(tl[e0 + 1], tl[e0 - 1], tl[e0 + TILE_Y], tl[e0 - TILE_Y],
+                                                         tl[e0 + TILE_Z], tl[e0 - TILE_Z], tl[e0], C);
+                        if (f)
+                            fb |= 1u << i;
+                        else
+                            net |= 1u << i;
+                    }
                 }
             }
+            cnt[SG_SUR_TRIVIAL_IN] += __popc(tin);
+            cnt[SG_SUR_TRIVIAL_OUT] += 4 - __popc(tin | fb | net);
+            cnt[SG_SUR_FALLBACK] += __popc(fb);
+            cnt[SG_SUR_NETWORK] += __popc(net);
             float w[4], ax[4], ay[4], az[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                w[i] = cls[i] == SG_SUR_TRIVIAL_IN ? 1.0f : 0.0f;
+                w[i] = (tin >> i) & 1u ? 1.0f : 0.0f;
                 ax[i] = ay[i] = az[i] = 0.0f;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) cnt[c] += cls[i] == c ? 1u : 0u;
             }
             if (fb) {  // the exact sums exactly as mode 0 forms them
                 float sw, sx, sy, sz;
