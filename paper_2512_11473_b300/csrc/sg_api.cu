@@ -594,7 +594,7 @@ sg_status sg_probe(sg_grid* g, int64_t n, const float* x, const float* y, const 
                 "probe sort");
         order = ord;
     }
-    SG_CUDA(g, launch_probe(G, (const int32_t*)g->cell_pkg.p, (const int32_t*)g->nbr.p, F, n, x, y, z, order, unsorted,
+    SG_CUDA(g, launch_probe(G, (const int32_t*)g->cell_pkg.p, (const int32_t*)g->nbr.p, F, g->P, n, x, y, z, order, unsorted,
                             O, g->stream),
             "probe");
     return SG_OK;

@@ -283,7 +283,7 @@ constexpr int RX_TILES = 16;     // consecutive tiles a CTA walks
 // the integrals) and move by -step h clip(phi / h, -1, 1) n.  A CTA owns one
 // tile of RX_THREADS consecutive particles of one body; its body is the last
 // whose first tile is at most blockIdx.x.
-template <int NF>
+template <int NF, bool OFF32>
 // A CTA walks RX_TILES consecutive 256-particle tiles (of one body or of
 // consecutive bodies), so that a warp's successive particles are near each
 // other in the Morton walk and hit the packages L1 holds.
@@ -310,7 +310,10 @@ __global__ void __launch_bounds__(RX_THREADS) k_batch_relax(const RelaxBody* __r
         const float pos[3] = {x[q], y[q], z[q]};
         const ProbeAt A = probe_locate(B.lat_c, B.lat_ih, B.dims, cells + B.cells, B.far_out, pos);
         float acc[8];
-        probe_interp_packed<NF>(nbr, tab, A, acc);
+        if (OFF32)
+            probe_interp_packed32<NF>(nbr, tab, A, acc);
+        else
+            probe_interp_packed<NF>(nbr, tab, A, acc);
         const float inv = probe_inv_norm(acc);
         const float n0 = acc[1] * inv, n1 = acc[2] * inv, n2 = acc[3] * inv;
         const float m = B.step_h * fminf(fmaxf(acc[0] * B.inv_h, -1.0f), 1.0f);
@@ -496,13 +499,20 @@ cudaError_t record_relax(sg_batch* b, const sg_relax& r, int64_t tiles, cudaStre
     // the outputs kept are the last step's: the steps before it interpolate
     // only what the move needs (phi and g) and write only the positions
     const ProbeOut none{};
+    const bool off32 = b->P < ((int64_t)1 << 21);  // table offsets in bytes fit 32 bits
     for (int k = 0; k < r.steps; ++k) {
         const bool last = k == r.steps - 1;
-        if (last && integ)
-            k_batch_relax<8><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, o);
-        else
-            k_batch_relax<4><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z,
-                                                          last ? o : none);
+        const ProbeOut& ok = last ? o : none;
+        if (last && integ) {
+            if (off32)
+                k_batch_relax<8, true><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, o);
+            else
+                k_batch_relax<8, false><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, o);
+        } else if (off32) {
+            k_batch_relax<4, true><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, ok);
+        } else {
+            k_batch_relax<4, false><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, ok);
+        }
         note_launch();
     }
     return cudaGetLastError();

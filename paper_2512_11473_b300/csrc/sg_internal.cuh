@@ -235,7 +235,7 @@ cudaError_t morton_sort(const GridF& G, int64_t n, const float* x, const float* 
 // fields.
 cudaError_t launch_pack_probe(const ProbeFields& F, float* tab, int64_t n_points, cudaStream_t s);
 cudaError_t launch_probe(const GridF& G, const int32_t* cell_pkg, const int32_t* nbr, const ProbeFields& F,
-                         int64_t n, const float* x, const float* y, const float* z, const int32_t* order,
+                         int64_t P, int64_t n, const float* x, const float* y, const float* z, const int32_t* order,
                          const int* unsorted, const ProbeOut& out, cudaStream_t s);
 
 }  // namespace sg

@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_pack_probe(ProbeFields F, float*
     }
 }
 
+template <bool OFF32>
 __global__ void __launch_bounds__(PR_THREADS) k_probe(GridF G, const int32_t* __restrict__ cell_pkg,
                                                        const int32_t* __restrict__ nbr, ProbeFields F, int64_t n,
                                                        const float* __restrict__ x, const float* __restrict__ y,
@@ -249,7 +250,10 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe(GridF G, const int32_t* __
         const float pos[3] = {__ldg(x + q), __ldg(y + q), __ldg(z + q)};
         const ProbeAt A = probe_locate(G.lat_c, G.lat_ih, G.dims, cell_pkg, 1, pos);
         float acc[8];
-        probe_interp<8>(nbr, F, A, acc);
+        if (OFF32)
+            probe_interp32<8>(nbr, F, A, acc);
+        else
+            probe_interp<8>(nbr, F, A, acc);
         const float inv = probe_inv_norm(acc);
         if (out.o[0]) out.o[0][q] = acc[0];
         if (out.o[1]) out.o[1][q] = acc[1] * inv;
@@ -375,13 +379,16 @@ cudaError_t launch_pack_probe(const ProbeFields& F, float* tab, int64_t n_points
 }
 
 cudaError_t launch_probe(const GridF& G, const int32_t* cell_pkg, const int32_t* nbr, const ProbeFields& F,
-                         int64_t n, const float* x, const float* y, const float* z, const int32_t* order,
+                         int64_t P, int64_t n, const float* x, const float* y, const float* z, const int32_t* order,
                          const int* unsorted, const ProbeOut& out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     // up to 148 x 128 CTAs, each a contiguous stretch of about 2.6k particles
     // at 50M (9,472 CTAs measured 2% slower on the torus)
     const int64_t ctas = std::min<int64_t>((n + PR_THREADS - 1) / PR_THREADS, 148 * 128);
-    k_probe<<<(unsigned)ctas, PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, unsorted, out);
+    if (P < ((int64_t)1 << 24))
+        k_probe<true><<<(unsigned)ctas, PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, unsorted, out);
+    else
+        k_probe<false><<<(unsigned)ctas, PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, unsorted, out);
     note_launch();
     return cudaGetLastError();
 }

@@ -92,6 +92,38 @@ __device__ __forceinline__ void probe_interp(const int32_t* __restrict__ nbr, co
     }
 }
 
+// probe_interp with 32-bit byte offsets (for stores of fewer than 2^24
+// packages): a corner's offset is formed once and each field's load adds it
+// to that field's base address, without 64-bit address arithmetic per load.
+// Same sums in the same order.
+template <int NF>
+__device__ __forceinline__ void probe_interp32(const int32_t* __restrict__ nbr, const ProbeFields& F, const ProbeAt& A,
+                                               float (&acc)[8]) {
+    const int32_t* nb = nbr + A.home * NB;
+    const uint32_t home = (uint32_t)A.home;
+    int up[3], lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        up[a] = A.l[a] == 3 ? 1 : 0;
+        lo[a] = A.l[a];
+        hi[a] = up[a] ? 0 : A.l[a] + 1;
+    }
+#pragma unroll
+    for (int f = 0; f < 8; ++f) acc[f] = 0.0f;
+#pragma unroll
+    for (int cr = 0; cr < 8; ++cr) {
+        const int a0 = cr & 1, a1 = (cr >> 1) & 1, a2 = (cr >> 2) & 1;
+        const float w = (a0 ? A.t[0] : 1.0f - A.t[0]) * (a1 ? A.t[1] : 1.0f - A.t[1]) * (a2 ? A.t[2] : 1.0f - A.t[2]);
+        const int slot = (a0 ? up[0] : 0) + 3 * (a1 ? up[1] : 0) + 9 * (a2 ? up[2] : 0);
+        const uint32_t pkg = slot == 0 ? home : (uint32_t)__ldg(nb + 13 + slot);
+        const uint32_t off =
+            4u * (pkg * PKG3 + (uint32_t)((a0 ? hi[0] : lo[0]) + PKG * (a1 ? hi[1] : lo[1]) + PKG * PKG * (a2 ? hi[2] : lo[2])));
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+            acc[f] = fmaf(w, __ldg(reinterpret_cast<const float*>(reinterpret_cast<const char*>(F.f[f]) + off)), acc[f]);
+    }
+}
+
 // The same interpolation from the packed probe table: package p holds its 8
 // fields one after the other, field f of data point d at tab[512 p + 64 f + d],
 // so the 8 loads of a corner share one address and differ by constant
@@ -117,6 +149,36 @@ __device__ __forceinline__ void probe_interp_packed(const int32_t* __restrict__ 
         const int64_t pkg = slot == 0 ? A.home : (int64_t)__ldg(nb + 13 + slot);
         const float* q = tab + pkg * (8 * PKG3) + (a0 ? hi[0] : lo[0]) + PKG * (a1 ? hi[1] : lo[1]) +
                          PKG * PKG * (a2 ? hi[2] : lo[2]);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) acc[f] = fmaf(w, __ldg(q + f * PKG3), acc[f]);
+    }
+}
+
+// probe_interp_packed with 32-bit byte offsets into the table (tables of
+// fewer than 2^21 packages).  Same sums in the same order.
+template <int NF>
+__device__ __forceinline__ void probe_interp_packed32(const int32_t* __restrict__ nbr, const float* __restrict__ tab,
+                                                      const ProbeAt& A, float (&acc)[8]) {
+    const int32_t* nb = nbr + A.home * NB;
+    const uint32_t home = (uint32_t)A.home;
+    int up[3], lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        up[a] = A.l[a] == 3 ? 1 : 0;
+        lo[a] = A.l[a];
+        hi[a] = up[a] ? 0 : A.l[a] + 1;
+    }
+#pragma unroll
+    for (int f = 0; f < 8; ++f) acc[f] = 0.0f;
+#pragma unroll
+    for (int cr = 0; cr < 8; ++cr) {
+        const int a0 = cr & 1, a1 = (cr >> 1) & 1, a2 = (cr >> 2) & 1;
+        const float w = (a0 ? A.t[0] : 1.0f - A.t[0]) * (a1 ? A.t[1] : 1.0f - A.t[1]) * (a2 ? A.t[2] : 1.0f - A.t[2]);
+        const int slot = (a0 ? up[0] : 0) + 3 * (a1 ? up[1] : 0) + 9 * (a2 ? up[2] : 0);
+        const uint32_t pkg = slot == 0 ? home : (uint32_t)__ldg(nb + 13 + slot);
+        const uint32_t off = 4u * (pkg * (8 * PKG3) + (uint32_t)((a0 ? hi[0] : lo[0]) + PKG * (a1 ? hi[1] : lo[1]) +
+                                                                 PKG * PKG * (a2 ? hi[2] : lo[2])));
+        const float* q = reinterpret_cast<const float*>(reinterpret_cast<const char*>(tab) + off);
 #pragma unroll
         for (int f = 0; f < NF; ++f) acc[f] = fmaf(w, __ldg(q + f * PKG3), acc[f]);
     }
