@@ -276,8 +276,9 @@ SG_API sg_status sg_reinit(sg_grid *g, int32_t iterations, float cfl);
  * tiles (a product that never completes within its bounded wait sets the
  * device error word: sg_status_sync returns SG_ERR_TIMEOUT).  The grid
  * keeps the list's buffer (4 bytes per data point) for later calls.
- * Errors: SG_ERR_INVALID for an unknown mode or a missing or extra network.
- * Requires phi. */
+ * Errors: SG_ERR_INVALID for an unknown mode or a missing or extra network;
+ * SG_ERR_CAPACITY for mode 1 on 2^24 or more packages (the surrogate path
+ * indexes points and gathers in 32 bits).  Requires phi. */
 SG_API sg_status sg_kernel_integrals(sg_grid *g, int32_t mode, const void *mlp);
 
 /* Particle probe ("Grid-Particle Coupling"): trilinear interpolation of phi,
@@ -350,7 +351,8 @@ SG_API sg_status sg_batch_reset(sg_batch *b);
  * graph on its first run and replayed afterwards.  Per body the results
  * equal those of the single-grid calls bit for bit.
  * Errors: SG_ERR_INVALID (bad plan), SG_ERR_CAPACITY (more than 1020
- * sweeps), SG_ERR_CUDA. */
+ * sweeps, or surrogate integrals on a store of 2^24 or more packages),
+ * SG_ERR_CUDA. */
 SG_API sg_status sg_batch_run(sg_batch *b, const sg_batch_plan *plan);
 
 /* Time runs of every (pkgs_per_item, depth) pair for the plan's sweeps
@@ -406,8 +408,8 @@ typedef struct {
  * API (the paper states the coupling; the batched relaxation is this
  * library's).
  * Errors: SG_ERR_INVALID (null arrays, bad offsets, bad plan, steps < 0),
- * SG_ERR_CAPACITY (2^31 or more particle tiles of 256), SG_ERR_OOM,
- * SG_ERR_CUDA. */
+ * SG_ERR_CAPACITY (2^31 or more particle tiles of 256; surrogate sweeps on a
+ * store of 2^24 or more packages), SG_ERR_OOM, SG_ERR_CUDA. */
 SG_API sg_status sg_batch_relax(sg_batch *b, const sg_batch_plan *plan, const sg_relax *r);
 
 /* ------------------------------------------------------------------------ */

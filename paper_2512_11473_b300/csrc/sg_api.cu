@@ -528,6 +528,8 @@ sg_status sg_kernel_integrals(sg_grid* g, int32_t mode, const void* mlp) {
     if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_kernel_integrals: phi not initialised");
     if (mode == 1 && !default_kernel(g->desc))
         return fail(g, SG_ERR_INVALID, "sg_kernel_integrals: the surrogate needs kernel support 2h and eps = h");
+    if (mode == 1 && g->P >= SUR_MAX_PACKAGES)
+        return fail(g, SG_ERR_CAPACITY, "sg_kernel_integrals: the surrogate takes fewer than 2^24 packages");
     DeviceGuard dg(g->device);
     float* o[4];
     for (int a = 0; a < 4; ++a)

@@ -701,6 +701,8 @@ sg_status sg_batch_reset(sg_batch* b) {
 sg_status sg_batch_run(sg_batch* b, const sg_batch_plan* plan) {
     if (!b || !plan) return SG_ERR_INVALID;
     if (!valid_plan(b, plan)) return b_fail(b, SG_ERR_INVALID, "sg_batch_run: bad plan");
+    if (plan->integrals_mode == 1 && b->P >= SUR_MAX_PACKAGES)
+        return b_fail(b, SG_ERR_CAPACITY, "sg_batch_run: the surrogate takes fewer than 2^24 packages");
     if ((size_t)plan->reinit_iterations + 4 > b->n_counters)
         return b_fail(b, SG_ERR_CAPACITY, "sg_batch_run: too many reinit iterations");
     cudaError_t e;
@@ -835,6 +837,8 @@ sg_status sg_batch_relax(sg_batch* b, const sg_batch_plan* plan, const sg_relax*
     if (tiles >= (1LL << 31)) return b_fail(b, SG_ERR_CAPACITY, "sg_batch_relax: too many particles");
     if (r->sweeps) {
         if (!valid_plan(b, plan)) return b_fail(b, SG_ERR_INVALID, "sg_batch_relax: bad plan");
+        if (plan->integrals_mode == 1 && b->P >= SUR_MAX_PACKAGES)
+            return b_fail(b, SG_ERR_CAPACITY, "sg_batch_relax: the surrogate takes fewer than 2^24 packages");
         if ((size_t)plan->reinit_iterations + 4 > b->n_counters)
             return b_fail(b, SG_ERR_CAPACITY, "sg_batch_relax: too many reinit iterations");
     }

@@ -194,6 +194,10 @@ cudaError_t launch_surrogate_integrals(sg_grid* g, const sg_mlp* m, void* work, 
 // |f| >= h_up, and |f| < h when |f| < h_up), and the curvature bound
 // 0.1 h of the fallback's Laplacian numerator, in float and float-float;
 // 1/eps of the Heaviside (eps = h).
+// The surrogate path indexes data points in 32 bits (list entries) and
+// gathers with 32-bit byte offsets: stores of at most 2^24 - 1 packages.
+constexpr int64_t SUR_MAX_PACKAGES = (int64_t)1 << 24;
+
 struct SurConst {
     float inv_h, h_up, kap_thr;
     ff kap_thr_ff;

@@ -786,8 +786,10 @@ __device__ __forceinline__ void gather27(const int32_t* __restrict__ nbr, const 
         const int ii = i + n % 3 - 1, jj = j + (n / 3) % 3 - 1, kk = k + n / 9 - 1;
         const int ox = ((ii + 4) >> 2) - 1, oy = ((jj + 4) >> 2) - 1, oz = ((kk + 4) >> 2) - 1;
         const int slot = 13 + ox + 3 * oy + 9 * oz;
-        const int64_t pk = slot == 13 ? p : (int64_t)__ldg(nbr + p * NB + slot);
-        f[n] = __ldg(phi + pk * PKG3 + (ii - 4 * ox) + PKG * (jj - 4 * oy) + PKG * PKG * (kk - 4 * oz));
+        const uint32_t pk = slot == 13 ? (uint32_t)p : (uint32_t)__ldg(nbr + p * NB + slot);
+        // 32-bit byte offsets: the store holds fewer than 2^24 packages (checked at launch)
+        const uint32_t off = 4u * (pk * PKG3 + (uint32_t)((ii - 4 * ox) + PKG * (jj - 4 * oy) + PKG * PKG * (kk - 4 * oz)));
+        f[n] = __ldg(reinterpret_cast<const float*>(reinterpret_cast<const char*>(phi) + off));
     }
 }
 

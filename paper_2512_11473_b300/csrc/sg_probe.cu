@@ -247,21 +247,36 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe(GridF G, const int32_t* __
     const int64_t r1 = min(n, (int64_t)blockIdx.x * per + per);
     for (int64_t r = (int64_t)blockIdx.x * per + threadIdx.x; r < r1; r += blockDim.x) {
         const int64_t q = use_order ? (int64_t)__ldg(order + r) : r;
-        const float pos[3] = {__ldg(x + q), __ldg(y + q), __ldg(z + q)};
-        const ProbeAt A = probe_locate(G.lat_c, G.lat_ih, G.dims, cell_pkg, 1, pos);
         float acc[8];
-        if (OFF32)
+        if (OFF32) {
+            // particle arrays of fewer than 2^30 entries: 32-bit byte offsets here too
+            const uint32_t qb = 4u * (uint32_t)q;
+            auto at = [qb](const float* a) { return reinterpret_cast<const float*>(reinterpret_cast<const char*>(a) + qb); };
+            auto st = [qb](float* a, float v) { *reinterpret_cast<float*>(reinterpret_cast<char*>(a) + qb) = v; };
+            const float pos[3] = {__ldg(at(x)), __ldg(at(y)), __ldg(at(z))};
+            const ProbeAt A = probe_locate(G.lat_c, G.lat_ih, G.dims, cell_pkg, 1, pos);
             probe_interp32<8>(nbr, F, A, acc);
-        else
-            probe_interp<8>(nbr, F, A, acc);
-        const float inv = probe_inv_norm(acc);
-        if (out.o[0]) out.o[0][q] = acc[0];
-        if (out.o[1]) out.o[1][q] = acc[1] * inv;
-        if (out.o[2]) out.o[2][q] = acc[2] * inv;
-        if (out.o[3]) out.o[3][q] = acc[3] * inv;
+            const float inv = probe_inv_norm(acc);
+            if (out.o[0]) st(out.o[0], acc[0]);
+            if (out.o[1]) st(out.o[1], acc[1] * inv);
+            if (out.o[2]) st(out.o[2], acc[2] * inv);
+            if (out.o[3]) st(out.o[3], acc[3] * inv);
 #pragma unroll
-        for (int f = 4; f < 8; ++f)
-            if (out.o[f]) out.o[f][q] = acc[f];
+            for (int f = 4; f < 8; ++f)
+                if (out.o[f]) st(out.o[f], acc[f]);
+        } else {
+            const float pos[3] = {__ldg(x + q), __ldg(y + q), __ldg(z + q)};
+            const ProbeAt A = probe_locate(G.lat_c, G.lat_ih, G.dims, cell_pkg, 1, pos);
+            probe_interp<8>(nbr, F, A, acc);
+            const float inv = probe_inv_norm(acc);
+            if (out.o[0]) out.o[0][q] = acc[0];
+            if (out.o[1]) out.o[1][q] = acc[1] * inv;
+            if (out.o[2]) out.o[2][q] = acc[2] * inv;
+            if (out.o[3]) out.o[3][q] = acc[3] * inv;
+#pragma unroll
+            for (int f = 4; f < 8; ++f)
+                if (out.o[f]) out.o[f][q] = acc[f];
+        }
     }
 }
 
@@ -385,7 +400,7 @@ cudaError_t launch_probe(const GridF& G, const int32_t* cell_pkg, const int32_t*
     // up to 148 x 128 CTAs, each a contiguous stretch of about 2.6k particles
     // at 50M (9,472 CTAs measured 2% slower on the torus)
     const int64_t ctas = std::min<int64_t>((n + PR_THREADS - 1) / PR_THREADS, 148 * 128);
-    if (P < ((int64_t)1 << 24))
+    if (P < ((int64_t)1 << 24) && n < ((int64_t)1 << 30))
         k_probe<true><<<(unsigned)ctas, PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, unsorted, out);
     else
         k_probe<false><<<(unsigned)ctas, PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, unsorted, out);
