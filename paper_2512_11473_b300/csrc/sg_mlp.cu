@@ -613,9 +613,11 @@ __global__ void __launch_bounds__(SA_WARPS * 32, SG_SA_MIN_CTAS)
             const int d0 = (int)((wq >> 13) & 63u), e0 = (int)(wq >> 19);
             if (pk < 0 || !((okm >> pk) & 1u)) continue;
             const int* nb = tnb[pk];
-            const float4 v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb[nbs + 1] * PKG3 + d0));
-            const float vm = __ldg(phi + (int64_t)nb[nbs] * PKG3 + d0 + 3);
-            const float vp = __ldg(phi + (int64_t)nb[nbs + 2] * PKG3 + d0);
+            // 32-bit byte offsets (stores of fewer than 2^24 packages)
+            const char* pb = reinterpret_cast<const char*>(phi) + 4u * (uint32_t)d0;
+            const float4 v = __ldg(reinterpret_cast<const float4*>(pb + 4u * PKG3 * (uint32_t)nb[nbs + 1]));
+            const float vm = __ldg(reinterpret_cast<const float*>(pb + 4u * (PKG3 * (uint32_t)nb[nbs] + 3u)));
+            const float vp = __ldg(reinterpret_cast<const float*>(pb + 4u * PKG3 * (uint32_t)nb[nbs + 2]));
             const float f[6] = {vm, v.x, v.y, v.z, v.w, vp};
             const float ie = s_B[warp][pk].inv_eps, hu = s_B[warp][pk].C.h_up;
             float* t = tH[pk] + e0;
@@ -707,11 +709,12 @@ __global__ void __launch_bounds__(SA_WARPS * 32, SG_SA_MIN_CTAS)
                     }
                 }
             }
-            const int64_t q4 = pt0 >> 2;
-            reinterpret_cast<float4*>(W)[q4] = make_float4(w[0], w[1], w[2], w[3]);
-            reinterpret_cast<float4*>(gx)[q4] = make_float4(ax[0], ax[1], ax[2], ax[3]);
-            reinterpret_cast<float4*>(gy)[q4] = make_float4(ay[0], ay[1], ay[2], ay[3]);
-            reinterpret_cast<float4*>(gz)[q4] = make_float4(az[0], az[1], az[2], az[3]);
+            const uint32_t ob = 4u * (uint32_t)pt0;
+            auto row = [ob](float* a) { return reinterpret_cast<float4*>(reinterpret_cast<char*>(a) + ob); };
+            *row(W) = make_float4(w[0], w[1], w[2], w[3]);
+            *row(gx) = make_float4(ax[0], ax[1], ax[2], ax[3]);
+            *row(gy) = make_float4(ay[0], ay[1], ay[2], ay[3]);
+            *row(gz) = make_float4(az[0], az[1], az[2], az[3]);
         }
         // network points: one list reservation per warp
         const unsigned c = __popc(net);
