@@ -81,6 +81,7 @@ constexpr int IW_ROWS = 72;  // staged rows per package pair
 #define SG_IW_MIN_CTAS 4
 #endif
 
+template <bool OFF32>
 __global__ void __launch_bounds__(IW_WARPS * 32, SG_IW_MIN_CTAS) k_kernel_integrals(const int32_t* __restrict__ nbr,
                                                                      const float* __restrict__ phi,
                                                                      float* __restrict__ W, float* __restrict__ gx,
@@ -136,9 +137,18 @@ __global__ void __launch_bounds__(IW_WARPS * 32, SG_IW_MIN_CTAS) k_kernel_integr
             const int pk = r_pk[q];
             if (pk < 0 || (pk == 1 && !two)) continue;
             const int* nb = tnb[pk];
-            const float4 v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb[r_nb[q] + 1] * PKG3 + r_d0[q]));
-            const float vm = __ldg(phi + (int64_t)nb[r_nb[q]] * PKG3 + r_d0[q] + 3);
-            const float vp = __ldg(phi + (int64_t)nb[r_nb[q] + 2] * PKG3 + r_d0[q]);
+            float4 v;
+            float vm, vp;
+            if (OFF32) {  // 32-bit byte offsets (stores of fewer than 2^24 packages)
+                const char* pb = reinterpret_cast<const char*>(phi) + 4u * (uint32_t)r_d0[q];
+                v = __ldg(reinterpret_cast<const float4*>(pb + 4u * PKG3 * (uint32_t)nb[r_nb[q] + 1]));
+                vm = __ldg(reinterpret_cast<const float*>(pb + 4u * (PKG3 * (uint32_t)nb[r_nb[q]] + 3u)));
+                vp = __ldg(reinterpret_cast<const float*>(pb + 4u * PKG3 * (uint32_t)nb[r_nb[q] + 2]));
+            } else {
+                v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb[r_nb[q] + 1] * PKG3 + r_d0[q]));
+                vm = __ldg(phi + (int64_t)nb[r_nb[q]] * PKG3 + r_d0[q] + 3);
+                vp = __ldg(phi + (int64_t)nb[r_nb[q] + 2] * PKG3 + r_d0[q]);
+            }
             const float f[6] = {vm, v.x, v.y, v.z, v.w, vp};
             float* t = tH[pk] + r_e0[q];
             unsigned b = 0;
@@ -170,11 +180,20 @@ __global__ void __launch_bounds__(IW_WARPS * 32, SG_IW_MIN_CTAS) k_kernel_integr
 #pragma unroll
                 for (int i = 1; i < 4; ++i) w[i] = w[0], ax[i] = ax[0], ay[i] = ay[0], az[i] = az[0];
             }
-            const int64_t q4 = p * 16 + r;
-            reinterpret_cast<float4*>(W)[q4] = make_float4(w[0], w[1], w[2], w[3]);
-            reinterpret_cast<float4*>(gx)[q4] = make_float4(ax[0], ax[1], ax[2], ax[3]);
-            reinterpret_cast<float4*>(gy)[q4] = make_float4(ay[0], ay[1], ay[2], ay[3]);
-            reinterpret_cast<float4*>(gz)[q4] = make_float4(az[0], az[1], az[2], az[3]);
+            if (OFF32) {
+                const uint32_t ob = 16u * (uint32_t)(p * 16 + r);
+                auto row = [ob](float* a) { return reinterpret_cast<float4*>(reinterpret_cast<char*>(a) + ob); };
+                *row(W) = make_float4(w[0], w[1], w[2], w[3]);
+                *row(gx) = make_float4(ax[0], ax[1], ax[2], ax[3]);
+                *row(gy) = make_float4(ay[0], ay[1], ay[2], ay[3]);
+                *row(gz) = make_float4(az[0], az[1], az[2], az[3]);
+            } else {
+                const int64_t q4 = p * 16 + r;
+                reinterpret_cast<float4*>(W)[q4] = make_float4(w[0], w[1], w[2], w[3]);
+                reinterpret_cast<float4*>(gx)[q4] = make_float4(ax[0], ax[1], ax[2], ax[3]);
+                reinterpret_cast<float4*>(gy)[q4] = make_float4(ay[0], ay[1], ay[2], ay[3]);
+                reinterpret_cast<float4*>(gz)[q4] = make_float4(az[0], az[1], az[2], az[3]);
+            }
         }
         __syncwarp();  // the next pair's staging overwrites the tiles
     }
@@ -296,7 +315,7 @@ unsigned integrals_grid(int64_t P) {
     if (!sms) {
         int dev = 0;
         cudaGetDevice(&dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kernel_integrals, IW_WARPS * 32, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kernel_integrals<true>, IW_WARPS * 32, 0) !=
                 cudaSuccess ||
             per_sm < 1) {
             cudaGetLastError();
@@ -323,9 +342,12 @@ cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const fl
     if (R > 2.0)
         k_kernel_integrals_wide<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(R),
                                                                       (float)(1.0 / eps));
+    else if (P < ((int64_t)1 << 24))  // byte offsets of every field fit 32 bits
+        k_kernel_integrals<true><<<integrals_grid(P), IW_WARPS * 32, 0, s>>>(nbr, phi, W, gx, gy, gz, P,
+                                                                             kernel_coef(R), (float)(1.0 / eps));
     else
-        k_kernel_integrals<<<integrals_grid(P), IW_WARPS * 32, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(R),
-                                                                       (float)(1.0 / eps));
+        k_kernel_integrals<false><<<integrals_grid(P), IW_WARPS * 32, 0, s>>>(nbr, phi, W, gx, gy, gz, P,
+                                                                              kernel_coef(R), (float)(1.0 / eps));
     note_launch();
     return cudaGetLastError();
 }
