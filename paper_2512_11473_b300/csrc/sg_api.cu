@@ -269,7 +269,9 @@ static sg_status tag_common(sg_grid* g, Flags flags, int64_t* n_packages) {
     SG_CUDA(g, flags(ct, core), "tag flags");
     SG_CUDA(g, launch_tag_inner(G, ct, core, act, count, nc, g->stream), "tag inner");
     SG_CUDA(g, exclusive_scan_u32(count, count, nw, total, scan_scratch, g->stream), "tag scan");
-    SG_CUDA(g, cudaMemcpyAsync(g->host_pin.p, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream), "tag count");
+    // the package count and, 128 bytes on, the multi-resolution evaluation
+    // counter (when the flags kernel kept one): one read-back for both
+    SG_CUDA(g, cudaMemcpyAsync(g->host_pin.p, total, 136, cudaMemcpyDeviceToHost, g->stream), "tag count");
     SG_CUDA(g, cudaStreamSynchronize(g->stream), "tag sync");
     const int64_t P = 2 + (int64_t)*(uint32_t*)g->host_pin.p;
     if (P >= (1LL << 31) / NB) return fail(g, SG_ERR_CAPACITY, "sg_tag_allocate: too many packages");
@@ -366,13 +368,8 @@ sg_status sg_tag_allocate_from(sg_grid* g, const sg_grid* coarse, const sg_shape
         },
         n_packages);
     if (st != SG_OK) return st;
-    if (evaluated) {
-        SG_CUDA(g, cudaMemcpyAsync((char*)g->host_pin.p + 128, ev, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                                   g->stream),
-                "tag counter");
-        SG_CUDA(g, cudaStreamSynchronize(g->stream), "tag counter");
-        *evaluated = (int64_t)*(unsigned long long*)((char*)g->host_pin.p + 128);
-    }
+    // read back with the package count (tag_common)
+    if (evaluated) *evaluated = (int64_t)*(unsigned long long*)((char*)g->host_pin.p + 128);
     return SG_OK;
 }
 
