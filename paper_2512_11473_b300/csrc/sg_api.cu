@@ -4,7 +4,9 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "sg_internal.cuh"
 
@@ -172,6 +174,59 @@ const char* sg_version(void) { return "libsg 0.1 (sm_103a)"; }
 
 int64_t sg_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+namespace {
+
+// The 256-byte pinned read-back word of a grid comes from one process-wide
+// pinned block of PIN_SLOTS slots (portable to every device), taken on first
+// use and kept until exit, so that creating a grid page-locks nothing (a
+// stack of multi-resolution layers creates one grid per layer); past
+// PIN_SLOTS live grids each takes its own.
+constexpr int PIN_SLOTS = 256;
+std::mutex g_pin_mu;
+unsigned char* g_pin_block = nullptr;
+bool g_pin_tried = false;
+std::vector<int> g_pin_free;
+
+void* pin_get(bool* pooled) {
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        if (!g_pin_tried) {
+            g_pin_tried = true;
+            if (cudaHostAlloc((void**)&g_pin_block, (size_t)PIN_SLOTS * 256, cudaHostAllocPortable) == cudaSuccess) {
+                for (int i = PIN_SLOTS - 1; i >= 0; --i) g_pin_free.push_back(i);
+            } else {
+                cudaGetLastError();
+                g_pin_block = nullptr;
+            }
+        }
+        if (!g_pin_free.empty()) {
+            const int i = g_pin_free.back();
+            g_pin_free.pop_back();
+            *pooled = true;
+            return g_pin_block + (size_t)i * 256;
+        }
+    }
+    *pooled = false;
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, 256, cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void pin_put(void* p, bool pooled) {
+    if (!p) return;
+    if (!pooled) {
+        cudaFreeHost(p);
+        return;
+    }
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back((int)(((unsigned char*)p - g_pin_block) / 256));
+}
+
+}  // namespace
+
 sg_status sg_create(const sg_grid_desc* desc, const sg_allocator* alloc, void* stream, sg_grid** out) {
     if (!desc || !out) return SG_ERR_INVALID;
     *out = nullptr;
@@ -209,7 +264,7 @@ sg_status sg_create(const sg_grid_desc* desc, const sg_allocator* alloc, void* s
         return SG_ERR_OOM;
     }
     if (cudaMemsetAsync(g->err.p, 0, 256, g->stream) != cudaSuccess ||
-        cudaMallocHost(&g->host_pin.p, 256) != cudaSuccess) {
+        !(g->host_pin.p = pin_get(&g->host_pin_pooled))) {
         cudaGetLastError();
         grid_free(g, g->err);
         delete g;
@@ -227,7 +282,10 @@ sg_status sg_destroy(sg_grid* g) {
                    &g->phi_tmp,  &g->err,       &g->scratch,  &g->stats,    &g->sur_work};
     for (Buf* b : bufs) grid_free(g, *b);
     for (int f = 0; f < SG_N_FLOAT_FIELDS; ++f) grid_free(g, g->field[f]);
-    if (g->host_pin.p) cudaFreeHost(g->host_pin.p);
+    // every read-back into the pinned word is waited for when it is issued;
+    // the wait here only makes the slot's reuse independent of that
+    if (g->host_pin.p && cudaStreamSynchronize(g->stream) != cudaSuccess) cudaGetLastError();
+    pin_put(g->host_pin.p, g->host_pin_pooled);
     delete g;
     return SG_OK;
 }

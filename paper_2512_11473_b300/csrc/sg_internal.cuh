@@ -80,6 +80,7 @@ struct sg_grid {
     sg::Buf stats;     // class counts of the last surrogate integral call
     sg::Buf sur_work;  // list of network points of the surrogate integrals
     sg::Buf host_pin;  // pinned host word for read-backs
+    bool host_pin_pooled = false;  // a slot of the process-wide pinned block (sg_api.cu)
     std::string last_error;
 };
 
