@@ -242,6 +242,14 @@ SG_API sg_status sg_debug_consistency(sg_grid *g, float trust, int32_t flags, in
 /* sg_debug_consistency with SG_DEBUG_CC_ABSENT_POINTS | SG_DEBUG_CC_ABSENT_CELLS. */
 SG_API sg_status sg_debug_consistency_absent_cta(sg_grid *g, float trust);
 
+/* Testing hook, process-wide: with on != 0 the probe, the exact kernel
+ * integrals and the relaxation steps recorded afterwards take their 64-bit
+ * address kernels, which otherwise serve only stores too large for 32-bit
+ * byte offsets (2^24 packages and more for the probe and the integrals,
+ * 2^21 for the relaxation's table, 2^30 particles for the probe).  Results
+ * are the same bit for bit either way. */
+SG_API void sg_debug_wide_offsets(int32_t on);
+
 /* The "sequential" benchmark of "Performance Evaluation": a small change to
  * every active value, phi <- phi + delta on every active package (far
  * packages untouched).  Requires phi. */

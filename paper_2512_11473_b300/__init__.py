@@ -94,6 +94,8 @@ def lib():
         L.sg_sequential_update.argtypes = [vp, C.c_float]
         L.sg_consistency_correct.argtypes = [vp, C.c_float, C.POINTER(i64)]
         L.sg_debug_consistency_absent_cta.argtypes = [vp, C.c_float]
+        L.sg_debug_wide_offsets.argtypes = [C.c_int32]
+        L.sg_debug_wide_offsets.restype = None
         L.sg_debug_consistency.argtypes = [vp, C.c_float, C.c_int32, C.POINTER(i64)]
         L.sg_tag_allocate_from.argtypes = [vp, vp, C.POINTER(sg_shape), C.POINTER(i64), C.POINTER(i64)]
         L.sg_multires_layers.argtypes = [C.POINTER(sg_grid_desc), i32]
@@ -716,3 +718,10 @@ def version() -> str:
 def kernel_launch_count() -> int:
     """Kernels launched by libsg in this process so far."""
     return int(lib().sg_kernel_launch_count())
+
+
+def debug_wide_offsets(on: bool) -> None:
+    """Testing hook (process-wide): take the 64-bit address kernels of the
+    probe, the exact integrals and the relaxation at any store size (see
+    sg_debug_wide_offsets); results are bitwise the same."""
+    lib().sg_debug_wide_offsets(1 if on else 0)

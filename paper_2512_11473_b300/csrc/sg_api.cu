@@ -15,6 +15,7 @@ namespace sg {
 namespace {
 
 std::atomic<int64_t> g_launches{0};
+std::atomic<bool> g_wide_offsets{false};
 
 struct DeviceGuard {
     int prev = -1;
@@ -32,6 +33,8 @@ ff split(double v) { return split_ff(v); }
 }  // namespace
 
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+bool force_wide_offsets() { return g_wide_offsets.load(std::memory_order_relaxed); }
 
 void* grid_alloc(sg_grid* g, size_t bytes) {
     if (bytes == 0) bytes = 256;
@@ -510,6 +513,8 @@ sg_status sg_debug_consistency(sg_grid* g, float trust, int32_t flags, int64_t* 
         return fail(g, SG_ERR_DEVICE, "sg_debug_consistency: no cooperative launch on this device");
     return consistency(g, trust, out, (unsigned)flags);
 }
+
+void sg_debug_wide_offsets(int32_t on) { g_wide_offsets.store(on != 0, std::memory_order_relaxed); }
 
 sg_status sg_debug_consistency_absent_cta(sg_grid* g, float trust) {
     return sg_debug_consistency(g, trust, SG_DEBUG_CC_ABSENT_POINTS | SG_DEBUG_CC_ABSENT_CELLS, nullptr);

@@ -499,7 +499,7 @@ cudaError_t record_relax(sg_batch* b, const sg_relax& r, int64_t tiles, cudaStre
     // the outputs kept are the last step's: the steps before it interpolate
     // only what the move needs (phi and g) and write only the positions
     const ProbeOut none{};
-    const bool off32 = b->P < ((int64_t)1 << 21);  // table offsets in bytes fit 32 bits
+    const bool off32 = b->P < ((int64_t)1 << 21) && !force_wide_offsets();  // table offsets in bytes fit 32 bits
     for (int k = 0; k < r.steps; ++k) {
         const bool last = k == r.steps - 1;
         const ProbeOut& ok = last ? o : none;

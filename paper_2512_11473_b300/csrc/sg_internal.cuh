@@ -95,6 +95,8 @@ __device__ __forceinline__ void write_far(float* f, float v_in, float v_out) {
 
 // process-wide count of kernels launched by the library (sg_api.cu)
 void note_launch(int n = 1);
+// sg_debug_wide_offsets: take the 64-bit address kernels at any size (sg_api.cu)
+bool force_wide_offsets();
 
 // memory (sg_api.cu)
 void* grid_alloc(sg_grid* g, size_t bytes);

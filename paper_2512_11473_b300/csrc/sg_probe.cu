@@ -400,7 +400,7 @@ cudaError_t launch_probe(const GridF& G, const int32_t* cell_pkg, const int32_t*
     // up to 148 x 128 CTAs, each a contiguous stretch of about 2.6k particles
     // at 50M (9,472 CTAs measured 2% slower on the torus)
     const int64_t ctas = std::min<int64_t>((n + PR_THREADS - 1) / PR_THREADS, 148 * 128);
-    if (P < ((int64_t)1 << 24) && n < ((int64_t)1 << 30))
+    if (P < ((int64_t)1 << 24) && n < ((int64_t)1 << 30) && !force_wide_offsets())
         k_probe<true><<<(unsigned)ctas, PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, unsorted, out);
     else
         k_probe<false><<<(unsigned)ctas, PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, unsorted, out);

@@ -342,7 +342,7 @@ cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const fl
     if (R > 2.0)
         k_kernel_integrals_wide<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(R),
                                                                       (float)(1.0 / eps));
-    else if (P < ((int64_t)1 << 24))  // byte offsets of every field fit 32 bits
+    else if (P < ((int64_t)1 << 24) && !force_wide_offsets())  // byte offsets of every field fit 32 bits
         k_kernel_integrals<true><<<integrals_grid(P), IW_WARPS * 32, 0, s>>>(nbr, phi, W, gx, gy, gz, P,
                                                                              kernel_coef(R), (float)(1.0 / eps));
     else
