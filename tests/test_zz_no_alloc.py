@@ -137,3 +137,29 @@ def test_noalloc_wrapper_rejects_bad_arrays(sg):
                                           None, C.c_void_p(o.data_ptr()),
                                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == sg.SG_ERR_INVALID
+
+
+def test_noalloc_records_into_a_graph(sg):
+    """A call recorded in a CUDA graph in global capture mode (where an
+    allocation or a synchronisation by the library would end the capture
+    with an error) and replayed gives the regular entry point's result."""
+    shape = si.torus(0.6, 0.2)
+    spec = si.GridSpec((-1.0, -1.0, -0.4), (50, 50, 20), 0.01)
+    x, y, z = si.box_particles(50_000, spec.lo, spec.hi(), seed=34)
+    X, Y, Z = (torch.from_numpy(v).cuda() for v in (x, y, z))
+    _noalloc_raw(sg, spec, X, Y, Z)  # the device's first call loads the scratch array
+    n = X.numel()
+    keys = torch.full((n,), -1, dtype=torch.int64, device="cuda")
+    order = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    desc = sg._desc(spec)
+    args = [C.c_void_p(t.data_ptr()) for t in (X, Y, Z, keys, order)]
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, capture_error_mode="global"):
+        st = sg.lib().sg_morton_order_noalloc(C.byref(desc), n, *args,
+                                              C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == sg.SG_OK
+    graph.replay()
+    torch.cuda.synchronize()
+    rk, ro = _regular(sg, spec, shape, X, Y, Z)
+    assert torch.equal(keys.cpu(), rk) and torch.equal(order.cpu(), ro)
