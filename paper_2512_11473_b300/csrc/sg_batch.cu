@@ -277,6 +277,10 @@ struct RelaxBody {
 };
 
 constexpr int RX_THREADS = 256;  // particles per tile
+// bounded to 40 registers, six CTAs per SM, without spills (the gathers'
+// latency wants the warps: 10^8-particle step 1.61 ms at 48 registers and
+// five CTAs, 1.57 ms here)
+constexpr int RX_MIN_CTAS = 6;
 constexpr int RX_TILES = 16;     // consecutive tiles a CTA walks
 
 // One relaxation step for every particle: probe (phi, g and, with NF = 8,
@@ -287,7 +291,7 @@ template <int NF, bool OFF32>
 // A CTA walks RX_TILES consecutive 256-particle tiles (of one body or of
 // consecutive bodies), so that a warp's successive particles are near each
 // other in the Morton walk and hit the packages L1 holds.
-__global__ void __launch_bounds__(RX_THREADS) k_batch_relax(const RelaxBody* __restrict__ rb, int nbody,
+__global__ void __launch_bounds__(RX_THREADS, RX_MIN_CTAS) k_batch_relax(const RelaxBody* __restrict__ rb, int nbody,
                                                             int64_t tiles, const int32_t* __restrict__ cells,
                                                             const int32_t* __restrict__ nbr,
                                                             const float* __restrict__ tab,
