@@ -118,3 +118,31 @@ def test_full_probe_50m_sampled(body, sg):
     for k, name_ in enumerate(("nx", "ny", "nz")):
         assert np.max(np.abs(got[name_][strong] - ref[1 + k][strong])) <= 1e-5
     g.sync()
+
+
+def test_full_surrogate_classes(body, sg):
+    """Surrogate integrals at full size (random weights: the classes and the
+    fallback do not depend on them): pass A's class counts equal the
+    classification kernel's, the classes equal the oracle's FP64 definition
+    with no point within 1e-9 of a threshold, fallback points carry the
+    exact sums bit for bit and trivial points the exact constants."""
+    name, shape, spec, g, P, O = body
+    g.init_sdf(shape)
+    g.reinit(50, 0.5)
+    g.kernel_integrals()
+    exact = {f: g.field(f).clone() for f in ("W", "Gx", "Gy", "Gz")}
+    net = sg.MLP(si.mlp_init_params(16))
+    g.kernel_integrals(mode=1, mlp=net)
+    cls = g.surrogate_classify()
+    assert g.surrogate_stats() == [int((cls[2:] == c).sum()) for c in range(4)]
+    ref, ties = oracle.surrogate_class(spec, O.nbr, H(g.field("phi")), ties=True)
+    assert ties == 0
+    assert np.array_equal(H(cls), ref)
+    fb = cls == 2
+    for f in exact:
+        assert torch.equal(g.field(f)[fb], exact[f][fb]), f
+    tin, tout = cls == 0, cls == 1
+    assert bool((g.field("W")[tin] == 1).all()) and bool((g.field("W")[tout] == 0).all())
+    for f in ("Gx", "Gy", "Gz"):
+        assert bool((g.field(f)[tin | tout] == 0).all()), f
+    net.close()
