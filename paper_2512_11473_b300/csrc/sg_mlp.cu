@@ -773,8 +773,8 @@ unsigned sur_a_grid(int64_t P, int device) {
 // weights, measured 347 against 334 us for one on the h = 0.002 torus (at
 // the 64 registers that four CTAs of two groups allow, the kernel spills)
 constexpr int SB_GROUPS = 1;
-constexpr int SB_POS = PK_FWD_BYTES;                   // canonical input positions [6][27] bytes (see canon_row)
-constexpr int SB_T = SB_POS + 256;                     // tile operands, one per group
+constexpr int SB_POS = PK_FWD_BYTES;                   // canonical input columns [6][27] (see canon_row)
+constexpr int SB_T = SB_POS + 384;                     // tile operands, one per group
 constexpr int SB_BYTES = SB_T + SB_GROUPS * TC_ROWS * MLP_H * 2;
 static_assert(SB_T % 128 == 0, "tile alignment");
 
@@ -799,14 +799,17 @@ __device__ __forceinline__ void gather27(const int32_t* __restrict__ nbr, const 
 // Canonical input row of a point into the tile operand T (row r); returns
 // the transform code.
 // The reflections are applied to the input index (digit d -> 2 - d on a
-// reversed axis) and only the six permutations are tabled, pos6[perm][n] =
-// canon_pos(n, 0, perm): 162 bytes of shared memory instead of 1296, which
-// lets a seventh CTA onto each SM.
-__device__ __forceinline__ int canon_row(const float (&f)[MLP_IN], float inv_h, const uint8_t* pos6, unsigned char* T,
+// reversed axis) and only the six permutations are tabled, as the K-major
+// byte offset of the canonical column, col6[perm][n] = kmajor_byte(0,
+// canon_pos(n, 0, perm), K1): 324 bytes of shared memory instead of the 1296
+// of all 48 transforms, which lets a seventh CTA onto each SM.
+static_assert(!MLP_SPLIT, "canon_row writes the inputs' BF16 values only");
+__device__ __forceinline__ int canon_row(const float (&f)[MLP_IN], float inv_h, const uint16_t* col6, unsigned char* T,
                                          int r) {
     const int code = canon_code(f[13], f[14], f[12], f[16], f[10], f[22], f[4]);
     const float sgn = (code & 1) ? -1.0f : 1.0f;
-    const uint8_t* ps = pos6 + (code >> 4) * MLP_IN;
+    const uint16_t* ps = col6 + (code >> 4) * MLP_IN;
+    unsigned char* Tr = T + umma::kmajor_byte(r, 0, MLP_K1);
     const int fx = (code >> 1) & 1, fy = (code >> 2) & 1, fz = (code >> 3) & 1;
 #pragma unroll
     for (int c = MLP_SPLIT ? 2 * MLP_IN : MLP_IN; c < MLP_K1; ++c) put_bf16(T, umma::kmajor_byte(r, c, MLP_K1), 0.0f);
@@ -814,19 +817,16 @@ __device__ __forceinline__ int canon_row(const float (&f)[MLP_IN], float inv_h, 
     for (int n = 0; n < MLP_IN; ++n) {
         const float v = fminf(fmaxf(__fmul_rn(sgn * f[n], inv_h), -1.0f), 1.0f);
         const int m = n + fx * (2 - 2 * (n % 3)) + fy * 3 * (2 - 2 * ((n / 3) % 3)) + fz * 9 * (2 - 2 * (n / 9));
-        const int c = ps[m];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        *reinterpret_cast<__nv_bfloat16*>(T + umma::kmajor_byte(r, c, MLP_K1)) = hi;
-        if (MLP_SPLIT) put_bf16(T, umma::kmajor_byte(r, MLP_IN + c, MLP_K1), v - __bfloat162float(hi));
+        *reinterpret_cast<__nv_bfloat16*>(Tr + ps[m]) = __float2bfloat16_rn(v);
     }
     return code;
 }
 
-// Canonical positions of the 27 inputs under the six permutations alone:
-// pos6[perm * 27 + n].
-__device__ __forceinline__ void build_pos6(uint8_t* pos6) {
+// K-major byte offsets of the canonical columns of the 27 inputs under the
+// six permutations alone: col6[perm * 27 + n].
+__device__ __forceinline__ void build_col6(uint16_t* col6) {
     for (int e = threadIdx.x; e < 6 * MLP_IN; e += blockDim.x)
-        pos6[e] = (uint8_t)canon_pos(e % MLP_IN, 0, e / MLP_IN);
+        col6[e] = (uint16_t)umma::kmajor_byte(0, canon_pos(e % MLP_IN, 0, e / MLP_IN), MLP_K1);
 }
 
 // Canonical positions of the 27 inputs under each of the 48 (reflection,
@@ -855,8 +855,8 @@ __global__ void __launch_bounds__(SB_GROUPS * TC_ROWS) k_sur_b(const int32_t* __
     __shared__ __align__(8) uint64_t bars[SB_GROUPS];
     __shared__ uint32_t slot;
     stage_bytes(smem, packed, PK_FWD_BYTES);
-    uint8_t* pos = smem + SB_POS;
-    build_pos6(pos);
+    uint16_t* pos = reinterpret_cast<uint16_t*>(smem + SB_POS);
+    build_col6(pos);
     Tc t = tc_begin(bars, &slot, 64 * SB_GROUPS, SB_GROUPS > 1 ? SB_GROUPS : 0);  // one group: the whole CTA
     const uint32_t tbase = slot;
     unsigned char* T = smem + SB_T + (t.group > 0 ? t.group : 0) * TC_ROWS * MLP_H * 2;
