@@ -26,14 +26,15 @@ struct KernelCoef {
 KernelCoef kernel_coef(double R = 2.0);
 
 // A package's 6^3 tile (the package plus a one-point halo) in shared
-// memory: rows of 6 along x, planes of 40 (6 x 6 padded), 241 floats per
-// package.  When 16 threads of a package take one row (j, k) each and a warp
-// holds two packages, every tap load falls on 32 distinct banks: the rows
-// 6 j + 40 k cover the even banks, the odd tile size puts the second
-// package on the odd ones (6 x 36 x 216 gave 3-way conflicts).
+// memory: rows of 6 along x, planes of 40 (6 x 6 padded), 242 floats per
+// package, so that every row starts on an 8-byte boundary.  When 16 threads
+// of a package take one row (j, k) each and read 8-byte pairs, a warp's two
+// packages are served in two half-warp phases and each phase meets 16
+// distinct bank pairs (the rows 6 j + 40 k: 3 j + 20 k pairs, distinct mod
+// 16); 6 x 36 x 216 gave 3-way conflicts.
 constexpr int TILE_Y = 6;
 constexpr int TILE_Z = 40;
-constexpr int TILE_N = 241;
+constexpr int TILE_N = 242;
 
 namespace {
 
@@ -211,10 +212,9 @@ __device__ __forceinline__ void integrals_point2(const float* tile, int d, const
         float2 h0[3], a[3], b[3];
 #pragma unroll
         for (int sy = -1; sy <= 1; ++sy) {
-            const float* row = H + TILE_Y * sy + TILE_Z * sz;
-            const float r0 = row[-1], r1 = row[0], r2 = row[1], r3 = row[2];
-            const float2 m = make_float2(r0, r1), p = make_float2(r2, r3);
-            h0[sy + 1] = make_float2(r1, r2);
+            const float* row = H + TILE_Y * sy + TILE_Z * sz;  // row - 1 is 8-byte aligned (d even)
+            const float2 m = *reinterpret_cast<const float2*>(row - 1), p = *reinterpret_cast<const float2*>(row + 1);
+            h0[sy + 1] = make_float2(m.y, p.x);
             a[sy + 1] = __fadd2_rn(m, p);
             b[sy + 1] = __fadd2_rn(m, neg2(p));
         }

@@ -542,8 +542,8 @@ __global__ void __launch_bounds__(SA_WARPS * 32, SG_SA_MIN_CTAS)
             SurBody B0, const uint8_t* __restrict__ type, const int32_t* __restrict__ body,
             const SurBody* __restrict__ sb, int32_t* __restrict__ list, unsigned* __restrict__ count,
             unsigned long long* __restrict__ stats) {
-    __shared__ float s_H[SA_WARPS][2][TILE_N];
-    __shared__ float s_phi[SA_WARPS][2][TILE_N];
+    __shared__ __align__(16) float s_H[SA_WARPS][2][TILE_N];
+    __shared__ __align__(16) float s_phi[SA_WARPS][2][TILE_N];
     __shared__ uint16_t s_mask[SA_WARPS][2][36];
     __shared__ int s_nb[SA_WARPS][2][32];
     __shared__ SurBody s_B[SA_WARPS][2];
@@ -620,15 +620,18 @@ __global__ void __launch_bounds__(SA_WARPS * 32, SG_SA_MIN_CTAS)
             const float vp = __ldg(reinterpret_cast<const float*>(pb + 4u * PKG3 * (uint32_t)nb[nbs + 2]));
             const float f[6] = {vm, v.x, v.y, v.z, v.w, vp};
             const float ie = s_B[warp][pk].inv_eps, hu = s_B[warp][pk].C.h_up;
-            float* t = tH[pk] + e0;
-            float* tp = tP[pk] + e0;
+            float2* t = reinterpret_cast<float2*>(tH[pk] + e0);  // rows start on 8-byte boundaries
+            float2* tp = reinterpret_cast<float2*>(tP[pk] + e0);
             unsigned b = 0, mo = 0, mi = 0;
 #pragma unroll
+            for (int i = 0; i < 6; i += 2) {
+                const float h0 = heaviside_neg(f[i], ie), h1 = heaviside_neg(f[i + 1], ie);
+                t[i / 2] = make_float2(h0, h1);
+                tp[i / 2] = make_float2(f[i], f[i + 1]);
+                b |= (h0 != 0.0f ? 1u : 0u) | (h0 != 1.0f ? 2u : 0u) | (h1 != 0.0f ? 1u : 0u) | (h1 != 1.0f ? 2u : 0u);
+            }
+#pragma unroll
             for (int i = 0; i < 6; ++i) {
-                const float hv = heaviside_neg(f[i], ie);
-                t[i] = hv;
-                tp[i] = f[i];
-                b |= (hv != 0.0f ? 1u : 0u) | (hv != 1.0f ? 2u : 0u);
                 mo |= (f[i] >= hu ? 1u : 0u) << i;
                 mi |= (-f[i] >= hu ? 1u : 0u) << i;
             }

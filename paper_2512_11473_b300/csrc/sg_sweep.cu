@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(IW_WARPS * 32, SG_IW_MIN_CTAS) k_kernel_integr
                                                                      float* __restrict__ W, float* __restrict__ gx,
                                                                      float* __restrict__ gy, float* __restrict__ gz,
                                                                      int64_t P, KernelCoef K, float inv_eps) {
-    __shared__ float s_H[IW_WARPS][2][TILE_N];
+    __shared__ __align__(16) float s_H[IW_WARPS][2][TILE_N];
     __shared__ int s_nb[IW_WARPS][2][32];  // rows of 27, padded: the two packages' rows start on bank 0
     write_far(W, 1.0f, 0.0f);
     write_far(gx, 0.0f, 0.0f);
@@ -150,13 +150,13 @@ __global__ void __launch_bounds__(IW_WARPS * 32, SG_IW_MIN_CTAS) k_kernel_integr
                 vp = __ldg(phi + (int64_t)nb[r_nb[q] + 2] * PKG3 + r_d0[q]);
             }
             const float f[6] = {vm, v.x, v.y, v.z, v.w, vp};
-            float* t = tH[pk] + r_e0[q];
+            float2* t = reinterpret_cast<float2*>(tH[pk] + r_e0[q]);  // rows start on 8-byte boundaries
             unsigned b = 0;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                const float hv = heaviside_neg(f[i], inv_eps);
-                t[i] = hv;
-                b |= (hv != 0.0f ? 1u : 0u) | (hv != 1.0f ? 2u : 0u);
+            for (int i = 0; i < 6; i += 2) {
+                const float h0 = heaviside_neg(f[i], inv_eps), h1 = heaviside_neg(f[i + 1], inv_eps);
+                t[i / 2] = make_float2(h0, h1);
+                b |= (h0 != 0.0f ? 1u : 0u) | (h0 != 1.0f ? 2u : 0u) | (h1 != 0.0f ? 1u : 0u) | (h1 != 1.0f ? 2u : 0u);
             }
             bits[pk] |= b;
         }
