@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(BT) k_batch_integrals(const int32_t* __restric
                                                         float* __restrict__ gx, float* __restrict__ gy,
                                                         float* __restrict__ gz, int64_t P, KernelCoef K) {
     __shared__ int s_nb[BT_HW][NB];
-    __shared__ float s_H[BT_HW][TILE_N];
+    __shared__ __align__(16) float s_H[BT_HW][TILE_N];
     __shared__ unsigned s_sat[BT_HW];
     __shared__ float s_ieps[BT_HW];
     __shared__ int s_ok[BT_HW];
@@ -231,7 +231,14 @@ __global__ void __launch_bounds__(BT) k_batch_integrals(const int32_t* __restric
     float w[4], ax[4], ay[4], az[4];
     if (!integrals_saturated(s_sat[lp], w[0], ax[0], ay[0], az[0])) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) integrals_point(s_H[lp], 4 * r + i, K, w[i], ax[i], ay[i], az[i]);
+        for (int pp = 0; pp < 2; ++pp) {  // x-neighbour pairs on paired FP32 instructions (the same bits)
+            float2 w2, x2, y2, z2;
+            integrals_point2(s_H[lp], 4 * r + 2 * pp, K, w2, x2, y2, z2);
+            w[2 * pp] = w2.x, w[2 * pp + 1] = w2.y;
+            ax[2 * pp] = x2.x, ax[2 * pp + 1] = x2.y;
+            ay[2 * pp] = y2.x, ay[2 * pp + 1] = y2.y;
+            az[2 * pp] = z2.x, az[2 * pp + 1] = z2.y;
+        }
     } else {
 #pragma unroll
         for (int i = 1; i < 4; ++i) w[i] = w[0], ax[i] = ax[0], ay[i] = ay[0], az[i] = az[0];

@@ -58,6 +58,7 @@ __device__ __forceinline__ float heaviside_neg(float phi, float inv_eps) {
 // smoothed Heaviside to tH (either may be null); returns the saturation
 // bits of the H values this thread staged: bit 0 unless all were 0, bit 1
 // unless all were 1 (a tile whose bits OR to 1 is all ones, to 2 all zeros).
+// The tiles (8-byte aligned, TILE_N floats apart) take the row as three pairs.
 __device__ __forceinline__ unsigned stage_rows(const int* nb27, const float* __restrict__ phi, float inv_eps, int d,
                                                float* tphi, float* tH) {
     unsigned bits = 0;
@@ -69,15 +70,15 @@ __device__ __forceinline__ unsigned stage_rows(const int* nb27, const float* __r
         const float4 v = __ldg(reinterpret_cast<const float4*>(phi + (int64_t)nb27[nb + 1] * PKG3 + d0));
         const float vm = __ldg(phi + (int64_t)nb27[nb] * PKG3 + d0 + 3);
         const float vp = __ldg(phi + (int64_t)nb27[nb + 2] * PKG3 + d0);
-        const int e0 = TILE_Y * (y + 1) + TILE_Z * (z + 1);
+        const int e0 = TILE_Y * (y + 1) + TILE_Z * (z + 1);  // even: rows start on 8-byte boundaries
         const float f[6] = {vm, v.x, v.y, v.z, v.w, vp};
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            if (tphi) tphi[e0 + i] = f[i];
+        for (int i = 0; i < 6; i += 2) {
+            if (tphi) *reinterpret_cast<float2*>(tphi + e0 + i) = make_float2(f[i], f[i + 1]);
             if (tH) {
-                const float hv = heaviside_neg(f[i], inv_eps);
-                tH[e0 + i] = hv;
-                bits |= (hv != 0.0f ? 1u : 0u) | (hv != 1.0f ? 2u : 0u);
+                const float h0 = heaviside_neg(f[i], inv_eps), h1 = heaviside_neg(f[i + 1], inv_eps);
+                *reinterpret_cast<float2*>(tH + e0 + i) = make_float2(h0, h1);
+                bits |= (h0 != 0.0f ? 1u : 0u) | (h0 != 1.0f ? 2u : 0u) | (h1 != 0.0f ? 1u : 0u) | (h1 != 1.0f ? 2u : 0u);
             }
         }
     }

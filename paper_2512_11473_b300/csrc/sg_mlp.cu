@@ -907,7 +907,7 @@ __global__ void __launch_bounds__(SU_THREADS) k_sur_classify(const int32_t* __re
                                                              const float* __restrict__ phi, int64_t P, SurConst C,
                                                              uint8_t* __restrict__ cls) {
     __shared__ int s_nb[SU_PK][NB];
-    __shared__ float s_phi[SU_PK][TILE_N];
+    __shared__ __align__(16) float s_phi[SU_PK][TILE_N];
     const int lp = threadIdx.x >> 6, d = threadIdx.x & 63;
     const int64_t p = (int64_t)blockIdx.x * SU_PK + lp;
     const bool act = p >= 2 && p < P;
@@ -940,7 +940,7 @@ __global__ void __launch_bounds__(SU_THREADS) k_sur_samples(const int32_t* __res
                                                             const float* __restrict__ gy, const float* __restrict__ gz,
                                                             __nv_bfloat16* __restrict__ xo, float* __restrict__ to) {
     __shared__ int s_nb[SU_PK][NB];
-    __shared__ float s_phi[SU_PK][TILE_N];
+    __shared__ __align__(16) float s_phi[SU_PK][TILE_N];
     __shared__ unsigned s_ball[SU_PK][2];
     __shared__ uint8_t s_pos[48 * MLP_IN];
     const int lp = threadIdx.x >> 6, d = threadIdx.x & 63, lane = threadIdx.x & 31;
