@@ -147,11 +147,16 @@ __global__ void __launch_bounds__(BT, DEPTH == 1 ? 6 : 1) k_batch_reinit(const i
             Rows w[DEPTH];
             float4 sg[DEPTH];
             float cfl[DEPTH], dtv[DEPTH];
+            bool act[DEPTH];
+            // the rows of every package in the store are loaded (a far package's
+            // face rows name itself), so that the loads do not wait for the
+            // package's type and body constants; only active packages store
 #pragma unroll
             for (int d = 0; d < DEPTH; ++d) {
                 const int64_t p = item * per_item + (int64_t)(k + d) * BT_HW + (threadIdx.x >> 4);
                 const int64_t pc = p < P ? p : 0;
-                sl[d] = make_slot(p, p < P && k + d < ppi && __ldg(type + pc) >= 2);
+                sl[d] = make_slot(p, p < P && k + d < ppi);
+                act[d] = sl[d].valid && __ldg(type + pc) >= 2;
                 const BodyParams* bp = prm + __ldg(body + pc);
                 cfl[d] = __ldg(&bp->cfl);
                 dtv[d] = __ldg(&bp->dt);
@@ -162,7 +167,7 @@ __global__ void __launch_bounds__(BT, DEPTH == 1 ? 6 : 1) k_batch_reinit(const i
             for (int d = 0; d < DEPTH; ++d) w[d] = load_rows(phi_in, faces, sl[d]);
 #pragma unroll
             for (int d = 0; d < DEPTH; ++d) {
-                if (!sl[d].valid) continue;
+                if (!act[d]) continue;
                 reinterpret_cast<float4*>(phi_out)[sl[d].q4] = reinit_row(w[d], sg[d], cfl[d], dtv[d]);
             }
         }
