@@ -102,18 +102,24 @@ __global__ void __launch_bounds__(BT) k_batch_gradient(const int32_t* __restrict
         for (int k = 0; k < ppi; k += DEPTH) {
             RowSlot sl[DEPTH];
             Rows w[DEPTH];
+            bool act[DEPTH];
+            float inv2h[DEPTH];
+            // rows loaded for every package (as in the reinit sweep), stored for active ones
 #pragma unroll
             for (int d = 0; d < DEPTH; ++d) {
                 const int64_t p = item * per_item + (int64_t)(k + d) * BT_HW + (threadIdx.x >> 4);
-                sl[d] = make_slot(p, p < P && k + d < ppi && __ldg(type + (p < P ? p : 0)) >= 2);
+                const int64_t pc = p < P ? p : 0;
+                sl[d] = make_slot(p, p < P && k + d < ppi);
+                act[d] = sl[d].valid && __ldg(type + pc) >= 2;
+                inv2h[d] = __ldg(&prm[__ldg(body + pc)].inv2h);
             }
 #pragma unroll
             for (int d = 0; d < DEPTH; ++d) w[d] = load_rows(phi, faces, sl[d]);
 #pragma unroll
             for (int d = 0; d < DEPTH; ++d) {
-                if (!sl[d].valid) continue;
+                if (!act[d]) continue;
                 float4 ox, oy, oz;
-                gradient_row(w[d], __ldg(&prm[__ldg(body + sl[d].p)].inv2h), ox, oy, oz);
+                gradient_row(w[d], inv2h[d], ox, oy, oz);
                 reinterpret_cast<float4*>(gx)[sl[d].q4] = ox;
                 reinterpret_cast<float4*>(gy)[sl[d].q4] = oy;
                 reinterpret_cast<float4*>(gz)[sl[d].q4] = oz;
