@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(BT) k_batch_gradient(const int32_t* __restrict
                                                        const int32_t* __restrict__ body,
                                                        const BodyParams* __restrict__ prm, const float* __restrict__ phi,
                                                        float* __restrict__ gx, float* __restrict__ gy,
-                                                       float* __restrict__ gz, int64_t P, int ppi, unsigned* counter) {
+                                                       float* __restrict__ gz, float* __restrict__ s0, int64_t P, int ppi,
+                                                       unsigned* counter) {
     __shared__ int s_item;
     const int64_t per_item = (int64_t)BT_HW * ppi, items = (P + per_item - 1) / per_item;
     for (;;) {
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(BT) k_batch_gradient(const int32_t* __restrict
             RowSlot sl[DEPTH];
             Rows w[DEPTH];
             bool act[DEPTH];
-            float inv2h[DEPTH];
+            float inv2h[DEPTH], h2[DEPTH];
             // rows loaded for every package (as in the reinit sweep), stored for active ones
 #pragma unroll
             for (int d = 0; d < DEPTH; ++d) {
@@ -111,7 +112,9 @@ __global__ void __launch_bounds__(BT) k_batch_gradient(const int32_t* __restrict
                 const int64_t pc = p < P ? p : 0;
                 sl[d] = make_slot(p, p < P && k + d < ppi);
                 act[d] = sl[d].valid && __ldg(type + pc) >= 2;
-                inv2h[d] = __ldg(&prm[__ldg(body + pc)].inv2h);
+                const BodyParams* bp = prm + __ldg(body + pc);
+                inv2h[d] = __ldg(&bp->inv2h);
+                h2[d] = __ldg(&bp->h2);
             }
 #pragma unroll
             for (int d = 0; d < DEPTH; ++d) w[d] = load_rows(phi, faces, sl[d]);
@@ -123,6 +126,13 @@ __global__ void __launch_bounds__(BT) k_batch_gradient(const int32_t* __restrict
                 reinterpret_cast<float4*>(gx)[sl[d].q4] = ox;
                 reinterpret_cast<float4*>(gy)[sl[d].q4] = oy;
                 reinterpret_cast<float4*>(gz)[sl[d].q4] = oz;
+                // the smoothed sign of the sweeps that follow, from the same row of phi
+                float4 sg = w[d].c;
+                sg.x = smoothed_sign(sg.x, h2[d]);
+                sg.y = smoothed_sign(sg.y, h2[d]);
+                sg.z = smoothed_sign(sg.z, h2[d]);
+                sg.w = smoothed_sign(sg.w, h2[d]);
+                reinterpret_cast<float4*>(s0)[sl[d].q4] = sg;
             }
         }
     }
@@ -144,7 +154,7 @@ __global__ void __launch_bounds__(BT, DEPTH == 1 ? 6 : 1) k_batch_reinit(const i
         int64_t item = next_item(counter, &s_item);
         if (item >= items) break;
         // every other sweep walks the store backwards (the first one, after the
-        // forward smoothed-sign pass, among them), so that it starts on the
+        // forward gradient and smoothed-sign pass, among them), so that it starts on the
         // packages the previous pass left in L2 (the Jacobi results do not
         // depend on the order)
         if (reverse) item = items - 1 - item;
@@ -177,25 +187,6 @@ __global__ void __launch_bounds__(BT, DEPTH == 1 ? 6 : 1) k_batch_reinit(const i
                 reinterpret_cast<float4*>(phi_out)[sl[d].q4] = reinit_row(w[d], sg[d], cfl[d], dtv[d]);
             }
         }
-    }
-}
-
-// Smoothed sign over the active packages of every body (one float4 row per
-// thread, grid-stride).
-__global__ void __launch_bounds__(BT) k_batch_s0(const uint8_t* __restrict__ type, const int32_t* __restrict__ body,
-                                                 const BodyParams* __restrict__ prm, const float* __restrict__ phi,
-                                                 float* __restrict__ s0, int64_t P) {
-    const int64_t rows = P * 16;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < rows; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = q >> 4;
-        if (__ldg(type + p) < 2) continue;
-        const float h2 = __ldg(&prm[__ldg(body + p)].h2);
-        float4 v = __ldg(reinterpret_cast<const float4*>(phi) + q);
-        v.x = smoothed_sign(v.x, h2);
-        v.y = smoothed_sign(v.y, h2);
-        v.z = smoothed_sign(v.z, h2);
-        v.w = smoothed_sign(v.w, h2);
-        reinterpret_cast<float4*>(s0)[q] = v;
     }
 }
 
@@ -461,13 +452,13 @@ cudaError_t record_run(sg_batch* b, const sg_batch_plan& plan, cudaStream_t s) {
     const KernelCoef K = kernel_coef(b->R);
     if (plan.depth == 2) {
         const int nb = persistent_blocks((const void*)k_batch_gradient<2>, b->device);
-        k_batch_gradient<2><<<nb, BT, 0, s>>>(faces, type, body, prm, phi, fo[1], fo[2], fo[3], b->P, ppi, ctr + c++);
+        k_batch_gradient<2><<<nb, BT, 0, s>>>(faces, type, body, prm, phi, fo[1], fo[2], fo[3], s0, b->P, ppi,
+                                              ctr + c++);
     } else {
         const int nb = persistent_blocks((const void*)k_batch_gradient<1>, b->device);
-        k_batch_gradient<1><<<nb, BT, 0, s>>>(faces, type, body, prm, phi, fo[1], fo[2], fo[3], b->P, ppi, ctr + c++);
+        k_batch_gradient<1><<<nb, BT, 0, s>>>(faces, type, body, prm, phi, fo[1], fo[2], fo[3], s0, b->P, ppi,
+                                              ctr + c++);
     }
-    note_launch();
-    k_batch_s0<<<flat_grid(b->P * 16), BT, 0, s>>>(type, body, prm, phi, s0, b->P);
     note_launch();
     float* a = phi;
     float* o = tmp;
