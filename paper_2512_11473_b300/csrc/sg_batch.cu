@@ -17,6 +17,7 @@
 // and displaced by one kernel per step; the sweeps and every step are
 // captured into one graph.
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <string>
@@ -188,68 +189,6 @@ __global__ void __launch_bounds__(BT, DEPTH == 1 ? 6 : 1) k_batch_reinit(const i
             }
         }
     }
-}
-
-// Kernel integrals over the global store, as the single-grid kernel: a CTA
-// per 16 consecutive packages (the batch's store is one package array), all
-// threads staging the 16 Heaviside tiles, then each thread summing one
-// package row of four points.  Far packages are skipped; each package takes
-// the Heaviside width of its body.
-__global__ void __launch_bounds__(BT) k_batch_integrals(const int32_t* __restrict__ nbr, const uint8_t* __restrict__ type,
-                                                        const int32_t* __restrict__ body,
-                                                        const BodyParams* __restrict__ prm,
-                                                        const float* __restrict__ phi, float* __restrict__ W,
-                                                        float* __restrict__ gx, float* __restrict__ gy,
-                                                        float* __restrict__ gz, int64_t P, KernelCoef K) {
-    __shared__ int s_nb[BT_HW][NB];
-    __shared__ __align__(16) float s_H[BT_HW][TILE_N];
-    __shared__ unsigned s_sat[BT_HW];
-    __shared__ float s_ieps[BT_HW];
-    __shared__ int s_ok[BT_HW];
-    const int64_t p0 = (int64_t)blockIdx.x * BT_HW;
-    if (threadIdx.x < BT_HW) {
-        const int64_t p = p0 + threadIdx.x;
-        const bool ok = p < P && __ldg(type + p) >= 2;
-        s_ok[threadIdx.x] = ok;
-        s_sat[threadIdx.x] = 0;
-        s_ieps[threadIdx.x] = ok ? __ldg(&prm[__ldg(body + p)].inv_eps) : 0.0f;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < BT_HW * NB; e += BT) {
-        const int lp = e / NB;
-        if (s_ok[lp]) s_nb[lp][e - lp * NB] = __ldg(nbr + (p0 + lp) * NB + (e - lp * NB));
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < BT_HW * 36; e += BT) {
-        const int lp = e / 36;
-        if (s_ok[lp]) {
-            const unsigned bits = integrals_stage(s_nb[lp], phi, s_ieps[lp], e - lp * 36, s_H[lp]);
-            if (bits) atomicOr(&s_sat[lp], bits);
-        }
-    }
-    __syncthreads();
-    const int lp = threadIdx.x >> 4, r = threadIdx.x & 15;
-    if (!s_ok[lp]) return;
-    float w[4], ax[4], ay[4], az[4];
-    if (!integrals_saturated(s_sat[lp], w[0], ax[0], ay[0], az[0])) {
-#pragma unroll
-        for (int pp = 0; pp < 2; ++pp) {  // x-neighbour pairs on paired FP32 instructions (the same bits)
-            float2 w2, x2, y2, z2;
-            integrals_point2(s_H[lp], 4 * r + 2 * pp, K, w2, x2, y2, z2);
-            w[2 * pp] = w2.x, w[2 * pp + 1] = w2.y;
-            ax[2 * pp] = x2.x, ax[2 * pp + 1] = x2.y;
-            ay[2 * pp] = y2.x, ay[2 * pp + 1] = y2.y;
-            az[2 * pp] = z2.x, az[2 * pp + 1] = z2.y;
-        }
-    } else {
-#pragma unroll
-        for (int i = 1; i < 4; ++i) w[i] = w[0], ax[i] = ax[0], ay[i] = ay[0], az[i] = az[0];
-    }
-    const int64_t q4 = (p0 + lp) * 16 + r;
-    reinterpret_cast<float4*>(W)[q4] = make_float4(w[0], w[1], w[2], w[3]);
-    reinterpret_cast<float4*>(gx)[q4] = make_float4(ax[0], ax[1], ax[2], ax[3]);
-    reinterpret_cast<float4*>(gy)[q4] = make_float4(ay[0], ay[1], ay[2], ay[3]);
-    reinterpret_cast<float4*>(gz)[q4] = make_float4(az[0], az[1], az[2], az[3]);
 }
 
 __global__ void k_batch_offset_nbr(const int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t n,
@@ -449,7 +388,6 @@ cudaError_t record_run(sg_batch* b, const sg_batch_plan& plan, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(ctr, 0, b->n_counters * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     int c = 0;
-    const KernelCoef K = kernel_coef(b->R);
     if (plan.depth == 2) {
         const int nb = persistent_blocks((const void*)k_batch_gradient<2>, b->device);
         k_batch_gradient<2><<<nb, BT, 0, s>>>(faces, type, body, prm, phi, fo[1], fo[2], fo[3], s0, b->P, ppi,
@@ -482,11 +420,12 @@ cudaError_t record_run(sg_batch* b, const sg_batch_plan& plan, cudaStream_t s) {
     if (plan.integrals_mode == 1)
         return launch_batch_surrogate_integrals(nbr, type, body, (const SurBody*)b->sur.p, phi, fo[4], fo[5], fo[6],
                                                 fo[7], b->P, b->mlp, b->sur_work.p, mlp_err(b->mlp), b->device, s);
-    // a plain grid: the integrals' per-package work is even, so they need no work counter
-    k_batch_integrals<<<(unsigned)((b->P + BT_HW - 1) / BT_HW), BT, 0, s>>>(nbr, type, body, prm, phi, fo[4], fo[5],
-                                                                           fo[6], fo[7], b->P, K);
-    note_launch();
-    return cudaGetLastError();
+    // the single-grid kernel's warps on package pairs, with each body's Heaviside width
+    static_assert(sizeof(BodyParams) % sizeof(float) == 0, "BodyParams as floats");
+    return launch_batch_kernel_integrals(nbr, type, body,
+                                         reinterpret_cast<const float*>(prm) + offsetof(BodyParams, inv_eps) / sizeof(float),
+                                         (int)(sizeof(BodyParams) / sizeof(float)), phi, fo[4], fo[5], fo[6], fo[7],
+                                         b->P, b->R, s);
 }
 
 // Record the packing of the probe table and `steps` relaxation steps on

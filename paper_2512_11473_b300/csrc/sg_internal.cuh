@@ -177,6 +177,12 @@ cudaError_t launch_copy_active(const float* src, float* dst, int64_t P, cudaStre
 // phi <- phi + delta on the active packages
 cudaError_t launch_sequential(float* phi, float delta, int64_t P, cudaStream_t s);
 // R: kernel support in units of h (<= 3); eps: Heaviside half width.
+// The exact integrals (support <= 2h) over a batch's store: packages of type
+// < 2 are left as they are, each package takes the Heaviside width of its
+// body, 1 / ieps_b[body[p] * ieps_stride].
+cudaError_t launch_batch_kernel_integrals(const int32_t* nbr, const uint8_t* type, const int32_t* body,
+                                          const float* ieps_b, int ieps_stride, const float* phi, float* W, float* gx,
+                                          float* gy, float* gz, int64_t P, double R, cudaStream_t s);
 cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const float* phi, float* W, float* gx,
                                     float* gy, float* gz, int64_t P, double R, double eps, cudaStream_t s);
 // The kernel support of a grid in units of h and its Heaviside half width.

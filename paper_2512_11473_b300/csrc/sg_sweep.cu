@@ -81,18 +81,28 @@ constexpr int IW_ROWS = 72;  // staged rows per package pair
 #define SG_IW_MIN_CTAS 4
 #endif
 
-template <bool OFF32>
+// With BATCH the store is a batch's: packages of type < 2 (every body's far
+// packages) are skipped and left as they are, and each package takes the
+// Heaviside width of its body, ieps_b[body[p] * ieps_stride].
+template <bool OFF32, bool BATCH>
 __global__ void __launch_bounds__(IW_WARPS * 32, SG_IW_MIN_CTAS) k_kernel_integrals(const int32_t* __restrict__ nbr,
                                                                      const float* __restrict__ phi,
                                                                      float* __restrict__ W, float* __restrict__ gx,
                                                                      float* __restrict__ gy, float* __restrict__ gz,
-                                                                     int64_t P, KernelCoef K, float inv_eps) {
+                                                                     int64_t P, KernelCoef K, float inv_eps,
+                                                                     const uint8_t* __restrict__ type,
+                                                                     const int32_t* __restrict__ body,
+                                                                     const float* __restrict__ ieps_b,
+                                                                     int ieps_stride) {
     __shared__ __align__(16) float s_H[IW_WARPS][2][TILE_N];
     __shared__ int s_nb[IW_WARPS][2][32];  // rows of 27, padded: the two packages' rows start on bank 0
-    write_far(W, 1.0f, 0.0f);
-    write_far(gx, 0.0f, 0.0f);
-    write_far(gy, 0.0f, 0.0f);
-    write_far(gz, 0.0f, 0.0f);
+    if (!BATCH) {
+        write_far(W, 1.0f, 0.0f);
+        write_far(gx, 0.0f, 0.0f);
+        write_far(gy, 0.0f, 0.0f);
+        write_far(gz, 0.0f, 0.0f);
+    }
+    constexpr int first = BATCH ? 0 : 2;  // a single grid's far packages are 0 and 1
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float(*tH)[TILE_N] = s_H[warp];
     int(*tnb)[32] = s_nb[warp];
@@ -109,18 +119,30 @@ __global__ void __launch_bounds__(IW_WARPS * 32, SG_IW_MIN_CTAS) k_kernel_integr
         r_e0[q] = TILE_Y * (y + 1) + TILE_Z * (z + 1);
     }
     const int half = lane >> 4, r = lane & 15;
-    const int64_t pairs = (P - 2 + 1) / 2;
+    const int64_t pairs = (P - first + 1) / 2;
     const int64_t stride = (int64_t)gridDim.x * IW_WARPS;
     // the neighbourhood rows of the next pair are loaded while this pair's taps are summed
     int nb_next[2] = {0, 0};
     int64_t pr = (int64_t)blockIdx.x * IW_WARPS + warp;
     if (pr < pairs && lane < NB) {
-        nb_next[0] = __ldg(nbr + (2 + 2 * pr) * NB + lane);
-        if (3 + 2 * pr < P) nb_next[1] = __ldg(nbr + (3 + 2 * pr) * NB + lane);
+        nb_next[0] = __ldg(nbr + (first + 2 * pr) * NB + lane);
+        if (first + 1 + 2 * pr < P) nb_next[1] = __ldg(nbr + (first + 1 + 2 * pr) * NB + lane);
     }
     for (; pr < pairs; pr += stride) {
-        const int64_t p0 = 2 + 2 * pr;
+        const int64_t p0 = first + 2 * pr;
         const bool two = p0 + 1 < P;
+        // which of the two packages take part (bit k: package p0 + k), and
+        // their Heaviside widths (lane k holds package k's)
+        unsigned okm = two ? 3u : 1u;
+        float ie_l = inv_eps;
+        if (BATCH) {
+            bool ok = lane < 2 && (lane == 0 || two);
+            if (ok) {
+                ok = __ldg(type + p0 + lane) >= 2;
+                if (ok) ie_l = __ldg(ieps_b + (int64_t)__ldg(body + p0 + lane) * ieps_stride);
+            }
+            okm = __ballot_sync(0xffffffffu, ok);
+        }
         if (lane < NB) {
             tnb[0][lane] = nb_next[0];
             tnb[1][lane] = nb_next[1];
@@ -128,14 +150,15 @@ __global__ void __launch_bounds__(IW_WARPS * 32, SG_IW_MIN_CTAS) k_kernel_integr
         __syncwarp();
         const int64_t pn = pr + stride;
         if (pn < pairs && lane < NB) {
-            nb_next[0] = __ldg(nbr + (2 + 2 * pn) * NB + lane);
-            if (3 + 2 * pn < P) nb_next[1] = __ldg(nbr + (3 + 2 * pn) * NB + lane);
+            nb_next[0] = __ldg(nbr + (first + 2 * pn) * NB + lane);
+            if (first + 1 + 2 * pn < P) nb_next[1] = __ldg(nbr + (first + 1 + 2 * pn) * NB + lane);
         }
         unsigned bits[2] = {0u, 0u};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             const int pk = r_pk[q];
-            if (pk < 0 || (pk == 1 && !two)) continue;
+            const float ie = BATCH ? __shfl_sync(0xffffffffu, ie_l, pk < 0 ? 0 : pk) : inv_eps;
+            if (pk < 0 || !((okm >> pk) & 1u)) continue;
             const int* nb = tnb[pk];
             float4 v;
             float vm, vp;
@@ -154,7 +177,7 @@ __global__ void __launch_bounds__(IW_WARPS * 32, SG_IW_MIN_CTAS) k_kernel_integr
             unsigned b = 0;
 #pragma unroll
             for (int i = 0; i < 6; i += 2) {
-                const float h0 = heaviside_neg(f[i], inv_eps), h1 = heaviside_neg(f[i + 1], inv_eps);
+                const float h0 = heaviside_neg(f[i], ie), h1 = heaviside_neg(f[i + 1], ie);
                 t[i / 2] = make_float2(h0, h1);
                 b |= (h0 != 0.0f ? 1u : 0u) | (h0 != 1.0f ? 2u : 0u) | (h1 != 0.0f ? 1u : 0u) | (h1 != 1.0f ? 2u : 0u);
             }
@@ -163,7 +186,7 @@ __global__ void __launch_bounds__(IW_WARPS * 32, SG_IW_MIN_CTAS) k_kernel_integr
         bits[0] = __reduce_or_sync(0xffffffffu, bits[0]);
         bits[1] = __reduce_or_sync(0xffffffffu, bits[1]);
         __syncwarp();
-        if (half == 0 || two) {
+        if ((okm >> half) & 1u) {
             const int64_t p = p0 + half;
             float w[4], ax[4], ay[4], az[4];
             if (!integrals_saturated(bits[half], w[0], ax[0], ay[0], az[0])) {
@@ -315,7 +338,7 @@ unsigned integrals_grid(int64_t P) {
     if (!sms) {
         int dev = 0;
         cudaGetDevice(&dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kernel_integrals<true>, IW_WARPS * 32, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kernel_integrals<true, false>, IW_WARPS * 32, 0) !=
                 cudaSuccess ||
             per_sm < 1) {
             cudaGetLastError();
@@ -343,11 +366,26 @@ cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const fl
         k_kernel_integrals_wide<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(R),
                                                                       (float)(1.0 / eps));
     else if (P < ((int64_t)1 << 24) && !force_wide_offsets())  // byte offsets of every field fit 32 bits
-        k_kernel_integrals<true><<<integrals_grid(P), IW_WARPS * 32, 0, s>>>(nbr, phi, W, gx, gy, gz, P,
-                                                                             kernel_coef(R), (float)(1.0 / eps));
+        k_kernel_integrals<true, false><<<integrals_grid(P), IW_WARPS * 32, 0, s>>>(
+            nbr, phi, W, gx, gy, gz, P, kernel_coef(R), (float)(1.0 / eps), nullptr, nullptr, nullptr, 0);
     else
-        k_kernel_integrals<false><<<integrals_grid(P), IW_WARPS * 32, 0, s>>>(nbr, phi, W, gx, gy, gz, P,
-                                                                              kernel_coef(R), (float)(1.0 / eps));
+        k_kernel_integrals<false, false><<<integrals_grid(P), IW_WARPS * 32, 0, s>>>(
+            nbr, phi, W, gx, gy, gz, P, kernel_coef(R), (float)(1.0 / eps), nullptr, nullptr, nullptr, 0);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_kernel_integrals(const int32_t* nbr, const uint8_t* type, const int32_t* body,
+                                          const float* ieps_b, int ieps_stride, const float* phi, float* W, float* gx,
+                                          float* gy, float* gz, int64_t P, double R, cudaStream_t s) {
+    if (P < 1) return cudaSuccess;
+    const KernelCoef K = kernel_coef(R);
+    if (P < ((int64_t)1 << 24) && !force_wide_offsets())
+        k_kernel_integrals<true, true><<<integrals_grid(P + 2), IW_WARPS * 32, 0, s>>>(
+            nbr, phi, W, gx, gy, gz, P, K, 0.0f, type, body, ieps_b, ieps_stride);
+    else
+        k_kernel_integrals<false, true><<<integrals_grid(P + 2), IW_WARPS * 32, 0, s>>>(
+            nbr, phi, W, gx, gy, gz, P, K, 0.0f, type, body, ieps_b, ieps_stride);
     note_launch();
     return cudaGetLastError();
 }
