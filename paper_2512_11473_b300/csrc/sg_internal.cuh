@@ -95,6 +95,33 @@ __device__ __forceinline__ void write_far(float* f, float v_in, float v_out) {
 
 // process-wide count of kernels launched by the library (sg_api.cu)
 void note_launch(int n = 1);
+
+// Programmatic dependent launch: a kernel launched by launch_pdl may start
+// while the kernel before it on the stream drains.  It calls pdl_enter()
+// before touching memory: that waits until the previous grid has completed
+// (its writes visible), then lets the next programmatic dependent launch.
+// Without a programmatic prerequisite both instructions return at once.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+    note_launch();
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
 // sg_debug_wide_offsets: take the 64-bit address kernels at any size (sg_api.cu)
 bool force_wide_offsets();
 

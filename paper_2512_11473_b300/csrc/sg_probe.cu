@@ -50,6 +50,7 @@ __device__ __forceinline__ uint64_t morton_key(const GridF& G, float x, float y,
 __global__ void __launch_bounds__(RS_THREADS) k_morton_check(GridF G, int64_t n, const float* __restrict__ x,
                                                              const float* __restrict__ y, const float* __restrict__ z,
                                                              int* unsorted) {
+    pdl_enter();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t iters = (n + stride - 1) / stride;
     const int lane = threadIdx.x & 31;
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_morton_check_sampled(GridF G, in
                                                                      const float* __restrict__ y,
                                                                      const float* __restrict__ z, int stride,
                                                                      int* unsorted) {
+    pdl_enter();
     const int64_t pairs = (n - 1 + stride - 1) / stride;
     bool bad = false;
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < pairs; m += (int64_t)gridDim.x * blockDim.x) {
@@ -87,6 +89,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_morton_keys(GridF G, int64_t n, 
                                                             const float* __restrict__ y, const float* __restrict__ z,
                                                             KeyT* __restrict__ keys, uint32_t* __restrict__ vals,
                                                             uint64_t* __restrict__ keys_out, const int* unsorted) {
+    pdl_enter();
     const bool sort = *unsorted != 0;
     if (!sort && !keys_out) return;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
@@ -100,6 +103,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_morton_keys(GridF G, int64_t n, 
 }
 
 __global__ void k_identity_if_sorted(const int* __restrict__ unsorted, int32_t* __restrict__ order, int64_t n) {
+    pdl_enter();
     if (*unsorted) return;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
         order[q] = (int32_t)q;
@@ -109,6 +113,7 @@ __global__ void k_identity_if_sorted(const int* __restrict__ unsorted, int32_t* 
 template <typename KeyT>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const KeyT* __restrict__ keys, int64_t n, int shift,
                                                         uint32_t* __restrict__ hist, int64_t nb, const int* run) {
+    pdl_enter();
     if (*run == 0) return;  // keys already in order
     __shared__ uint32_t h[256];
     for (int64_t tile = blockIdx.x; tile < nb; tile += gridDim.x) {
@@ -137,6 +142,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_rs_scatter(const KeyT* __rest
                                                            KeyT* __restrict__ kout, uint32_t* __restrict__ vout,
                                                            int64_t n, int shift, const uint32_t* __restrict__ offs,
                                                            int64_t nb, const int* run) {
+    pdl_enter();
     if (*run == 0) return;  // keys already in order
     extern __shared__ __align__(16) unsigned char smem[];
     KeyT* s_k = (KeyT*)smem;
@@ -243,6 +249,7 @@ __global__ void __launch_bounds__(PR_THREADS, PR_MIN_CTAS) k_probe(GridF G, cons
                                                        const float* __restrict__ x, const float* __restrict__ y,
                                                        const float* __restrict__ z, const int32_t* __restrict__ order,
                                                        const int* __restrict__ unsorted, ProbeOut out) {
+    pdl_enter();
     // with the input already in Morton order the walk is the input order
     const bool use_order = order && (!unsorted || *unsorted != 0);
     // each CTA walks one contiguous stretch of the walk, so that a warp's
@@ -317,15 +324,16 @@ cudaError_t sort_impl(const GridF& G, int64_t n, int key_bits, const float* x, c
     cudaError_t e = cudaMemsetAsync(unsorted, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (check_stride > 1)
-        k_morton_check_sampled<<<blocks_for((n + check_stride - 1) / check_stride, RS_THREADS), RS_THREADS, 0, s>>>(
-            G, n, x, y, z, check_stride, unsorted);
+        e = launch_pdl(k_morton_check_sampled, blocks_for((n + check_stride - 1) / check_stride, RS_THREADS), RS_THREADS,
+                       0, s, G, n, x, y, z, check_stride, unsorted);
     else
-        k_morton_check<<<blocks_for(n, RS_THREADS), RS_THREADS, 0, s>>>(G, n, x, y, z, unsorted);
+        e = launch_pdl(k_morton_check, blocks_for(n, RS_THREADS), RS_THREADS, 0, s, G, n, x, y, z, unsorted);
+    if (e != cudaSuccess) return e;
     // grid-stride kernels that may find nothing to do: a bounded grid ends at once
     const unsigned small_grid = blocks_for(n, RS_THREADS) < 148 * 8 ? blocks_for(n, RS_THREADS) : 148 * 8;
-    k_morton_keys<KeyT><<<small_grid, RS_THREADS, 0, s>>>(G, n, x, y, z, k0, v0, keys_out, unsorted);
-    note_launch(2);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_pdl(k_morton_keys<KeyT>, small_grid, RS_THREADS, 0, s, G, n, x, y, z, k0, v0, keys_out, unsorted)) !=
+        cudaSuccess)
+        return e;
     const int passes = (key_bits + 7) / 8;
     const size_t smem = RS_TILE * (sizeof(KeyT) + sizeof(uint32_t));
     e = cudaFuncSetAttribute(k_rs_scatter<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -336,26 +344,24 @@ cudaError_t sort_impl(const GridF& G, int64_t n, int key_bits, const float* x, c
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         uint32_t* vout = (p == passes - 1) ? (uint32_t*)order_out : V[1 - cur];
-        k_rs_hist<KeyT><<<(unsigned)(nb < 148 * 8 ? nb : 148 * 8), RS_THREADS, 0, s>>>(K[cur], n, shift, hist, nb,
-                                                                                          unsorted);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_pdl(k_rs_hist<KeyT>, (unsigned)(nb < 148 * 8 ? nb : 148 * 8), RS_THREADS, 0, s,
+                            (const KeyT*)K[cur], n, shift, hist, nb, unsorted)) != cudaSuccess)
+            return e;
         if ((e = exclusive_scan_u32(hist, hist, 256 * nb, nullptr, scan_scratch, s, unsorted)) != cudaSuccess)
             return e;
         // two blocks of the scatter fit on an SM (128 registers, 42-74 KB of shared memory)
-        k_rs_scatter<KeyT><<<(unsigned)(nb < 148 * 2 ? nb : 148 * 2), RS_THREADS, smem, s>>>(
-            K[cur], V[cur], K[1 - cur], vout, n, shift, hist, nb, unsorted);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_pdl(k_rs_scatter<KeyT>, (unsigned)(nb < 148 * 2 ? nb : 148 * 2), RS_THREADS, smem, s, K[cur],
+                            V[cur], K[1 - cur], vout, n, shift, hist, nb, unsorted)) != cudaSuccess)
+            return e;
         cur = 1 - cur;
     }
     if (passes == 0) {
         if ((e = cudaMemcpyAsync(order_out, V[0], n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
             return e;
     } else if (identity_out) {
-        k_identity_if_sorted<<<small_grid, RS_THREADS, 0, s>>>(unsorted, order_out, n);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_pdl(k_identity_if_sorted, small_grid, RS_THREADS, 0, s, (const int*)unsorted, order_out, n)) !=
+            cudaSuccess)
+            return e;
     }
     if (unsorted_out) *unsorted_out = unsorted;
     return cudaSuccess;
@@ -406,11 +412,10 @@ cudaError_t launch_probe(const GridF& G, const int32_t* cell_pkg, const int32_t*
     // at 50M (9,472 CTAs measured 2% slower on the torus)
     const int64_t ctas = std::min<int64_t>((n + PR_THREADS - 1) / PR_THREADS, 148 * 128);
     if (P < ((int64_t)1 << 24) && n < ((int64_t)1 << 30) && !force_wide_offsets())
-        k_probe<true><<<(unsigned)ctas, PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, unsorted, out);
-    else
-        k_probe<false><<<(unsigned)ctas, PR_THREADS, 0, s>>>(G, cell_pkg, nbr, F, n, x, y, z, order, unsorted, out);
-    note_launch();
-    return cudaGetLastError();
+        return launch_pdl(k_probe<true>, (unsigned)ctas, PR_THREADS, 0, s, G, cell_pkg, nbr, F, n, x, y, z, order,
+                          unsorted, out);
+    return launch_pdl(k_probe<false>, (unsigned)ctas, PR_THREADS, 0, s, G, cell_pkg, nbr, F, n, x, y, z, order, unsorted,
+                      out);
 }
 
 }  // namespace sg

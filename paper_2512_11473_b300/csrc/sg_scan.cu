@@ -49,6 +49,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
 // so that a launch whose `go` flag is clear ends at once).
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n, int64_t nb,
                                                                uint32_t* __restrict__ partial, const int* go) {
+    pdl_enter();
     if (go && *go == 0) return;
     __shared__ uint32_t red[SCAN_THREADS / 32];
     for (int64_t tile = blockIdx.x; tile < nb; tile += gridDim.x) {
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __
 
 __global__ void __launch_bounds__(SPINE_THREADS) k_scan_spine(uint32_t* __restrict__ partial, int64_t nb,
                                                                uint32_t* __restrict__ total, const int* go) {
+    pdl_enter();
     if (go && *go == 0) return;
     __shared__ uint32_t carry_s;
     if (threadIdx.x == 0) carry_s = 0;
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(SPINE_THREADS) k_scan_spine(uint32_t* __restri
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* in, uint32_t* out, int64_t n, int64_t nb,
                                                              const uint32_t* __restrict__ partial, const int* go) {
+    pdl_enter();
     if (go && *go == 0) return;
     for (int64_t tile = blockIdx.x; tile < nb; tile += gridDim.x) {
         const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
@@ -127,13 +130,10 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uin
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     uint32_t* partial = (uint32_t*)scratch;
     const unsigned grid = (unsigned)(nb < SCAN_GRID ? nb : SCAN_GRID);
-    k_scan_reduce<<<grid, SCAN_THREADS, 0, s>>>(in, n, nb, partial, go);
-    note_launch();
-    k_scan_spine<<<1, SPINE_THREADS, 0, s>>>(partial, nb, total, go);
-    note_launch();
-    k_scan_down<<<grid, SCAN_THREADS, 0, s>>>(in, out, n, nb, partial, go);
-    note_launch();
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(k_scan_reduce, grid, SCAN_THREADS, 0, s, in, n, nb, partial, go);
+    if (e == cudaSuccess) e = launch_pdl(k_scan_spine, 1, SPINE_THREADS, 0, s, partial, nb, total, go);
+    if (e == cudaSuccess) e = launch_pdl(k_scan_down, grid, SCAN_THREADS, 0, s, in, out, n, nb, partial, go);
+    return e;
 }
 
 }  // namespace sg

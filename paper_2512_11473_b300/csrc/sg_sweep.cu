@@ -23,6 +23,7 @@ __global__ void __launch_bounds__(SW_THREADS) k_set_far(float* f, float v_in, fl
 __global__ void __launch_bounds__(ROW_THREADS) k_gradient(const int32_t* __restrict__ faces, const float* __restrict__ phi,
                                                            float* __restrict__ gx, float* __restrict__ gy,
                                                            float* __restrict__ gz, int64_t P, float inv2h) {
+    pdl_enter();
     write_far(gx, 0.0f, 0.0f);
     write_far(gy, 0.0f, 0.0f);
     write_far(gz, 0.0f, 0.0f);
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(IW_WARPS * 32, SG_IW_MIN_CTAS) k_kernel_integr
                                                                      const int32_t* __restrict__ body,
                                                                      const float* __restrict__ ieps_b,
                                                                      int ieps_stride) {
+    pdl_enter();
     __shared__ __align__(16) float s_H[IW_WARPS][2][TILE_N];
     __shared__ int s_nb[IW_WARPS][2][32];  // rows of 27, padded: the two packages' rows start on bank 0
     if (!BATCH) {
@@ -300,9 +302,7 @@ cudaError_t launch_set_far(float* f, float v_in, float v_out, cudaStream_t s) {
 cudaError_t launch_gradient(const GridF& G, const int32_t* faces, const float* phi, float* gx, float* gy, float* gz,
                             int64_t P, cudaStream_t s) {
     if (P <= 2) return cudaSuccess;
-    k_gradient<<<row_blocks(P), ROW_THREADS, 0, s>>>(faces, phi, gx, gy, gz, P, (float)(1.0 / (2.0 * G.h_d)));
-    note_launch();
-    return cudaGetLastError();
+    return launch_pdl(k_gradient, row_blocks(P), ROW_THREADS, 0, s, faces, phi, gx, gy, gz, P, (float)(1.0 / (2.0 * G.h_d)));
 }
 
 cudaError_t launch_laplacian(const GridF& G, const int32_t* faces, const float* phi, float* lap, int64_t P,
@@ -366,11 +366,11 @@ cudaError_t launch_kernel_integrals(const GridF& G, const int32_t* nbr, const fl
         k_kernel_integrals_wide<<<pkg_blocks(P), SW_THREADS, 0, s>>>(nbr, phi, W, gx, gy, gz, P, kernel_coef(R),
                                                                       (float)(1.0 / eps));
     else if (P < ((int64_t)1 << 24) && !force_wide_offsets())  // byte offsets of every field fit 32 bits
-        k_kernel_integrals<true, false><<<integrals_grid(P), IW_WARPS * 32, 0, s>>>(
-            nbr, phi, W, gx, gy, gz, P, kernel_coef(R), (float)(1.0 / eps), nullptr, nullptr, nullptr, 0);
+        return launch_pdl(k_kernel_integrals<true, false>, integrals_grid(P), IW_WARPS * 32, 0, s, nbr, phi, W, gx, gy, gz,
+                          P, kernel_coef(R), (float)(1.0 / eps), nullptr, nullptr, nullptr, 0);
     else
-        k_kernel_integrals<false, false><<<integrals_grid(P), IW_WARPS * 32, 0, s>>>(
-            nbr, phi, W, gx, gy, gz, P, kernel_coef(R), (float)(1.0 / eps), nullptr, nullptr, nullptr, 0);
+        return launch_pdl(k_kernel_integrals<false, false>, integrals_grid(P), IW_WARPS * 32, 0, s, nbr, phi, W, gx, gy,
+                          gz, P, kernel_coef(R), (float)(1.0 / eps), nullptr, nullptr, nullptr, 0);
     note_launch();
     return cudaGetLastError();
 }

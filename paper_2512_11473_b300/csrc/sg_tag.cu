@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(TAG_THREADS) k_tag_inner(GridFF G, uint8_t* __
                                                             const uint32_t* __restrict__ core,
                                                             uint32_t* __restrict__ act, uint32_t* __restrict__ count,
                                                             int64_t nc) {
+    pdl_enter();
     const int nx = G.dims[0], ny = G.dims[1], nz = G.dims[2];
     const int64_t nw = (nc + 31) >> 5, plane = (int64_t)nx * ny;
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
@@ -221,6 +222,7 @@ __global__ void __launch_bounds__(TAG_THREADS) k_tag_scatter(const uint8_t* __re
 __global__ void __launch_bounds__(TAG_THREADS) k_fill_nbr(GridFF G, const int32_t* __restrict__ cell_pkg,
                                                            const int32_t* __restrict__ pkg_cell,
                                                            int32_t* __restrict__ nbr, int64_t P) {
+    pdl_enter();
     const int nx = G.dims[0], ny = G.dims[1], nz = G.dims[2];
     const int64_t total = P * 9;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -248,6 +250,7 @@ __global__ void __launch_bounds__(TAG_THREADS) k_fill_nbr(GridFF G, const int32_
 // Compact face table: entries 12, 14, 10, 16, 4, 22 of each neighbourhood.
 __global__ void __launch_bounds__(TAG_THREADS) k_fill_faces(const int32_t* __restrict__ nbr,
                                                              int32_t* __restrict__ faces, int64_t P) {
+    pdl_enter();
     const int face_n[8] = {12, 14, 10, 16, 4, 22, -1, -1};
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P * 8;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -310,6 +313,7 @@ __global__ void __launch_bounds__(TAG_THREADS) k_check_tables(GridFF G, const in
 // [0, 4 dims_a), of the three axes in float-float, one after the other:
 // the data points' coordinates, tabulated once per call.
 __global__ void __launch_bounds__(TAG_THREADS) k_coord_table(GridFF G, ff* __restrict__ tab) {
+    pdl_enter();
     const int n0 = 4 * G.dims[0], n1 = 4 * G.dims[1], n = n0 + n1 + 4 * G.dims[2];
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const int a = e < n0 ? 0 : (e < n0 + n1 ? 1 : 2);
@@ -351,6 +355,7 @@ __global__ void __launch_bounds__(TAG_THREADS, K == SHAPE_PRISM ? 4 : 8) k_init_
                                                                const int32_t* __restrict__ pkg_cell,
                                                                const ff* __restrict__ tab, float* __restrict__ phi,
                                                                int64_t P, float F) {
+    pdl_enter();
     write_far(phi, -F, F);
     const int64_t total = (P - 2) * 16;
     const int off[3] = {0, 4 * G.dims[0], 4 * (G.dims[0] + G.dims[1])};
@@ -454,9 +459,8 @@ cudaError_t launch_renumber(const int32_t* order, const int32_t* old_cell, const
 cudaError_t launch_tag_inner(const GridFF& G, uint8_t* cell_type, const uint32_t* core_bits, uint32_t* act_bits,
                              uint32_t* count, int64_t nc, cudaStream_t s) {
     const int64_t nw = (nc + 31) >> 5;
-    k_tag_inner<<<grid_for(nw, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_type, core_bits, act_bits, count, nc);
-    note_launch();
-    return cudaGetLastError();
+    return launch_pdl(k_tag_inner, grid_for(nw, TAG_THREADS), TAG_THREADS, 0, s, G, cell_type, core_bits, act_bits, count,
+                      nc);
 }
 
 cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* act_bits, const uint32_t* prefix,
@@ -469,30 +473,26 @@ cudaError_t launch_tag_scatter(const uint8_t* cell_type, const uint32_t* act_bit
 
 cudaError_t launch_fill_nbr(const GridFF& G, const int32_t* cell_pkg, const int32_t* pkg_cell, int32_t* nbr,
                             int64_t P, cudaStream_t s) {
-    k_fill_nbr<<<grid_for(P * 9, TAG_THREADS), TAG_THREADS, 0, s>>>(G, cell_pkg, pkg_cell, nbr, P);
-    note_launch();
-    return cudaGetLastError();
+    return launch_pdl(k_fill_nbr, grid_for(P * 9, TAG_THREADS), TAG_THREADS, 0, s, G, cell_pkg, pkg_cell, nbr, P);
 }
 
 cudaError_t launch_fill_faces(const int32_t* nbr, int32_t* faces, int64_t P, cudaStream_t s) {
-    k_fill_faces<<<grid_for(P * 8, TAG_THREADS), TAG_THREADS, 0, s>>>(nbr, faces, P);
-    note_launch();
-    return cudaGetLastError();
+    return launch_pdl(k_fill_faces, grid_for(P * 8, TAG_THREADS), TAG_THREADS, 0, s, nbr, faces, P);
 }
 
 cudaError_t launch_init_sdf(const GridFF& G, const ShapeFF& S, const int32_t* pkg_cell, float* phi, float F,
                             int64_t P, void* table, cudaStream_t s) {
     if (P <= 2) return launch_set_far(phi, -F, F, s);  // otherwise the init kernel writes the far packages
     const int n = 4 * (G.dims[0] + G.dims[1] + G.dims[2]);
-    k_coord_table<<<(n + TAG_THREADS - 1) / TAG_THREADS, TAG_THREADS, 0, s>>>(G, (ff*)table);
-    note_launch();
+    cudaError_t e = launch_pdl(k_coord_table, (n + TAG_THREADS - 1) / TAG_THREADS, TAG_THREADS, 0, s, G, (ff*)table);
+    if (e != cudaSuccess) return e;
     const ff* tab = (const ff*)table;
     if (S.plain && S.kind == SHAPE_TORUS)
-        k_init_sdf_col<SHAPE_TORUS><<<grid_for((P - 2) * 16, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, pkg_cell, tab,
-                                                                                              phi, P, F);
-    else if (S.plain && S.kind == SHAPE_PRISM)
-        k_init_sdf_col<SHAPE_PRISM><<<grid_for((P - 2) * 16, TAG_THREADS), TAG_THREADS, 0, s>>>(G, S, pkg_cell, tab,
-                                                                                              phi, P, F);
+        return launch_pdl(k_init_sdf_col<SHAPE_TORUS>, grid_for((P - 2) * 16, TAG_THREADS), TAG_THREADS, 0, s, G, S,
+                          pkg_cell, tab, phi, P, F);
+    if (S.plain && S.kind == SHAPE_PRISM)
+        return launch_pdl(k_init_sdf_col<SHAPE_PRISM>, grid_for((P - 2) * 16, TAG_THREADS), TAG_THREADS, 0, s, G, S,
+                          pkg_cell, tab, phi, P, F);
     else
         SG_SHAPE_DISPATCH(S.kind, (k_init_sdf<K><<<grid_for((P - 2) * PKG3, TAG_THREADS), TAG_THREADS, 0, s>>>(
                                       G, S, pkg_cell, tab, phi, P, F)));
