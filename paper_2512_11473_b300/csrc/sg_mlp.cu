@@ -40,6 +40,7 @@ struct sg_mlp {
     int64_t part_ctas = 0;
     int* err = nullptr;  // device error word (ERR_TIMEOUT)
     int64_t step = 0;
+    bool train_smem_set = false;  // the training kernel's shared-memory limit raised on this device
     std::string last_error;
 };
 
@@ -85,32 +86,73 @@ __global__ void k_mlp_pack(const float* __restrict__ master, unsigned char* __re
     if (k < MLP_NPARAM) pack_param(k, master[k], packed);
 }
 
-// Sum of the per-CTA partials in CTA order: the gradient (and loss) of the
+// Sums of the per-CTA partials in CTA order: the gradient (and loss) of the
 // whole batch, independent of scheduling.
-__global__ void k_mlp_grad_sum(const float* __restrict__ part, int ctas, float* __restrict__ grad,
-                               float* __restrict__ loss) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < MLP_NPARAM) {
-        float g = 0.0f;
-        for (int c = 0; c < ctas; ++c) g += part[(int64_t)c * MLP_NPARAM + k];
-        grad[k] = g;
+//
+// Sum over c = 0 .. n-1 of a[c * stride], added in order of c, by the four
+// lanes of an aligned lane quad: for each block of 128 terms, lane j of the
+// quad loads terms 32 j .. 32 j + 31 (all 32 in flight at once), then lane 0
+// adds its terms to the running sum, hands it to lane 1 by a shuffle, and so
+// on: the same additions in the same order as one thread walking c = 0 .. n-1,
+// with one memory latency per 128 terms.  Every lane of the warp must call it
+// (with `active` false for quads without a sum); every lane of a quad gets
+// the sum.
+__device__ __forceinline__ float ordered_sum_quad(const float* __restrict__ a, int n, int64_t stride, bool active) {
+    const int lane = threadIdx.x & 31, j = lane & 3, base = lane & ~3;
+    float s = 0.0f;
+    for (int c0 = 0; c0 < n; c0 += 128) {
+        float q[32];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+            const int c = c0 + 32 * j + u;
+            q[u] = (active && c < n) ? a[(int64_t)c * stride] : 0.0f;
+        }
+#pragma unroll
+        for (int st = 0; st < 4; ++st) {
+            if (j == st) {
+#pragma unroll
+                for (int u = 0; u < 32; ++u)
+                    if (c0 + 32 * st + u < n) s += q[u];
+            }
+            s = __shfl_sync(0xffffffffu, s, base + st);
+        }
     }
-    if (k == 0 && loss) {
-        float l = 0.0f;
-        for (int c = 0; c < ctas; ++c) l += part[(int64_t)ctas * MLP_NPARAM + c];
-        *loss = l;
+    return s;
+}
+
+// Threads of the partial-sum kernels: a lane quad per parameter.
+constexpr int SUM_THREADS = 256;
+inline unsigned sum_blocks() { return (unsigned)((4 * MLP_NPARAM + SUM_THREADS - 1) / SUM_THREADS); }
+
+// The loss: the CTAs' loss shares in CTA order, by warp 0 of CTA 0.
+__device__ __forceinline__ void sum_loss(const float* __restrict__ part, int ctas, float* __restrict__ loss) {
+    if (loss && blockIdx.x == 0 && threadIdx.x < 32) {
+        const float l = ordered_sum_quad(part + (int64_t)ctas * MLP_NPARAM, ctas, 1, true);
+        if (threadIdx.x == 0) *loss = l;
     }
+}
+
+// The gradient and loss of the batch (sg_mlp_loss_grad).
+__global__ void __launch_bounds__(SUM_THREADS) k_mlp_grad_sum(const float* __restrict__ part, int ctas,
+                                                              float* __restrict__ grad, float* __restrict__ loss) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x, k = e >> 2;
+    const bool act = k < MLP_NPARAM;
+    const float g = ordered_sum_quad(part + (act ? k : 0), ctas, MLP_NPARAM, act);
+    if (act && (e & 3) == 0) grad[k] = g;
+    sum_loss(part, ctas, loss);
 }
 
 // Ordered sum of the partials, bias-corrected Adam step on the master
 // weights, repacking of the BF16 copy.
-__global__ void k_mlp_adam(const float* __restrict__ part, int ctas, float* __restrict__ master, float* __restrict__ m,
-                           float* __restrict__ v, unsigned char* __restrict__ packed, float lr, float beta1,
-                           float beta2, float eps, float c1, float c2, float* __restrict__ loss) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < MLP_NPARAM) {
-        float g = 0.0f;
-        for (int c = 0; c < ctas; ++c) g += part[(int64_t)c * MLP_NPARAM + k];
+__global__ void __launch_bounds__(SUM_THREADS) k_mlp_adam(const float* __restrict__ part, int ctas,
+                                                          float* __restrict__ master, float* __restrict__ m,
+                                                          float* __restrict__ v, unsigned char* __restrict__ packed,
+                                                          float lr, float beta1, float beta2, float eps, float c1,
+                                                          float c2, float* __restrict__ loss) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x, k = e >> 2;
+    const bool act = k < MLP_NPARAM;
+    const float g = ordered_sum_quad(part + (act ? k : 0), ctas, MLP_NPARAM, act);
+    if (act && (e & 3) == 0) {
         const float mk = beta1 * m[k] + (1.0f - beta1) * g;
         const float vk = beta2 * v[k] + (1.0f - beta2) * g * g;
         m[k] = mk;
@@ -119,11 +161,7 @@ __global__ void k_mlp_adam(const float* __restrict__ part, int ctas, float* __re
         master[k] = w;
         pack_param(k, w, packed);
     }
-    if (k == 0 && loss) {
-        float l = 0.0f;
-        for (int c = 0; c < ctas; ++c) l += part[(int64_t)ctas * MLP_NPARAM + c];
-        *loss = l;
-    }
+    sum_loss(part, ctas, loss);
 }
 
 // ---------------------------------------------------------------------------
@@ -141,6 +179,11 @@ struct Tc {
 };
 
 __device__ __forceinline__ int tc_row() { return threadIdx.x & (TC_ROWS - 1); }
+
+// The thread that issues the group's products: the group's first thread, or
+// thread 0 when the whole CTA (of one or more warpgroups on the same rows)
+// works one tile.
+__device__ __forceinline__ bool tc_issuer(const Tc& t) { return t.group < 0 ? threadIdx.x == 0 : tc_row() == 0; }
 
 __device__ __forceinline__ void tc_sync(const Tc& t) {
     if (t.group < 0)
@@ -194,7 +237,7 @@ __device__ __forceinline__ void tc_publish(const Tc& t) {
 // commits.
 __device__ __forceinline__ void tc_gemm(const Tc& t, uint32_t tcol, const unsigned char* A, const unsigned char* B,
                                         int K, int N) {
-    if (tc_row() == 0) {
+    if (tc_issuer(t)) {
         umma::fence_after_sync();
         const uint32_t id = umma::idesc_bf16(TC_ROWS, N), sa = umma::smem_u32(A), sb = umma::smem_u32(B);
         for (int k = 0; k < K; k += 16)
@@ -216,7 +259,7 @@ __device__ __forceinline__ bool tc_wait(Tc& t) {
 // first wait (bounded) for the group's product still in flight and raise
 // ERR_TIMEOUT.
 __device__ __forceinline__ void tc_end(Tc& t, uint32_t slot_base, uint32_t ncols, int* err) {
-    if (!t.ok && tc_row() == 0) {
+    if (!t.ok && tc_issuer(t)) {
         umma::mbar_wait(t.bar, t.phase, WAIT_POLLS);
         if (err) atomicOr(err, ERR_TIMEOUT);
     }
@@ -240,19 +283,22 @@ __device__ __forceinline__ void tc_ld32(const Tc& t, int col, float (&v)[32]) {
     for (int i = 0; i < 16; ++i) v[i] = a[i], v[16 + i] = b[i];
 }
 
-// Hidden layer out of TMEM: row r of the 64 columns at tcol, plus bias,
-// SiLU, rounded to BF16 into the K-major operand A ([128][64]).
-__device__ __forceinline__ void tc_hidden(const Tc& t, int tcol, const float* bias, unsigned char* A) {
+// Hidden layer out of TMEM: row r of the 32 columns of half h at tcol, plus
+// bias, SiLU, rounded to BF16 into the K-major operand A ([128][64]).
+__device__ __forceinline__ void tc_hidden_half(const Tc& t, int tcol, const float* bias, unsigned char* A, int h) {
     const int r = tc_row();
+    float v[32];
+    tc_ld32(t, tcol + 32 * h, v);
+    silu32_bias(v, bias + 32 * h);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        float v[32];
-        tc_ld32(t, tcol + 32 * h, v);
-        silu32_bias(v, bias + 32 * h);
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(A + umma::kmajor_byte(r, 32 * h + 8 * q, MLP_H)) = umma::pack8_bf16(v + 8 * q);
+}
+
+// Both halves (the 64 columns) by this thread.
+__device__ __forceinline__ void tc_hidden(const Tc& t, int tcol, const float* bias, unsigned char* A) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<uint4*>(A + umma::kmajor_byte(r, 32 * h + 8 * q, MLP_H)) = umma::pack8_bf16(v + 8 * q);
-    }
+    for (int h = 0; h < 2; ++h) tc_hidden_half(t, tcol, bias, A, h);
 }
 
 // The three layers of one 128-row tile: T holds the K-major input rows
@@ -339,14 +385,114 @@ __device__ __forceinline__ float get_bf16(const unsigned char* base, uint32_t by
     return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(base + byte));
 }
 
+// The threads of the training kernel: TR_GROUPS warpgroups work the same 128
+// rows (thread r of each: row r, in the TMEM lane quarter of its warp).
+// Every epilogue over 64 columns is split between the groups, group g
+// taking columns TR_CW g .. TR_CW g + TR_CW - 1, so each thread's serial chain
+// of TMEM loads, SiLU and operand stores is 1 / TR_GROUPS as long as with one
+// thread per row.  Every value is formed by the same operations whatever the
+// split.
+constexpr int TR_GROUPS = 4;  // (two groups: 18.7 us per batch of 16384 against 18.4 us)
+constexpr int TR_THREADS = TR_GROUPS * TC_ROWS;
+constexpr int TR_CW = MLP_H / TR_GROUPS;
+static_assert(TR_GROUPS >= 2 && TR_CW % 16 == 0, "column split of the training epilogues");
+
+// N consecutive accumulator columns of this thread's row (N a multiple of 16).
+template <int N>
+__device__ __forceinline__ void tc_ldn(const Tc& t, int col, float (&v)[N]) {
+#pragma unroll
+    for (int c = 0; c < N; c += 16) {
+        float a[16];
+        umma::tmem_ld16(lane_col(t, col + c), a);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[c + i] = a[i];
+    }
+    umma::tmem_wait_ld();
+}
+
+// v[i] = silu_(v[i] + bias[i]) for N consecutive columns (the pairs of
+// silu32_bias: the same bits)
+template <int N>
+__device__ __forceinline__ void silu_bias_n(float (&v)[N], const float* bias) {
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+        const float2 s = silu2_bias(make_float2(v[i], v[i + 1]), *reinterpret_cast<const float2*>(bias + i));
+        v[i] = s.x;
+        v[i + 1] = s.y;
+    }
+}
+
+// Copy `bytes` (a multiple of 16) from global to shared memory with up to
+// eight 16-byte loads per thread in flight.
+__device__ __forceinline__ void stage_bytes_ahead(unsigned char* dst, const unsigned char* __restrict__ src, int bytes) {
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    const int n = bytes / 16;
+    for (int b = threadIdx.x; b < n; b += 8 * blockDim.x) {
+        uint4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = b + u * (int)blockDim.x;
+            if (i < n) v[u] = __ldg(s + i);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = b + u * (int)blockDim.x;
+            if (i < n) d[i] = v[u];
+        }
+    }
+}
+
+// The gradient product's output rows (hidden units) m against columns
+// C0 .. C0 + 15: row m < 64 is unit m of layer 1 (columns: the inputs, the
+// ones column for the bias), row m >= 64 unit m - 64 of layer 2 (columns
+// K1 .. K1 + 63: the layer-1 activations).
+template <int C0>
+__device__ __forceinline__ void grad_chunk(const Tc& t, int m, float* __restrict__ pg) {
+    float v[16];
+    tc_ldn<16>(t, TM_G + C0, v);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int c = C0 + i;
+        if (m < MLP_H) {
+            if (c < MLP_IN) pg[MLP_OFF_W1 + m * MLP_IN + c] = v[i];
+            if (c == ONES) pg[MLP_OFF_B1 + m] = v[i];
+        } else {
+            if (c >= MLP_K1) pg[MLP_OFF_W2 + (m - MLP_H) * MLP_H + (c - MLP_K1)] = v[i];
+            if (c == ONES) pg[MLP_OFF_B2 + (m - MLP_H)] = v[i];
+        }
+    }
+    if (MLP_SPLIT && m < MLP_H) {
+        // columns 27..53 carry the low parts of the same inputs
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int c = C0 + i;
+            if (c >= MLP_IN && c < 2 * MLP_IN) pg[MLP_OFF_W1 + m * MLP_IN + (c - MLP_IN)] += v[i];
+        }
+    }
+}
+
+// Chunk q (columns 16 q .. 16 q + 15) of the gradient product.
+__device__ __forceinline__ void grad_chunk_q(const Tc& t, int q, int m, float* __restrict__ pg) {
+    static_assert(NG == 96, "six 16-column chunks of the gradient product");
+    switch (q) {
+        case 0: grad_chunk<0>(t, m, pg); break;
+        case 1: grad_chunk<16>(t, m, pg); break;
+        case 2: grad_chunk<32>(t, m, pg); break;
+        case 3: grad_chunk<48>(t, m, pg); break;
+        case 4: grad_chunk<64>(t, m, pg); break;
+        default: grad_chunk<80>(t, m, pg); break;
+    }
+}
+
 // Gradient of L = scale * sum over rows and outputs of (y - t)^2 for rows
 // idx[0..n) (or 0..n): CTA c writes part[c][MLP_NPARAM] and its loss share
 // part[gridDim.x * MLP_NPARAM + c].
-__global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* __restrict__ packed, int64_t n,
-                                                           const __nv_bfloat16* __restrict__ x,
-                                                           const float* __restrict__ tgt,
-                                                           const int32_t* __restrict__ idx, float scale,
-                                                           float* __restrict__ part, int* err) {
+__global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(const unsigned char* __restrict__ packed, int64_t n,
+                                                              const __nv_bfloat16* __restrict__ x,
+                                                              const float* __restrict__ tgt,
+                                                              const int32_t* __restrict__ idx, float scale,
+                                                              float* __restrict__ part, int* err) {
     using umma::kmajor_byte;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
@@ -356,24 +502,36 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* _
     unsigned char *X = smem + TR_X, *A1 = smem + TR_A1, *A2 = smem + TR_A2, *DY = smem + TR_DY,
                   *DZ2 = smem + TR_DZ2, *AG = smem + TR_AG, *BG = smem + TR_BG;
     float* red = reinterpret_cast<float*>(smem + TR_RED);
-    stage_bytes(smem, packed, PK_BYTES);
-    const int r = threadIdx.x;
+    const int r = tc_row();
+    const int g = threadIdx.x / TC_ROWS;  // warpgroup: columns TR_CW g ..
+    const int cg = TR_CW * g;
     const int64_t row = (int64_t)blockIdx.x * TC_ROWS + r;
     const bool valid = row < n;
     const int64_t src = valid ? (idx ? (int64_t)__ldg(idx + row) : row) : 0;
-    // inputs: X (K-major rows) and X^T (rows 0..K1-1 of the gradient product's B; row ONES = 1)
+    // the row's targets, read ahead for the loss (group 0)
+    float tv[MLP_OUT];
+#pragma unroll
+    for (int o = 0; o < MLP_OUT; ++o) tv[o] = (g == 0 && valid) ? __ldg(tgt + src * MLP_OUT + o) : 0.0f;
+    stage_bytes_ahead(smem, packed, PK_BYTES);
+    // inputs: X (K-major rows, group 0) and X^T (rows 0..K1-1 of the gradient
+    // product's B, shared by the other groups; row ONES = 1)
     {
         __align__(16) __nv_bfloat16 xr[MLP_K1];
 #pragma unroll
         for (int c = 0; c < MLP_K1 / 8; ++c) {
             const uint4 v = valid ? __ldg(reinterpret_cast<const uint4*>(x + src * MLP_K1) + c) : make_uint4(0, 0, 0, 0);
-            *reinterpret_cast<uint4*>(X + kmajor_byte(r, 8 * c, MLP_K1)) = v;
-            *reinterpret_cast<uint4*>(xr + 8 * c) = v;
+            if (g == 0)
+                *reinterpret_cast<uint4*>(X + kmajor_byte(r, 8 * c, MLP_K1)) = v;
+            else
+                *reinterpret_cast<uint4*>(xr + 8 * c) = v;
         }
+        if (g > 0) {
 #pragma unroll
-        for (int c = 0; c < MLP_K1; ++c)
-            *reinterpret_cast<__nv_bfloat16*>(BG + kmajor_byte(c, r, TC_ROWS)) =
-                c == ONES ? __float2bfloat16_rn(1.0f) : xr[c];
+            for (int c = 0; c < MLP_K1; ++c)
+                if (c % (TR_GROUPS - 1) == g - 1)
+                    *reinterpret_cast<__nv_bfloat16*>(BG + kmajor_byte(c, r, TC_ROWS)) =
+                        c == ONES ? __float2bfloat16_rn(1.0f) : xr[c];
+        }
     }
     Tc t = tc_begin(&bar, &slot, 256);
     const uint32_t tbase = t.tmem;
@@ -383,27 +541,33 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* _
         tc_publish(t);
         tc_gemm(t, TM_Z1, X, W + PK_W1, MLP_K1, MLP_H);
         if (!tc_wait(t)) break;
+        {
+            float v[TR_CW];
+            tc_ldn<TR_CW>(t, TM_Z1 + cg, v);
+            silu_bias_n<TR_CW>(v, bias + cg);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float v[32];
-            tc_ld32(t, TM_Z1 + 32 * h, v);
-            silu32_bias(v, bias + 32 * h);
+            for (int q = 0; q < TR_CW / 8; ++q)
+                *reinterpret_cast<uint4*>(A1 + kmajor_byte(r, cg + 8 * q, MLP_H)) = umma::pack8_bf16(v + 8 * q);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                *reinterpret_cast<uint4*>(A1 + kmajor_byte(r, 32 * h + 8 * q, MLP_H)) = umma::pack8_bf16(v + 8 * q);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) put_bf16(BG, kmajor_byte(MLP_K1 + 32 * h + i, r, TC_ROWS), v[i]);
+            for (int i = 0; i < TR_CW; ++i) put_bf16(BG, kmajor_byte(MLP_K1 + cg + i, r, TC_ROWS), v[i]);
         }
         // layer 2
         tc_publish(t);
         tc_gemm(t, TM_Z2, A1, W + PK_W2, MLP_H, MLP_H);
         if (!tc_wait(t)) break;
-        tc_hidden(t, TM_Z2, bias + MLP_H, A2);
-        // layer 3, loss, dY
+        {
+            float v[TR_CW];
+            tc_ldn<TR_CW>(t, TM_Z2 + cg, v);
+            silu_bias_n<TR_CW>(v, bias + MLP_H + cg);
+#pragma unroll
+            for (int q = 0; q < TR_CW / 8; ++q)
+                *reinterpret_cast<uint4*>(A2 + kmajor_byte(r, cg + 8 * q, MLP_H)) = umma::pack8_bf16(v + 8 * q);
+        }
+        // layer 3, loss, dY (group 0: the 16 output columns)
         tc_publish(t);
         tc_gemm(t, TM_Y, A2, W + PK_W3, MLP_H, MLP_N3);
         if (!tc_wait(t)) break;
-        {
+        if (g == 0) {
             float v[16], dy[16];
             umma::tmem_ld16(lane_col(t, TM_Y), v);
             umma::tmem_wait_ld();
@@ -413,7 +577,7 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* _
 #pragma unroll
             for (int o = 0; o < MLP_OUT; ++o) {
                 if (valid) {
-                    const float e = v[o] + bias[2 * MLP_H + o] - __ldg(tgt + src * MLP_OUT + o);
+                    const float e = v[o] + bias[2 * MLP_H + o] - tv[o];
                     l += e * e * scale;
                     dy[o] = 2.0f * e * scale;
                 }
@@ -427,73 +591,51 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* _
         tc_publish(t);
         tc_gemm(t, TM_DA, DY, W + PK_W3T, MLP_N3, MLP_H);
         if (!tc_wait(t)) break;
+        {
+            float da[TR_CW], z[TR_CW];
+            tc_ldn<TR_CW>(t, TM_DA + cg, da);
+            tc_ldn<TR_CW>(t, TM_Z2 + cg, z);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float da[32], z[32];
-            tc_ld32(t, TM_DA + 32 * h, da);
-            tc_ld32(t, TM_Z2 + 32 * h, z);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const float zz = z[i] + bias[MLP_H + 32 * h + i], s = sigmoidf_(zz);
+            for (int i = 0; i < TR_CW; ++i) {
+                const float zz = z[i] + bias[MLP_H + cg + i], s = sigmoidf_(zz);
                 da[i] *= s * (1.0f + zz * (1.0f - s));
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                *reinterpret_cast<uint4*>(DZ2 + kmajor_byte(r, 32 * h + 8 * q, MLP_H)) = umma::pack8_bf16(da + 8 * q);
+            for (int q = 0; q < TR_CW / 8; ++q)
+                *reinterpret_cast<uint4*>(DZ2 + kmajor_byte(r, cg + 8 * q, MLP_H)) = umma::pack8_bf16(da + 8 * q);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) put_bf16(AG, kmajor_byte(MLP_H + 32 * h + i, r, TC_ROWS), da[i]);
+            for (int i = 0; i < TR_CW; ++i) put_bf16(AG, kmajor_byte(MLP_H + cg + i, r, TC_ROWS), da[i]);
         }
         // dA1 = dZ2 W2, dZ1 = dA1 SiLU'(z1)
         tc_publish(t);
         tc_gemm(t, TM_DA, DZ2, W + PK_W2T, MLP_H, MLP_H);
         if (!tc_wait(t)) break;
+        {
+            float da[TR_CW], z[TR_CW];
+            tc_ldn<TR_CW>(t, TM_DA + cg, da);
+            tc_ldn<TR_CW>(t, TM_Z1 + cg, z);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float da[32], z[32];
-            tc_ld32(t, TM_DA + 32 * h, da);
-            tc_ld32(t, TM_Z1 + 32 * h, z);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const float zz = z[i] + bias[32 * h + i], s = sigmoidf_(zz);
-                put_bf16(AG, kmajor_byte(32 * h + i, r, TC_ROWS), da[i] * (s * (1.0f + zz * (1.0f - s))));
+            for (int i = 0; i < TR_CW; ++i) {
+                const float zz = z[i] + bias[cg + i], s = sigmoidf_(zz);
+                put_bf16(AG, kmajor_byte(cg + i, r, TC_ROWS), da[i] * (s * (1.0f + zz * (1.0f - s))));
             }
         }
         // [dZ1^T; dZ2^T] [X | A1]: dW1, db1 (rows 0..63), dW2, db2 (rows 64..127)
         tc_publish(t);
         tc_gemm(t, TM_G, AG, BG, TC_ROWS, NG);
         if (!tc_wait(t)) break;
-        {
-            const int m = r;  // gradient row: hidden unit m of layer 1, or m - 64 of layer 2
-#pragma unroll
-            for (int c0 = 0; c0 < NG; c0 += 32) {
-                float v[32];
-                tc_ld32(t, TM_G + c0, v);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int c = c0 + i;
-                    if (m < MLP_H) {
-                        if (c < MLP_IN) pg[MLP_OFF_W1 + m * MLP_IN + c] = v[i];
-                        if (c == ONES) pg[MLP_OFF_B1 + m] = v[i];
-                    } else {
-                        if (c >= MLP_K1) pg[MLP_OFF_W2 + (m - MLP_H) * MLP_H + (c - MLP_K1)] = v[i];
-                        if (c == ONES) pg[MLP_OFF_B2 + (m - MLP_H)] = v[i];
-                    }
-                }
-                if (MLP_SPLIT && m < MLP_H) {
-                    // columns 27..53 carry the low parts of the same inputs
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int c = c0 + i;
-                        if (c >= MLP_IN && c < 2 * MLP_IN) pg[MLP_OFF_W1 + m * MLP_IN + (c - MLP_IN)] += v[i];
-                    }
-                }
-            }
+        if (MLP_SPLIT) {
+            // the low-part columns add into entries of several chunks: one thread per row
+            if (g == 0)
+                for (int q = 0; q < NG / 16; ++q) grad_chunk_q(t, q, r, pg);
+        } else {
+            for (int q = g; q < NG / 16; q += TR_GROUPS) grad_chunk_q(t, q, r, pg);
         }
     } while (false);
     __syncthreads();
     if (t.ok) {
         // dW3 = dY^T A2 and db3 on the CUDA cores (4 x 65 sums over the rows, in row order)
-        for (int e = r; e < MLP_OUT * (MLP_H + 1); e += TC_ROWS) {
+        for (int e = threadIdx.x; e < MLP_OUT * (MLP_H + 1); e += TR_THREADS) {
             const int o = e / (MLP_H + 1), i = e % (MLP_H + 1);
             float s = 0.0f;
             for (int k = 0; k < TC_ROWS; ++k) {
@@ -505,7 +647,7 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_train(const unsigned char* _
             else
                 pg[MLP_OFF_B3 + o] = s;
         }
-        if (r == 0) {
+        if (threadIdx.x == 0) {
             float l = 0.0f;
             for (int k = 0; k < TC_ROWS; ++k) l += red[k];
             part[(int64_t)gridDim.x * MLP_NPARAM + blockIdx.x] = l;
@@ -1054,10 +1196,13 @@ bool ensure_part(sg_mlp* m, int64_t ctas) {
 }
 
 cudaError_t launch_train(sg_mlp* m, int64_t n, const void* x, const float* t, const int32_t* idx) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_BYTES);
-    if (e != cudaSuccess) return e;
-    k_mlp_train<<<cdiv(n, TC_ROWS), TC_ROWS, TR_BYTES, m->stream>>>(m->packed, n, (const __nv_bfloat16*)x, t, idx,
-                                                                    1.0f / (float)(n * MLP_OUT), m->part, m->err);
+    if (!m->train_smem_set) {
+        const cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_BYTES);
+        if (e != cudaSuccess) return e;
+        m->train_smem_set = true;
+    }
+    k_mlp_train<<<cdiv(n, TC_ROWS), TR_THREADS, TR_BYTES, m->stream>>>(m->packed, n, (const __nv_bfloat16*)x, t, idx,
+                                                                       1.0f / (float)(n * MLP_OUT), m->part, m->err);
     note_launch();
     return cudaGetLastError();
 }
@@ -1157,7 +1302,7 @@ sg_status sg_mlp_loss_grad(sg_mlp* m, int64_t n, const void* x, const float* t, 
     if (!ensure_part(m, ctas)) return m_fail(m, SG_ERR_OOM, "loss_grad: out of memory");
     cudaError_t e = launch_train(m, n, x, t, idx);
     if (e == cudaSuccess) {
-        k_mlp_grad_sum<<<cdiv(MLP_NPARAM, 256), 256, 0, m->stream>>>(m->part, (int)ctas, grad, loss);
+        k_mlp_grad_sum<<<sum_blocks(), SUM_THREADS, 0, m->stream>>>(m->part, (int)ctas, grad, loss);
         note_launch();
         e = cudaGetLastError();
     }
@@ -1175,7 +1320,7 @@ sg_status sg_mlp_train_step(sg_mlp* m, int64_t batch, const void* x, const float
         m->step += 1;
         const double b1 = 0.9, b2 = 0.999;
         const float c1 = (float)(1.0 - std::pow(b1, (double)m->step)), c2 = (float)(1.0 - std::pow(b2, (double)m->step));
-        k_mlp_adam<<<cdiv(MLP_NPARAM, 256), 256, 0, m->stream>>>(m->part, (int)ctas, m->master, m->m, m->v, m->packed,
+        k_mlp_adam<<<sum_blocks(), SUM_THREADS, 0, m->stream>>>(m->part, (int)ctas, m->master, m->m, m->v, m->packed,
                                                                 lr, (float)b1, (float)b2, 1e-8f, c1, c2, loss);
         note_launch();
         e = cudaGetLastError();

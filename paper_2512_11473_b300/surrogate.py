@@ -86,15 +86,21 @@ def train(net: MLP, X, T, steps=300_000, batch=16384, lr=3e-3, seed=4, log_every
     perm = None
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     hist = []
+    # the step call with its pointers formed once (the loop issues a step in
+    # a few microseconds, below the step's device time)
+    step_fn, h = net._lib.sg_mlp_train_step, net.handle
+    xp, tp, lp = X.data_ptr(), T.data_ptr(), loss.data_ptr()
     t0 = time.perf_counter()
     for s in range(steps):
         b = s % per_epoch
         if b == 0:
             perm = torch.randperm(n, generator=gen, device="cuda").to(torch.int32)
-        idx = perm[b * batch:(b + 1) * batch]
+            pp = perm.data_ptr()
         lr_s = lr * 0.5 * (1.0 + math.cos(math.pi * s / steps))
         want = log_every and (s % log_every == 0 or s == steps - 1)
-        net.train_step(X, T, idx, lr_s, loss if want else None)
+        st = step_fn(h, batch, xp, tp, pp + 4 * b * batch, lr_s, lp if want else None)
+        if st != 0:
+            net._check(st)
         if want:
             hist.append((s, float(loss.item())))
             if log:
