@@ -512,6 +512,11 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(const unsigned char
     float tv[MLP_OUT];
 #pragma unroll
     for (int o = 0; o < MLP_OUT; ++o) tv[o] = (g == 0 && valid) ? __ldg(tgt + src * MLP_OUT + o) : 0.0f;
+    // the row's inputs, read ahead of the weights
+    uint4 xv[MLP_K1 / 8];
+#pragma unroll
+    for (int c = 0; c < MLP_K1 / 8; ++c)
+        xv[c] = valid ? __ldg(reinterpret_cast<const uint4*>(x + src * MLP_K1) + c) : make_uint4(0, 0, 0, 0);
     stage_bytes_ahead(smem, packed, PK_BYTES);
     // inputs: X (K-major rows, group 0) and X^T (rows 0..K1-1 of the gradient
     // product's B, shared by the other groups; row ONES = 1)
@@ -519,7 +524,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(const unsigned char
         __align__(16) __nv_bfloat16 xr[MLP_K1];
 #pragma unroll
         for (int c = 0; c < MLP_K1 / 8; ++c) {
-            const uint4 v = valid ? __ldg(reinterpret_cast<const uint4*>(x + src * MLP_K1) + c) : make_uint4(0, 0, 0, 0);
+            const uint4 v = xv[c];
             if (g == 0)
                 *reinterpret_cast<uint4*>(X + kmajor_byte(r, 8 * c, MLP_K1)) = v;
             else
@@ -536,6 +541,8 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(const unsigned char
     Tc t = tc_begin(&bar, &slot, 256);
     const uint32_t tbase = t.tmem;
     float* pg = part + (int64_t)blockIdx.x * MLP_NPARAM;
+    float s3 = 0.0f;  // this thread's dW3 / db3 sum (the last thread: the loss share)
+    static_assert(TR_THREADS > MLP_OUT * (MLP_H + 1), "one dW3 / db3 sum per thread, and a thread for the loss");
     do {
         // layer 1
         tc_publish(t);
@@ -623,6 +630,27 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(const unsigned char
         // [dZ1^T; dZ2^T] [X | A1]: dW1, db1 (rows 0..63), dW2, db2 (rows 64..127)
         tc_publish(t);
         tc_gemm(t, TM_G, AG, BG, TC_ROWS, NG);
+        // while that product runs: dW3 = dY^T A2 and db3 on the CUDA cores
+        // (4 x 65 sums over the rows in row order, one per thread; stored
+        // below once the product has completed)
+        if (threadIdx.x < MLP_OUT * (MLP_H + 1)) {
+            const int o = threadIdx.x / (MLP_H + 1), i = threadIdx.x % (MLP_H + 1), ia = i < MLP_H ? i : 0;
+#pragma unroll 1
+            for (int k0 = 0; k0 < TC_ROWS; k0 += 16) {
+                float dyv[16], av[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    dyv[u] = get_bf16(DY, kmajor_byte(k0 + u, o, MLP_N3));
+                    av[u] = get_bf16(A2, kmajor_byte(k0 + u, ia, MLP_H));
+                }
+#pragma unroll
+                for (int u = 0; u < 16; ++u) s3 += i < MLP_H ? dyv[u] * av[u] : dyv[u];
+            }
+        } else if (threadIdx.x == TR_THREADS - 1) {
+            // and the CTA's loss share, in row order
+#pragma unroll 16
+            for (int k = 0; k < TC_ROWS; ++k) s3 += red[k];
+        }
         if (!tc_wait(t)) break;
         if (MLP_SPLIT) {
             // the low-part columns add into entries of several chunks: one thread per row
@@ -634,24 +662,14 @@ __global__ void __launch_bounds__(TR_THREADS, 1) k_mlp_train(const unsigned char
     } while (false);
     __syncthreads();
     if (t.ok) {
-        // dW3 = dY^T A2 and db3 on the CUDA cores (4 x 65 sums over the rows, in row order)
-        for (int e = threadIdx.x; e < MLP_OUT * (MLP_H + 1); e += TR_THREADS) {
-            const int o = e / (MLP_H + 1), i = e % (MLP_H + 1);
-            float s = 0.0f;
-            for (int k = 0; k < TC_ROWS; ++k) {
-                const float dy = get_bf16(DY, kmajor_byte(k, o, MLP_N3));
-                s += i < MLP_H ? dy * get_bf16(A2, kmajor_byte(k, i, MLP_H)) : dy;
-            }
+        if (threadIdx.x < MLP_OUT * (MLP_H + 1)) {
+            const int o = threadIdx.x / (MLP_H + 1), i = threadIdx.x % (MLP_H + 1);
             if (i < MLP_H)
-                pg[MLP_OFF_W3 + o * MLP_H + i] = s;
+                pg[MLP_OFF_W3 + o * MLP_H + i] = s3;
             else
-                pg[MLP_OFF_B3 + o] = s;
+                pg[MLP_OFF_B3 + o] = s3;
         }
-        if (threadIdx.x == 0) {
-            float l = 0.0f;
-            for (int k = 0; k < TC_ROWS; ++k) l += red[k];
-            part[(int64_t)gridDim.x * MLP_NPARAM + blockIdx.x] = l;
-        }
+        if (threadIdx.x == TR_THREADS - 1) part[(int64_t)gridDim.x * MLP_NPARAM + blockIdx.x] = s3;
     }
     tc_end(t, tbase, 256, err);
 }
