@@ -936,8 +936,7 @@ unsigned sur_a_grid(int64_t P, int device) {
 // weights, measured 347 against 334 us for one on the h = 0.002 torus (at
 // the 64 registers that four CTAs of two groups allow, the kernel spills)
 constexpr int SB_GROUPS = 1;
-constexpr int SB_POS = PK_FWD_BYTES;                   // canonical input columns [6][27] (see canon_row)
-constexpr int SB_T = SB_POS + 384;                     // tile operands, one per group
+constexpr int SB_T = PK_FWD_BYTES;                     // tile operands, one per group
 constexpr int SB_BYTES = SB_T + SB_GROUPS * TC_ROWS * MLP_H * 2;
 static_assert(SB_T % 128 == 0, "tile alignment");
 
@@ -959,37 +958,69 @@ __device__ __forceinline__ void gather27(const int32_t* __restrict__ nbr, const 
     }
 }
 
-// Canonical input row of a point into the tile operand T (row r); returns
-// the transform code.
-// The reflections are applied to the input index (digit d -> 2 - d on a
-// reversed axis) and only the six permutations are tabled, as the K-major
-// byte offset of the canonical column, col6[perm][n] = kmajor_byte(0,
-// canon_pos(n, 0, perm), K1): 324 bytes of shared memory instead of the 1296
-// of all 48 transforms, which lets a seventh CTA onto each SM.
-static_assert(!MLP_SPLIT, "canon_row writes the inputs' BF16 values only");
-__device__ __forceinline__ int canon_row(const float (&f)[MLP_IN], float inv_h, const uint16_t* col6, unsigned char* T,
-                                         int r) {
-    const int code = canon_code(f[13], f[14], f[12], f[16], f[10], f[22], f[4]);
-    const float sgn = (code & 1) ? -1.0f : 1.0f;
-    const uint16_t* ps = col6 + (code >> 4) * MLP_IN;
-    unsigned char* Tr = T + umma::kmajor_byte(r, 0, MLP_K1);
-    const int fx = (code >> 1) & 1, fy = (code >> 2) & 1, fz = (code >> 3) & 1;
+// In-register moves of a row of 27 values indexed n = x + 3 y + 9 z (slots
+// 27.. untouched).  With `on`, v[m] becomes v[t(m)] for a digit map t that
+// is an involution, so the pairs (m, t(m)) swap; selects, so that v stays
+// in registers.
+__host__ __device__ constexpr int pow3(int a) { return a == 0 ? 1 : 3 * pow3(a - 1); }
+
+// t: digit A -> 2 - digit A (the reflection of axis A)
+template <int A>
+__device__ __forceinline__ void cond_reflect(float (&v)[32], bool on) {
 #pragma unroll
-    for (int c = MLP_SPLIT ? 2 * MLP_IN : MLP_IN; c < MLP_K1; ++c) put_bf16(T, umma::kmajor_byte(r, c, MLP_K1), 0.0f);
-#pragma unroll
-    for (int n = 0; n < MLP_IN; ++n) {
-        const float v = fminf(fmaxf(__fmul_rn(sgn * f[n], inv_h), -1.0f), 1.0f);
-        const int m = n + fx * (2 - 2 * (n % 3)) + fy * 3 * (2 - 2 * ((n / 3) % 3)) + fz * 9 * (2 - 2 * (n / 9));
-        *reinterpret_cast<__nv_bfloat16*>(Tr + ps[m]) = __float2bfloat16_rn(v);
+    for (int m = 0; m < MLP_IN; ++m) {
+        if ((m / pow3(A)) % 3 != 0) continue;
+        const int m2 = m + 2 * pow3(A);
+        const float a = v[m], b = v[m2];
+        v[m] = on ? b : a;
+        v[m2] = on ? a : b;
     }
-    return code;
 }
 
-// K-major byte offsets of the canonical columns of the 27 inputs under the
-// six permutations alone: col6[perm * 27 + n].
-__device__ __forceinline__ void build_col6(uint16_t* col6) {
-    for (int e = threadIdx.x; e < 6 * MLP_IN; e += blockDim.x)
-        col6[e] = (uint16_t)umma::kmajor_byte(0, canon_pos(e % MLP_IN, 0, e / MLP_IN), MLP_K1);
+// t: digits A and B exchanged
+template <int A, int B>
+__device__ __forceinline__ void cond_swap_axes(float (&v)[32], bool on) {
+#pragma unroll
+    for (int m = 0; m < MLP_IN; ++m) {
+        const int da = (m / pow3(A)) % 3, db = (m / pow3(B)) % 3;
+        if (da >= db) continue;
+        const int m2 = m + (db - da) * (pow3(A) - pow3(B));
+        const float a = v[m], b = v[m2];
+        v[m] = on ? b : a;
+        v[m2] = on ? a : b;
+    }
+}
+
+// Which of the conditional axis exchanges (0 1), then (1 2), then (0 1)
+// carry the reflected row to canonical order under each of the six
+// permutations (3 bits per permutation, first exchange in the low bit).
+constexpr uint32_t PERM_EXCHANGES = 0u | 2u << 3 | 4u << 6 | 3u << 9 | 6u << 12 | 7u << 15;
+
+// Canonical input row of a point into the tile operand T (row r); returns
+// the transform code.  The row is put in canonical order in registers (the
+// value of original input n goes to column canon_pos(n, reflections, perm):
+// the reflections, then the permutation as up to three axis exchanges) and
+// written as four 16-byte stores of eight BF16 values (columns 27.. zero).
+static_assert(!MLP_SPLIT && MLP_K1 == 32, "canon_row writes 27 BF16 inputs and 5 zero columns");
+__device__ __forceinline__ int canon_row(const float (&f)[MLP_IN], float inv_h, unsigned char* T, int r) {
+    const int code = canon_code(f[13], f[14], f[12], f[16], f[10], f[22], f[4]);
+    const float sgn = (code & 1) ? -1.0f : 1.0f;
+    float v[MLP_K1];
+#pragma unroll
+    for (int n = 0; n < MLP_IN; ++n) v[n] = fminf(fmaxf(__fmul_rn(sgn * f[n], inv_h), -1.0f), 1.0f);
+#pragma unroll
+    for (int n = MLP_IN; n < MLP_K1; ++n) v[n] = 0.0f;
+    cond_reflect<0>(v, (code >> 1) & 1);
+    cond_reflect<1>(v, (code >> 2) & 1);
+    cond_reflect<2>(v, (code >> 3) & 1);
+    const uint32_t ex = PERM_EXCHANGES >> (3 * (code >> 4));
+    cond_swap_axes<0, 1>(v, ex & 1u);
+    cond_swap_axes<1, 2>(v, ex & 2u);
+    cond_swap_axes<0, 1>(v, ex & 4u);
+#pragma unroll
+    for (int q = 0; q < MLP_K1 / 8; ++q)
+        *reinterpret_cast<uint4*>(T + umma::kmajor_byte(r, 8 * q, MLP_K1)) = umma::pack8_bf16(v + 8 * q);
+    return code;
 }
 
 // Canonical positions of the 27 inputs under each of the 48 (reflection,
@@ -1018,8 +1049,6 @@ __global__ void __launch_bounds__(SB_GROUPS * TC_ROWS) k_sur_b(const int32_t* __
     __shared__ __align__(8) uint64_t bars[SB_GROUPS];
     __shared__ uint32_t slot;
     stage_bytes(smem, packed, PK_FWD_BYTES);
-    uint16_t* pos = reinterpret_cast<uint16_t*>(smem + SB_POS);
-    build_col6(pos);
     Tc t = tc_begin(bars, &slot, 64 * SB_GROUPS, SB_GROUPS > 1 ? SB_GROUPS : 0);  // one group: the whole CTA
     const uint32_t tbase = slot;
     unsigned char* T = smem + SB_T + (t.group > 0 ? t.group : 0) * TC_ROWS * MLP_H * 2;
@@ -1037,7 +1066,7 @@ __global__ void __launch_bounds__(SB_GROUPS * TC_ROWS) k_sur_b(const int32_t* __
             float f[MLP_IN];
             gather27(nbr, phi, q, f);
             const float inv_h = BATCH ? sb[__ldg(body + (q >> 6))].C.inv_h : inv_h0;
-            code = canon_row(f, inv_h, pos, T, r);
+            code = canon_row(f, inv_h, T, r);
         } else {
 #pragma unroll
             for (int c = 0; c < MLP_K1 / 8; ++c)
