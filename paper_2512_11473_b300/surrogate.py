@@ -75,7 +75,7 @@ def collect_samples(n_bodies=500, seed=4, target=20_000_000, p_lo=1e2, p_hi=1e5,
 def train(net: MLP, X, T, steps=300_000, batch=16384, lr=3e-3, seed=4, log_every=0, log=None):
     """Adam with lr * (1 + cos(pi s / steps)) / 2 on seeded random batches
     (epochs of a seeded permutation).  The defaults are the production
-    recipe: 300k steps of 16384 samples (about 9 s on one B300) take the
+    recipe: 300k steps of 16384 samples (about 8 s on one B300) take the
     h = 0.002 torus to a max abs error near 8e-4 after fallback.  Returns
     ([(step, loss)], seconds)."""
     torch = _torch()
