@@ -59,7 +59,8 @@ enum {
     SG_ERR_STATE = 4,    /* call out of order (e.g. a sweep before init) */
     SG_ERR_CAPACITY = 5, /* sizes beyond the supported range */
     SG_ERR_TIMEOUT = 6,  /* a bounded device wait gave up */
-    SG_ERR_DEVICE = 7    /* a kernel reported an inconsistency */
+    SG_ERR_DEVICE = 7,   /* a kernel reported an inconsistency */
+    SG_ERR_IO = 8        /* a file could not be written */
 };
 
 enum {
@@ -368,6 +369,37 @@ SG_API sg_status sg_batch_run(sg_batch *b, const sg_batch_plan *plan);
  * and, when times_ms is not NULL, the mean time of each of the 7 candidates
  * (1,1) (2,1) (2,2) (4,1) (4,2) (8,1) (8,2) in that order.  Leaves phi reset. */
 SG_API sg_status sg_batch_autotune(sg_batch *b, sg_batch_plan *plan, int32_t reps, float *times_ms);
+
+/* The autotuner with a cache file (not in the paper; the batched launch and
+ * its autotuner are this library's).  The key names the GPU (name, SM count,
+ * compute capability), the plan's reinit_iterations and integrals_mode, and
+ * the batch's package count rounded down to a power of two.  When the file
+ * `path` has an entry for the key, its (pkgs_per_item, depth) go into *plan
+ * without a run and *hit (if not NULL) is 1; otherwise the call is
+ * sg_batch_autotune(b, plan, reps, NULL), whose choice is appended to the
+ * file, and *hit is 0.  A missing file is an empty cache.  The file holds
+ * one line "<key> <pkgs_per_item> <depth>" per tuning; the last line of a
+ * key wins; lines that do not parse, or name no candidate, are ignored.
+ * Appends of one short line each are safe between processes sharing the
+ * file.  Errors: those of sg_batch_autotune, SG_ERR_INVALID (null, reps <
+ * 1), SG_ERR_IO (the choice could not be appended; *plan holds it anyway). */
+SG_API sg_status sg_batch_autotune_cached(sg_batch *b, sg_batch_plan *plan, int32_t reps, const char *path,
+                                          int32_t *hit);
+
+/* The cache key of (b, plan) as sg_batch_autotune_cached forms it, into
+ * key[0 .. cap).  Errors: SG_ERR_INVALID, SG_ERR_CUDA, SG_ERR_CAPACITY (cap
+ * too small). */
+SG_API sg_status sg_batch_autotune_key(const sg_batch *b, const sg_batch_plan *plan, char *key, int32_t cap);
+
+/* Host-only access to a cache file (no device needed).  lookup: *found = 1
+ * and the entry's values when the file has a valid line for `key` (the last
+ * one), else *found = 0 (also when the file does not exist).  store: append
+ * "<key> <pkgs_per_item> <depth>"; `key` must be 1..399 characters without
+ * blanks and the pair one of the seven candidates.  Errors: SG_ERR_INVALID,
+ * SG_ERR_IO (store only). */
+SG_API sg_status sg_autotune_cache_lookup(const char *path, const char *key, int32_t *pkgs_per_item, int32_t *depth,
+                                          int32_t *found);
+SG_API sg_status sg_autotune_cache_store(const char *path, const char *key, int32_t pkgs_per_item, int32_t depth);
 
 /* Borrow body `body`'s slice of a batch field (SG_FIELD_PHI, _GX.._GZ, _W,
  * _GWX.._GWZ, _S0: [P_body][64] floats; SG_FIELD_NBR: [P_body][27] global

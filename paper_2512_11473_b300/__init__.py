@@ -20,9 +20,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsg.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "sg.h")
 
-SG_OK, SG_ERR_INVALID, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_STATE, SG_ERR_CAPACITY, SG_ERR_TIMEOUT, SG_ERR_DEVICE = range(8)
+(SG_OK, SG_ERR_INVALID, SG_ERR_OOM, SG_ERR_CUDA, SG_ERR_STATE, SG_ERR_CAPACITY, SG_ERR_TIMEOUT, SG_ERR_DEVICE,
+ SG_ERR_IO) = range(9)
 STATUS_NAMES = ["SG_OK", "SG_ERR_INVALID", "SG_ERR_OOM", "SG_ERR_CUDA", "SG_ERR_STATE", "SG_ERR_CAPACITY",
-                "SG_ERR_TIMEOUT", "SG_ERR_DEVICE"]
+                "SG_ERR_TIMEOUT", "SG_ERR_DEVICE", "SG_ERR_IO"]
 
 FIELDS = {"phi": 0, "gx": 1, "gy": 2, "gz": 3, "W": 4, "Gx": 5, "Gy": 6, "Gz": 7, "lap": 8, "S0": 9}
 INT_FIELDS = {"cell_pkg": (100, "<i4"), "pkg_cell": (101, "<i4"), "pkg_type": (102, "|u1"), "nbr": (103, "<i4")}
@@ -134,6 +135,10 @@ def lib():
         L.sg_batch_reset.argtypes = [vp]
         L.sg_batch_run.argtypes = [vp, C.POINTER(sg_batch_plan)]
         L.sg_batch_autotune.argtypes = [vp, C.POINTER(sg_batch_plan), i32, C.POINTER(C.c_float)]
+        L.sg_batch_autotune_cached.argtypes = [vp, C.POINTER(sg_batch_plan), i32, C.c_char_p, C.POINTER(i32)]
+        L.sg_batch_autotune_key.argtypes = [vp, C.POINTER(sg_batch_plan), C.c_char_p, i32]
+        L.sg_autotune_cache_lookup.argtypes = [C.c_char_p, C.c_char_p, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+        L.sg_autotune_cache_store.argtypes = [C.c_char_p, C.c_char_p, i32, i32]
         L.sg_batch_get_field.argtypes = [vp, i32, i32, C.POINTER(vp), C.POINTER(i64)]
         L.sg_batch_n_packages.argtypes = [vp]
         L.sg_batch_n_packages.restype = i64
@@ -478,6 +483,21 @@ class Batch:
         self._check(self._lib.sg_batch_autotune(self._h, C.byref(plan), int(reps), times))
         return plan, {c: float(times[i]) for i, c in enumerate(BATCH_CANDIDATES)}
 
+    def autotune_cached(self, path, plan=None, reps=3, **kw):
+        """sg_batch_autotune_cached: returns (plan, hit), hit True when the
+        cache file `path` already held this batch's key."""
+        plan = plan if plan is not None else make_plan(**kw)
+        hit = C.c_int32(0)
+        self._check(self._lib.sg_batch_autotune_cached(self._h, C.byref(plan), int(reps), os.fsencode(path),
+                                                       C.byref(hit)))
+        return plan, bool(hit.value)
+
+    def autotune_key(self, plan=None, **kw):
+        plan = plan if plan is not None else make_plan(**kw)
+        buf = C.create_string_buffer(400)
+        self._check(self._lib.sg_batch_autotune_key(self._h, C.byref(plan), buf, 400))
+        return buf.value.decode()
+
     def field(self, body, name):
         torch = _torch()
         p = C.c_void_p()
@@ -709,6 +729,23 @@ def morton_order_noalloc(spec, x, y, z, keys=None, order=None, stream=None):
     if st != SG_OK:
         raise SgError(st, "sg_morton_order_noalloc failed")
     return keys, order
+
+
+def autotune_cache_lookup(path, key):
+    """(pkgs_per_item, depth) of key's entry in an autotuner cache file, or
+    None (sg_autotune_cache_lookup; host only)."""
+    ppi, dep, found = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+    st = lib().sg_autotune_cache_lookup(os.fsencode(path), key.encode(), C.byref(ppi), C.byref(dep), C.byref(found))
+    if st != SG_OK:
+        raise SgError(st, "sg_autotune_cache_lookup failed")
+    return (ppi.value, dep.value) if found.value else None
+
+
+def autotune_cache_store(path, key, pkgs_per_item, depth):
+    """Append an entry to an autotuner cache file (sg_autotune_cache_store; host only)."""
+    st = lib().sg_autotune_cache_store(os.fsencode(path), key.encode(), int(pkgs_per_item), int(depth))
+    if st != SG_OK:
+        raise SgError(st, "sg_autotune_cache_store failed")
 
 
 def version() -> str:

@@ -390,6 +390,7 @@ static sg_status tag_common(sg_grid* g, Flags flags, int64_t* n_packages) {
 extern "C" {
 
 sg_status sg_tag_allocate(sg_grid* g, const sg_shape* shape, int64_t* n_packages) {
+    SG_TRACE("sg_tag_allocate");
     SG_CHECK_GRID(g);
     if (!valid_shape(shape)) return fail(g, SG_ERR_INVALID, "sg_tag_allocate: bad shape");
     DeviceGuard dg(g->device);
@@ -402,6 +403,7 @@ sg_status sg_tag_allocate(sg_grid* g, const sg_shape* shape, int64_t* n_packages
 
 sg_status sg_tag_allocate_from(sg_grid* g, const sg_grid* coarse, const sg_shape* shape, int64_t* n_packages,
                                int64_t* evaluated) {
+    SG_TRACE("sg_tag_allocate_from");
     SG_CHECK_GRID(g);
     if (!coarse || coarse == g) return fail(g, SG_ERR_INVALID, "sg_tag_allocate_from: no coarse layer");
     if (!valid_shape(shape)) return fail(g, SG_ERR_INVALID, "sg_tag_allocate_from: bad shape");
@@ -449,6 +451,7 @@ int32_t sg_multires_layers(const sg_grid_desc* finest, int32_t min_dims) {
 }
 
 sg_status sg_init_sdf(sg_grid* g, const sg_shape* shape) {
+    SG_TRACE("sg_init_sdf");
     SG_CHECK_GRID(g);
     if (!valid_shape(shape)) return fail(g, SG_ERR_INVALID, "sg_init_sdf: bad shape");
     if (g->state < 1) return fail(g, SG_ERR_STATE, "sg_init_sdf: grid not tagged");
@@ -464,6 +467,7 @@ sg_status sg_init_sdf(sg_grid* g, const sg_shape* shape) {
 }
 
 sg_status sg_gradient(sg_grid* g) {
+    SG_TRACE("sg_gradient");
     SG_CHECK_GRID(g);
     if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_gradient: phi not initialised");
     DeviceGuard dg(g->device);
@@ -499,7 +503,10 @@ static sg_status consistency(sg_grid* g, float trust, int64_t* out, unsigned deb
     return SG_OK;
 }
 
-sg_status sg_consistency_correct(sg_grid* g, float trust, int64_t* out) { return consistency(g, trust, out, 0); }
+sg_status sg_consistency_correct(sg_grid* g, float trust, int64_t* out) {
+    SG_TRACE("sg_consistency_correct");
+    return consistency(g, trust, out, 0);
+}
 
 sg_status sg_debug_consistency(sg_grid* g, float trust, int32_t flags, int64_t* out) {
     SG_CHECK_GRID(g);
@@ -521,6 +528,7 @@ sg_status sg_debug_consistency_absent_cta(sg_grid* g, float trust) {
 }
 
 sg_status sg_sequential_update(sg_grid* g, float delta) {
+    SG_TRACE("sg_sequential_update");
     SG_CHECK_GRID(g);
     if (!std::isfinite(delta)) return fail(g, SG_ERR_INVALID, "sg_sequential_update: delta not finite");
     if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_sequential_update: phi not initialised");
@@ -532,6 +540,7 @@ sg_status sg_sequential_update(sg_grid* g, float delta) {
 }
 
 sg_status sg_laplacian(sg_grid* g) {
+    SG_TRACE("sg_laplacian");
     SG_CHECK_GRID(g);
     if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_laplacian: phi not initialised");
     DeviceGuard dg(g->device);
@@ -545,6 +554,7 @@ sg_status sg_laplacian(sg_grid* g) {
 }
 
 sg_status sg_reinit(sg_grid* g, int32_t iterations, float cfl) {
+    SG_TRACE("sg_reinit");
     SG_CHECK_GRID(g);
     if (iterations < 0 || !(cfl > 0.0f) || !std::isfinite(cfl)) return fail(g, SG_ERR_INVALID, "sg_reinit: bad args");
     if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_reinit: phi not initialised");
@@ -582,6 +592,7 @@ sg_status sg_reinit(sg_grid* g, int32_t iterations, float cfl) {
 }
 
 sg_status sg_kernel_integrals(sg_grid* g, int32_t mode, const void* mlp) {
+    SG_TRACE("sg_kernel_integrals");
     SG_CHECK_GRID(g);
     if (!((mode == 0 && mlp == nullptr) || (mode == 1 && mlp != nullptr)))
         return fail(g, SG_ERR_INVALID, "sg_kernel_integrals: mode 0 takes no network, mode 1 needs one");
@@ -610,6 +621,7 @@ sg_status sg_kernel_integrals(sg_grid* g, int32_t mode, const void* mlp) {
 
 sg_status sg_morton_order(sg_grid* g, int64_t n, const float* x, const float* y, const float* z, uint64_t* keys,
                           int32_t* order) {
+    SG_TRACE("sg_morton_order");
     SG_CHECK_GRID(g);
     if (n < 0 || (n > 0 && (!x || !y || !z || !order))) return fail(g, SG_ERR_INVALID, "sg_morton_order: bad args");
     if (n >= (1LL << 31)) return fail(g, SG_ERR_CAPACITY, "sg_morton_order: too many particles");
@@ -625,6 +637,7 @@ sg_status sg_morton_order(sg_grid* g, int64_t n, const float* x, const float* y,
 
 sg_status sg_probe(sg_grid* g, int64_t n, const float* x, const float* y, const float* z, float* phi, float* nx,
                    float* ny, float* nz, float* W, float* Gx, float* Gy, float* Gz, int32_t flags) {
+    SG_TRACE("sg_probe");
     SG_CHECK_GRID(g);
     if (n < 0 || (n > 0 && (!x || !y || !z))) return fail(g, SG_ERR_INVALID, "sg_probe: bad args");
     if (n >= (1LL << 31)) return fail(g, SG_ERR_CAPACITY, "sg_probe: too many particles");
@@ -701,6 +714,7 @@ sg_status sg_get_field(sg_grid* g, int32_t field, void** dev_ptr, int64_t* n_ele
 
 sg_status sg_restore(sg_grid* g, int64_t P, const int32_t* cell_pkg, const int32_t* pkg_cell, const uint8_t* pkg_type,
                      const int32_t* nbr, const float* phi) {
+    SG_TRACE("sg_restore");
     SG_CHECK_GRID(g);
     if (P < 2 || !cell_pkg || !pkg_cell || !pkg_type || !nbr)
         return fail(g, SG_ERR_INVALID, "sg_restore: P < 2 or a null table");
@@ -743,6 +757,7 @@ sg_status sg_restore(sg_grid* g, int64_t P, const int32_t* cell_pkg, const int32
 }
 
 sg_status sg_check_tables(sg_grid* g) {
+    SG_TRACE("sg_check_tables");
     SG_CHECK_GRID(g);
     if (g->state < 1) return fail(g, SG_ERR_STATE, "sg_check_tables: grid not tagged");
     DeviceGuard dg(g->device);

@@ -16,8 +16,10 @@
 // relaxation): particles of all bodies, stored body after body, are probed
 // and displaced by one kernel per step; the sweeps and every step are
 // captured into one graph.
+#include <cctype>
 #include <cmath>
 #include <cstddef>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -507,6 +509,7 @@ using namespace sg;
 extern "C" {
 
 sg_status sg_batch_create(sg_grid* const* grids, int32_t n, void* stream, sg_batch** out) {
+    SG_TRACE("sg_batch_create");
     if (!grids || n < 1 || !out) return SG_ERR_INVALID;
     *out = nullptr;
     int64_t P = 0;
@@ -643,6 +646,7 @@ int64_t sg_batch_n_packages(const sg_batch* b) { return b ? b->P : 0; }
 const char* sg_batch_last_error(const sg_batch* b) { return b ? b->last_error.c_str() : "null batch"; }
 
 sg_status sg_batch_reset(sg_batch* b) {
+    SG_TRACE("sg_batch_reset");
     if (!b) return SG_ERR_INVALID;
     const size_t fb = (size_t)b->P * PKG3 * sizeof(float);
     cudaError_t e = cudaMemcpyAsync(b->phi.p, b->phi0.p, fb, cudaMemcpyDeviceToDevice, b->stream);
@@ -651,6 +655,7 @@ sg_status sg_batch_reset(sg_batch* b) {
 }
 
 sg_status sg_batch_run(sg_batch* b, const sg_batch_plan* plan) {
+    SG_TRACE("sg_batch_run");
     if (!b || !plan) return SG_ERR_INVALID;
     if (!valid_plan(b, plan)) return b_fail(b, SG_ERR_INVALID, "sg_batch_run: bad plan");
     if (plan->integrals_mode == 1 && b->P >= SUR_MAX_PACKAGES)
@@ -688,6 +693,7 @@ sg_status sg_batch_run(sg_batch* b, const sg_batch_plan* plan) {
 }
 
 sg_status sg_batch_autotune(sg_batch* b, sg_batch_plan* plan, int32_t reps, float* times_ms) {
+    SG_TRACE("sg_batch_autotune");
     if (!b || !plan || reps < 1) return SG_ERR_INVALID;
     static const int cand[8][2] = {{1, 1}, {2, 1}, {2, 2}, {4, 1}, {4, 2}, {8, 1}, {8, 2}, {1, 1}};
     float best = INFINITY;
@@ -722,6 +728,81 @@ sg_status sg_batch_autotune(sg_batch* b, sg_batch_plan* plan, int32_t reps, floa
     if (st != SG_OK) return st;
     *plan = best_plan;
     return sg_batch_reset(b);
+}
+
+// Autotuner cache: a text file of lines "<key> <pkgs_per_item> <depth>";
+// the last line of a key wins, lines that do not parse or name no candidate
+// are skipped.
+sg_status sg_autotune_cache_lookup(const char* path, const char* key, int32_t* pkgs_per_item, int32_t* depth,
+                                   int32_t* found) {
+    if (!path || !key || !pkgs_per_item || !depth || !found) return SG_ERR_INVALID;
+    *found = 0;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return SG_OK;  // no cache yet
+    char line[512], k[400];
+    int ppi = 0, dep = 0;
+    while (std::fgets(line, sizeof line, f)) {
+        if (std::sscanf(line, "%399s %d %d", k, &ppi, &dep) != 3 || std::strcmp(k, key) != 0) continue;
+        const bool ok = (ppi == 1 || ppi == 2 || ppi == 4 || ppi == 8) && (dep == 1 || dep == 2) && dep <= ppi;
+        if (!ok) continue;
+        *pkgs_per_item = ppi;
+        *depth = dep;
+        *found = 1;
+    }
+    std::fclose(f);
+    return SG_OK;
+}
+
+sg_status sg_autotune_cache_store(const char* path, const char* key, int32_t pkgs_per_item, int32_t depth) {
+    if (!path || !key || !*key || std::strlen(key) >= 400) return SG_ERR_INVALID;
+    for (const char* c = key; *c; ++c)
+        if (*c == ' ' || *c == '\t' || *c == '\n' || *c == '\r') return SG_ERR_INVALID;
+    if (!(pkgs_per_item == 1 || pkgs_per_item == 2 || pkgs_per_item == 4 || pkgs_per_item == 8) ||
+        !(depth == 1 || depth == 2) || depth > pkgs_per_item)
+        return SG_ERR_INVALID;
+    FILE* f = std::fopen(path, "a");  // one short line per append
+    if (!f) return SG_ERR_IO;
+    const int w = std::fprintf(f, "%s %d %d\n", key, (int)pkgs_per_item, (int)depth);
+    const int c = std::fclose(f);
+    return (w < 0 || c != 0) ? SG_ERR_IO : SG_OK;
+}
+
+sg_status sg_batch_autotune_key(const sg_batch* b, const sg_batch_plan* plan, char* key, int32_t cap) {
+    if (!b || !plan || !key || cap < 1) return SG_ERR_INVALID;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, b->device) != cudaSuccess) {
+        cudaGetLastError();
+        return SG_ERR_CUDA;
+    }
+    std::string name(prop.name);
+    for (char& ch : name)
+        if (!(std::isalnum((unsigned char)ch) || ch == '-' || ch == '.')) ch = '_';
+    int bucket = 0;
+    while (bucket < 62 && ((int64_t)1 << (bucket + 1)) <= b->P) ++bucket;
+    const int n = std::snprintf(key, (size_t)cap, "gpu=%s;sm=%d;cc=%d.%d;sweeps=%d;integrals=%d;packages=2^%d",
+                                name.c_str(), prop.multiProcessorCount, prop.major, prop.minor,
+                                (int)plan->reinit_iterations, (int)plan->integrals_mode, bucket);
+    return (n < 0 || n >= cap) ? SG_ERR_CAPACITY : SG_OK;
+}
+
+sg_status sg_batch_autotune_cached(sg_batch* b, sg_batch_plan* plan, int32_t reps, const char* path, int32_t* hit) {
+    SG_TRACE("sg_batch_autotune_cached");
+    if (!b || !plan || !path || reps < 1) return SG_ERR_INVALID;
+    if (hit) *hit = 0;
+    char key[400];
+    sg_status st = sg_batch_autotune_key(b, plan, key, (int32_t)sizeof key);
+    if (st != SG_OK) return b_fail(b, st, "autotune: cache key");
+    int32_t ppi = 0, dep = 0, found = 0;
+    if ((st = sg_autotune_cache_lookup(path, key, &ppi, &dep, &found)) != SG_OK) return st;
+    if (found) {
+        plan->pkgs_per_item = ppi;
+        plan->depth = dep;
+        if (hit) *hit = 1;
+        return SG_OK;
+    }
+    if ((st = sg_batch_autotune(b, plan, reps, nullptr)) != SG_OK) return st;
+    st = sg_autotune_cache_store(path, key, plan->pkgs_per_item, plan->depth);
+    return st == SG_OK ? SG_OK : b_fail(b, st, std::string("autotune: cannot write the cache file ") + path);
 }
 
 sg_status sg_batch_get_field(sg_batch* b, int32_t body, int32_t field, void** dev_ptr, int64_t* n_elems) {
@@ -775,6 +856,7 @@ sg_status sg_batch_set_surrogate(sg_batch* b, const sg_mlp* m) {
 }
 
 sg_status sg_batch_relax(sg_batch* b, const sg_batch_plan* plan, const sg_relax* r) {
+    SG_TRACE("sg_batch_relax");
     if (!b || !r || !r->offsets || r->n < 0 || r->steps < 0 || !std::isfinite(r->step) || (r->sweeps && !plan))
         return SG_ERR_INVALID;
     if (r->n > 0 && (!r->x || !r->y || !r->z)) return SG_ERR_INVALID;

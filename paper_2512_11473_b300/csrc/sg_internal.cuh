@@ -9,6 +9,33 @@
 #include "sg.h"
 #include "sg_ff.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
+namespace sg {
+// A named NVTX range in the library's own domain ("libsg") around each
+// boundary call that issues work, so that a profiler files every kernel
+// under the call that launched it.  NVTX is header-only: with no tool
+// attached a push and a pop are calls through stubs that do nothing.
+inline nvtxDomainHandle_t trace_domain() {
+    static const nvtxDomainHandle_t d = nvtxDomainCreateA("libsg");
+    return d;
+}
+struct TraceRange {
+    explicit TraceRange(const char* name) {
+        nvtxEventAttributes_t a = {};
+        a.version = NVTX_VERSION;
+        a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+        a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+        a.message.ascii = name;
+        nvtxDomainRangePushEx(trace_domain(), &a);
+    }
+    ~TraceRange() { nvtxDomainRangePop(trace_domain()); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
+}  // namespace sg
+#define SG_TRACE(name) const ::sg::TraceRange sg_trace_range_(name)
+
 namespace sg {
 
 constexpr int PKG = 4;    // data per axis in a package

@@ -1328,6 +1328,7 @@ sg_status sg_mlp_get_params(sg_mlp* m, float* params) {
 }
 
 sg_status sg_mlp_forward(sg_mlp* m, int64_t n, const void* x, float* y) {
+    SG_TRACE("sg_mlp_forward");
     if (!m || n < 0 || (n > 0 && (!x || !y))) return SG_ERR_INVALID;
     if (n == 0) return SG_OK;
     const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
@@ -1344,6 +1345,7 @@ sg_status sg_mlp_forward(sg_mlp* m, int64_t n, const void* x, float* y) {
 
 sg_status sg_mlp_loss_grad(sg_mlp* m, int64_t n, const void* x, const float* t, const int32_t* idx, float* grad,
                            float* loss) {
+    SG_TRACE("sg_mlp_loss_grad");
     if (!m || n < 1 || !x || !t || !grad) return SG_ERR_INVALID;
     const int64_t ctas = (n + TC_ROWS - 1) / TC_ROWS;
     if (!ensure_part(m, ctas)) return m_fail(m, SG_ERR_OOM, "loss_grad: out of memory");
@@ -1359,6 +1361,7 @@ sg_status sg_mlp_loss_grad(sg_mlp* m, int64_t n, const void* x, const float* t, 
 
 sg_status sg_mlp_train_step(sg_mlp* m, int64_t batch, const void* x, const float* t, const int32_t* idx, float lr,
                             float* loss) {
+    SG_TRACE("sg_mlp_train_step");
     if (!m || batch < 1 || !x || !t || !(lr >= 0.0f)) return SG_ERR_INVALID;
     const int64_t ctas = (batch + TC_ROWS - 1) / TC_ROWS;
     if (!ensure_part(m, ctas)) return m_fail(m, SG_ERR_OOM, "train_step: out of memory");
@@ -1379,6 +1382,7 @@ sg_status sg_mlp_train_step(sg_mlp* m, int64_t batch, const void* x, const float
 const char* sg_mlp_last_error(const sg_mlp* m) { return m ? m->last_error.c_str() : "null mlp"; }
 
 sg_status sg_surrogate_classify(sg_grid* g, uint8_t* cls) {
+    SG_TRACE("sg_surrogate_classify");
     if (!g || !cls) return SG_ERR_INVALID;
     if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_surrogate_classify: phi not initialised");
     k_sur_classify<<<cdiv(g->P, SU_PK), SU_THREADS, 0, g->stream>>>((const int32_t*)g->nbr.p,
@@ -1392,6 +1396,7 @@ sg_status sg_surrogate_classify(sg_grid* g, uint8_t* cls) {
 
 sg_status sg_surrogate_samples(sg_grid* g, uint64_t seed, float keep, int64_t cap, void* x_bf16, float* t,
                                int64_t* count) {
+    SG_TRACE("sg_surrogate_samples");
     if (!g || !count || cap < 0 || !(keep >= 0.0f && keep <= 1.0f) || (cap > 0 && (!x_bf16 || !t)))
         return SG_ERR_INVALID;
     if (g->state < 2) return fail(g, SG_ERR_STATE, "sg_surrogate_samples: phi not initialised");
@@ -1430,6 +1435,7 @@ sg_status sg_surrogate_samples(sg_grid* g, uint64_t seed, float keep, int64_t ca
 }
 
 sg_status sg_surrogate_stats(sg_grid* g, int64_t* counts) {
+    SG_TRACE("sg_surrogate_stats");
     if (!g || !counts) return SG_ERR_INVALID;
     if (!g->stats.p) {
         for (int i = 0; i < 4; ++i) counts[i] = 0;

@@ -101,6 +101,29 @@ def test_batch_autotune(sg, setup):
     _check(batch, ref20)
 
 
+def test_batch_autotune_cached(sg, setup, tmp_path):
+    """The first call tunes and appends its choice to the cache file; the
+    second finds it there (no runs) and returns the same plan."""
+    bodies, grids, ref20, _ = setup
+    batch = sg.Batch(grids)
+    path = tmp_path / "tune.txt"
+    key = batch.autotune_key(sg.make_plan(reinit_iterations=20))
+    assert key.startswith("gpu=") and ";sweeps=20;integrals=0;packages=2^" in key and " " not in key
+    p1, hit1 = batch.autotune_cached(path, sg.make_plan(reinit_iterations=20), reps=2)
+    assert not hit1
+    assert (p1.pkgs_per_item, p1.depth) in sg.BATCH_CANDIDATES
+    assert path.read_text().splitlines() == ["%s %d %d" % (key, p1.pkgs_per_item, p1.depth)]
+    assert sg.autotune_cache_lookup(path, key) == (p1.pkgs_per_item, p1.depth)
+    p2, hit2 = batch.autotune_cached(path, sg.make_plan(reinit_iterations=20), reps=2)
+    assert hit2 and (p2.pkgs_per_item, p2.depth) == (p1.pkgs_per_item, p1.depth)
+    assert len(path.read_text().splitlines()) == 1
+    # another sweep count is another key: tuned and appended
+    p3, hit3 = batch.autotune_cached(path, sg.make_plan(reinit_iterations=7), reps=1)
+    assert not hit3 and len(path.read_text().splitlines()) == 2
+    batch.run(p2)
+    _check(batch, ref20)
+
+
 def test_batch_global_neighbour_ids(sg, setup):
     bodies, grids, _, _ = setup
     batch = sg.Batch(grids)
