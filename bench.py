@@ -572,16 +572,22 @@ def relax_section(sg, torch, net, trained, n_particles=100_000_000, steps=50, n_
     batch.close()
     step_ms = relax_ms / steps
     n_out = len(out)
-    # this rank's algorithmic bytes: the probe table packed once (8 fields
-    # read, written), steps before the last (positions read and written, the
-    # four fields phi, g read once), the last step (also its n_out outputs and
-    # all eight fields)
+    # this rank's algorithmic bytes of the call: the probe table packed once
+    # (8 fields read, written), then one launch that takes every particle
+    # through all the steps: positions read and written once, the n_out
+    # outputs written, the fields the steps interpolate (phi, g and, for the
+    # last step's outputs, W, G) read once
     pack_bytes = 64 * 64 * P_act
-    inner_bytes = n_mine * 24 + 16 * 64 * P_act
-    last_bytes = n_mine * (24 + 4 * n_out) + 32 * 64 * P_act
-    alg_total = pack_bytes + (steps - 1) * inner_bytes + last_bytes
+    relax_bytes = n_mine * (24 + 4 * n_out) + 32 * 64 * P_act
+    alg_total = pack_bytes + relax_bytes
     hbm, kind = measured_peaks()
     achieved = alg_total / (relax_ms * 1e-3) / 1e9
+    # the bound: 4-byte gathers served by L1, 32 per particle-step (8 corners
+    # x phi, g; 64 in the last step), against one warp-wide load per SM and
+    # clock (every lane's value in one 128-byte line), 148 SMs at the maximum
+    # SM clock
+    gathers = n_mine * (32 * (steps - 1) + 64)
+    gather_peak = 148 * 32 * 2032e6
     return {"workload": "%d mixed bodies (first %d of the 256-body batch, seed %d), %d particles near their surfaces, "
                         "20 reinit sweeps + surrogate integrals with fallback, %d relaxation steps of 0.1 h, one graph"
                         % (n_bodies, n_bodies, seed, n_particles, steps),
@@ -593,12 +599,15 @@ def relax_section(sg, torch, net, trained, n_particles=100_000_000, steps=50, n_
             "pipeline_particle_steps_per_s": pts * steps / (full_ms * 1e-3),
             "partition": ({"ranks": ws, "rule": "greedy largest-first by target package count, no collective"}
                           if ws > 1 else None),
-            "roofline": {"kernel": "k_batch_relax", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                         "unit": "GB/s", "frac": achieved / hbm, "peak_kind": kind,
-                         "algorithmic_bytes_per_launch": inner_bytes,
-                         "bytes_rule": "over the whole relaxation call: probe table packed once (64 B per point), "
-                                       "each step before the last 24 B per particle + 16 B per point (phi, g), the "
-                                       "last step 24 + 4 x outputs B per particle + 32 B per point"},
+            "roofline": {"kernel": "k_batch_relax", "bound": "l1 gathers",
+                         "achieved": gathers / (relax_ms * 1e-3) / 1e9, "peak": gather_peak / 1e9,
+                         "unit": "Ggathers/s", "frac": gathers / (relax_ms * 1e-3) / gather_peak,
+                         "peak_rule": "one warp-wide 4-byte load per SM and clock: 148 SMs x 32 lanes x 2032 MHz",
+                         "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                                 "peak_kind": kind, "algorithmic_bytes_per_call": alg_total,
+                                 "bytes_rule": "probe table packed once (64 B per point), positions read and written "
+                                               "once (24 B per particle), 4 B per output per particle, 32 B per "
+                                               "point of fields read once"}},
             "max_displacement": moved, "setup_seconds": gen_s}
 
 

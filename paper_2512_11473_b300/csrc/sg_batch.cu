@@ -227,26 +227,32 @@ struct RelaxBody {
 };
 
 constexpr int RX_THREADS = 256;  // particles per tile
-// bounded to 40 registers, six CTAs per SM, without spills (the gathers'
-// latency wants the warps: 10^8-particle step 1.61 ms at 48 registers and
-// five CTAs, 1.57 ms here)
-constexpr int RX_MIN_CTAS = 6;
-constexpr int RX_TILES = 16;     // consecutive tiles a CTA walks
+// Launch bounds of the relaxation kernel (each thread takes its particle
+// through all the steps): three CTAs per SM, 80 registers without spills.
+// 50 steps of 10^8 particles on 64 bodies: 53.4 ms; four CTAs (64
+// registers) 54.1 ms, five (48, spilling) 58.3 ms, six (40, spilling) 65.4
+// ms; one launch per step at six CTAs, 78.5 ms.
+constexpr int RX_MIN_CTAS = 3;
+constexpr int RX_TILES = 16;     // consecutive tiles a CTA walks (4: 54.0 ms at four CTAs per SM)
 
-// One relaxation step for every particle: probe (phi, g and, with NF = 8,
-// the integrals) and move by -step h clip(phi / h, -1, 1) n.  A CTA owns one
-// tile of RX_THREADS consecutive particles of one body; its body is the last
-// whose first tile is at most blockIdx.x.
-template <int NF, bool OFF32>
-// A CTA walks RX_TILES consecutive 256-particle tiles (of one body or of
-// consecutive bodies), so that a warp's successive particles are near each
-// other in the Morton walk and hit the packages L1 holds.
+// `steps` relaxation steps for every particle: each step probes phi and g
+// (and, in the last step with NFL = 8, the integrals) and moves the particle
+// by -step h clip(phi / h, -1, 1) n.  The fields do not change during a call
+// and particles do not interact, so a thread takes its particle through all
+// the steps with the position in registers and writes it back once; every
+// step's arithmetic is that of a step-by-step sweep over all particles, so
+// the positions and outputs are bitwise the same.  A CTA walks RX_TILES
+// consecutive 256-particle tiles (of one body or of consecutive bodies), so
+// that a warp's successive particles are near each other in the Morton walk
+// and hit the packages L1 holds; its first body is the last whose first tile
+// is at most its first tile.
+template <int NFL, bool OFF32>
 __global__ void __launch_bounds__(RX_THREADS, RX_MIN_CTAS) k_batch_relax(const RelaxBody* __restrict__ rb, int nbody,
                                                             int64_t tiles, const int32_t* __restrict__ cells,
                                                             const int32_t* __restrict__ nbr,
                                                             const float* __restrict__ tab,
                                                             float* __restrict__ x, float* __restrict__ y,
-                                                            float* __restrict__ z, ProbeOut out) {
+                                                            float* __restrict__ z, int steps, ProbeOut out) {
     const int64_t t0 = (int64_t)blockIdx.x * RX_TILES, t1 = min(tiles, t0 + RX_TILES);
     int lo = 0, hi = nbody - 1;
     while (lo < hi) {
@@ -261,13 +267,27 @@ __global__ void __launch_bounds__(RX_THREADS, RX_MIN_CTAS) k_batch_relax(const R
         const RelaxBody B = rb[lo];
         const int64_t q = B.first + (t - B.tile0) * RX_THREADS + threadIdx.x;
         if (q >= B.end) continue;
-        const float pos[3] = {x[q], y[q], z[q]};
-        const ProbeAt A = probe_locate(B.lat_c, B.lat_ih, B.dims, cells + B.cells, B.far_out, pos);
+        float pos[3] = {x[q], y[q], z[q]};
         float acc[8];
+        // the steps before the last: phi and g, the move
+        for (int k = 1; k < steps; ++k) {
+            const ProbeAt A = probe_locate(B.lat_c, B.lat_ih, B.dims, cells + B.cells, B.far_out, pos);
+            if (OFF32)
+                probe_interp_packed32<4>(nbr, tab, A, acc);
+            else
+                probe_interp_packed<4>(nbr, tab, A, acc);
+            const float inv = probe_inv_norm(acc);
+            const float m = B.step_h * fminf(fmaxf(acc[0] * B.inv_h, -1.0f), 1.0f);
+            pos[0] = fmaf(-m, acc[1] * inv, pos[0]);
+            pos[1] = fmaf(-m, acc[2] * inv, pos[1]);
+            pos[2] = fmaf(-m, acc[3] * inv, pos[2]);
+        }
+        // the last step: also the outputs asked for
+        const ProbeAt A = probe_locate(B.lat_c, B.lat_ih, B.dims, cells + B.cells, B.far_out, pos);
         if (OFF32)
-            probe_interp_packed32<NF>(nbr, tab, A, acc);
+            probe_interp_packed32<NFL>(nbr, tab, A, acc);
         else
-            probe_interp_packed<NF>(nbr, tab, A, acc);
+            probe_interp_packed<NFL>(nbr, tab, A, acc);
         const float inv = probe_inv_norm(acc);
         const float n0 = acc[1] * inv, n1 = acc[2] * inv, n2 = acc[3] * inv;
         const float m = B.step_h * fminf(fmaxf(acc[0] * B.inv_h, -1.0f), 1.0f);
@@ -278,7 +298,7 @@ __global__ void __launch_bounds__(RX_THREADS, RX_MIN_CTAS) k_batch_relax(const R
         if (out.o[1]) out.o[1][q] = n0;
         if (out.o[2]) out.o[2][q] = n1;
         if (out.o[3]) out.o[3][q] = n2;
-        if (NF == 8) {
+        if (NFL == 8) {
 #pragma unroll
             for (int f = 4; f < 8; ++f)
                 if (out.o[f]) out.o[f][q] = acc[f];
@@ -450,25 +470,21 @@ cudaError_t record_relax(sg_batch* b, const sg_relax& r, int64_t tiles, cudaStre
     cudaError_t e = launch_pack_probe(F, tab, b->P * PKG3, s);
     if (e != cudaSuccess) return e;
     const unsigned ctas = (unsigned)((tiles + RX_TILES - 1) / RX_TILES);
-    // the outputs kept are the last step's: the steps before it interpolate
-    // only what the move needs (phi and g) and write only the positions
-    const ProbeOut none{};
+    // one launch for all the steps; the last step interpolates W, G as well
+    // when they are asked for
     const bool off32 = b->P < ((int64_t)1 << 21) && !force_wide_offsets();  // table offsets in bytes fit 32 bits
-    for (int k = 0; k < r.steps; ++k) {
-        const bool last = k == r.steps - 1;
-        const ProbeOut& ok = last ? o : none;
-        if (last && integ) {
-            if (off32)
-                k_batch_relax<8, true><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, o);
-            else
-                k_batch_relax<8, false><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, o);
-        } else if (off32) {
-            k_batch_relax<4, true><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, ok);
-        } else {
-            k_batch_relax<4, false><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, ok);
-        }
-        note_launch();
+    const int steps = (int)r.steps;
+    if (integ) {
+        if (off32)
+            k_batch_relax<8, true><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, steps, o);
+        else
+            k_batch_relax<8, false><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, steps, o);
+    } else if (off32) {
+        k_batch_relax<4, true><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, steps, o);
+    } else {
+        k_batch_relax<4, false><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, steps, o);
     }
+    note_launch();
     return cudaGetLastError();
 }
 
