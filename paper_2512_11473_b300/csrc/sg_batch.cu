@@ -250,7 +250,7 @@ template <int NFL, bool OFF32>
 __global__ void __launch_bounds__(RX_THREADS, RX_MIN_CTAS) k_batch_relax(const RelaxBody* __restrict__ rb, int nbody,
                                                             int64_t tiles, const int32_t* __restrict__ cells,
                                                             const int32_t* __restrict__ nbr,
-                                                            const float* __restrict__ tab,
+                                                            const float4* __restrict__ tab, int64_t half,
                                                             float* __restrict__ x, float* __restrict__ y,
                                                             float* __restrict__ z, int steps, ProbeOut out) {
     const int64_t t0 = (int64_t)blockIdx.x * RX_TILES, t1 = min(tiles, t0 + RX_TILES);
@@ -273,9 +273,9 @@ __global__ void __launch_bounds__(RX_THREADS, RX_MIN_CTAS) k_batch_relax(const R
         for (int k = 1; k < steps; ++k) {
             const ProbeAt A = probe_locate(B.lat_c, B.lat_ih, B.dims, cells + B.cells, B.far_out, pos);
             if (OFF32)
-                probe_interp_packed32<4>(nbr, tab, A, acc);
+                probe_interp_quad32<4>(nbr, tab, 16u * (uint32_t)half, A, acc);
             else
-                probe_interp_packed<4>(nbr, tab, A, acc);
+                probe_interp_quad<4>(nbr, tab, half, A, acc);
             const float inv = probe_inv_norm(acc);
             const float m = B.step_h * fminf(fmaxf(acc[0] * B.inv_h, -1.0f), 1.0f);
             pos[0] = fmaf(-m, acc[1] * inv, pos[0]);
@@ -285,9 +285,9 @@ __global__ void __launch_bounds__(RX_THREADS, RX_MIN_CTAS) k_batch_relax(const R
         // the last step: also the outputs asked for
         const ProbeAt A = probe_locate(B.lat_c, B.lat_ih, B.dims, cells + B.cells, B.far_out, pos);
         if (OFF32)
-            probe_interp_packed32<NFL>(nbr, tab, A, acc);
+            probe_interp_quad32<NFL>(nbr, tab, 16u * (uint32_t)half, A, acc);
         else
-            probe_interp_packed<NFL>(nbr, tab, A, acc);
+            probe_interp_quad<NFL>(nbr, tab, half, A, acc);
         const float inv = probe_inv_norm(acc);
         const float n0 = acc[1] * inv, n1 = acc[2] * inv, n2 = acc[3] * inv;
         const float m = B.step_h * fminf(fmaxf(acc[0] * B.inv_h, -1.0f), 1.0f);
@@ -465,7 +465,8 @@ cudaError_t record_relax(sg_batch* b, const sg_relax& r, int64_t tiles, cudaStre
     const RelaxBody* rb = (const RelaxBody*)b->relax.p;
     const int32_t* cells = (const int32_t*)b->cells.p;
     const int32_t* nbr = (const int32_t*)b->nbr.p;
-    float* tab = (float*)b->probe_tab.p;
+    float4* tab = (float4*)b->probe_tab.p;
+    const int64_t half = b->P * PKG3;  // the table's second half: W, G
     if (r.steps < 1 || tiles < 1) return cudaSuccess;
     cudaError_t e = launch_pack_probe(F, tab, b->P * PKG3, s);
     if (e != cudaSuccess) return e;
@@ -476,13 +477,13 @@ cudaError_t record_relax(sg_batch* b, const sg_relax& r, int64_t tiles, cudaStre
     const int steps = (int)r.steps;
     if (integ) {
         if (off32)
-            k_batch_relax<8, true><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, steps, o);
+            k_batch_relax<8, true><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z, steps, o);
         else
-            k_batch_relax<8, false><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, steps, o);
+            k_batch_relax<8, false><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z, steps, o);
     } else if (off32) {
-        k_batch_relax<4, true><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, steps, o);
+        k_batch_relax<4, true><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z, steps, o);
     } else {
-        k_batch_relax<4, false><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, r.x, r.y, r.z, steps, o);
+        k_batch_relax<4, false><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z, steps, o);
     }
     note_launch();
     return cudaGetLastError();

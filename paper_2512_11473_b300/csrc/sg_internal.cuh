@@ -298,9 +298,9 @@ size_t sort_scratch_bytes(int64_t n, int key_bits);
 cudaError_t morton_sort(const GridF& G, int64_t n, const float* x, const float* y, const float* z, uint64_t* keys_out,
                         int32_t* order_out, void* scratch, cudaStream_t s, bool identity_out = true,
                         const int** unsorted_out = nullptr, int check_stride = 1);
-// Packed probe table of n_points data points ([P][8][64] floats) from the 8
-// fields.
-cudaError_t launch_pack_probe(const ProbeFields& F, float* tab, int64_t n_points, cudaStream_t s);
+// Point-interleaved probe table of n_points data points from the 8 fields:
+// tab[e] = (phi, gx, gy, gz), tab[n_points + e] = (W, Gx, Gy, Gz).
+cudaError_t launch_pack_probe(const ProbeFields& F, float4* tab, int64_t n_points, cudaStream_t s);
 cudaError_t launch_probe(const GridF& G, const int32_t* cell_pkg, const int32_t* nbr, const ProbeFields& F,
                          int64_t P, int64_t n, const float* x, const float* y, const float* z, const int32_t* order,
                          const int* unsorted, const ProbeOut& out, cudaStream_t s);

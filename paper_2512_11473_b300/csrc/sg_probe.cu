@@ -228,13 +228,12 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_rs_scatter(const KeyT* __rest
     }
 }
 
-// Packed probe table: package p holds its 8 probe fields one after the
-// other, tab[512 p + 64 f + d] = field f at data point d.
-__global__ void __launch_bounds__(PR_THREADS) k_pack_probe(ProbeFields F, float* __restrict__ tab, int64_t n) {
+// Point-interleaved probe table of n data points: tab[e] = (phi, gx, gy,
+// gz) and tab[n + e] = (W, Gx, Gy, Gz) of data point e.
+__global__ void __launch_bounds__(PR_THREADS) k_pack_probe(ProbeFields F, float4* __restrict__ tab, int64_t n) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = e >> 6, d = e & 63;
-#pragma unroll
-        for (int f = 0; f < 8; ++f) tab[p * (8 * PKG3) + f * PKG3 + d] = __ldg(F.f[f] + e);
+        tab[e] = make_float4(__ldg(F.f[0] + e), __ldg(F.f[1] + e), __ldg(F.f[2] + e), __ldg(F.f[3] + e));
+        tab[n + e] = make_float4(__ldg(F.f[4] + e), __ldg(F.f[5] + e), __ldg(F.f[6] + e), __ldg(F.f[7] + e));
     }
 }
 
@@ -397,7 +396,7 @@ cudaError_t morton_sort(const GridF& G, int64_t n, const float* x, const float* 
                                check_stride);
 }
 
-cudaError_t launch_pack_probe(const ProbeFields& F, float* tab, int64_t n_points, cudaStream_t s) {
+cudaError_t launch_pack_probe(const ProbeFields& F, float4* tab, int64_t n_points, cudaStream_t s) {
     if (n_points <= 0) return cudaSuccess;
     k_pack_probe<<<blocks_for(n_points, PR_THREADS), PR_THREADS, 0, s>>>(F, tab, n_points);
     note_launch();

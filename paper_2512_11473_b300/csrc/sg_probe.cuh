@@ -123,13 +123,15 @@ __device__ __forceinline__ void probe_interp32(const int32_t* __restrict__ nbr, 
     }
 }
 
-// The same interpolation from the packed probe table: package p holds its 8
-// fields one after the other, field f of data point d at tab[512 p + 64 f + d],
-// so the 8 loads of a corner share one address and differ by constant
-// offsets.  Same sums in the same order as probe_interp.
+// The same interpolation from the point-interleaved probe table: data
+// point d of package p holds (phi, gx, gy, gz) in tab[64 p + d] and
+// (W, Gx, Gy, Gz) in tab[half + 64 p + d] (half = 64 P), so a corner's first
+// four fields come in one 16-byte load and the other four in a second.
+// Same sums in the same order as probe_interp.
 template <int NF>
-__device__ __forceinline__ void probe_interp_packed(const int32_t* __restrict__ nbr, const float* __restrict__ tab,
-                                                    const ProbeAt& A, float (&acc)[8]) {
+__device__ __forceinline__ void probe_interp_quad(const int32_t* __restrict__ nbr, const float4* __restrict__ tab,
+                                                  int64_t half, const ProbeAt& A, float (&acc)[8]) {
+    static_assert(NF == 4 || NF == 8, "four or eight fields");
     const int32_t* nb = nbr + A.home * NB;
     int up[3], lo[3], hi[3];
 #pragma unroll
@@ -146,18 +148,29 @@ __device__ __forceinline__ void probe_interp_packed(const int32_t* __restrict__ 
         const float w = (a0 ? A.t[0] : 1.0f - A.t[0]) * (a1 ? A.t[1] : 1.0f - A.t[1]) * (a2 ? A.t[2] : 1.0f - A.t[2]);
         const int slot = (a0 ? up[0] : 0) + 3 * (a1 ? up[1] : 0) + 9 * (a2 ? up[2] : 0);
         const int64_t pkg = slot == 0 ? A.home : (int64_t)__ldg(nb + 13 + slot);
-        const float* q = tab + pkg * (8 * PKG3) + (a0 ? hi[0] : lo[0]) + PKG * (a1 ? hi[1] : lo[1]) +
-                         PKG * PKG * (a2 ? hi[2] : lo[2]);
-#pragma unroll
-        for (int f = 0; f < NF; ++f) acc[f] = fmaf(w, __ldg(q + f * PKG3), acc[f]);
+        const float4* q = tab + pkg * PKG3 + (a0 ? hi[0] : lo[0]) + PKG * (a1 ? hi[1] : lo[1]) +
+                          PKG * PKG * (a2 ? hi[2] : lo[2]);
+        const float4 v = __ldg(q);
+        acc[0] = fmaf(w, v.x, acc[0]);
+        acc[1] = fmaf(w, v.y, acc[1]);
+        acc[2] = fmaf(w, v.z, acc[2]);
+        acc[3] = fmaf(w, v.w, acc[3]);
+        if (NF == 8) {
+            const float4 u = __ldg(q + half);
+            acc[4] = fmaf(w, u.x, acc[4]);
+            acc[5] = fmaf(w, u.y, acc[5]);
+            acc[6] = fmaf(w, u.z, acc[6]);
+            acc[7] = fmaf(w, u.w, acc[7]);
+        }
     }
 }
 
-// probe_interp_packed with 32-bit byte offsets into the table (tables of
-// fewer than 2^21 packages).  Same sums in the same order.
+// probe_interp_quad with 32-bit byte offsets into the table (tables of fewer
+// than 2^21 packages; half_bytes = 16 half).  Same sums in the same order.
 template <int NF>
-__device__ __forceinline__ void probe_interp_packed32(const int32_t* __restrict__ nbr, const float* __restrict__ tab,
-                                                      const ProbeAt& A, float (&acc)[8]) {
+__device__ __forceinline__ void probe_interp_quad32(const int32_t* __restrict__ nbr, const float4* __restrict__ tab,
+                                                    uint32_t half_bytes, const ProbeAt& A, float (&acc)[8]) {
+    static_assert(NF == 4 || NF == 8, "four or eight fields");
     const int32_t* nb = nbr + A.home * NB;
     const uint32_t home = (uint32_t)A.home;
     int up[3], lo[3], hi[3];
@@ -175,11 +188,21 @@ __device__ __forceinline__ void probe_interp_packed32(const int32_t* __restrict_
         const float w = (a0 ? A.t[0] : 1.0f - A.t[0]) * (a1 ? A.t[1] : 1.0f - A.t[1]) * (a2 ? A.t[2] : 1.0f - A.t[2]);
         const int slot = (a0 ? up[0] : 0) + 3 * (a1 ? up[1] : 0) + 9 * (a2 ? up[2] : 0);
         const uint32_t pkg = slot == 0 ? home : (uint32_t)__ldg(nb + 13 + slot);
-        const uint32_t off = 4u * (pkg * (8 * PKG3) + (uint32_t)((a0 ? hi[0] : lo[0]) + PKG * (a1 ? hi[1] : lo[1]) +
-                                                                 PKG * PKG * (a2 ? hi[2] : lo[2])));
-        const float* q = reinterpret_cast<const float*>(reinterpret_cast<const char*>(tab) + off);
-#pragma unroll
-        for (int f = 0; f < NF; ++f) acc[f] = fmaf(w, __ldg(q + f * PKG3), acc[f]);
+        const uint32_t off = 16u * (pkg * PKG3 + (uint32_t)((a0 ? hi[0] : lo[0]) + PKG * (a1 ? hi[1] : lo[1]) +
+                                                            PKG * PKG * (a2 ? hi[2] : lo[2])));
+        const char* base = reinterpret_cast<const char*>(tab);
+        const float4 v = __ldg(reinterpret_cast<const float4*>(base + off));
+        acc[0] = fmaf(w, v.x, acc[0]);
+        acc[1] = fmaf(w, v.y, acc[1]);
+        acc[2] = fmaf(w, v.z, acc[2]);
+        acc[3] = fmaf(w, v.w, acc[3]);
+        if (NF == 8) {
+            const float4 u = __ldg(reinterpret_cast<const float4*>(base + (off + half_bytes)));
+            acc[4] = fmaf(w, u.x, acc[4]);
+            acc[5] = fmaf(w, u.y, acc[5]);
+            acc[6] = fmaf(w, u.z, acc[6]);
+            acc[7] = fmaf(w, u.w, acc[7]);
+        }
     }
 }
 
