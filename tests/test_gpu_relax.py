@@ -208,6 +208,18 @@ def test_relax_replay_sweeps_and_empty_bodies(sg, small):
         assert torch.equal(Y[a], Y6[a])
     for k in OUTS:
         assert torch.equal(out[k], o6[k])
+    # and six calls of one step each: a launch per step, against one launch
+    # that takes every particle through the six steps
+    batch.reset()
+    batch.run(plan)
+    Z = [v.clone() for v in X]
+    for _ in range(6):
+        batch.relax(*Z, off, 1, 0.1, sweeps=False, out=out)
+    torch.cuda.synchronize()
+    for a in range(3):
+        assert torch.equal(Z[a], Y6[a])
+    for k in OUTS:
+        assert torch.equal(out[k], o6[k])
     # bodies 1 and 5 without particles: the others move exactly as before
     keep = [b for b in range(len(bodies)) if b not in (1, 5)]
     segs = [(int(off[b]), int(off[b + 1])) for b in keep]
