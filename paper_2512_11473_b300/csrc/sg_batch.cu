@@ -475,15 +475,20 @@ cudaError_t record_relax(sg_batch* b, const sg_relax& r, int64_t tiles, cudaStre
     // when they are asked for
     const bool off32 = b->P < ((int64_t)1 << 21) && !force_wide_offsets();  // table offsets in bytes fit 32 bits
     const int steps = (int)r.steps;
+    const dim3 grid(ctas), block(RX_THREADS);
     if (integ) {
         if (off32)
-            k_batch_relax<8, true><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z, steps, o);
+            k_batch_relax<8, true><<<grid, block, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z,
+                                                          steps, o);
         else
-            k_batch_relax<8, false><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z, steps, o);
+            k_batch_relax<8, false><<<grid, block, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z,
+                                                           steps, o);
     } else if (off32) {
-        k_batch_relax<4, true><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z, steps, o);
+        k_batch_relax<4, true><<<grid, block, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z, steps,
+                                                      o);
     } else {
-        k_batch_relax<4, false><<<ctas, RX_THREADS, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z, steps, o);
+        k_batch_relax<4, false><<<grid, block, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z, steps,
+                                                       o);
     }
     note_launch();
     return cudaGetLastError();
