@@ -228,12 +228,14 @@ struct RelaxBody {
 
 constexpr int RX_THREADS = 256;  // particles per tile
 // Launch bounds of the relaxation kernel (each thread takes its particle
-// through all the steps): three CTAs per SM, 80 registers without spills.
+// through the steps of a launch): three CTAs per SM, 80 registers without
+// spills.
 // 50 steps of 10^8 particles on 64 bodies: 53.4 ms; four CTAs (64
 // registers) 54.1 ms, five (48, spilling) 58.3 ms, six (40, spilling) 65.4
 // ms; one launch per step at six CTAs, 78.5 ms.
 constexpr int RX_MIN_CTAS = 3;
-constexpr int RX_TILES = 16;     // consecutive tiles a CTA walks (4: 54.0 ms at four CTAs per SM)
+constexpr int RX_TILES = 16;      // consecutive tiles a CTA walks (4: 54.0 ms at four CTAs per SM)
+constexpr int RX_MAX_STEPS = 64;  // steps per launch
 
 // `steps` relaxation steps for every particle: each step probes phi and g
 // (and, in the last step with NFL = 8, the integrals) and moves the particle
@@ -471,26 +473,33 @@ cudaError_t record_relax(sg_batch* b, const sg_relax& r, int64_t tiles, cudaStre
     cudaError_t e = launch_pack_probe(F, tab, b->P * PKG3, s);
     if (e != cudaSuccess) return e;
     const unsigned ctas = (unsigned)((tiles + RX_TILES - 1) / RX_TILES);
-    // one launch for all the steps; the last step interpolates W, G as well
-    // when they are asked for
+    // a launch takes every particle through up to RX_MAX_STEPS steps (a
+    // launch of 10^8 particles then lasts at most about 70 ms, whatever the
+    // call's step count); the last launch interpolates W, G as well when
+    // they are asked for, and only it writes the outputs
     const bool off32 = b->P < ((int64_t)1 << 21) && !force_wide_offsets();  // table offsets in bytes fit 32 bits
-    const int steps = (int)r.steps;
+    const ProbeOut none{};
     const dim3 grid(ctas), block(RX_THREADS);
-    if (integ) {
-        if (off32)
-            k_batch_relax<8, true><<<grid, block, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z,
-                                                          steps, o);
-        else
-            k_batch_relax<8, false><<<grid, block, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z,
-                                                           steps, o);
-    } else if (off32) {
-        k_batch_relax<4, true><<<grid, block, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z, steps,
-                                                      o);
-    } else {
-        k_batch_relax<4, false><<<grid, block, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z, steps,
-                                                       o);
+    for (int k0 = 0; k0 < r.steps; k0 += RX_MAX_STEPS) {
+        const int n = std::min(RX_MAX_STEPS, (int)r.steps - k0);
+        const bool last = k0 + n == (int)r.steps;
+        const ProbeOut& oo = last ? o : none;
+        if (last && integ) {
+            if (off32)
+                k_batch_relax<8, true><<<grid, block, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z,
+                                                              n, oo);
+            else
+                k_batch_relax<8, false><<<grid, block, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z,
+                                                               n, oo);
+        } else if (off32) {
+            k_batch_relax<4, true><<<grid, block, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z, n,
+                                                          oo);
+        } else {
+            k_batch_relax<4, false><<<grid, block, 0, s>>>(rb, b->n, tiles, cells, nbr, tab, half, r.x, r.y, r.z, n,
+                                                           oo);
+        }
+        note_launch();
     }
-    note_launch();
     return cudaGetLastError();
 }
 

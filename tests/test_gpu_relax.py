@@ -190,6 +190,28 @@ def test_relax_end_to_end_oracle_chain(sg, small):
     batch.close()
 
 
+def test_relax_steps_beyond_one_launch(sg, small):
+    """A call runs at most 64 steps per launch: 70 steps in one call (64 + 6)
+    equal seven calls of 10 steps bit for bit, positions and outputs."""
+    bodies, grids, X, off, O = small
+    batch = sg.Batch(grids)
+    plan = sg.make_plan(4, 1, 20, 0.5)
+    Y70, o70 = _relax(sg, batch, X, off, 70, True, plan)
+    batch.reset()
+    batch.run(plan)
+    Y = [v.clone() for v in X]
+    out = {k: torch.empty_like(Y[0]) for k in OUTS}
+    for _ in range(7):
+        batch.relax(*Y, off, 10, 0.1, sweeps=False, out=out)
+    torch.cuda.synchronize()
+    for a in range(3):
+        assert torch.equal(Y[a], Y70[a])
+    for k in OUTS:
+        assert torch.equal(out[k], o70[k])
+    assert max(float((a - b).abs().max()) for a, b in zip(Y70, X)) > 0  # the particles moved
+    batch.close()
+
+
 def test_relax_replay_sweeps_and_empty_bodies(sg, small):
     bodies, grids, X, off, O = small
     batch = sg.Batch(grids)
