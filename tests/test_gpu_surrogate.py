@@ -101,6 +101,35 @@ def test_train_step_matches_oracle_adam(sg):
     assert np.max(np.abs(got - p)) <= 1e-6
 
 
+def test_many_ctas_gradient_and_adam(sg):
+    """70,000 rows are 547 CTAs of 128: the partial gradients are summed in
+    several blocks of 128 CTAs and a ragged rest.  Against the oracle; every
+    row twice gives the same mean loss and gradient (a block of partials
+    dropped or counted twice would not); the Adam kernel's own sum of the
+    partials gives the oracle's Adam step from the summed gradient."""
+    n = 70_000
+    par = si.mlp_init_params(15)
+    net = sg.MLP(par)
+    x, t = _data(8, n)
+    X = rows32(x)
+    T = torch.from_numpy(t.astype(np.float32)).cuda()
+    g, loss = net.loss_grad(X, T)
+    gd = g.cpu().numpy().astype(np.float64)
+    xr = X.float().cpu().numpy()[:, :27].astype(np.float64)
+    lref, gref = oracle.mlp_loss_grad(bf16_round(par), xr, t.astype(np.float32).astype(np.float64))
+    assert abs(loss.item() - lref) <= 2e-2 * lref
+    assert np.linalg.norm(gd - gref) <= 2e-2 * np.linalg.norm(gref)
+    g2, loss2 = net.loss_grad(torch.cat([X, X]), torch.cat([T, T]))
+    assert abs(loss2.item() - loss.item()) <= 1e-5 * loss.item()
+    assert np.linalg.norm(g2.cpu().numpy().astype(np.float64) - gd) <= 1e-5 * np.linalg.norm(gd)
+    net.train_step(X, T, None, 1e-3)
+    got = net.get_params().astype(np.float64)
+    p = par.astype(np.float64)
+    m, v = np.zeros_like(p), np.zeros_like(p)
+    oracle.adam_step(p, gd, m, v, lr=1e-3, step=1)
+    assert np.max(np.abs(got - p)) <= 1e-6
+
+
 def test_training_is_reproducible(sg):
     """The partial gradients of the CTAs are summed in a fixed order: two
     trainings from the same start on the same batches end bit for bit equal."""
