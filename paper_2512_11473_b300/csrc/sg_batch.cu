@@ -228,12 +228,13 @@ struct RelaxBody {
 
 constexpr int RX_THREADS = 256;  // particles per tile
 // Launch bounds of the relaxation kernel (each thread takes its particle
-// through the steps of a launch): three CTAs per SM, 80 registers without
-// spills.
-// 50 steps of 10^8 particles on 64 bodies: 53.4 ms; four CTAs (64
-// registers) 54.1 ms, five (48, spilling) 58.3 ms, six (40, spilling) 65.4
-// ms; one launch per step at six CTAs, 78.5 ms.
-constexpr int RX_MIN_CTAS = 3;
+// through the steps of a launch): four CTAs per SM, 64 registers (a 4-byte
+// spill in two instantiations).  50 steps of 10^8 particles on 64 bodies,
+// point-interleaved table: 51.4 ms, against 52.3 ms at three CTAs (80
+// registers, no spill).  With the scalar [P][8][64] table: three CTAs 53.4
+// ms, four 54.1, five (spilling) 58.3, six (spilling) 65.4; one launch per
+// step at six CTAs, 78.5 ms.
+constexpr int RX_MIN_CTAS = 4;
 constexpr int RX_TILES = 16;      // consecutive tiles a CTA walks (4: 54.0 ms at four CTAs per SM)
 constexpr int RX_MAX_STEPS = 64;  // steps per launch
 
@@ -480,9 +481,9 @@ cudaError_t record_relax(sg_batch* b, const sg_relax& r, int64_t tiles, cudaStre
     const bool off32 = b->P < ((int64_t)1 << 21) && !force_wide_offsets();  // table offsets in bytes fit 32 bits
     const ProbeOut none{};
     const dim3 grid(ctas), block(RX_THREADS);
-    for (int k0 = 0; k0 < r.steps; k0 += RX_MAX_STEPS) {
-        const int n = std::min(RX_MAX_STEPS, (int)r.steps - k0);
-        const bool last = k0 + n == (int)r.steps;
+    for (int64_t k0 = 0; k0 < r.steps; k0 += RX_MAX_STEPS) {
+        const int n = (int)std::min<int64_t>(RX_MAX_STEPS, r.steps - k0);
+        const bool last = k0 + n == r.steps;
         const ProbeOut& oo = last ? o : none;
         if (last && integ) {
             if (off32)
