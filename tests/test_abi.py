@@ -81,6 +81,15 @@ def test_null_arguments_rejected_without_gpu(libsg):
     assert libsg.sg_gradient(None) == 1
     libsg.sg_destroy.argtypes = [C.c_void_p]
     assert libsg.sg_destroy(None) == 1
+    # the cached autotuner and its key need a batch and a plan
+    libsg.sg_batch_autotune_cached.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_char_p, C.c_void_p]
+    assert libsg.sg_batch_autotune_cached(None, None, 1, b"x", None) == 1
+    libsg.sg_batch_autotune_key.argtypes = [C.c_void_p, C.c_void_p, C.c_char_p, C.c_int32]
+    assert libsg.sg_batch_autotune_key(None, None, C.create_string_buffer(8), 8) == 1
+    libsg.sg_autotune_cache_lookup.argtypes = [C.c_char_p, C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    assert libsg.sg_autotune_cache_lookup(None, b"k", None, None, None) == 1
+    libsg.sg_autotune_cache_store.argtypes = [C.c_char_p, C.c_char_p, C.c_int32, C.c_int32]
+    assert libsg.sg_autotune_cache_store(b"x", None, 4, 1) == 1
 
 
 def test_product_refuses_to_run_without_cuda(monkeypatch):
